@@ -1,0 +1,77 @@
+/*
+ * oracle.h - declarations of the plain FP64 CPU oracle (test infrastructure
+ * only; see oracle.c).  This header belongs to the oracle alone: the CUDA
+ * path never includes it.
+ *
+ * Layouts: CSR with int64 row pointers (n+1), int32 columns, float64 values;
+ * the Lanczos basis V and the Ritz vectors U are column-major (n rows, one
+ * column per vector); the small matrices T and Y are dense row-major m x m.
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORACLE_LARGEST_MAGNITUDE 0
+#define ORACLE_LARGEST_ALGEBRAIC 1
+
+#define ORACLE_BREAKDOWN_TOL 1e-12
+#define ORACLE_JACOBI_TOL 1e-16
+#define ORACLE_JACOBI_MAX_SWEEPS 100
+
+/* planted mistakes, for the test that shows the pins catch them */
+#define ORACLE_FAULT_NONE 0
+#define ORACLE_FAULT_BETA_INDEX 1
+#define ORACLE_FAULT_ALPHA_SIGN 2
+#define ORACLE_FAULT_NO_REORTH 3
+#define ORACLE_FAULT_JACOBI_SIGN 4
+#define ORACLE_FAULT_RITZ_TRANSPOSE 5
+#define ORACLE_FAULT_SELECT_ALGEBRAIC 6
+#define ORACLE_FAULT_SPMV_SKIP_LAST 7
+#define ORACLE_FAULT_NO_V1_NORMALISE 8
+
+void oracle_set_fault(int kind);
+int oracle_get_fault(void);
+int oracle_num_threads(void);
+
+/* Algorithm 1, SpMV step: y = M x (each row summed left to right) */
+void oracle_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                 const double* x, double* y);
+double oracle_spmv_row(const int64_t* rp, const int32_t* ci, const double* val,
+                       const double* x, int64_t r);
+
+/* Algorithm 1: m Lanczos steps with one MGS reorthogonalisation pass each.
+   alpha[m], beta[m+1] (beta[0] = beta_1 = 0, beta[i] = beta_{i+1}),
+   V n x m column-major; w_out (optional, n) receives the last unnormalised
+   v_nxt, whose norm is beta[m].  Returns 0 on success. */
+int oracle_lanczos(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                   const double* v1_raw, int32_t m, uint64_t seed, double tol,
+                   double* alpha, double* beta, double* V, double* w_out,
+                   int32_t* restarts_out);
+
+/* cyclic-by-row Jacobi: T (m x m, symmetric, row-major) is diagonalised in
+   place, Y receives the eigenvectors (columns).  Returns 0 if converged. */
+int oracle_jacobi(int32_t m, double* T, double* Y, double tol, int32_t max_sweeps,
+                  int32_t* sweeps_out);
+
+void oracle_select_topk(int32_t m, const double* theta, int32_t K, int32_t which,
+                        int32_t* idx);
+
+/* U[:,k] = sign_k * V Y[:, idx[k]] (U n x K column-major) */
+void oracle_ritz(int64_t n, int32_t m, const double* V, const double* Y, int32_t K,
+                 const int32_t* idx, double* U);
+
+/* whole solve; info[0] = restarts, info[1] = Jacobi sweeps, info[2] = Jacobi rc.
+   U, residuals, alpha_out, beta_out and info may be NULL. */
+int oracle_topk_eigs(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                     const double* v1_raw, int32_t K, int32_t m, int32_t which, uint64_t seed,
+                     double* eigvals, double* U, double* residuals, double* alpha_out,
+                     double* beta_out, int32_t* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

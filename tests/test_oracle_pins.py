@@ -1,0 +1,285 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each pin checks one oracle routine against a closed form, a brute-force
+computation, a hand-worked example or an invariant of the mathematics.  The
+last test plants, one at a time, a plausible mistake in the oracle and checks
+that at least one pin fails for each.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")
+
+
+def _dense_csr(d):
+    return synth.from_dense(np.asarray(d, dtype=np.float64))
+
+
+# ---------------------------------------------------------------------------
+# pin functions: return None when the pin holds, else a message
+# ---------------------------------------------------------------------------
+
+def pin_spmv_brute_force():
+    """SpMV against a dense mat-vec (brute force), including empty rows."""
+    A = synth.uniform_sym(300, 3, seed=7)
+    # knock out a few rows/cols to create empty rows
+    d = A.to_dense()
+    d[[5, 17, 299], :] = 0.0
+    d[:, [5, 17, 299]] = 0.0
+    B = synth.from_dense(d)
+    x = synth.uniform_pm1(300, 3, 0)
+    y = oracle.spmv(B, x)
+    ref = d @ x
+    err = np.max(np.abs(y - ref)) / np.max(np.abs(ref))
+    if err > 1e-14:
+        return f"spmv rel err {err}"
+    rows = [0, 5, 100, 299]
+    ys = oracle.spmv_rows(B, x, rows)
+    if np.max(np.abs(ys - ref[rows])) > 1e-13:
+        return "spmv_rows mismatch"
+    return None
+
+
+def pin_hand_examples():
+    """Alpha/beta and eigenvalues of the hand-worked examples."""
+    cases = json.load(open(GOLDEN))["cases"]
+    for c in cases:
+        A = _dense_csr(c["dense"])
+        m = c["m"]
+        r = oracle.lanczos(A, np.array(c["v1"], dtype=float), m)
+        if "alpha" in c:
+            if np.max(np.abs(r.alpha - np.array(c["alpha"]))) > 1e-14:
+                return f"{c['name']}: alpha {r.alpha}"
+            if np.max(np.abs(r.beta - np.array(c["beta"]))) > 1e-14:
+                return f"{c['name']}: beta {r.beta}"
+        if "alpha_first" in c:
+            if abs(r.alpha[0] - c["alpha_first"]) > 1e-14:
+                return f"{c['name']}: alpha_1 {r.alpha[0]}"
+            if abs(r.alpha.sum() - c["alpha_sum"]) > 1e-13:
+                return f"{c['name']}: trace {r.alpha.sum()}"
+        res = oracle.topk_eigs(A, m, m, np.array(c["v1"], dtype=float))
+        if "eigenvalues_desc" in c:
+            got = np.sort(res.eigvals)[::-1]
+            if np.max(np.abs(got - np.array(c["eigenvalues_desc"]))) > 1e-13:
+                return f"{c['name']}: eigenvalues {got}"
+        if "eigenvalues_lm" in c:
+            if np.max(np.abs(res.eigvals - np.array(c["eigenvalues_lm"]))) > 1e-13:
+                return f"{c['name']}: LM order {res.eigvals}"
+    return None
+
+
+def pin_jacobi_toeplitz():
+    """Tridiagonal Toeplitz (a, b): eigenvalues a + 2 b cos(pi k / (m+1))."""
+    for m, a, b in [(1, 0.7, 0.0), (2, 1.0, -0.5), (7, 2.0, -1.0), (24, -0.3, 0.9), (48, 1.5, 0.25)]:
+        T = np.diag(np.full(m, a)) + np.diag(np.full(m - 1, b), 1) + np.diag(np.full(m - 1, b), -1)
+        theta, Y, _, conv = oracle.jacobi(T)
+        if not conv:
+            return f"jacobi m={m} not converged"
+        exact = np.sort(a + 2 * b * np.cos(np.pi * np.arange(1, m + 1) / (m + 1)))
+        err = np.max(np.abs(np.sort(theta) - exact))
+        if err > 1e-13 * max(1.0, np.linalg.norm(T)):
+            return f"jacobi toeplitz m={m} err {err}"
+    return None
+
+
+def pin_jacobi_2x2():
+    """2x2 closed form (a+c)/2 +- sqrt(((a-c)/2)^2 + b^2)."""
+    for a, b, c in [(2.0, 1.0, 2.0), (1.0, 3.0, -2.0), (5.0, 1e-9, 5.0), (0.0, -1.0, 0.0)]:
+        theta, Y, _, _ = oracle.jacobi(np.array([[a, b], [b, c]]))
+        mid, rad = (a + c) / 2, math.hypot((a - c) / 2, b)
+        if np.max(np.abs(np.sort(theta) - np.array([mid - rad, mid + rad]))) > 1e-14 * (abs(mid) + rad):
+            return f"jacobi 2x2 {(a, b, c)} -> {theta}"
+        T = np.array([[a, b], [b, c]])
+        if np.max(np.abs(T @ Y - Y * theta)) > 1e-14 * (abs(mid) + rad):
+            return "jacobi 2x2 eigenvectors"
+    return None
+
+
+def pin_jacobi_random():
+    """Random symmetric matrices vs a library eigensolver (test-only)."""
+    rng = np.random.default_rng(11)
+    for m in [3, 16, 33, 64]:
+        G = rng.standard_normal((m, m))
+        T = (G + G.T) / 2
+        theta, Y, _, conv = oracle.jacobi(T)
+        nrm = np.linalg.norm(T)
+        if not conv:
+            return f"jacobi random m={m} no convergence"
+        if np.max(np.abs(np.sort(theta) - np.linalg.eigvalsh(T))) > 1e-13 * nrm:
+            return f"jacobi random m={m} eigenvalues"
+        if np.max(np.abs(T @ Y - Y * theta)) > 1e-13 * nrm:
+            return f"jacobi random m={m} residual"
+        if np.max(np.abs(Y.T @ Y - np.eye(m))) > 1e-13:
+            return f"jacobi random m={m} orthogonality"
+    return None
+
+
+def pin_lanczos_path_full():
+    """Path Laplacian, full Krylov space: 2 - 2 cos(pi k / n)."""
+    n = 60
+    A = synth.path_laplacian(n)
+    v1 = synth.start_vector(n, 5)
+    res = oracle.topk_eigs(A, n, n, v1)
+    exact = np.sort(2 - 2 * np.cos(np.pi * np.arange(n) / n))
+    err = np.max(np.abs(np.sort(res.eigvals) - exact))
+    if err > 1e-12 * 4:
+        return f"path laplacian err {err}"
+    return None
+
+
+def pin_lanczos_cycle_full():
+    """Cycle Laplacian: 2 - 2 cos(2 pi k / n) with multiplicities (needs restarts)."""
+    n = 40
+    A = synth.cycle_laplacian(n)
+    v1 = synth.start_vector(n, 9)
+    res = oracle.topk_eigs(A, n, n, v1)
+    exact = np.sort(2 - 2 * np.cos(2 * np.pi * np.arange(n) / n))
+    err = np.max(np.abs(np.sort(res.eigvals) - exact))
+    if res.restarts < 1:
+        return "cycle laplacian: no restart happened"
+    if err > 1e-12 * 4:
+        return f"cycle laplacian err {err}"
+    return None
+
+
+def pin_lanczos_diagonal_trace():
+    """Diagonal matrix, m = n: sum(alpha) = trace and Ritz values = diagonal."""
+    d = np.linspace(-3.0, 5.0, 50) + 0.01 * np.arange(50) ** 1.5
+    A = synth.diagonal(d)
+    v1 = synth.start_vector(50, 3)
+    r = oracle.lanczos(A, v1, 50)
+    if abs(r.alpha.sum() - d.sum()) > 1e-12 * np.abs(d).sum():
+        return f"trace {r.alpha.sum()} vs {d.sum()}"
+    theta, _, _, _ = oracle.jacobi(r.T())
+    if np.max(np.abs(np.sort(theta) - np.sort(d))) > 1e-12 * np.abs(d).max():
+        return "diagonal ritz values"
+    return None
+
+
+def pin_lanczos_dense_bruteforce():
+    """Random sparse symmetric n <= 200, m = n: eigenvalues, V^T V, residuals."""
+    for n, per_row, seed in [(150, 3, 1), (200, 2, 2)]:
+        A = synth.uniform_sym(n, per_row, seed)
+        d = A.to_dense()
+        v1 = synth.start_vector(n, seed)
+        res = oracle.topk_eigs(A, n, n, v1)
+        lam = np.linalg.eigvalsh(d)
+        nrm = np.max(np.abs(lam))
+        if np.max(np.abs(np.sort(res.eigvals) - lam)) > 1e-12 * nrm:
+            return f"dense brute force n={n}"
+        r = oracle.lanczos(A, v1, n)
+        if np.max(np.abs(r.V.T @ r.V - np.eye(n))) > 1e-12:
+            return f"V^T V n={n}"
+        top = np.argsort(-np.abs(res.eigvals))[:8]
+        rel = res.residuals[top] / np.abs(res.eigvals[top])
+        if np.max(rel) > 1e-10:
+            return f"relative residual {np.max(rel)}"
+    return None
+
+
+def pin_lanczos_partial_invariants():
+    """m << n: T = V^T A V, A V - V T = w e_m^T, V^T V = I, residual identity, interlacing."""
+    n, m = 2000, 20
+    A = synth.uniform_sym(n, 5, 21)
+    d = A.to_dense()
+    v1 = synth.start_vector(n, 21)
+    r = oracle.lanczos(A, v1, m)
+    V, T = r.V, r.T()
+    nrm = np.linalg.norm(d, 2)
+    if np.max(np.abs(V[:, 0] - v1 / np.linalg.norm(v1))) > 1e-15:
+        return "v_1 is not the normalised start vector"
+    if np.max(np.abs(V.T @ d @ V - T)) > 1e-12 * nrm:
+        return "T != V^T A V"
+    R = d @ V - V @ T
+    R[:, -1] -= r.w_last
+    if np.max(np.abs(R)) > 1e-12 * nrm:
+        return "Lanczos relation"
+    if abs(np.linalg.norm(r.w_last) - r.beta[m]) > 1e-14 * nrm:
+        return "beta_{m+1} != ||w||"
+    if np.max(np.abs(V.T @ V - np.eye(m))) > 1e-12:
+        return "orthogonality"
+    theta, Y, _, _ = oracle.jacobi(T)
+    lam = np.linalg.eigvalsh(d)
+    if theta.max() > lam[-1] + 1e-12 * nrm or theta.min() < lam[0] - 1e-12 * nrm:
+        return "interlacing"
+    res = oracle.topk_eigs(A, 6, m, v1)
+    idx = oracle.select_topk(theta, 6)
+    for k in range(6):
+        ident = r.beta[m] * abs(Y[m - 1, idx[k]])
+        if abs(res.residuals[k] - ident) > 1e-10 * nrm:
+            return f"residual identity k={k}: {res.residuals[k]} vs {ident}"
+    return None
+
+
+def pin_selection():
+    """Largest in modulo: |theta| descending, positive first on ties, then index."""
+    theta = np.array([0.5, -2.0, 2.0, 1.0, -1.0, 0.0, -0.5])
+    lm = oracle.select_topk(theta, 7, oracle.LARGEST_MAGNITUDE)
+    if list(lm) != [2, 1, 3, 4, 0, 6, 5]:
+        return f"LM order {list(lm)}"
+    la = oracle.select_topk(theta, 7, oracle.LARGEST_ALGEBRAIC)
+    if list(la) != [2, 3, 0, 5, 6, 4, 1]:
+        return f"LA order {list(la)}"
+    return None
+
+
+def pin_ritz_vectors():
+    """Full Krylov: Ritz vectors are eigenvectors (vs a library, up to sign)."""
+    n = 80
+    A = synth.uniform_sym(n, 4, 33)
+    d = A.to_dense()
+    v1 = synth.start_vector(n, 33)
+    res = oracle.topk_eigs(A, 5, n, v1)
+    lam, W = np.linalg.eigh(d)
+    for k in range(5):
+        u = res.eigvecs[:, k]
+        j = np.argmin(np.abs(lam - res.eigvals[k]))
+        c = abs(np.dot(u, W[:, j])) / np.linalg.norm(u)
+        if abs(c - 1) > 1e-10:
+            return f"ritz vector {k} cos {c}"
+        if abs(np.linalg.norm(u) - 1) > 1e-12:
+            return "ritz vector norm"
+    # R9 sign convention on a direct call
+    r = oracle.lanczos(A, v1, 10)
+    theta, Y, _, _ = oracle.jacobi(r.T())
+    idx = oracle.select_topk(theta, 3)
+    U = oracle.ritz(r.V, Y, idx)
+    for k in range(3):
+        y = Y[:, idx[k]]
+        s = np.sign(y[np.argmax(np.abs(y))])
+        if np.max(np.abs(U[:, k] - s * (r.V @ y))) > 1e-13:
+            return "ritz contraction"
+    return None
+
+
+PINS = [pin_spmv_brute_force, pin_hand_examples, pin_jacobi_toeplitz, pin_jacobi_2x2,
+        pin_jacobi_random, pin_lanczos_path_full, pin_lanczos_cycle_full,
+        pin_lanczos_diagonal_trace, pin_lanczos_dense_bruteforce,
+        pin_lanczos_partial_invariants, pin_selection, pin_ritz_vectors]
+
+
+@pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
+def test_pin(pin):
+    msg = pin()
+    assert msg is None, msg
+
+
+@pytest.mark.parametrize("name", [k for k in oracle.FAULTS if k != "none"])
+def test_planted_mistake_is_caught(name):
+    failures = []
+    with oracle.fault(name):
+        for pin in PINS:
+            try:
+                msg = pin()
+            except Exception as e:  # a crash also counts as caught
+                msg = f"raised {type(e).__name__}"
+            if msg is not None:
+                failures.append(pin.__name__)
+    assert failures, f"planted mistake {name!r} passed every pin"
