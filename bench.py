@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Top-K sparse eigensolver.
+
+Workload (default): symmetric R-MAT graph, n = 2^24, edge factor 8 (about
+268M stored non-zeros after symmetrisation), (a, b, c, d) = (0.57, 0.19, 0.19,
+0.05), no self-loops, normalised adjacency D^-1/2 A D^-1/2, seed 1; top K = 24
+eigenpairs with 2K = 48 Lanczos steps.  Synthetic stand-in for the paper's
+SuiteSparse / GAP graphs.
+
+One step = one complete Top-K solve (Lanczos with full reorthogonalisation,
+Jacobi on T, Ritz vectors) in the chosen mixed precision FDF (binary32
+values and basis, double-float arithmetic), launched as one CUDA graph with
+the matrix already resident in HBM.  The plain FP64 path (DDD) and the K = 8,
+m = 16 solves are timed alongside and reported as extra keys.
+
+--impl reference times the CPU oracle (plain FP64 C) on a bounded sample of
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "top-K solve ms, SpMV GB/s vs FP64 plain at fixed error; solves/s, p99 ms"
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--scale", type=int, default=24)
+    p.add_argument("--edge-factor", type=int, default=8)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--K", type=int, default=24)
+    p.add_argument("--m", type=int, default=48)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the DDD and K=8 timings")
+    p.add_argument("--oracle-steps", type=int, default=6)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+def make_inputs(args):
+    import synth
+    t0 = time.perf_counter()
+    A = synth.rmat_sym(args.scale, args.edge_factor, args.seed)
+    gen_s = time.perf_counter() - t0
+    v1 = synth.start_vector(A.n, args.seed)
+    return A, v1, gen_s
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(A, v1, K, m, steps, seed):
+    """Time the oracle's Lanczos for the first `steps` steps on the full matrix
+    plus one SpMV, and extrapolate to the m-step solve with
+    t_step(i) = t_spmv + (i+1) t_col, t_ritz = K m t_col / 2."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.spmv(A, v1)
+    t_spmv = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.lanczos(A, v1, steps, seed=seed)
+    t_s = time.perf_counter() - t0
+    cols = steps * (steps + 1) / 2
+    t_col = max(t_s - steps * t_spmv, 0.0) / cols
+    est = m * t_spmv + t_col * m * (m + 1) / 2 + K * m * t_col / 2
+    sample = (f"oracle Lanczos, first {steps} of {m} steps on the full matrix ({t_s:.1f} s) "
+              f"+ one SpMV ({t_spmv:.2f} s), extrapolated to the {m}-step solve + Ritz "
+              f"with t_step(i) = t_SpMV + (i+1) t_MGS-column")
+    return est * 1e3, sample, oracle.num_threads(), t_s + t_spmv
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    A, v1, _ = make_inputs(args)
+    ms, sample, cores, spent = oracle_sample(A, v1, args.K, args.m, args.oracle_steps, args.seed)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(args, A),
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def workload_config(args, A):
+    return {
+        "workload": f"rmat{args.scale}_ef{args.edge_factor}_normadj_seed{args.seed}"
+                    f"_K{args.K}_m{args.m}",
+        "n": int(A.n), "nnz": int(A.nnz), "K": args.K, "krylov_steps": args.m,
+        "rmat": [0.57, 0.19, 0.19, 0.05],
+        "precision": "FDF: f32 values + f32 Lanczos basis, double-float arithmetic, "
+                     "f64 cross-block sums and Jacobi",
+        "l2": "no flush: inputs larger than L2 (CSR and basis are several GB each)",
+        "parallelism": "replicas",
+    }
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def time_plan(plan, steps, warmup, world, want_vectors=True):
+    import torch
+    ev = torch.empty(plan.K, dtype=torch.float64, device="cuda")
+    U = torch.empty((plan.K, plan.n), dtype=torch.float64, device="cuda") if want_vectors else None
+    for _ in range(warmup):
+        plan.launch(ev, U)
+    torch.cuda.synchronize()
+    plan.status()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        plan.launch(ev, U)
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / steps
+    plan.status()
+    return ms, ev.cpu().numpy(), U
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2201_07498_gb300 as te
+    torch.cuda.set_device(local)
+    te.load_library(build_if_missing=True)
+    A, v1, gen_s = make_inputs(args)
+    K, m = args.K, args.m
+
+    csr_f = te.CSR.from_host(A, "fdf")
+    plan_f = te.Plan(csr_f, K, m, "fdf", seed=args.seed)
+    kernels_per_solve = plan_f.kernel_count + 1  # + the per-solve set-up kernel
+
+    peak, peak_kind = measured_peaks()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_f, ev_f, _ = time_plan(plan_f, args.steps, args.warmup, world)
+    clk = clocks.stop()
+    ms_f_max = max_over_ranks(ms_f, world)
+
+    # per-kernel durations (CUDA events on the launch stream, one un-graphed solve)
+    prof = plan_f.profile()
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    d_ms, d_n, d_bytes = kinds[dom]
+    achieved = d_bytes / (d_ms * 1e-3) / 1e9
+    sp_ms, sp_n, sp_bytes = prof["spmv"]
+    spmv_gbs = sp_bytes / (sp_ms * 1e-3) / 1e9
+
+    extras = {}
+    if not args.no_extras:
+        csr_d = te.CSR.from_host(A, "ddd")
+        plan_d = te.Plan(csr_d, K, m, "ddd", seed=args.seed)
+        ms_d, ev_d, _ = time_plan(plan_d, max(2, args.steps // 2), args.warmup, world)
+        prof_d = plan_d.profile()
+        spd_ms, _, spd_bytes = prof_d["spmv"]
+        rel = float(np.max(np.abs(ev_f - ev_d) / np.abs(ev_d)))
+        extras.update({
+            "fp64_plain_solve_ms": ms_d,
+            "speedup_vs_fp64_plain": ms_d / ms_f,
+            "spmv_gbs": spmv_gbs,
+            "spmv_gbs_fp64_plain": spd_bytes / (spd_ms * 1e-3) / 1e9,
+            "rel_eig_err_vs_fp64_plain": rel,
+        })
+        del plan_d
+        Ks, ms_ = max(1, K // 3), max(2, m // 3)
+        plan_fs = te.Plan(csr_f, Ks, ms_, "fdf", seed=args.seed)
+        ms_fs, _, _ = time_plan(plan_fs, args.steps, args.warmup, world)
+        plan_ds = te.Plan(csr_d, Ks, ms_, "ddd", seed=args.seed)
+        ms_ds, _, _ = time_plan(plan_ds, max(2, args.steps // 2), args.warmup, world)
+        extras[f"solve_ms_K{Ks}_m{ms_}"] = {"fdf": ms_fs, "ddd": ms_ds}
+        del plan_fs, plan_ds, csr_d
+    else:
+        extras["spmv_gbs"] = spmv_gbs
+
+    # end to end through the public API: host (pinned) CSR in, host results out
+    host = te.CSR.from_host(A, "fdf", device="cpu", pin=True)
+    h2d = host.row_ptr.numel() * 8 + host.col.numel() * 4 + host.val.numel() * 4
+    d2h = K * 8 + A.n * K * 8
+    e2e_ms = []
+    ev_out = torch.empty(K, dtype=torch.float64).pin_memory()
+    U_out = torch.empty((K, A.n), dtype=torch.float64).pin_memory()
+    for it in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(s)
+        te.topk_eigs(host, K, m, "fdf", seed=args.seed, out=(ev_out, U_out))
+        a1.record(s)
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_ms.append(a0.elapsed_time(a1))
+    e2e = statistics.median(e2e_ms)
+    e2e = max_over_ranks(e2e, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms_o, sample, cores, _ = oracle_sample(A, v1, K, m, args.oracle_steps, args.seed)
+        cpu = {"value": ms_o, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": ms_f_max, "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_f_max,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/df64", "data": "synthetic",
+            "config": workload_config(args, A),
+            "solves_per_s": 1e3 * world / ms_f_max,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "launches_per_solve": d_n, "ms_per_solve": d_ms,
+                         "algorithmic_bytes_per_solve": d_bytes},
+            "kernels": {k: {"ms": v[0], "launches": v[1], "gbs": (v[2] / (v[0] * 1e-3) / 1e9
+                                                                  if v[0] > 0 and v[2] > 0
+                                                                  else None)}
+                        for k, v in kinds.items()},
+            "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(kernels_per_solve * args.steps),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "generate_s": gen_s,
+        }
+        out.update(extras)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

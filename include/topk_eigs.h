@@ -1,0 +1,215 @@
+/*
+ * topk_eigs.h - C ABI of the GB300 (sm_103a) Top-K sparse eigensolver.
+ *
+ * Method: Sgherzi, Parravicini & Santambrogio, "A Mixed Precision, Multi-GPU
+ * Design for Large-scale Top-K Sparse Eigenproblems", arXiv 2201.07498.
+ * A Lanczos phase (Algorithm 1, Section III) builds an orthonormal Krylov
+ * basis V = [v_1..v_m] of the symmetric matrix M from an L2-normalised
+ * random start vector, with full reorthogonalisation, and a tridiagonal
+ * T = tridiag(alpha_1..alpha_m; beta_2..beta_m); a Jacobi phase (Section III,
+ * Fig. 1) diagonalises T; eigenvectors of M are V times the eigenvectors of
+ * T (Section III).  The K eigenpairs "largest in modulo" (Section I) are
+ * returned.  Precision follows Section III-A: matrix values, arithmetic and
+ * vector storage can differ ("FDF" = float values, double arithmetic, float
+ * vectors; "DDD" = all double).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a te_status; nothing aborts.  te_last_error() gives a
+ *     thread-local message for the last failing call on this thread.
+ *   - The caller owns every buffer it passes; the library never frees them.
+ *     Work memory is allocated inside the call (or the plan) and freed before
+ *     return (or at te_plan_destroy).
+ *   - Device pointers are CUDA device (or managed) memory of the current
+ *     device.  "Host" outputs may be pageable or pinned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *     return results to the host synchronise that stream once, at the end.
+ *   - Matrices are square (n x n), symmetric (Lanczos requires it; symmetry
+ *     is not checked), stored as CSR with int64 row pointers (n+1 entries,
+ *     row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz) and int32 column
+ *     indices in [0, n).  Column order within a row is free.
+ *   - Dense results are column-major: eigenvector k occupies
+ *     eigvecs[k*n .. k*n+n-1].
+ *   - On any error the outputs are left untouched.
+ */
+#ifndef TOPK_EIGS_H
+#define TOPK_EIGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TE_OK = 0,
+  TE_ERR_INVALID_ARG = 1,    /* bad sizes, NULL pointers, malformed CSR */
+  TE_ERR_OUT_OF_MEMORY = 2,  /* device allocation failed or over budget */
+  TE_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  TE_ERR_BREAKDOWN = 4,      /* the Krylov space could not be extended */
+  TE_ERR_NOT_CONVERGED = 5,  /* the Jacobi sweeps hit their limit */
+  TE_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+  TE_ERR_UNSUPPORTED = 7     /* a valid but unimplemented combination */
+} te_status;
+
+/* element types (Section III-A's precision letters) */
+typedef enum { TE_F64 = 0, TE_F32 = 1, TE_BF16 = 2, TE_FP8_E4M3 = 3 } te_dtype;
+
+/* (matrix values, arithmetic, vector storage).  Supported:
+ *   DDD = {TE_F64, TE_F64, TE_F64}: plain binary64 on the FP64 pipe.
+ *   FDF = {TE_F32, TE_F64, TE_F32}: binary32 matrix values and Lanczos
+ *         vectors; every product and sum of the SpMV, the
+ *         reorthogonalisation and the Ritz contraction is carried in
+ *         double-float (about 48 significant bits) on the FP32 pipes, and
+ *         cross-block sums in binary64. */
+typedef struct {
+  int32_t values;
+  int32_t arithmetic;
+  int32_t vectors;
+} te_precision;
+
+#define TE_DEVICE 0 /* CSR arrays live in device memory */
+#define TE_HOST 1   /* CSR arrays live in host memory (copied in by the call) */
+
+typedef struct {
+  int64_t n;              /* rows = columns, >= 1, < 2^31 */
+  int64_t nnz;            /* stored entries, >= 0 */
+  const int64_t* row_ptr; /* n + 1 */
+  const int32_t* col_idx; /* nnz */
+  const void* values;     /* nnz elements of type precision.values */
+  const float* row_scale; /* reserved for scaled 8-bit values; must be NULL */
+  int32_t where;          /* TE_DEVICE or TE_HOST */
+} te_csr;
+
+#define TE_WHICH_LARGEST_MAGNITUDE 0 /* |theta| descending; ties: positive, then index */
+#define TE_WHICH_LARGEST_ALGEBRAIC 1 /* theta descending; ties: lower index */
+
+typedef struct {
+  uint64_t seed;    /* SplitMix64 seed: start vector = stream 0, restart r = stream r */
+  const double* v1; /* optional raw start vector (n, device); NULL = draw from seed */
+  int32_t which;    /* TE_WHICH_* */
+  int32_t use_graph; /* plans: capture the whole solve as one CUDA graph (default 1) */
+  size_t device_budget_bytes; /* 0 = no limit on the work memory */
+} te_options;
+
+/* Fill `opt` with the defaults: seed 0, v1 NULL, largest magnitude, graphs on,
+ * no budget. */
+void te_default_options(te_options* opt);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char* te_last_error(void);
+
+/* Static name of a status code. */
+const char* te_status_string(te_status s);
+
+/* Bytes of device work memory a plan for (A, K, krylov_steps, p) allocates,
+ * excluding a device copy of a host CSR.  Returns 0 for invalid arguments. */
+size_t te_workspace_bytes(const te_csr* A, int32_t K, int32_t krylov_steps, te_precision p);
+
+/*
+ * One complete Top-K solve (Algorithm 1 + Jacobi + Ritz vectors, Section III):
+ *   K            number of eigenpairs, 1 <= K <= krylov_steps
+ *   krylov_steps m, the Lanczos steps (size of T), K <= m <= min(n, 64)
+ *   eigvals      K doubles, host or device: the selected Ritz values
+ *   eigvecs      n*K doubles (column-major), host or device, or NULL to skip
+ *                the Ritz-vector contraction
+ *   residuals    K doubles, host or device, or NULL: the Ritz residual
+ *                estimates |beta_{m+1} * y_k[m]| (= ||M u_k - theta_k u_k|| in
+ *                exact arithmetic)
+ * With A->where == TE_HOST the matrix is copied to the device inside the call.
+ * Synchronises `stream` before returning.  TE_ERR_BREAKDOWN is returned (with
+ * all outputs written) when a restart could not produce a new direction.
+ */
+te_status te_topk_eigs(const te_csr* A, int32_t K, int32_t krylov_steps, te_precision p,
+                       const te_options* opt, double* eigvals, double* eigvecs,
+                       double* residuals, void* stream);
+
+/* ---- plans: reuse the analysis, work memory and CUDA graph across solves ---- */
+typedef struct te_plan te_plan;
+
+/* Analyse A (row partition for the SpMV, CSR validation), allocate the work
+ * memory and, with opt->use_graph, capture the solve as a CUDA graph.  A
+ * TE_HOST matrix is copied into plan-owned device memory; a TE_DEVICE matrix
+ * is referenced (it must outlive the plan and not change).  *out is NULL on
+ * error. */
+te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_precision p,
+                         const te_options* opt, void* stream, te_plan** out);
+
+/* Run one solve on `stream`.  v1: optional raw start vector (n, device) that
+ * overrides the plan's option for this solve; outputs as in te_topk_eigs. */
+te_status te_plan_solve(te_plan* plan, const double* v1, double* eigvals, double* eigvecs,
+                        double* residuals, void* stream);
+
+/* Launch one solve on `stream` without waiting for it: eigenvalues go to the
+ * device buffer `eigvals_dev` (K doubles) and Ritz vectors to `eigvecs_dev`
+ * (or NULL).  The caller synchronises; te_plan_status then reports the
+ * device-side status of the last finished solve. */
+te_status te_plan_launch(te_plan* plan, const double* v1, double* eigvals_dev,
+                         double* eigvecs_dev, void* stream);
+te_status te_plan_status(te_plan* plan);
+
+/* Kernel kinds reported by te_plan_profile. */
+#define TE_KIND_SPMV 0       /* SpMV of Algorithm 1 (with the long-row finalize) */
+#define TE_KIND_DOT 1        /* first Gram-Schmidt sweep: dots against the basis */
+#define TE_KIND_AXPY_DOT 2   /* first update fused with the second sweep's dots */
+#define TE_KIND_AXPY_STORE 3 /* second update, norms (beta), next basis vector */
+#define TE_KIND_RESTART 4    /* restart passes (return at once unless a breakdown) */
+#define TE_KIND_JACOBI 5     /* Jacobi phase, selection, Ritz coefficients */
+#define TE_KIND_RITZ 6       /* Ritz-vector contraction V * Y */
+#define TE_KIND_OTHER 7      /* solve set-up and start-vector pass */
+#define TE_NUM_KINDS 8
+
+/* Run one solve on `stream` without the CUDA graph, timing every kernel with
+ * CUDA events recorded on `stream`, and synchronise.  For each kind k:
+ * ms[k] = summed kernel time, launches[k] = kernel count, bytes[k] = the
+ * algorithmic bytes those launches must move (SpMV: nnz*(4+value bytes) +
+ * 8(n+1) + n*(vector bytes) + 8n; basis passes: the basis columns they read
+ * plus the n-vectors they read and write; Ritz: m basis columns + 8nK).
+ * Arrays have TE_NUM_KINDS entries; any may be NULL. */
+te_status te_plan_profile(te_plan* plan, double* ms, int32_t* launches, double* bytes,
+                          void* stream);
+
+/* Number of kernels one solve launches (graph nodes when captured). */
+int32_t te_plan_kernel_count(const te_plan* plan);
+
+void te_plan_destroy(te_plan* plan);
+
+/* ---- single phases, for testing and for callers composing their own solver ---- */
+
+/* y = M x with the solver's SpMV (Algorithm 1, SpMV step).  x: n elements of
+ * type p.vectors (device); y: n doubles (device).  A must be TE_DEVICE. */
+te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, void* stream);
+
+/* The Lanczos phase alone (Algorithm 1): writes alpha[0..m-1] and
+ * beta[0..m] (beta[0] = beta_1 = 0, beta[i] = beta_{i+1}; host arrays) and,
+ * if `basis` is not NULL, the basis V as n x m doubles (device, column-major).
+ * `restarts` (host, may be NULL) receives the number of breakdown restarts. */
+te_status te_lanczos(const te_csr* A, int32_t krylov_steps, te_precision p,
+                     const te_options* opt, double* alpha, double* beta, double* basis,
+                     int32_t* restarts, void* stream);
+
+/* The Jacobi phase alone on T = tridiag(alpha; beta[1..m-1]) (Section III):
+ * alpha (m) and beta (m+1, beta[0] ignored) are device arrays; theta
+ * receives all m eigenvalues in selection order (`which`), Y (m x m,
+ * column-major, device) the matching unit eigenvectors of T, each with its
+ * largest-magnitude entry positive.  sweeps (host, may be NULL) receives the
+ * number of sweeps.  m <= 64. */
+te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, int32_t which,
+                          double* theta, double* Y, int32_t* sweeps, void* stream);
+
+/* Host-side analysis behind the SpMV (no GPU needed; row_ptr in host memory).
+ * Rows are packed, in order, into blocks of at most tile_nnz non-zeros and
+ * 1024 rows (tile_nnz = 2048 for DDD, 4096 for FDF); a row with more than
+ * tile_nnz/4 non-zeros is "long" and cut into chunks of tile_nnz non-zeros.
+ * Writes the three counts; if `blocks` is not NULL it receives 2*nblocks
+ * int32 (first row, one past last row) and if `chunks` is not NULL it
+ * receives 3*nchunks int64 (first nnz, one past last nnz, row).  Returns
+ * TE_ERR_INVALID_ARG for a malformed row_ptr. */
+te_status te_spmv_partition(const int64_t* row_ptr, int64_t n, int64_t nnz, te_precision p,
+                            int64_t* nblocks, int64_t* nchunks, int64_t* nlong_rows,
+                            int32_t* blocks, int64_t* chunks);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOPK_EIGS_H */

@@ -1,0 +1,355 @@
+"""Thin Python binding of the GB300 Top-K sparse eigensolver C ABI.
+
+The arithmetic runs in ``libtopk_eigs.so`` (hand-written CUDA for sm_103a,
+declared in ``include/topk_eigs.h``); this module only marshals arguments with
+ctypes.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library is missing, importing the solver entry points raises.
+
+Method: Sgherzi, Parravicini & Santambrogio, "A Mixed Precision, Multi-GPU
+Design for Large-scale Top-K Sparse Eigenproblems" (arXiv 2201.07498):
+Lanczos with full reorthogonalisation (Algorithm 1), Jacobi on the
+tridiagonal T, Ritz vectors V*Y (Section III), mixed precision (Section III-A).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import _build
+
+__all__ = ["CSR", "Plan", "TEError", "topk_eigs", "spmv", "lanczos", "tridiag_eigs",
+           "spmv_partition", "library_path", "load_library", "PRECISIONS"]
+
+TE_F64, TE_F32, TE_BF16, TE_FP8_E4M3 = 0, 1, 2, 3
+TE_DEVICE, TE_HOST = 0, 1
+WHICH = {"LM": 0, "LA": 1}
+PRECISIONS = {"ddd": (TE_F64, TE_F64, TE_F64), "fdf": (TE_F32, TE_F64, TE_F32)}
+STATUS = {0: "TE_OK", 1: "TE_ERR_INVALID_ARG", 2: "TE_ERR_OUT_OF_MEMORY", 3: "TE_ERR_CUDA",
+          4: "TE_ERR_BREAKDOWN", 5: "TE_ERR_NOT_CONVERGED", 6: "TE_ERR_TIMEOUT",
+          7: "TE_ERR_UNSUPPORTED"}
+
+
+class TEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class te_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("values", ctypes.c_void_p),
+                ("row_scale", ctypes.c_void_p), ("where", ctypes.c_int32)]
+
+
+class te_precision(ctypes.Structure):
+    _fields_ = [("values", ctypes.c_int32), ("arithmetic", ctypes.c_int32),
+                ("vectors", ctypes.c_int32)]
+
+
+class te_options(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("v1", ctypes.c_void_p), ("which", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("device_budget_bytes", ctypes.c_size_t)]
+
+
+# every symbol the header declares, with its ctypes signature
+_SIGS = {
+    "te_default_options": (None, [ctypes.c_void_p]),
+    "te_last_error": (ctypes.c_char_p, []),
+    "te_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "te_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                             te_precision]),
+    "te_topk_eigs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, te_precision,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "te_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                      te_precision, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "te_plan_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "te_plan_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "te_plan_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "te_plan_kernel_count": (ctypes.c_int32, [ctypes.c_void_p]),
+    "te_plan_destroy": (None, [ctypes.c_void_p]),
+    "te_spmv": (ctypes.c_int, [ctypes.c_void_p, te_precision, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p]),
+    "te_lanczos": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, te_precision,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "te_tridiag_eigs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "te_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "te_spmv_partition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                         te_precision, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = False):
+    """Load libtopk_eigs.so (raises if it is missing, unless asked to build it)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise ImportError(
+                f"{_build.LIB} is missing: build it with __graft_entry__.build() "
+                "(there is no CPU fallback)")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load_library().te_last_error().decode(errors="replace")
+        raise TEError(rc, msg)
+
+
+def _prec(precision) -> te_precision:
+    if isinstance(precision, str):
+        v, a, w = PRECISIONS[precision.lower()]
+    else:
+        v, a, w = precision
+    return te_precision(v, a, w)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class CSR:
+    """CSR matrix held in torch tensors (device or host).
+
+    row_ptr: int64 (n+1); col: int32 (nnz); val: float64 (DDD) or float32 (FDF).
+    """
+    n: int
+    row_ptr: "object"
+    col: "object"
+    val: "object"
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @property
+    def on_device(self) -> bool:
+        return bool(self.row_ptr.is_cuda)
+
+    def to_ctypes(self) -> te_csr:
+        for t in (self.row_ptr, self.col, self.val):
+            if not t.is_contiguous():
+                raise ValueError("CSR tensors must be contiguous")
+        return te_csr(self.n, self.nnz, self.row_ptr.data_ptr(), self.col.data_ptr(),
+                      self.val.data_ptr(), None, TE_DEVICE if self.on_device else TE_HOST)
+
+    @staticmethod
+    def from_host(host_csr, precision: str = "ddd", device: str = "cuda", pin: bool = False):
+        """Make a CSR from numpy arrays (an object with n, row_ptr, col, val)."""
+        import numpy as np
+        import torch
+        vdt = np.float32 if _prec(precision).values == TE_F32 else np.float64
+        rp = torch.from_numpy(np.ascontiguousarray(host_csr.row_ptr, dtype=np.int64))
+        ci = torch.from_numpy(np.ascontiguousarray(host_csr.col, dtype=np.int32))
+        va = torch.from_numpy(np.ascontiguousarray(host_csr.val, dtype=vdt))
+        if device == "cpu":
+            if pin:
+                rp, ci, va = rp.pin_memory(), ci.pin_memory(), va.pin_memory()
+            return CSR(int(host_csr.n), rp, ci, va)
+        return CSR(int(host_csr.n), rp.to(device), ci.to(device), va.to(device))
+
+
+def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0) -> te_options:
+    o = te_options()
+    load_library().te_default_options(ctypes.byref(o))
+    o.seed = seed
+    o.v1 = None if v1 is None else v1.data_ptr()
+    o.which = WHICH[which] if isinstance(which, str) else int(which)
+    o.use_graph = 1 if use_graph else 0
+    o.device_budget_bytes = budget
+    return o
+
+
+def topk_eigs(csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0, v1=None,
+              which="LM", vectors: bool = True, residuals: bool = False, stream=None, out=None):
+    """One Top-K solve; returns (eigvals [K] float64 cpu, eigvecs [n, K] float64 or None,
+    residual estimates [K] or None).  Vectors live where the matrix lives unless
+    `out = (eigvals [K], eigvecs [K, n] or None)` gives preallocated buffers."""
+    import torch
+    lib = load_library()
+    A = csr.to_ctypes()
+    opt = _options(seed, v1, which)
+    if out is not None:
+        ev, U = out
+    else:
+        ev = torch.empty(K, dtype=torch.float64)
+        dev = "cuda" if csr.on_device else "cpu"
+        U = torch.empty((K, csr.n), dtype=torch.float64, device=dev) if vectors else None
+    res = torch.empty(K, dtype=torch.float64) if residuals else None
+    rc = lib.te_topk_eigs(ctypes.byref(A), K, krylov_steps, _prec(precision), ctypes.byref(opt),
+                          ctypes.c_void_p(ev.data_ptr()),
+                          None if U is None else ctypes.c_void_p(U.data_ptr()),
+                          None if res is None else ctypes.c_void_p(res.data_ptr()),
+                          _stream_ptr(stream))
+    _check(rc)
+    return ev, (None if U is None else U.t()), res
+
+
+class Plan:
+    """A reusable solve (row partition, work memory and captured CUDA graph)."""
+
+    def __init__(self, csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0,
+                 v1=None, which="LM", use_graph: bool = True, budget: int = 0, stream=None):
+        self._lib = load_library()
+        self.csr, self.K, self.m, self.n = csr, K, krylov_steps, csr.n
+        A = csr.to_ctypes()
+        opt = _options(seed, v1, which, use_graph, budget)
+        h = ctypes.c_void_p()
+        rc = self._lib.te_plan_create(ctypes.byref(A), K, krylov_steps, _prec(precision),
+                                      ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h))
+        _check(rc)
+        self._h = h
+
+    @property
+    def kernel_count(self) -> int:
+        return int(self._lib.te_plan_kernel_count(self._h))
+
+    def solve(self, v1=None, vectors: bool = True, residuals: bool = False, stream=None):
+        import torch
+        ev = torch.empty(self.K, dtype=torch.float64)
+        U = (torch.empty((self.K, self.n), dtype=torch.float64, device="cuda")
+             if vectors else None)
+        res = torch.empty(self.K, dtype=torch.float64) if residuals else None
+        rc = self._lib.te_plan_solve(self._h, None if v1 is None else ctypes.c_void_p(v1.data_ptr()),
+                                     ctypes.c_void_p(ev.data_ptr()),
+                                     None if U is None else ctypes.c_void_p(U.data_ptr()),
+                                     None if res is None else ctypes.c_void_p(res.data_ptr()),
+                                     _stream_ptr(stream))
+        _check(rc)
+        return ev, (None if U is None else U.t()), res
+
+    def launch(self, eigvals_dev, eigvecs_dev=None, v1=None, stream=None):
+        """Asynchronous solve into device buffers (eigvecs_dev: (K, n) contiguous or None)."""
+        rc = self._lib.te_plan_launch(self._h, None if v1 is None else ctypes.c_void_p(v1.data_ptr()),
+                                      ctypes.c_void_p(eigvals_dev.data_ptr()),
+                                      None if eigvecs_dev is None
+                                      else ctypes.c_void_p(eigvecs_dev.data_ptr()),
+                                      _stream_ptr(stream))
+        _check(rc)
+
+    def status(self):
+        _check(self._lib.te_plan_status(self._h))
+
+    KINDS = ("spmv", "dot", "axpy_dot", "axpy_store", "restart", "jacobi", "ritz", "other")
+
+    def profile(self, stream=None):
+        """One un-graphed solve with CUDA events around every kernel:
+        {kind: (ms, launches, algorithmic bytes)}."""
+        import numpy as np
+        nk = len(self.KINDS)
+        ms = np.zeros(nk)
+        cnt = np.zeros(nk, dtype=np.int32)
+        by = np.zeros(nk)
+        rc = self._lib.te_plan_profile(self._h, ctypes.c_void_p(ms.ctypes.data),
+                                       ctypes.c_void_p(cnt.ctypes.data),
+                                       ctypes.c_void_p(by.ctypes.data), _stream_ptr(stream))
+        _check(rc)
+        return {k: (float(ms[i]), int(cnt[i]), float(by[i])) for i, k in enumerate(self.KINDS)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.te_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spmv(csr: CSR, x, precision="ddd", stream=None):
+    """y = M x (float64 output) with the solver's SpMV kernel."""
+    import torch
+    lib = load_library()
+    A = csr.to_ctypes()
+    y = torch.empty(csr.n, dtype=torch.float64, device="cuda")
+    rc = lib.te_spmv(ctypes.byref(A), _prec(precision), ctypes.c_void_p(x.data_ptr()),
+                     ctypes.c_void_p(y.data_ptr()), _stream_ptr(stream))
+    _check(rc)
+    return y
+
+
+def lanczos(csr: CSR, krylov_steps: int, precision="ddd", *, seed: int = 0, v1=None,
+            basis: bool = True, stream=None):
+    """The Lanczos phase: returns (alpha [m], beta [m+1], V [n, m] or None, restarts)."""
+    import torch
+    lib = load_library()
+    A = csr.to_ctypes()
+    opt = _options(seed, v1, "LM", False)
+    alpha = torch.empty(krylov_steps, dtype=torch.float64)
+    beta = torch.empty(krylov_steps + 1, dtype=torch.float64)
+    V = (torch.empty((krylov_steps, csr.n), dtype=torch.float64, device="cuda")
+         if basis else None)
+    restarts = ctypes.c_int32(0)
+    rc = lib.te_lanczos(ctypes.byref(A), krylov_steps, _prec(precision), ctypes.byref(opt),
+                        ctypes.c_void_p(alpha.data_ptr()), ctypes.c_void_p(beta.data_ptr()),
+                        None if V is None else ctypes.c_void_p(V.data_ptr()),
+                        ctypes.byref(restarts), _stream_ptr(stream))
+    _check(rc)
+    return alpha, beta, (None if V is None else V.t()), int(restarts.value)
+
+
+def spmv_partition(row_ptr, nnz: int, precision="fdf"):
+    """Host analysis behind the SpMV: returns (blocks [B,2] int32, chunks [C,3] int64,
+    number of long rows).  row_ptr: numpy int64 array of n+1 entries."""
+    import numpy as np
+    lib = load_library()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    n = len(rp) - 1
+    nb, nc, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rc = lib.te_spmv_partition(ctypes.c_void_p(rp.ctypes.data), n, nnz, _prec(precision),
+                               ctypes.byref(nb), ctypes.byref(nc), ctypes.byref(nl), None, None)
+    _check(rc)
+    blocks = np.zeros((nb.value, 2), dtype=np.int32)
+    chunks = np.zeros((nc.value, 3), dtype=np.int64)
+    rc = lib.te_spmv_partition(ctypes.c_void_p(rp.ctypes.data), n, nnz, _prec(precision), None,
+                               None, None, ctypes.c_void_p(blocks.ctypes.data),
+                               ctypes.c_void_p(chunks.ctypes.data))
+    _check(rc)
+    return blocks, chunks, int(nl.value)
+
+
+def tridiag_eigs(alpha, beta, which="LM", stream=None):
+    """Jacobi on tridiag(alpha; beta[1..m-1]) (device tensors); returns
+    (theta [m] in selection order, Y [m, m] columns = eigenvectors, sweeps)."""
+    import torch
+    lib = load_library()
+    m = int(alpha.numel())
+    theta = torch.empty(m, dtype=torch.float64, device="cuda")
+    Y = torch.empty((m, m), dtype=torch.float64, device="cuda")
+    sweeps = ctypes.c_int32(0)
+    rc = lib.te_tridiag_eigs(m, ctypes.c_void_p(alpha.data_ptr()), ctypes.c_void_p(beta.data_ptr()),
+                             WHICH[which] if isinstance(which, str) else int(which),
+                             ctypes.c_void_p(theta.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                             ctypes.byref(sweeps), _stream_ptr(stream))
+    _check(rc)
+    return theta, Y.t(), int(sweeps.value)

@@ -1,0 +1,155 @@
+// te_internal.h - declarations shared by the CUDA translation units of the
+// Top-K Lanczos eigensolver (device state layout, kernel argument blocks and
+// host-side launch wrappers).  Not part of the public C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "topk_eigs.h"
+
+namespace te {
+
+constexpr int MAX_M = 64;        // largest supported krylov_steps
+constexpr int TILE_R = 256;      // rows per tile of the basis passes
+constexpr int PSTRIDE = MAX_M + 4;  // per-CTA partial slots (columns + 2 norms)
+constexpr int CONSUMERS = 256;   // compute threads of the basis passes
+constexpr int PASS_THREADS = CONSUMERS + 32;  // + one producer warp
+constexpr int MAX_STAGES = 16;
+constexpr int SPMV_THREADS = 256;
+constexpr int SPMV_RMAX = 1024;  // rows per short SpMV block
+
+enum Prec : int { PREC_DDD = 0, PREC_FDF = 1 };
+
+// Device-resident state of one solve (lives in the plan's work memory).
+struct LzState {
+  double s[MAX_M + 2];      // v_j = s[j] * stored column j
+  double alpha[MAX_M + 1];  // alpha[i] = alpha_{i+1}
+  double beta[MAX_M + 2];   // beta[0] = beta_1 = 0, beta[i] = beta_{i+1}
+  double c1[MAX_M + 2];     // coefficients of the first axpy pass
+  double c2[MAX_M + 2];     // coefficients of the second axpy pass
+  double xscale;            // multiplier of the source vector in the first axpy
+  double anorm;             // max_j |alpha_j| + beta_j + beta_{j+1}
+  double theta_sel[MAX_M];  // selected Ritz values (selection order)
+  double resid_est[MAX_M];  // |beta_{m+1} y_k[m-1]|
+  double C[MAX_M * MAX_M];  // Ritz coefficients C[j*K + k] = s_j sign_k Y[j][idx_k]
+  int restart_flag;         // set when the last step broke down
+  int restarts;             // restarts so far (random stream = restarts + 1)
+  int status;               // te_status of the solve so far
+  int sweeps;               // Jacobi sweeps
+  unsigned int ticket;      // last-CTA counter
+  int pad_;
+  // per-solve inputs (written by the host before each solve)
+  const double* v1;
+  double* eigvecs;
+  double* eigvals_out;
+};
+
+struct LongChunk {
+  int64_t k0, k1;  // nnz range
+  int32_t row;
+  int32_t pad_;
+};
+struct LongRow {
+  int32_t row, first, count, pad_;
+};
+
+// Host-side SpMV partition (row blocks for the CSR-stream kernel).
+struct Partition {
+  std::vector<int2> blocks;       // short blocks [row0, row1)
+  std::vector<LongChunk> chunks;  // chunks of long rows
+  std::vector<LongRow> lrows;     // long rows -> their chunks
+};
+
+// Device copy of a partition.
+struct DevPartition {
+  int2* blocks = nullptr;
+  LongChunk* chunks = nullptr;
+  LongRow* lrows = nullptr;
+  void* lpart = nullptr;  // one partial per chunk (8 bytes)
+  int nshort = 0, nchunks = 0, nlrows = 0;
+};
+
+int spmv_tile_nnz(int prec);
+// returns false (and a message) if row_ptr is malformed
+bool make_partition(const int64_t* rp, int64_t n, int64_t nnz, int tnnz, Partition& out,
+                    std::string& err);
+
+// SpMV: y = A x.  out_f64: write binary64 (else the precision's vector type).
+cudaError_t launch_spmv(int prec, const int64_t* rp, const int32_t* ci, const void* val,
+                        const void* x, void* y, int64_t n, const DevPartition& P,
+                        bool out_f64, cudaStream_t s);
+cudaError_t launch_validate_cols(const int32_t* ci, int64_t nnz, int64_t n, int* flag,
+                                 cudaStream_t s);
+
+// ---- basis passes ----
+enum PassMode : int { MODE_DOT = 0, MODE_AXPY_DOT = 1, MODE_AXPY_STORE = 2, MODE_RITZ = 3 };
+enum XSource : int { X_VEC = 0, X_RANDOM = 1, X_V1 = 2 };
+enum Finalize : int {
+  FIN_DOT_STEP = 0,
+  FIN_DOT_RESTART = 1,
+  FIN_AXPYDOT = 2,
+  FIN_STORE_STEP = 3,
+  FIN_STORE_RESTART = 4,
+  FIN_STORE_INIT = 5,
+  FIN_NONE = 6
+};
+
+struct PassArgs {
+  const void* V;     // stored basis (column-major, leading dimension ld)
+  void* Vmut;        // same buffer, for the column written by AXPY_STORE
+  int64_t ld;        // padded rows
+  int64_t n;         // true rows
+  int nb;            // basis columns read by this pass
+  int col_out;       // column written by AXPY_STORE
+  int step;          // Lanczos step (0-based)
+  int m;             // krylov steps of the solve
+  int K;             // eigenpairs (RITZ)
+  int xsrc;          // XSource
+  int fin;           // Finalize
+  int only_on_restart;  // exit at once unless st->restart_flag is set
+  const void* xvec;  // source vector (precision's vector type), X_VEC
+  void* wout;        // AXPY_DOT: output vector
+  uint64_t seed;
+  double tol;        // breakdown tolerance (relative to anorm)
+  LzState* st;
+  void* partials;    // gridDim.x * PSTRIDE slots
+};
+
+struct PassLaunch {
+  int grid = 0;
+  size_t smem = 0;
+  size_t region = 0;  // bytes of the stage buffers
+  int stages = 0;
+};
+// configure a pass kernel for `max_cols` basis columns (and K Ritz vectors);
+// returns the launch shape
+cudaError_t pass_config(int prec, int mode, int max_cols, int K, int num_sms, PassLaunch& out);
+cudaError_t launch_pass(int prec, int mode, const PassArgs& a, const PassLaunch& L,
+                        cudaStream_t s);
+
+// ---- Jacobi phase ----
+struct JacobiArgs {
+  const double* alpha;  // m
+  const double* beta;   // m+1 (beta[1..m-1] off-diagonal, beta[m] = beta_{m+1})
+  const double* s;      // column scales (for Ritz coefficients), or nullptr
+  int m, K, which;
+  double* theta_out;    // K (selection order)
+  double* Y_out;        // optional m x K column-major (sign-fixed eigenvectors)
+  double* C_out;        // optional Ritz coefficients C[j*K+k]
+  double* resid_out;    // optional residual estimates
+  double* eigvals_dev;  // optional copy of theta_out
+  LzState* st;          // status / sweeps (may be nullptr)
+  int* sweeps_out;      // optional
+  int* status_out;      // optional
+};
+cudaError_t jacobi_prepare();  // once per process/device, outside stream capture
+cudaError_t launch_jacobi(const JacobiArgs& a, cudaStream_t s);
+
+// ---- small utilities ----
+cudaError_t launch_basis_to_f64(int prec, const void* V, int64_t ld, int64_t n, int cols,
+                                const double* s_dev, double* out, cudaStream_t st);
+
+}  // namespace te

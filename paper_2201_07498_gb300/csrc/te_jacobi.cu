@@ -1,0 +1,218 @@
+// te_jacobi.cu - the Jacobi phase (Section III, Fig. 1): eigen-decomposition
+// of the small tridiagonal T produced by the Lanczos phase, the selection of
+// the K eigenvalues largest in modulo (Section I), and the coefficients of the
+// Ritz-vector contraction.
+//
+// The paper ran this step on the CPU because one 24x24 matrix cannot fill a
+// GPU; here it stays on the device so that a solve needs no host round trip
+// before the Ritz contraction.  One CTA holds T and the eigenvector matrix Y in
+// shared memory and applies cyclic Jacobi with the parallel (round-robin,
+// "circle method") ordering of Brent & Luk: every round rotates m/2 disjoint
+// index pairs at once, T <- J^T T J, Y <- Y J.  Rotation angle (textbook
+// form, e.g. Golub & Van Loan Sec. 8.5): zeta = (t_qq - t_pp) / (2 t_pq),
+// t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = t c;
+// a pair is rotated when |t_pq| > 1e-16 ||T||_F and the sweeps stop after
+// one without rotations.  Arithmetic is binary64.
+#include "te_common.cuh"
+#include "te_internal.h"
+
+namespace te {
+
+constexpr int JAC_THREADS = 256;
+constexpr int JAC_MAX_SWEEPS = 100;
+constexpr int JLD = MAX_M + 1;  // padded row length in shared memory
+
+// position j of the round-robin schedule in round r (player 0 stays put)
+TE_DEV int rr_player(int j, int r, int mm) { return j == 0 ? 0 : 1 + (j - 1 + r) % (mm - 1); }
+
+TE_DEV bool sel_before(double a, int ia, double b, int ib, int which) {
+  if (which == TE_WHICH_LARGEST_ALGEBRAIC) {
+    if (a != b) return a > b;
+    return ia < ib;
+  }
+  double fa = fabs(a), fb = fabs(b);
+  if (fa != fb) return fa > fb;
+  if ((a > 0) != (b > 0)) return a > 0;
+  return ia < ib;
+}
+
+constexpr size_t JAC_SMEM = 2 * (size_t)MAX_M * JLD * sizeof(double);
+
+__global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
+  extern __shared__ __align__(16) double jsm[];
+  double* T = jsm;
+  double* Y = jsm + MAX_M * JLD;
+  __shared__ double rc[MAX_M / 2], rs[MAX_M / 2], rt[MAX_M / 2];
+  __shared__ double d_pp[MAX_M / 2], d_qq[MAX_M / 2], d_pq[MAX_M / 2];
+  __shared__ int rp_[MAX_M / 2], rq_[MAX_M / 2], rot[MAX_M / 2];
+  __shared__ int any_rot;
+  __shared__ int sel[MAX_M];
+  __shared__ double thr_s;
+
+  const int tid = threadIdx.x;
+  const int m = a.m;
+  const int mm = m + (m & 1);  // even size; a dummy index never rotates
+  const int half = mm / 2;
+
+  for (int e = tid; e < mm * mm; e += JAC_THREADS) {
+    const int r = e / mm, c = e % mm;
+    double v = 0.0;
+    if (r < m && c < m) {
+      if (r == c) v = a.alpha[r];
+      else if (r - c == 1 || c - r == 1) v = a.beta[r > c ? r : c];
+    }
+    T[r * JLD + c] = v;
+    Y[r * JLD + c] = (r == c) ? 1.0 : 0.0;
+  }
+  if (tid == 0) {
+    double f = 0.0;
+    for (int r = 0; r < m; ++r) f += a.alpha[r] * a.alpha[r];
+    for (int r = 1; r < m; ++r) f += 2.0 * a.beta[r] * a.beta[r];
+    thr_s = 1e-16 * sqrt(f);
+  }
+  __syncthreads();
+  const double thr = thr_s;
+
+  int sweep = 0;
+  for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
+    if (tid == 0) any_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < mm - 1; ++round) {
+      if (tid < half) {
+        int p = rr_player(tid, round, mm), q = rr_player(mm - 1 - tid, round, mm);
+        if (p > q) {
+          int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        rp_[tid] = p;
+        rq_[tid] = q;
+        const double tpq = T[p * JLD + q];
+        if (fabs(tpq) > thr) {
+          const double tpp = T[p * JLD + p], tqq = T[q * JLD + q];
+          const double zeta = (tqq - tpp) / (2.0 * tpq);
+          double t;
+          if (fabs(zeta) > 1e150) t = 0.5 / zeta;
+          else t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t);
+          rc[tid] = c;
+          rs[tid] = t * c;
+          rt[tid] = t;
+          d_pp[tid] = tpp;
+          d_qq[tid] = tqq;
+          d_pq[tid] = tpq;
+          rot[tid] = 1;
+          any_rot = 1;
+        } else {
+          rot[tid] = 0;
+        }
+      }
+      __syncthreads();
+      // rows p, q  <-  J^T T
+      for (int e = tid; e < half * mm; e += JAC_THREADS) {
+        const int k = e / mm, col = e % mm;
+        if (!rot[k]) continue;
+        const int p = rp_[k], q = rq_[k];
+        const double c = rc[k], s = rs[k];
+        const double g = T[p * JLD + col], h = T[q * JLD + col];
+        T[p * JLD + col] = c * g - s * h;
+        T[q * JLD + col] = s * g + c * h;
+      }
+      __syncthreads();
+      // columns p, q  <-  T J, and Y <- Y J
+      for (int e = tid; e < half * mm; e += JAC_THREADS) {
+        const int k = e / mm, row = e % mm;
+        if (!rot[k]) continue;
+        const int p = rp_[k], q = rq_[k];
+        const double c = rc[k], s = rs[k];
+        const double g = T[row * JLD + p], h = T[row * JLD + q];
+        T[row * JLD + p] = c * g - s * h;
+        T[row * JLD + q] = s * g + c * h;
+        const double gy = Y[row * JLD + p], hy = Y[row * JLD + q];
+        Y[row * JLD + p] = c * gy - s * hy;
+        Y[row * JLD + q] = s * gy + c * hy;
+      }
+      __syncthreads();
+      // the 2x2 block of each pair: exact post-rotation values
+      if (tid < half && rot[tid]) {
+        const int p = rp_[tid], q = rq_[tid];
+        T[p * JLD + p] = d_pp[tid] - rt[tid] * d_pq[tid];
+        T[q * JLD + q] = d_qq[tid] + rt[tid] * d_pq[tid];
+        T[p * JLD + q] = 0.0;
+        T[q * JLD + p] = 0.0;
+      }
+      __syncthreads();
+    }
+    if (!any_rot) break;
+    __syncthreads();
+  }
+
+  // selection: rank of each Ritz value under the selection order
+  if (tid < m) {
+    const double th = T[tid * JLD + tid];
+    int rank = 0;
+    for (int l = 0; l < m; ++l)
+      if (l != tid && sel_before(T[l * JLD + l], l, th, tid, a.which)) ++rank;
+    sel[rank] = tid;
+  }
+  __syncthreads();
+  double* eigvals_dev = a.eigvals_dev;
+  if (a.st != nullptr) eigvals_dev = a.st->eigvals_out;
+  // one warp per selected pair: sign, outputs, Ritz coefficients
+  const int wid = tid >> 5, lane = tid & 31;
+  for (int k = wid; k < a.K; k += JAC_THREADS / 32) {
+    const int j = sel[k];
+    // largest-magnitude entry of y (lowest index on ties)
+    double best = -1.0;
+    int bi = m;
+    for (int r = lane; r < m; r += 32) {
+      const double v = fabs(Y[r * JLD + j]);
+      if (v > best || (v == best && r < bi)) {
+        best = v;
+        bi = r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    const double sgn = Y[bi * JLD + j] < 0.0 ? -1.0 : 1.0;
+    const double th = T[j * JLD + j];
+    if (lane == 0) {
+      a.theta_out[k] = th;
+      if (eigvals_dev) eigvals_dev[k] = th;
+      if (a.resid_out) a.resid_out[k] = fabs(a.beta[m] * Y[(m - 1) * JLD + j]);
+    }
+    for (int r = lane; r < m; r += 32) {
+      const double y = sgn * Y[r * JLD + j];
+      if (a.Y_out) a.Y_out[(size_t)k * m + r] = y;
+      if (a.C_out) a.C_out[(size_t)r * a.K + k] = (a.s ? a.s[r] : 1.0) * y;
+    }
+  }
+  if (tid == 0) {
+    const int conv = sweep < JAC_MAX_SWEEPS;
+    if (a.sweeps_out) *a.sweeps_out = sweep;
+    if (a.status_out) *a.status_out = conv ? 0 : (int)TE_ERR_NOT_CONVERGED;
+    if (a.st) {
+      a.st->sweeps = sweep;
+      if (!conv && a.st->status == 0) a.st->status = (int)TE_ERR_NOT_CONVERGED;
+    }
+  }
+}
+
+cudaError_t jacobi_prepare() {
+  return cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)JAC_SMEM);
+}
+
+cudaError_t launch_jacobi(const JacobiArgs& a, cudaStream_t s) {
+  jacobi_kernel<<<1, JAC_THREADS, JAC_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace te

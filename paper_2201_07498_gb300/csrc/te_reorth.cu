@@ -1,0 +1,572 @@
+// te_reorth.cu - the passes over the Lanczos basis for sm_103a:
+// reorthogonalisation (Algorithm 1, lines 11-19, done as classical
+// Gram-Schmidt applied twice), the normalisation that yields beta and the
+// next basis vector (lines 6-7), and the Ritz-vector contraction V*Y
+// (Section III).
+//
+// One persistent kernel template serves every pass.  The basis V is stored
+// column-major with a padded leading dimension (a multiple of TILE_R rows, the
+// padding kept at zero); column j holds an unnormalised vector whose scale
+// s_j (so that v_j = s_j * stored_j) lives in the device state.  A CTA owns
+// every gridDim.x-th tile of TILE_R rows.  One producer warp moves the
+// tile's basis columns into shared memory with bulk (TMA) copies into a
+// multi-stage mbarrier pipeline; eight consumer warps then
+//   phase A (axpy):  w_r = xscale * x_r - sum_j c_j V[r, j]    (thread per row)
+//   phase B (dots):  g_j += sum_r V[r, j] w_r                  (warp per column)
+// so the second Gram-Schmidt sweep's dot products read the same shared-memory
+// tile as the first sweep's update: one HBM read of V per fused pass.  The
+// per-CTA sums go to a partial buffer; the last CTA to finish (ticket counter)
+// reduces them in a fixed order and computes the next pass's coefficients,
+// alpha, beta and the breakdown flag on the device - no host round trip.
+//
+// Precision: DDD uses binary64 FMA.  FDF stores V in binary32 and carries
+// every product and sum in double-float (te_common.cuh); per-CTA partials are
+// double-float, the final cross-CTA sums binary64.
+#include "te_common.cuh"
+#include "te_internal.h"
+
+namespace te {
+
+template <int P>
+struct PassTr;
+template <>
+struct PassTr<PREC_DDD> {
+  using basis_t = double;
+  using vec_t = double;
+  using acc_t = double;
+  using coef_t = double;
+};
+template <>
+struct PassTr<PREC_FDF> {
+  using basis_t = float;
+  using vec_t = float2;
+  using acc_t = dacc;
+  using coef_t = float2;
+};
+
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr int QMAX = MAX_M / (CONSUMERS / 32);  // dot columns per warp
+constexpr int RITZ_KC = 8;                      // Ritz outputs per register block
+
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct SmemPlan {
+  size_t region, ws_off, coef_off, ritz_off, red_off, bar_off, total;
+};
+// ritz_elems: m*K coefficients held by the Ritz pass (0 for the other passes)
+__host__ __device__ inline SmemPlan smem_plan(int mode, size_t region, int ritz_elems) {
+  SmemPlan p{};
+  p.region = region;
+  p.ws_off = align_up(region, 128);
+  p.coef_off = p.ws_off + TILE_R * 8;
+  p.ritz_off = p.coef_off + (MAX_M + 2) * 8;
+  size_t ritz = (mode == MODE_RITZ) ? align_up((size_t)ritz_elems * 8, 128) : 0;
+  p.red_off = p.ritz_off + ritz;
+  p.bar_off = align_up(p.red_off + 64 * 8, 8);
+  p.total = p.bar_off + 2 * MAX_STAGES * 8 + 16;
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// small helpers specialised per precision
+// ---------------------------------------------------------------------------
+template <int P>
+TE_DEV typename PassTr<P>::acc_t zero_acc() {
+  if constexpr (P == PREC_FDF) return dacc_zero();
+  else return 0.0;
+}
+// acc += v * c
+template <int P>
+TE_DEV void acc_fma(typename PassTr<P>::acc_t& acc, typename PassTr<P>::basis_t v,
+                    typename PassTr<P>::coef_t c) {
+  if constexpr (P == PREC_FDF) dacc_fma(acc, v, c.x, c.y);
+  else acc = fma(v, c, acc);
+}
+template <int P>
+TE_DEV typename PassTr<P>::acc_t acc_merge(typename PassTr<P>::acc_t a,
+                                           typename PassTr<P>::acc_t b) {
+  if constexpr (P == PREC_FDF) return dacc_merge(a, b);
+  else return a + b;
+}
+template <int P>
+TE_DEV typename PassTr<P>::coef_t to_coef(double c) {
+  if constexpr (P == PREC_FDF) {
+    dw d = dw_from_double(c);
+    return make_float2(d.hi, d.lo);
+  } else {
+    return c;
+  }
+}
+template <int P>
+TE_DEV typename PassTr<P>::vec_t vec_from_double(double x) {
+  if constexpr (P == PREC_FDF) {
+    dw d = dw_from_double(x);
+    return make_float2(d.hi, d.lo);
+  } else {
+    return x;
+  }
+}
+template <int P>
+TE_DEV typename PassTr<P>::vec_t vec_zero() {
+  if constexpr (P == PREC_FDF) return make_float2(0.f, 0.f);
+  else return 0.0;
+}
+// partial slot (8 bytes) <-> accumulator
+template <int P>
+TE_DEV void put_partial(void* part, size_t idx, typename PassTr<P>::acc_t a) {
+  if constexpr (P == PREC_FDF) static_cast<float2*>(part)[idx] = dw_to_f2(dacc_value(a));
+  else static_cast<double*>(part)[idx] = a;
+}
+template <int P>
+TE_DEV void add_partial(typename PassTr<P>::acc_t& acc, const void* part, size_t idx) {
+  if constexpr (P == PREC_FDF) {
+    float2 v = __ldcg(static_cast<const float2*>(part) + idx);
+    dacc_add_pair(acc, v.x, v.y);
+  } else {
+    acc += __ldcg(static_cast<const double*>(part) + idx);
+  }
+}
+template <int P>
+TE_DEV double acc_to_double(typename PassTr<P>::acc_t a) {
+  if constexpr (P == PREC_FDF) return dw_to_double(dacc_value(a));
+  else return a;
+}
+
+// ---------------------------------------------------------------------------
+// last-CTA epilogue: turns the reduced sums into the next coefficients
+// ---------------------------------------------------------------------------
+TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
+  LzState* st = a.st;
+  const int i = a.step;
+  switch (a.fin) {
+    case FIN_DOT_STEP: {
+      // tot[j] = stored_j . ytilde with y = s_i ytilde = M v_i
+      const double si = st->s[i];
+      for (int j = 0; j < a.nb; ++j) {
+        double h = st->s[j] * si * tot[j];  // v_j . M v_i
+        st->c1[j] = h * st->s[j];
+      }
+      st->alpha[i] = st->s[i] * si * tot[i];  // Algorithm 1, line 10
+      st->xscale = si;
+      break;
+    }
+    case FIN_DOT_RESTART: {
+      for (int j = 0; j < a.nb; ++j) st->c1[j] = st->s[j] * st->s[j] * tot[j];
+      st->xscale = 1.0;
+      break;
+    }
+    case FIN_AXPYDOT: {
+      for (int j = 0; j < a.nb; ++j) st->c2[j] = st->s[j] * st->s[j] * tot[j];
+      break;
+    }
+    case FIN_STORE_STEP: {
+      // tot[0] = ||w||^2, tot[1] = ||stored(w)||^2 (Algorithm 1, line 6)
+      const double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
+      const double ns = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);
+      st->s[i + 1] = ns > 0.0 ? 1.0 / ns : 0.0;
+      double cand = fabs(st->alpha[i]) + st->beta[i] + b;
+      if (cand > st->anorm) st->anorm = cand;
+      st->beta[i + 1] = b;
+      st->restart_flag = 0;
+      if (i + 1 < a.m && !(b > a.tol * st->anorm)) {
+        st->restart_flag = 1;
+        st->beta[i + 1] = 0.0;
+      }
+      break;
+    }
+    case FIN_STORE_RESTART: {
+      const double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
+      const double ns = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);
+      if (ns > 0.0 && b > 0.0) st->s[i + 1] = 1.0 / ns;
+      else st->status = TE_ERR_BREAKDOWN;
+      st->restarts += 1;
+      st->restart_flag = 0;
+      break;
+    }
+    case FIN_STORE_INIT: {
+      const double ns = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);
+      if (ns > 0.0) st->s[0] = 1.0 / ns;
+      else st->status = TE_ERR_INVALID_ARG;
+      st->beta[0] = 0.0;
+      st->anorm = 0.0;
+      st->restart_flag = 0;
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the pass kernel
+// ---------------------------------------------------------------------------
+template <int P, int MODE>
+__global__ void __launch_bounds__(PASS_THREADS, 1) pass_kernel(PassArgs a, size_t region) {
+  using Tr = PassTr<P>;
+  using basis_t = typename Tr::basis_t;
+  using vec_t = typename Tr::vec_t;
+  using acc_t = typename Tr::acc_t;
+  using coef_t = typename Tr::coef_t;
+  constexpr bool HAS_AXPY = (MODE == MODE_AXPY_DOT || MODE == MODE_AXPY_STORE);
+  constexpr bool HAS_DOT = (MODE == MODE_DOT || MODE == MODE_AXPY_DOT);
+
+  extern __shared__ __align__(128) unsigned char sm[];
+  LzState* st = a.st;
+  if (a.only_on_restart) {
+    if (*((volatile int*)&st->restart_flag) == 0) return;
+  }
+  const SmemPlan L = smem_plan(MODE, region, MODE == MODE_RITZ ? a.nb * a.K : 0);
+  basis_t* stg = reinterpret_cast<basis_t*>(sm);
+  vec_t* ws = reinterpret_cast<vec_t*>(sm + L.ws_off);
+  coef_t* coef = reinterpret_cast<coef_t*>(sm + L.coef_off);
+  coef_t* rC = reinterpret_cast<coef_t*>(sm + L.ritz_off);
+  acc_t* red = reinterpret_cast<acc_t*>(sm + L.red_off);
+  double* tot = reinterpret_cast<double*>(sm + L.red_off);  // reused by the last CTA
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar_off);
+  uint64_t* empty = full + MAX_STAGES;
+  int* lastflag = reinterpret_cast<int*>(empty + MAX_STAGES);
+  int* abortflag = lastflag + 1;
+
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int64_t tiles = a.ld / TILE_R;
+  const int nb = a.nb;
+  const size_t stage_elems = (size_t)nb * TILE_R;
+  const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(basis_t));
+  int S = 0;
+  if (nb > 0) {
+    S = (int)(region / stage_bytes);
+    if (S > MAX_STAGES) S = MAX_STAGES;
+  }
+
+  if (tid == 0) *abortflag = 0;
+  if (tid == 0 && nb > 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], CONSUMERS / 32);
+    }
+    fence_mbar_init();
+  }
+  if constexpr (MODE == MODE_AXPY_DOT) {
+    for (int j = tid; j < nb; j += PASS_THREADS) coef[j] = to_coef<P>(st->c1[j]);
+  }
+  if constexpr (MODE == MODE_AXPY_STORE) {
+    for (int j = tid; j < nb; j += PASS_THREADS) coef[j] = to_coef<P>(st->c2[j]);
+  }
+  if constexpr (MODE == MODE_RITZ) {
+    if (st->eigvecs == nullptr) return;  // uniform: no vectors requested
+    for (int e = tid; e < nb * a.K; e += PASS_THREADS) rC[e] = to_coef<P>(st->C[e]);
+  }
+  __syncthreads();
+
+  const basis_t* Vg = static_cast<const basis_t*>(a.V);
+
+  // ------------------------- producer warp -------------------------
+  if (wid == CONSUMERS / 32) {
+    if (nb > 0 && lane == 0) {
+      const uint64_t pol = policy_evict_first();
+      int it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+        const int s = it % S, k = it / S;
+        if (k > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)((k - 1) & 1), WAIT_LIMIT)) {
+          atomicExch(&st->status, (int)TE_ERR_TIMEOUT);
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(&full[s], stage_bytes);
+        basis_t* dst = stg + (size_t)s * stage_elems;
+        const basis_t* src = Vg + t * TILE_R;
+        for (int j = 0; j < nb; ++j)
+          bulk_g2s(dst + (size_t)j * TILE_R, src + (size_t)j * a.ld,
+                   (uint32_t)(TILE_R * sizeof(basis_t)), &full[s], pol);
+      }
+      // drain: every issued copy must land before this warp retires
+      const int issued = it;
+      for (int s = 0; s < S && s < issued; ++s) {
+        const int klast = (issued - 1 - s) / S;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)(klast & 1), WAIT_LIMIT)) {
+          atomicExch(&st->status, (int)TE_ERR_TIMEOUT);
+        }
+      }
+      (void)ok;
+    }
+    return;
+  }
+
+  // ------------------------- consumer warps -------------------------
+  const double xs_d = (MODE == MODE_AXPY_DOT) ? st->xscale : 1.0;
+  coef_t xscale = to_coef<P>(xs_d);
+  const uint64_t rstream = (a.xsrc == X_V1) ? 0ull : (uint64_t)(st->restarts + 1);
+  const double* v1 = st->v1;
+  acc_t dots[QMAX];
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) dots[q] = zero_acc<P>();
+  acc_t n1 = zero_acc<P>(), n2 = zero_acc<P>();
+  basis_t* Vout = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_out * a.ld;
+
+  int it = 0;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+    const int64_t row = t * TILE_R + tid;
+    // the source value is fetched before waiting on the tile to overlap latency
+    vec_t x = vec_zero<P>();
+    if constexpr (MODE != MODE_RITZ) {
+      if (a.xsrc == X_VEC) {
+        x = static_cast<const vec_t*>(a.xvec)[row];
+      } else if (a.xsrc == X_V1 && v1 != nullptr) {
+        if (row < a.n) x = vec_from_double<P>(v1[row]);
+      } else {
+        if (row < a.n) x = vec_from_double<P>(sm64_uniform_pm1(a.seed, rstream, (uint64_t)row));
+      }
+    }
+    int s = 0;
+    if (nb > 0) {
+      s = it % S;
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((it / S) & 1), WAIT_LIMIT)) {
+        atomicExch(&st->status, (int)TE_ERR_TIMEOUT);
+        *abortflag = 1;
+      }
+      // every consumer leaves together if any of them gave up waiting
+      named_bar_sync(1, CONSUMERS);
+      if (*abortflag) break;
+    }
+    const basis_t* tv = stg + (size_t)s * stage_elems;
+
+    if constexpr (HAS_AXPY) {
+      // phase A: t_r = sum_j c_j V[r, j] with four independent chains
+      acc_t ta[4] = {zero_acc<P>(), zero_acc<P>(), zero_acc<P>(), zero_acc<P>()};
+      int j = 0;
+      for (; j + 4 <= nb; j += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc_fma<P>(ta[u], tv[(size_t)(j + u) * TILE_R + tid], coef[j + u]);
+      }
+      for (; j < nb; ++j) acc_fma<P>(ta[0], tv[(size_t)j * TILE_R + tid], coef[j]);
+      acc_t tacc = acc_merge<P>(acc_merge<P>(ta[0], ta[1]), acc_merge<P>(ta[2], ta[3]));
+      vec_t w;
+      if constexpr (P == PREC_FDF) {
+        dw xv = dw_from_f2(x);
+        dw sx = (MODE == MODE_AXPY_DOT) ? dw_mul(dw_from_f2(xscale), xv) : xv;
+        dw wd = dw_sub(sx, dacc_value(tacc));
+        w = dw_to_f2(wd);
+      } else {
+        w = (MODE == MODE_AXPY_DOT) ? fma(xscale, x, -tacc) : x - tacc;
+      }
+      if constexpr (MODE == MODE_AXPY_DOT) {
+        static_cast<vec_t*>(a.wout)[row] = w;
+        ws[tid] = w;
+      } else {
+        // store the next basis vector (unnormalised) and its two norms
+        if constexpr (P == PREC_FDF) {
+          Vout[row] = w.x;
+          dacc_fma(n1, w.x, w.x, 2.0f * w.y);
+          dacc_fma(n2, w.x, w.x, 0.0f);
+        } else {
+          Vout[row] = w;
+          n1 = fma(w, w, n1);
+        }
+      }
+    } else if constexpr (MODE == MODE_DOT) {
+      ws[tid] = x;
+    }
+
+    if constexpr (HAS_DOT) {
+      named_bar_sync(1, CONSUMERS);
+      // phase B: warp `wid` owns columns wid, wid+8, ...; lanes stride rows
+#pragma unroll 2
+      for (int rr = 0; rr < TILE_R / 32; ++rr) {
+        const int r = lane + 32 * rr;
+        const vec_t wr = ws[r];
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+          const int jj = wid + (CONSUMERS / 32) * q;
+          if (jj < nb) {
+            const basis_t v = tv[(size_t)jj * TILE_R + r];
+            if constexpr (P == PREC_FDF) dacc_fma(dots[q], v, wr.x, wr.y);
+            else dots[q] = fma(v, wr, dots[q]);
+          }
+        }
+      }
+    }
+
+    if constexpr (MODE == MODE_RITZ) {
+      const int K = a.K;
+      double* U = st->eigvecs;
+      for (int k0 = 0; k0 < K; k0 += RITZ_KC) {
+        acc_t ra[RITZ_KC];
+#pragma unroll
+        for (int kk = 0; kk < RITZ_KC; ++kk) ra[kk] = zero_acc<P>();
+        for (int j = 0; j < nb; ++j) {
+          const basis_t v = tv[(size_t)j * TILE_R + tid];
+#pragma unroll
+          for (int kk = 0; kk < RITZ_KC; ++kk)
+            if (k0 + kk < K) acc_fma<P>(ra[kk], v, rC[j * K + k0 + kk]);
+        }
+        if (row < a.n) {
+#pragma unroll
+          for (int kk = 0; kk < RITZ_KC; ++kk)
+            if (k0 + kk < K) U[(size_t)(k0 + kk) * a.n + row] = acc_to_double<P>(ra[kk]);
+        }
+      }
+    }
+
+    if (nb > 0) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    if constexpr (HAS_DOT) named_bar_sync(1, CONSUMERS);
+  }
+
+  if (a.fin == FIN_NONE) return;
+
+  // ---- per-CTA partial sums ----
+  if constexpr (HAS_DOT) {
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      const int jj = wid + (CONSUMERS / 32) * q;
+      if (jj < nb) {
+        acc_t v = dots[q];
+        if constexpr (P == PREC_FDF) v = warp_sum(v);
+        else v = warp_sum(v);
+        if (lane == 0) put_partial<P>(a.partials, (size_t)blockIdx.x * PSTRIDE + jj, v);
+      }
+    }
+  }
+  if constexpr (MODE == MODE_AXPY_STORE) {
+    if constexpr (P == PREC_DDD) n2 = n1;
+    n1 = warp_sum(n1);
+    n2 = warp_sum(n2);
+    if (lane == 0) {
+      red[2 * wid] = n1;
+      red[2 * wid + 1] = n2;
+    }
+    named_bar_sync(1, CONSUMERS);
+    if (tid == 0) {
+      acc_t t1 = red[0], t2 = red[1];
+      for (int w = 1; w < CONSUMERS / 32; ++w) {
+        t1 = acc_merge<P>(t1, red[2 * w]);
+        t2 = acc_merge<P>(t2, red[2 * w + 1]);
+      }
+      put_partial<P>(a.partials, (size_t)blockIdx.x * PSTRIDE + MAX_M, t1);
+      put_partial<P>(a.partials, (size_t)blockIdx.x * PSTRIDE + MAX_M + 1, t2);
+    }
+  }
+
+  // ---- the last CTA reduces every CTA's partials in a fixed order ----
+  __threadfence();
+  named_bar_sync(1, CONSUMERS);
+  if (tid == 0) {
+    unsigned int tk = atomicAdd(&st->ticket, 1u);
+    *lastflag = (tk == gridDim.x - 1) ? 1 : 0;
+  }
+  named_bar_sync(1, CONSUMERS);
+  if (*lastflag == 0) return;
+  __threadfence();
+  const int slots = (MODE == MODE_AXPY_STORE) ? 2 : nb;
+  for (int q = wid; q < slots; q += CONSUMERS / 32) {
+    const int slot = (MODE == MODE_AXPY_STORE) ? MAX_M + q : q;
+    acc_t acc = zero_acc<P>();
+    for (int b = lane; b < (int)gridDim.x; b += 32)
+      add_partial<P>(acc, a.partials, (size_t)b * PSTRIDE + slot);
+    acc = warp_sum(acc);
+    if (lane == 0) tot[q] = acc_to_double<P>(acc);
+  }
+  named_bar_sync(1, CONSUMERS);
+  if (tid == 0) {
+    finalize_pass(a, tot);
+    __threadfence();
+    st->ticket = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <int P, int MODE>
+static cudaError_t config_t(int max_cols, int K, int num_sms, PassLaunch& out) {
+  using basis_t = typename PassTr<P>::basis_t;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const int ritz_elems = MODE == MODE_RITZ ? max_cols * K : 0;
+  const size_t fixed = smem_plan(MODE, 0, ritz_elems).total + 128;
+  size_t avail = (size_t)optin > fixed ? (size_t)optin - fixed : 0;
+  const size_t per_stage = (size_t)(max_cols > 0 ? max_cols : 1) * TILE_R * sizeof(basis_t);
+  int stages = (int)(avail / per_stage);
+  if (stages > 4) stages = 4;
+  if (stages < 1) return cudaErrorInvalidConfiguration;
+  const size_t region = align_up((size_t)stages * per_stage, 128);
+  const size_t total = smem_plan(MODE, region, ritz_elems).total;
+  e = cudaFuncSetAttribute(pass_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)total);
+  if (e != cudaSuccess) return e;
+  out.grid = num_sms;
+  out.smem = total;
+  out.stages = stages;
+  out.region = region;
+  return cudaSuccess;
+}
+
+cudaError_t pass_config(int prec, int mode, int max_cols, int K, int num_sms, PassLaunch& out) {
+#define TE_CFG(PP, MM) \
+  if (prec == PP && mode == MM) return config_t<PP, MM>(max_cols, K, num_sms, out);
+  TE_CFG(PREC_DDD, MODE_DOT)
+  TE_CFG(PREC_DDD, MODE_AXPY_DOT)
+  TE_CFG(PREC_DDD, MODE_AXPY_STORE)
+  TE_CFG(PREC_DDD, MODE_RITZ)
+  TE_CFG(PREC_FDF, MODE_DOT)
+  TE_CFG(PREC_FDF, MODE_AXPY_DOT)
+  TE_CFG(PREC_FDF, MODE_AXPY_STORE)
+  TE_CFG(PREC_FDF, MODE_RITZ)
+#undef TE_CFG
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pass(int prec, int mode, const PassArgs& a, const PassLaunch& L,
+                        cudaStream_t s) {
+#define TE_LAUNCH(PP, MM)                                                        \
+  if (prec == PP && mode == MM) {                                                \
+    pass_kernel<PP, MM><<<L.grid, PASS_THREADS, L.smem, s>>>(a, L.region);       \
+    return cudaGetLastError();                                                   \
+  }
+  TE_LAUNCH(PREC_DDD, MODE_DOT)
+  TE_LAUNCH(PREC_DDD, MODE_AXPY_DOT)
+  TE_LAUNCH(PREC_DDD, MODE_AXPY_STORE)
+  TE_LAUNCH(PREC_DDD, MODE_RITZ)
+  TE_LAUNCH(PREC_FDF, MODE_DOT)
+  TE_LAUNCH(PREC_FDF, MODE_AXPY_DOT)
+  TE_LAUNCH(PREC_FDF, MODE_AXPY_STORE)
+  TE_LAUNCH(PREC_FDF, MODE_RITZ)
+#undef TE_LAUNCH
+  return cudaErrorInvalidValue;
+}
+
+// out[j*n + r] = s_j * V[j*ld + r]
+template <typename B>
+__global__ void basis_to_f64_kernel(const B* V, int64_t ld, int64_t n, int cols,
+                                    const double* s, double* out) {
+  const int64_t total = n * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n, r = e - j * n;
+    out[e] = s[j] * (double)V[j * ld + r];
+  }
+}
+
+cudaError_t launch_basis_to_f64(int prec, const void* V, int64_t ld, int64_t n, int cols,
+                                const double* s_dev, double* out, cudaStream_t st) {
+  const int64_t total = n * cols;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  if (blocks < 1) blocks = 1;
+  if (prec == PREC_DDD)
+    basis_to_f64_kernel<double><<<(int)blocks, 256, 0, st>>>(static_cast<const double*>(V), ld,
+                                                              n, cols, s_dev, out);
+  else
+    basis_to_f64_kernel<float><<<(int)blocks, 256, 0, st>>>(static_cast<const float*>(V), ld, n,
+                                                             cols, s_dev, out);
+  return cudaGetLastError();
+}
+
+}  // namespace te

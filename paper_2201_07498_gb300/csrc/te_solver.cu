@@ -1,0 +1,833 @@
+// te_solver.cu - host driver and C ABI of the Top-K Lanczos eigensolver.
+//
+// A plan owns the analysis of one matrix (SpMV row partition, validation),
+// the work memory (Lanczos basis, vectors, device state) and, optionally, the
+// whole solve captured as one CUDA graph: init pass, m Lanczos steps (SpMV,
+// three basis passes, three restart passes that exit at once unless the step
+// broke down), the Jacobi kernel and the Ritz contraction.  Scalars (alpha,
+// beta, coefficients, breakdown flag) never leave the device during a solve;
+// the only host synchronisation is the final read of the eigenvalues and the
+// status word.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "te_internal.h"
+#include "topk_eigs.h"
+
+using namespace te;
+
+namespace {
+
+thread_local std::string g_err;
+
+te_status fail(te_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+te_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return e == cudaErrorMemoryAllocation ? TE_ERR_OUT_OF_MEMORY : TE_ERR_CUDA;
+}
+
+#define TE_CK(call, what)                              \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+int prec_of(te_precision p) {
+  if (p.values == TE_F64 && p.arithmetic == TE_F64 && p.vectors == TE_F64) return PREC_DDD;
+  if (p.values == TE_F32 && p.arithmetic == TE_F64 && p.vectors == TE_F32) return PREC_FDF;
+  return -1;
+}
+size_t basis_elt(int prec) { return prec == PREC_DDD ? 8 : 4; }
+size_t value_elt(int prec) { return prec == PREC_DDD ? 8 : 4; }
+
+double breakdown_tol(int prec) { return prec == PREC_DDD ? 1e-12 : 1e-6; }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Work {
+  // byte offsets inside one allocation
+  size_t V = 0, ytil = 0, w = 0, partials = 0, st = 0, blocks = 0, chunks = 0, lrows = 0,
+         lpart = 0, flag = 0, total = 0;
+};
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+Work layout(int prec, int64_t n_pad, int m, int grid, size_t nblocks, size_t nchunks,
+            size_t nlrows) {
+  Work w;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = al256(off + bytes);
+    return o;
+  };
+  w.V = take((size_t)n_pad * (size_t)(m + 1) * basis_elt(prec));
+  w.ytil = take((size_t)n_pad * 8);
+  w.w = take((size_t)n_pad * 8);
+  w.partials = take((size_t)grid * PSTRIDE * 8);
+  w.st = take(sizeof(LzState));
+  w.blocks = take(std::max<size_t>(nblocks, 1) * sizeof(int2));
+  w.chunks = take(std::max<size_t>(nchunks, 1) * sizeof(LongChunk));
+  w.lrows = take(std::max<size_t>(nlrows, 1) * sizeof(LongRow));
+  w.lpart = take(std::max<size_t>(nchunks, 1) * 8);
+  w.flag = take(16);
+  w.total = off;
+  return w;
+}
+
+int64_t pad_rows(int64_t n) { return (n + TILE_R - 1) / TILE_R * TILE_R; }
+
+te_status check_args(const te_csr* A, int32_t K, int32_t m, te_precision p) {
+  if (!A) return fail(TE_ERR_INVALID_ARG, "A is NULL");
+  if (A->n < 1 || A->n >= (int64_t)1 << 31) return fail(TE_ERR_INVALID_ARG, "n out of range");
+  if (A->nnz < 0) return fail(TE_ERR_INVALID_ARG, "nnz < 0");
+  if (!A->row_ptr || !A->col_idx || (!A->values && A->nnz > 0))
+    return fail(TE_ERR_INVALID_ARG, "CSR arrays must not be NULL");
+  if (A->row_scale) return fail(TE_ERR_UNSUPPORTED, "row_scale is reserved (must be NULL)");
+  if (A->where != TE_DEVICE && A->where != TE_HOST)
+    return fail(TE_ERR_INVALID_ARG, "where must be TE_DEVICE or TE_HOST");
+  if (prec_of(p) < 0) return fail(TE_ERR_UNSUPPORTED, "precision must be DDD or FDF");
+  if (K < 1) return fail(TE_ERR_INVALID_ARG, "K must be >= 1");
+  if (m < K) return fail(TE_ERR_INVALID_ARG, "krylov_steps must be >= K");
+  if (m > MAX_M) return fail(TE_ERR_UNSUPPORTED, "krylov_steps must be <= 64");
+  if ((int64_t)m > A->n) return fail(TE_ERR_INVALID_ARG, "krylov_steps must be <= n");
+  return TE_OK;
+}
+
+std::once_flag g_prep_once;
+cudaError_t g_prep_err = cudaSuccess;
+
+}  // namespace
+
+struct te_plan {
+  int prec = 0;
+  int64_t n = 0, n_pad = 0, nnz = 0;
+  int K = 0, m = 0;
+  te_options opt{};
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const void* val = nullptr;
+  void* owned_csr = nullptr;
+  int dev = 0, num_sms = 0;
+  DevPartition part;
+  Work W;
+  char* work = nullptr;
+  LzState* st = nullptr;
+  PassLaunch Ldot, Laxd, Lsto, Lritz;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int nkernels = 0;
+  // profiling: when set, every launch is bracketed by events of kind `kind`
+  struct Prof {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    std::vector<cudaEvent_t> ev;  // pairs
+    std::vector<int> kind;
+    std::vector<double> bytes;
+  } prof;
+  struct HostRes {
+    int restart_flag, restarts, status, sweeps;  // same order as in LzState
+    double theta[MAX_M];
+    double resid[MAX_M];
+  };
+  HostRes* hres = nullptr;  // pinned
+};
+
+namespace {
+
+void* at(te_plan* P, size_t off) { return P->work + off; }
+
+PassArgs base_args(te_plan* P) {
+  PassArgs a;
+  memset(&a, 0, sizeof(a));
+  a.V = at(P, P->W.V);
+  a.Vmut = at(P, P->W.V);
+  a.ld = P->n_pad;
+  a.n = P->n;
+  a.m = P->m;
+  a.K = P->K;
+  a.seed = P->opt.seed;
+  a.tol = breakdown_tol(P->prec);
+  a.st = P->st;
+  a.partials = at(P, P->W.partials);
+  a.fin = FIN_NONE;
+  return a;
+}
+
+// profiling helpers: bracket a launch with two events when profiling is on
+cudaError_t prof_begin(te_plan* P, cudaStream_t s) {
+  if (!P->prof.on) return cudaSuccess;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return e;
+  P->prof.ev.push_back(e0);
+  P->prof.ev.push_back(e1);
+  return cudaEventRecord(e0, s);
+}
+cudaError_t prof_end(te_plan* P, cudaStream_t s, int kind, double bytes) {
+  if (!P->prof.on) return cudaSuccess;
+  P->prof.kind.push_back(kind);
+  P->prof.bytes.push_back(bytes);
+  return cudaEventRecord(P->prof.ev.back(), s);
+}
+
+double pass_bytes(te_plan* P, int mode, const PassArgs& a) {
+  const double n = (double)P->n, sb = (double)basis_elt(P->prec);
+  const double vcols = (double)a.nb * n * sb;
+  switch (mode) {
+    case MODE_DOT: return vcols + n * 8.0;
+    case MODE_AXPY_DOT: return vcols + 2.0 * n * 8.0;
+    case MODE_AXPY_STORE: return vcols + n * 8.0 + n * sb;
+    default: return vcols + n * 8.0 * (double)P->K;
+  }
+}
+
+cudaError_t pass(te_plan* P, int mode, const PassArgs& a, cudaStream_t s) {
+  const PassLaunch& L = mode == MODE_DOT        ? P->Ldot
+                        : mode == MODE_AXPY_DOT ? P->Laxd
+                        : mode == MODE_AXPY_STORE ? P->Lsto
+                                                  : P->Lritz;
+  P->nkernels++;
+  cudaError_t e = prof_begin(P, s);
+  if (e != cudaSuccess) return e;
+  e = launch_pass(P->prec, mode, a, L, s);
+  if (e != cudaSuccess) return e;
+  int kind = mode == MODE_DOT          ? TE_KIND_DOT
+             : mode == MODE_AXPY_DOT   ? TE_KIND_AXPY_DOT
+             : mode == MODE_AXPY_STORE ? TE_KIND_AXPY_STORE
+                                       : TE_KIND_RITZ;
+  if (a.only_on_restart) kind = TE_KIND_RESTART;
+  if (a.fin == FIN_STORE_INIT) kind = TE_KIND_OTHER;
+  return prof_end(P, s, kind, a.only_on_restart ? 0.0 : pass_bytes(P, mode, a));
+}
+
+// Enqueue the Lanczos phase (Algorithm 1): init + m steps.
+cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
+  cudaError_t e;
+  const size_t belt = basis_elt(P->prec);
+  // v_1 = normalised start vector (stored unnormalised, scale s_0)
+  {
+    PassArgs a = base_args(P);
+    a.nb = 0;
+    a.col_out = 0;
+    a.xsrc = X_V1;
+    a.fin = FIN_STORE_INIT;
+    a.step = 0;
+    if ((e = pass(P, MODE_AXPY_STORE, a, s)) != cudaSuccess) return e;
+  }
+  for (int i = 0; i < P->m; ++i) {
+    const void* xi = static_cast<const char*>(at(P, P->W.V)) + (size_t)i * P->n_pad * belt;
+    P->nkernels += 1 + (P->part.nlrows > 0 ? 1 : 0);
+    if ((e = prof_begin(P, s)) != cudaSuccess) return e;
+    e = launch_spmv(P->prec, P->rp, P->ci, P->val, xi, at(P, P->W.ytil), P->n, P->part, false, s);
+    if (e != cudaSuccess) return e;
+    {
+      const double n = (double)P->n, nnz = (double)P->nnz;
+      const double bytes = nnz * (4.0 + (double)value_elt(P->prec)) + 8.0 * (n + 1.0) +
+                           n * (double)basis_elt(P->prec) + n * 8.0;
+      if ((e = prof_end(P, s, TE_KIND_SPMV, bytes)) != cudaSuccess) return e;
+    }
+    PassArgs a = base_args(P);
+    a.nb = i + 1;
+    a.step = i;
+    a.xsrc = X_VEC;
+    a.xvec = at(P, P->W.ytil);
+    a.fin = FIN_DOT_STEP;
+    if ((e = pass(P, MODE_DOT, a, s)) != cudaSuccess) return e;
+    a.wout = at(P, P->W.w);
+    a.fin = FIN_AXPYDOT;
+    if ((e = pass(P, MODE_AXPY_DOT, a, s)) != cudaSuccess) return e;
+    a.xvec = at(P, P->W.w);
+    a.col_out = i + 1;
+    a.fin = FIN_STORE_STEP;
+    if ((e = pass(P, MODE_AXPY_STORE, a, s)) != cudaSuccess) return e;
+    if (i + 1 < P->m) {
+      // restart from a fresh random vector if this step broke down
+      PassArgs r = base_args(P);
+      r.nb = i + 1;
+      r.step = i;
+      r.only_on_restart = 1;
+      r.xsrc = X_RANDOM;
+      r.fin = FIN_DOT_RESTART;
+      if ((e = pass(P, MODE_DOT, r, s)) != cudaSuccess) return e;
+      r.wout = at(P, P->W.w);
+      r.fin = FIN_AXPYDOT;
+      if ((e = pass(P, MODE_AXPY_DOT, r, s)) != cudaSuccess) return e;
+      r.xsrc = X_VEC;
+      r.xvec = at(P, P->W.w);
+      r.col_out = i + 1;
+      r.fin = FIN_STORE_RESTART;
+      if ((e = pass(P, MODE_AXPY_STORE, r, s)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_solve(te_plan* P, cudaStream_t s) {
+  P->nkernels = 0;
+  cudaError_t e = enqueue_lanczos(P, s);
+  if (e != cudaSuccess) return e;
+  JacobiArgs j;
+  memset(&j, 0, sizeof(j));
+  j.alpha = P->st->alpha;
+  j.beta = P->st->beta;
+  j.s = P->st->s;
+  j.m = P->m;
+  j.K = P->K;
+  j.which = P->opt.which;
+  j.theta_out = P->st->theta_sel;
+  j.C_out = P->st->C;
+  j.resid_out = P->st->resid_est;
+  j.st = P->st;
+  P->nkernels++;
+  if ((e = prof_begin(P, s)) != cudaSuccess) return e;
+  if ((e = launch_jacobi(j, s)) != cudaSuccess) return e;
+  if ((e = prof_end(P, s, TE_KIND_JACOBI, 0.0)) != cudaSuccess) return e;
+  PassArgs a = base_args(P);
+  a.nb = P->m;
+  a.fin = FIN_NONE;
+  return pass(P, MODE_RITZ, a, s);
+}
+
+__global__ void solve_begin_kernel(LzState* st, const double* v1, double* eigvecs,
+                                   double* eigvals) {
+  st->v1 = v1;
+  st->eigvecs = eigvecs;
+  st->eigvals_out = eigvals;
+  st->status = 0;
+  st->restarts = 0;
+  st->restart_flag = 0;
+  st->sweeps = 0;
+  st->ticket = 0;
+}
+
+te_status plan_begin(te_plan* P, const double* v1, double* eigvecs_dev, double* eigvals_dev,
+                     cudaStream_t s) {
+  solve_begin_kernel<<<1, 1, 0, s>>>(P->st, v1 ? v1 : P->opt.v1, eigvecs_dev, eigvals_dev);
+  TE_CK(cudaGetLastError(), "solve_begin launch");
+  return TE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void te_default_options(te_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->seed = 0;
+  opt->v1 = nullptr;
+  opt->which = TE_WHICH_LARGEST_MAGNITUDE;
+  opt->use_graph = 1;
+  opt->device_budget_bytes = 0;
+}
+
+const char* te_last_error(void) { return g_err.c_str(); }
+
+const char* te_status_string(te_status s) {
+  switch (s) {
+    case TE_OK: return "TE_OK";
+    case TE_ERR_INVALID_ARG: return "TE_ERR_INVALID_ARG";
+    case TE_ERR_OUT_OF_MEMORY: return "TE_ERR_OUT_OF_MEMORY";
+    case TE_ERR_CUDA: return "TE_ERR_CUDA";
+    case TE_ERR_BREAKDOWN: return "TE_ERR_BREAKDOWN";
+    case TE_ERR_NOT_CONVERGED: return "TE_ERR_NOT_CONVERGED";
+    case TE_ERR_TIMEOUT: return "TE_ERR_TIMEOUT";
+    case TE_ERR_UNSUPPORTED: return "TE_ERR_UNSUPPORTED";
+  }
+  return "TE_ERR_UNKNOWN";
+}
+
+size_t te_workspace_bytes(const te_csr* A, int32_t K, int32_t krylov_steps, te_precision p) {
+  if (check_args(A, K, krylov_steps, p) != TE_OK) return 0;
+  const int prec = prec_of(p);
+  // partition sizes are bounded without reading the matrix
+  const int tn = spmv_tile_nnz(prec);
+  const size_t nblocks = (size_t)(A->nnz / (tn / 4) + A->n / SPMV_RMAX + 2);
+  const size_t nchunks = (size_t)(A->nnz / tn + A->nnz / (tn / 4) + 1);
+  Work w = layout(prec, pad_rows(A->n), krylov_steps, 1024, nblocks, nchunks, nchunks);
+  return w.total;
+}
+
+void te_plan_destroy(te_plan* P) {
+  if (!P) return;
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  if (P->work) cudaFree(P->work);
+  if (P->owned_csr) cudaFree(P->owned_csr);
+  if (P->hres) cudaFreeHost(P->hres);
+  delete P;
+}
+
+te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_precision p,
+                         const te_options* opt_in, void* stream, te_plan** out) {
+  if (!out) return fail(TE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  te_status st0 = check_args(A, K, krylov_steps, p);
+  if (st0 != TE_OK) return st0;
+  te_options opt;
+  if (opt_in) opt = *opt_in;
+  else te_default_options(&opt);
+  if (opt.which != TE_WHICH_LARGEST_MAGNITUDE && opt.which != TE_WHICH_LARGEST_ALGEBRAIC)
+    return fail(TE_ERR_INVALID_ARG, "which must be TE_WHICH_*");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  std::call_once(g_prep_once, [] { g_prep_err = jacobi_prepare(); });
+  if (g_prep_err != cudaSuccess) return cuda_fail(g_prep_err, "jacobi_prepare");
+
+  te_plan* P = new te_plan();
+  struct Guard {
+    te_plan*& p;
+    bool keep = false;
+    ~Guard() {
+      if (!keep) te_plan_destroy(p);
+    }
+  } guard{P};
+
+  P->prec = prec_of(p);
+  P->n = A->n;
+  P->nnz = A->nnz;
+  P->n_pad = pad_rows(A->n);
+  P->K = K;
+  P->m = krylov_steps;
+  P->opt = opt;
+  TE_CK(cudaGetDevice(&P->dev), "cudaGetDevice");
+  TE_CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev),
+        "device attribute");
+
+  // row pointers on the host for the partition
+  std::vector<int64_t> rp_host;
+  const int64_t* rph = A->row_ptr;
+  if (A->where == TE_DEVICE) {
+    rp_host.resize((size_t)A->n + 1);
+    TE_CK(cudaMemcpyAsync(rp_host.data(), A->row_ptr, sizeof(int64_t) * (A->n + 1),
+                          cudaMemcpyDeviceToHost, s),
+          "copy row_ptr to host");
+    TE_CK(cudaStreamSynchronize(s), "sync");
+    rph = rp_host.data();
+  }
+  Partition part;
+  std::string perr;
+  if (!make_partition(rph, A->n, A->nnz, spmv_tile_nnz(P->prec), part, perr))
+    return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+
+  // launch shapes of the basis passes
+  TE_CK(pass_config(P->prec, MODE_DOT, P->m, P->K, P->num_sms, P->Ldot), "configure dot pass");
+  TE_CK(pass_config(P->prec, MODE_AXPY_DOT, P->m, P->K, P->num_sms, P->Laxd),
+        "configure axpy pass");
+  TE_CK(pass_config(P->prec, MODE_AXPY_STORE, P->m, P->K, P->num_sms, P->Lsto),
+        "configure store pass");
+  TE_CK(pass_config(P->prec, MODE_RITZ, P->m, P->K, P->num_sms, P->Lritz),
+        "configure ritz pass");
+  const int grid = std::max(std::max(P->Ldot.grid, P->Laxd.grid),
+                            std::max(P->Lsto.grid, P->Lritz.grid));
+
+  P->W = layout(P->prec, P->n_pad, P->m, grid, part.blocks.size(), part.chunks.size(),
+                part.lrows.size());
+  size_t csr_bytes = 0;
+  if (A->where == TE_HOST)
+    csr_bytes = al256(sizeof(int64_t) * (A->n + 1)) + al256(sizeof(int32_t) * A->nnz) +
+                al256(value_elt(P->prec) * A->nnz);
+  if (opt.device_budget_bytes > 0 && P->W.total + csr_bytes > opt.device_budget_bytes)
+    return fail(TE_ERR_OUT_OF_MEMORY, "work memory exceeds device_budget_bytes");
+
+  TE_CK(cudaMalloc(&P->work, P->W.total), "allocate work memory");
+  TE_CK(cudaMallocHost(&P->hres, sizeof(te_plan::HostRes)), "allocate pinned result buffer");
+  P->st = static_cast<LzState*>(at(P, P->W.st));
+
+  if (A->where == TE_HOST) {
+    TE_CK(cudaMalloc(&P->owned_csr, csr_bytes), "allocate device CSR");
+    char* b = static_cast<char*>(P->owned_csr);
+    int64_t* drp = reinterpret_cast<int64_t*>(b);
+    int32_t* dci = reinterpret_cast<int32_t*>(b + al256(sizeof(int64_t) * (A->n + 1)));
+    void* dval = b + al256(sizeof(int64_t) * (A->n + 1)) + al256(sizeof(int32_t) * A->nnz);
+    TE_CK(cudaMemcpyAsync(drp, A->row_ptr, sizeof(int64_t) * (A->n + 1),
+                          cudaMemcpyHostToDevice, s),
+          "copy row_ptr");
+    if (A->nnz > 0) {
+      TE_CK(cudaMemcpyAsync(dci, A->col_idx, sizeof(int32_t) * A->nnz, cudaMemcpyHostToDevice,
+                            s),
+            "copy col_idx");
+      TE_CK(cudaMemcpyAsync(dval, A->values, value_elt(P->prec) * A->nnz,
+                            cudaMemcpyHostToDevice, s),
+            "copy values");
+    }
+    P->rp = drp;
+    P->ci = dci;
+    P->val = dval;
+  } else {
+    P->rp = A->row_ptr;
+    P->ci = A->col_idx;
+    P->val = A->values;
+  }
+
+  // zero the work memory (the padded rows of V, y and w must stay zero)
+  TE_CK(cudaMemsetAsync(P->work, 0, P->W.total, s), "clear work memory");
+  // partition to the device
+  P->part.nshort = (int)part.blocks.size();
+  P->part.nchunks = (int)part.chunks.size();
+  P->part.nlrows = (int)part.lrows.size();
+  P->part.blocks = static_cast<int2*>(at(P, P->W.blocks));
+  P->part.chunks = static_cast<LongChunk*>(at(P, P->W.chunks));
+  P->part.lrows = static_cast<LongRow*>(at(P, P->W.lrows));
+  P->part.lpart = at(P, P->W.lpart);
+  if (!part.blocks.empty())
+    TE_CK(cudaMemcpyAsync(P->part.blocks, part.blocks.data(), part.blocks.size() * sizeof(int2),
+                          cudaMemcpyHostToDevice, s),
+          "copy partition");
+  if (!part.chunks.empty())
+    TE_CK(cudaMemcpyAsync(P->part.chunks, part.chunks.data(),
+                          part.chunks.size() * sizeof(LongChunk), cudaMemcpyHostToDevice, s),
+          "copy partition");
+  if (!part.lrows.empty())
+    TE_CK(cudaMemcpyAsync(P->part.lrows, part.lrows.data(), part.lrows.size() * sizeof(LongRow),
+                          cudaMemcpyHostToDevice, s),
+          "copy partition");
+  // column indices must lie in [0, n)
+  int* dflag = static_cast<int*>(at(P, P->W.flag));
+  TE_CK(launch_validate_cols(P->ci, P->nnz, P->n, dflag, s), "validate columns");
+  int hflag = 0;
+  TE_CK(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
+  TE_CK(cudaStreamSynchronize(s), "plan setup");
+  if (hflag) return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
+
+  if (opt.use_graph) {
+    TE_CK(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking), "create capture stream");
+    TE_CK(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = enqueue_solve(P, P->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(P->cap, &g);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e, "capture solve");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+    e = cudaGraphInstantiate(&P->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
+  }
+  guard.keep = true;
+  *out = P;
+  return TE_OK;
+}
+
+te_status te_plan_launch(te_plan* P, const double* v1, double* eigvals_dev, double* eigvecs_dev,
+                         void* stream) {
+  if (!P) return fail(TE_ERR_INVALID_ARG, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  te_status r = plan_begin(P, v1, eigvecs_dev, eigvals_dev, s);
+  if (r != TE_OK) return r;
+  if (P->gexec) {
+    TE_CK(cudaGraphLaunch(P->gexec, s), "graph launch");
+  } else {
+    TE_CK(enqueue_solve(P, s), "enqueue solve");
+  }
+  return TE_OK;
+}
+
+te_status te_plan_status(te_plan* P) {
+  if (!P) return fail(TE_ERR_INVALID_ARG, "plan is NULL");
+  int status = 0;
+  TE_CK(cudaMemcpy(&status, &P->st->status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  if (status != 0) return fail((te_status)status, "device-side status of the last solve");
+  return TE_OK;
+}
+
+int32_t te_plan_kernel_count(const te_plan* P) { return P ? P->nkernels : 0; }
+
+te_status te_plan_profile(te_plan* P, double* ms, int32_t* launches, double* bytes,
+                          void* stream) {
+  if (!P) return fail(TE_ERR_INVALID_ARG, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* U = nullptr;  // the Ritz contraction needs somewhere to write
+  TE_CK(cudaMalloc(&U, sizeof(double) * (size_t)P->n * P->K), "allocate profile eigvecs");
+  te_status r = plan_begin(P, nullptr, U, nullptr, s);
+  if (r != TE_OK) {
+    cudaFree(U);
+    return r;
+  }
+  P->prof = te_plan::Prof();
+  P->prof.on = true;
+  const int saved = P->nkernels;
+  cudaError_t e = enqueue_solve(P, s);
+  P->nkernels = saved;
+  P->prof.on = false;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  double acc_ms[TE_NUM_KINDS] = {0}, acc_b[TE_NUM_KINDS] = {0};
+  int32_t cnt[TE_NUM_KINDS] = {0};
+  for (size_t k = 0; e == cudaSuccess && k < P->prof.kind.size(); ++k) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, P->prof.ev[2 * k], P->prof.ev[2 * k + 1]);
+    acc_ms[P->prof.kind[k]] += t;
+    acc_b[P->prof.kind[k]] += P->prof.bytes[k];
+    cnt[P->prof.kind[k]] += 1;
+  }
+  for (cudaEvent_t ev : P->prof.ev) cudaEventDestroy(ev);
+  P->prof = te_plan::Prof();
+  cudaFree(U);
+  if (e != cudaSuccess) return cuda_fail(e, "te_plan_profile");
+  for (int k = 0; k < TE_NUM_KINDS; ++k) {
+    if (ms) ms[k] = acc_ms[k];
+    if (launches) launches[k] = cnt[k];
+    if (bytes) bytes[k] = acc_b[k];
+  }
+  return te_plan_status(P);
+}
+
+te_status te_plan_solve(te_plan* P, const double* v1, double* eigvals, double* eigvecs,
+                        double* residuals, void* stream) {
+  if (!P) return fail(TE_ERR_INVALID_ARG, "plan is NULL");
+  if (!eigvals) return fail(TE_ERR_INVALID_ARG, "eigvals is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* U = eigvecs;
+  double* Utmp = nullptr;
+  if (eigvecs && !is_device_ptr(eigvecs)) {
+    TE_CK(cudaMalloc(&Utmp, sizeof(double) * (size_t)P->n * P->K), "allocate eigvecs staging");
+    U = Utmp;
+  }
+  te_status r = te_plan_launch(P, v1, nullptr, U, stream);
+  if (r != TE_OK) {
+    if (Utmp) cudaFree(Utmp);
+    return r;
+  }
+  cudaError_t e = cudaMemcpyAsync(&P->hres->restart_flag, &P->st->restart_flag, 4 * sizeof(int),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P->hres->theta, P->st->theta_sel, sizeof(double) * P->K,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(P->hres->resid, P->st->resid_est, sizeof(double) * P->K,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    if (Utmp) cudaFree(Utmp);
+    return cuda_fail(e, "solve");
+  }
+  const int status = P->hres->status;
+  if (status != 0 && status != TE_ERR_BREAKDOWN) {
+    if (Utmp) cudaFree(Utmp);
+    return fail((te_status)status, std::string("device-side failure: ") +
+                                       te_status_string((te_status)status));
+  }
+  // outputs
+  if (Utmp) {
+    e = cudaMemcpy(eigvecs, Utmp, sizeof(double) * (size_t)P->n * P->K, cudaMemcpyDeviceToHost);
+    cudaFree(Utmp);
+    if (e != cudaSuccess) return cuda_fail(e, "copy eigvecs");
+  }
+  const cudaMemcpyKind kv = is_device_ptr(eigvals) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  TE_CK(cudaMemcpy(eigvals, P->hres->theta, sizeof(double) * P->K, kv), "copy eigvals");
+  if (residuals) {
+    const cudaMemcpyKind kr =
+        is_device_ptr(residuals) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    TE_CK(cudaMemcpy(residuals, P->hres->resid, sizeof(double) * P->K, kr), "copy residuals");
+  }
+  if (status == TE_ERR_BREAKDOWN) return fail(TE_ERR_BREAKDOWN, "Krylov space could not be extended");
+  return TE_OK;
+}
+
+te_status te_topk_eigs(const te_csr* A, int32_t K, int32_t krylov_steps, te_precision p,
+                       const te_options* opt, double* eigvals, double* eigvecs,
+                       double* residuals, void* stream) {
+  te_options o;
+  if (opt) o = *opt;
+  else te_default_options(&o);
+  o.use_graph = 0;  // a single solve: launch directly
+  te_plan* P = nullptr;
+  te_status r = te_plan_create(A, K, krylov_steps, p, &o, stream, &P);
+  if (r != TE_OK) return r;
+  r = te_plan_solve(P, nullptr, eigvals, eigvecs, residuals, stream);
+  std::string keep = g_err;
+  te_plan_destroy(P);
+  g_err = keep;
+  return r;
+}
+
+te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, void* stream) {
+  if (!A) return fail(TE_ERR_INVALID_ARG, "A is NULL");
+  te_status r = check_args(A, 1, 1, p);
+  if (r != TE_OK) return r;
+  if (A->where != TE_DEVICE) return fail(TE_ERR_INVALID_ARG, "te_spmv needs a TE_DEVICE matrix");
+  if (!x || !y) return fail(TE_ERR_INVALID_ARG, "x and y must not be NULL");
+  const int prec = prec_of(p);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<int64_t> rp((size_t)A->n + 1);
+  TE_CK(cudaMemcpyAsync(rp.data(), A->row_ptr, sizeof(int64_t) * (A->n + 1),
+                        cudaMemcpyDeviceToHost, s),
+        "copy row_ptr");
+  TE_CK(cudaStreamSynchronize(s), "sync");
+  Partition part;
+  std::string perr;
+  if (!make_partition(rp.data(), A->n, A->nnz, spmv_tile_nnz(prec), part, perr))
+    return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+  const size_t b0 = al256(std::max<size_t>(part.blocks.size(), 1) * sizeof(int2));
+  const size_t b1 = al256(std::max<size_t>(part.chunks.size(), 1) * sizeof(LongChunk));
+  const size_t b2 = al256(std::max<size_t>(part.lrows.size(), 1) * sizeof(LongRow));
+  const size_t b3 = al256(std::max<size_t>(part.chunks.size(), 1) * 8);
+  char* buf = nullptr;
+  TE_CK(cudaMalloc(&buf, b0 + b1 + b2 + b3 + 256), "allocate SpMV partition");
+  DevPartition dp;
+  dp.blocks = reinterpret_cast<int2*>(buf);
+  dp.chunks = reinterpret_cast<LongChunk*>(buf + b0);
+  dp.lrows = reinterpret_cast<LongRow*>(buf + b0 + b1);
+  dp.lpart = buf + b0 + b1 + b2;
+  int* flag = reinterpret_cast<int*>(buf + b0 + b1 + b2 + b3);
+  dp.nshort = (int)part.blocks.size();
+  dp.nchunks = (int)part.chunks.size();
+  dp.nlrows = (int)part.lrows.size();
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e == cudaSuccess && dp.nshort)
+    e = cudaMemcpyAsync(dp.blocks, part.blocks.data(), dp.nshort * sizeof(int2),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && dp.nchunks)
+    e = cudaMemcpyAsync(dp.chunks, part.chunks.data(), dp.nchunks * sizeof(LongChunk),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && dp.nlrows)
+    e = cudaMemcpyAsync(dp.lrows, part.lrows.data(), dp.nlrows * sizeof(LongRow),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_validate_cols(A->col_idx, A->nnz, A->n, flag, s);
+  int hflag = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && hflag) {
+    cudaFree(buf);
+    return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
+  }
+  if (e == cudaSuccess)
+    e = launch_spmv(prec, A->row_ptr, A->col_idx, A->values, x, y, A->n, dp, true, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "te_spmv");
+  return TE_OK;
+}
+
+te_status te_lanczos(const te_csr* A, int32_t krylov_steps, te_precision p, const te_options* opt,
+                     double* alpha, double* beta, double* basis, int32_t* restarts,
+                     void* stream) {
+  if (!alpha || !beta) return fail(TE_ERR_INVALID_ARG, "alpha and beta must not be NULL");
+  te_options o;
+  if (opt) o = *opt;
+  else te_default_options(&o);
+  o.use_graph = 0;
+  te_plan* P = nullptr;
+  te_status r = te_plan_create(A, 1, krylov_steps, p, &o, stream, &P);
+  if (r != TE_OK) return r;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  r = plan_begin(P, nullptr, nullptr, nullptr, s);
+  cudaError_t e = cudaSuccess;
+  if (r == TE_OK) e = enqueue_lanczos(P, s);
+  std::vector<double> a_h(krylov_steps), b_h(krylov_steps + 1);
+  int hst[4] = {0, 0, 0, 0};
+  if (r == TE_OK && e == cudaSuccess)
+    e = cudaMemcpyAsync(a_h.data(), P->st->alpha, sizeof(double) * krylov_steps,
+                        cudaMemcpyDeviceToHost, s);
+  if (r == TE_OK && e == cudaSuccess)
+    e = cudaMemcpyAsync(b_h.data(), P->st->beta, sizeof(double) * (krylov_steps + 1),
+                        cudaMemcpyDeviceToHost, s);
+  if (r == TE_OK && e == cudaSuccess)
+    e = cudaMemcpyAsync(hst, &P->st->restart_flag, sizeof(hst), cudaMemcpyDeviceToHost, s);
+  if (r == TE_OK && e == cudaSuccess && basis)
+    e = launch_basis_to_f64(P->prec, at(P, P->W.V), P->n_pad, P->n, krylov_steps, P->st->s,
+                            basis, s);
+  if (r == TE_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (r == TE_OK && e != cudaSuccess) r = cuda_fail(e, "te_lanczos");
+  if (r == TE_OK) {
+    const int status = hst[2];
+    if (status != 0 && status != TE_ERR_BREAKDOWN)
+      r = fail((te_status)status, "device-side failure in the Lanczos phase");
+  }
+  if (r == TE_OK) {
+    memcpy(alpha, a_h.data(), sizeof(double) * krylov_steps);
+    memcpy(beta, b_h.data(), sizeof(double) * (krylov_steps + 1));
+    if (restarts) *restarts = hst[1];
+    if (hst[2] == TE_ERR_BREAKDOWN) r = fail(TE_ERR_BREAKDOWN, "restart failed");
+  }
+  std::string keep = g_err;
+  te_plan_destroy(P);
+  g_err = keep;
+  return r;
+}
+
+te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, int32_t which,
+                          double* theta, double* Y, int32_t* sweeps, void* stream) {
+  if (m < 1 || m > MAX_M) return fail(TE_ERR_INVALID_ARG, "m must be in [1, 64]");
+  if (!alpha || !beta || !theta) return fail(TE_ERR_INVALID_ARG, "NULL argument");
+  if (which != TE_WHICH_LARGEST_MAGNITUDE && which != TE_WHICH_LARGEST_ALGEBRAIC)
+    return fail(TE_ERR_INVALID_ARG, "which must be TE_WHICH_*");
+  std::call_once(g_prep_once, [] { g_prep_err = jacobi_prepare(); });
+  if (g_prep_err != cudaSuccess) return cuda_fail(g_prep_err, "jacobi_prepare");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* dbuf = nullptr;
+  TE_CK(cudaMalloc(&dbuf, 2 * sizeof(int)), "allocate status");
+  JacobiArgs j;
+  memset(&j, 0, sizeof(j));
+  j.alpha = alpha;
+  j.beta = beta;
+  j.m = m;
+  j.K = m;
+  j.which = which;
+  j.theta_out = theta;
+  j.Y_out = Y;
+  j.sweeps_out = dbuf;
+  j.status_out = dbuf + 1;
+  cudaError_t e = launch_jacobi(j, s);
+  int h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, dbuf, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dbuf);
+  if (e != cudaSuccess) return cuda_fail(e, "te_tridiag_eigs");
+  if (sweeps) *sweeps = h[0];
+  if (h[1] != 0) return fail((te_status)h[1], "Jacobi sweeps did not converge");
+  return TE_OK;
+}
+
+te_status te_spmv_partition(const int64_t* row_ptr, int64_t n, int64_t nnz, te_precision p,
+                            int64_t* nblocks, int64_t* nchunks, int64_t* nlong_rows,
+                            int32_t* blocks, int64_t* chunks) {
+  if (!row_ptr || n < 1 || nnz < 0) return fail(TE_ERR_INVALID_ARG, "bad arguments");
+  const int prec = prec_of(p);
+  if (prec < 0) return fail(TE_ERR_UNSUPPORTED, "precision must be DDD or FDF");
+  Partition part;
+  std::string perr;
+  if (!make_partition(row_ptr, n, nnz, spmv_tile_nnz(prec), part, perr))
+    return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+  if (nblocks) *nblocks = (int64_t)part.blocks.size();
+  if (nchunks) *nchunks = (int64_t)part.chunks.size();
+  if (nlong_rows) *nlong_rows = (int64_t)part.lrows.size();
+  if (blocks)
+    for (size_t b = 0; b < part.blocks.size(); ++b) {
+      blocks[2 * b] = part.blocks[b].x;
+      blocks[2 * b + 1] = part.blocks[b].y;
+    }
+  if (chunks)
+    for (size_t c = 0; c < part.chunks.size(); ++c) {
+      chunks[3 * c] = part.chunks[c].k0;
+      chunks[3 * c + 1] = part.chunks[c].k1;
+      chunks[3 * c + 2] = part.chunks[c].row;
+    }
+  return TE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The library must load, export every function ``include/*.h`` declares,
+reject bad arguments before touching the GPU, and partition rows for the
+SpMV so that every row and every non-zero is covered exactly once.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def te():
+    from paper_2201_07498_gb300 import _build
+    _build.build()
+    import paper_2201_07498_gb300 as te
+    te.load_library()
+    return te
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(te_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(te):
+    names = _declared_functions()
+    assert len(names) >= 14, names
+    lib = ctypes.CDLL(te.library_path())
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+    # the Python binding covers every declared function too
+    assert set(names) <= set(te._SIGS), set(names) - set(te._SIGS)
+
+
+def test_status_strings_and_defaults(te):
+    lib = te.load_library()
+    assert lib.te_status_string(0) == b"TE_OK"
+    assert lib.te_status_string(4) == b"TE_ERR_BREAKDOWN"
+    o = te.te_options()
+    lib.te_default_options(ctypes.byref(o))
+    assert o.seed == 0 and o.which == 0 and o.use_graph == 1 and o.device_budget_bytes == 0
+
+
+def _desc(n, nnz, where=1, scale=None):
+    rp = np.zeros(n + 1, dtype=np.int64)
+    ci = np.zeros(max(nnz, 1), dtype=np.int32)
+    va = np.zeros(max(nnz, 1))
+    keep = (rp, ci, va)
+    A = __import__("paper_2201_07498_gb300").te_csr(n, nnz, rp.ctypes.data, ci.ctypes.data,
+                                                    va.ctypes.data, scale, where)
+    return A, keep
+
+
+@pytest.mark.parametrize("K,m,prec,expect", [
+    (0, 4, "ddd", 1),          # K < 1
+    (5, 4, "ddd", 1),          # m < K
+    (4, 65, "ddd", 7),         # m above the supported maximum
+    (4, 11, "ddd", 1),         # m > n (n = 10)
+    (2, 4, (1, 1, 1), 7),      # FFF not implemented
+    (2, 4, (2, 0, 0), 7),      # BF16 values not implemented
+])
+def test_argument_validation_before_gpu(te, K, m, prec, expect):
+    lib = te.load_library()
+    A, keep = _desc(10, 0)
+    ev = np.zeros(max(K, 1))
+    rc = lib.te_topk_eigs(ctypes.byref(A), K, m, te._prec(prec), None,
+                          ctypes.c_void_p(ev.ctypes.data), None, None, None)
+    assert rc == expect, (rc, lib.te_last_error())
+    assert lib.te_last_error() != b""
+
+
+def test_null_and_reserved_arguments(te):
+    lib = te.load_library()
+    ev = np.zeros(4)
+    assert lib.te_topk_eigs(None, 2, 4, te._prec("ddd"), None, ctypes.c_void_p(ev.ctypes.data),
+                            None, None, None) == 1
+    A, keep = _desc(10, 0, scale=ctypes.c_void_p(ev.ctypes.data).value)
+    assert lib.te_topk_eigs(ctypes.byref(A), 2, 4, te._prec("ddd"), None,
+                            ctypes.c_void_p(ev.ctypes.data), None, None, None) == 7
+    A, keep = _desc(10, 0, where=5)
+    assert lib.te_topk_eigs(ctypes.byref(A), 2, 4, te._prec("ddd"), None,
+                            ctypes.c_void_p(ev.ctypes.data), None, None, None) == 1
+
+
+def test_workspace_bytes(te):
+    lib = te.load_library()
+    n = 1 << 24
+    A, keep = _desc(1, 0)
+    A.n, A.nnz = n, 268_000_000
+    b_fdf = lib.te_workspace_bytes(ctypes.byref(A), 24, 48, te._prec("fdf"))
+    b_ddd = lib.te_workspace_bytes(ctypes.byref(A), 24, 48, te._prec("ddd"))
+    # basis (m+1 columns) + two n-vectors dominate
+    assert b_fdf >= n * 49 * 4 + 2 * n * 8
+    assert b_ddd >= n * 49 * 8 + 2 * n * 8
+    assert b_ddd > b_fdf
+    assert lib.te_workspace_bytes(ctypes.byref(A), 0, 48, te._prec("fdf")) == 0
+
+
+def _check_partition(rp, nnz, blocks, chunks, nlong, tile):
+    n = len(rp) - 1
+    lens = np.diff(rp)
+    long_rows = np.nonzero(lens > tile // 4)[0]
+    assert nlong == len(long_rows)
+    covered = np.zeros(n, dtype=np.int64)
+    prev_end = 0
+    for r0, r1 in blocks:
+        assert r1 > r0
+        assert r1 - r0 <= 1024
+        assert rp[r1] - rp[r0] <= tile
+        assert np.all(lens[r0:r1] <= tile // 4)
+        covered[r0:r1] += 1
+        assert r0 >= prev_end
+        prev_end = r1
+    nz_cov = np.zeros(n, dtype=np.int64)
+    for k0, k1, row in chunks:
+        assert rp[row] <= k0 < k1 <= rp[row + 1]
+        assert k1 - k0 <= tile
+        nz_cov[row] += k1 - k0
+    for r in long_rows:
+        assert covered[r] == 0
+        assert nz_cov[r] == lens[r]
+    short = np.ones(n, dtype=bool)
+    short[long_rows] = False
+    assert np.all(covered[short] == 1)
+
+
+@pytest.mark.parametrize("prec,tile", [("ddd", 2048), ("fdf", 4096)])
+def test_partition_covers_rows_once(te, prec, tile):
+    mats = [synth.uniform_sym(5000, 7, 3), synth.rmat_sym(14, 8, 5)]
+    # crafted: empty rows, a star (one very long row), rows around the thresholds
+    n = 20000
+    lens = np.zeros(n, dtype=np.int64)
+    lens[::7] = 3
+    lens[5] = n - 1
+    lens[100] = tile // 4
+    lens[101] = tile // 4 + 1
+    lens[102] = tile
+    lens[103] = tile + 1
+    lens[104] = 3 * tile
+    rp = np.concatenate([[0], np.cumsum(lens)])
+    for A in mats:
+        blocks, chunks, nl = te.spmv_partition(A.row_ptr, A.nnz, prec)
+        _check_partition(A.row_ptr, A.nnz, blocks, chunks, nl, tile)
+    blocks, chunks, nl = te.spmv_partition(rp, int(rp[-1]), prec)
+    _check_partition(rp, int(rp[-1]), blocks, chunks, nl, tile)
+    assert nl == 5
+
+
+def test_partition_rejects_malformed_row_ptr(te):
+    with pytest.raises(te.TEError) as e:
+        te.spmv_partition(np.array([0, 3, 2, 5]), 5)
+    assert e.value.status == 1
+    with pytest.raises(te.TEError):
+        te.spmv_partition(np.array([1, 3, 4]), 4)
+    with pytest.raises(te.TEError):
+        te.spmv_partition(np.array([0, 3, 4]), 5)
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The product package must not import the oracle or the generators."""
+    pkg = os.path.join(ROOT, "paper_2201_07498_gb300")
+    for f in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True) + \
+            glob.glob(os.path.join(pkg, "csrc", "*")):
+        src = open(f).read()
+        assert "import oracle" not in src and "from oracle" not in src, f
+        assert "oracle.h" not in src, f
+        assert "import synth" not in src, f
