@@ -1,0 +1,109 @@
+"""Parity at the benchmark's full size: symmetric R-MAT 2^24, edge factor 8,
+normalised adjacency, seed 1 (about 268M stored non-zeros).
+
+* SpMV: sampled rows (random rows, the longest rows, empty rows) against the
+  oracle computing those rows one by one, within the summation bound.
+* FP64 solve, K = 8, m = 16: against the full oracle run (same start vector).
+* FDF solve, K = 24, m = 48, through a plan with its CUDA graph (the launch
+  configuration the benchmark times): eigenvalues within 1e-6 of the FP64
+  GPU solve, inside the spectrum bound |lambda| <= 1 of a normalised
+  adjacency, and residual estimates consistent with true residuals.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SCALE, EF, SEED = 24, 8, 1
+
+
+@pytest.fixture(scope="module")
+def te():
+    import paper_2201_07498_gb300 as te
+    te.load_library(build_if_missing=True)
+    return te
+
+
+@pytest.fixture(scope="module")
+def big():
+    A = synth.rmat_sym(SCALE, EF, SEED)
+    v1 = synth.start_vector(A.n, SEED)
+    return A, v1
+
+
+def _sample_rows(A, rng):
+    deg = np.diff(A.row_ptr)
+    rows = list(rng.choice(A.n, size=2000, replace=False))
+    rows += list(np.argsort(deg)[-20:])          # the longest rows (multi-chunk)
+    rows += list(np.nonzero(deg == 0)[0][:10])   # empty rows
+    return np.array(sorted(set(int(r) for r in rows)))
+
+
+@pytest.mark.parametrize("prec", ["ddd", "fdf"])
+def test_fullsize_spmv_sampled_rows(te, big, prec):
+    A, _ = big
+    x = synth.uniform_pm1(A.n, 77, 3)
+    rows = _sample_rows(A, np.random.default_rng(0))
+    if prec == "fdf":
+        val = A.val.astype(np.float32).astype(np.float64)
+        x = x.astype(np.float32).astype(np.float64)
+        xd = torch.from_numpy(x.astype(np.float32)).cuda()
+        u = 2.0 ** -44
+    else:
+        val = A.val
+        xd = torch.from_numpy(x).cuda()
+        u = 2.0 ** -53
+    Ah = synth.CSR(A.n, A.row_ptr, A.col, val)
+    y = te.spmv(te.CSR.from_host(Ah, prec), xd, prec)[torch.from_numpy(rows).cuda()].cpu().numpy()
+    ref = oracle.spmv_rows(Ah, x, rows)
+    absref = oracle.spmv_rows(synth.CSR(A.n, A.row_ptr, A.col, np.abs(val)), np.abs(x), rows)
+    k = np.maximum(np.diff(A.row_ptr)[rows], 1)
+    bound = 2 * k * u / (1 - k * u) * absref + 1e-300
+    assert np.all(np.abs(y - ref) <= bound)
+
+
+def test_fullsize_fp64_solve_matches_oracle(te, big):
+    A, v1 = big
+    K, m = 8, 16
+    ref = oracle.topk_eigs(A, K, m, v1, seed=SEED, want_residuals=False)
+    csr = te.CSR.from_host(A, "ddd")
+    plan = te.Plan(csr, K, m, "ddd", seed=SEED)
+    ev, U, _ = plan.solve()
+    ev = ev.numpy()
+    assert np.all(np.diff(np.abs(ev)) <= 0)
+    # +-1 tie in modulus: compare as sets, then the vectors pairwise
+    order_g, order_r = np.argsort(ev), np.argsort(ref.eigvals)
+    assert np.max(np.abs(ev[order_g] - ref.eigvals[order_r])) <= 1e-10
+    Ug = U.cpu().numpy()
+    for a, b in zip(order_g, order_r):
+        u, w = Ug[:, a], ref.eigvecs[:, b]
+        s = np.linalg.norm(u / np.linalg.norm(u) - np.sign(u @ w) * w / np.linalg.norm(w))
+        assert s <= 1e-8, (a, s)
+
+
+def test_fullsize_fdf_solve_in_benchmark_configuration(te, big):
+    A, _ = big
+    K, m = 24, 48
+    plan_f = te.Plan(te.CSR.from_host(A, "fdf"), K, m, "fdf", seed=SEED)
+    ev_f, U_f, res_f = plan_f.solve(residuals=True)
+    ev_f2, _, _ = plan_f.solve()
+    assert torch.equal(ev_f, ev_f2)  # graph replays are deterministic
+    del plan_f
+    csr_d = te.CSR.from_host(A, "ddd")
+    plan_d = te.Plan(csr_d, K, m, "ddd", seed=SEED)
+    ev_d, _, _ = plan_d.solve(vectors=False)
+    del plan_d
+    ev_f, ev_d = ev_f.numpy(), ev_d.numpy()
+    assert np.all(np.abs(ev_f) <= 1 + 1e-6)
+    assert abs(abs(ev_f[0]) - 1.0) <= 1e-6
+    assert np.max(np.abs(np.sort(ev_f) - np.sort(ev_d))) <= 1e-6
+    # true residuals of three Ritz pairs against the FP64 matrix
+    for k in (0, K // 2, K - 1):
+        u = U_f[:, k].contiguous()
+        r = te.spmv(csr_d, u, "ddd") - ev_f[k] * u
+        true = float(torch.linalg.norm(r)) / float(torch.linalg.norm(u))
+        assert abs(true - res_f[k].item()) <= 1e-5 + 1e-2 * res_f[k].item(), (k, true, res_f[k])
