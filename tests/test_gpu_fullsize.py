@@ -5,9 +5,10 @@ normalised adjacency, seed 1 (about 268M stored non-zeros).
   oracle computing those rows one by one, within the summation bound.
 * FP64 solve, K = 8, m = 16: against the full oracle run (same start vector).
 * FDF solve, K = 24, m = 48, through a plan with its CUDA graph (the launch
-  configuration the benchmark times): eigenvalues within 1e-6 of the FP64
-  GPU solve, inside the spectrum bound |lambda| <= 1 of a normalised
-  adjacency, and residual estimates consistent with true residuals.
+  configuration the benchmark times): the FP64 solve's converged Ritz values
+  reproduced within 1e-6, all values inside the spectrum bound |lambda| <= 1
+  of a normalised adjacency, residual estimates consistent with true
+  residuals.
 """
 import numpy as np
 import pytest
@@ -86,6 +87,13 @@ def test_fullsize_fp64_solve_matches_oracle(te, big):
 
 
 def test_fullsize_fdf_solve_in_benchmark_configuration(te, big):
+    """FDF vs FP64 on a matrix whose eigenvalues +-1 have huge multiplicity
+    (one per small component).  Rounding the Lanczos vectors to binary32
+    injects ~1e-8 components into those eigenspaces, so after a few dozen
+    steps FDF finds extra copies of +-1 that the FP64 process does not: the
+    two Krylov spaces legitimately differ.  What both must share are the
+    converged pairs, and every FDF pair must be an eigen-pair of M to within
+    its (true) residual."""
     A, _ = big
     K, m = 24, 48
     plan_f = te.Plan(te.CSR.from_host(A, "fdf"), K, m, "fdf", seed=SEED)
@@ -95,12 +103,15 @@ def test_fullsize_fdf_solve_in_benchmark_configuration(te, big):
     del plan_f
     csr_d = te.CSR.from_host(A, "ddd")
     plan_d = te.Plan(csr_d, K, m, "ddd", seed=SEED)
-    ev_d, _, _ = plan_d.solve(vectors=False)
+    ev_d, _, res_d = plan_d.solve(vectors=False, residuals=True)
     del plan_d
-    ev_f, ev_d = ev_f.numpy(), ev_d.numpy()
+    ev_f, ev_d, res_d = ev_f.numpy(), ev_d.numpy(), res_d.numpy()
     assert np.all(np.abs(ev_f) <= 1 + 1e-6)
     assert abs(abs(ev_f[0]) - 1.0) <= 1e-6
-    assert np.max(np.abs(np.sort(ev_f) - np.sort(ev_d))) <= 1e-6
+    converged = np.nonzero(res_d <= 1e-9)[0]
+    assert len(converged) >= 2
+    for k in converged:
+        assert np.min(np.abs(ev_f - ev_d[k])) <= 1e-6, (k, ev_d[k])
     # true residuals of three Ritz pairs against the FP64 matrix
     for k in (0, K // 2, K - 1):
         u = U_f[:, k].contiguous()
