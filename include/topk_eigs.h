@@ -197,6 +197,21 @@ te_status te_lanczos(const te_csr* A, int32_t krylov_steps, te_precision p,
 te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, int32_t which,
                           double* theta, double* Y, int32_t* sweeps, void* stream);
 
+/* y = M x like te_spmv, but without allocating any device memory: for callers
+ * that cannot call cudaMalloc (for instance when another allocator already
+ * owns the device memory, or when a serving loop must not take the
+ * allocator's locks and latency).  The paper has no counterpart; it exists
+ * for such callers.  Work memory is one fixed 4 MiB __device__ array inside
+ * the library, shared by all calls on a device, which limits nnz to
+ * 131072 * 2048 (DDD) or 131072 * 4096 (FDF); larger matrices get
+ * TE_ERR_INVALID_ARG.  The first call on each device looks up the array's
+ * device address (do that first call before any stream capture).  Calls that
+ * overlap on the GPU (other streams, other host threads) race on the array
+ * and must be serialised by the caller.  A must be TE_DEVICE; x has n
+ * elements of type p.vectors; y receives n doubles.  Synchronises `stream`. */
+te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void* x, double* y,
+                          void* stream);
+
 /* Host-side analysis behind the SpMV (no GPU needed; row_ptr in host memory).
  * Rows are packed, in order, into blocks of at most tile_nnz non-zeros and
  * 1024 rows (tile_nnz = 2048 for DDD, 4096 for FDF); a row with more than

@@ -80,6 +80,8 @@ _SIGS = {
     "te_tridiag_eigs": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "te_spmv_noalloc": (ctypes.c_int, [ctypes.c_void_p, te_precision, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "te_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "te_spmv_partition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -316,6 +318,21 @@ def lanczos(csr: CSR, krylov_steps: int, precision="ddd", *, seed: int = 0, v1=N
                         ctypes.byref(restarts), _stream_ptr(stream))
     _check(rc)
     return alpha, beta, (None if V is None else V.t()), int(restarts.value)
+
+
+def spmv_noalloc(csr: CSR, x, y=None, precision="ddd", stream=None):
+    """y = M x (float64) through te_spmv_noalloc, which allocates no device
+    memory (its work memory is a fixed array inside the library).  Pass a
+    preallocated `y` to keep this call free of allocations on the Python side."""
+    import torch
+    lib = load_library()
+    A = csr.to_ctypes()
+    if y is None:
+        y = torch.empty(csr.n, dtype=torch.float64, device="cuda")
+    rc = lib.te_spmv_noalloc(ctypes.byref(A), _prec(precision), ctypes.c_void_p(x.data_ptr()),
+                             ctypes.c_void_p(y.data_ptr()), _stream_ptr(stream))
+    _check(rc)
+    return y
 
 
 def spmv_partition(row_ptr, nnz: int, precision="fdf"):

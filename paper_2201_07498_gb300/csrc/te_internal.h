@@ -149,6 +149,8 @@ cudaError_t jacobi_prepare();  // once per process/device, outside stream captur
 cudaError_t launch_jacobi(const JacobiArgs& a, cudaStream_t s);
 
 // ---- small utilities ----
+// record the thread-local message returned by te_last_error()
+void set_last_error(const std::string& msg);
 cudaError_t launch_basis_to_f64(int prec, const void* V, int64_t ld, int64_t n, int cols,
                                 const double* s_dev, double* out, cudaStream_t st);
 

@@ -118,6 +118,8 @@ cudaError_t g_prep_err = cudaSuccess;
 
 }  // namespace
 
+void te::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct te_plan {
   int prec = 0;
   int64_t n = 0, n_pad = 0, nnz = 0;
