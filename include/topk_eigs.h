@@ -214,7 +214,7 @@ te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void* x, double
 
 /* Host-side analysis behind the SpMV (no GPU needed; row_ptr in host memory).
  * Rows are packed, in order, into blocks of at most tile_nnz non-zeros and
- * 1024 rows (tile_nnz = 2048 for DDD, 4096 for FDF); a row with more than
+ * 1024 rows (tile_nnz = 4080 for DDD, 8160 for FDF); a row with more than
  * tile_nnz/4 non-zeros is "long" and cut into chunks of tile_nnz non-zeros.
  * Writes the three counts; if `blocks` is not NULL it receives 2*nblocks
  * int32 (first row, one past last row) and if `chunks` is not NULL it

@@ -63,23 +63,48 @@ struct Partition {
   std::vector<LongRow> lrows;     // long rows -> their chunks
 };
 
+// One unit of SpMV work: a block of rows (lslot < 0) or a chunk of a long row
+// (lslot = index of its partial sum).
+struct SpmvDesc {
+  int64_t k0;      // first non-zero
+  int32_t nz;      // non-zeros
+  int32_t r0, r1;  // rows [r0, r1)
+  int32_t lslot;   // long-row chunk: index of its partial sum; -1 otherwise
+  int32_t nrows;   // non-empty rows in the block
+  int32_t pad_;
+  int64_t meta;    // offset of the block's row records in the row-record array
+};
+
+constexpr int SPMV_T = 256;  // threads per SpMV CTA (one CTA per descriptor)
+
 // Device copy of a partition.
 struct DevPartition {
-  int2* blocks = nullptr;
-  LongChunk* chunks = nullptr;
+  SpmvDesc* desc = nullptr;
+  uint16_t* runrow = nullptr;  // SPMV_T entries per descriptor: first row record of each run
+  uint32_t* rowrec = nullptr;  // per non-empty row: (end offset in the block << 16) | row offset
   LongRow* lrows = nullptr;
-  void* lpart = nullptr;  // one partial per chunk (8 bytes)
-  int nshort = 0, nchunks = 0, nlrows = 0;
+  void* lpart = nullptr;  // one partial per long-row chunk (8 bytes)
+  int ndesc = 0, nlrows = 0, nchunks = 0;
+  int grid = 0;           // persistent CTAs (one per SM)
 };
 
 int spmv_tile_nnz(int prec);
 // returns false (and a message) if row_ptr is malformed
 bool make_partition(const int64_t* rp, int64_t n, int64_t nnz, int tnnz, Partition& out,
                     std::string& err);
+// descriptors; for every non-empty row a 32-bit record (end offset within its
+// block << 16 | row offset); for every thread's run the index of the record of
+// the row holding its first element.  Empty rows are never written by the
+// SpMV kernel: the caller keeps them zero.
+void make_descriptors(int prec, const Partition& P, const int64_t* rp,
+                      std::vector<SpmvDesc>& out, std::vector<uint16_t>& runrow,
+                      std::vector<uint32_t>& rowrec);
+cudaError_t spmv_prepare();  // once per process/device, outside stream capture
 
 // SpMV: y = A x.  out_f64: write binary64 (else the precision's vector type).
+// The CSR arrays must be 16-byte aligned.
 cudaError_t launch_spmv(int prec, const int64_t* rp, const int32_t* ci, const void* val,
-                        const void* x, void* y, int64_t n, const DevPartition& P,
+                        const void* x, void* y, int64_t n, int64_t nnz, const DevPartition& P,
                         bool out_f64, cudaStream_t s);
 cudaError_t launch_validate_cols(const int32_t* ci, int64_t nnz, int64_t n, int* flag,
                                  cudaStream_t s);

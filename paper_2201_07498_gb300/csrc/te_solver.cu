@@ -65,14 +65,14 @@ bool is_device_ptr(const void* p) {
 
 struct Work {
   // byte offsets inside one allocation
-  size_t V = 0, ytil = 0, w = 0, partials = 0, st = 0, blocks = 0, chunks = 0, lrows = 0,
-         lpart = 0, flag = 0, total = 0;
+  size_t V = 0, ytil = 0, w = 0, partials = 0, st = 0, desc = 0, runrow = 0, rowrec = 0,
+         lrows = 0, lpart = 0, flag = 0, total = 0;
 };
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 Work layout(int prec, int64_t n_pad, int m, int grid, size_t nblocks, size_t nchunks,
-            size_t nlrows) {
+            size_t nlrows, size_t nrec) {
   Work w;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -85,8 +85,9 @@ Work layout(int prec, int64_t n_pad, int m, int grid, size_t nblocks, size_t nch
   w.w = take((size_t)n_pad * 8);
   w.partials = take((size_t)grid * PSTRIDE * 8);
   w.st = take(sizeof(LzState));
-  w.blocks = take(std::max<size_t>(nblocks, 1) * sizeof(int2));
-  w.chunks = take(std::max<size_t>(nchunks, 1) * sizeof(LongChunk));
+  w.desc = take(std::max<size_t>(nblocks + nchunks, 1) * sizeof(SpmvDesc));
+  w.runrow = take(std::max<size_t>(nblocks + nchunks, 1) * SPMV_T * sizeof(uint16_t));
+  w.rowrec = take(std::max<size_t>(nrec, 1) * sizeof(uint32_t));
   w.lrows = take(std::max<size_t>(nlrows, 1) * sizeof(LongRow));
   w.lpart = take(std::max<size_t>(nchunks, 1) * 8);
   w.flag = take(16);
@@ -115,6 +116,17 @@ te_status check_args(const te_csr* A, int32_t K, int32_t m, te_precision p) {
 
 std::once_flag g_prep_once;
 cudaError_t g_prep_err = cudaSuccess;
+
+// kernel attributes (dynamic shared memory) are set once, before any capture
+cudaError_t prepare_kernels() {
+  std::call_once(g_prep_once, [] {
+    g_prep_err = jacobi_prepare();
+    if (g_prep_err == cudaSuccess) g_prep_err = spmv_prepare();
+  });
+  return g_prep_err;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 }  // namespace
 
@@ -242,7 +254,8 @@ cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
     const void* xi = static_cast<const char*>(at(P, P->W.V)) + (size_t)i * P->n_pad * belt;
     P->nkernels += 1 + (P->part.nlrows > 0 ? 1 : 0);
     if ((e = prof_begin(P, s)) != cudaSuccess) return e;
-    e = launch_spmv(P->prec, P->rp, P->ci, P->val, xi, at(P, P->W.ytil), P->n, P->part, false, s);
+    e = launch_spmv(P->prec, P->rp, P->ci, P->val, xi, at(P, P->W.ytil), P->n, P->nnz, P->part,
+                    false, s);
     if (e != cudaSuccess) return e;
     {
       const double n = (double)P->n, nnz = (double)P->nnz;
@@ -368,7 +381,8 @@ size_t te_workspace_bytes(const te_csr* A, int32_t K, int32_t krylov_steps, te_p
   const int tn = spmv_tile_nnz(prec);
   const size_t nblocks = (size_t)(A->nnz / (tn / 4) + A->n / SPMV_RMAX + 2);
   const size_t nchunks = (size_t)(A->nnz / tn + A->nnz / (tn / 4) + 1);
-  Work w = layout(prec, pad_rows(A->n), krylov_steps, 1024, nblocks, nchunks, nchunks);
+  Work w = layout(prec, pad_rows(A->n), krylov_steps, 1024, nblocks, nchunks, nchunks,
+                  (size_t)(A->n < A->nnz ? A->n : A->nnz) + nchunks);
   return w.total;
 }
 
@@ -395,8 +409,10 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     return fail(TE_ERR_INVALID_ARG, "which must be TE_WHICH_*");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  std::call_once(g_prep_once, [] { g_prep_err = jacobi_prepare(); });
-  if (g_prep_err != cudaSuccess) return cuda_fail(g_prep_err, "jacobi_prepare");
+  if (prepare_kernels() != cudaSuccess) return cuda_fail(g_prep_err, "kernel set-up");
+  if (A->where == TE_DEVICE &&
+      !(aligned16(A->row_ptr) && aligned16(A->col_idx) && aligned16(A->values)))
+    return fail(TE_ERR_INVALID_ARG, "device CSR arrays must be 16-byte aligned");
 
   te_plan* P = new te_plan();
   struct Guard {
@@ -445,8 +461,12 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   const int grid = std::max(std::max(P->Ldot.grid, P->Laxd.grid),
                             std::max(P->Lsto.grid, P->Lritz.grid));
 
+  std::vector<SpmvDesc> desc;
+  std::vector<uint16_t> runrow;
+  std::vector<uint32_t> rowrec;
+  make_descriptors(P->prec, part, rph, desc, runrow, rowrec);
   P->W = layout(P->prec, P->n_pad, P->m, grid, part.blocks.size(), part.chunks.size(),
-                part.lrows.size());
+                part.lrows.size(), rowrec.size());
   size_t csr_bytes = 0;
   if (A->where == TE_HOST)
     csr_bytes = al256(sizeof(int64_t) * (A->n + 1)) + al256(sizeof(int32_t) * A->nnz) +
@@ -487,21 +507,26 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   // zero the work memory (the padded rows of V, y and w must stay zero)
   TE_CK(cudaMemsetAsync(P->work, 0, P->W.total, s), "clear work memory");
   // partition to the device
-  P->part.nshort = (int)part.blocks.size();
+  P->part.ndesc = (int)desc.size();
   P->part.nchunks = (int)part.chunks.size();
   P->part.nlrows = (int)part.lrows.size();
-  P->part.blocks = static_cast<int2*>(at(P, P->W.blocks));
-  P->part.chunks = static_cast<LongChunk*>(at(P, P->W.chunks));
+  P->part.grid = P->num_sms;
+  P->part.desc = static_cast<SpmvDesc*>(at(P, P->W.desc));
+  P->part.runrow = static_cast<uint16_t*>(at(P, P->W.runrow));
+  P->part.rowrec = static_cast<uint32_t*>(at(P, P->W.rowrec));
   P->part.lrows = static_cast<LongRow*>(at(P, P->W.lrows));
   P->part.lpart = at(P, P->W.lpart);
-  if (!part.blocks.empty())
-    TE_CK(cudaMemcpyAsync(P->part.blocks, part.blocks.data(), part.blocks.size() * sizeof(int2),
+  if (!desc.empty()) {
+    TE_CK(cudaMemcpyAsync(P->part.desc, desc.data(), desc.size() * sizeof(SpmvDesc),
                           cudaMemcpyHostToDevice, s),
           "copy partition");
-  if (!part.chunks.empty())
-    TE_CK(cudaMemcpyAsync(P->part.chunks, part.chunks.data(),
-                          part.chunks.size() * sizeof(LongChunk), cudaMemcpyHostToDevice, s),
+    TE_CK(cudaMemcpyAsync(P->part.runrow, runrow.data(), runrow.size() * sizeof(uint16_t),
+                          cudaMemcpyHostToDevice, s),
           "copy partition");
+    TE_CK(cudaMemcpyAsync(P->part.rowrec, rowrec.data(), rowrec.size() * sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, s),
+          "copy partition");
+  }
   if (!part.lrows.empty())
     TE_CK(cudaMemcpyAsync(P->part.lrows, part.lrows.data(), part.lrows.size() * sizeof(LongRow),
                           cudaMemcpyHostToDevice, s),
@@ -672,6 +697,9 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
   if (r != TE_OK) return r;
   if (A->where != TE_DEVICE) return fail(TE_ERR_INVALID_ARG, "te_spmv needs a TE_DEVICE matrix");
   if (!x || !y) return fail(TE_ERR_INVALID_ARG, "x and y must not be NULL");
+  if (!(aligned16(A->row_ptr) && aligned16(A->col_idx) && aligned16(A->values)))
+    return fail(TE_ERR_INVALID_ARG, "device CSR arrays must be 16-byte aligned");
+  if (prepare_kernels() != cudaSuccess) return cuda_fail(g_prep_err, "kernel set-up");
   const int prec = prec_of(p);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<int64_t> rp((size_t)A->n + 1);
@@ -683,28 +711,43 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
   std::string perr;
   if (!make_partition(rp.data(), A->n, A->nnz, spmv_tile_nnz(prec), part, perr))
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
-  const size_t b0 = al256(std::max<size_t>(part.blocks.size(), 1) * sizeof(int2));
-  const size_t b1 = al256(std::max<size_t>(part.chunks.size(), 1) * sizeof(LongChunk));
+  std::vector<SpmvDesc> desc;
+  std::vector<uint16_t> runrow;
+  std::vector<uint32_t> rowrec;
+  make_descriptors(prec, part, rp.data(), desc, runrow, rowrec);
+  const size_t bd = al256(std::max<size_t>(desc.size(), 1) * sizeof(SpmvDesc));
+  const size_t br = al256(std::max<size_t>(runrow.size(), 1) * sizeof(uint16_t));
+  const size_t b0 = bd + br + al256(std::max<size_t>(rowrec.size(), 1) * sizeof(uint32_t));
   const size_t b2 = al256(std::max<size_t>(part.lrows.size(), 1) * sizeof(LongRow));
   const size_t b3 = al256(std::max<size_t>(part.chunks.size(), 1) * 8);
   char* buf = nullptr;
-  TE_CK(cudaMalloc(&buf, b0 + b1 + b2 + b3 + 256), "allocate SpMV partition");
+  TE_CK(cudaMalloc(&buf, b0 + b2 + b3 + 256), "allocate SpMV partition");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   DevPartition dp;
-  dp.blocks = reinterpret_cast<int2*>(buf);
-  dp.chunks = reinterpret_cast<LongChunk*>(buf + b0);
-  dp.lrows = reinterpret_cast<LongRow*>(buf + b0 + b1);
-  dp.lpart = buf + b0 + b1 + b2;
-  int* flag = reinterpret_cast<int*>(buf + b0 + b1 + b2 + b3);
-  dp.nshort = (int)part.blocks.size();
+  dp.desc = reinterpret_cast<SpmvDesc*>(buf);
+  dp.runrow = reinterpret_cast<uint16_t*>(buf + bd);
+  dp.rowrec = reinterpret_cast<uint32_t*>(buf + bd + br);
+  dp.lrows = reinterpret_cast<LongRow*>(buf + b0);
+  dp.lpart = buf + b0 + b2;
+  int* flag = reinterpret_cast<int*>(buf + b0 + b2 + b3);
+  dp.ndesc = (int)desc.size();
   dp.nchunks = (int)part.chunks.size();
   dp.nlrows = (int)part.lrows.size();
+  dp.grid = sms;
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
-  if (e == cudaSuccess && dp.nshort)
-    e = cudaMemcpyAsync(dp.blocks, part.blocks.data(), dp.nshort * sizeof(int2),
+  if (e == cudaSuccess && dp.ndesc)
+    e = cudaMemcpyAsync(dp.desc, desc.data(), dp.ndesc * sizeof(SpmvDesc),
                         cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && dp.nchunks)
-    e = cudaMemcpyAsync(dp.chunks, part.chunks.data(), dp.nchunks * sizeof(LongChunk),
+  if (e == cudaSuccess && dp.ndesc)
+    e = cudaMemcpyAsync(dp.runrow, runrow.data(), runrow.size() * sizeof(uint16_t),
                         cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && dp.ndesc)
+    e = cudaMemcpyAsync(dp.rowrec, rowrec.data(), rowrec.size() * sizeof(uint32_t),
+                        cudaMemcpyHostToDevice, s);
+  // the kernel writes non-empty rows only
+  if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, sizeof(double) * A->n, s);
   if (e == cudaSuccess && dp.nlrows)
     e = cudaMemcpyAsync(dp.lrows, part.lrows.data(), dp.nlrows * sizeof(LongRow),
                         cudaMemcpyHostToDevice, s);
@@ -718,7 +761,7 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
   }
   if (e == cudaSuccess)
-    e = launch_spmv(prec, A->row_ptr, A->col_idx, A->values, x, y, A->n, dp, true, s);
+    e = launch_spmv(prec, A->row_ptr, A->col_idx, A->values, x, y, A->n, A->nnz, dp, true, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(buf);
   if (e != cudaSuccess) return cuda_fail(e, "te_spmv");
@@ -778,8 +821,7 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
   if (!alpha || !beta || !theta) return fail(TE_ERR_INVALID_ARG, "NULL argument");
   if (which != TE_WHICH_LARGEST_MAGNITUDE && which != TE_WHICH_LARGEST_ALGEBRAIC)
     return fail(TE_ERR_INVALID_ARG, "which must be TE_WHICH_*");
-  std::call_once(g_prep_once, [] { g_prep_err = jacobi_prepare(); });
-  if (g_prep_err != cudaSuccess) return cuda_fail(g_prep_err, "jacobi_prepare");
+  if (prepare_kernels() != cudaSuccess) return cuda_fail(g_prep_err, "kernel set-up");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* dbuf = nullptr;
   TE_CK(cudaMalloc(&dbuf, 2 * sizeof(int)), "allocate status");

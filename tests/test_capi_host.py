@@ -138,7 +138,7 @@ def _check_partition(rp, nnz, blocks, chunks, nlong, tile):
     assert np.all(covered[short] == 1)
 
 
-@pytest.mark.parametrize("prec,tile", [("ddd", 2048), ("fdf", 4096)])
+@pytest.mark.parametrize("prec,tile", [("ddd", 4080), ("fdf", 8160)])
 def test_partition_covers_rows_once(te, prec, tile):
     mats = [synth.uniform_sym(5000, 7, 3), synth.rmat_sym(14, 8, 5)]
     # crafted: empty rows, a star (one very long row), rows around the thresholds

@@ -127,8 +127,8 @@ SPMV_CASES = {
     "n7_empty_rows": lambda: synth.from_triplets(7, [1, 3, 3, 6], [3, 1, 6, 3], [1.0, 1.0, -2.0, -2.0]),
     "star_ragged": lambda: star_plus_random(9000, 3),
     "rmat14": lambda: synth.rmat_sym(14, 8, 2),
-    "thresholds_ddd": lambda: threshold_rows(2048),
-    "thresholds_fdf": lambda: threshold_rows(4096),
+    "thresholds_ddd": lambda: threshold_rows(4080),
+    "thresholds_fdf": lambda: threshold_rows(8160),
 }
 
 
@@ -247,7 +247,7 @@ SOLVE_CASES = [
     ("rmat13_K6_m20", lambda: synth.rmat_sym(13, 8, 9), 6, 20, "LM"),
     ("star_K4_m12", lambda: star_plus_random(9000, 4), 4, 12, "LM"),
     ("uniform_K_eq_m", lambda: synth.uniform_sym(500, 4, 2), 10, 10, "LA"),
-    ("thresholds_K3_m9", lambda: threshold_rows(4096, symmetric=True), 3, 9, "LM"),
+    ("thresholds_K3_m9", lambda: threshold_rows(8160, symmetric=True), 3, 9, "LM"),
 ]
 
 
