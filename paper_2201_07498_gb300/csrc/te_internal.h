@@ -115,11 +115,12 @@ enum XSource : int { X_VEC = 0, X_RANDOM = 1, X_V1 = 2 };
 enum Finalize : int {
   FIN_DOT_STEP = 0,
   FIN_DOT_RESTART = 1,
-  FIN_AXPYDOT = 2,
+  FIN_AXPYDOT = 2,       // second-sweep coefficients (restart passes)
   FIN_STORE_STEP = 3,
   FIN_STORE_RESTART = 4,
   FIN_STORE_INIT = 5,
-  FIN_NONE = 6
+  FIN_NONE = 6,
+  FIN_AXPYDOT_STEP = 7   // second-sweep coefficients and alpha = h1_i + h2_i
 };
 
 struct PassArgs {

@@ -45,6 +45,8 @@ struct PassTr<PREC_FDF> {
 };
 
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
+// FDF tiles are half the size of DDD tiles: two CTAs per SM still double-buffer
+__host__ __device__ constexpr int pass_ctas_per_sm(int prec) { return prec == PREC_FDF ? 2 : 1; }
 constexpr int QMAX = MAX_M / (CONSUMERS / 32);  // dot columns per warp
 constexpr int RITZ_KC = 8;                      // Ritz outputs per register block
 
@@ -143,11 +145,19 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       // tot[j] = stored_j . ytilde with y = s_i ytilde = M v_i
       const double si = st->s[i];
       for (int j = 0; j < a.nb; ++j) {
-        double h = st->s[j] * si * tot[j];  // v_j . M v_i
+        double h = st->s[j] * si * tot[j];  // v_j . M v_i (first sweep)
         st->c1[j] = h * st->s[j];
       }
-      st->alpha[i] = st->s[i] * si * tot[i];  // Algorithm 1, line 10
+      // Algorithm 1, line 10: alpha_i = v_i . M v_i; the second sweep adds its
+      // correction (FIN_AXPYDOT_STEP), so alpha keeps full accuracy even when
+      // the first sweep's dots are taken in binary32 chunks
+      st->alpha[i] = st->s[i] * si * tot[i];
       st->xscale = si;
+      break;
+    }
+    case FIN_AXPYDOT_STEP: {
+      for (int j = 0; j < a.nb; ++j) st->c2[j] = st->s[j] * st->s[j] * tot[j];
+      st->alpha[i] += st->s[i] * tot[i];  // + v_i . w after the first sweep
       break;
     }
     case FIN_DOT_RESTART: {
@@ -201,7 +211,7 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
 // the pass kernel
 // ---------------------------------------------------------------------------
 template <int P, int MODE>
-__global__ void __launch_bounds__(PASS_THREADS, 1) pass_kernel(PassArgs a, size_t region) {
+__global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel(PassArgs a, size_t region) {
   using Tr = PassTr<P>;
   using basis_t = typename Tr::basis_t;
   using vec_t = typename Tr::vec_t;
@@ -370,19 +380,40 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) pass_kernel(PassArgs a, size_
 
     if constexpr (HAS_DOT) {
       named_bar_sync(1, CONSUMERS);
-      // phase B: warp `wid` owns columns wid, wid+8, ...; lanes stride rows
-#pragma unroll 2
-      for (int rr = 0; rr < TILE_R / 32; ++rr) {
-        const int r = lane + 32 * rr;
-        const vec_t wr = ws[r];
+      // phase B: warp `wid` owns columns wid, wid+8, ...; lanes stride rows.
+      // The column loop stops at this warp's last column (uniform branch).
+      // Dots of the first sweep (MODE_DOT, FDF) are summed in binary32 over
+      // the tile's 8 rows per lane and then added exactly: their error is
+      // removed by the second sweep.  The second sweep's dots use exact
+      // products and double-float sums.
 #pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-          const int jj = wid + (CONSUMERS / 32) * q;
-          if (jj < nb) {
-            const basis_t v = tv[(size_t)jj * TILE_R + r];
-            if constexpr (P == PREC_FDF) dacc_fma(dots[q], v, wr.x, wr.y);
-            else dots[q] = fma(v, wr, dots[q]);
+      for (int q = 0; q < QMAX; ++q) {
+        const int jj = wid + (CONSUMERS / 32) * q;
+        if (jj >= nb) break;
+        const basis_t* col = tv + (size_t)jj * TILE_R;
+        if constexpr (P == PREC_FDF && MODE == MODE_DOT) {
+          float c0 = 0.f, c1 = 0.f;
+#pragma unroll
+          for (int rr = 0; rr < TILE_R / 32; rr += 2) {
+            c0 = __fmaf_rn(col[lane + 32 * rr], ws[lane + 32 * rr].x, c0);
+            c1 = __fmaf_rn(col[lane + 32 * (rr + 1)], ws[lane + 32 * (rr + 1)].x, c1);
           }
+          dacc_add_pair(dots[q], c0, c1);
+        } else {
+          acc_t e0 = zero_acc<P>(), e1 = zero_acc<P>();
+#pragma unroll
+          for (int rr = 0; rr < TILE_R / 32; rr += 2) {
+            const vec_t w0 = ws[lane + 32 * rr], w1 = ws[lane + 32 * (rr + 1)];
+            const basis_t v0 = col[lane + 32 * rr], v1 = col[lane + 32 * (rr + 1)];
+            if constexpr (P == PREC_FDF) {
+              dacc_fma(e0, v0, w0.x, w0.y);
+              dacc_fma(e1, v1, w1.x, w1.y);
+            } else {
+              e0 = fma(v0, w0, e0);
+              e1 = fma(v1, w1, e1);
+            }
+          }
+          dots[q] = acc_merge<P>(dots[q], acc_merge<P>(e0, e1));
         }
       }
     }
@@ -490,8 +521,15 @@ static cudaError_t config_t(int max_cols, int K, int num_sms, PassLaunch& out) {
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   const int ritz_elems = MODE == MODE_RITZ ? max_cols * K : 0;
+  // pass_ctas_per_sm CTAs per SM share the SM's shared memory (minus the
+  // per-CTA reservation of 1 KB)
   const size_t fixed = smem_plan(MODE, 0, ritz_elems).total + 128;
-  size_t avail = (size_t)optin > fixed ? (size_t)optin - fixed : 0;
+  int persm = 0;
+  e = cudaDeviceGetAttribute(&persm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e != cudaSuccess) return e;
+  const size_t half = (size_t)persm / pass_ctas_per_sm(P) - 1024;
+  const size_t cap = half < (size_t)optin ? half : (size_t)optin;
+  size_t avail = cap > fixed ? cap - fixed : 0;
   const size_t per_stage = (size_t)(max_cols > 0 ? max_cols : 1) * TILE_R * sizeof(basis_t);
   int stages = (int)(avail / per_stage);
   if (stages > 4) stages = 4;
@@ -501,7 +539,7 @@ static cudaError_t config_t(int max_cols, int K, int num_sms, PassLaunch& out) {
   e = cudaFuncSetAttribute(pass_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)total);
   if (e != cudaSuccess) return e;
-  out.grid = num_sms;
+  out.grid = num_sms * pass_ctas_per_sm(P);
   out.smem = total;
   out.stages = stages;
   out.region = region;

@@ -271,7 +271,7 @@ cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
     a.fin = FIN_DOT_STEP;
     if ((e = pass(P, MODE_DOT, a, s)) != cudaSuccess) return e;
     a.wout = at(P, P->W.w);
-    a.fin = FIN_AXPYDOT;
+    a.fin = FIN_AXPYDOT_STEP;
     if ((e = pass(P, MODE_AXPY_DOT, a, s)) != cudaSuccess) return e;
     a.xvec = at(P, P->W.w);
     a.col_out = i + 1;
