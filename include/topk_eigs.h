@@ -212,17 +212,21 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
 te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void* x, double* y,
                           void* stream);
 
-/* Host-side analysis behind the SpMV (no GPU needed; row_ptr in host memory).
- * Rows are packed, in order, into blocks of at most tile_nnz non-zeros and
- * 1024 rows (tile_nnz = 4080 for DDD, 8160 for FDF); a row with more than
- * tile_nnz/4 non-zeros is "long" and cut into chunks of tile_nnz non-zeros.
- * Writes the three counts; if `blocks` is not NULL it receives 2*nblocks
- * int32 (first row, one past last row) and if `chunks` is not NULL it
- * receives 3*nchunks int64 (first nnz, one past last nnz, row).  Returns
- * TE_ERR_INVALID_ARG for a malformed row_ptr. */
-te_status te_spmv_partition(const int64_t* row_ptr, int64_t n, int64_t nnz, te_precision p,
-                            int64_t* nblocks, int64_t* nchunks, int64_t* nlong_rows,
-                            int32_t* blocks, int64_t* chunks);
+/* Host-side layout behind the SpMV (no GPU needed; row_ptr in host memory):
+ * the SELL-C-sigma arrangement a plan builds (Kreutzer et al., SIAM J. Sci.
+ * Comput. 2014).  Rows are cut into pieces of at most 64 entries; within each
+ * window of 2048 consecutive rows the pieces are sorted by length (longest
+ * first) and grouped into slices of 32 lanes, each slice padded to its
+ * longest piece.  Writes the slice count, the padded entry count and the
+ * number of rows cut into several pieces.  Optional per-slice output
+ * slice_len[nslices]; optional per-lane outputs (32 * nslices entries):
+ * lane_out = the row the lane sums (>= 0), -1 - p for piece p of a cut row,
+ * or INT32_MIN for an empty lane; lane_src = first CSR entry of its piece;
+ * lane_len = entries of its piece.  Returns TE_ERR_INVALID_ARG for a
+ * malformed row_ptr. */
+te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int64_t* nslices,
+                         int64_t* entries, int64_t* nlong_rows, int32_t* slice_len,
+                         int32_t* lane_out, int64_t* lane_src, int32_t* lane_len);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ from dataclasses import dataclass
 from . import _build
 
 __all__ = ["CSR", "Plan", "TEError", "topk_eigs", "spmv", "lanczos", "tridiag_eigs",
-           "spmv_partition", "library_path", "load_library", "PRECISIONS"]
+           "spmv_layout", "library_path", "load_library", "PRECISIONS"]
 
 TE_F64, TE_F32, TE_BF16, TE_FP8_E4M3 = 0, 1, 2, 3
 TE_DEVICE, TE_HOST = 0, 1
@@ -84,9 +84,10 @@ _SIGS = {
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "te_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
-    "te_spmv_partition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
-                                         te_precision, ctypes.c_void_p, ctypes.c_void_p,
-                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "te_spmv_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
 }
 
 _lib = None
@@ -335,24 +336,30 @@ def spmv_noalloc(csr: CSR, x, y=None, precision="ddd", stream=None):
     return y
 
 
-def spmv_partition(row_ptr, nnz: int, precision="fdf"):
-    """Host analysis behind the SpMV: returns (blocks [B,2] int32, chunks [C,3] int64,
-    number of long rows).  row_ptr: numpy int64 array of n+1 entries."""
+def spmv_layout(row_ptr, nnz: int):
+    """The SELL-C-sigma layout a plan builds for the SpMV (host analysis):
+    returns a dict with slice lengths [S], and per lane (32 per slice) the
+    output (row, -1 - piece, or INT32_MIN), the first CSR entry and the length
+    of its piece, plus the padded entry count and the number of cut rows."""
     import numpy as np
     lib = load_library()
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     n = len(rp) - 1
-    nb, nc, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    rc = lib.te_spmv_partition(ctypes.c_void_p(rp.ctypes.data), n, nnz, _prec(precision),
-                               ctypes.byref(nb), ctypes.byref(nc), ctypes.byref(nl), None, None)
+    ns, ne, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rc = lib.te_spmv_layout(ctypes.c_void_p(rp.ctypes.data), n, nnz, ctypes.byref(ns),
+                            ctypes.byref(ne), ctypes.byref(nl), None, None, None, None)
     _check(rc)
-    blocks = np.zeros((nb.value, 2), dtype=np.int32)
-    chunks = np.zeros((nc.value, 3), dtype=np.int64)
-    rc = lib.te_spmv_partition(ctypes.c_void_p(rp.ctypes.data), n, nnz, _prec(precision), None,
-                               None, None, ctypes.c_void_p(blocks.ctypes.data),
-                               ctypes.c_void_p(chunks.ctypes.data))
+    S = ns.value
+    slen = np.zeros(S, dtype=np.int32)
+    lout = np.zeros(S * 32, dtype=np.int32)
+    lsrc = np.zeros(S * 32, dtype=np.int64)
+    llen = np.zeros(S * 32, dtype=np.int32)
+    rc = lib.te_spmv_layout(ctypes.c_void_p(rp.ctypes.data), n, nnz, None, None, None,
+                            ctypes.c_void_p(slen.ctypes.data), ctypes.c_void_p(lout.ctypes.data),
+                            ctypes.c_void_p(lsrc.ctypes.data), ctypes.c_void_p(llen.ctypes.data))
     _check(rc)
-    return blocks, chunks, int(nl.value)
+    return {"slice_len": slen, "lane_out": lout, "lane_src": lsrc, "lane_len": llen,
+            "entries": int(ne.value), "long_rows": int(nl.value)}
 
 
 def tridiag_eigs(alpha, beta, which="LM", stream=None):

@@ -18,8 +18,6 @@ constexpr int PSTRIDE = MAX_M + 4;  // per-CTA partial slots (columns + 2 norms)
 constexpr int CONSUMERS = 256;   // compute threads of the basis passes
 constexpr int PASS_THREADS = CONSUMERS + 32;  // + one producer warp
 constexpr int MAX_STAGES = 16;
-constexpr int SPMV_THREADS = 256;
-constexpr int SPMV_RMAX = 1024;  // rows per short SpMV block
 
 enum Prec : int { PREC_DDD = 0, PREC_FDF = 1 };
 
@@ -47,65 +45,60 @@ struct LzState {
   double* eigvals_out;
 };
 
-struct LongChunk {
-  int64_t k0, k1;  // nnz range
-  int32_t row;
-  int32_t pad_;
-};
 struct LongRow {
-  int32_t row, first, count, pad_;
+  int32_t row, first, count, pad_;  // a row cut into `count` pieces, partials at [first, ...)
 };
 
-// Host-side SpMV partition (row blocks for the CSR-stream kernel).
-struct Partition {
-  std::vector<int2> blocks;       // short blocks [row0, row1)
-  std::vector<LongChunk> chunks;  // chunks of long rows
-  std::vector<LongRow> lrows;     // long rows -> their chunks
-};
+// SELL-C-sigma layout of the matrix for the SpMV (Kreutzer et al., SISC 2014):
+// rows are cut into pieces of at most SELL_VMAX entries, the pieces of every
+// window of SELL_WINDOW consecutive rows are sorted by length (longest first)
+// and grouped in slices of SELL_C; a slice stores its entries column-major
+// (entry k of lane i at base + k*SELL_C + i), padded with zero values to the
+// length of its longest piece.
+constexpr int SELL_C = 32;
+constexpr int SELL_VMAX = 64;
+constexpr int SELL_WINDOW = 2048;
+constexpr int32_t SELL_SKIP = INT32_MIN;  // lane without a piece
 
-// One unit of SpMV work: a block of rows (lslot < 0) or a chunk of a long row
-// (lslot = index of its partial sum).
-struct SpmvDesc {
-  int64_t k0;      // first non-zero
-  int32_t nz;      // non-zeros
-  int32_t r0, r1;  // rows [r0, r1)
-  int32_t lslot;   // long-row chunk: index of its partial sum; -1 otherwise
-  int32_t nrows;   // non-empty rows in the block
+struct SellSlice {
+  int64_t base;  // first entry of the slice
+  int32_t len;   // entries per lane (length of its longest piece)
   int32_t pad_;
-  int64_t meta;    // offset of the block's row records in the row-record array
 };
 
-constexpr int SPMV_T = 256;  // threads per SpMV CTA (one CTA per descriptor)
-
-// Device copy of a partition.
-struct DevPartition {
-  SpmvDesc* desc = nullptr;
-  uint16_t* runrow = nullptr;  // SPMV_T entries per descriptor: first row record of each run
-  uint32_t* rowrec = nullptr;  // per non-empty row: (end offset in the block << 16) | row offset
-  LongRow* lrows = nullptr;
-  void* lpart = nullptr;  // one partial per long-row chunk (8 bytes)
-  int ndesc = 0, nlrows = 0, nchunks = 0;
-  int grid = 0;           // persistent CTAs (one per SM)
+struct SellHost {
+  std::vector<SellSlice> slices;
+  std::vector<int32_t> vout;  // per lane: row (>= 0), -1 - partial slot, or SELL_SKIP
+  std::vector<int64_t> vsrc;  // per lane: first CSR entry of its piece
+  std::vector<int32_t> vlen;  // per lane: entries of its piece
+  std::vector<LongRow> lrows;
+  int64_t entries = 0;        // padded entries
+  int64_t pieces = 0;         // partial sums of cut rows
 };
-
-int spmv_tile_nnz(int prec);
 // returns false (and a message) if row_ptr is malformed
-bool make_partition(const int64_t* rp, int64_t n, int64_t nnz, int tnnz, Partition& out,
-                    std::string& err);
-// descriptors; for every non-empty row a 32-bit record (end offset within its
-// block << 16 | row offset); for every thread's run the index of the record of
-// the row holding its first element.  Empty rows are never written by the
-// SpMV kernel: the caller keeps them zero.
-void make_descriptors(int prec, const Partition& P, const int64_t* rp,
-                      std::vector<SpmvDesc>& out, std::vector<uint16_t>& runrow,
-                      std::vector<uint32_t>& rowrec);
+bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err);
+
+// Device copy of a SELL layout.
+struct DevSell {
+  const SellSlice* slices = nullptr;
+  const int32_t* vout = nullptr;
+  int32_t* cols = nullptr;
+  void* vals = nullptr;
+  void* vpart = nullptr;  // partial sums of cut rows (8 bytes each)
+  const LongRow* lrows = nullptr;
+  int nslices = 0, nlrows = 0;
+};
+
+// fill cols/vals of the SELL layout from the CSR (one thread per lane)
+cudaError_t launch_sell_build(int prec, const int32_t* ci, const void* val,
+                              const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
+                              int nslices, int32_t* cols, void* vals, cudaStream_t s);
 cudaError_t spmv_prepare();  // once per process/device, outside stream capture
 
 // SpMV: y = A x.  out_f64: write binary64 (else the precision's vector type).
-// The CSR arrays must be 16-byte aligned.
-cudaError_t launch_spmv(int prec, const int64_t* rp, const int32_t* ci, const void* val,
-                        const void* x, void* y, int64_t n, int64_t nnz, const DevPartition& P,
-                        bool out_f64, cudaStream_t s);
+// Rows without entries are not written (the caller keeps them zero).
+cudaError_t launch_spmv(int prec, const DevSell& S, const void* x, void* y, bool out_f64,
+                        cudaStream_t s);
 cudaError_t launch_validate_cols(const int32_t* ci, int64_t nnz, int64_t n, int* flag,
                                  cudaStream_t s);
 

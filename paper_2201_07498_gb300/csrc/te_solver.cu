@@ -65,14 +65,18 @@ bool is_device_ptr(const void* p) {
 
 struct Work {
   // byte offsets inside one allocation
-  size_t V = 0, ytil = 0, w = 0, partials = 0, st = 0, desc = 0, runrow = 0, rowrec = 0,
-         lrows = 0, lpart = 0, flag = 0, total = 0;
+  size_t V = 0, ytil = 0, w = 0, partials = 0, st = 0, slices = 0, vout = 0, scols = 0,
+         svals = 0, lrows = 0, vpart = 0, flag = 0, total = 0;
 };
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
-Work layout(int prec, int64_t n_pad, int m, int grid, size_t nblocks, size_t nchunks,
-            size_t nlrows, size_t nrec) {
+// sizes of the SELL layout of the SpMV (see te_internal.h)
+struct SellSizes {
+  size_t slices = 0, entries = 0, lrows = 0, pieces = 0;
+};
+
+Work layout(int prec, int64_t n_pad, int m, int grid, const SellSizes& z) {
   Work w;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -85,11 +89,12 @@ Work layout(int prec, int64_t n_pad, int m, int grid, size_t nblocks, size_t nch
   w.w = take((size_t)n_pad * 8);
   w.partials = take((size_t)grid * PSTRIDE * 8);
   w.st = take(sizeof(LzState));
-  w.desc = take(std::max<size_t>(nblocks + nchunks, 1) * sizeof(SpmvDesc));
-  w.runrow = take(std::max<size_t>(nblocks + nchunks, 1) * SPMV_T * sizeof(uint16_t));
-  w.rowrec = take(std::max<size_t>(nrec, 1) * sizeof(uint32_t));
-  w.lrows = take(std::max<size_t>(nlrows, 1) * sizeof(LongRow));
-  w.lpart = take(std::max<size_t>(nchunks, 1) * 8);
+  w.slices = take(std::max<size_t>(z.slices, 1) * sizeof(SellSlice));
+  w.vout = take(std::max<size_t>(z.slices, 1) * SELL_C * sizeof(int32_t));
+  w.scols = take(std::max<size_t>(z.entries, 1) * sizeof(int32_t));
+  w.svals = take(std::max<size_t>(z.entries, 1) * value_elt(prec));
+  w.lrows = take(std::max<size_t>(z.lrows, 1) * sizeof(LongRow));
+  w.vpart = take(std::max<size_t>(z.pieces, 1) * 8);
   w.flag = take(16);
   w.total = off;
   return w;
@@ -142,7 +147,7 @@ struct te_plan {
   const void* val = nullptr;
   void* owned_csr = nullptr;
   int dev = 0, num_sms = 0;
-  DevPartition part;
+  DevSell sell;
   Work W;
   char* work = nullptr;
   LzState* st = nullptr;
@@ -169,6 +174,40 @@ struct te_plan {
 namespace {
 
 void* at(te_plan* P, size_t off) { return P->work + off; }
+
+// Upload the SELL metadata and convert the (device) CSR into the SELL arrays.
+cudaError_t upload_sell(int prec, const SellHost& H, const int32_t* ci, const void* val,
+                        const DevSell& D, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (!H.slices.empty()) {
+    e = cudaMemcpyAsync(const_cast<SellSlice*>(D.slices), H.slices.data(),
+                        H.slices.size() * sizeof(SellSlice), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(const_cast<int32_t*>(D.vout), H.vout.data(),
+                          H.vout.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess && !H.lrows.empty())
+    e = cudaMemcpyAsync(const_cast<LongRow*>(D.lrows), H.lrows.data(),
+                        H.lrows.size() * sizeof(LongRow), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess || H.slices.empty()) return e;
+  // lane -> CSR piece map, needed only while converting
+  int64_t* dsrc = nullptr;
+  int32_t* dlen = nullptr;
+  e = cudaMalloc(&dsrc, H.vsrc.size() * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&dlen, H.vlen.size() * sizeof(int32_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dsrc, H.vsrc.data(), H.vsrc.size() * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dlen, H.vlen.data(), H.vlen.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_sell_build(prec, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols, D.vals, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (dsrc) cudaFree(dsrc);
+  if (dlen) cudaFree(dlen);
+  return e;
+}
 
 PassArgs base_args(te_plan* P) {
   PassArgs a;
@@ -252,10 +291,9 @@ cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
   }
   for (int i = 0; i < P->m; ++i) {
     const void* xi = static_cast<const char*>(at(P, P->W.V)) + (size_t)i * P->n_pad * belt;
-    P->nkernels += 1 + (P->part.nlrows > 0 ? 1 : 0);
+    P->nkernels += 1 + (P->sell.nlrows > 0 ? 1 : 0);
     if ((e = prof_begin(P, s)) != cudaSuccess) return e;
-    e = launch_spmv(P->prec, P->rp, P->ci, P->val, xi, at(P, P->W.ytil), P->n, P->nnz, P->part,
-                    false, s);
+    e = launch_spmv(P->prec, P->sell, xi, at(P, P->W.ytil), false, s);
     if (e != cudaSuccess) return e;
     {
       const double n = (double)P->n, nnz = (double)P->nnz;
@@ -377,12 +415,16 @@ const char* te_status_string(te_status s) {
 size_t te_workspace_bytes(const te_csr* A, int32_t K, int32_t krylov_steps, te_precision p) {
   if (check_args(A, K, krylov_steps, p) != TE_OK) return 0;
   const int prec = prec_of(p);
-  // partition sizes are bounded without reading the matrix
-  const int tn = spmv_tile_nnz(prec);
-  const size_t nblocks = (size_t)(A->nnz / (tn / 4) + A->n / SPMV_RMAX + 2);
-  const size_t nchunks = (size_t)(A->nnz / tn + A->nnz / (tn / 4) + 1);
-  Work w = layout(prec, pad_rows(A->n), krylov_steps, 1024, nblocks, nchunks, nchunks,
-                  (size_t)(A->n < A->nnz ? A->n : A->nnz) + nchunks);
+  // an upper bound of the SELL layout without reading the matrix: every
+  // window pads at most SELL_C * SELL_VMAX entries to sort order and one
+  // partial slice
+  const size_t windows = (size_t)((A->n + SELL_WINDOW - 1) / SELL_WINDOW);
+  SellSizes z;
+  z.pieces = (size_t)(A->nnz / SELL_VMAX + 1);
+  z.slices = (size_t)((A->n + z.pieces) / SELL_C + windows + 1);
+  z.entries = (size_t)A->nnz + windows * 2 * SELL_C * SELL_VMAX;
+  z.lrows = (size_t)(A->nnz / SELL_VMAX + 1);
+  Work w = layout(prec, pad_rows(A->n), krylov_steps, 1024, z);
   return w.total;
 }
 
@@ -445,9 +487,9 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     TE_CK(cudaStreamSynchronize(s), "sync");
     rph = rp_host.data();
   }
-  Partition part;
+  SellHost sell;
   std::string perr;
-  if (!make_partition(rph, A->n, A->nnz, spmv_tile_nnz(P->prec), part, perr))
+  if (!make_sell(rph, A->n, A->nnz, sell, perr))
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
 
   // launch shapes of the basis passes
@@ -461,12 +503,12 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   const int grid = std::max(std::max(P->Ldot.grid, P->Laxd.grid),
                             std::max(P->Lsto.grid, P->Lritz.grid));
 
-  std::vector<SpmvDesc> desc;
-  std::vector<uint16_t> runrow;
-  std::vector<uint32_t> rowrec;
-  make_descriptors(P->prec, part, rph, desc, runrow, rowrec);
-  P->W = layout(P->prec, P->n_pad, P->m, grid, part.blocks.size(), part.chunks.size(),
-                part.lrows.size(), rowrec.size());
+  SellSizes zs;
+  zs.slices = sell.slices.size();
+  zs.entries = (size_t)sell.entries;
+  zs.lrows = sell.lrows.size();
+  zs.pieces = (size_t)sell.pieces;
+  P->W = layout(P->prec, P->n_pad, P->m, grid, zs);
   size_t csr_bytes = 0;
   if (A->where == TE_HOST)
     csr_bytes = al256(sizeof(int64_t) * (A->n + 1)) + al256(sizeof(int32_t) * A->nnz) +
@@ -504,40 +546,31 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     P->val = A->values;
   }
 
-  // zero the work memory (the padded rows of V, y and w must stay zero)
-  TE_CK(cudaMemsetAsync(P->work, 0, P->W.total, s), "clear work memory");
-  // partition to the device
-  P->part.ndesc = (int)desc.size();
-  P->part.nchunks = (int)part.chunks.size();
-  P->part.nlrows = (int)part.lrows.size();
-  P->part.grid = P->num_sms;
-  P->part.desc = static_cast<SpmvDesc*>(at(P, P->W.desc));
-  P->part.runrow = static_cast<uint16_t*>(at(P, P->W.runrow));
-  P->part.rowrec = static_cast<uint32_t*>(at(P, P->W.rowrec));
-  P->part.lrows = static_cast<LongRow*>(at(P, P->W.lrows));
-  P->part.lpart = at(P, P->W.lpart);
-  if (!desc.empty()) {
-    TE_CK(cudaMemcpyAsync(P->part.desc, desc.data(), desc.size() * sizeof(SpmvDesc),
-                          cudaMemcpyHostToDevice, s),
-          "copy partition");
-    TE_CK(cudaMemcpyAsync(P->part.runrow, runrow.data(), runrow.size() * sizeof(uint16_t),
-                          cudaMemcpyHostToDevice, s),
-          "copy partition");
-    TE_CK(cudaMemcpyAsync(P->part.rowrec, rowrec.data(), rowrec.size() * sizeof(uint32_t),
-                          cudaMemcpyHostToDevice, s),
-          "copy partition");
-  }
-  if (!part.lrows.empty())
-    TE_CK(cudaMemcpyAsync(P->part.lrows, part.lrows.data(), part.lrows.size() * sizeof(LongRow),
-                          cudaMemcpyHostToDevice, s),
-          "copy partition");
+  // zero the solver vectors and state (the padded rows of V, y and w and the
+  // empty rows of y must stay zero); the SELL arrays are written below
+  TE_CK(cudaMemsetAsync(P->work, 0, P->W.slices, s), "clear work memory");
   // column indices must lie in [0, n)
   int* dflag = static_cast<int*>(at(P, P->W.flag));
+  TE_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s), "clear flag");
   TE_CK(launch_validate_cols(P->ci, P->nnz, P->n, dflag, s), "validate columns");
   int hflag = 0;
   TE_CK(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
   TE_CK(cudaStreamSynchronize(s), "plan setup");
   if (hflag) return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
+  // the SELL copy of the matrix that the solve streams
+  P->sell.slices = static_cast<SellSlice*>(at(P, P->W.slices));
+  P->sell.vout = static_cast<int32_t*>(at(P, P->W.vout));
+  P->sell.cols = static_cast<int32_t*>(at(P, P->W.scols));
+  P->sell.vals = at(P, P->W.svals);
+  P->sell.lrows = static_cast<LongRow*>(at(P, P->W.lrows));
+  P->sell.vpart = at(P, P->W.vpart);
+  P->sell.nslices = (int)sell.slices.size();
+  P->sell.nlrows = (int)sell.lrows.size();
+  TE_CK(upload_sell(P->prec, sell, P->ci, P->val, P->sell, s), "build the SELL layout");
+  if (P->owned_csr) {  // the solve reads only the SELL copy
+    cudaFree(P->owned_csr);
+    P->owned_csr = nullptr;
+  }
 
   if (opt.use_graph) {
     TE_CK(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking), "create capture stream");
@@ -707,50 +740,36 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
                         cudaMemcpyDeviceToHost, s),
         "copy row_ptr");
   TE_CK(cudaStreamSynchronize(s), "sync");
-  Partition part;
+  SellHost sell;
   std::string perr;
-  if (!make_partition(rp.data(), A->n, A->nnz, spmv_tile_nnz(prec), part, perr))
+  if (!make_sell(rp.data(), A->n, A->nnz, sell, perr))
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
-  std::vector<SpmvDesc> desc;
-  std::vector<uint16_t> runrow;
-  std::vector<uint32_t> rowrec;
-  make_descriptors(prec, part, rp.data(), desc, runrow, rowrec);
-  const size_t bd = al256(std::max<size_t>(desc.size(), 1) * sizeof(SpmvDesc));
-  const size_t br = al256(std::max<size_t>(runrow.size(), 1) * sizeof(uint16_t));
-  const size_t b0 = bd + br + al256(std::max<size_t>(rowrec.size(), 1) * sizeof(uint32_t));
-  const size_t b2 = al256(std::max<size_t>(part.lrows.size(), 1) * sizeof(LongRow));
-  const size_t b3 = al256(std::max<size_t>(part.chunks.size(), 1) * 8);
+  const size_t b_sl = al256(std::max<size_t>(sell.slices.size(), 1) * sizeof(SellSlice));
+  const size_t b_vo = al256(std::max<size_t>(sell.vout.size(), 1) * sizeof(int32_t));
+  const size_t b_co = al256(std::max<size_t>((size_t)sell.entries, 1) * sizeof(int32_t));
+  const size_t b_va = al256(std::max<size_t>((size_t)sell.entries, 1) * value_elt(prec));
+  const size_t b_lr = al256(std::max<size_t>(sell.lrows.size(), 1) * sizeof(LongRow));
+  const size_t b_vp = al256(std::max<size_t>((size_t)sell.pieces, 1) * 8);
   char* buf = nullptr;
-  TE_CK(cudaMalloc(&buf, b0 + b2 + b3 + 256), "allocate SpMV partition");
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  DevPartition dp;
-  dp.desc = reinterpret_cast<SpmvDesc*>(buf);
-  dp.runrow = reinterpret_cast<uint16_t*>(buf + bd);
-  dp.rowrec = reinterpret_cast<uint32_t*>(buf + bd + br);
-  dp.lrows = reinterpret_cast<LongRow*>(buf + b0);
-  dp.lpart = buf + b0 + b2;
-  int* flag = reinterpret_cast<int*>(buf + b0 + b2 + b3);
-  dp.ndesc = (int)desc.size();
-  dp.nchunks = (int)part.chunks.size();
-  dp.nlrows = (int)part.lrows.size();
-  dp.grid = sms;
+  TE_CK(cudaMalloc(&buf, b_sl + b_vo + b_co + b_va + b_lr + b_vp + 256), "allocate SpMV layout");
+  DevSell D;
+  size_t off = 0;
+  D.slices = reinterpret_cast<SellSlice*>(buf + off);
+  off += b_sl;
+  D.vout = reinterpret_cast<int32_t*>(buf + off);
+  off += b_vo;
+  D.cols = reinterpret_cast<int32_t*>(buf + off);
+  off += b_co;
+  D.vals = buf + off;
+  off += b_va;
+  D.lrows = reinterpret_cast<LongRow*>(buf + off);
+  off += b_lr;
+  D.vpart = buf + off;
+  off += b_vp;
+  int* flag = reinterpret_cast<int*>(buf + off);
+  D.nslices = (int)sell.slices.size();
+  D.nlrows = (int)sell.lrows.size();
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
-  if (e == cudaSuccess && dp.ndesc)
-    e = cudaMemcpyAsync(dp.desc, desc.data(), dp.ndesc * sizeof(SpmvDesc),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && dp.ndesc)
-    e = cudaMemcpyAsync(dp.runrow, runrow.data(), runrow.size() * sizeof(uint16_t),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && dp.ndesc)
-    e = cudaMemcpyAsync(dp.rowrec, rowrec.data(), rowrec.size() * sizeof(uint32_t),
-                        cudaMemcpyHostToDevice, s);
-  // the kernel writes non-empty rows only
-  if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, sizeof(double) * A->n, s);
-  if (e == cudaSuccess && dp.nlrows)
-    e = cudaMemcpyAsync(dp.lrows, part.lrows.data(), dp.nlrows * sizeof(LongRow),
-                        cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_validate_cols(A->col_idx, A->nnz, A->n, flag, s);
   int hflag = 0;
   if (e == cudaSuccess)
@@ -760,8 +779,10 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
     cudaFree(buf);
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
   }
-  if (e == cudaSuccess)
-    e = launch_spmv(prec, A->row_ptr, A->col_idx, A->values, x, y, A->n, A->nnz, dp, true, s);
+  if (e == cudaSuccess) e = upload_sell(prec, sell, A->col_idx, A->values, D, s);
+  // the kernel writes rows with entries only
+  if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, sizeof(double) * A->n, s);
+  if (e == cudaSuccess) e = launch_spmv(prec, D, x, y, true, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(buf);
   if (e != cudaSuccess) return cuda_fail(e, "te_spmv");
@@ -847,30 +868,24 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
   return TE_OK;
 }
 
-te_status te_spmv_partition(const int64_t* row_ptr, int64_t n, int64_t nnz, te_precision p,
-                            int64_t* nblocks, int64_t* nchunks, int64_t* nlong_rows,
-                            int32_t* blocks, int64_t* chunks) {
+te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int64_t* nslices,
+                         int64_t* entries, int64_t* nlong_rows, int32_t* slice_len,
+                         int32_t* lane_out, int64_t* lane_src, int32_t* lane_len) {
   if (!row_ptr || n < 1 || nnz < 0) return fail(TE_ERR_INVALID_ARG, "bad arguments");
-  const int prec = prec_of(p);
-  if (prec < 0) return fail(TE_ERR_UNSUPPORTED, "precision must be DDD or FDF");
-  Partition part;
+  SellHost sell;
   std::string perr;
-  if (!make_partition(row_ptr, n, nnz, spmv_tile_nnz(prec), part, perr))
+  if (!make_sell(row_ptr, n, nnz, sell, perr))
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
-  if (nblocks) *nblocks = (int64_t)part.blocks.size();
-  if (nchunks) *nchunks = (int64_t)part.chunks.size();
-  if (nlong_rows) *nlong_rows = (int64_t)part.lrows.size();
-  if (blocks)
-    for (size_t b = 0; b < part.blocks.size(); ++b) {
-      blocks[2 * b] = part.blocks[b].x;
-      blocks[2 * b + 1] = part.blocks[b].y;
-    }
-  if (chunks)
-    for (size_t c = 0; c < part.chunks.size(); ++c) {
-      chunks[3 * c] = part.chunks[c].k0;
-      chunks[3 * c + 1] = part.chunks[c].k1;
-      chunks[3 * c + 2] = part.chunks[c].row;
-    }
+  if (nslices) *nslices = (int64_t)sell.slices.size();
+  if (entries) *entries = sell.entries;
+  if (nlong_rows) *nlong_rows = (int64_t)sell.lrows.size();
+  for (size_t i = 0; i < sell.slices.size(); ++i)
+    if (slice_len) slice_len[i] = sell.slices[i].len;
+  for (size_t l = 0; l < sell.vout.size(); ++l) {
+    if (lane_out) lane_out[l] = sell.vout[l];
+    if (lane_src) lane_src[l] = sell.vsrc[l];
+    if (lane_len) lane_len[l] = sell.vlen[l];
+  }
   return TE_OK;
 }
 

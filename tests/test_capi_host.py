@@ -110,64 +110,84 @@ def test_workspace_bytes(te):
     assert lib.te_workspace_bytes(ctypes.byref(A), 0, 48, te._prec("fdf")) == 0
 
 
-def _check_partition(rp, nnz, blocks, chunks, nlong, tile):
+VMAX, C, WINDOW = 64, 32, 2048
+
+
+def _check_layout(rp, L):
+    """Every entry of every non-empty row is summed by exactly one lane piece;
+    short rows are one lane, cut rows are contiguous pieces of <= VMAX; slices
+    hold pieces of one window, longest first, padded to their longest piece."""
     n = len(rp) - 1
     lens = np.diff(rp)
-    long_rows = np.nonzero(lens > tile // 4)[0]
-    assert nlong == len(long_rows)
-    covered = np.zeros(n, dtype=np.int64)
-    prev_end = 0
-    for r0, r1 in blocks:
-        assert r1 > r0
-        assert r1 - r0 <= 1024
-        assert rp[r1] - rp[r0] <= tile
-        assert np.all(lens[r0:r1] <= tile // 4)
-        covered[r0:r1] += 1
-        assert r0 >= prev_end
-        prev_end = r1
-    nz_cov = np.zeros(n, dtype=np.int64)
-    for k0, k1, row in chunks:
-        assert rp[row] <= k0 < k1 <= rp[row + 1]
-        assert k1 - k0 <= tile
-        nz_cov[row] += k1 - k0
-    for r in long_rows:
-        assert covered[r] == 0
-        assert nz_cov[r] == lens[r]
-    short = np.ones(n, dtype=bool)
-    short[long_rows] = False
-    assert np.all(covered[short] == 1)
+    slen, out, src, ln = L["slice_len"], L["lane_out"], L["lane_src"], L["lane_len"]
+    S = len(slen)
+    assert len(out) == 32 * S
+    assert L["entries"] == 32 * int(slen.sum())
+    assert np.all(ln <= VMAX)
+    cover = np.zeros(int(rp[-1]) + 1, dtype=np.int64)
+    seen_rows = np.zeros(n, dtype=np.int64)
+    piece_rows = {}
+    for s in range(S):
+        lanes = slice(32 * s, 32 * s + 32)
+        l = ln[lanes]
+        assert slen[s] == l.max()
+        assert np.all(np.diff(l) <= 0), "lanes of a slice sorted longest first"
+        o = out[lanes]
+        live = o != np.iinfo(np.int32).min
+        rows = []
+        for lane in np.nonzero(live)[0]:
+            a, b = src[32 * s + lane], src[32 * s + lane] + ln[32 * s + lane]
+            assert b > a
+            cover[a:b] += 1
+            r = int(np.searchsorted(rp, a, side="right") - 1)
+            assert rp[r] <= a and b <= rp[r + 1]
+            rows.append(r)
+            if o[lane] >= 0:
+                assert o[lane] == r and a == rp[r] and b == rp[r + 1]
+                seen_rows[r] += 1
+            else:
+                piece_rows.setdefault(r, []).append((-1 - int(o[lane]), a, b))
+        assert len({r // WINDOW for r in rows}) <= 1, "a slice stays inside one window"
+    assert np.all(cover[: int(rp[-1])] == 1)
+    short = (lens > 0) & (lens <= VMAX)
+    assert np.all(seen_rows[short] == 1) and np.all(seen_rows[~short] == 0)
+    cut = np.nonzero(lens > VMAX)[0]
+    assert set(piece_rows) == set(int(r) for r in cut)
+    assert L["long_rows"] == len(cut)
+    for r, ps in piece_rows.items():
+        ps.sort()
+        slots = [p[0] for p in ps]
+        assert slots == list(range(slots[0], slots[0] + len(slots)))
+        assert ps[0][1] == rp[r] and ps[-1][2] == rp[r + 1]
+    windows = (n + WINDOW - 1) // WINDOW
+    assert L["entries"] <= rp[-1] + windows * 2 * C * VMAX
 
 
-@pytest.mark.parametrize("prec,tile", [("ddd", 4080), ("fdf", 8160)])
-def test_partition_covers_rows_once(te, prec, tile):
+def test_layout_covers_every_entry_once(te):
     mats = [synth.uniform_sym(5000, 7, 3), synth.rmat_sym(14, 8, 5)]
-    # crafted: empty rows, a star (one very long row), rows around the thresholds
+    # crafted: empty rows, a star (one very long row), rows around the cut length
     n = 20000
     lens = np.zeros(n, dtype=np.int64)
     lens[::7] = 3
     lens[5] = n - 1
-    lens[100] = tile // 4
-    lens[101] = tile // 4 + 1
-    lens[102] = tile
-    lens[103] = tile + 1
-    lens[104] = 3 * tile
+    for i, L in enumerate([63, 64, 65, 127, 128, 129, 4000]):
+        lens[100 + i] = L
     rp = np.concatenate([[0], np.cumsum(lens)])
     for A in mats:
-        blocks, chunks, nl = te.spmv_partition(A.row_ptr, A.nnz, prec)
-        _check_partition(A.row_ptr, A.nnz, blocks, chunks, nl, tile)
-    blocks, chunks, nl = te.spmv_partition(rp, int(rp[-1]), prec)
-    _check_partition(rp, int(rp[-1]), blocks, chunks, nl, tile)
-    assert nl == 5
+        _check_layout(A.row_ptr, te.spmv_layout(A.row_ptr, A.nnz))
+    L = te.spmv_layout(rp, int(rp[-1]))
+    _check_layout(rp, L)
+    assert L["long_rows"] == 6
 
 
-def test_partition_rejects_malformed_row_ptr(te):
+def test_layout_rejects_malformed_row_ptr(te):
     with pytest.raises(te.TEError) as e:
-        te.spmv_partition(np.array([0, 3, 2, 5]), 5)
+        te.spmv_layout(np.array([0, 3, 2, 5]), 5)
     assert e.value.status == 1
     with pytest.raises(te.TEError):
-        te.spmv_partition(np.array([1, 3, 4]), 4)
+        te.spmv_layout(np.array([1, 3, 4]), 4)
     with pytest.raises(te.TEError):
-        te.spmv_partition(np.array([0, 3, 4]), 5)
+        te.spmv_layout(np.array([0, 3, 4]), 5)
 
 
 def test_product_path_has_no_cpu_fallback():

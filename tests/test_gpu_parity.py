@@ -104,11 +104,11 @@ def star_plus_random(n, seed):
     return synth.from_triplets(n, r + c, c + r, np.concatenate([v, v]))
 
 
-def threshold_rows(tile, symmetric=False):
-    """Rows of length exactly around the long-row thresholds (plus their
-    transposes when `symmetric`)."""
-    lens = [0, 1, 31, 32, 33, tile // 4, tile // 4 + 1, tile, tile + 1, 2 * tile + 7, 5, 0, 2]
-    n = 3 * tile
+def threshold_rows(symmetric=False):
+    """Rows of length exactly around the SpMV's cut length (64) and its
+    multiples, plus a row of thousands (plus transposes when `symmetric`)."""
+    lens = [0, 1, 31, 32, 33, 63, 64, 65, 127, 128, 129, 4000, 5, 0, 2]
+    n = 12000
     rows, cols = [], []
     rng = np.random.default_rng(1)
     for i, L in enumerate(lens):
@@ -127,8 +127,7 @@ SPMV_CASES = {
     "n7_empty_rows": lambda: synth.from_triplets(7, [1, 3, 3, 6], [3, 1, 6, 3], [1.0, 1.0, -2.0, -2.0]),
     "star_ragged": lambda: star_plus_random(9000, 3),
     "rmat14": lambda: synth.rmat_sym(14, 8, 2),
-    "thresholds_ddd": lambda: threshold_rows(4080),
-    "thresholds_fdf": lambda: threshold_rows(8160),
+    "thresholds": lambda: threshold_rows(),
 }
 
 
@@ -247,7 +246,7 @@ SOLVE_CASES = [
     ("rmat13_K6_m20", lambda: synth.rmat_sym(13, 8, 9), 6, 20, "LM"),
     ("star_K4_m12", lambda: star_plus_random(9000, 4), 4, 12, "LM"),
     ("uniform_K_eq_m", lambda: synth.uniform_sym(500, 4, 2), 10, 10, "LA"),
-    ("thresholds_K3_m9", lambda: threshold_rows(8160, symmetric=True), 3, 9, "LM"),
+    ("thresholds_K3_m9", lambda: threshold_rows(symmetric=True), 3, 9, "LM"),
 ]
 
 
