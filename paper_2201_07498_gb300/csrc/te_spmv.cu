@@ -227,31 +227,28 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
       acc = fma(v, xv, acc);
     }
   };
-  int k = 0;
-  for (; k + SPMV_UNROLL <= sl.len; k += SPMV_UNROLL) {
+  // chunks of SPMV_UNROLL entries per lane; all loads of a chunk go out
+  // before its gathers, and the tail of a slice is a predicated chunk
+  for (int k = 0; k < sl.len; k += SPMV_UNROLL) {
     int32_t c[SPMV_UNROLL];
     val_t v[SPMV_UNROLL];
 #pragma unroll
     for (int u = 0; u < SPMV_UNROLL; ++u) {
-      c[u] = ld_stream_i32(cp + (int64_t)(k + u) * SELL_C, pol);
-      if constexpr (P == PREC_FDF) v[u] = ld_stream_f32(vp + (int64_t)(k + u) * SELL_C, pol);
-      else v[u] = ld_stream_f64(vp + (int64_t)(k + u) * SELL_C, pol);
+      const bool ok = k + u < sl.len;
+      c[u] = ok ? ld_stream_i32(cp + (int64_t)(k + u) * SELL_C, pol) : 0;
+      if constexpr (P == PREC_FDF)
+        v[u] = ok ? ld_stream_f32(vp + (int64_t)(k + u) * SELL_C, pol) : 0.f;
+      else
+        v[u] = ok ? ld_stream_f64(vp + (int64_t)(k + u) * SELL_C, pol) : 0.0;
     }
     x_t xv[SPMV_UNROLL];
 #pragma unroll
-    for (int u = 0; u < SPMV_UNROLL; ++u) xv[u] = __ldg(x + c[u]);
+    for (int u = 0; u < SPMV_UNROLL; ++u) xv[u] = __ldg(x + c[u]);  // padding reads x[0]
 #pragma unroll
     for (int u = 0; u < SPMV_UNROLL; u += 2) {
       add(acc0, v[u], xv[u]);
       add(acc1, v[u + 1], xv[u + 1]);
     }
-  }
-  for (; k < sl.len; ++k) {
-    const int32_t c = ld_stream_i32(cp + (int64_t)k * SELL_C, pol);
-    val_t v;
-    if constexpr (P == PREC_FDF) v = ld_stream_f32(vp + (int64_t)k * SELL_C, pol);
-    else v = ld_stream_f64(vp + (int64_t)k * SELL_C, pol);
-    add(acc0, v, __ldg(x + c));
   }
   acc_t acc;
   if constexpr (P == PREC_FDF) acc = dacc_merge(acc0, acc1);
