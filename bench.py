@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--K", type=int, default=24)
     p.add_argument("--m", type=int, default=48)
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=3, help="0 skips the end-to-end leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the DDD and K=8 timings")
     p.add_argument("--oracle-steps", type=int, default=6)
@@ -315,7 +315,7 @@ def main():
     e2e_ms = []
     ev_out = torch.empty(K, dtype=torch.float64).pin_memory()
     U_out = torch.empty((K, A.n), dtype=torch.float64).pin_memory()
-    for it in range(args.e2e_steps + 1):
+    for it in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         s = torch.cuda.current_stream()
         a0 = torch.cuda.Event(enable_timing=True)
@@ -326,8 +326,7 @@ def main():
         torch.cuda.synchronize()
         if it > 0:
             e2e_ms.append(a0.elapsed_time(a1))
-    e2e = statistics.median(e2e_ms)
-    e2e = max_over_ranks(e2e, world)
+    e2e = max_over_ranks(statistics.median(e2e_ms), world) if e2e_ms else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -351,8 +350,8 @@ def main():
                                                                   if v[0] > 0 and v[2] > 0
                                                                   else None)}
                         for k, v in kinds.items()},
-            "e2e": {"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+            "e2e": ({"value": e2e, "unit": "ms", "h2d_bytes_per_step": int(h2d),
+                     "d2h_bytes_per_step": int(d2h)} if e2e is not None else None),
             "gpu_launches": int(kernels_per_solve * args.steps),
             "clocks": clk,
             "cpu_baseline": cpu,
