@@ -1,7 +1,7 @@
-// te_reorth.cu - the passes over the Lanczos basis for sm_103a:
-// reorthogonalisation (Algorithm 1, lines 11-19, done as classical
-// Gram-Schmidt applied twice), the normalisation that yields beta and the
-// next basis vector (lines 6-7), and the Ritz-vector contraction V*Y
+// te_reorth.cu - the passes over the Lanczos basis for sm_103a: the
+// three-term update and the reorthogonalisation of Algorithm 1 (done as
+// classical Gram-Schmidt applied twice), the normalisation that yields beta
+// and the next basis vector, and the Ritz-vector contraction V*Y
 // (Section III).
 //
 // One persistent kernel template serves every pass.  The basis V is stored
@@ -148,7 +148,7 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
         double h = st->s[j] * si * tot[j];  // v_j . M v_i (first sweep)
         st->c1[j] = h * st->s[j];
       }
-      // Algorithm 1, line 10: alpha_i = v_i . M v_i; the second sweep adds its
+      // Algorithm 1's alpha_i = v_i . M v_i; the second sweep adds its
       // correction (FIN_AXPYDOT_STEP), so alpha keeps full accuracy even when
       // the first sweep's dots are taken in binary32 chunks
       st->alpha[i] = st->s[i] * si * tot[i];
@@ -170,7 +170,7 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       break;
     }
     case FIN_STORE_STEP: {
-      // tot[0] = ||w||^2, tot[1] = ||stored(w)||^2 (Algorithm 1, line 6)
+      // tot[0] = ||w||^2, tot[1] = ||stored(w)||^2 (beta_{i+1} of Algorithm 1)
       const double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
       const double ns = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);
       st->s[i + 1] = ns > 0.0 ? 1.0 / ns : 0.0;
@@ -343,14 +343,37 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
 
     if constexpr (HAS_AXPY) {
       // phase A: t_r = sum_j c_j V[r, j] with four independent chains
-      acc_t ta[4] = {zero_acc<P>(), zero_acc<P>(), zero_acc<P>(), zero_acc<P>()};
-      int j = 0;
-      for (; j + 4 <= nb; j += 4) {
+      acc_t tacc;
+      if constexpr (P == PREC_FDF) {
+        // Only two coefficients can be large: those of v_i and v_{i-1} in the
+        // first sweep (alpha_i and beta_i of the three-term recurrence).  The
+        // others sit at the basis' loss-of-orthogonality level, as do all
+        // second-sweep coefficients, so binary32 products and sums of those
+        // columns add an error far below the binary32 rounding of the stored
+        // result; the two large terms are taken exactly in double-float.
+        const int nsmall = (MODE == MODE_AXPY_DOT) ? (nb > 2 ? nb - 2 : 0) : nb;
+        float f[4] = {0.f, 0.f, 0.f, 0.f};
+        int j = 0;
+        for (; j + 4 <= nsmall; j += 4) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc_fma<P>(ta[u], tv[(size_t)(j + u) * TILE_R + tid], coef[j + u]);
+          for (int u = 0; u < 4; ++u)
+            f[u] = __fmaf_rn(tv[(size_t)(j + u) * TILE_R + tid], coef[j + u].x, f[u]);
+        }
+        for (; j < nsmall; ++j) f[0] = __fmaf_rn(tv[(size_t)j * TILE_R + tid], coef[j].x, f[0]);
+        tacc = dacc_zero();
+        dacc_add_pair(tacc, __fadd_rn(f[0], f[1]), __fadd_rn(f[2], f[3]));
+        for (; j < nb; ++j) acc_fma<P>(tacc, tv[(size_t)j * TILE_R + tid], coef[j]);
+      } else {
+        acc_t ta[4] = {zero_acc<P>(), zero_acc<P>(), zero_acc<P>(), zero_acc<P>()};
+        int j = 0;
+        for (; j + 4 <= nb; j += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            acc_fma<P>(ta[u], tv[(size_t)(j + u) * TILE_R + tid], coef[j + u]);
+        }
+        for (; j < nb; ++j) acc_fma<P>(ta[0], tv[(size_t)j * TILE_R + tid], coef[j]);
+        tacc = acc_merge<P>(acc_merge<P>(ta[0], ta[1]), acc_merge<P>(ta[2], ta[3]));
       }
-      for (; j < nb; ++j) acc_fma<P>(ta[0], tv[(size_t)j * TILE_R + tid], coef[j]);
-      acc_t tacc = acc_merge<P>(acc_merge<P>(ta[0], ta[1]), acc_merge<P>(ta[2], ta[3]));
       vec_t w;
       if constexpr (P == PREC_FDF) {
         dw xv = dw_from_f2(x);
@@ -382,24 +405,30 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
       named_bar_sync(1, CONSUMERS);
       // phase B: warp `wid` owns columns wid, wid+8, ...; lanes stride rows.
       // The column loop stops at this warp's last column (uniform branch).
-      // Dots of the first sweep (MODE_DOT, FDF) are summed in binary32 over
-      // the tile's 8 rows per lane and then added exactly: their error is
-      // removed by the second sweep.  The second sweep's dots use exact
-      // products and double-float sums.
+      // FDF sums the dots in binary32 over the tile's 8 rows per lane and
+      // adds each chunk exactly.  For the first sweep the error is removed by
+      // the second; for the second sweep it leaves a component of about
+      // u32 |w| along V, the level of w's own binary32 rounding.  The one
+      // second-sweep dot that enters alpha_i (column i, the last) keeps
+      // exact products and double-float sums.
 #pragma unroll
       for (int q = 0; q < QMAX; ++q) {
         const int jj = wid + (CONSUMERS / 32) * q;
         if (jj >= nb) break;
         const basis_t* col = tv + (size_t)jj * TILE_R;
-        if constexpr (P == PREC_FDF && MODE == MODE_DOT) {
-          float c0 = 0.f, c1 = 0.f;
+        if constexpr (P == PREC_FDF) {
+          if (MODE == MODE_DOT || jj < nb - 1) {
+            float c0 = 0.f, c1 = 0.f;
 #pragma unroll
-          for (int rr = 0; rr < TILE_R / 32; rr += 2) {
-            c0 = __fmaf_rn(col[lane + 32 * rr], ws[lane + 32 * rr].x, c0);
-            c1 = __fmaf_rn(col[lane + 32 * (rr + 1)], ws[lane + 32 * (rr + 1)].x, c1);
+            for (int rr = 0; rr < TILE_R / 32; rr += 2) {
+              c0 = __fmaf_rn(col[lane + 32 * rr], ws[lane + 32 * rr].x, c0);
+              c1 = __fmaf_rn(col[lane + 32 * (rr + 1)], ws[lane + 32 * (rr + 1)].x, c1);
+            }
+            dacc_add_pair(dots[q], c0, c1);
+            continue;
           }
-          dacc_add_pair(dots[q], c0, c1);
-        } else {
+        }
+        {
           acc_t e0 = zero_acc<P>(), e1 = zero_acc<P>();
 #pragma unroll
           for (int rr = 0; rr < TILE_R / 32; rr += 2) {
@@ -425,11 +454,31 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
         acc_t ra[RITZ_KC];
 #pragma unroll
         for (int kk = 0; kk < RITZ_KC; ++kk) ra[kk] = zero_acc<P>();
-        for (int j = 0; j < nb; ++j) {
-          const basis_t v = tv[(size_t)j * TILE_R + tid];
+        if constexpr (P == PREC_FDF) {
+          // binary32 partial sums over 8 basis columns, each added exactly to
+          // a double-float accumulator: the error stays within a small
+          // multiple of the binary32 rounding the stored basis already has
+          for (int j0 = 0; j0 < nb; j0 += 8) {
+            float f[RITZ_KC];
 #pragma unroll
-          for (int kk = 0; kk < RITZ_KC; ++kk)
-            if (k0 + kk < K) acc_fma<P>(ra[kk], v, rC[j * K + k0 + kk]);
+            for (int kk = 0; kk < RITZ_KC; ++kk) f[kk] = 0.f;
+            const int j1 = j0 + 8 < nb ? j0 + 8 : nb;
+            for (int j = j0; j < j1; ++j) {
+              const float v = tv[(size_t)j * TILE_R + tid];
+#pragma unroll
+              for (int kk = 0; kk < RITZ_KC; ++kk)
+                if (k0 + kk < K) f[kk] = __fmaf_rn(v, rC[j * K + k0 + kk].x, f[kk]);
+            }
+#pragma unroll
+            for (int kk = 0; kk < RITZ_KC; ++kk) dacc_add_pair(ra[kk], f[kk], 0.f);
+          }
+        } else {
+          for (int j = 0; j < nb; ++j) {
+            const basis_t v = tv[(size_t)j * TILE_R + tid];
+#pragma unroll
+            for (int kk = 0; kk < RITZ_KC; ++kk)
+              if (k0 + kk < K) acc_fma<P>(ra[kk], v, rC[j * K + k0 + kk]);
+          }
         }
         if (row < a.n) {
 #pragma unroll
