@@ -44,6 +44,9 @@ FAULTS = {
     "select_algebraic": 6,
     "spmv_skip_last": 7,
     "no_v1_normalise": 8,
+    "refine_no_norm": 9,
+    "angle_signed": 10,
+    "reorth_ignored": 11,
 }
 
 
@@ -87,6 +90,16 @@ def _load():
         lib.oracle_topk_eigs.argtypes = [i64, vp, vp, vp, vp, i32, i32, i32, u64, vp, vp, vp,
                                          vp, vp, vp]
         lib.oracle_topk_eigs.restype = ctypes.c_int
+        lib.oracle_lanczos_ex.argtypes = [i64, vp, vp, vp, vp, i32, u64, dbl, i32, vp, vp, vp,
+                                          vp, vp]
+        lib.oracle_lanczos_ex.restype = ctypes.c_int
+        lib.oracle_topk_eigs_ex.argtypes = [i64, vp, vp, vp, vp, i32, i32, i32, u64, i32, vp,
+                                            vp, vp, vp, vp, vp]
+        lib.oracle_topk_eigs_ex.restype = ctypes.c_int
+        lib.oracle_refine.argtypes = [i64, vp, vp, vp, i32, vp, vp, vp]
+        lib.oracle_refine.restype = None
+        lib.oracle_mean_pairwise_angle.argtypes = [i64, i32, vp]
+        lib.oracle_mean_pairwise_angle.restype = dbl
         _lib = lib
         return lib
 
@@ -152,7 +165,9 @@ class LanczosResult:
                 + np.diag(self.beta[1:m], -1))
 
 
-def lanczos(csr, v1_raw, m: int, seed: int = 0, tol: float = BREAKDOWN_TOL) -> LanczosResult:
+def lanczos(csr, v1_raw, m: int, seed: int = 0, tol: float = BREAKDOWN_TOL,
+            reorth: bool = True) -> LanczosResult:
+    """Algorithm 1 (reorth=False: the variant without reorthogonalisation)."""
     n, rp, ci, val = _csr_arrays(csr)
     v1 = np.ascontiguousarray(v1_raw, dtype=np.float64)
     alpha = np.empty(m)
@@ -160,8 +175,9 @@ def lanczos(csr, v1_raw, m: int, seed: int = 0, tol: float = BREAKDOWN_TOL) -> L
     V = np.empty((m, n))  # row j of this array is column j of V
     w = np.empty(n)
     restarts = np.zeros(1, dtype=np.int32)
-    rc = _load().oracle_lanczos(n, _p(rp), _p(ci), _p(val), _p(v1), m, seed, tol, _p(alpha),
-                                _p(beta), _p(V), _p(w), _p(restarts))
+    rc = _load().oracle_lanczos_ex(n, _p(rp), _p(ci), _p(val), _p(v1), m, seed, tol,
+                                   1 if reorth else 0, _p(alpha), _p(beta), _p(V), _p(w),
+                                   _p(restarts))
     if rc != 0:
         raise ValueError(f"oracle_lanczos failed with code {rc}")
     return LanczosResult(alpha, beta, V.T.copy(), w, int(restarts[0]))
@@ -208,8 +224,28 @@ class TopKResult:
     converged: bool
 
 
+def refine(csr, U):
+    """Rayleigh quotients u'Mu/u'u and residuals ||Mu - theta u|| / ||u|| of the
+    columns of U (n x K), in binary64."""
+    n, rp, ci, val = _csr_arrays(csr)
+    Uc = np.ascontiguousarray(np.asarray(U, dtype=np.float64).T)  # column-major
+    K = Uc.shape[0]
+    th = np.empty(K)
+    res = np.empty(K)
+    _load().oracle_refine(n, _p(rp), _p(ci), _p(val), K, _p(Uc), _p(th), _p(res))
+    return th, res
+
+
+def mean_pairwise_angle(U) -> float:
+    """Mean sign-free angle (degrees) between the columns of U (n x K)."""
+    Uc = np.ascontiguousarray(np.asarray(U, dtype=np.float64).T)
+    K, n = Uc.shape
+    return float(_load().oracle_mean_pairwise_angle(n, K, _p(Uc)))
+
+
 def topk_eigs(csr, K: int, m: int, v1_raw, which: int = LARGEST_MAGNITUDE, seed: int = 0,
-              want_vectors: bool = True, want_residuals: bool = True) -> TopKResult:
+              want_vectors: bool = True, want_residuals: bool = True,
+              reorth: bool = True) -> TopKResult:
     n, rp, ci, val = _csr_arrays(csr)
     v1 = np.ascontiguousarray(v1_raw, dtype=np.float64)
     ev = np.empty(K)
@@ -218,8 +254,9 @@ def topk_eigs(csr, K: int, m: int, v1_raw, which: int = LARGEST_MAGNITUDE, seed:
     alpha = np.empty(m)
     beta = np.empty(m + 1)
     info = np.zeros(3, dtype=np.int32)
-    rc = _load().oracle_topk_eigs(n, _p(rp), _p(ci), _p(val), _p(v1), K, m, which, seed,
-                                  _p(ev), _p(U), _p(res), _p(alpha), _p(beta), _p(info))
+    rc = _load().oracle_topk_eigs_ex(n, _p(rp), _p(ci), _p(val), _p(v1), K, m, which, seed,
+                                     1 if reorth else 0, _p(ev), _p(U), _p(res), _p(alpha),
+                                     _p(beta), _p(info))
     if rc < 0:
         raise ValueError(f"oracle_topk_eigs failed with code {rc}")
     return TopKResult(ev, None if U is None else U.T.copy(), res, alpha, beta, int(info[0]),

@@ -16,6 +16,11 @@
  *   - oracle_select_topk: "largest in modulo" (Section I).
  *   - oracle_ritz:        eigenvectors of M as (Lanczos basis) x (eigenvectors
  *                         of T) (Section III).
+ *   - oracle_lanczos_ex:  the same Lanczos with reorthogonalisation switched
+ *                         off (the comparison of Section IV-D).
+ *   - oracle_refine:      Rayleigh quotient u'Mu/u'u and residual of given
+ *                         vectors (definition).
+ *   - oracle_mean_pairwise_angle: the orthogonality metric of Section IV-D.
  *
  * Readings where the paper is silent or garbled (listed with reasons in the
  * design notes of the repository):
@@ -120,7 +125,7 @@ void oracle_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* 
 }
 
 /* ---------------- Lanczos with MGS reorthogonalisation ---------------- */
-/* MGS pass of w against columns 0..cols-1 of V (Algorithm 1, lines 12-19) */
+/* MGS pass of w against columns 0..cols-1 of V (Algorithm 1's reorthogonalisation) */
 static void om_mgs(int64_t n, int32_t cols, const double* V, double* w) {
   for (int32_t j = 0; j < cols; ++j) {
     const double* vj = V + (size_t)j * (size_t)n;
@@ -133,6 +138,14 @@ int oracle_lanczos(int64_t n, const int64_t* rp, const int32_t* ci, const double
                    const double* v1_raw, int32_t m, uint64_t seed, double tol,
                    double* alpha, double* beta, double* V, double* w_out,
                    int32_t* restarts_out) {
+  return oracle_lanczos_ex(n, rp, ci, val, v1_raw, m, seed, tol, 1, alpha, beta, V, w_out,
+                           restarts_out);
+}
+
+int oracle_lanczos_ex(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                      const double* v1_raw, int32_t m, uint64_t seed, double tol, int32_t reorth,
+                      double* alpha, double* beta, double* V, double* w_out,
+                      int32_t* restarts_out) {
   if (n < 1 || m < 1 || m > n || !rp || !ci || !val || !v1_raw || !alpha || !beta || !V)
     return -1;
   double* vt = (double*)malloc(sizeof(double) * (size_t)n);
@@ -151,11 +164,11 @@ int oracle_lanczos(int64_t n, const int64_t* rp, const int32_t* ci, const double
   for (int32_t i = 0; i < m; ++i) {
     const double* vi = V + (size_t)i * (size_t)n;
     const double* vim1 = i > 0 ? V + (size_t)(i - 1) * (size_t)n : NULL;
-    /* line 9: v_t <- SpMV(M, v_i) */
+    /* SpMV step: v_t <- M v_i */
     oracle_spmv(n, rp, ci, val, vi, vt);
-    /* line 10: alpha_i <- v_i . v_t */
+    /* alpha_i <- v_i . v_t */
     alpha[i] = om_dot(n, vi, vt);
-    /* line 11: v_nxt <- v_t - alpha_i v_i - beta_i v_{i-1} */
+    /* three-term update: v_nxt <- v_t - alpha_i v_i - beta_i v_{i-1} */
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n; ++k) {
       double x = vt[k] - alpha[i] * vi[k];
@@ -163,9 +176,10 @@ int oracle_lanczos(int64_t n, const int64_t* rp, const int32_t* ci, const double
       w[k] = x;
     }
     if (g_fault == ORACLE_FAULT_ALPHA_SIGN) alpha[i] = -alpha[i];
-    /* lines 12-19: reorthogonalise v_nxt against v_1..v_i (one MGS pass) */
-    if (g_fault != ORACLE_FAULT_NO_REORTH) om_mgs(n, i + 1, V, w);
-    /* line 6 of the next iteration: beta_{i+1} <- ||v_nxt|| */
+    /* reorthogonalise v_nxt against v_1..v_i (one MGS pass) */
+    if ((reorth || g_fault == ORACLE_FAULT_REORTH_IGNORED) && g_fault != ORACLE_FAULT_NO_REORTH)
+      om_mgs(n, i + 1, V, w);
+    /* start of the next iteration: beta_{i+1} <- ||v_nxt|| */
     double b = om_norm(n, w);
     double cand = fabs(alpha[i]) + beta[i] + b;
     if (cand > anorm) anorm = cand;
@@ -184,7 +198,7 @@ int oracle_lanczos(int64_t n, const int64_t* rp, const int32_t* ci, const double
         for (int64_t k = 0; k < n; ++k) vnext[k] = w[k] / br;
         beta[i + 1] = 0.0;
       } else {
-        /* line 7: v_{i+1} <- v_nxt / beta_{i+1} */
+        /* v_{i+1} <- v_nxt / beta_{i+1} */
         for (int64_t k = 0; k < n; ++k) vnext[k] = w[k] / b;
       }
     } else if (w_out) {
@@ -303,11 +317,59 @@ void oracle_ritz(int64_t n, int32_t m, const double* V, const double* Y, int32_t
   }
 }
 
+/* ---------------- Rayleigh quotient, residual, pairwise angles ---------------- */
+void oracle_refine(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                   int32_t K, const double* U, double* theta_out, double* resid_out) {
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  double* r = (double*)malloc(sizeof(double) * (size_t)n);
+  for (int32_t k = 0; k < K; ++k) {
+    const double* u = U + (size_t)k * (size_t)n;
+    oracle_spmv(n, rp, ci, val, u, y);
+    const double uu = om_dot(n, u, u);
+    const double th = om_dot(n, u, y) / (g_fault == ORACLE_FAULT_REFINE_NO_NORM ? 1.0 : uu);
+    theta_out[k] = th;
+    if (resid_out) {
+      for (int64_t i = 0; i < n; ++i) r[i] = y[i] - th * u[i];
+      resid_out[k] = om_norm(n, r) / sqrt(uu);
+    }
+  }
+  free(y);
+  free(r);
+}
+
+double oracle_mean_pairwise_angle(int64_t n, int32_t K, const double* U) {
+  if (K < 2) return 0.0;
+  const double pi = acos(-1.0);
+  double sum = 0.0;
+  int64_t pairs = 0;
+  for (int32_t a = 0; a < K; ++a) {
+    const double* ua = U + (size_t)a * (size_t)n;
+    for (int32_t b = a + 1; b < K; ++b) {
+      const double* ub = U + (size_t)b * (size_t)n;
+      double d = om_dot(n, ua, ub);
+      if (g_fault != ORACLE_FAULT_ANGLE_SIGNED) d = fabs(d);
+      double c = d / (om_norm(n, ua) * om_norm(n, ub));
+      if (c > 1.0) c = 1.0;
+      sum += acos(c) * 180.0 / pi;
+      pairs += 1;
+    }
+  }
+  return sum / (double)pairs;
+}
+
 /* ---------------- the whole pipeline ---------------- */
 int oracle_topk_eigs(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
                      const double* v1_raw, int32_t K, int32_t m, int32_t which, uint64_t seed,
                      double* eigvals, double* U, double* residuals, double* alpha_out,
                      double* beta_out, int32_t* info) {
+  return oracle_topk_eigs_ex(n, rp, ci, val, v1_raw, K, m, which, seed, 1, eigvals, U,
+                             residuals, alpha_out, beta_out, info);
+}
+
+int oracle_topk_eigs_ex(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                        const double* v1_raw, int32_t K, int32_t m, int32_t which,
+                        uint64_t seed, int32_t reorth, double* eigvals, double* U,
+                        double* residuals, double* alpha_out, double* beta_out, int32_t* info) {
   if (K < 1 || m < K || m > n || !eigvals) return -1;
   double* V = (double*)malloc(sizeof(double) * (size_t)n * (size_t)m);
   double* alpha = (double*)malloc(sizeof(double) * (size_t)m);
@@ -318,8 +380,8 @@ int oracle_topk_eigs(int64_t n, const int64_t* rp, const int32_t* ci, const doub
   int rc = -2;
   if (!V || !alpha || !beta || !T || !Y || !idx) goto done;
   int32_t restarts = 0, sweeps = 0;
-  rc = oracle_lanczos(n, rp, ci, val, v1_raw, m, seed, ORACLE_BREAKDOWN_TOL, alpha, beta, V,
-                      NULL, &restarts);
+  rc = oracle_lanczos_ex(n, rp, ci, val, v1_raw, m, seed, ORACLE_BREAKDOWN_TOL, reorth, alpha,
+                         beta, V, NULL, &restarts);
   if (rc != 0) goto done;
   for (int32_t i = 0; i < m; ++i) {
     T[(size_t)i * m + i] = alpha[i];

@@ -32,6 +32,9 @@ extern "C" {
 #define ORACLE_FAULT_SELECT_ALGEBRAIC 6
 #define ORACLE_FAULT_SPMV_SKIP_LAST 7
 #define ORACLE_FAULT_NO_V1_NORMALISE 8
+#define ORACLE_FAULT_REFINE_NO_NORM 9     /* Rayleigh quotient without the 1/u'u */
+#define ORACLE_FAULT_ANGLE_SIGNED 10      /* angle metric without the absolute value */
+#define ORACLE_FAULT_REORTH_IGNORED 11    /* reorth = 0 still reorthogonalises */
 
 void oracle_set_fault(int kind);
 int oracle_get_fault(void);
@@ -52,6 +55,26 @@ int oracle_lanczos(int64_t n, const int64_t* rp, const int32_t* ci, const double
                    double* alpha, double* beta, double* V, double* w_out,
                    int32_t* restarts_out);
 
+/* Lanczos with a choice of reorthogonalisation: reorth = 1 is oracle_lanczos;
+   reorth = 0 keeps only Algorithm 1's SpMV, alpha and three-term update:
+   the variant without reorthogonalisation of Section IV-D. */
+int oracle_lanczos_ex(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                      const double* v1_raw, int32_t m, uint64_t seed, double tol, int32_t reorth,
+                      double* alpha, double* beta, double* V, double* w_out,
+                      int32_t* restarts_out);
+
+/* Rayleigh quotient and residual of K given vectors (U n x K column-major):
+   theta_out[k] = u_k' M u_k / u_k' u_k and resid_out[k] = ||M u_k -
+   theta_out[k] u_k|| / ||u_k||, both in binary64 (definition; the
+   refinement step of the mixed-precision forms).  resid_out may be NULL. */
+void oracle_refine(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                   int32_t K, const double* U, double* theta_out, double* resid_out);
+
+/* Mean over the pairs a < b of the angle (degrees) between u_a and u_b,
+   taken sign-free: acos(|u_a . u_b| / (||u_a|| ||u_b||)) (the orthogonality
+   metric of Section IV-D; 90 for an orthogonal set).  K >= 2. */
+double oracle_mean_pairwise_angle(int64_t n, int32_t K, const double* U);
+
 /* cyclic-by-row Jacobi: T (m x m, symmetric, row-major) is diagonalised in
    place, Y receives the eigenvectors (columns).  Returns 0 if converged. */
 int oracle_jacobi(int32_t m, double* T, double* Y, double tol, int32_t max_sweeps,
@@ -70,6 +93,11 @@ int oracle_topk_eigs(int64_t n, const int64_t* rp, const int32_t* ci, const doub
                      const double* v1_raw, int32_t K, int32_t m, int32_t which, uint64_t seed,
                      double* eigvals, double* U, double* residuals, double* alpha_out,
                      double* beta_out, int32_t* info);
+/* the same with the reorthogonalisation choice of oracle_lanczos_ex */
+int oracle_topk_eigs_ex(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
+                        const double* v1_raw, int32_t K, int32_t m, int32_t which,
+                        uint64_t seed, int32_t reorth, double* eigvals, double* U,
+                        double* residuals, double* alpha_out, double* beta_out, int32_t* info);
 
 #ifdef __cplusplus
 }

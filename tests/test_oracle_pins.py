@@ -259,10 +259,78 @@ def pin_ritz_vectors():
     return None
 
 
+def pin_lanczos_without_reorth():
+    """Reorthogonalisation off: the hand-worked examples (exact arithmetic does
+    not need it), the three-term relation A V - V T = w e_m^T (which holds
+    without reorthogonalisation), and the loss of orthogonality once the
+    dominant Ritz value converges (Paige's theory), absent with it on."""
+    for c in json.load(open(GOLDEN))["cases"]:
+        if "alpha" not in c:
+            continue
+        r = oracle.lanczos(_dense_csr(c["dense"]), np.array(c["v1"], dtype=float), c["m"],
+                           reorth=False)
+        if np.max(np.abs(r.alpha - np.array(c["alpha"]))) > 1e-14:
+            return f"{c['name']}: alpha without reorth {r.alpha}"
+    n, m = 400, 40
+    d = np.concatenate([[10.0], np.linspace(0.0, 1.0, n - 1)])
+    A = synth.diagonal(d)
+    v1 = synth.start_vector(n, 5)
+    r0 = oracle.lanczos(A, v1, m, reorth=False)
+    r1 = oracle.lanczos(A, v1, m, reorth=True)
+    R = np.diag(d) @ r0.V - r0.V @ r0.T()
+    R[:, -1] -= r0.w_last
+    if np.max(np.abs(R)) > 1e-12 * 10:
+        return "three-term relation without reorth"
+    lost0 = np.max(np.abs(r0.V.T @ r0.V - np.eye(m)))
+    lost1 = np.max(np.abs(r1.V.T @ r1.V - np.eye(m)))
+    if not (lost0 > 1e-6 and lost1 < 1e-12):
+        return f"orthogonality without / with reorth: {lost0:.2e} / {lost1:.2e}"
+    return None
+
+
+def pin_refine_closed_form():
+    """Rayleigh quotient and residual of u = c (e_1 + eps e_2) on diag(d):
+    theta = (d1 + eps^2 d2) / (1 + eps^2), residual = |eps (d2 - d1)| / (1 + eps^2);
+    an exact eigenvector gives its eigenvalue and residual 0."""
+    d = np.array([3.0, -1.5, 0.25, 2.0])
+    A = synth.diagonal(d)
+    eps, c = 1e-3, 2.5
+    u = np.zeros((4, 2))
+    u[0, 0], u[1, 0] = c, c * eps
+    u[3, 1] = -0.7
+    th, res = oracle.refine(A, u)
+    th_ref = (d[0] + eps ** 2 * d[1]) / (1 + eps ** 2)
+    res_ref = abs(eps * (d[1] - d[0])) / (1 + eps ** 2)
+    if abs(th[0] - th_ref) > 1e-15 or abs(res[0] - res_ref) > 1e-15:
+        return f"perturbed vector: {th[0]} {res[0]} vs {th_ref} {res_ref}"
+    if th[1] != d[3] or res[1] != 0.0:
+        return f"exact eigenvector: {th[1]} {res[1]}"
+    return None
+
+
+def pin_pairwise_angle():
+    """Orthogonal columns give 90 degrees; cos = +-0.5 gives 60 either sign;
+    three vectors at known angles give their mean."""
+    Q, _ = np.linalg.qr(synth.uniform_pm1(600, 3, 1).reshape(100, 6))
+    if abs(oracle.mean_pairwise_angle(Q) - 90.0) > 1e-9:
+        return "orthonormal set"
+    a = np.array([1.0, 0.0, 0.0])
+    b = np.array([0.5, math.sqrt(3) / 2, 0.0])
+    for sgn in (1.0, -1.0):
+        if abs(oracle.mean_pairwise_angle(np.stack([a, sgn * b], 1)) - 60.0) > 1e-12:
+            return f"60 degrees, sign {sgn}"
+    c = np.array([0.0, 0.0, 2.0])
+    # angles: (a,b) 60, (a,c) 90, (b,c) 90
+    if abs(oracle.mean_pairwise_angle(np.stack([a, -b, c], 1)) - 80.0) > 1e-12:
+        return "three vectors"
+    return None
+
+
 PINS = [pin_spmv_brute_force, pin_hand_examples, pin_jacobi_toeplitz, pin_jacobi_2x2,
         pin_jacobi_random, pin_lanczos_path_full, pin_lanczos_cycle_full,
         pin_lanczos_diagonal_trace, pin_lanczos_dense_bruteforce,
-        pin_lanczos_partial_invariants, pin_selection, pin_ritz_vectors]
+        pin_lanczos_partial_invariants, pin_selection, pin_ritz_vectors,
+        pin_lanczos_without_reorth, pin_refine_closed_form, pin_pairwise_angle]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
