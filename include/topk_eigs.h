@@ -76,13 +76,22 @@ typedef struct {
   int64_t nnz;            /* stored entries, >= 0 */
   const int64_t* row_ptr; /* n + 1 */
   const int32_t* col_idx; /* nnz */
-  const void* values;     /* nnz elements of type precision.values */
+  const void* values;     /* nnz elements: binary64 if values_f64, else of type
+                             precision.values */
   const float* row_scale; /* reserved for scaled 8-bit values; must be NULL */
   int32_t where;          /* TE_DEVICE or TE_HOST */
+  int32_t values_f64;     /* 0: `values` already have type precision.values.
+                             1: `values` are binary64; the library rounds them to
+                             precision.values (to nearest, ties to even) when it
+                             builds its copy of the matrix, and keeps the binary64
+                             values when refinement is requested. */
 } te_csr;
 
 #define TE_WHICH_LARGEST_MAGNITUDE 0 /* |theta| descending; ties: positive, then index */
 #define TE_WHICH_LARGEST_ALGEBRAIC 1 /* theta descending; ties: lower index */
+
+#define TE_REORTH_FULL 0 /* full reorthogonalisation every step (Algorithm 1) */
+#define TE_REORTH_NONE 1 /* three-term recurrence only (Section IV-D's comparison) */
 
 typedef struct {
   uint64_t seed;    /* SplitMix64 seed: start vector = stream 0, restart r = stream r */
@@ -90,10 +99,17 @@ typedef struct {
   int32_t which;    /* TE_WHICH_* */
   int32_t use_graph; /* plans: capture the whole solve as one CUDA graph (default 1) */
   size_t device_budget_bytes; /* 0 = no limit on the work memory */
+  int32_t reorth;   /* TE_REORTH_FULL (default) or TE_REORTH_NONE */
+  int32_t refine;   /* 1: after the Ritz vectors, replace each selected Ritz value by
+                       the binary64 Rayleigh quotient u'Mu/u'u of its vector against
+                       the binary64 matrix, and its residual by the true residual
+                       ||Mu - theta u|| / ||u||.  Needs A->values_f64 = 1.  Costs K
+                       binary64 SpMVs; with eigvecs NULL the plan keeps its own
+                       vectors.  Default 0. */
 } te_options;
 
 /* Fill `opt` with the defaults: seed 0, v1 NULL, largest magnitude, graphs on,
- * no budget. */
+ * no budget, full reorthogonalisation, no refinement. */
 void te_default_options(te_options* opt);
 
 /* Thread-local message describing the last error on this thread ("" if none). */
@@ -115,7 +131,8 @@ size_t te_workspace_bytes(const te_csr* A, int32_t K, int32_t krylov_steps, te_p
  *                the Ritz-vector contraction
  *   residuals    K doubles, host or device, or NULL: the Ritz residual
  *                estimates |beta_{m+1} * y_k[m]| (= ||M u_k - theta_k u_k|| in
- *                exact arithmetic)
+ *                exact arithmetic), or with opt->refine the true residuals
+ *                ||M u_k - theta_k u_k|| / ||u_k|| in binary64
  * With A->where == TE_HOST the matrix is copied to the device inside the call.
  * Synchronises `stream` before returning.  TE_ERR_BREAKDOWN is returned (with
  * all outputs written) when a restart could not produce a new direction.
@@ -157,7 +174,8 @@ te_status te_plan_status(te_plan* plan);
 #define TE_KIND_JACOBI 5     /* Jacobi phase, selection, Ritz coefficients */
 #define TE_KIND_RITZ 6       /* Ritz-vector contraction V * Y */
 #define TE_KIND_OTHER 7      /* solve set-up and start-vector pass */
-#define TE_NUM_KINDS 8
+#define TE_KIND_REFINE 8     /* binary64 Rayleigh-quotient refinement (SpMVs + reductions) */
+#define TE_NUM_KINDS 9
 
 /* Run one solve on `stream` without the CUDA graph, timing every kernel with
  * CUDA events recorded on `stream`, and synchronise.  For each kind k:
@@ -177,7 +195,8 @@ void te_plan_destroy(te_plan* plan);
 /* ---- single phases, for testing and for callers composing their own solver ---- */
 
 /* y = M x with the solver's SpMV (Algorithm 1, SpMV step).  x: n elements of
- * type p.vectors (device); y: n doubles (device).  A must be TE_DEVICE. */
+ * type p.vectors (device); y: n doubles (device).  A must be TE_DEVICE; with
+ * A->values_f64 the values are rounded to p.values first, as in a plan. */
 te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, void* stream);
 
 /* The Lanczos phase alone (Algorithm 1): writes alpha[0..m-1] and
@@ -207,10 +226,17 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
  * TE_ERR_INVALID_ARG.  The first call on each device looks up the array's
  * device address (do that first call before any stream capture).  Calls that
  * overlap on the GPU (other streams, other host threads) race on the array
- * and must be serialised by the caller.  A must be TE_DEVICE; x has n
+ * and must be serialised by the caller.  A must be TE_DEVICE with
+ * values_f64 = 0 (there is no room to round the values); x has n
  * elements of type p.vectors; y receives n doubles.  Synchronises `stream`. */
 te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void* x, double* y,
                           void* stream);
+
+/* Gram matrix G = U^T U of K vectors (U: n x K, column-major, device), summed
+ * in binary64 in a fixed order; G (K x K, row-major) is written to host memory.
+ * For the orthogonality metric of Section IV-D (the mean angle between pairs
+ * of eigenvectors).  1 <= K <= 64.  Synchronises `stream`. */
+te_status te_gram(int64_t n, int32_t K, const double* U, double* G, void* stream);
 
 /* Host-side layout behind the SpMV (no GPU needed; row_ptr in host memory):
  * the SELL-C-sigma arrangement a plan builds (Kreutzer et al., SIAM J. Sci.

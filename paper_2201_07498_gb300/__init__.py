@@ -19,11 +19,12 @@ from dataclasses import dataclass
 from . import _build
 
 __all__ = ["CSR", "Plan", "TEError", "topk_eigs", "spmv", "lanczos", "tridiag_eigs",
-           "spmv_layout", "library_path", "load_library", "PRECISIONS"]
+           "spmv_layout", "gram", "library_path", "load_library", "PRECISIONS"]
 
 TE_F64, TE_F32, TE_BF16, TE_FP8_E4M3 = 0, 1, 2, 3
 TE_DEVICE, TE_HOST = 0, 1
 WHICH = {"LM": 0, "LA": 1}
+REORTH = {"full": 0, "none": 1}
 PRECISIONS = {"ddd": (TE_F64, TE_F64, TE_F64), "fdf": (TE_F32, TE_F64, TE_F32)}
 STATUS = {0: "TE_OK", 1: "TE_ERR_INVALID_ARG", 2: "TE_ERR_OUT_OF_MEMORY", 3: "TE_ERR_CUDA",
           4: "TE_ERR_BREAKDOWN", 5: "TE_ERR_NOT_CONVERGED", 6: "TE_ERR_TIMEOUT",
@@ -39,7 +40,8 @@ class TEError(RuntimeError):
 class te_csr(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
                 ("col_idx", ctypes.c_void_p), ("values", ctypes.c_void_p),
-                ("row_scale", ctypes.c_void_p), ("where", ctypes.c_int32)]
+                ("row_scale", ctypes.c_void_p), ("where", ctypes.c_int32),
+                ("values_f64", ctypes.c_int32)]
 
 
 class te_precision(ctypes.Structure):
@@ -49,7 +51,8 @@ class te_precision(ctypes.Structure):
 
 class te_options(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("v1", ctypes.c_void_p), ("which", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("device_budget_bytes", ctypes.c_size_t)]
+                ("use_graph", ctypes.c_int32), ("device_budget_bytes", ctypes.c_size_t),
+                ("reorth", ctypes.c_int32), ("refine", ctypes.c_int32)]
 
 
 # every symbol the header declares, with its ctypes signature
@@ -84,6 +87,8 @@ _SIGS = {
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "te_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "te_gram": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p]),
     "te_spmv_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -142,12 +147,14 @@ def _stream_ptr(stream):
 class CSR:
     """CSR matrix held in torch tensors (device or host).
 
-    row_ptr: int64 (n+1); col: int32 (nnz); val: float64 (DDD) or float32 (FDF).
+    row_ptr: int64 (n+1); col: int32 (nnz); val: float64 (DDD, or any form
+    when values_f64: the library rounds them itself) or float32 (FDF).
     """
     n: int
     row_ptr: "object"
     col: "object"
     val: "object"
+    values_f64: bool = False
 
     @property
     def nnz(self) -> int:
@@ -162,25 +169,30 @@ class CSR:
             if not t.is_contiguous():
                 raise ValueError("CSR tensors must be contiguous")
         return te_csr(self.n, self.nnz, self.row_ptr.data_ptr(), self.col.data_ptr(),
-                      self.val.data_ptr(), None, TE_DEVICE if self.on_device else TE_HOST)
+                      self.val.data_ptr(), None, TE_DEVICE if self.on_device else TE_HOST,
+                      1 if self.values_f64 else 0)
 
     @staticmethod
-    def from_host(host_csr, precision: str = "ddd", device: str = "cuda", pin: bool = False):
-        """Make a CSR from numpy arrays (an object with n, row_ptr, col, val)."""
+    def from_host(host_csr, precision: str = "ddd", device: str = "cuda", pin: bool = False,
+                  values_f64: bool = False):
+        """Make a CSR from numpy arrays (an object with n, row_ptr, col, val).
+        values_f64 keeps binary64 values for any precision (the library rounds
+        them; needed for refinement)."""
         import numpy as np
         import torch
-        vdt = np.float32 if _prec(precision).values == TE_F32 else np.float64
+        vdt = np.float32 if (_prec(precision).values == TE_F32 and not values_f64) else np.float64
         rp = torch.from_numpy(np.ascontiguousarray(host_csr.row_ptr, dtype=np.int64))
         ci = torch.from_numpy(np.ascontiguousarray(host_csr.col, dtype=np.int32))
         va = torch.from_numpy(np.ascontiguousarray(host_csr.val, dtype=vdt))
         if device == "cpu":
             if pin:
                 rp, ci, va = rp.pin_memory(), ci.pin_memory(), va.pin_memory()
-            return CSR(int(host_csr.n), rp, ci, va)
-        return CSR(int(host_csr.n), rp.to(device), ci.to(device), va.to(device))
+            return CSR(int(host_csr.n), rp, ci, va, values_f64)
+        return CSR(int(host_csr.n), rp.to(device), ci.to(device), va.to(device), values_f64)
 
 
-def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0) -> te_options:
+def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full",
+             refine=False) -> te_options:
     o = te_options()
     load_library().te_default_options(ctypes.byref(o))
     o.seed = seed
@@ -188,18 +200,22 @@ def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0) -> te_option
     o.which = WHICH[which] if isinstance(which, str) else int(which)
     o.use_graph = 1 if use_graph else 0
     o.device_budget_bytes = budget
+    o.reorth = REORTH[reorth] if isinstance(reorth, str) else int(reorth)
+    o.refine = 1 if refine else 0
     return o
 
 
 def topk_eigs(csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0, v1=None,
-              which="LM", vectors: bool = True, residuals: bool = False, stream=None, out=None):
+              which="LM", vectors: bool = True, residuals: bool = False, reorth="full",
+              refine: bool = False, stream=None, out=None):
     """One Top-K solve; returns (eigvals [K] float64 cpu, eigvecs [n, K] float64 or None,
-    residual estimates [K] or None).  Vectors live where the matrix lives unless
-    `out = (eigvals [K], eigvecs [K, n] or None)` gives preallocated buffers."""
+    residuals [K] or None: estimates, or true binary64 residuals with refine).
+    Vectors live where the matrix lives unless `out = (eigvals [K], eigvecs
+    [K, n] or None)` gives preallocated buffers."""
     import torch
     lib = load_library()
     A = csr.to_ctypes()
-    opt = _options(seed, v1, which)
+    opt = _options(seed, v1, which, reorth=reorth, refine=refine)
     if out is not None:
         ev, U = out
     else:
@@ -220,11 +236,12 @@ class Plan:
     """A reusable solve (row partition, work memory and captured CUDA graph)."""
 
     def __init__(self, csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0,
-                 v1=None, which="LM", use_graph: bool = True, budget: int = 0, stream=None):
+                 v1=None, which="LM", use_graph: bool = True, budget: int = 0,
+                 reorth="full", refine: bool = False, stream=None):
         self._lib = load_library()
         self.csr, self.K, self.m, self.n = csr, K, krylov_steps, csr.n
         A = csr.to_ctypes()
-        opt = _options(seed, v1, which, use_graph, budget)
+        opt = _options(seed, v1, which, use_graph, budget, reorth, refine)
         h = ctypes.c_void_p()
         rc = self._lib.te_plan_create(ctypes.byref(A), K, krylov_steps, _prec(precision),
                                       ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h))
@@ -261,7 +278,8 @@ class Plan:
     def status(self):
         _check(self._lib.te_plan_status(self._h))
 
-    KINDS = ("spmv", "dot", "axpy_dot", "axpy_store", "restart", "jacobi", "ritz", "other")
+    KINDS = ("spmv", "dot", "axpy_dot", "axpy_store", "restart", "jacobi", "ritz", "other",
+             "refine")
 
     def profile(self, stream=None):
         """One un-graphed solve with CUDA events around every kernel:
@@ -302,12 +320,12 @@ def spmv(csr: CSR, x, precision="ddd", stream=None):
 
 
 def lanczos(csr: CSR, krylov_steps: int, precision="ddd", *, seed: int = 0, v1=None,
-            basis: bool = True, stream=None):
+            basis: bool = True, reorth="full", stream=None):
     """The Lanczos phase: returns (alpha [m], beta [m+1], V [n, m] or None, restarts)."""
     import torch
     lib = load_library()
     A = csr.to_ctypes()
-    opt = _options(seed, v1, "LM", False)
+    opt = _options(seed, v1, "LM", False, reorth=reorth)
     alpha = torch.empty(krylov_steps, dtype=torch.float64)
     beta = torch.empty(krylov_steps + 1, dtype=torch.float64)
     V = (torch.empty((krylov_steps, csr.n), dtype=torch.float64, device="cuda")
@@ -360,6 +378,20 @@ def spmv_layout(row_ptr, nnz: int):
     _check(rc)
     return {"slice_len": slen, "lane_out": lout, "lane_src": lsrc, "lane_len": llen,
             "entries": int(ne.value), "long_rows": int(nl.value)}
+
+
+def gram(U, stream=None):
+    """G = U^T U (float64, K x K numpy) of the columns of U ((n, K) view of a
+    contiguous (K, n) device tensor, or a (K, n) contiguous tensor of rows)."""
+    import numpy as np
+    lib = load_library()
+    base = U.t() if (U.dim() == 2 and not U.is_contiguous() and U.t().is_contiguous()) else U
+    K, n = base.shape
+    G = np.zeros((K, K))
+    rc = lib.te_gram(n, K, ctypes.c_void_p(base.data_ptr()), ctypes.c_void_p(G.ctypes.data),
+                     _stream_ptr(stream))
+    _check(rc)
+    return G
 
 
 def tridiag_eigs(alpha, beta, which="LM", stream=None):

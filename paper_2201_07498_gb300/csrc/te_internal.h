@@ -43,6 +43,7 @@ struct LzState {
   const double* v1;
   double* eigvecs;
   double* eigvals_out;
+  double* eigvecs_user;  // with refinement: the caller's buffer (eigvecs is the plan's)
 };
 
 struct LongRow {
@@ -74,7 +75,9 @@ struct SellHost {
   std::vector<LongRow> lrows;
   int64_t entries = 0;        // padded entries
   int64_t pieces = 0;         // partial sums of cut rows
+  int64_t nbig = 0;           // leading cut rows (most pieces first) summed by a whole warp
 };
+constexpr int SELL_BIG_PIECES = 16;  // cut rows with more pieces get a whole warp
 // returns false (and a message) if row_ptr is malformed
 bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err);
 
@@ -87,10 +90,13 @@ struct DevSell {
   void* vpart = nullptr;  // partial sums of cut rows (8 bytes each)
   const LongRow* lrows = nullptr;
   int nslices = 0, nlrows = 0;
+  int nlbig = 0;  // lrows[0, nlbig) have more than SELL_BIG_PIECES pieces
 };
 
 // fill cols/vals of the SELL layout from the CSR (one thread per lane)
-cudaError_t launch_sell_build(int prec, const int32_t* ci, const void* val,
+// in_type / out_type: TE_F64 or TE_F32 (te_dtype); binary64 -> binary32 rounds
+// to nearest even
+cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, const void* val,
                               const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
                               int nslices, int32_t* cols, void* vals, cudaStream_t s);
 cudaError_t spmv_prepare();  // once per process/device, outside stream capture
@@ -113,7 +119,9 @@ enum Finalize : int {
   FIN_STORE_RESTART = 4,
   FIN_STORE_INIT = 5,
   FIN_NONE = 6,
-  FIN_AXPYDOT_STEP = 7   // second-sweep coefficients and alpha = h1_i + h2_i
+  FIN_AXPYDOT_STEP = 7,  // second-sweep coefficients and alpha = h1_i + h2_i
+  FIN_DOT_NOREORTH = 8,  // alpha_i alone and the three-term coefficients
+  FIN_STORE_NOREORTH = 9 // beta_{i+1} of the three-term update (source scaled by s_i)
 };
 
 struct PassArgs {
@@ -121,7 +129,9 @@ struct PassArgs {
   void* Vmut;        // same buffer, for the column written by AXPY_STORE
   int64_t ld;        // padded rows
   int64_t n;         // true rows
-  int nb;            // basis columns read by this pass
+  int nb;            // basis columns read by this pass: col0 .. col0 + nb - 1
+  int col0;          // first basis column read (0 unless reorthogonalisation is off)
+  int exact_tail;    // FDF phase A: the last exact_tail columns in double-float
   int col_out;       // column written by AXPY_STORE
   int step;          // Lanczos step (0-based)
   int m;             // krylov steps of the solve
@@ -166,6 +176,22 @@ struct JacobiArgs {
 };
 cudaError_t jacobi_prepare();  // once per process/device, outside stream capture
 cudaError_t launch_jacobi(const JacobiArgs& a, cudaStream_t s);
+
+// ---- Rayleigh-quotient refinement and Gram matrix ----
+// For Ritz vector k (st->eigvecs + k*n) and y = M u_k (binary64): replaces
+// st->theta_sel[k] by the Rayleigh quotient theta + u'r/u'u (r = y - theta u)
+// and st->resid_est[k] by ||y - theta' u|| / ||u||; also writes
+// st->eigvals_out[k] when set.  `partials`: grid * 4 doubles.
+cudaError_t launch_refine(LzState* st, const double* y, int64_t n, int k, double* partials,
+                          int grid, cudaStream_t s);
+int refine_grid(int num_sms);
+// copy `count` doubles from src to st->eigvecs_user (no-op when it is NULL)
+cudaError_t launch_copy_out(LzState* st, const double* src, size_t count, int grid,
+                            cudaStream_t s);
+// G[a*K + b] = u_a . u_b (device), per-block partials in `partials`
+// (grid * K*(K+1)/2 doubles)
+cudaError_t launch_gram(const double* U, int64_t n, int K, double* partials, int grid,
+                        double* G, cudaStream_t s);
 
 // ---- small utilities ----
 // record the thread-local message returned by te_last_error()

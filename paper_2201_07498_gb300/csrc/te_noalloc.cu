@@ -216,6 +216,9 @@ extern "C" te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void
   if (p.values == TE_F64 && p.arithmetic == TE_F64 && p.vectors == TE_F64) prec = PREC_DDD;
   if (p.values == TE_F32 && p.arithmetic == TE_F64 && p.vectors == TE_F32) prec = PREC_FDF;
   if (prec < 0) return fail(TE_ERR_UNSUPPORTED, "te_spmv_noalloc: precision must be DDD or FDF");
+  if (A->values_f64 && prec != PREC_DDD)
+    return fail(TE_ERR_INVALID_ARG,
+                "te_spmv_noalloc: values must already have the precision's type (values_f64 = 0)");
   const int chunk = prec == PREC_DDD ? NaTr<PREC_DDD>::CHUNK : NaTr<PREC_FDF>::CHUNK;
   const int64_t nchunks = (A->nnz + chunk - 1) / chunk;
   if (nchunks > NOALLOC_MAX_CHUNKS)

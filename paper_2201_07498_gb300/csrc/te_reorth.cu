@@ -169,9 +169,12 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       for (int j = 0; j < a.nb; ++j) st->c2[j] = st->s[j] * st->s[j] * tot[j];
       break;
     }
-    case FIN_STORE_STEP: {
-      // tot[0] = ||w||^2, tot[1] = ||stored(w)||^2 (beta_{i+1} of Algorithm 1)
-      const double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
+    case FIN_STORE_STEP:
+    case FIN_STORE_NOREORTH: {
+      // tot[0] = ||w||^2, tot[1] = ||stored(w)||^2 (beta_{i+1} of Algorithm 1);
+      // without reorthogonalisation the pass formed w / s_i
+      double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
+      if (a.fin == FIN_STORE_NOREORTH) b *= st->s[i];
       const double ns = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);
       st->s[i + 1] = ns > 0.0 ? 1.0 / ns : 0.0;
       double cand = fabs(st->alpha[i]) + st->beta[i] + b;
@@ -181,6 +184,20 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       if (i + 1 < a.m && !(b > a.tol * st->anorm)) {
         st->restart_flag = 1;
         st->beta[i + 1] = 0.0;
+      }
+      break;
+    }
+    case FIN_DOT_NOREORTH: {
+      // tot[0] = stored_i . ytilde: alpha_i = v_i . M v_i.  The store pass then
+      // forms w / s_i = ytilde - alpha_i stored_i - (beta_i s_{i-1} / s_i) stored_{i-1}
+      const double si = st->s[i];
+      const double al = si * si * tot[0];
+      st->alpha[i] = al;
+      if (i > 0) {
+        st->c2[0] = st->beta[i] * st->s[i - 1] / si;
+        st->c2[1] = al;
+      } else {
+        st->c2[0] = al;
       }
       break;
     }
@@ -268,7 +285,7 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
   }
   __syncthreads();
 
-  const basis_t* Vg = static_cast<const basis_t*>(a.V);
+  const basis_t* Vg = static_cast<const basis_t*>(a.V) + (size_t)a.col0 * a.ld;
 
   // ------------------------- producer warp -------------------------
   if (wid == CONSUMERS / 32) {
@@ -350,8 +367,11 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
         // others sit at the basis' loss-of-orthogonality level, as do all
         // second-sweep coefficients, so binary32 products and sums of those
         // columns add an error far below the binary32 rounding of the stored
-        // result; the two large terms are taken exactly in double-float.
-        const int nsmall = (MODE == MODE_AXPY_DOT) ? (nb > 2 ? nb - 2 : 0) : nb;
+        // result.  The host marks the trailing columns whose coefficients can
+        // be large (exact_tail: 2 in the first sweep, all of them without
+        // reorthogonalisation and in restarts); those are taken exactly in
+        // double-float.
+        const int nsmall = nb > a.exact_tail ? nb - a.exact_tail : 0;
         float f[4] = {0.f, 0.f, 0.f, 0.f};
         int j = 0;
         for (; j + 4 <= nsmall; j += 4) {
@@ -417,7 +437,10 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
         if (jj >= nb) break;
         const basis_t* col = tv + (size_t)jj * TILE_R;
         if constexpr (P == PREC_FDF) {
-          if (MODE == MODE_DOT || jj < nb - 1) {
+          // (without reorthogonalisation the DOT pass's one dot is alpha_i
+          // itself, with no second sweep to correct it: exact)
+          if ((MODE == MODE_DOT && a.fin != FIN_DOT_NOREORTH) ||
+              (MODE == MODE_AXPY_DOT && jj < nb - 1)) {
             float c0 = 0.f, c1 = 0.f;
 #pragma unroll
             for (int rr = 0; rr < TILE_R / 32; rr += 2) {

@@ -65,8 +65,8 @@ bool is_device_ptr(const void* p) {
 
 struct Work {
   // byte offsets inside one allocation
-  size_t V = 0, ytil = 0, w = 0, partials = 0, st = 0, slices = 0, vout = 0, scols = 0,
-         svals = 0, lrows = 0, vpart = 0, flag = 0, total = 0;
+  size_t V = 0, ytil = 0, w = 0, partials = 0, st = 0, Uint = 0, slices = 0, vout = 0,
+         scols = 0, svals = 0, svals64 = 0, lrows = 0, vpart = 0, flag = 0, total = 0;
 };
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
@@ -76,7 +76,10 @@ struct SellSizes {
   size_t slices = 0, entries = 0, lrows = 0, pieces = 0;
 };
 
-Work layout(int prec, int64_t n_pad, int m, int grid, const SellSizes& z) {
+// refine: room for the plan's own Ritz vectors (n x K) and, for a
+// mixed-precision form, a binary64 copy of the SELL values
+Work layout(int prec, int64_t n_pad, int m, int grid, const SellSizes& z, bool refine = false,
+            int64_t n = 0, int K = 0) {
   Work w;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -89,10 +92,12 @@ Work layout(int prec, int64_t n_pad, int m, int grid, const SellSizes& z) {
   w.w = take((size_t)n_pad * 8);
   w.partials = take((size_t)grid * PSTRIDE * 8);
   w.st = take(sizeof(LzState));
+  w.Uint = refine ? take((size_t)n * (size_t)K * 8) : 0;
   w.slices = take(std::max<size_t>(z.slices, 1) * sizeof(SellSlice));
   w.vout = take(std::max<size_t>(z.slices, 1) * SELL_C * sizeof(int32_t));
   w.scols = take(std::max<size_t>(z.entries, 1) * sizeof(int32_t));
   w.svals = take(std::max<size_t>(z.entries, 1) * value_elt(prec));
+  w.svals64 = (refine && prec != PREC_DDD) ? take(std::max<size_t>(z.entries, 1) * 8) : 0;
   w.lrows = take(std::max<size_t>(z.lrows, 1) * sizeof(LongRow));
   w.vpart = take(std::max<size_t>(z.pieces, 1) * 8);
   w.flag = take(16);
@@ -111,6 +116,8 @@ te_status check_args(const te_csr* A, int32_t K, int32_t m, te_precision p) {
   if (A->row_scale) return fail(TE_ERR_UNSUPPORTED, "row_scale is reserved (must be NULL)");
   if (A->where != TE_DEVICE && A->where != TE_HOST)
     return fail(TE_ERR_INVALID_ARG, "where must be TE_DEVICE or TE_HOST");
+  if (A->values_f64 != 0 && A->values_f64 != 1)
+    return fail(TE_ERR_INVALID_ARG, "values_f64 must be 0 or 1");
   if (prec_of(p) < 0) return fail(TE_ERR_UNSUPPORTED, "precision must be DDD or FDF");
   if (K < 1) return fail(TE_ERR_INVALID_ARG, "K must be >= 1");
   if (m < K) return fail(TE_ERR_INVALID_ARG, "krylov_steps must be >= K");
@@ -141,6 +148,8 @@ struct te_plan {
   int prec = 0;
   int64_t n = 0, n_pad = 0, nnz = 0;
   int K = 0, m = 0;
+  int in_type = TE_F64;  // type of the caller's values (TE_F64 or the precision's)
+  bool refine = false, noreorth = false;
   te_options opt{};
   const int64_t* rp = nullptr;
   const int32_t* ci = nullptr;
@@ -148,6 +157,8 @@ struct te_plan {
   void* owned_csr = nullptr;
   int dev = 0, num_sms = 0;
   DevSell sell;
+  DevSell sell64;  // binary64 values for the refinement (same layout)
+  double* ubase = nullptr;  // with refinement: the plan's Ritz vectors (n x K)
   Work W;
   char* work = nullptr;
   LzState* st = nullptr;
@@ -176,8 +187,10 @@ namespace {
 void* at(te_plan* P, size_t off) { return P->work + off; }
 
 // Upload the SELL metadata and convert the (device) CSR into the SELL arrays.
-cudaError_t upload_sell(int prec, const SellHost& H, const int32_t* ci, const void* val,
-                        const DevSell& D, cudaStream_t s) {
+// in_type: the caller's value type; out_type: the layout's; D64 (optional): a
+// second value array receiving the binary64 values
+cudaError_t upload_sell(int in_type, int out_type, const SellHost& H, const int32_t* ci,
+                        const void* val, const DevSell& D, void* vals64, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (!H.slices.empty()) {
     e = cudaMemcpyAsync(const_cast<SellSlice*>(D.slices), H.slices.data(),
@@ -202,7 +215,11 @@ cudaError_t upload_sell(int prec, const SellHost& H, const int32_t* ci, const vo
     e = cudaMemcpyAsync(dlen, H.vlen.data(), H.vlen.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = launch_sell_build(prec, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols, D.vals, s);
+    e = launch_sell_build(in_type, out_type, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols,
+                          D.vals, s);
+  if (e == cudaSuccess && vals64)
+    e = launch_sell_build(TE_F64, TE_F64, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols,
+                          vals64, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (dsrc) cudaFree(dsrc);
   if (dlen) cudaFree(dlen);
@@ -302,23 +319,41 @@ cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
       if ((e = prof_end(P, s, TE_KIND_SPMV, bytes)) != cudaSuccess) return e;
     }
     PassArgs a = base_args(P);
-    a.nb = i + 1;
     a.step = i;
     a.xsrc = X_VEC;
     a.xvec = at(P, P->W.ytil);
-    a.fin = FIN_DOT_STEP;
-    if ((e = pass(P, MODE_DOT, a, s)) != cudaSuccess) return e;
-    a.wout = at(P, P->W.w);
-    a.fin = FIN_AXPYDOT_STEP;
-    if ((e = pass(P, MODE_AXPY_DOT, a, s)) != cudaSuccess) return e;
-    a.xvec = at(P, P->W.w);
-    a.col_out = i + 1;
-    a.fin = FIN_STORE_STEP;
-    if ((e = pass(P, MODE_AXPY_STORE, a, s)) != cudaSuccess) return e;
+    if (P->noreorth) {
+      // three-term recurrence only: alpha_i from v_i alone, then
+      // w / s_i = ytilde - alpha_i stored_i - (beta_i s_{i-1} / s_i) stored_{i-1}
+      a.col0 = i;
+      a.nb = 1;
+      a.fin = FIN_DOT_NOREORTH;
+      if ((e = pass(P, MODE_DOT, a, s)) != cudaSuccess) return e;
+      a.col0 = i > 0 ? i - 1 : 0;
+      a.nb = i > 0 ? 2 : 1;
+      a.exact_tail = a.nb;
+      a.col_out = i + 1;
+      a.fin = FIN_STORE_NOREORTH;
+      if ((e = pass(P, MODE_AXPY_STORE, a, s)) != cudaSuccess) return e;
+    } else {
+      a.nb = i + 1;
+      a.fin = FIN_DOT_STEP;
+      if ((e = pass(P, MODE_DOT, a, s)) != cudaSuccess) return e;
+      a.wout = at(P, P->W.w);
+      a.fin = FIN_AXPYDOT_STEP;
+      a.exact_tail = 2;  // alpha_i v_i and beta_i v_{i-1}
+      if ((e = pass(P, MODE_AXPY_DOT, a, s)) != cudaSuccess) return e;
+      a.xvec = at(P, P->W.w);
+      a.col_out = i + 1;
+      a.fin = FIN_STORE_STEP;
+      a.exact_tail = 0;  // second-sweep coefficients are all small
+      if ((e = pass(P, MODE_AXPY_STORE, a, s)) != cudaSuccess) return e;
+    }
     if (i + 1 < P->m) {
       // restart from a fresh random vector if this step broke down
       PassArgs r = base_args(P);
       r.nb = i + 1;
+      r.exact_tail = i + 1;  // a random vector: every coefficient may be large
       r.step = i;
       r.only_on_restart = 1;
       r.xsrc = X_RANDOM;
@@ -360,13 +395,38 @@ cudaError_t enqueue_solve(te_plan* P, cudaStream_t s) {
   PassArgs a = base_args(P);
   a.nb = P->m;
   a.fin = FIN_NONE;
-  return pass(P, MODE_RITZ, a, s);
+  if ((e = pass(P, MODE_RITZ, a, s)) != cudaSuccess) return e;
+  if (!P->refine) return cudaSuccess;
+  // binary64 Rayleigh-quotient refinement: y = M u_k, then the reduction
+  double* y = static_cast<double*>(at(P, P->W.ytil));
+  double* part = static_cast<double*>(at(P, P->W.partials));
+  const int rgrid = refine_grid(P->num_sms);
+  for (int k = 0; k < P->K; ++k) {
+    P->nkernels += 2 + (P->sell64.nlrows > 0 ? 1 : 0);
+    if ((e = prof_begin(P, s)) != cudaSuccess) return e;
+    e = launch_spmv(PREC_DDD, P->sell64, P->ubase + (size_t)k * P->n, y, true, s);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_refine(P->st, y, P->n, k, part, rgrid, s)) != cudaSuccess) return e;
+    const double n = (double)P->n, nnz = (double)P->nnz;
+    if ((e = prof_end(P, s, TE_KIND_REFINE, nnz * 12.0 + 8.0 * (n + 1.0) + 8.0 * n * 3.0)) !=
+        cudaSuccess)
+      return e;
+  }
+  // the refined vectors stay the Ritz vectors: hand them to the caller's buffer
+  P->nkernels++;
+  if ((e = prof_begin(P, s)) != cudaSuccess) return e;
+  if ((e = launch_copy_out(P->st, P->ubase, (size_t)P->n * P->K, rgrid * 4, s)) != cudaSuccess)
+    return e;
+  return prof_end(P, s, TE_KIND_REFINE, 16.0 * (double)P->n * P->K);
 }
 
 __global__ void solve_begin_kernel(LzState* st, const double* v1, double* eigvecs,
-                                   double* eigvals) {
+                                   double* eigvals, double* plan_vecs) {
   st->v1 = v1;
-  st->eigvecs = eigvecs;
+  // with refinement the Ritz vectors go to the plan's buffer (the refinement
+  // SpMVs read them at a fixed address) and are copied out at the end
+  st->eigvecs = plan_vecs ? plan_vecs : eigvecs;
+  st->eigvecs_user = plan_vecs ? eigvecs : nullptr;
   st->eigvals_out = eigvals;
   st->status = 0;
   st->restarts = 0;
@@ -377,7 +437,8 @@ __global__ void solve_begin_kernel(LzState* st, const double* v1, double* eigvec
 
 te_status plan_begin(te_plan* P, const double* v1, double* eigvecs_dev, double* eigvals_dev,
                      cudaStream_t s) {
-  solve_begin_kernel<<<1, 1, 0, s>>>(P->st, v1 ? v1 : P->opt.v1, eigvecs_dev, eigvals_dev);
+  solve_begin_kernel<<<1, 1, 0, s>>>(P->st, v1 ? v1 : P->opt.v1, eigvecs_dev, eigvals_dev,
+                                     P->refine ? P->ubase : nullptr);
   TE_CK(cudaGetLastError(), "solve_begin launch");
   return TE_OK;
 }
@@ -449,6 +510,13 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   else te_default_options(&opt);
   if (opt.which != TE_WHICH_LARGEST_MAGNITUDE && opt.which != TE_WHICH_LARGEST_ALGEBRAIC)
     return fail(TE_ERR_INVALID_ARG, "which must be TE_WHICH_*");
+  if (opt.reorth != TE_REORTH_FULL && opt.reorth != TE_REORTH_NONE)
+    return fail(TE_ERR_INVALID_ARG, "reorth must be TE_REORTH_FULL or TE_REORTH_NONE");
+  if (opt.refine != 0 && opt.refine != 1) return fail(TE_ERR_INVALID_ARG, "refine must be 0 or 1");
+  const int in_type = A->values_f64 ? TE_F64 : p.values;
+  if (opt.refine && in_type != TE_F64)
+    return fail(TE_ERR_INVALID_ARG,
+                "refinement needs the binary64 values (values_f64 = 1, or a binary64 form)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   if (prepare_kernels() != cudaSuccess) return cuda_fail(g_prep_err, "kernel set-up");
@@ -472,6 +540,9 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   P->K = K;
   P->m = krylov_steps;
   P->opt = opt;
+  P->in_type = in_type;
+  P->refine = opt.refine != 0;
+  P->noreorth = opt.reorth == TE_REORTH_NONE;
   TE_CK(cudaGetDevice(&P->dev), "cudaGetDevice");
   TE_CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev),
         "device attribute");
@@ -508,11 +579,12 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   zs.entries = (size_t)sell.entries;
   zs.lrows = sell.lrows.size();
   zs.pieces = (size_t)sell.pieces;
-  P->W = layout(P->prec, P->n_pad, P->m, grid, zs);
+  P->W = layout(P->prec, P->n_pad, P->m, grid, zs, P->refine, P->n, P->K);
+  const size_t in_elt = in_type == TE_F64 ? 8 : 4;
   size_t csr_bytes = 0;
   if (A->where == TE_HOST)
     csr_bytes = al256(sizeof(int64_t) * (A->n + 1)) + al256(sizeof(int32_t) * A->nnz) +
-                al256(value_elt(P->prec) * A->nnz);
+                al256(in_elt * A->nnz);
   if (opt.device_budget_bytes > 0 && P->W.total + csr_bytes > opt.device_budget_bytes)
     return fail(TE_ERR_OUT_OF_MEMORY, "work memory exceeds device_budget_bytes");
 
@@ -533,8 +605,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
       TE_CK(cudaMemcpyAsync(dci, A->col_idx, sizeof(int32_t) * A->nnz, cudaMemcpyHostToDevice,
                             s),
             "copy col_idx");
-      TE_CK(cudaMemcpyAsync(dval, A->values, value_elt(P->prec) * A->nnz,
-                            cudaMemcpyHostToDevice, s),
+      TE_CK(cudaMemcpyAsync(dval, A->values, in_elt * A->nnz, cudaMemcpyHostToDevice, s),
             "copy values");
     }
     P->rp = drp;
@@ -566,7 +637,16 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   P->sell.vpart = at(P, P->W.vpart);
   P->sell.nslices = (int)sell.slices.size();
   P->sell.nlrows = (int)sell.lrows.size();
-  TE_CK(upload_sell(P->prec, sell, P->ci, P->val, P->sell, s), "build the SELL layout");
+  P->sell.nlbig = (int)sell.nbig;
+  const int out_type = P->prec == PREC_DDD ? TE_F64 : TE_F32;
+  void* vals64 = P->W.svals64 ? at(P, P->W.svals64) : nullptr;
+  TE_CK(upload_sell(in_type, out_type, sell, P->ci, P->val, P->sell, vals64, s),
+        "build the SELL layout");
+  if (P->refine) {
+    P->sell64 = P->sell;
+    if (vals64) P->sell64.vals = vals64;
+    P->ubase = static_cast<double*>(at(P, P->W.Uint));
+  }
   if (P->owned_csr) {  // the solve reads only the SELL copy
     cudaFree(P->owned_csr);
     P->owned_csr = nullptr;
@@ -769,6 +849,7 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
   int* flag = reinterpret_cast<int*>(buf + off);
   D.nslices = (int)sell.slices.size();
   D.nlrows = (int)sell.lrows.size();
+  D.nlbig = (int)sell.nbig;
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
   if (e == cudaSuccess) e = launch_validate_cols(A->col_idx, A->nnz, A->n, flag, s);
   int hflag = 0;
@@ -779,7 +860,10 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
     cudaFree(buf);
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
   }
-  if (e == cudaSuccess) e = upload_sell(prec, sell, A->col_idx, A->values, D, s);
+  const int in_type = A->values_f64 ? TE_F64 : p.values;
+  const int out_type = prec == PREC_DDD ? TE_F64 : TE_F32;
+  if (e == cudaSuccess)
+    e = upload_sell(in_type, out_type, sell, A->col_idx, A->values, D, nullptr, s);
   // the kernel writes rows with entries only
   if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, sizeof(double) * A->n, s);
   if (e == cudaSuccess) e = launch_spmv(prec, D, x, y, true, s);
@@ -865,6 +949,27 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
   if (e != cudaSuccess) return cuda_fail(e, "te_tridiag_eigs");
   if (sweeps) *sweeps = h[0];
   if (h[1] != 0) return fail((te_status)h[1], "Jacobi sweeps did not converge");
+  return TE_OK;
+}
+
+te_status te_gram(int64_t n, int32_t K, const double* U, double* G, void* stream) {
+  if (n < 1 || K < 1 || K > MAX_M) return fail(TE_ERR_INVALID_ARG, "need n >= 1, 1 <= K <= 64");
+  if (!U || !G) return fail(TE_ERR_INVALID_ARG, "NULL argument");
+  if (!is_device_ptr(U)) return fail(TE_ERR_INVALID_ARG, "U must be device memory");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  TE_CK(cudaGetDevice(&dev), "cudaGetDevice");
+  TE_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  const int grid = sms * 2;
+  const size_t np = (size_t)K * (K + 1) / 2;
+  double* buf = nullptr;
+  TE_CK(cudaMalloc(&buf, sizeof(double) * (np * grid + (size_t)K * K)), "allocate Gram work");
+  cudaError_t e = launch_gram(U, n, K, buf, grid, buf + np * grid, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G, buf + np * grid, sizeof(double) * K * K, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "te_gram");
   return TE_OK;
 }
 

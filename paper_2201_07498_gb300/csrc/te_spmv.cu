@@ -104,6 +104,12 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
       out.entries += (int64_t)SELL_C * sl.len;
     }
   }
+  // cut rows with the most pieces first (their finalising lanes run longest)
+  std::stable_sort(out.lrows.begin(), out.lrows.end(),
+                   [](const LongRow& a, const LongRow& b) { return a.count > b.count; });
+  out.nbig = 0;
+  while (out.nbig < (int64_t)out.lrows.size() && out.lrows[out.nbig].count > SELL_BIG_PIECES)
+    ++out.nbig;
   return true;
 }
 
@@ -111,10 +117,17 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
 // layout conversion: one thread per lane, entries k = 0..len-1 (padding:
 // column 0, value 0)
 // ---------------------------------------------------------------------------
-template <typename V>
-__global__ void sell_build_kernel(const int32_t* ci, const V* val, const SellSlice* slices,
+// Vin -> Vout: binary64 -> binary32 rounds to nearest even (__double2float_rn)
+template <typename Vin, typename Vout>
+TE_DEV Vout convert_value(Vin v) {
+  if constexpr (sizeof(Vin) == 8 && sizeof(Vout) == 4) return __double2float_rn(v);
+  else return (Vout)v;
+}
+
+template <typename Vin, typename Vout>
+__global__ void sell_build_kernel(const int32_t* ci, const Vin* val, const SellSlice* slices,
                                   const int64_t* vsrc, const int32_t* vlen, int nslices,
-                                  int32_t* cols, V* vals) {
+                                  int32_t* cols, Vout* vals) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)nslices * SELL_C) return;
   const int64_t s = t / SELL_C;
@@ -126,28 +139,34 @@ __global__ void sell_build_kernel(const int32_t* ci, const V* val, const SellSli
     const int64_t dst = sl.base + (int64_t)k * SELL_C + lane;
     if (k < len) {
       cols[dst] = ci[src + k];
-      vals[dst] = val[src + k];
+      vals[dst] = convert_value<Vin, Vout>(val[src + k]);
     } else {
       cols[dst] = 0;
-      vals[dst] = (V)0;
+      vals[dst] = (Vout)0;
     }
   }
 }
 
-cudaError_t launch_sell_build(int prec, const int32_t* ci, const void* val,
+cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, const void* val,
                               const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
                               int nslices, int32_t* cols, void* vals, cudaStream_t s) {
   if (nslices <= 0) return cudaSuccess;
   const int64_t lanes = (int64_t)nslices * SELL_C;
   const unsigned blocks = (unsigned)((lanes + 255) / 256);
-  if (prec == PREC_DDD)
-    sell_build_kernel<double><<<blocks, 256, 0, s>>>(ci, static_cast<const double*>(val), slices,
-                                                     vsrc, vlen, nslices, cols,
-                                                     static_cast<double*>(vals));
+  if (in_type == TE_F64 && out_type == TE_F64)
+    sell_build_kernel<double, double><<<blocks, 256, 0, s>>>(
+        ci, static_cast<const double*>(val), slices, vsrc, vlen, nslices, cols,
+        static_cast<double*>(vals));
+  else if (in_type == TE_F64 && out_type == TE_F32)
+    sell_build_kernel<double, float><<<blocks, 256, 0, s>>>(
+        ci, static_cast<const double*>(val), slices, vsrc, vlen, nslices, cols,
+        static_cast<float*>(vals));
+  else if (in_type == TE_F32 && out_type == TE_F32)
+    sell_build_kernel<float, float><<<blocks, 256, 0, s>>>(
+        ci, static_cast<const float*>(val), slices, vsrc, vlen, nslices, cols,
+        static_cast<float*>(vals));
   else
-    sell_build_kernel<float><<<blocks, 256, 0, s>>>(ci, static_cast<const float*>(val), slices,
-                                                    vsrc, vlen, nslices, cols,
-                                                    static_cast<float*>(vals));
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -263,16 +282,25 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
   }
 }
 
-// one warp per cut row: sum its piece partials in order of a fixed tree
+// Cut rows: the first nbig rows (most pieces first) get a whole warp each,
+// the others FIN_G lanes each (most cut rows have a handful of pieces).
+// Each lane sums a strided subset of the row's piece partials, then a fixed
+// shuffle tree adds the lanes (deterministic).
+constexpr int FIN_G = 4;
 template <int P, bool F64OUT>
-__global__ void spmv_long_finalize(const LongRow* lrows, int nl, const void* vpart, void* y) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= nl) return;
-  LongRow lr = lrows[w];
+__global__ void spmv_long_finalize(const LongRow* lrows, int nl, int nbig, int big_blocks,
+                                   const void* vpart, void* y) {
+  const bool big = (int)blockIdx.x < big_blocks;  // uniform per block
+  const int G = big ? 32 : FIN_G;
+  const int64_t t = (int64_t)(big ? blockIdx.x : blockIdx.x - big_blocks) * blockDim.x + threadIdx.x;
+  const int64_t g = (big ? 0 : nbig) + t / G;
+  const int sub = threadIdx.x & (G - 1);
+  const bool live = big ? (g < nbig) : (g < nl);  // every lane reaches the shuffles below
+  LongRow lr{0, 0, 0, 0};
+  if (live) lr = lrows[g];
   typename SpmvTr<P>::acc_t acc;
   acc_zero<P>(acc);
-  for (int c = lane; c < lr.count; c += 32) {
+  for (int c = sub; c < lr.count; c += G) {
     if constexpr (P == PREC_FDF) {
       float2 v = static_cast<const float2*>(vpart)[lr.first + c];
       dacc_add_pair(acc, v.x, v.y);
@@ -280,8 +308,8 @@ __global__ void spmv_long_finalize(const LongRow* lrows, int nl, const void* vpa
       acc += static_cast<const double*>(vpart)[lr.first + c];
     }
   }
-  acc = warp_sum(acc);
-  if (lane == 0) store_row<P, F64OUT>(y, lr.row, acc);
+  acc = group_sum(acc, G);
+  if (live && sub == 0) store_row<P, F64OUT>(y, lr.row, acc);
 }
 
 template <int P, bool F64OUT>
@@ -290,8 +318,11 @@ static cudaError_t launch_spmv_t(const SpmvArgs& a, const DevSell& S, cudaStream
     spmv_kernel<P, F64OUT><<<(S.nslices + SPMV_WPB - 1) / SPMV_WPB, 32 * SPMV_WPB, 0, s>>>(a);
   if (S.nlrows > 0) {
     const int threads = 256;
-    const int blocks = (S.nlrows * 32 + threads - 1) / threads;
-    spmv_long_finalize<P, F64OUT><<<blocks, threads, 0, s>>>(S.lrows, S.nlrows, S.vpart, a.y);
+    const int big_blocks = (int)(((int64_t)S.nlbig * 32 + threads - 1) / threads);
+    const int small_blocks =
+        (int)(((int64_t)(S.nlrows - S.nlbig) * FIN_G + threads - 1) / threads);
+    spmv_long_finalize<P, F64OUT><<<big_blocks + small_blocks, threads, 0, s>>>(
+        S.lrows, S.nlrows, S.nlbig, big_blocks, S.vpart, a.y);
   }
   return cudaGetLastError();
 }

@@ -83,6 +83,36 @@ def test_argument_validation_before_gpu(te, K, m, prec, expect):
     assert lib.te_last_error() != b""
 
 
+def test_option_validation_before_gpu(te):
+    """New options are checked before any device work: refinement needs the
+    binary64 values, reorth and refine take their documented values only."""
+    lib = te.load_library()
+    ev = np.zeros(4)
+    A, keep = _desc(10, 0)
+
+    def call(A, **kw):
+        o = te.te_options()
+        lib.te_default_options(ctypes.byref(o))
+        assert o.reorth == 0 and o.refine == 0
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return lib.te_topk_eigs(ctypes.byref(A), 2, 4, te._prec("fdf"), ctypes.byref(o),
+                                ctypes.c_void_p(ev.ctypes.data), None, None, None)
+
+    assert call(A, refine=1) == 1 and b"binary64" in lib.te_last_error()
+    assert call(A, reorth=2) == 1
+    assert call(A, refine=3) == 1
+    A.values_f64 = 2
+    assert call(A) == 1
+    A.values_f64 = 1
+    # noalloc cannot round values (rejected before the pointers are used)
+    B, keep2 = _desc(10, 0, where=0)
+    B.values_f64 = 1
+    assert lib.te_spmv_noalloc(ctypes.byref(B), te._prec("fdf"), ctypes.c_void_p(ev.ctypes.data),
+                               ctypes.c_void_p(ev.ctypes.data), None) == 1
+    assert b"values_f64" in lib.te_last_error()
+
+
 def test_null_and_reserved_arguments(te):
     lib = te.load_library()
     ev = np.zeros(4)
