@@ -47,6 +47,7 @@ FAULTS = {
     "refine_no_norm": 9,
     "angle_signed": 10,
     "reorth_ignored": 11,
+    "ties_away": 12,
 }
 
 
@@ -100,6 +101,12 @@ def _load():
         lib.oracle_refine.restype = None
         lib.oracle_mean_pairwise_angle.argtypes = [i64, i32, vp]
         lib.oracle_mean_pairwise_angle.restype = dbl
+        lib.oracle_round_bf16.argtypes = [i64, vp, vp, vp]
+        lib.oracle_round_bf16.restype = None
+        lib.oracle_quantize_e4m3_rows.argtypes = [i64, vp, vp, vp, vp, vp]
+        lib.oracle_quantize_e4m3_rows.restype = None
+        lib.oracle_e4m3_value.argtypes = [ctypes.c_uint8]
+        lib.oracle_e4m3_value.restype = dbl
         _lib = lib
         return lib
 
@@ -234,6 +241,30 @@ def refine(csr, U):
     res = np.empty(K)
     _load().oracle_refine(n, _p(rp), _p(ci), _p(val), K, _p(Uc), _p(th), _p(res))
     return th, res
+
+
+def round_bf16(x):
+    """bfloat16 rounding (nearest, ties to even): (codes uint16, values float64)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    codes = np.empty(x.shape, dtype=np.uint16)
+    deq = np.empty(x.shape)
+    _load().oracle_round_bf16(x.size, _p(x), _p(codes), _p(deq))
+    return codes, deq
+
+
+def quantize_e4m3_rows(csr):
+    """FP8 E4M3 with one binary32 scale per row: (codes uint8 [nnz],
+    scales float32 [n], dequantised values float64 [nnz])."""
+    n, rp, ci, val = _csr_arrays(csr)
+    codes = np.empty(len(val), dtype=np.uint8)
+    scale = np.empty(n, dtype=np.float32)
+    deq = np.empty(len(val))
+    _load().oracle_quantize_e4m3_rows(n, _p(rp), _p(val), _p(codes), _p(scale), _p(deq))
+    return codes, scale, deq
+
+
+def e4m3_value(code: int) -> float:
+    return float(_load().oracle_e4m3_value(code))
 
 
 def mean_pairwise_angle(U) -> float:

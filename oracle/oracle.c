@@ -21,6 +21,8 @@
  *   - oracle_refine:      Rayleigh quotient u'Mu/u'u and residual of given
  *                         vectors (definition).
  *   - oracle_mean_pairwise_angle: the orthogonality metric of Section IV-D.
+ *   - oracle_round_bf16, oracle_quantize_e4m3_rows: the reduced-precision
+ *                         matrix values of the mixed forms (Section III-A).
  *
  * Readings where the paper is silent or garbled (listed with reasons in the
  * design notes of the repository):
@@ -355,6 +357,78 @@ double oracle_mean_pairwise_angle(int64_t n, int32_t K, const double* U) {
     }
   }
   return sum / (double)pairs;
+}
+
+/* ---------------- rounding to the storage types ---------------- */
+/* Round |x| > 0 to p significant bits, with the quantum never below 2^qmin
+   (gradual underflow): x = f * 2^e with f in [0.5, 1); the quantum is
+   2^(e - p), clamped; keep floor(|x| / quantum) and round up when the rest
+   exceeds a half, or equals a half and the kept integer is odd. */
+static double om_round_sig(double ax, int p, int qmin) {
+  int e;
+  (void)frexp(ax, &e);
+  int qe = e - p;
+  if (qe < qmin) qe = qmin;
+  const double quantum = ldexp(1.0, qe);
+  const double t = ax / quantum; /* exact: a power-of-two scaling */
+  double f = floor(t);
+  const double rest = t - f;     /* exact */
+  const int up_on_tie = g_fault == ORACLE_FAULT_TIES_AWAY ? 1 : (fmod(f, 2.0) != 0.0);
+  if (rest > 0.5 || (rest == 0.5 && up_on_tie)) f += 1.0;
+  return f * quantum;
+}
+
+void oracle_round_bf16(int64_t count, const double* x, uint16_t* codes, double* deq) {
+  for (int64_t i = 0; i < count; ++i) {
+    const double ax = fabs(x[i]);
+    double r = ax > 0.0 ? om_round_sig(ax, 8, -133) : 0.0;
+    if (r != 0.0 && x[i] < 0.0) r = -r;
+    float f = (float)r; /* exact: r has at most 8 significant bits */
+    uint32_t bits;
+    memcpy(&bits, &f, 4);
+    if (r == 0.0) bits = 0;
+    if (codes) codes[i] = (uint16_t)(bits >> 16);
+    if (deq) deq[i] = r;
+  }
+}
+
+double oracle_e4m3_value(uint8_t code) {
+  const int e = (code >> 3) & 15, m = code & 7;
+  double v = e == 0 ? ldexp((double)m, -9) : ldexp(1.0 + m / 8.0, e - 7);
+  return (code & 0x80) ? -v : v;
+}
+
+static uint8_t om_e4m3_code(double x) {
+  const double ax = fabs(x);
+  double r = ax > 0.0 ? om_round_sig(ax, 4, -9) : 0.0;
+  if (r > 448.0) r = 448.0;
+  if (r == 0.0) return 0;
+  int e;
+  double f = frexp(r, &e); /* r = f 2^e, f in [0.5, 1) */
+  uint8_t code;
+  if (e - 1 < -6) {
+    code = (uint8_t)(r / ldexp(1.0, -9)); /* subnormal: m * 2^-9 */
+  } else {
+    const int m = (int)(f * 16.0) - 8; /* 1.mmm = 2f */
+    code = (uint8_t)(((e - 1 + 7) << 3) | m);
+  }
+  return (uint8_t)(x < 0.0 ? (code | 0x80) : code);
+}
+
+void oracle_quantize_e4m3_rows(int64_t n, const int64_t* rp, const double* val,
+                               uint8_t* codes, float* scale, double* deq) {
+  for (int64_t r = 0; r < n; ++r) {
+    double mx = 0.0;
+    for (int64_t k = rp[r]; k < rp[r + 1]; ++k)
+      if (fabs(val[k]) > mx) mx = fabs(val[k]);
+    const float s = mx > 0.0 ? (float)(mx / 448.0) : 1.0f;
+    if (scale) scale[r] = s;
+    for (int64_t k = rp[r]; k < rp[r + 1]; ++k) {
+      const uint8_t c = om_e4m3_code(val[k] / (double)s);
+      if (codes) codes[k] = c;
+      if (deq) deq[k] = (double)s * oracle_e4m3_value(c);
+    }
+  }
 }
 
 /* ---------------- the whole pipeline ---------------- */

@@ -35,6 +35,7 @@ extern "C" {
 #define ORACLE_FAULT_REFINE_NO_NORM 9     /* Rayleigh quotient without the 1/u'u */
 #define ORACLE_FAULT_ANGLE_SIGNED 10      /* angle metric without the absolute value */
 #define ORACLE_FAULT_REORTH_IGNORED 11    /* reorth = 0 still reorthogonalises */
+#define ORACLE_FAULT_TIES_AWAY 12         /* rounding ties away from zero, not to even */
 
 void oracle_set_fault(int kind);
 int oracle_get_fault(void);
@@ -74,6 +75,21 @@ void oracle_refine(int64_t n, const int64_t* rp, const int32_t* ci, const double
    taken sign-free: acos(|u_a . u_b| / (||u_a|| ||u_b||)) (the orthogonality
    metric of Section IV-D; 90 for an orthogonal set).  K >= 2. */
 double oracle_mean_pairwise_angle(int64_t n, int32_t K, const double* U);
+
+/* Rounding of matrix values to the storage types of the mixed forms
+   (Section III-A; readings: round to nearest, ties to even, from the
+   binary64 value directly; a zero result is +0).
+   oracle_round_bf16: bfloat16 (8 significant bits, binary32 exponent range);
+     codes[i] = the 16-bit pattern, deq[i] = its value.
+   oracle_quantize_e4m3_rows: FP8 E4M3 (4 significant bits, bias 7, largest
+     finite 448, no infinities) with one binary32 scale per row,
+     scale_r = (binary32) (max_j |a_rj| / 448) (1 for an all-zero row);
+     code = round(a / scale_r), saturated to +-448; deq = scale_r * code.
+   Values are finite with |a| < 2^127. */
+void oracle_round_bf16(int64_t count, const double* x, uint16_t* codes, double* deq);
+void oracle_quantize_e4m3_rows(int64_t n, const int64_t* rp, const double* val,
+                               uint8_t* codes, float* scale, double* deq);
+double oracle_e4m3_value(uint8_t code);
 
 /* cyclic-by-row Jacobi: T (m x m, symmetric, row-major) is diagonalised in
    place, Y receives the eigenvectors (columns).  Returns 0 if converged. */

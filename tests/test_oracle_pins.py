@@ -326,11 +326,126 @@ def pin_pairwise_angle():
     return None
 
 
+def _bf16_table():
+    """Every finite non-negative bfloat16 value, by code (brute force)."""
+    codes = np.arange(0, 0x7F80, dtype=np.uint32)
+    return codes, (codes << 16).view(np.float32).astype(np.float64)
+
+
+def _e4m3_table():
+    """Every finite non-negative E4M3 value, by code, from the format's
+    definition: exponent field e (bias 7), 3 fraction bits m; e = 0 is
+    subnormal m 2^-9; code 0x7F is NaN."""
+    vals = []
+    for c in range(0x7F):
+        e, m = c >> 3, c & 7
+        vals.append(m * 2.0 ** -9 if e == 0 else (1 + m / 8) * 2.0 ** (e - 7))
+    return np.arange(0x7F), np.array(vals)
+
+
+def _check_nearest_even(x, got_codes, got_vals, codes, table, sat=None):
+    """got_vals is the nearest table value to |x| (ties: even code), with
+    saturation at `sat`; got_codes carry the sign bit of x (zero is +0)."""
+    ax = np.abs(x)
+    if sat is not None:
+        ax = np.minimum(ax, sat)
+    j = np.clip(np.searchsorted(table, ax), 1, len(table) - 1)
+    lo, hi = table[j - 1], table[j]
+    pick = np.where(ax - lo < hi - ax, j - 1, j)
+    tie = (ax - lo) == (hi - ax)
+    pick = np.where(tie, np.where(codes[j - 1] % 2 == 0, j - 1, j), pick)
+    want = table[pick]
+    if not np.array_equal(np.abs(got_vals), want):
+        k = int(np.argmax(np.abs(got_vals) != want))
+        return f"x={x[k]!r}: got {got_vals[k]!r}, nearest-even {want[k]!r}"
+    return None
+
+
+def pin_round_bf16_bruteforce():
+    """bfloat16 rounding against the nearest of all 32640 finite magnitudes,
+    ties to the even code, including exact midpoints and subnormals."""
+    codes, table = _bf16_table()
+    rng = np.random.default_rng(12)
+    x = np.exp2(rng.uniform(-140, 120, 20000)) * rng.choice([-1.0, 1.0], 20000)
+    mids = (table[1:2000:7] + table[2:2001:7]) / 2          # exact midpoints (subnormal)
+    mids2 = (table[16000:16400] + table[16001:16401]) / 2   # exact midpoints (normal)
+    x = np.concatenate([x, mids, -mids2, mids2, [0.0, -0.0, 1.0, -2.5]])
+    got_codes, got = oracle.round_bf16(x)
+    msg = _check_nearest_even(x, got_codes, got, codes, table)
+    if msg:
+        return "bf16 " + msg
+    want_sign = (x < 0) & (got != 0)
+    if not np.array_equal((got_codes >> 15).astype(bool), want_sign):
+        return "bf16 sign bit"
+    # the code is the upper half of the binary32 pattern of the value
+    if not np.array_equal(((got_codes.astype(np.uint32) << 16).view(np.float32)).astype(float), got):
+        return "bf16 code/value mismatch"
+    return None
+
+
+def pin_e4m3_bruteforce():
+    """E4M3 rounding at scale 1 (each value shares its row with 448, which
+    fixes the scale at 1) against the nearest of all 127 finite magnitudes,
+    ties to even; the code table decodes as the format defines.  (With the
+    row scale max|a|/448 a scaled value never exceeds 448 (1 + 2^-24), so the
+    saturation at 448 cannot be reached from a row.)"""
+    codes, table = _e4m3_table()
+    for c in range(0x7F):
+        if oracle.e4m3_value(c) != table[c] or oracle.e4m3_value(c | 0x80) != -table[c]:
+            return f"decode {c:#x}"
+    rng = np.random.default_rng(13)
+    x = np.concatenate([rng.uniform(-448, 448, 4000),
+                        np.exp2(rng.uniform(-12, 8.8, 4000)) * rng.choice([-1.0, 1.0], 4000),
+                        (table[:-1] + table[1:]) / 2, [0.0, 448.0, -448.0, 447.9]])
+    n = len(x)
+    # one row per value, each row padded with +-448 so that its scale is exactly 1
+    rp = np.arange(0, 2 * n + 1, 2, dtype=np.int64)
+    val = np.empty(2 * n)
+    val[0::2] = x
+    val[1::2] = 448.0
+    col = np.zeros(2 * n, dtype=np.int32)
+    col[1::2] = 1
+    A = synth.CSR(n, rp, col, val)
+    got_codes, scale, deq = oracle.quantize_e4m3_rows(A)
+    if not np.all(scale == 1.0):
+        return "scale of a row whose largest value is 448"
+    msg = _check_nearest_even(x, got_codes[0::2], deq[0::2], codes, table, sat=448.0)
+    if msg:
+        return "e4m3 " + msg
+    return None
+
+
+def pin_e4m3_row_scales():
+    """Per-row scales: binary32(max |a| / 448), 1 for an empty or all-zero
+    row; each dequantised value is scale * code value exactly, and a row's
+    largest entry maps to the largest code."""
+    A = synth.rmat_sym(10, 8, 3)
+    val = A.val.copy()
+    val[A.row_ptr[7]:A.row_ptr[8]] = 0.0  # an all-zero row
+    B = synth.CSR(A.n, A.row_ptr, A.col, val * 3.7)
+    codes, scale, deq = oracle.quantize_e4m3_rows(B)
+    _, table = _e4m3_table()
+    for r in range(B.n):
+        a, b = B.row_ptr[r], B.row_ptr[r + 1]
+        mx = np.max(np.abs(B.val[a:b])) if b > a else 0.0
+        want = np.float32(mx / 448.0) if mx > 0 else np.float32(1.0)
+        if scale[r] != want:
+            return f"scale of row {r}"
+        if b > a:
+            dv = np.array([oracle.e4m3_value(int(c)) for c in codes[a:b]])
+            if not np.array_equal(deq[a:b], float(scale[r]) * dv):
+                return f"dequantised values of row {r}"
+            if mx > 0 and np.max(np.abs(dv)) != 448.0:
+                return f"row {r} max code"
+    return None
+
+
 PINS = [pin_spmv_brute_force, pin_hand_examples, pin_jacobi_toeplitz, pin_jacobi_2x2,
         pin_jacobi_random, pin_lanczos_path_full, pin_lanczos_cycle_full,
         pin_lanczos_diagonal_trace, pin_lanczos_dense_bruteforce,
         pin_lanczos_partial_invariants, pin_selection, pin_ritz_vectors,
-        pin_lanczos_without_reorth, pin_refine_closed_form, pin_pairwise_angle]
+        pin_lanczos_without_reorth, pin_refine_closed_form, pin_pairwise_angle,
+        pin_round_bf16_bruteforce, pin_e4m3_bruteforce, pin_e4m3_row_scales]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
