@@ -61,7 +61,13 @@ typedef enum { TE_F64 = 0, TE_F32 = 1, TE_BF16 = 2, TE_FP8_E4M3 = 3 } te_dtype;
  *         vectors; every product and sum of the SpMV, the
  *         reorthogonalisation and the Ritz contraction is carried in
  *         double-float (about 48 significant bits) on the FP32 pipes, and
- *         cross-block sums in binary64. */
+ *         cross-block sums in binary64.
+ *   BDF = {TE_BF16, TE_F64, TE_F32}: as FDF with bfloat16 matrix values.
+ *   8DF = {TE_FP8_E4M3, TE_F64, TE_F32}: as FDF with FP8 E4M3 matrix values
+ *         and one binary32 scale per row (scale_r = max_j |a_rj| / 448).
+ *   BDF and 8DF are built from binary64 values (te_csr.values_f64 = 1); the
+ *   library rounds them (see te_quantize).  With te_options.refine the
+ *   selected Ritz values are refined against the binary64 values. */
 typedef struct {
   int32_t values;
   int32_t arithmetic;
@@ -231,6 +237,21 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
  * elements of type p.vectors; y receives n doubles.  Synchronises `stream`. */
 te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void* x, double* y,
                           void* stream);
+
+/* Round binary64 CSR values (A: TE_DEVICE, values_f64 = 1) to a storage type,
+ * on the device, in CSR order, as the plans do (Section III-A's reduced
+ * precisions): round to nearest, ties to even, from the binary64 value
+ * directly; a zero result is +0.
+ *   to = TE_F32:      out = nnz floats.
+ *   to = TE_BF16:     out = nnz uint16 bfloat16 codes (8 significant bits).
+ *   to = TE_FP8_E4M3: out = nnz uint8 E4M3 codes (bias 7, largest finite 448,
+ *                     no infinities) and row_scale = n floats:
+ *                     scale_r = binary32(max_j |a_rj| / 448), 1 for an
+ *                     all-zero row; code = round(a / scale_r) saturated at 448;
+ *                     the stored matrix entry is scale_r * value(code).
+ * row_scale must be given for TE_FP8_E4M3 and only then.  Values must be
+ * finite with magnitude below 2^127.  Synchronises `stream`. */
+te_status te_quantize(const te_csr* A, int32_t to, void* out, float* row_scale, void* stream);
 
 /* Gram matrix G = U^T U of K vectors (U: n x K, column-major, device), summed
  * in binary64 in a fixed order; G (K x K, row-major) is written to host memory.

@@ -19,13 +19,14 @@ from dataclasses import dataclass
 from . import _build
 
 __all__ = ["CSR", "Plan", "TEError", "topk_eigs", "spmv", "lanczos", "tridiag_eigs",
-           "spmv_layout", "gram", "library_path", "load_library", "PRECISIONS"]
+           "spmv_layout", "gram", "quantize", "library_path", "load_library", "PRECISIONS"]
 
 TE_F64, TE_F32, TE_BF16, TE_FP8_E4M3 = 0, 1, 2, 3
 TE_DEVICE, TE_HOST = 0, 1
 WHICH = {"LM": 0, "LA": 1}
 REORTH = {"full": 0, "none": 1}
-PRECISIONS = {"ddd": (TE_F64, TE_F64, TE_F64), "fdf": (TE_F32, TE_F64, TE_F32)}
+PRECISIONS = {"ddd": (TE_F64, TE_F64, TE_F64), "fdf": (TE_F32, TE_F64, TE_F32),
+              "bdf": (TE_BF16, TE_F64, TE_F32), "8df": (TE_FP8_E4M3, TE_F64, TE_F32)}
 STATUS = {0: "TE_OK", 1: "TE_ERR_INVALID_ARG", 2: "TE_ERR_OUT_OF_MEMORY", 3: "TE_ERR_CUDA",
           4: "TE_ERR_BREAKDOWN", 5: "TE_ERR_NOT_CONVERGED", 6: "TE_ERR_TIMEOUT",
           7: "TE_ERR_UNSUPPORTED"}
@@ -87,6 +88,8 @@ _SIGS = {
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "te_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "te_quantize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
     "te_gram": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p]),
     "te_spmv_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -180,7 +183,10 @@ class CSR:
         them; needed for refinement)."""
         import numpy as np
         import torch
-        vdt = np.float32 if (_prec(precision).values == TE_F32 and not values_f64) else np.float64
+        pv = _prec(precision).values
+        if pv in (TE_BF16, TE_FP8_E4M3):
+            values_f64 = True  # the library quantises binary64 values itself
+        vdt = np.float32 if (pv == TE_F32 and not values_f64) else np.float64
         rp = torch.from_numpy(np.ascontiguousarray(host_csr.row_ptr, dtype=np.int64))
         ci = torch.from_numpy(np.ascontiguousarray(host_csr.col, dtype=np.int32))
         va = torch.from_numpy(np.ascontiguousarray(host_csr.val, dtype=vdt))
@@ -378,6 +384,25 @@ def spmv_layout(row_ptr, nnz: int):
     _check(rc)
     return {"slice_len": slen, "lane_out": lout, "lane_src": lsrc, "lane_len": llen,
             "entries": int(ne.value), "long_rows": int(nl.value)}
+
+
+def quantize(csr: CSR, to: str, stream=None):
+    """Round the binary64 values of a device CSR (values_f64) to "f32", "bf16"
+    (uint16 codes) or "e4m3" (uint8 codes + float32 row scales), in CSR order,
+    with the plans' device rounding.  Returns (out, row_scale or None)."""
+    import torch
+    lib = load_library()
+    kinds = {"f32": (TE_F32, torch.float32), "bf16": (TE_BF16, torch.int16),
+             "e4m3": (TE_FP8_E4M3, torch.uint8)}
+    code, dt = kinds[to]
+    out = torch.empty(max(csr.nnz, 1), dtype=dt, device="cuda")
+    scale = torch.empty(csr.n, dtype=torch.float32, device="cuda") if to == "e4m3" else None
+    A = csr.to_ctypes()
+    rc = lib.te_quantize(ctypes.byref(A), code, ctypes.c_void_p(out.data_ptr()),
+                         None if scale is None else ctypes.c_void_p(scale.data_ptr()),
+                         _stream_ptr(stream))
+    _check(rc)
+    return out[:csr.nnz], scale
 
 
 def gram(U, stream=None):

@@ -188,6 +188,27 @@ TE_DEV float ld_stream_f32(const float* a, uint64_t pol) {
                : "=f"(v) : "l"(a), "l"(pol));
   return v;
 }
+TE_DEV uint32_t ld_stream_u16(const uint16_t* a, uint64_t pol) {
+  unsigned short v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;"
+               : "=h"(v) : "l"(a), "l"(pol));
+  return v;
+}
+TE_DEV uint32_t ld_stream_u8(const uint8_t* a, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u8 %0, [%1], %2;"
+               : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+// reduced-precision matrix values -> binary32 (exact)
+TE_DEV float bf16_to_f32(uint32_t code) { return __uint_as_float(code << 16); }
+// FP8 E4M3: sign, 4 exponent bits (bias 7), 3 fraction bits; exponent 0 is
+// subnormal (m * 2^-9).  The all-ones NaN code is never produced.
+TE_DEV float e4m3_to_f32(uint32_t code) {
+  const uint32_t e = (code >> 3) & 15u, m = code & 7u;
+  const float v = e ? __uint_as_float(((e + 120u) << 23) | (m << 20)) : (float)m * 0x1p-9f;
+  return (code & 0x80u) ? -v : v;
+}
 TE_DEV double ld_stream_f64(const double* a, uint64_t pol) {
   double v;
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;"

@@ -72,6 +72,7 @@ struct SellHost {
   std::vector<int32_t> vout;  // per lane: row (>= 0), -1 - partial slot, or SELL_SKIP
   std::vector<int64_t> vsrc;  // per lane: first CSR entry of its piece
   std::vector<int32_t> vlen;  // per lane: entries of its piece
+  std::vector<int32_t> vrow;  // per lane: the row its piece belongs to (-1: empty lane)
   std::vector<LongRow> lrows;
   int64_t entries = 0;        // padded entries
   int64_t pieces = 0;         // partial sums of cut rows
@@ -87,6 +88,8 @@ struct DevSell {
   const int32_t* vout = nullptr;
   int32_t* cols = nullptr;
   void* vals = nullptr;
+  int vk = TE_F64;               // te_dtype of vals: F64, F32, BF16 or FP8_E4M3
+  const float* lscale = nullptr; // FP8: per-lane scale (the row's), else nullptr
   void* vpart = nullptr;  // partial sums of cut rows (8 bytes each)
   const LongRow* lrows = nullptr;
   int nslices = 0, nlrows = 0;
@@ -94,11 +97,17 @@ struct DevSell {
 };
 
 // fill cols/vals of the SELL layout from the CSR (one thread per lane)
-// in_type / out_type: TE_F64 or TE_F32 (te_dtype); binary64 -> binary32 rounds
-// to nearest even
+// in_type / out_type (te_dtype): F64 -> F64, F64 -> F32 (round to nearest
+// even), F32 -> F32, BF16 -> BF16, FP8_E4M3 -> FP8_E4M3 (codes copied).  For
+// FP8 also lane_scale[lane] = row_scale[vrow[lane]] (0 for empty lanes).
 cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, const void* val,
                               const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
-                              int nslices, int32_t* cols, void* vals, cudaStream_t s);
+                              int nslices, int32_t* cols, void* vals, const int32_t* vrow,
+                              const float* row_scale, float* lane_scale, cudaStream_t s);
+// binary64 CSR values -> `to` (TE_F32, TE_BF16 codes, TE_FP8_E4M3 codes with
+// per-row scales); round to nearest, ties to even (te_quant.cu)
+cudaError_t launch_quantize(int to, const int64_t* rp, const double* val, int64_t n, int64_t nnz,
+                            void* out, float* row_scale, cudaStream_t s);
 cudaError_t spmv_prepare();  // once per process/device, outside stream capture
 
 // SpMV: y = A x.  out_f64: write binary64 (else the precision's vector type).

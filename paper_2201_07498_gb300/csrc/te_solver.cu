@@ -43,13 +43,19 @@ te_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
+// DDD, or binary32 vectors with double-float arithmetic and binary32, bfloat16
+// or FP8 E4M3 matrix values (FDF, BDF, 8DF)
 int prec_of(te_precision p) {
   if (p.values == TE_F64 && p.arithmetic == TE_F64 && p.vectors == TE_F64) return PREC_DDD;
-  if (p.values == TE_F32 && p.arithmetic == TE_F64 && p.vectors == TE_F32) return PREC_FDF;
+  if ((p.values == TE_F32 || p.values == TE_BF16 || p.values == TE_FP8_E4M3) &&
+      p.arithmetic == TE_F64 && p.vectors == TE_F32)
+    return PREC_FDF;
   return -1;
 }
 size_t basis_elt(int prec) { return prec == PREC_DDD ? 8 : 4; }
-size_t value_elt(int prec) { return prec == PREC_DDD ? 8 : 4; }
+size_t elt_of(int dtype) {
+  return dtype == TE_F64 ? 8 : dtype == TE_F32 ? 4 : dtype == TE_BF16 ? 2 : 1;
+}
 
 double breakdown_tol(int prec) { return prec == PREC_DDD ? 1e-12 : 1e-6; }
 
@@ -66,7 +72,8 @@ bool is_device_ptr(const void* p) {
 struct Work {
   // byte offsets inside one allocation
   size_t V = 0, ytil = 0, w = 0, partials = 0, st = 0, Uint = 0, slices = 0, vout = 0,
-         scols = 0, svals = 0, svals64 = 0, lrows = 0, vpart = 0, flag = 0, total = 0;
+         scols = 0, svals = 0, svals64 = 0, lscale = 0, lrows = 0, vpart = 0, flag = 0,
+         total = 0;
 };
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
@@ -78,8 +85,8 @@ struct SellSizes {
 
 // refine: room for the plan's own Ritz vectors (n x K) and, for a
 // mixed-precision form, a binary64 copy of the SELL values
-Work layout(int prec, int64_t n_pad, int m, int grid, const SellSizes& z, bool refine = false,
-            int64_t n = 0, int K = 0) {
+Work layout(int prec, int vk, int64_t n_pad, int m, int grid, const SellSizes& z,
+            bool refine = false, int64_t n = 0, int K = 0) {
   Work w;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -96,8 +103,9 @@ Work layout(int prec, int64_t n_pad, int m, int grid, const SellSizes& z, bool r
   w.slices = take(std::max<size_t>(z.slices, 1) * sizeof(SellSlice));
   w.vout = take(std::max<size_t>(z.slices, 1) * SELL_C * sizeof(int32_t));
   w.scols = take(std::max<size_t>(z.entries, 1) * sizeof(int32_t));
-  w.svals = take(std::max<size_t>(z.entries, 1) * value_elt(prec));
+  w.svals = take(std::max<size_t>(z.entries, 1) * elt_of(vk));
   w.svals64 = (refine && prec != PREC_DDD) ? take(std::max<size_t>(z.entries, 1) * 8) : 0;
+  w.lscale = vk == TE_FP8_E4M3 ? take(std::max<size_t>(z.slices, 1) * SELL_C * 4) : 0;
   w.lrows = take(std::max<size_t>(z.lrows, 1) * sizeof(LongRow));
   w.vpart = take(std::max<size_t>(z.pieces, 1) * 8);
   w.flag = take(16);
@@ -118,7 +126,12 @@ te_status check_args(const te_csr* A, int32_t K, int32_t m, te_precision p) {
     return fail(TE_ERR_INVALID_ARG, "where must be TE_DEVICE or TE_HOST");
   if (A->values_f64 != 0 && A->values_f64 != 1)
     return fail(TE_ERR_INVALID_ARG, "values_f64 must be 0 or 1");
-  if (prec_of(p) < 0) return fail(TE_ERR_UNSUPPORTED, "precision must be DDD or FDF");
+  if (prec_of(p) < 0)
+    return fail(TE_ERR_UNSUPPORTED, "precision must be DDD, FDF, BDF (bfloat16 values) or 8DF "
+                                    "(FP8 E4M3 values)");
+  if ((p.values == TE_BF16 || p.values == TE_FP8_E4M3) && A->values_f64 != 1)
+    return fail(TE_ERR_INVALID_ARG,
+                "bfloat16 and FP8 storage is built from binary64 values (values_f64 = 1)");
   if (K < 1) return fail(TE_ERR_INVALID_ARG, "K must be >= 1");
   if (m < K) return fail(TE_ERR_INVALID_ARG, "krylov_steps must be >= K");
   if (m > MAX_M) return fail(TE_ERR_UNSUPPORTED, "krylov_steps must be <= 64");
@@ -149,6 +162,7 @@ struct te_plan {
   int64_t n = 0, n_pad = 0, nnz = 0;
   int K = 0, m = 0;
   int in_type = TE_F64;  // type of the caller's values (TE_F64 or the precision's)
+  int vk = TE_F64;       // storage type of the plan's copy of the values
   bool refine = false, noreorth = false;
   te_options opt{};
   const int64_t* rp = nullptr;
@@ -187,10 +201,14 @@ namespace {
 void* at(te_plan* P, size_t off) { return P->work + off; }
 
 // Upload the SELL metadata and convert the (device) CSR into the SELL arrays.
-// in_type: the caller's value type; out_type: the layout's; D64 (optional): a
-// second value array receiving the binary64 values
-cudaError_t upload_sell(int in_type, int out_type, const SellHost& H, const int32_t* ci,
-                        const void* val, const DevSell& D, void* vals64, cudaStream_t s) {
+// Build the SELL copy of a device CSR: upload the host partition, round or
+// quantise the values (in_type: the caller's value type, binary64 when the
+// storage type D.vk differs), and optionally write a second value array with
+// the binary64 values (vals64, for the refinement).  Temporaries are freed
+// before returning.
+cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const int32_t* ci,
+                        const void* val, int64_t n, int64_t nnz, const DevSell& D, void* vals64,
+                        float* lane_scale, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (!H.slices.empty()) {
     e = cudaMemcpyAsync(const_cast<SellSlice*>(D.slices), H.slices.data(),
@@ -203,26 +221,44 @@ cudaError_t upload_sell(int in_type, int out_type, const SellHost& H, const int3
     e = cudaMemcpyAsync(const_cast<LongRow*>(D.lrows), H.lrows.data(),
                         H.lrows.size() * sizeof(LongRow), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess || H.slices.empty()) return e;
-  // lane -> CSR piece map, needed only while converting
+  const bool quant = D.vk == TE_BF16 || D.vk == TE_FP8_E4M3;
+  const bool fp8 = D.vk == TE_FP8_E4M3;
+  // lane -> CSR piece map (and row), quantised values and row scales: needed
+  // only while building
   int64_t* dsrc = nullptr;
   int32_t* dlen = nullptr;
+  int32_t* drow = nullptr;
+  void* q = nullptr;
+  float* rscale = nullptr;
   e = cudaMalloc(&dsrc, H.vsrc.size() * sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&dlen, H.vlen.size() * sizeof(int32_t));
+  if (e == cudaSuccess && fp8) e = cudaMalloc(&drow, H.vrow.size() * sizeof(int32_t));
+  if (e == cudaSuccess && quant) e = cudaMalloc(&q, std::max<size_t>(nnz, 1) * elt_of(D.vk));
+  if (e == cudaSuccess && fp8) e = cudaMalloc(&rscale, std::max<int64_t>(n, 1) * sizeof(float));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dsrc, H.vsrc.data(), H.vsrc.size() * sizeof(int64_t),
                         cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dlen, H.vlen.data(), H.vlen.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && fp8)
+    e = cudaMemcpyAsync(drow, H.vrow.data(), H.vrow.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && quant)
+    e = launch_quantize(D.vk, rp, static_cast<const double*>(val), n, nnz, q, rscale, s);
   if (e == cudaSuccess)
-    e = launch_sell_build(in_type, out_type, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols,
-                          D.vals, s);
+    e = launch_sell_build(quant ? D.vk : in_type, D.vk, ci, quant ? q : val, D.slices, dsrc,
+                          dlen, D.nslices, D.cols, D.vals, drow, rscale,
+                          fp8 ? lane_scale : nullptr, s);
   if (e == cudaSuccess && vals64)
     e = launch_sell_build(TE_F64, TE_F64, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols,
-                          vals64, s);
+                          vals64, nullptr, nullptr, nullptr, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (dsrc) cudaFree(dsrc);
-  if (dlen) cudaFree(dlen);
+  cudaFree(dsrc);
+  cudaFree(dlen);
+  if (drow) cudaFree(drow);
+  if (q) cudaFree(q);
+  if (rscale) cudaFree(rscale);
   return e;
 }
 
@@ -314,8 +350,9 @@ cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     {
       const double n = (double)P->n, nnz = (double)P->nnz;
-      const double bytes = nnz * (4.0 + (double)value_elt(P->prec)) + 8.0 * (n + 1.0) +
-                           n * (double)basis_elt(P->prec) + n * 8.0;
+      const double bytes = nnz * (4.0 + (double)elt_of(P->vk)) + 8.0 * (n + 1.0) +
+                           n * (double)basis_elt(P->prec) + n * 8.0 +
+                           (P->vk == TE_FP8_E4M3 ? 4.0 * n : 0.0);
       if ((e = prof_end(P, s, TE_KIND_SPMV, bytes)) != cudaSuccess) return e;
     }
     PassArgs a = base_args(P);
@@ -485,7 +522,7 @@ size_t te_workspace_bytes(const te_csr* A, int32_t K, int32_t krylov_steps, te_p
   z.slices = (size_t)((A->n + z.pieces) / SELL_C + windows + 1);
   z.entries = (size_t)A->nnz + windows * 2 * SELL_C * SELL_VMAX;
   z.lrows = (size_t)(A->nnz / SELL_VMAX + 1);
-  Work w = layout(prec, pad_rows(A->n), krylov_steps, 1024, z);
+  Work w = layout(prec, p.values, pad_rows(A->n), krylov_steps, 1024, z);
   return w.total;
 }
 
@@ -541,6 +578,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   P->m = krylov_steps;
   P->opt = opt;
   P->in_type = in_type;
+  P->vk = p.values;
   P->refine = opt.refine != 0;
   P->noreorth = opt.reorth == TE_REORTH_NONE;
   TE_CK(cudaGetDevice(&P->dev), "cudaGetDevice");
@@ -579,7 +617,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   zs.entries = (size_t)sell.entries;
   zs.lrows = sell.lrows.size();
   zs.pieces = (size_t)sell.pieces;
-  P->W = layout(P->prec, P->n_pad, P->m, grid, zs, P->refine, P->n, P->K);
+  P->W = layout(P->prec, P->vk, P->n_pad, P->m, grid, zs, P->refine, P->n, P->K);
   const size_t in_elt = in_type == TE_F64 ? 8 : 4;
   size_t csr_bytes = 0;
   if (A->where == TE_HOST)
@@ -638,12 +676,16 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   P->sell.nslices = (int)sell.slices.size();
   P->sell.nlrows = (int)sell.lrows.size();
   P->sell.nlbig = (int)sell.nbig;
-  const int out_type = P->prec == PREC_DDD ? TE_F64 : TE_F32;
   void* vals64 = P->W.svals64 ? at(P, P->W.svals64) : nullptr;
-  TE_CK(upload_sell(in_type, out_type, sell, P->ci, P->val, P->sell, vals64, s),
+  P->sell.vk = P->vk;
+  P->sell.lscale = P->W.lscale ? static_cast<const float*>(at(P, P->W.lscale)) : nullptr;
+  TE_CK(upload_sell(in_type, sell, P->rp, P->ci, P->val, P->n, P->nnz, P->sell, vals64,
+                    P->W.lscale ? static_cast<float*>(at(P, P->W.lscale)) : nullptr, s),
         "build the SELL layout");
   if (P->refine) {
     P->sell64 = P->sell;
+    P->sell64.vk = TE_F64;
+    P->sell64.lscale = nullptr;
     if (vals64) P->sell64.vals = vals64;
     P->ubase = static_cast<double*>(at(P, P->W.Uint));
   }
@@ -827,11 +869,14 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
   const size_t b_sl = al256(std::max<size_t>(sell.slices.size(), 1) * sizeof(SellSlice));
   const size_t b_vo = al256(std::max<size_t>(sell.vout.size(), 1) * sizeof(int32_t));
   const size_t b_co = al256(std::max<size_t>((size_t)sell.entries, 1) * sizeof(int32_t));
-  const size_t b_va = al256(std::max<size_t>((size_t)sell.entries, 1) * value_elt(prec));
+  const size_t b_va = al256(std::max<size_t>((size_t)sell.entries, 1) * elt_of(p.values));
   const size_t b_lr = al256(std::max<size_t>(sell.lrows.size(), 1) * sizeof(LongRow));
   const size_t b_vp = al256(std::max<size_t>((size_t)sell.pieces, 1) * 8);
+  const size_t b_ls =
+      p.values == TE_FP8_E4M3 ? al256(std::max<size_t>(sell.vout.size(), 1) * 4) : 0;
   char* buf = nullptr;
-  TE_CK(cudaMalloc(&buf, b_sl + b_vo + b_co + b_va + b_lr + b_vp + 256), "allocate SpMV layout");
+  TE_CK(cudaMalloc(&buf, b_sl + b_vo + b_co + b_va + b_lr + b_vp + b_ls + 256),
+        "allocate SpMV layout");
   DevSell D;
   size_t off = 0;
   D.slices = reinterpret_cast<SellSlice*>(buf + off);
@@ -846,6 +891,10 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
   off += b_lr;
   D.vpart = buf + off;
   off += b_vp;
+  float* lscale = b_ls ? reinterpret_cast<float*>(buf + off) : nullptr;
+  off += b_ls;
+  D.vk = p.values;
+  D.lscale = lscale;
   int* flag = reinterpret_cast<int*>(buf + off);
   D.nslices = (int)sell.slices.size();
   D.nlrows = (int)sell.lrows.size();
@@ -861,9 +910,9 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
   }
   const int in_type = A->values_f64 ? TE_F64 : p.values;
-  const int out_type = prec == PREC_DDD ? TE_F64 : TE_F32;
   if (e == cudaSuccess)
-    e = upload_sell(in_type, out_type, sell, A->col_idx, A->values, D, nullptr, s);
+    e = upload_sell(in_type, sell, A->row_ptr, A->col_idx, A->values, A->n, A->nnz, D, nullptr,
+                    lscale, s);
   // the kernel writes rows with entries only
   if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, sizeof(double) * A->n, s);
   if (e == cudaSuccess) e = launch_spmv(prec, D, x, y, true, s);
@@ -949,6 +998,24 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
   if (e != cudaSuccess) return cuda_fail(e, "te_tridiag_eigs");
   if (sweeps) *sweeps = h[0];
   if (h[1] != 0) return fail((te_status)h[1], "Jacobi sweeps did not converge");
+  return TE_OK;
+}
+
+te_status te_quantize(const te_csr* A, int32_t to, void* out, float* row_scale, void* stream) {
+  if (!A || !out) return fail(TE_ERR_INVALID_ARG, "NULL argument");
+  if (A->where != TE_DEVICE || A->values_f64 != 1)
+    return fail(TE_ERR_INVALID_ARG, "te_quantize needs a TE_DEVICE matrix with binary64 values");
+  if (A->n < 1 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && !A->values))
+    return fail(TE_ERR_INVALID_ARG, "bad CSR sizes or pointers");
+  if (to != TE_F32 && to != TE_BF16 && to != TE_FP8_E4M3)
+    return fail(TE_ERR_INVALID_ARG, "to must be TE_F32, TE_BF16 or TE_FP8_E4M3");
+  if ((to == TE_FP8_E4M3) != (row_scale != nullptr))
+    return fail(TE_ERR_INVALID_ARG, "row_scale is required for TE_FP8_E4M3 and only for it");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_quantize(to, A->row_ptr, static_cast<const double*>(A->values), A->n,
+                                  A->nnz, out, row_scale, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "te_quantize");
   return TE_OK;
 }
 

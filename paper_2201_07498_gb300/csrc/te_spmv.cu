@@ -44,7 +44,7 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
   }
   struct Piece {
     int64_t src;
-    int32_t len, out;
+    int32_t len, out, row;
   };
   std::vector<Piece> win, sorted;
   std::vector<int64_t> pos(SELL_VMAX + 2);
@@ -55,7 +55,7 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
       const int64_t L = rp[r + 1] - rp[r];
       if (L == 0) continue;  // empty rows: never written by the kernel
       if (L <= SELL_VMAX) {
-        win.push_back({rp[r], (int32_t)L, (int32_t)r});
+        win.push_back({rp[r], (int32_t)L, (int32_t)r, (int32_t)r});
         continue;
       }
       LongRow lr;
@@ -66,7 +66,7 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
       for (int32_t c = 0; c < lr.count; ++c) {
         const int64_t s0 = rp[r] + (int64_t)c * SELL_VMAX;
         const int64_t l = std::min<int64_t>(SELL_VMAX, rp[r + 1] - s0);
-        win.push_back({s0, (int32_t)l, -1 - (int32_t)(out.pieces + c)});
+        win.push_back({s0, (int32_t)l, -1 - (int32_t)(out.pieces + c), (int32_t)r});
       }
       out.pieces += lr.count;
       out.lrows.push_back(lr);
@@ -81,7 +81,7 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
       pos[L] = acc;
       acc += c;
     }
-    sorted.assign(win.size(), Piece{0, 0, 0});
+    sorted.assign(win.size(), Piece{0, 0, 0, 0});
     for (const Piece& p : win) sorted[pos[p.len]++] = p;
     // slices of SELL_C lanes
     for (size_t i = 0; i < sorted.size(); i += SELL_C) {
@@ -95,10 +95,12 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
           out.vout.push_back(sorted[i + l].out);
           out.vsrc.push_back(sorted[i + l].src);
           out.vlen.push_back(sorted[i + l].len);
+          out.vrow.push_back(sorted[i + l].row);
         } else {
           out.vout.push_back(SELL_SKIP);
           out.vsrc.push_back(0);
           out.vlen.push_back(0);
+          out.vrow.push_back(-1);
         }
       }
       out.entries += (int64_t)SELL_C * sl.len;
@@ -127,7 +129,8 @@ TE_DEV Vout convert_value(Vin v) {
 template <typename Vin, typename Vout>
 __global__ void sell_build_kernel(const int32_t* ci, const Vin* val, const SellSlice* slices,
                                   const int64_t* vsrc, const int32_t* vlen, int nslices,
-                                  int32_t* cols, Vout* vals) {
+                                  int32_t* cols, Vout* vals, const int32_t* vrow,
+                                  const float* row_scale, float* lane_scale) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)nslices * SELL_C) return;
   const int64_t s = t / SELL_C;
@@ -135,6 +138,10 @@ __global__ void sell_build_kernel(const int32_t* ci, const Vin* val, const SellS
   const SellSlice sl = slices[s];
   const int64_t src = vsrc[t];
   const int len = vlen[t];
+  if (lane_scale) {
+    const int32_t r = vrow[t];
+    lane_scale[t] = r >= 0 ? row_scale[r] : 0.f;
+  }
   for (int k = 0; k < sl.len; ++k) {
     const int64_t dst = sl.base + (int64_t)k * SELL_C + lane;
     if (k < len) {
@@ -149,25 +156,26 @@ __global__ void sell_build_kernel(const int32_t* ci, const Vin* val, const SellS
 
 cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, const void* val,
                               const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
-                              int nslices, int32_t* cols, void* vals, cudaStream_t s) {
+                              int nslices, int32_t* cols, void* vals, const int32_t* vrow,
+                              const float* row_scale, float* lane_scale, cudaStream_t s) {
   if (nslices <= 0) return cudaSuccess;
   const int64_t lanes = (int64_t)nslices * SELL_C;
   const unsigned blocks = (unsigned)((lanes + 255) / 256);
-  if (in_type == TE_F64 && out_type == TE_F64)
-    sell_build_kernel<double, double><<<blocks, 256, 0, s>>>(
-        ci, static_cast<const double*>(val), slices, vsrc, vlen, nslices, cols,
-        static_cast<double*>(vals));
-  else if (in_type == TE_F64 && out_type == TE_F32)
-    sell_build_kernel<double, float><<<blocks, 256, 0, s>>>(
-        ci, static_cast<const double*>(val), slices, vsrc, vlen, nslices, cols,
-        static_cast<float*>(vals));
-  else if (in_type == TE_F32 && out_type == TE_F32)
-    sell_build_kernel<float, float><<<blocks, 256, 0, s>>>(
-        ci, static_cast<const float*>(val), slices, vsrc, vlen, nslices, cols,
-        static_cast<float*>(vals));
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
+#define TE_BUILD(IN, OUT, TI, TO)                                                               \
+  if (in_type == IN && out_type == OUT) {                                                      \
+    sell_build_kernel<TI, TO><<<blocks, 256, 0, s>>>(ci, static_cast<const TI*>(val), slices, \
+                                                     vsrc, vlen, nslices, cols,                \
+                                                     static_cast<TO*>(vals), vrow, row_scale,  \
+                                                     lane_scale);                              \
+    return cudaGetLastError();                                                                 \
+  }
+  TE_BUILD(TE_F64, TE_F64, double, double)
+  TE_BUILD(TE_F64, TE_F32, double, float)
+  TE_BUILD(TE_F32, TE_F32, float, float)
+  TE_BUILD(TE_BF16, TE_BF16, uint16_t, uint16_t)
+  TE_BUILD(TE_FP8_E4M3, TE_FP8_E4M3, uint8_t, uint8_t)
+#undef TE_BUILD
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -210,6 +218,7 @@ struct SpmvArgs {
   const int32_t* vout;
   const int32_t* cols;
   const void* vals;
+  const float* lscale;  // FP8: per-lane scale
   const void* x;
   void* y;
   void* vpart;
@@ -219,12 +228,44 @@ struct SpmvArgs {
 constexpr int SPMV_WPB = 8;     // warps (slices) per CTA
 constexpr int SPMV_UNROLL = 8;  // entries per lane in flight
 
-template <int P, bool F64OUT>
+// stored matrix value type per te_dtype, and its streaming load + exact
+// conversion to the arithmetic's input type
+template <int VK>
+struct VStore;
+template <>
+struct VStore<TE_F64> {
+  using t = double;
+};
+template <>
+struct VStore<TE_F32> {
+  using t = float;
+};
+template <>
+struct VStore<TE_BF16> {
+  using t = uint16_t;
+};
+template <>
+struct VStore<TE_FP8_E4M3> {
+  using t = uint8_t;
+};
+template <int VK>
+TE_DEV auto load_value(const typename VStore<VK>::t* p, uint64_t pol) {
+  if constexpr (VK == TE_F64) return ld_stream_f64(p, pol);
+  else if constexpr (VK == TE_F32) return ld_stream_f32(p, pol);
+  else if constexpr (VK == TE_BF16) return bf16_to_f32(ld_stream_u16(p, pol));
+  else return e4m3_to_f32(ld_stream_u8(p, pol));
+}
+
+// Reduced-precision values (BF16, FP8 codes) are exact binary32 numbers, so
+// the FDF arithmetic (exact products, double-float sums) is unchanged; FP8
+// rows are summed over their codes and multiplied by the row scale at the end.
+template <int P, int VK, bool F64OUT>
 __global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
   using Tr = SpmvTr<P>;
   using val_t = typename Tr::val_t;
   using x_t = typename Tr::x_t;
   using acc_t = typename Tr::acc_t;
+  using store_t = typename VStore<VK>::t;
   const int lane = threadIdx.x & 31;
   const int slice = blockIdx.x * SPMV_WPB + (threadIdx.x >> 5);
   if (slice >= a.nslices) return;
@@ -232,7 +273,7 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
   const int32_t out = a.vout[(int64_t)slice * SELL_C + lane];
   const uint64_t pol = policy_evict_first();
   const int32_t* cp = a.cols + sl.base + lane;
-  const val_t* vp = static_cast<const val_t*>(a.vals) + sl.base + lane;
+  const store_t* vp = static_cast<const store_t*>(a.vals) + sl.base + lane;
   const x_t* x = static_cast<const x_t*>(a.x);
   acc_t acc0, acc1;
   acc_zero<P>(acc0);
@@ -255,10 +296,7 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
     for (int u = 0; u < SPMV_UNROLL; ++u) {
       const bool ok = k + u < sl.len;
       c[u] = ok ? ld_stream_i32(cp + (int64_t)(k + u) * SELL_C, pol) : 0;
-      if constexpr (P == PREC_FDF)
-        v[u] = ok ? ld_stream_f32(vp + (int64_t)(k + u) * SELL_C, pol) : 0.f;
-      else
-        v[u] = ok ? ld_stream_f64(vp + (int64_t)(k + u) * SELL_C, pol) : 0.0;
+      v[u] = ok ? (val_t)load_value<VK>(vp + (int64_t)(k + u) * SELL_C, pol) : (val_t)0;
     }
     x_t xv[SPMV_UNROLL];
 #pragma unroll
@@ -269,16 +307,20 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
       add(acc1, v[u + 1], xv[u + 1]);
     }
   }
-  acc_t acc;
-  if constexpr (P == PREC_FDF) acc = dacc_merge(acc0, acc1);
-  else acc = acc0 + acc1;
-  if (out >= 0) {
-    store_row<P, F64OUT>(a.y, out, acc);
-  } else if (out != SELL_SKIP) {
-    if constexpr (P == PREC_FDF)
-      static_cast<float2*>(a.vpart)[-1 - (int64_t)out] = dw_to_f2(dacc_value(acc));
-    else
-      static_cast<double*>(a.vpart)[-1 - (int64_t)out] = acc;
+  if constexpr (P == PREC_FDF) {
+    dw r = dacc_value(dacc_merge(acc0, acc1));
+    if constexpr (VK == TE_FP8_E4M3)
+      r = dw_mul(r, dw{a.lscale[(int64_t)slice * SELL_C + lane], 0.f});
+    if (out >= 0) {
+      if constexpr (F64OUT) static_cast<double*>(a.y)[out] = dw_to_double(r);
+      else static_cast<float2*>(a.y)[out] = dw_to_f2(r);
+    } else if (out != SELL_SKIP) {
+      static_cast<float2*>(a.vpart)[-1 - (int64_t)out] = dw_to_f2(r);
+    }
+  } else {
+    const double r = acc0 + acc1;
+    if (out >= 0) static_cast<double*>(a.y)[out] = r;
+    else if (out != SELL_SKIP) static_cast<double*>(a.vpart)[-1 - (int64_t)out] = r;
   }
 }
 
@@ -312,10 +354,10 @@ __global__ void spmv_long_finalize(const LongRow* lrows, int nl, int nbig, int b
   if (live && sub == 0) store_row<P, F64OUT>(y, lr.row, acc);
 }
 
-template <int P, bool F64OUT>
+template <int P, int VK, bool F64OUT>
 static cudaError_t launch_spmv_t(const SpmvArgs& a, const DevSell& S, cudaStream_t s) {
   if (S.nslices > 0)
-    spmv_kernel<P, F64OUT><<<(S.nslices + SPMV_WPB - 1) / SPMV_WPB, 32 * SPMV_WPB, 0, s>>>(a);
+    spmv_kernel<P, VK, F64OUT><<<(S.nslices + SPMV_WPB - 1) / SPMV_WPB, 32 * SPMV_WPB, 0, s>>>(a);
   if (S.nlrows > 0) {
     const int threads = 256;
     const int big_blocks = (int)(((int64_t)S.nlbig * 32 + threads - 1) / threads);
@@ -336,13 +378,25 @@ cudaError_t launch_spmv(int prec, const DevSell& S, const void* x, void* y, bool
   a.vout = S.vout;
   a.cols = S.cols;
   a.vals = S.vals;
+  a.lscale = S.lscale;
   a.x = x;
   a.y = y;
   a.vpart = S.vpart;
   a.nslices = S.nslices;
-  if (prec == PREC_DDD) return launch_spmv_t<PREC_DDD, true>(a, S, s);
-  if (out_f64) return launch_spmv_t<PREC_FDF, true>(a, S, s);
-  return launch_spmv_t<PREC_FDF, false>(a, S, s);
+  if (prec == PREC_DDD) {
+    if (S.vk != TE_F64) return cudaErrorInvalidValue;
+    return launch_spmv_t<PREC_DDD, TE_F64, true>(a, S, s);
+  }
+#define TE_SPMV_FDF(VK)                                              \
+  if (S.vk == VK) {                                                  \
+    if (out_f64) return launch_spmv_t<PREC_FDF, VK, true>(a, S, s);  \
+    return launch_spmv_t<PREC_FDF, VK, false>(a, S, s);              \
+  }
+  TE_SPMV_FDF(TE_F32)
+  TE_SPMV_FDF(TE_BF16)
+  TE_SPMV_FDF(TE_FP8_E4M3)
+#undef TE_SPMV_FDF
+  return cudaErrorInvalidValue;
 }
 
 __global__ void validate_cols_kernel(const int32_t* ci, int64_t nnz, int64_t n, int* flag) {

@@ -71,7 +71,9 @@ def _desc(n, nnz, where=1, scale=None):
     (4, 65, "ddd", 7),         # m above the supported maximum
     (4, 11, "ddd", 1),         # m > n (n = 10)
     (2, 4, (1, 1, 1), 7),      # FFF not implemented
-    (2, 4, (2, 0, 0), 7),      # BF16 values not implemented
+    (2, 4, (2, 0, 0), 7),      # BF16 values with binary64 vectors: not a supported form
+    (2, 4, (2, 0, 1), 1),      # BDF needs binary64 input values (values_f64)
+    (2, 4, (3, 0, 1), 1),      # 8DF likewise
 ])
 def test_argument_validation_before_gpu(te, K, m, prec, expect):
     lib = te.load_library()

@@ -189,3 +189,117 @@ def test_orthogonality_metric_with_and_without_reorth(te):
     ang_ref = oracle.mean_pairwise_angle(ref_none.eigvecs)
     assert abs(ang["full"] - 90.0) <= 1e-6, ang
     assert ang["none"] < 89.0 and ang_ref < 89.0, (ang, ang_ref)
+
+
+# ---------------------------------------------------------------------------
+# reduced-precision matrix values (bfloat16, FP8 E4M3 with row scales)
+# ---------------------------------------------------------------------------
+
+def _quant_test_matrix():
+    """Values over a wide range, exact bfloat16 midpoints, zeros, an all-zero
+    row and rows whose largest magnitude is 448 (FP8 scale exactly 1) holding
+    exact E4M3 midpoints."""
+    rng = np.random.default_rng(21)
+    n = 3000
+    rows, cols, vals = [], [], []
+    for r in range(20, n):  # rows 0..19 hold the crafted entries below only
+        k = int(rng.integers(0, 30))
+        rows += [r] * k
+        cols += [int(c) for c in rng.integers(0, n, k)]
+        vals += list(np.exp2(rng.uniform(-30, 30, k)) * rng.choice([-1.0, 1.0], k))
+    bf = (np.arange(0x3F00, 0x3F80, dtype=np.uint32) << 16).view(np.float32).astype(float)
+    mids_bf = (bf[:-1] + bf[1:]) / 2
+    for i, v in enumerate(mids_bf):
+        rows.append(5)
+        cols.append(i)
+        vals.append(v)
+    e4 = np.array([(1 + m / 8) * 2.0 ** (e - 7) for e in range(1, 16) for m in range(8)][:-1])
+    mids_e4 = (e4[:-1] + e4[1:]) / 2
+    for i, v in enumerate(mids_e4):
+        rows += [9, 9]
+        cols += [2 * i, 2 * i + 1]
+        vals += [v, -448.0]
+    rows += [11, 11]
+    cols += [0, 1]
+    vals += [0.0, 0.0]
+    return synth.from_triplets(n, rows, cols, np.array(vals))
+
+
+def test_quantize_is_bit_exact(te):
+    A = _quant_test_matrix()
+    csr = te.CSR.from_host(A, "ddd", values_f64=True)
+    codes, _ = te.quantize(csr, "bf16")
+    want, _ = oracle.round_bf16(A.val)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint16), want)
+    f32, _ = te.quantize(csr, "f32")
+    assert np.array_equal(f32.cpu().numpy(), A.val.astype(np.float32))
+    c8, sc = te.quantize(csr, "e4m3")
+    w8, wsc, _ = oracle.quantize_e4m3_rows(A)
+    assert np.array_equal(sc.cpu().numpy(), wsc)
+    assert np.array_equal(c8.cpu().numpy(), w8)
+
+
+def _dequantised(A, prec):
+    if prec == "bdf":
+        return synth.CSR(A.n, A.row_ptr, A.col, oracle.round_bf16(A.val)[1])
+    return synth.CSR(A.n, A.row_ptr, A.col, oracle.quantize_e4m3_rows(A)[2])
+
+
+@pytest.mark.parametrize("prec", ["bdf", "8df"])
+def test_spmv_reduced_precision_matches_oracle(te, prec):
+    from test_gpu_parity import SPMV_CASES, spmv_bound
+    for name in ("uniform_1e4", "thresholds"):
+        A = SPMV_CASES[name]()
+        Aq = _dequantised(A, prec)
+        x = synth.uniform_pm1(A.n, 7, 1).astype(np.float32).astype(np.float64)
+        y = te.spmv(te.CSR.from_host(A, prec), torch.from_numpy(x.astype(np.float32)).cuda(),
+                    prec).cpu().numpy()
+        ref = oracle.spmv(Aq, x)
+        assert np.all(np.abs(y - ref) <= spmv_bound(Aq, x, 2.0 ** -44)), name
+
+
+@pytest.mark.parametrize("prec", ["bdf", "8df"])
+def test_topk_reduced_precision_matches_oracle(te, prec):
+    """The form's arithmetic is FDF's: against the FP64 oracle run on the same
+    rounded matrix the Ritz values agree to the binary32-vector level; with
+    refinement they are the binary64 Rayleigh quotients of the vectors."""
+    A = synth.uniform_sym(10000, 10, 0)
+    Aq = _dequantised(A, prec)
+    K, m = 8, 16
+    v1 = synth.start_vector(A.n, 0)
+    ref = oracle.topk_eigs(Aq, K, m, v1, seed=0)
+    csr = te.CSR.from_host(A, prec)
+    ev, _, _ = te.topk_eigs(csr, K, m, prec, seed=0)
+    ev = ev.numpy()
+    scale = np.max(np.abs(ref.eigvals))
+    perm = match_pairs(ev, ref.eigvals, 1e-6 * scale)
+    assert np.max(np.abs(ev - ref.eigvals[perm])) <= 1e-6 * scale
+    evr, Ur, resr = te.topk_eigs(csr, K, m, prec, seed=0, refine=True, residuals=True)
+    evr, resr = evr.numpy(), resr.numpy()
+    th_o, res_o = oracle.refine(A, ref.eigvecs[:, perm])
+    assert np.max(np.abs(evr - th_o)) <= 1e-5 * scale
+    th_g, res_g = oracle.refine(A, Ur.cpu().numpy())
+    assert np.max(np.abs(evr - th_g)) <= 1e-12 * scale
+    assert np.max(np.abs(resr - res_g)) <= 1e-10 * scale
+
+
+@pytest.mark.parametrize("prec", ["bdf", "8df"])
+def test_refine_recovers_diagonal_eigenvalues_from_reduced_values(te, prec):
+    """Rounding a diagonal matrix moves its eigenvalues by the rounding error
+    but not its eigenvectors; the binary64 Rayleigh quotients of the converged
+    Ritz vectors are the exact eigenvalues.  (bfloat16: up to 2^-9 relative;
+    FP8: a one-entry row is its own maximum, code 448, so only the binary32
+    rounding of the row scale, up to 2^-24, moves it.)"""
+    n = 3000
+    d = np.concatenate([[5.0, -4.0, 3.0], np.linspace(-1.0, 1.0, n - 3)])
+    d = d + 1e-3 * np.sin(np.arange(n))
+    A = synth.diagonal(d)
+    K, m = 3, 40
+    csr = te.CSR.from_host(A, prec)
+    ev, _, res = te.topk_eigs(csr, K, m, prec, seed=4, refine=True, residuals=True)
+    ev0, _, _ = te.topk_eigs(csr, K, m, prec, seed=4)
+    exact = d[:3]
+    err_ref = np.abs(ev.numpy() - exact[match_pairs(ev.numpy(), exact, 0.5)])
+    err_raw = np.abs(ev0.numpy() - exact[match_pairs(ev0.numpy(), exact, 0.5)])
+    assert np.max(err_ref) <= 1e-11 * 5, err_ref
+    assert np.max(err_raw) >= (1e-5 if prec == "bdf" else 1e-8), err_raw
