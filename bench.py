@@ -49,6 +49,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the DDD and K=8 timings")
     p.add_argument("--oracle-steps", type=int, default=6)
+    p.add_argument("--no-ooc", action="store_true",
+                   help="skip the host-streamed solve (R-MAT 2^25, edge factor 16, 4 GB budget)")
+    p.add_argument("--no-sweep", action="store_true",
+                   help="skip the precision sweep (R-MAT 2^22, edge factor 16, K=16, m=32)")
     return p.parse_args()
 
 
@@ -219,6 +223,113 @@ def workload_config(args, A):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def converged_match_err(ev_test, ev_ref, res_ref, tol=1e-9):
+    """Largest relative distance from each converged reference Ritz value
+    (residual <= tol |theta|) to the nearest value of the tested form, and how
+    many reference pairs were converged."""
+    import numpy as np
+    errs = []
+    for th, r in zip(ev_ref, res_ref):
+        if r <= tol * abs(th):
+            errs.append(float(np.min(np.abs(ev_test - th)) / abs(th)))
+    return (max(errs) if errs else None), len(errs)
+
+
+def nearest_rel_err(ev_test, ev_ref):
+    """Largest relative distance from a tested value to the nearest reference value."""
+    import numpy as np
+    return float(max(np.min(np.abs(ev_ref - t)) / abs(t) for t in ev_test))
+
+
+def precision_sweep(te, world, steps=5, warmup=3):
+    """Every supported form on R-MAT scale 22, edge factor 16, seed 2
+    (normalised adjacency), K = 16, m = 32: solve time, and the error of the
+    Ritz values against the plain FP64 path, without and with the binary64
+    Rayleigh-quotient refinement."""
+    import numpy as np
+    import synth
+    A = synth.rmat_sym(22, 16, 2)
+    K, m, seed = 16, 32, 2
+    csr = te.CSR.from_host(A, "ddd", values_f64=True)  # binary64 values serve every form
+    out = {"workload": "rmat22_ef16_normadj_seed2_K16_m32", "n": int(A.n), "nnz": int(A.nnz),
+           "forms": {}}
+    plan = te.Plan(csr, K, m, "ddd", seed=seed)
+    ms_d, _, _ = time_plan(plan, steps, warmup, world)
+    ev_d, _, res_d = plan.solve(vectors=False, residuals=True)
+    ev_d, res_d = ev_d.numpy(), res_d.numpy()
+    out["forms"]["ddd"] = {"solve_ms": ms_d, "spmv_value_bytes": 8,
+                           "fp64_converged_pairs": int(np.sum(res_d <= 1e-9 * np.abs(ev_d)))}
+    del plan
+    for prec, vb in (("fdf", 4), ("bdf", 2), ("8df", 1)):
+        row = {"spmv_value_bytes": vb}
+        plan = te.Plan(csr, K, m, prec, seed=seed)
+        row["solve_ms"], ev, _ = time_plan(plan, steps, warmup, world)
+        row["spmv_ms"] = plan.profile()["spmv"][0]
+        del plan
+        row["max_rel_err_vs_fp64_converged"] = converged_match_err(ev, ev_d, res_d)[0]
+        row["max_rel_err_vs_fp64_nearest"] = nearest_rel_err(ev, ev_d)
+        plan = te.Plan(csr, K, m, prec, seed=seed, refine=True)
+        ms_r, _, _ = time_plan(plan, steps, warmup, world)
+        ev_r, _, res_r = plan.solve(vectors=False, residuals=True)
+        ev_r, res_r = ev_r.numpy(), res_r.numpy()
+        del plan
+        row["refined"] = {
+            "solve_ms": ms_r,
+            "max_rel_err_vs_fp64_converged": converged_match_err(ev_r, ev_d, res_d)[0],
+            "max_rel_err_vs_fp64_nearest": nearest_rel_err(ev_r, ev_d),
+            "max_rel_residual": float(np.max(res_r / np.abs(ev_r))),
+        }
+        out["forms"][prec] = row
+    return out
+
+
+def h2d_probe(nbytes=1 << 30, reps=5):
+    """Pinned host -> device copy bandwidth (GB/s, best of reps, CUDA events)."""
+    import torch
+    src = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    best = 0.0
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    del src, dst
+    return best
+
+
+def out_of_core(te, world, steps=2, warmup=1):
+    """Host-streamed solve: R-MAT scale 25, edge factor 16, seed 3 (normalised
+    adjacency), int32 columns + binary32 values in pinned host memory, device
+    matrix budget 4 GB, binary64 vectors and arithmetic (FDD), K = 8, m = 16."""
+    import synth
+    t0 = time.perf_counter()
+    A = synth.rmat_sym(25, 16, 3)
+    gen_s = time.perf_counter() - t0
+    n, nnz = int(A.n), int(A.nnz)
+    host = te.CSR.from_host(A, "fdd", device="cpu", pin=True)
+    del A
+    t0 = time.perf_counter()
+    plan = te.Plan(host, 8, 16, "fdd", seed=3, matrix_budget=4 << 30)
+    build_s = time.perf_counter() - t0
+    ms, _, _ = time_plan(plan, steps, warmup, world)
+    prof = plan.profile()
+    sp_ms, sp_n, sp_bytes = prof["spmv"]
+    blocks = plan.stream_blocks
+    del plan, host
+    link = h2d_probe()
+    spmv_gbs = sp_bytes / (sp_ms * 1e-3) / 1e9
+    return {"workload": "rmat25_ef16_normadj_seed3_K8_m16_fdd_budget4GB", "n": n, "nnz": nnz,
+            "solve_ms": ms, "stream_blocks": blocks, "spmv_ms_per_step": sp_ms / max(sp_n, 1),
+            "spmv_gbs": spmv_gbs, "h2d_probe_gbs": link,
+            "roofline": {"bound": "host link", "achieved": spmv_gbs, "peak": link,
+                         "frac": spmv_gbs / link, "unit": "GB/s"},
+            "generate_s": gen_s, "plan_build_s": build_s}
+
+
 def time_plan(plan, steps, warmup, world, want_vectors=True):
     import torch
     ev = torch.empty(plan.K, dtype=torch.float64, device="cuda")
@@ -284,26 +395,50 @@ def main():
 
     extras = {}
     if not args.no_extras:
+        # the plain FP64 path (DDD) on the same workload
         csr_d = te.CSR.from_host(A, "ddd")
         plan_d = te.Plan(csr_d, K, m, "ddd", seed=args.seed)
-        ms_d, ev_d, _ = time_plan(plan_d, max(2, args.steps // 2), args.warmup, world)
+        ms_d, _, _ = time_plan(plan_d, max(2, args.steps // 2), args.warmup, world)
+        ev_d, _, res_d = plan_d.solve(vectors=False, residuals=True)
+        ev_d, res_d = ev_d.numpy(), res_d.numpy()
         prof_d = plan_d.profile()
         spd_ms, _, spd_bytes = prof_d["spmv"]
-        rel = float(np.max(np.abs(ev_f - ev_d) / np.abs(ev_d)))
+        del plan_d
+        # the chosen form with the binary64 Rayleigh-quotient refinement
+        csr_r = te.CSR.from_host(A, "fdf", values_f64=True)
+        plan_r = te.Plan(csr_r, K, m, "fdf", seed=args.seed, refine=True)
+        ms_r, _, _ = time_plan(plan_r, max(2, args.steps // 2), args.warmup, world)
+        ev_r, _, res_r = plan_r.solve(vectors=False, residuals=True)
+        ev_r, res_r = ev_r.numpy(), res_r.numpy()
+        del plan_r, csr_r
+        err_f, n_conv = converged_match_err(ev_f, ev_d, res_d)
+        err_r, _ = converged_match_err(ev_r, ev_d, res_d)
         extras.update({
             "fp64_plain_solve_ms": ms_d,
             "speedup_vs_fp64_plain": ms_d / ms_f,
             "spmv_gbs": spmv_gbs,
             "spmv_gbs_fp64_plain": spd_bytes / (spd_ms * 1e-3) / 1e9,
-            "rel_eig_err_vs_fp64_plain": rel,
+            "fixed_error": {
+                "fp64_converged_pairs": n_conv,
+                "max_rel_err_fdf_vs_fp64_converged": err_f,
+                "max_rel_err_fdf_refined_vs_fp64_converged": err_r,
+                "fdf_refined_solve_ms": ms_r,
+                "fdf_refined_speedup_vs_fp64_plain": ms_d / ms_r,
+                "fdf_refined_max_rel_residual": float(np.max(res_r / np.abs(ev_r))),
+                "note": "eigenvalues +-1 have huge multiplicity here; a converged FP64 pair "
+                        "(residual <= 1e-9 |theta|) must appear in the mixed form's list; "
+                        "the refined residual bounds each value's distance to an eigenvalue",
+            },
         })
-        del plan_d
         Ks, ms_ = max(1, K // 3), max(2, m // 3)
         plan_fs = te.Plan(csr_f, Ks, ms_, "fdf", seed=args.seed)
-        ms_fs, _, _ = time_plan(plan_fs, args.steps, args.warmup, world)
+        ms_fs, ev_fs, _ = time_plan(plan_fs, args.steps, args.warmup, world)
         plan_ds = te.Plan(csr_d, Ks, ms_, "ddd", seed=args.seed)
-        ms_ds, _, _ = time_plan(plan_ds, max(2, args.steps // 2), args.warmup, world)
-        extras[f"solve_ms_K{Ks}_m{ms_}"] = {"fdf": ms_fs, "ddd": ms_ds}
+        ms_ds, ev_ds, _ = time_plan(plan_ds, max(2, args.steps // 2), args.warmup, world)
+        extras[f"solve_ms_K{Ks}_m{ms_}"] = {
+            "fdf": ms_fs, "ddd": ms_ds,
+            "max_rel_err_fdf_vs_fp64": float(np.max(
+                [np.min(np.abs(ev_fs - t)) / abs(t) for t in ev_ds]))}
         del plan_fs, plan_ds, csr_d
     else:
         extras["spmv_gbs"] = spmv_gbs
@@ -327,6 +462,11 @@ def main():
         if it > 0:
             e2e_ms.append(a0.elapsed_time(a1))
     e2e = max_over_ranks(statistics.median(e2e_ms), world) if e2e_ms else None
+
+    if not args.no_sweep and world == 1:
+        extras["precision_sweep"] = precision_sweep(te, world)
+    if not args.no_ooc and world == 1:
+        extras["out_of_core"] = out_of_core(te, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
