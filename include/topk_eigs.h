@@ -57,6 +57,8 @@ typedef enum { TE_F64 = 0, TE_F32 = 1, TE_BF16 = 2, TE_FP8_E4M3 = 3 } te_dtype;
 
 /* (matrix values, arithmetic, vector storage).  Supported:
  *   DDD = {TE_F64, TE_F64, TE_F64}: plain binary64 on the FP64 pipe.
+ *   FDD = {TE_F32, TE_F64, TE_F64}: as DDD with binary32 matrix values
+ *         (converted exactly to binary64 as they are read).
  *   FDF = {TE_F32, TE_F64, TE_F32}: binary32 matrix values and Lanczos
  *         vectors; every product and sum of the SpMV, the
  *         reorthogonalisation and the Ritz contraction is carried in
@@ -112,6 +114,15 @@ typedef struct {
                        ||Mu - theta u|| / ||u||.  Needs A->values_f64 = 1.  Costs K
                        binary64 SpMVs; with eigvecs NULL the plan keeps its own
                        vectors.  Default 0. */
+  size_t matrix_budget_bytes; /* 0 (default): the plan's copy of the matrix lives in device
+                       memory.  Otherwise, when that copy (about nnz * (4 + value bytes))
+                       would exceed this many bytes, a TE_HOST matrix stays in pinned
+                       host memory and every SpMV streams it in row blocks through two
+                       device buffers of at most matrix_budget_bytes / 2 each: the copy
+                       of the next block (on a second stream) overlaps the SpMV of the
+                       current one.  Binary64 or binary32 values only (DDD, FDD, FDF);
+                       no refinement.  A TE_DEVICE matrix over the budget is an error
+                       (TE_ERR_OUT_OF_MEMORY). */
 } te_options;
 
 /* Fill `opt` with the defaults: seed 0, v1 NULL, largest magnitude, graphs on,
@@ -195,6 +206,9 @@ te_status te_plan_profile(te_plan* plan, double* ms, int32_t* launches, double* 
 
 /* Number of kernels one solve launches (graph nodes when captured). */
 int32_t te_plan_kernel_count(const te_plan* plan);
+
+/* Row blocks each SpMV streams from host memory (0: the matrix is resident). */
+int64_t te_plan_stream_blocks(const te_plan* plan);
 
 void te_plan_destroy(te_plan* plan);
 

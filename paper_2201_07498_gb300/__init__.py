@@ -25,7 +25,8 @@ TE_F64, TE_F32, TE_BF16, TE_FP8_E4M3 = 0, 1, 2, 3
 TE_DEVICE, TE_HOST = 0, 1
 WHICH = {"LM": 0, "LA": 1}
 REORTH = {"full": 0, "none": 1}
-PRECISIONS = {"ddd": (TE_F64, TE_F64, TE_F64), "fdf": (TE_F32, TE_F64, TE_F32),
+PRECISIONS = {"ddd": (TE_F64, TE_F64, TE_F64), "fdd": (TE_F32, TE_F64, TE_F64),
+              "fdf": (TE_F32, TE_F64, TE_F32),
               "bdf": (TE_BF16, TE_F64, TE_F32), "8df": (TE_FP8_E4M3, TE_F64, TE_F32)}
 STATUS = {0: "TE_OK", 1: "TE_ERR_INVALID_ARG", 2: "TE_ERR_OUT_OF_MEMORY", 3: "TE_ERR_CUDA",
           4: "TE_ERR_BREAKDOWN", 5: "TE_ERR_NOT_CONVERGED", 6: "TE_ERR_TIMEOUT",
@@ -53,7 +54,8 @@ class te_precision(ctypes.Structure):
 class te_options(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("v1", ctypes.c_void_p), ("which", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("device_budget_bytes", ctypes.c_size_t),
-                ("reorth", ctypes.c_int32), ("refine", ctypes.c_int32)]
+                ("reorth", ctypes.c_int32), ("refine", ctypes.c_int32),
+                ("matrix_budget_bytes", ctypes.c_size_t)]
 
 
 # every symbol the header declares, with its ctypes signature
@@ -75,6 +77,7 @@ _SIGS = {
                                       ctypes.c_void_p, ctypes.c_void_p]),
     "te_plan_status": (ctypes.c_int, [ctypes.c_void_p]),
     "te_plan_kernel_count": (ctypes.c_int32, [ctypes.c_void_p]),
+    "te_plan_stream_blocks": (ctypes.c_int64, [ctypes.c_void_p]),
     "te_plan_destroy": (None, [ctypes.c_void_p]),
     "te_spmv": (ctypes.c_int, [ctypes.c_void_p, te_precision, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_void_p]),
@@ -198,7 +201,7 @@ class CSR:
 
 
 def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full",
-             refine=False) -> te_options:
+             refine=False, matrix_budget=0) -> te_options:
     o = te_options()
     load_library().te_default_options(ctypes.byref(o))
     o.seed = seed
@@ -208,12 +211,13 @@ def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full
     o.device_budget_bytes = budget
     o.reorth = REORTH[reorth] if isinstance(reorth, str) else int(reorth)
     o.refine = 1 if refine else 0
+    o.matrix_budget_bytes = matrix_budget
     return o
 
 
 def topk_eigs(csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0, v1=None,
               which="LM", vectors: bool = True, residuals: bool = False, reorth="full",
-              refine: bool = False, stream=None, out=None):
+              refine: bool = False, matrix_budget: int = 0, stream=None, out=None):
     """One Top-K solve; returns (eigvals [K] float64 cpu, eigvecs [n, K] float64 or None,
     residuals [K] or None: estimates, or true binary64 residuals with refine).
     Vectors live where the matrix lives unless `out = (eigvals [K], eigvecs
@@ -221,7 +225,7 @@ def topk_eigs(csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int
     import torch
     lib = load_library()
     A = csr.to_ctypes()
-    opt = _options(seed, v1, which, reorth=reorth, refine=refine)
+    opt = _options(seed, v1, which, reorth=reorth, refine=refine, matrix_budget=matrix_budget)
     if out is not None:
         ev, U = out
     else:
@@ -243,11 +247,11 @@ class Plan:
 
     def __init__(self, csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0,
                  v1=None, which="LM", use_graph: bool = True, budget: int = 0,
-                 reorth="full", refine: bool = False, stream=None):
+                 reorth="full", refine: bool = False, matrix_budget: int = 0, stream=None):
         self._lib = load_library()
         self.csr, self.K, self.m, self.n = csr, K, krylov_steps, csr.n
         A = csr.to_ctypes()
-        opt = _options(seed, v1, which, use_graph, budget, reorth, refine)
+        opt = _options(seed, v1, which, use_graph, budget, reorth, refine, matrix_budget)
         h = ctypes.c_void_p()
         rc = self._lib.te_plan_create(ctypes.byref(A), K, krylov_steps, _prec(precision),
                                       ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h))
@@ -257,6 +261,11 @@ class Plan:
     @property
     def kernel_count(self) -> int:
         return int(self._lib.te_plan_kernel_count(self._h))
+
+    @property
+    def stream_blocks(self) -> int:
+        """Row blocks each SpMV streams from host memory (0: resident matrix)."""
+        return int(self._lib.te_plan_stream_blocks(self._h))
 
     def solve(self, v1=None, vectors: bool = True, residuals: bool = False, stream=None):
         import torch

@@ -90,6 +90,8 @@ struct DevSell {
   void* vals = nullptr;
   int vk = TE_F64;               // te_dtype of vals: F64, F32, BF16 or FP8_E4M3
   const float* lscale = nullptr; // FP8: per-lane scale (the row's), else nullptr
+  int64_t ebase = 0;             // cols/vals hold entries [ebase, ...) of the layout
+                                 // (a streamed row block); 0 when resident
   void* vpart = nullptr;  // partial sums of cut rows (8 bytes each)
   const LongRow* lrows = nullptr;
   int nslices = 0, nlrows = 0;
@@ -104,6 +106,10 @@ cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, cons
                               const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
                               int nslices, int32_t* cols, void* vals, const int32_t* vrow,
                               const float* row_scale, float* lane_scale, cudaStream_t s);
+// the same arrays built on the host (in_type F64 or F32 -> vk F64 or F32);
+// false if a column index lies outside [0, n)
+bool build_sell_host(const SellHost& H, const int32_t* ci, const void* val, int in_type, int vk,
+                     int64_t n, int32_t* cols, void* vals);
 // binary64 CSR values -> `to` (TE_F32, TE_BF16 codes, TE_FP8_E4M3 codes with
 // per-row scales); round to nearest, ties to even (te_quant.cu)
 cudaError_t launch_quantize(int to, const int64_t* rp, const double* val, int64_t n, int64_t nnz,

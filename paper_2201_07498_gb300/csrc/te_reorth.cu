@@ -430,40 +430,52 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
       // the second; for the second sweep it leaves a component of about
       // u32 |w| along V, the level of w's own binary32 rounding.  The one
       // second-sweep dot that enters alpha_i (column i, the last) keeps
-      // exact products and double-float sums.
+      // exact products and double-float sums, and so does alpha_i's dot
+      // without reorthogonalisation (no second sweep corrects it).  Each
+      // lane's 8 vector values are read from shared memory once per tile.
+      if constexpr (P == PREC_FDF) {
+        float wx[TILE_R / 32], wy[TILE_R / 32];
 #pragma unroll
-      for (int q = 0; q < QMAX; ++q) {
-        const int jj = wid + (CONSUMERS / 32) * q;
-        if (jj >= nb) break;
-        const basis_t* col = tv + (size_t)jj * TILE_R;
-        if constexpr (P == PREC_FDF) {
-          // (without reorthogonalisation the DOT pass's one dot is alpha_i
-          // itself, with no second sweep to correct it: exact)
+        for (int rr = 0; rr < TILE_R / 32; ++rr) {
+          const float2 t = ws[lane + 32 * rr];
+          wx[rr] = t.x;
+          wy[rr] = t.y;
+        }
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+          const int jj = wid + (CONSUMERS / 32) * q;
+          if (jj >= nb) break;
+          const basis_t* col = tv + (size_t)jj * TILE_R;
           if ((MODE == MODE_DOT && a.fin != FIN_DOT_NOREORTH) ||
               (MODE == MODE_AXPY_DOT && jj < nb - 1)) {
             float c0 = 0.f, c1 = 0.f;
 #pragma unroll
             for (int rr = 0; rr < TILE_R / 32; rr += 2) {
-              c0 = __fmaf_rn(col[lane + 32 * rr], ws[lane + 32 * rr].x, c0);
-              c1 = __fmaf_rn(col[lane + 32 * (rr + 1)], ws[lane + 32 * (rr + 1)].x, c1);
+              c0 = __fmaf_rn(col[lane + 32 * rr], wx[rr], c0);
+              c1 = __fmaf_rn(col[lane + 32 * (rr + 1)], wx[rr + 1], c1);
             }
             dacc_add_pair(dots[q], c0, c1);
-            continue;
+          } else {
+            acc_t e0 = zero_acc<P>(), e1 = zero_acc<P>();
+#pragma unroll
+            for (int rr = 0; rr < TILE_R / 32; rr += 2) {
+              dacc_fma(e0, col[lane + 32 * rr], wx[rr], wy[rr]);
+              dacc_fma(e1, col[lane + 32 * (rr + 1)], wx[rr + 1], wy[rr + 1]);
+            }
+            dots[q] = acc_merge<P>(dots[q], acc_merge<P>(e0, e1));
           }
         }
-        {
+      } else {
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+          const int jj = wid + (CONSUMERS / 32) * q;
+          if (jj >= nb) break;
+          const basis_t* col = tv + (size_t)jj * TILE_R;
           acc_t e0 = zero_acc<P>(), e1 = zero_acc<P>();
 #pragma unroll
           for (int rr = 0; rr < TILE_R / 32; rr += 2) {
-            const vec_t w0 = ws[lane + 32 * rr], w1 = ws[lane + 32 * (rr + 1)];
-            const basis_t v0 = col[lane + 32 * rr], v1 = col[lane + 32 * (rr + 1)];
-            if constexpr (P == PREC_FDF) {
-              dacc_fma(e0, v0, w0.x, w0.y);
-              dacc_fma(e1, v1, w1.x, w1.y);
-            } else {
-              e0 = fma(v0, w0, e0);
-              e1 = fma(v1, w1, e1);
-            }
+            e0 = fma(col[lane + 32 * rr], ws[lane + 32 * rr], e0);
+            e1 = fma(col[lane + 32 * (rr + 1)], ws[lane + 32 * (rr + 1)], e1);
           }
           dots[q] = acc_merge<P>(dots[q], acc_merge<P>(e0, e1));
         }

@@ -43,10 +43,13 @@ te_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-// DDD, or binary32 vectors with double-float arithmetic and binary32, bfloat16
-// or FP8 E4M3 matrix values (FDF, BDF, 8DF)
+// binary64 vectors and arithmetic with binary64 or binary32 values (DDD, FDD),
+// or binary32 vectors with double-float arithmetic and binary32, bfloat16 or
+// FP8 E4M3 values (FDF, BDF, 8DF)
 int prec_of(te_precision p) {
-  if (p.values == TE_F64 && p.arithmetic == TE_F64 && p.vectors == TE_F64) return PREC_DDD;
+  if ((p.values == TE_F64 || p.values == TE_F32) && p.arithmetic == TE_F64 &&
+      p.vectors == TE_F64)
+    return PREC_DDD;
   if ((p.values == TE_F32 || p.values == TE_BF16 || p.values == TE_FP8_E4M3) &&
       p.arithmetic == TE_F64 && p.vectors == TE_F32)
     return PREC_FDF;
@@ -104,7 +107,7 @@ Work layout(int prec, int vk, int64_t n_pad, int m, int grid, const SellSizes& z
   w.vout = take(std::max<size_t>(z.slices, 1) * SELL_C * sizeof(int32_t));
   w.scols = take(std::max<size_t>(z.entries, 1) * sizeof(int32_t));
   w.svals = take(std::max<size_t>(z.entries, 1) * elt_of(vk));
-  w.svals64 = (refine && prec != PREC_DDD) ? take(std::max<size_t>(z.entries, 1) * 8) : 0;
+  w.svals64 = (refine && vk != TE_F64) ? take(std::max<size_t>(z.entries, 1) * 8) : 0;
   w.lscale = vk == TE_FP8_E4M3 ? take(std::max<size_t>(z.slices, 1) * SELL_C * 4) : 0;
   w.lrows = take(std::max<size_t>(z.lrows, 1) * sizeof(LongRow));
   w.vpart = take(std::max<size_t>(z.pieces, 1) * 8);
@@ -127,8 +130,8 @@ te_status check_args(const te_csr* A, int32_t K, int32_t m, te_precision p) {
   if (A->values_f64 != 0 && A->values_f64 != 1)
     return fail(TE_ERR_INVALID_ARG, "values_f64 must be 0 or 1");
   if (prec_of(p) < 0)
-    return fail(TE_ERR_UNSUPPORTED, "precision must be DDD, FDF, BDF (bfloat16 values) or 8DF "
-                                    "(FP8 E4M3 values)");
+    return fail(TE_ERR_UNSUPPORTED, "precision must be DDD, FDD, FDF, BDF (bfloat16 values) or "
+                                    "8DF (FP8 E4M3 values)");
   if ((p.values == TE_BF16 || p.values == TE_FP8_E4M3) && A->values_f64 != 1)
     return fail(TE_ERR_INVALID_ARG,
                 "bfloat16 and FP8 storage is built from binary64 values (values_f64 = 1)");
@@ -172,6 +175,20 @@ struct te_plan {
   int dev = 0, num_sms = 0;
   DevSell sell;
   DevSell sell64;  // binary64 values for the refinement (same layout)
+  // streamed matrix: the SELL arrays stay in pinned host memory and every
+  // SpMV copies them block by block into two device buffers
+  struct Block {
+    int first_slice, nslices;
+    int64_t ebase, entries;
+  };
+  bool streaming = false;
+  std::vector<Block> blocks;
+  int64_t cap_entries = 0;     // entries per device buffer
+  int32_t* hcols = nullptr;    // pinned host layout
+  void* hvals = nullptr;
+  cudaStream_t cs = nullptr;   // copy stream
+  cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* ubase = nullptr;  // with refinement: the plan's Ritz vectors (n x K)
   Work W;
   char* work = nullptr;
@@ -206,6 +223,23 @@ void* at(te_plan* P, size_t off) { return P->work + off; }
 // storage type D.vk differs), and optionally write a second value array with
 // the binary64 values (vals64, for the refinement).  Temporaries are freed
 // before returning.
+// slice records, lane outputs and cut-row records (small), then synchronise
+cudaError_t upload_meta(const SellHost& H, const DevSell& D, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (!H.slices.empty()) {
+    e = cudaMemcpyAsync(const_cast<SellSlice*>(D.slices), H.slices.data(),
+                        H.slices.size() * sizeof(SellSlice), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(const_cast<int32_t*>(D.vout), H.vout.data(),
+                          H.vout.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess && !H.lrows.empty())
+    e = cudaMemcpyAsync(const_cast<LongRow*>(D.lrows), H.lrows.data(),
+                        H.lrows.size() * sizeof(LongRow), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
 cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const int32_t* ci,
                         const void* val, int64_t n, int64_t nnz, const DevSell& D, void* vals64,
                         float* lane_scale, cudaStream_t s) {
@@ -328,6 +362,61 @@ cudaError_t pass(te_plan* P, int mode, const PassArgs& a, cudaStream_t s) {
   return prof_end(P, s, kind, a.only_on_restart ? 0.0 : pass_bytes(P, mode, a));
 }
 
+// y = M x for the solve.  A streamed matrix: fork the copy stream, then per
+// row block b (device buffer b % 2): the copy waits until the SpMV of block
+// b - 2 has released the buffer, the SpMV of block b waits for its copy; the
+// cut-row finaliser runs once all blocks are done.  The same sequence is
+// captured into the plan's graph (event record / wait become graph edges).
+cudaError_t enqueue_spmv(te_plan* P, const void* x, void* y, bool out_f64, cudaStream_t s) {
+  if (!P->streaming) {
+    P->nkernels += 1 + (P->sell.nlrows > 0 ? 1 : 0);
+    return launch_spmv(P->prec, P->sell, x, y, out_f64, s);
+  }
+  cudaError_t e;
+  const size_t elt = elt_of(P->vk);
+  int32_t* dcols = static_cast<int32_t*>(at(P, P->W.scols));
+  char* dvals = static_cast<char*>(at(P, P->W.svals));
+  if ((e = cudaEventRecord(P->ev_fork, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(P->cs, P->ev_fork, 0)) != cudaSuccess) return e;
+  for (size_t b = 0; b < P->blocks.size(); ++b) {
+    const te_plan::Block& B = P->blocks[b];
+    const int u = (int)(b & 1);
+    int32_t* bc = dcols + (size_t)u * P->cap_entries;
+    char* bv = dvals + (size_t)u * P->cap_entries * elt;
+    if (b >= 2 && (e = cudaStreamWaitEvent(P->cs, P->ev_free[u], 0)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(bc, P->hcols + B.ebase, (size_t)B.entries * 4,
+                             cudaMemcpyHostToDevice, P->cs)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(bv, static_cast<char*>(P->hvals) + (size_t)B.ebase * elt,
+                             (size_t)B.entries * elt, cudaMemcpyHostToDevice, P->cs)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(P->ev_ready[u], P->cs)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, P->ev_ready[u], 0)) != cudaSuccess) return e;
+    DevSell V = P->sell;
+    V.slices = P->sell.slices + B.first_slice;
+    V.vout = P->sell.vout + (size_t)B.first_slice * SELL_C;
+    V.nslices = B.nslices;
+    V.nlrows = 0;
+    V.nlbig = 0;
+    V.cols = bc;
+    V.vals = bv;
+    V.ebase = B.ebase;
+    P->nkernels += 1;
+    if ((e = launch_spmv(P->prec, V, x, y, out_f64, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(P->ev_free[u], s)) != cudaSuccess) return e;
+  }
+  if ((e = cudaEventRecord(P->ev_join, P->cs)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s, P->ev_join, 0)) != cudaSuccess) return e;
+  if (P->sell.nlrows > 0) {
+    DevSell V = P->sell;
+    V.nslices = 0;  // the finaliser alone
+    P->nkernels += 1;
+    if ((e = launch_spmv(P->prec, V, x, y, out_f64, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Enqueue the Lanczos phase (Algorithm 1): init + m steps.
 cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
   cudaError_t e;
@@ -344,9 +433,8 @@ cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
   }
   for (int i = 0; i < P->m; ++i) {
     const void* xi = static_cast<const char*>(at(P, P->W.V)) + (size_t)i * P->n_pad * belt;
-    P->nkernels += 1 + (P->sell.nlrows > 0 ? 1 : 0);
     if ((e = prof_begin(P, s)) != cudaSuccess) return e;
-    e = launch_spmv(P->prec, P->sell, xi, at(P, P->W.ytil), false, s);
+    e = enqueue_spmv(P, xi, at(P, P->W.ytil), false, s);
     if (e != cudaSuccess) return e;
     {
       const double n = (double)P->n, nnz = (double)P->nnz;
@@ -528,6 +616,12 @@ size_t te_workspace_bytes(const te_csr* A, int32_t K, int32_t krylov_steps, te_p
 
 void te_plan_destroy(te_plan* P) {
   if (!P) return;
+  for (cudaEvent_t e : {P->ev_ready[0], P->ev_ready[1], P->ev_free[0], P->ev_free[1], P->ev_fork,
+                        P->ev_join})
+    if (e) cudaEventDestroy(e);
+  if (P->cs) cudaStreamDestroy(P->cs);
+  if (P->hcols) cudaFreeHost(P->hcols);
+  if (P->hvals) cudaFreeHost(P->hvals);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->cap) cudaStreamDestroy(P->cap);
   if (P->work) cudaFree(P->work);
@@ -612,15 +706,46 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   const int grid = std::max(std::max(P->Ldot.grid, P->Laxd.grid),
                             std::max(P->Lsto.grid, P->Lritz.grid));
 
+  // a matrix whose layout exceeds matrix_budget_bytes stays in pinned host
+  // memory and is streamed in row blocks (whole slices) of at most half the
+  // budget each
+  const size_t velt = elt_of(P->vk);
+  P->streaming = opt.matrix_budget_bytes > 0 &&
+                 (size_t)sell.entries * (4 + velt) > opt.matrix_budget_bytes;
+  if (P->streaming) {
+    if (A->where != TE_HOST)
+      return fail(TE_ERR_OUT_OF_MEMORY,
+                  "the matrix layout exceeds matrix_budget_bytes; only a TE_HOST matrix can be "
+                  "streamed");
+    if (P->vk != TE_F64 && P->vk != TE_F32)
+      return fail(TE_ERR_UNSUPPORTED, "a streamed matrix holds binary64 or binary32 values");
+    if (P->refine)
+      return fail(TE_ERR_UNSUPPORTED, "refinement is not available with a streamed matrix");
+    P->cap_entries = (int64_t)(opt.matrix_budget_bytes / 2 / (4 + velt)) / 64 * 64;
+    te_plan::Block cur{0, 0, 0, 0};
+    for (size_t i = 0; i < sell.slices.size(); ++i) {
+      const int64_t ent = (int64_t)SELL_C * sell.slices[i].len;
+      if (ent > P->cap_entries)
+        return fail(TE_ERR_INVALID_ARG, "matrix_budget_bytes is too small to hold one slice");
+      if (cur.entries + ent > P->cap_entries) {
+        P->blocks.push_back(cur);
+        cur = te_plan::Block{(int)i, 0, sell.slices[i].base, 0};
+      }
+      cur.nslices += 1;
+      cur.entries += ent;
+    }
+    if (cur.nslices > 0) P->blocks.push_back(cur);
+  }
+
   SellSizes zs;
   zs.slices = sell.slices.size();
-  zs.entries = (size_t)sell.entries;
+  zs.entries = P->streaming ? (size_t)(2 * P->cap_entries) : (size_t)sell.entries;
   zs.lrows = sell.lrows.size();
   zs.pieces = (size_t)sell.pieces;
   P->W = layout(P->prec, P->vk, P->n_pad, P->m, grid, zs, P->refine, P->n, P->K);
   const size_t in_elt = in_type == TE_F64 ? 8 : 4;
   size_t csr_bytes = 0;
-  if (A->where == TE_HOST)
+  if (A->where == TE_HOST && !P->streaming)
     csr_bytes = al256(sizeof(int64_t) * (A->n + 1)) + al256(sizeof(int32_t) * A->nnz) +
                 al256(in_elt * A->nnz);
   if (opt.device_budget_bytes > 0 && P->W.total + csr_bytes > opt.device_budget_bytes)
@@ -630,7 +755,21 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   TE_CK(cudaMallocHost(&P->hres, sizeof(te_plan::HostRes)), "allocate pinned result buffer");
   P->st = static_cast<LzState*>(at(P, P->W.st));
 
-  if (A->where == TE_HOST) {
+  if (P->streaming) {
+    // the host layout, built once; the solve copies it block by block
+    TE_CK(cudaHostAlloc(reinterpret_cast<void**>(&P->hcols),
+                        std::max<size_t>((size_t)sell.entries, 1) * 4, cudaHostAllocDefault),
+          "allocate pinned layout");
+    TE_CK(cudaHostAlloc(&P->hvals, std::max<size_t>((size_t)sell.entries, 1) * velt,
+                        cudaHostAllocDefault),
+          "allocate pinned layout");
+    if (!build_sell_host(sell, A->col_idx, A->values, in_type, P->vk, A->n, P->hcols, P->hvals))
+      return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
+    TE_CK(cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking), "create copy stream");
+    for (cudaEvent_t* e : {&P->ev_ready[0], &P->ev_ready[1], &P->ev_free[0], &P->ev_free[1],
+                           &P->ev_fork, &P->ev_join})
+      TE_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "create event");
+  } else if (A->where == TE_HOST) {
     TE_CK(cudaMalloc(&P->owned_csr, csr_bytes), "allocate device CSR");
     char* b = static_cast<char*>(P->owned_csr);
     int64_t* drp = reinterpret_cast<int64_t*>(b);
@@ -658,14 +797,16 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   // zero the solver vectors and state (the padded rows of V, y and w and the
   // empty rows of y must stay zero); the SELL arrays are written below
   TE_CK(cudaMemsetAsync(P->work, 0, P->W.slices, s), "clear work memory");
-  // column indices must lie in [0, n)
-  int* dflag = static_cast<int*>(at(P, P->W.flag));
-  TE_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s), "clear flag");
-  TE_CK(launch_validate_cols(P->ci, P->nnz, P->n, dflag, s), "validate columns");
-  int hflag = 0;
-  TE_CK(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
-  TE_CK(cudaStreamSynchronize(s), "plan setup");
-  if (hflag) return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
+  if (!P->streaming) {
+    // column indices must lie in [0, n)
+    int* dflag = static_cast<int*>(at(P, P->W.flag));
+    TE_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s), "clear flag");
+    TE_CK(launch_validate_cols(P->ci, P->nnz, P->n, dflag, s), "validate columns");
+    int hflag = 0;
+    TE_CK(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
+    TE_CK(cudaStreamSynchronize(s), "plan setup");
+    if (hflag) return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
+  }
   // the SELL copy of the matrix that the solve streams
   P->sell.slices = static_cast<SellSlice*>(at(P, P->W.slices));
   P->sell.vout = static_cast<int32_t*>(at(P, P->W.vout));
@@ -679,9 +820,12 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   void* vals64 = P->W.svals64 ? at(P, P->W.svals64) : nullptr;
   P->sell.vk = P->vk;
   P->sell.lscale = P->W.lscale ? static_cast<const float*>(at(P, P->W.lscale)) : nullptr;
-  TE_CK(upload_sell(in_type, sell, P->rp, P->ci, P->val, P->n, P->nnz, P->sell, vals64,
-                    P->W.lscale ? static_cast<float*>(at(P, P->W.lscale)) : nullptr, s),
-        "build the SELL layout");
+  if (P->streaming)
+    TE_CK(upload_meta(sell, P->sell, s), "upload the SELL layout");
+  else
+    TE_CK(upload_sell(in_type, sell, P->rp, P->ci, P->val, P->n, P->nnz, P->sell, vals64,
+                      P->W.lscale ? static_cast<float*>(at(P, P->W.lscale)) : nullptr, s),
+          "build the SELL layout");
   if (P->refine) {
     P->sell64 = P->sell;
     P->sell64.vk = TE_F64;
@@ -737,6 +881,10 @@ te_status te_plan_status(te_plan* P) {
 }
 
 int32_t te_plan_kernel_count(const te_plan* P) { return P ? P->nkernels : 0; }
+
+int64_t te_plan_stream_blocks(const te_plan* P) {
+  return (P && P->streaming) ? (int64_t)P->blocks.size() : 0;
+}
 
 te_status te_plan_profile(te_plan* P, double* ms, int32_t* launches, double* bytes,
                           void* stream) {

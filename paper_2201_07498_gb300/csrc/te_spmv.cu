@@ -20,6 +20,7 @@
 // uses binary64 FMA.  Pieces of a cut row leave partial sums that a second
 // kernel adds in piece order (deterministic).
 #include <algorithm>
+#include <thread>
 
 #include "te_common.cuh"
 #include "te_internal.h"
@@ -119,6 +120,64 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
 // layout conversion: one thread per lane, entries k = 0..len-1 (padding:
 // column 0, value 0)
 // ---------------------------------------------------------------------------
+// Host build of the SELL arrays (for a matrix that stays in host memory and
+// is streamed to the device in row blocks): the same arrangement the device
+// build produces; binary64 -> binary32 rounds to nearest even.  Threads split
+// the slices; the output does not depend on their number.  Returns false if a
+// column index lies outside [0, n).
+template <typename Vin, typename Vout>
+static bool build_sell_host_t(const SellHost& H, const int32_t* ci, const Vin* val, int64_t n,
+                              int32_t* cols, Vout* vals) {
+  const int64_t S = (int64_t)H.slices.size();
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > 64) nt = 64;
+  std::vector<int> bad(nt, 0);
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) {
+    th.emplace_back([&, t] {
+      for (int64_t sl = (int64_t)t; sl < S; sl += nt) {
+        const SellSlice& q = H.slices[(size_t)sl];
+        for (int lane = 0; lane < SELL_C; ++lane) {
+          const size_t l = (size_t)sl * SELL_C + lane;
+          const int64_t src = H.vsrc[l];
+          const int len = H.vlen[l];
+          for (int k = 0; k < q.len; ++k) {
+            const int64_t dst = q.base + (int64_t)k * SELL_C + lane;
+            if (k < len) {
+              const int32_t c = ci[src + k];
+              if (c < 0 || (int64_t)c >= n) bad[t] = 1;
+              cols[dst] = c;
+              vals[dst] = (Vout)val[src + k];
+            } else {
+              cols[dst] = 0;
+              vals[dst] = (Vout)0;
+            }
+          }
+        }
+      }
+    });
+  }
+  for (auto& x : th) x.join();
+  for (int b : bad)
+    if (b) return false;
+  return true;
+}
+
+bool build_sell_host(const SellHost& H, const int32_t* ci, const void* val, int in_type, int vk,
+                     int64_t n, int32_t* cols, void* vals) {
+  if (in_type == TE_F64 && vk == TE_F64)
+    return build_sell_host_t(H, ci, static_cast<const double*>(val), n, cols,
+                             static_cast<double*>(vals));
+  if (in_type == TE_F64 && vk == TE_F32)
+    return build_sell_host_t(H, ci, static_cast<const double*>(val), n, cols,
+                             static_cast<float*>(vals));
+  if (in_type == TE_F32 && vk == TE_F32)
+    return build_sell_host_t(H, ci, static_cast<const float*>(val), n, cols,
+                             static_cast<float*>(vals));
+  return false;
+}
+
 // Vin -> Vout: binary64 -> binary32 rounds to nearest even (__double2float_rn)
 template <typename Vin, typename Vout>
 TE_DEV Vout convert_value(Vin v) {
@@ -219,6 +278,7 @@ struct SpmvArgs {
   const int32_t* cols;
   const void* vals;
   const float* lscale;  // FP8: per-lane scale
+  int64_t ebase;        // first layout entry held by cols/vals
   const void* x;
   void* y;
   void* vpart;
@@ -272,8 +332,8 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
   const SellSlice sl = a.slices[slice];
   const int32_t out = a.vout[(int64_t)slice * SELL_C + lane];
   const uint64_t pol = policy_evict_first();
-  const int32_t* cp = a.cols + sl.base + lane;
-  const store_t* vp = static_cast<const store_t*>(a.vals) + sl.base + lane;
+  const int32_t* cp = a.cols + (sl.base - a.ebase) + lane;
+  const store_t* vp = static_cast<const store_t*>(a.vals) + (sl.base - a.ebase) + lane;
   const x_t* x = static_cast<const x_t*>(a.x);
   acc_t acc0, acc1;
   acc_zero<P>(acc0);
@@ -379,13 +439,15 @@ cudaError_t launch_spmv(int prec, const DevSell& S, const void* x, void* y, bool
   a.cols = S.cols;
   a.vals = S.vals;
   a.lscale = S.lscale;
+  a.ebase = S.ebase;
   a.x = x;
   a.y = y;
   a.vpart = S.vpart;
   a.nslices = S.nslices;
   if (prec == PREC_DDD) {
-    if (S.vk != TE_F64) return cudaErrorInvalidValue;
-    return launch_spmv_t<PREC_DDD, TE_F64, true>(a, S, s);
+    if (S.vk == TE_F64) return launch_spmv_t<PREC_DDD, TE_F64, true>(a, S, s);
+    if (S.vk == TE_F32) return launch_spmv_t<PREC_DDD, TE_F32, true>(a, S, s);
+    return cudaErrorInvalidValue;
   }
 #define TE_SPMV_FDF(VK)                                              \
   if (S.vk == VK) {                                                  \
