@@ -273,6 +273,64 @@ te_status te_quantize(const te_csr* A, int32_t to, void* out, float* row_scale, 
  * of eigenvectors).  1 <= K <= 64.  Synchronises `stream`. */
 te_status te_gram(int64_t n, int32_t K, const double* U, double* G, void* stream);
 
+/* ---- serving engine: continuous batching of many small solves ----
+ *
+ * Not in the paper (a serving front end for its solver).  A server keeps up
+ * to max_slots solves resident on the device, each with its own matrix
+ * layout, Krylov basis and tridiagonal, and advances every resident solve by
+ * one Lanczos step per te_server_step: one batched SpMV launch, one batched
+ * launch per basis pass (and per restart pass), replayed as one captured
+ * CUDA graph.  A solve that reaches its m-th step is finished (Jacobi, Ritz
+ * vectors) and its slot and work memory are freed at once; pending requests
+ * are admitted, in submission order, whenever a slot and enough memory of the
+ * device pool are free, so requests that arrive while others run join the
+ * next step.  Each solve is given a number of pass CTAs that depends on its
+ * own size only, so its result is the same, bit for bit, whatever else runs
+ * beside it.
+ *
+ * Forms: FDF or BDF (binary32 basis, double-float arithmetic; binary32 or
+ * bfloat16 values; bfloat16 needs values_f64).  Calls on one server must not
+ * overlap (one host thread at a time). */
+typedef struct te_server te_server;
+
+typedef struct {
+  int32_t max_slots;          /* resident solves, 1 .. 64 */
+  int32_t max_krylov_steps;   /* largest m accepted, <= 64 */
+  size_t device_budget_bytes; /* device pool for resident solves and finished results */
+  int32_t use_graph;          /* replay each engine step as one captured CUDA graph */
+} te_server_options;
+
+/* Create a server (allocates the pool; work is issued on a stream the server
+ * owns). */
+te_status te_server_create(const te_server_options* opt, te_server** out);
+
+/* Queue one solve: A in host memory (copied by the call; it may be freed on
+ * return), K eigenpairs largest in modulo from m = krylov_steps Lanczos steps,
+ * start vector from `seed`.  *ticket identifies the request.  Malformed input
+ * is rejected here (TE_ERR_INVALID_ARG); a request larger than the whole pool
+ * fails with TE_ERR_OUT_OF_MEMORY when it reaches the head of the queue. */
+te_status te_server_submit(te_server* srv, const te_csr* A, int32_t K, int32_t krylov_steps,
+                           te_precision p, uint64_t seed, int64_t* ticket);
+
+/* One engine step: wait for the previous step, retire finished solves, admit
+ * pending ones, and launch one Lanczos step of every resident solve.  *live
+ * and *pending (may be NULL) receive the counts after admission.  Returns
+ * without waiting for the launched step. */
+te_status te_server_step(te_server* srv, int32_t* live, int32_t* pending);
+
+/* *done = 1 when the request has finished: eigvals (K), residual estimates
+ * (K, may be NULL) and, if eigvecs is not NULL, the n x K column-major Ritz
+ * vectors are written to host memory and the request is released; the call
+ * returns the request's own status.  *done = 0: nothing written. */
+te_status te_server_poll(te_server* srv, int64_t ticket, int32_t* done, double* eigvals,
+                         double* eigvecs, double* residuals);
+
+/* Resident and queued solves, pool bytes in use now and at most so far. */
+te_status te_server_stats(const te_server* srv, int32_t* live, int32_t* pending,
+                          size_t* pool_used, size_t* pool_peak);
+
+void te_server_destroy(te_server* srv);
+
 /* Host-side layout behind the SpMV (no GPU needed; row_ptr in host memory):
  * the SELL-C-sigma arrangement a plan builds (Kreutzer et al., SIAM J. Sci.
  * Comput. 2014).  Rows are cut into pieces of at most 64 entries; within each

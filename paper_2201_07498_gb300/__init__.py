@@ -18,7 +18,7 @@ from dataclasses import dataclass
 
 from . import _build
 
-__all__ = ["CSR", "Plan", "TEError", "topk_eigs", "spmv", "lanczos", "tridiag_eigs",
+__all__ = ["CSR", "Plan", "Server", "TEError", "topk_eigs", "spmv", "lanczos", "tridiag_eigs",
            "spmv_layout", "gram", "quantize", "library_path", "load_library", "PRECISIONS"]
 
 TE_F64, TE_F32, TE_BF16, TE_FP8_E4M3 = 0, 1, 2, 3
@@ -58,6 +58,11 @@ class te_options(ctypes.Structure):
                 ("matrix_budget_bytes", ctypes.c_size_t)]
 
 
+class te_server_options(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("max_krylov_steps", ctypes.c_int32),
+                ("device_budget_bytes", ctypes.c_size_t), ("use_graph", ctypes.c_int32)]
+
+
 # every symbol the header declares, with its ctypes signature
 _SIGS = {
     "te_default_options": (None, [ctypes.c_void_p]),
@@ -93,6 +98,16 @@ _SIGS = {
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "te_quantize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "te_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "te_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_int32, te_precision, ctypes.c_uint64,
+                                        ctypes.c_void_p]),
+    "te_server_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "te_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "te_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "te_server_destroy": (None, [ctypes.c_void_p]),
     "te_gram": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p]),
     "te_spmv_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -313,6 +328,80 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.te_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving engine (continuous batching of many small solves on the GPU):
+    submit host matrices, call step() repeatedly, poll() finished requests."""
+
+    def __init__(self, max_slots: int = 32, max_krylov_steps: int = 32,
+                 budget: int = 4 << 30, use_graph: bool = True):
+        self._lib = load_library()
+        o = te_server_options(max_slots, max_krylov_steps, budget, 1 if use_graph else 0)
+        h = ctypes.c_void_p()
+        _check(self._lib.te_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._meta = {}
+
+    def submit(self, host_csr, K: int, krylov_steps: int, precision="fdf", seed: int = 0) -> int:
+        """host_csr: an object with n, row_ptr, col, val (numpy); the values are
+        passed as binary64 (the library rounds them to the form's type)."""
+        import numpy as np
+        rp = np.ascontiguousarray(host_csr.row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(host_csr.col, dtype=np.int32)
+        va = np.ascontiguousarray(host_csr.val, dtype=np.float64)
+        A = te_csr(int(host_csr.n), len(ci), rp.ctypes.data, ci.ctypes.data, va.ctypes.data,
+                   None, TE_HOST, 1)
+        t = ctypes.c_int64()
+        _check(self._lib.te_server_submit(self._h, ctypes.byref(A), K, krylov_steps,
+                                          _prec(precision), seed, ctypes.byref(t)))
+        self._meta[t.value] = (int(host_csr.n), K)
+        return t.value
+
+    def step(self):
+        """One engine step; returns (resident, queued)."""
+        live, pend = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.te_server_step(self._h, ctypes.byref(live), ctypes.byref(pend)))
+        return live.value, pend.value
+
+    def poll(self, ticket: int, vectors: bool = True):
+        """None while running; else (eigvals [K], eigvecs [n, K] or None,
+        residual estimates [K]) as numpy arrays (raises on a failed request)."""
+        import numpy as np
+        n, K = self._meta[ticket]
+        ev = np.zeros(K)
+        res = np.zeros(K)
+        U = np.zeros((K, n)) if vectors else None
+        done = ctypes.c_int32()
+        rc = self._lib.te_server_poll(self._h, ticket, ctypes.byref(done),
+                                      ctypes.c_void_p(ev.ctypes.data),
+                                      None if U is None else ctypes.c_void_p(U.ctypes.data),
+                                      ctypes.c_void_p(res.ctypes.data))
+        if done.value:
+            del self._meta[ticket]
+        _check(rc)
+        if not done.value:
+            return None
+        return ev, (None if U is None else U.T), res
+
+    def stats(self):
+        live, pend = ctypes.c_int32(), ctypes.c_int32()
+        used, peak = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self._lib.te_server_stats(self._h, ctypes.byref(live), ctypes.byref(pend),
+                                         ctypes.byref(used), ctypes.byref(peak)))
+        return {"live": live.value, "pending": pend.value, "pool_used": used.value,
+                "pool_peak": peak.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.te_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

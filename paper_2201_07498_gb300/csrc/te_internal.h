@@ -208,6 +208,51 @@ cudaError_t launch_copy_out(LzState* st, const double* src, size_t count, int gr
 cudaError_t launch_gram(const double* U, int64_t n, int K, double* partials, int grid,
                         double* G, cudaStream_t s);
 
+// ---- serving engine: one launch per phase for every live solve ----
+constexpr int SRV_MAX_SLOTS = 64;  // solves resident at once
+constexpr int SRV_MAX_CTAS = 16;   // pass CTAs per solve (fixed by its size alone)
+
+// one live solve (FDF arithmetic: binary32 basis, binary32 or bfloat16 values)
+struct BatchSlot {
+  const SellSlice* slices;
+  const int32_t* vout;
+  const int32_t* cols;
+  const void* vals;
+  const LongRow* lrows;
+  void* vpart;
+  void* V;         // basis, n_pad x (m+1) binary32
+  void* ytil;      // SpMV output (double-float pairs)
+  void* w;         // first-sweep result
+  void* partials;  // ncta * PSTRIDE slots
+  LzState* st;
+  int64_t n, n_pad;
+  uint64_t seed;
+  double tol;
+  int vk, nslices, nlrows, m, K, step, ncta, pad_;
+};
+// the live solves of one engine step, with prefix offsets into the global
+// slice, cut-row and pass-block enumerations
+struct BatchTable {
+  int nslots, pad_;
+  int64_t slice_off[SRV_MAX_SLOTS + 1];
+  int64_t lrow_off[SRV_MAX_SLOTS + 1];
+  int item_off[SRV_MAX_SLOTS + 1];
+  BatchSlot slot[SRV_MAX_SLOTS];
+};
+constexpr int SRV_SPMV_BLOCKS = 1216;  // persistent grid of the batched SpMV (8 warps each)
+constexpr int SRV_FIN_BLOCKS = 608;    // persistent grid of the batched finaliser
+// y_s = M_s v_{s, step_s} for every slot (te_spmv.cu)
+cudaError_t launch_batch_spmv(const BatchTable* T, cudaStream_t s);
+// passes of the Lanczos step of every slot; restart = the breakdown passes
+// (te_reorth.cu); L: the launch configuration for the engine's largest m
+cudaError_t launch_batch_pass(int mode, const BatchTable* T, int restart, const PassLaunch& L,
+                              cudaStream_t s);
+cudaError_t batch_pass_prepare(const PassLaunch& L);  // outside stream capture
+// per-solve set-up kernel of a plan (te_solver.cu)
+cudaError_t launch_solve_begin(LzState* st, const double* v1, double* eigvecs, double* eigvals,
+                               double* plan_vecs, cudaStream_t s);
+double breakdown_tolerance(int prec);
+
 // ---- small utilities ----
 // record the thread-local message returned by te_last_error()
 void set_last_error(const std::string& msg);

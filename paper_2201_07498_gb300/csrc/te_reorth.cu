@@ -227,8 +227,12 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
 // ---------------------------------------------------------------------------
 // the pass kernel
 // ---------------------------------------------------------------------------
+// One CTA's share of a pass: CTA `cta` of `ncta` takes tiles cta, cta + ncta, ...
+// (the single-solve kernel passes blockIdx.x / gridDim.x; the batched kernel
+// of the serving engine maps its blocks onto the CTAs of several solves).
 template <int P, int MODE>
-__global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel(PassArgs a, size_t region) {
+__device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, const int cta,
+                                          const int ncta) {
   using Tr = PassTr<P>;
   using basis_t = typename Tr::basis_t;
   using vec_t = typename Tr::vec_t;
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
       const uint64_t pol = policy_evict_first();
       int it = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+      for (int64_t t = cta; t < tiles; t += ncta, ++it) {
         const int s = it % S, k = it / S;
         if (k > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)((k - 1) & 1), WAIT_LIMIT)) {
           atomicExch(&st->status, (int)TE_ERR_TIMEOUT);
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
   basis_t* Vout = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_out * a.ld;
 
   int it = 0;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+  for (int64_t t = cta; t < tiles; t += ncta, ++it) {
     const int64_t row = t * TILE_R + tid;
     // the source value is fetched before waiting on the tile to overlap latency
     vec_t x = vec_zero<P>();
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
         acc_t v = dots[q];
         if constexpr (P == PREC_FDF) v = warp_sum(v);
         else v = warp_sum(v);
-        if (lane == 0) put_partial<P>(a.partials, (size_t)blockIdx.x * PSTRIDE + jj, v);
+        if (lane == 0) put_partial<P>(a.partials, (size_t)cta * PSTRIDE + jj, v);
       }
     }
   }
@@ -560,8 +564,8 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
         t1 = acc_merge<P>(t1, red[2 * w]);
         t2 = acc_merge<P>(t2, red[2 * w + 1]);
       }
-      put_partial<P>(a.partials, (size_t)blockIdx.x * PSTRIDE + MAX_M, t1);
-      put_partial<P>(a.partials, (size_t)blockIdx.x * PSTRIDE + MAX_M + 1, t2);
+      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + MAX_M, t1);
+      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + MAX_M + 1, t2);
     }
   }
 
@@ -570,7 +574,7 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
   named_bar_sync(1, CONSUMERS);
   if (tid == 0) {
     unsigned int tk = atomicAdd(&st->ticket, 1u);
-    *lastflag = (tk == gridDim.x - 1) ? 1 : 0;
+    *lastflag = (tk == (unsigned)ncta - 1) ? 1 : 0;
   }
   named_bar_sync(1, CONSUMERS);
   if (*lastflag == 0) return;
@@ -579,7 +583,7 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
   for (int q = wid; q < slots; q += CONSUMERS / 32) {
     const int slot = (MODE == MODE_AXPY_STORE) ? MAX_M + q : q;
     acc_t acc = zero_acc<P>();
-    for (int b = lane; b < (int)gridDim.x; b += 32)
+    for (int b = lane; b < ncta; b += 32)
       add_partial<P>(acc, a.partials, (size_t)b * PSTRIDE + slot);
     acc = warp_sum(acc);
     if (lane == 0) tot[q] = acc_to_double<P>(acc);
@@ -590,6 +594,105 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel
     __threadfence();
     st->ticket = 0;
   }
+}
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(P)) pass_kernel(PassArgs a, size_t region) {
+  pass_body<P, MODE>(a, region, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// serving engine: one pass for every live solve.  Block b is CTA
+// b - item_off[s] of solve s (each solve has a fixed number of CTAs that
+// depends only on its size), so every solve's sums run in the same order
+// whatever else shares the launch.  The arguments are those the single-solve
+// plan uses at the solve's current step.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(PREC_FDF))
+    batch_pass_kernel(const BatchTable* T, int restart, size_t region) {
+  const int ns = T->nslots;
+  const int item = (int)blockIdx.x;
+  if (item >= T->item_off[ns]) return;
+  int sidx = 0;
+  while (T->item_off[sidx + 1] <= item) ++sidx;
+  const BatchSlot& B = T->slot[sidx];
+  const int i = B.step;
+  if (restart && i + 1 >= B.m) return;  // no restart after the last step
+  PassArgs a;
+  memset(&a, 0, sizeof(a));
+  a.V = B.V;
+  a.Vmut = B.V;
+  a.ld = B.n_pad;
+  a.n = B.n;
+  a.m = B.m;
+  a.K = B.K;
+  a.seed = B.seed;
+  a.tol = B.tol;
+  a.st = B.st;
+  a.partials = B.partials;
+  a.step = i;
+  a.nb = i + 1;
+  if (!restart) {
+    a.xsrc = X_VEC;
+    if (MODE == MODE_DOT) {
+      a.xvec = B.ytil;
+      a.fin = FIN_DOT_STEP;
+    } else if (MODE == MODE_AXPY_DOT) {
+      a.xvec = B.ytil;
+      a.wout = B.w;
+      a.fin = FIN_AXPYDOT_STEP;
+      a.exact_tail = 2;
+    } else {
+      a.xvec = B.w;
+      a.col_out = i + 1;
+      a.fin = FIN_STORE_STEP;
+      a.exact_tail = 0;
+    }
+  } else {
+    a.only_on_restart = 1;
+    a.exact_tail = i + 1;
+    if (MODE == MODE_DOT) {
+      a.xsrc = X_RANDOM;
+      a.fin = FIN_DOT_RESTART;
+    } else if (MODE == MODE_AXPY_DOT) {
+      a.xsrc = X_RANDOM;
+      a.wout = B.w;
+      a.fin = FIN_AXPYDOT;
+    } else {
+      a.xsrc = X_VEC;
+      a.xvec = B.w;
+      a.col_out = i + 1;
+      a.fin = FIN_STORE_RESTART;
+    }
+  }
+  pass_body<PREC_FDF, MODE>(a, region, item - T->item_off[sidx], B.ncta);
+}
+
+cudaError_t batch_pass_prepare(const PassLaunch& L) {
+  cudaError_t e = cudaFuncSetAttribute(batch_pass_kernel<MODE_DOT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_pass_kernel<MODE_AXPY_DOT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_pass_kernel<MODE_AXPY_STORE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+  return e;
+}
+
+cudaError_t launch_batch_pass(int mode, const BatchTable* T, int restart, const PassLaunch& L,
+                              cudaStream_t s) {
+  const int grid = SRV_MAX_SLOTS * SRV_MAX_CTAS;
+  if (mode == MODE_DOT)
+    batch_pass_kernel<MODE_DOT><<<grid, PASS_THREADS, L.smem, s>>>(T, restart, L.region);
+  else if (mode == MODE_AXPY_DOT)
+    batch_pass_kernel<MODE_AXPY_DOT><<<grid, PASS_THREADS, L.smem, s>>>(T, restart, L.region);
+  else if (mode == MODE_AXPY_STORE)
+    batch_pass_kernel<MODE_AXPY_STORE><<<grid, PASS_THREADS, L.smem, s>>>(T, restart, L.region);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,634 @@
+// te_server.cu - serving engine: continuous batching of many small Top-K
+// solves on one GPU.
+//
+// Host side.  A first-fit pool allocator hands out device memory from one
+// allocation; requests wait in submission order until a slot and enough pool
+// memory are free; admission builds the solve's SELL layout and state on the
+// device and runs its start-vector pass; every engine step then advances all
+// resident solves by one Lanczos step with the batched kernels (one launch per
+// phase, replayed as one captured graph that reads a device table of the
+// resident solves).  A solve that completes its m steps gets its Jacobi and
+// Ritz kernels in the same step; its work memory is freed at the next step and
+// its Ritz vectors stay in the pool until the client polls them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "te_internal.h"
+#include "topk_eigs.h"
+
+using namespace te;
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+te_status srv_fail(te_status s, const std::string& m) {
+  set_last_error(m);
+  return s;
+}
+te_status srv_cuda(cudaError_t e, const char* what) {
+  set_last_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+                 ")");
+  return e == cudaErrorMemoryAllocation ? TE_ERR_OUT_OF_MEMORY : TE_ERR_CUDA;
+}
+#define SRV_CK(call, what)                              \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return srv_cuda(e_, what);   \
+  } while (0)
+
+// First-fit allocator over one device allocation (offsets, 256-byte aligned);
+// freed blocks merge with free neighbours.
+class Pool {
+ public:
+  char* base = nullptr;
+  size_t size = 0, used = 0, peak = 0;
+  cudaError_t init(size_t bytes) {
+    size = al256(bytes);
+    cudaError_t e = cudaMalloc(&base, size);
+    if (e == cudaSuccess) free_[0] = size;
+    return e;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = al256(std::max<size_t>(bytes, 1));
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rest = it->second - bytes;
+      const size_t roff = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[roff] = rest;
+      used += bytes;
+      peak = std::max(peak, used);
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = al256(std::max<size_t>(bytes, 1));
+    used -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  ~Pool() {
+    if (base) cudaFree(base);
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+};
+
+enum ReqState { REQ_PENDING = 0, REQ_RUNNING = 1, REQ_FINISHED = 2 };
+
+struct Request {
+  int64_t ticket = 0;
+  int64_t n = 0, nnz = 0, n_pad = 0;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  std::vector<char> vals;  // binary64 or binary32, as given
+  int in_type = TE_F32, vk = TE_F32;
+  int K = 0, m = 0, ncta = 1;
+  uint64_t seed = 0;
+  int state = REQ_PENDING, status = 0, slot = -1, step = 0;
+  size_t work_off = 0, work_bytes = 0, res_off = 0, res_bytes = 0;
+  BatchSlot desc{};
+  std::vector<double> theta, resid;
+};
+
+struct SlotResult {  // pinned, written by the finishing copies
+  double theta[MAX_M];
+  double resid[MAX_M];
+  int hdr[4];  // restart_flag, restarts, status, sweeps (as in LzState)
+};
+
+int64_t pad_rows(int64_t n) { return (n + TILE_R - 1) / TILE_R * TILE_R; }
+
+// pass CTAs of a solve: a function of its size alone
+int ctas_for(int64_t n_pad) {
+  const int64_t tiles = n_pad / TILE_R;
+  int64_t c = (tiles + 3) / 4;
+  if (c < 1) c = 1;
+  if (c > SRV_MAX_CTAS) c = SRV_MAX_CTAS;
+  return (int)c;
+}
+
+}  // namespace
+
+struct te_server {
+  int max_slots = 0, max_m = 0, use_graph = 1, num_sms = 0;
+  cudaStream_t s = nullptr, ps = nullptr;  // engine stream, poll stream
+  Pool pool;
+  PassLaunch Lpass{}, Lritz{}, Lsto{};
+  BatchTable* table_h = nullptr;
+  BatchTable* table_d = nullptr;
+  SlotResult* res_h = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool inflight = false;
+  int64_t next_ticket = 1;
+  std::map<int64_t, Request*> reqs;
+  std::deque<Request*> pending;
+  std::vector<Request*> slots;
+  std::vector<std::pair<size_t, size_t>> deferred;  // pool blocks to free after the next sync
+  std::vector<int> finishing;                       // slots whose solve ends this step
+};
+
+namespace {
+
+// the batched step: SpMV (+ cut rows), three passes, three restart passes
+cudaError_t enqueue_step(te_server* S, cudaStream_t s) {
+  cudaError_t e = launch_batch_spmv(S->table_d, s);
+  for (int restart = 0; restart < 2 && e == cudaSuccess; ++restart) {
+    if (e == cudaSuccess) e = launch_batch_pass(MODE_DOT, S->table_d, restart, S->Lpass, s);
+    if (e == cudaSuccess) e = launch_batch_pass(MODE_AXPY_DOT, S->table_d, restart, S->Lpass, s);
+    if (e == cudaSuccess)
+      e = launch_batch_pass(MODE_AXPY_STORE, S->table_d, restart, S->Lpass, s);
+  }
+  return e;
+}
+
+// device work memory of a request: the SELL copy, the solver vectors and
+// state; `tmp`: what only the admission needs; `res`: the Ritz vectors
+struct AdmitLayout {
+  size_t slices, vout, cols, vals, lrows, vpart, V, ytil, w, partials, st, total;
+  size_t t_rp, t_ci, t_val, t_src, t_len, t_q, t_total;
+};
+
+AdmitLayout admit_layout(const Request& R, const SellHost& H) {
+  AdmitLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off = al256(off + std::max<size_t>(b, 1));
+    return o;
+  };
+  const size_t velt = R.vk == TE_BF16 ? 2 : 4;
+  L.slices = take(H.slices.size() * sizeof(SellSlice));
+  L.vout = take(H.vout.size() * sizeof(int32_t));
+  L.cols = take((size_t)H.entries * 4);
+  L.vals = take((size_t)H.entries * velt);
+  L.lrows = take(H.lrows.size() * sizeof(LongRow));
+  L.vpart = take((size_t)H.pieces * 8);
+  L.V = take((size_t)R.n_pad * (R.m + 1) * 4);
+  L.ytil = take((size_t)R.n_pad * 8);
+  L.w = take((size_t)R.n_pad * 8);
+  L.partials = take((size_t)R.ncta * PSTRIDE * 8);
+  L.st = take(sizeof(LzState));
+  L.total = off;
+  off = 0;
+  L.t_rp = take((size_t)(R.n + 1) * 8);
+  L.t_ci = take((size_t)R.nnz * 4);
+  L.t_val = take((size_t)R.nnz * (R.in_type == TE_F64 ? 8 : 4));
+  L.t_src = take(H.vsrc.size() * 8);
+  L.t_len = take(H.vlen.size() * 4);
+  L.t_q = take(R.vk == TE_BF16 ? (size_t)R.nnz * 2 : 0);
+  L.t_total = off;
+  return L;
+}
+
+// Try to admit R into slot k.  Returns 1 on success, 0 when the pool has no
+// room now, -1 on a CUDA error (status set).
+int admit(te_server* S, Request* R, int k, te_status* err) {
+  SellHost H;
+  std::string perr;
+  make_sell(R->rp.data(), R->n, R->nnz, H, perr);  // validated at submit
+  const AdmitLayout L = admit_layout(*R, H);
+  size_t work = 0, res = 0, tmp = 0;
+  if (!S->pool.alloc(L.total, &work)) return 0;
+  if (!S->pool.alloc((size_t)R->n * R->K * 8, &res)) {
+    S->pool.release(work, L.total);
+    return 0;
+  }
+  if (!S->pool.alloc(L.t_total, &tmp)) {
+    S->pool.release(work, L.total);
+    S->pool.release(res, (size_t)R->n * R->K * 8);
+    return 0;
+  }
+  R->work_off = work;
+  R->work_bytes = L.total;
+  R->res_off = res;
+  R->res_bytes = (size_t)R->n * R->K * 8;
+  S->deferred.push_back({tmp, L.t_total});
+  char* W = S->pool.base + work;
+  char* T = S->pool.base + tmp;
+  cudaStream_t s = S->s;
+  cudaError_t e = cudaMemsetAsync(W, 0, L.total, s);
+  auto h2d = [&](void* dst, const void* src, size_t b) {
+    if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s);
+  };
+  h2d(T + L.t_rp, R->rp.data(), (size_t)(R->n + 1) * 8);
+  h2d(T + L.t_ci, R->ci.data(), (size_t)R->nnz * 4);
+  h2d(T + L.t_val, R->vals.data(), R->vals.size());
+  h2d(T + L.t_src, H.vsrc.data(), H.vsrc.size() * 8);
+  h2d(T + L.t_len, H.vlen.data(), H.vlen.size() * 4);
+  h2d(W + L.slices, H.slices.data(), H.slices.size() * sizeof(SellSlice));
+  h2d(W + L.vout, H.vout.data(), H.vout.size() * 4);
+  h2d(W + L.lrows, H.lrows.data(), H.lrows.size() * sizeof(LongRow));
+  const void* vin = T + L.t_val;
+  int in_type = R->in_type;
+  if (e == cudaSuccess && R->vk == TE_BF16) {
+    e = launch_quantize(TE_BF16, reinterpret_cast<const int64_t*>(T + L.t_rp),
+                        reinterpret_cast<const double*>(T + L.t_val), R->n, R->nnz, T + L.t_q,
+                        nullptr, s);
+    vin = T + L.t_q;
+    in_type = TE_BF16;
+  }
+  if (e == cudaSuccess)
+    e = launch_sell_build(in_type, R->vk, reinterpret_cast<const int32_t*>(T + L.t_ci), vin,
+                          reinterpret_cast<const SellSlice*>(W + L.slices),
+                          reinterpret_cast<const int64_t*>(T + L.t_src),
+                          reinterpret_cast<const int32_t*>(T + L.t_len), (int)H.slices.size(),
+                          reinterpret_cast<int32_t*>(W + L.cols), W + L.vals, nullptr, nullptr,
+                          nullptr, s);
+  LzState* st = reinterpret_cast<LzState*>(W + L.st);
+  double* U = reinterpret_cast<double*>(S->pool.base + res);
+  if (e == cudaSuccess) e = launch_solve_begin(st, nullptr, U, nullptr, nullptr, s);
+  // the start vector: stream 0 of the seed, normalised (the init pass)
+  BatchSlot& B = R->desc;
+  B.slices = reinterpret_cast<const SellSlice*>(W + L.slices);
+  B.vout = reinterpret_cast<const int32_t*>(W + L.vout);
+  B.cols = reinterpret_cast<const int32_t*>(W + L.cols);
+  B.vals = W + L.vals;
+  B.lrows = reinterpret_cast<const LongRow*>(W + L.lrows);
+  B.vpart = W + L.vpart;
+  B.V = W + L.V;
+  B.ytil = W + L.ytil;
+  B.w = W + L.w;
+  B.partials = W + L.partials;
+  B.st = st;
+  B.n = R->n;
+  B.n_pad = R->n_pad;
+  B.seed = R->seed;
+  B.tol = breakdown_tolerance(PREC_FDF);
+  B.vk = R->vk;
+  B.nslices = (int)H.slices.size();
+  B.nlrows = (int)H.lrows.size();
+  B.m = R->m;
+  B.K = R->K;
+  B.step = 0;
+  B.ncta = R->ncta;
+  if (e == cudaSuccess) {
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.V = B.V;
+    a.Vmut = B.V;
+    a.ld = B.n_pad;
+    a.n = B.n;
+    a.m = B.m;
+    a.K = B.K;
+    a.seed = B.seed;
+    a.tol = B.tol;
+    a.st = st;
+    a.partials = B.partials;
+    a.nb = 0;
+    a.col_out = 0;
+    a.xsrc = X_V1;
+    a.fin = FIN_STORE_INIT;
+    PassLaunch Li = S->Lsto;
+    Li.grid = R->ncta;
+    e = launch_pass(PREC_FDF, MODE_AXPY_STORE, a, Li, s);
+  }
+  if (e != cudaSuccess) {
+    *err = srv_cuda(e, "admission");
+    return -1;
+  }
+  R->slot = k;
+  R->state = REQ_RUNNING;
+  R->step = 0;
+  // the host copies are no longer needed
+  std::vector<int64_t>().swap(R->rp);
+  std::vector<int32_t>().swap(R->ci);
+  std::vector<char>().swap(R->vals);
+  return 1;
+}
+
+// Jacobi, selection and Ritz vectors of a solve that completed its m steps,
+// then its eigenvalues, residual estimates and status to the pinned slot area
+cudaError_t enqueue_finish(te_server* S, Request* R) {
+  const BatchSlot& B = R->desc;
+  JacobiArgs j;
+  memset(&j, 0, sizeof(j));
+  j.alpha = B.st->alpha;
+  j.beta = B.st->beta;
+  j.s = B.st->s;
+  j.m = B.m;
+  j.K = B.K;
+  j.which = TE_WHICH_LARGEST_MAGNITUDE;
+  j.theta_out = B.st->theta_sel;
+  j.C_out = B.st->C;
+  j.resid_out = B.st->resid_est;
+  j.st = B.st;
+  cudaError_t e = launch_jacobi(j, S->s);
+  if (e == cudaSuccess) {
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.V = B.V;
+    a.Vmut = B.V;
+    a.ld = B.n_pad;
+    a.n = B.n;
+    a.m = B.m;
+    a.K = B.K;
+    a.st = B.st;
+    a.partials = B.partials;
+    a.nb = B.m;
+    a.fin = FIN_NONE;
+    PassLaunch Lr = S->Lritz;
+    Lr.grid = R->ncta;
+    e = launch_pass(PREC_FDF, MODE_RITZ, a, Lr, S->s);
+  }
+  SlotResult* out = S->res_h + R->slot;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out->theta, B.st->theta_sel, sizeof(double) * B.K, cudaMemcpyDeviceToHost,
+                        S->s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out->resid, B.st->resid_est, sizeof(double) * B.K,
+                        cudaMemcpyDeviceToHost, S->s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out->hdr, &B.st->restart_flag, sizeof(out->hdr), cudaMemcpyDeviceToHost,
+                        S->s);
+  return e;
+}
+
+te_status check_request(const te_csr* A, int32_t K, int32_t m, te_precision p, int max_m) {
+  if (!A) return srv_fail(TE_ERR_INVALID_ARG, "A is NULL");
+  if (A->where != TE_HOST) return srv_fail(TE_ERR_INVALID_ARG, "the server takes host matrices");
+  if (A->n < 1 || A->n >= (int64_t)1 << 31 || A->nnz < 0)
+    return srv_fail(TE_ERR_INVALID_ARG, "n or nnz out of range");
+  if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->values)))
+    return srv_fail(TE_ERR_INVALID_ARG, "CSR arrays must not be NULL");
+  if (A->row_scale) return srv_fail(TE_ERR_UNSUPPORTED, "row_scale is reserved (must be NULL)");
+  if (!(p.arithmetic == TE_F64 && p.vectors == TE_F32 &&
+        (p.values == TE_F32 || p.values == TE_BF16)))
+    return srv_fail(TE_ERR_UNSUPPORTED, "the server runs FDF and BDF");
+  if (p.values == TE_BF16 && A->values_f64 != 1)
+    return srv_fail(TE_ERR_INVALID_ARG, "bfloat16 storage is built from binary64 values");
+  if (K < 1 || m < K || (int64_t)m > A->n)
+    return srv_fail(TE_ERR_INVALID_ARG, "need 1 <= K <= krylov_steps <= n");
+  if (m > max_m) return srv_fail(TE_ERR_UNSUPPORTED, "krylov_steps above the server's maximum");
+  return TE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+te_status te_server_create(const te_server_options* o, te_server** out) {
+  if (!o || !out) return srv_fail(TE_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (o->max_slots < 1 || o->max_slots > SRV_MAX_SLOTS)
+    return srv_fail(TE_ERR_INVALID_ARG, "max_slots must be in [1, 64]");
+  if (o->max_krylov_steps < 1 || o->max_krylov_steps > MAX_M)
+    return srv_fail(TE_ERR_INVALID_ARG, "max_krylov_steps must be in [1, 64]");
+  if (o->device_budget_bytes < ((size_t)1 << 20))
+    return srv_fail(TE_ERR_INVALID_ARG, "device_budget_bytes must be at least 1 MiB");
+  te_server* S = new te_server();
+  struct Guard {
+    te_server*& p;
+    bool keep = false;
+    ~Guard() {
+      if (!keep) te_server_destroy(p);
+    }
+  } guard{S};
+  S->max_slots = o->max_slots;
+  S->max_m = o->max_krylov_steps;
+  S->use_graph = o->use_graph != 0;
+  S->slots.assign(S->max_slots, nullptr);
+  int dev = 0;
+  SRV_CK(cudaGetDevice(&dev), "cudaGetDevice");
+  SRV_CK(cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
+  SRV_CK(cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking), "create stream");
+  SRV_CK(cudaStreamCreateWithFlags(&S->ps, cudaStreamNonBlocking), "create stream");
+  SRV_CK(cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming), "create event");
+  SRV_CK(S->pool.init(o->device_budget_bytes), "allocate the device pool");
+  SRV_CK(cudaMallocHost(&S->table_h, sizeof(BatchTable)), "allocate the step table");
+  SRV_CK(cudaMalloc(&S->table_d, sizeof(BatchTable)), "allocate the step table");
+  SRV_CK(cudaMallocHost(&S->res_h, sizeof(SlotResult) * SRV_MAX_SLOTS), "allocate results");
+  memset(S->table_h, 0, sizeof(BatchTable));
+  SRV_CK(cudaMemcpy(S->table_d, S->table_h, sizeof(BatchTable), cudaMemcpyHostToDevice),
+         "clear the step table");
+  SRV_CK(jacobi_prepare(), "kernel set-up");
+  SRV_CK(pass_config(PREC_FDF, MODE_AXPY_DOT, S->max_m, 1, S->num_sms, S->Lpass),
+         "configure passes");
+  SRV_CK(pass_config(PREC_FDF, MODE_AXPY_STORE, S->max_m, 1, S->num_sms, S->Lsto),
+         "configure passes");
+  SRV_CK(pass_config(PREC_FDF, MODE_RITZ, S->max_m, S->max_m, S->num_sms, S->Lritz),
+         "configure passes");
+  SRV_CK(pass_config(PREC_FDF, MODE_DOT, S->max_m, 1, S->num_sms, S->Lpass), "configure passes");
+  SRV_CK(batch_pass_prepare(S->Lpass), "configure batched passes");
+  if (S->use_graph) {
+    cudaGraph_t g = nullptr;
+    SRV_CK(cudaStreamBeginCapture(S->s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = enqueue_step(S, S->s);
+    cudaError_t e2 = cudaStreamEndCapture(S->s, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return srv_cuda(e != cudaSuccess ? e : e2, "capture the engine step");
+    }
+    e = cudaGraphInstantiate(&S->gexec, g, 0);
+    cudaGraphDestroy(g);
+    SRV_CK(e, "instantiate the engine step");
+  }
+  guard.keep = true;
+  *out = S;
+  return TE_OK;
+}
+
+void te_server_destroy(te_server* S) {
+  if (!S) return;
+  if (S->s) cudaStreamSynchronize(S->s);
+  for (auto& kv : S->reqs) delete kv.second;
+  if (S->gexec) cudaGraphExecDestroy(S->gexec);
+  if (S->ev) cudaEventDestroy(S->ev);
+  if (S->table_h) cudaFreeHost(S->table_h);
+  if (S->table_d) cudaFree(S->table_d);
+  if (S->res_h) cudaFreeHost(S->res_h);
+  if (S->s) cudaStreamDestroy(S->s);
+  if (S->ps) cudaStreamDestroy(S->ps);
+  delete S;
+}
+
+te_status te_server_submit(te_server* S, const te_csr* A, int32_t K, int32_t m, te_precision p,
+                           uint64_t seed, int64_t* ticket) {
+  if (!S || !ticket) return srv_fail(TE_ERR_INVALID_ARG, "NULL argument");
+  te_status r = check_request(A, K, m, p, S->max_m);
+  if (r != TE_OK) return r;
+  // validate the CSR on the host now, so that admission cannot fail on it
+  const int64_t* rp = A->row_ptr;
+  if (rp[0] != 0 || rp[A->n] != A->nnz) return srv_fail(TE_ERR_INVALID_ARG, "malformed row_ptr");
+  for (int64_t i = 0; i < A->n; ++i)
+    if (rp[i + 1] < rp[i]) return srv_fail(TE_ERR_INVALID_ARG, "row_ptr must be non-decreasing");
+  for (int64_t k = 0; k < A->nnz; ++k)
+    if (A->col_idx[k] < 0 || (int64_t)A->col_idx[k] >= A->n)
+      return srv_fail(TE_ERR_INVALID_ARG, "a column index is outside [0, n)");
+  Request* R = new Request();
+  R->ticket = S->next_ticket++;
+  R->n = A->n;
+  R->nnz = A->nnz;
+  R->n_pad = pad_rows(A->n);
+  R->K = K;
+  R->m = m;
+  R->seed = seed;
+  R->vk = p.values;
+  R->in_type = A->values_f64 ? TE_F64 : TE_F32;
+  R->ncta = ctas_for(R->n_pad);
+  R->rp.assign(rp, rp + A->n + 1);
+  R->ci.assign(A->col_idx, A->col_idx + A->nnz);
+  const size_t vb = (size_t)A->nnz * (R->in_type == TE_F64 ? 8 : 4);
+  R->vals.resize(vb);
+  if (vb) memcpy(R->vals.data(), A->values, vb);
+  S->reqs[R->ticket] = R;
+  S->pending.push_back(R);
+  *ticket = R->ticket;
+  return TE_OK;
+}
+
+te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) {
+  if (!S) return srv_fail(TE_ERR_INVALID_ARG, "server is NULL");
+  // 1. the previous step has finished: retire the solves that ended in it
+  if (S->inflight) {
+    SRV_CK(cudaEventSynchronize(S->ev), "engine step");
+    S->inflight = false;
+    for (int k : S->finishing) {
+      Request* R = S->slots[k];
+      const SlotResult& o = S->res_h[k];
+      R->theta.assign(o.theta, o.theta + R->K);
+      R->resid.assign(o.resid, o.resid + R->K);
+      R->status = o.hdr[2];
+      R->state = REQ_FINISHED;
+      S->pool.release(R->work_off, R->work_bytes);
+      S->slots[k] = nullptr;
+      R->slot = -1;
+    }
+    S->finishing.clear();
+    for (auto& d : S->deferred) S->pool.release(d.first, d.second);
+    S->deferred.clear();
+  }
+  // 2. admit in submission order while a slot and pool memory are free
+  int live = 0;
+  for (Request* R : S->slots) live += R != nullptr;
+  while (!S->pending.empty() && live < S->max_slots) {
+    Request* R = S->pending.front();
+    int k = 0;
+    while (S->slots[k]) ++k;
+    te_status err = TE_OK;
+    const int a = admit(S, R, k, &err);
+    if (a < 0) return err;
+    if (a == 0) {
+      if (live == 0 && S->pool.used == 0) {
+        // nothing resident and the pool is empty: this request can never fit
+        R->status = TE_ERR_OUT_OF_MEMORY;
+        R->state = REQ_FINISHED;
+        S->pending.pop_front();
+        continue;
+      }
+      break;
+    }
+    S->pending.pop_front();
+    S->slots[k] = R;
+    ++live;
+  }
+  if (live_out) *live_out = live;
+  if (pending_out) *pending_out = (int32_t)S->pending.size();
+  if (live == 0) {
+    if (!S->deferred.empty()) {
+      SRV_CK(cudaEventRecord(S->ev, S->s), "record");
+      S->inflight = true;
+    }
+    return TE_OK;
+  }
+  // 3. the table of resident solves for this step
+  BatchTable* T = S->table_h;
+  int ns = 0;
+  T->slice_off[0] = 0;
+  T->lrow_off[0] = 0;
+  T->item_off[0] = 0;
+  for (int k = 0; k < S->max_slots; ++k) {
+    Request* R = S->slots[k];
+    if (!R) continue;
+    R->desc.step = R->step;
+    T->slot[ns] = R->desc;
+    T->slice_off[ns + 1] = T->slice_off[ns] + R->desc.nslices;
+    T->lrow_off[ns + 1] = T->lrow_off[ns] + R->desc.nlrows;
+    T->item_off[ns + 1] = T->item_off[ns] + R->desc.ncta;
+    ++ns;
+  }
+  T->nslots = ns;
+  SRV_CK(cudaMemcpyAsync(S->table_d, T, sizeof(BatchTable), cudaMemcpyHostToDevice, S->s),
+         "upload the step table");
+  // 4. one Lanczos step of every resident solve
+  if (S->gexec) SRV_CK(cudaGraphLaunch(S->gexec, S->s), "launch the engine step");
+  else SRV_CK(enqueue_step(S, S->s), "engine step");
+  // 5. solves that completed their m steps: Jacobi and Ritz vectors
+  for (int k = 0; k < S->max_slots; ++k) {
+    Request* R = S->slots[k];
+    if (!R) continue;
+    R->step += 1;
+    if (R->step == R->m) {
+      SRV_CK(enqueue_finish(S, R), "finish a solve");
+      S->finishing.push_back(k);
+    }
+  }
+  SRV_CK(cudaEventRecord(S->ev, S->s), "record");
+  S->inflight = true;
+  return TE_OK;
+}
+
+te_status te_server_poll(te_server* S, int64_t ticket, int32_t* done, double* eigvals,
+                         double* eigvecs, double* residuals) {
+  if (!S || !done) return srv_fail(TE_ERR_INVALID_ARG, "NULL argument");
+  *done = 0;
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return srv_fail(TE_ERR_INVALID_ARG, "unknown ticket");
+  Request* R = it->second;
+  if (R->state != REQ_FINISHED) return TE_OK;
+  *done = 1;
+  te_status st = (te_status)R->status;
+  if (R->res_bytes) {
+    if ((st == TE_OK || st == TE_ERR_BREAKDOWN) && eigvecs) {
+      cudaError_t e = cudaMemcpyAsync(eigvecs, S->pool.base + R->res_off, R->res_bytes,
+                                      cudaMemcpyDeviceToHost, S->ps);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(S->ps);
+      if (e != cudaSuccess) return srv_cuda(e, "copy the Ritz vectors");
+    }
+    S->pool.release(R->res_off, R->res_bytes);
+  }
+  if (st == TE_OK || st == TE_ERR_BREAKDOWN) {
+    if (eigvals) memcpy(eigvals, R->theta.data(), sizeof(double) * R->K);
+    if (residuals) memcpy(residuals, R->resid.data(), sizeof(double) * R->K);
+  }
+  S->reqs.erase(it);
+  delete R;
+  if (st != TE_OK) return srv_fail(st, std::string("request failed: ") + te_status_string(st));
+  return TE_OK;
+}
+
+te_status te_server_stats(const te_server* S, int32_t* live, int32_t* pending, size_t* used,
+                          size_t* peak) {
+  if (!S) return srv_fail(TE_ERR_INVALID_ARG, "server is NULL");
+  int n = 0;
+  for (Request* R : S->slots) n += R != nullptr;
+  if (live) *live = n;
+  if (pending) *pending = (int32_t)S->pending.size();
+  if (used) *used = S->pool.used;
+  if (peak) *peak = S->pool.peak;
+  return TE_OK;
+}
+
+}  // extern "C"

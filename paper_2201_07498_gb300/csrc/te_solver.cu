@@ -560,6 +560,17 @@ __global__ void solve_begin_kernel(LzState* st, const double* v1, double* eigvec
   st->ticket = 0;
 }
 
+}  // namespace
+
+cudaError_t te::launch_solve_begin(LzState* st, const double* v1, double* eigvecs, double* eigvals,
+                                   double* plan_vecs, cudaStream_t s) {
+  solve_begin_kernel<<<1, 1, 0, s>>>(st, v1, eigvecs, eigvals, plan_vecs);
+  return cudaGetLastError();
+}
+double te::breakdown_tolerance(int prec) { return breakdown_tol(prec); }
+
+namespace {
+
 te_status plan_begin(te_plan* P, const double* v1, double* eigvecs_dev, double* eigvals_dev,
                      cudaStream_t s) {
   solve_begin_kernel<<<1, 1, 0, s>>>(P->st, v1 ? v1 : P->opt.v1, eigvecs_dev, eigvals_dev,

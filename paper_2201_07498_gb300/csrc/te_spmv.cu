@@ -319,16 +319,15 @@ TE_DEV auto load_value(const typename VStore<VK>::t* p, uint64_t pol) {
 // Reduced-precision values (BF16, FP8 codes) are exact binary32 numbers, so
 // the FDF arithmetic (exact products, double-float sums) is unchanged; FP8
 // rows are summed over their codes and multiplied by the row scale at the end.
+// one warp sums one slice (lane = one piece); the serving engine's batched
+// SpMV runs the same body on the slices of several solves
 template <int P, int VK, bool F64OUT>
-__global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
+__device__ __forceinline__ void spmv_slice(const SpmvArgs& a, const int slice, const int lane) {
   using Tr = SpmvTr<P>;
   using val_t = typename Tr::val_t;
   using x_t = typename Tr::x_t;
   using acc_t = typename Tr::acc_t;
   using store_t = typename VStore<VK>::t;
-  const int lane = threadIdx.x & 31;
-  const int slice = blockIdx.x * SPMV_WPB + (threadIdx.x >> 5);
-  if (slice >= a.nslices) return;
   const SellSlice sl = a.slices[slice];
   const int32_t out = a.vout[(int64_t)slice * SELL_C + lane];
   const uint64_t pol = policy_evict_first();
@@ -384,6 +383,13 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
   }
 }
 
+template <int P, int VK, bool F64OUT>
+__global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
+  const int slice = blockIdx.x * SPMV_WPB + (threadIdx.x >> 5);
+  if (slice >= a.nslices) return;
+  spmv_slice<P, VK, F64OUT>(a, slice, threadIdx.x & 31);
+}
+
 // Cut rows: the first nbig rows (most pieces first) get a whole warp each,
 // the others FIN_G lanes each (most cut rows have a handful of pieces).
 // Each lane sums a strided subset of the row's piece partials, then a fixed
@@ -430,6 +436,83 @@ static cudaError_t launch_spmv_t(const SpmvArgs& a, const DevSell& S, cudaStream
 }
 
 cudaError_t spmv_prepare() { return cudaSuccess; }
+
+// ---------------------------------------------------------------------------
+// serving engine: the SpMV of every live solve in one launch.  Warps walk the
+// concatenated slice lists (a warp finds its solve from the prefix offsets);
+// x is the solve's current basis column, y its ytilde.  Each slice is summed
+// exactly as in the single-solve kernel, so a solve's result does not depend
+// on which other solves share the launch.
+// ---------------------------------------------------------------------------
+TE_DEV int find_slot(const int64_t* off, int nslots, int64_t g) {
+  int lo = 0, hi = nslots - 1;  // the last slot whose offset is <= g
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(32 * SPMV_WPB) batch_spmv_kernel(const BatchTable* T) {
+  const int lane = threadIdx.x & 31;
+  const int ns = T->nslots;
+  const int64_t total = T->slice_off[ns];
+  for (int64_t g = (int64_t)blockIdx.x * SPMV_WPB + (threadIdx.x >> 5); g < total;
+       g += (int64_t)gridDim.x * SPMV_WPB) {
+    const int sidx = find_slot(T->slice_off, ns, g);
+    const BatchSlot& B = T->slot[sidx];
+    SpmvArgs a;
+    a.slices = B.slices;
+    a.vout = B.vout;
+    a.cols = B.cols;
+    a.vals = B.vals;
+    a.lscale = nullptr;
+    a.ebase = 0;
+    a.x = static_cast<const float*>(B.V) + (size_t)B.step * (size_t)B.n_pad;
+    a.y = B.ytil;
+    a.vpart = B.vpart;
+    a.nslices = B.nslices;
+    const int slice = (int)(g - T->slice_off[sidx]);
+    if (B.vk == TE_BF16) spmv_slice<PREC_FDF, TE_BF16, false>(a, slice, lane);
+    else spmv_slice<PREC_FDF, TE_F32, false>(a, slice, lane);
+  }
+}
+
+// cut rows of every live solve, FIN_G lanes per row; the loop runs whole
+// warps so that every lane reaches the shuffles
+__global__ void batch_finalize_kernel(const BatchTable* T) {
+  const int ns = T->nslots;
+  const int64_t total = T->lrow_off[ns];
+  const int lane = threadIdx.x & 31, sub = lane & (FIN_G - 1);
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / FIN_G);
+       w0 < total; w0 += warps * (32 / FIN_G)) {
+    const int64_t g = w0 + lane / FIN_G;
+    const bool live = g < total;
+    LongRow lr{0, 0, 0, 0};
+    const BatchSlot* B = nullptr;
+    if (live) {
+      B = &T->slot[find_slot(T->lrow_off, ns, g)];
+      lr = B->lrows[g - T->lrow_off[B - T->slot]];
+    }
+    dacc acc = dacc_zero();
+    for (int c = sub; c < lr.count; c += FIN_G) {
+      const float2 v = static_cast<const float2*>(B->vpart)[lr.first + c];
+      dacc_add_pair(acc, v.x, v.y);
+    }
+    acc = group_sum(acc, FIN_G);
+    if (live && sub == 0) static_cast<float2*>(B->ytil)[lr.row] = dw_to_f2(dacc_value(acc));
+  }
+}
+
+cudaError_t launch_batch_spmv(const BatchTable* T, cudaStream_t s) {
+  batch_spmv_kernel<<<SRV_SPMV_BLOCKS, 32 * SPMV_WPB, 0, s>>>(T);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_finalize_kernel<<<SRV_FIN_BLOCKS, 256, 0, s>>>(T);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_spmv(int prec, const DevSell& S, const void* x, void* y, bool out_f64,
                         cudaStream_t s) {

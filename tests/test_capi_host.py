@@ -115,6 +115,15 @@ def test_option_validation_before_gpu(te):
     assert b"values_f64" in lib.te_last_error()
 
 
+def test_server_options_validated_before_gpu(te):
+    lib = te.load_library()
+    h = ctypes.c_void_p()
+    for slots, m, budget in [(0, 16, 1 << 30), (65, 16, 1 << 30), (8, 65, 1 << 30), (8, 16, 1000)]:
+        o = te.te_server_options(slots, m, budget, 1)
+        assert lib.te_server_create(ctypes.byref(o), ctypes.byref(h)) == 1
+    assert lib.te_server_create(None, ctypes.byref(h)) == 1
+
+
 def test_null_and_reserved_arguments(te):
     lib = te.load_library()
     ev = np.zeros(4)

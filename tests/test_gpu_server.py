@@ -1,0 +1,147 @@
+"""Serving engine (continuous batching): GPU tests through the C ABI.
+
+* a request served alone matches the single-solve plan within the FDF
+  tolerance, and a bfloat16 request matches the oracle on the rounded matrix;
+* a request's result is bit-identical alone and in a mix of requests of other
+  sizes admitted at other steps (each solve's sums do not depend on its
+  neighbours), with and without the captured step graph;
+* admission waits for pool memory: a small pool serves more requests than fit
+  at once, its use never exceeds the budget, and a request larger than the
+  whole pool fails with TE_ERR_OUT_OF_MEMORY without stopping the others.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from test_gpu_parity import match_pairs, subspace_angles
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def te():
+    import paper_2201_07498_gb300 as te
+    te.load_library(build_if_missing=True)
+    return te
+
+
+def _drain(srv, tickets, vectors=True, max_steps=10000):
+    out = {}
+    for _ in range(max_steps):
+        for t in list(tickets):
+            r = srv.poll(t, vectors)
+            if r is not None:
+                out[t] = r
+                tickets.remove(t)
+        if not tickets:
+            return out
+        srv.step()
+    raise AssertionError("requests did not finish")
+
+
+def _mix():
+    return [synth.rmat_sym(12, 6, 11), synth.uniform_sym(3000, 5, 12), synth.rmat_sym(10, 16, 13),
+            synth.uniform_sym(20000, 3, 14), synth.rmat_sym(14, 4, 15), synth.uniform_sym(700, 9, 16)]
+
+
+def test_server_request_matches_plan(te):
+    A = synth.uniform_sym(10000, 10, 0)
+    srv = te.Server(max_slots=4, max_krylov_steps=32, budget=256 << 20)
+    t = srv.submit(A, 8, 16, "fdf", seed=7)
+    ev, U, res = _drain(srv, [t])[t]
+    ev_p, U_p, res_p = te.topk_eigs(te.CSR.from_host(A, "fdf"), 8, 16, "fdf", seed=7,
+                                    residuals=True)
+    ev_p = ev_p.numpy()
+    scale = np.max(np.abs(ev_p))
+    perm = match_pairs(ev, ev_p, 1e-6 * scale)
+    assert np.max(np.abs(ev - ev_p[perm])) <= 1e-6 * scale
+    ang = subspace_angles(U, U_p.cpu().numpy()[:, perm], ev_p[perm])
+    assert np.max(ang) <= 1e-4, ang
+    assert np.max(np.abs(res - res_p.numpy()[perm])) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_alone_equals_in_mix(te, graph):
+    R = synth.rmat_sym(13, 8, 21)
+    srv = te.Server(max_slots=8, max_krylov_steps=32, budget=512 << 20, use_graph=graph)
+    t = srv.submit(R, 6, 20, "fdf", seed=3)
+    alone = _drain(srv, [t])[t]
+    srv.close()
+    srv = te.Server(max_slots=8, max_krylov_steps=32, budget=512 << 20, use_graph=graph)
+    mix = _mix()
+    tickets = [srv.submit(mix[0], 4, 8, "fdf", seed=1), srv.submit(mix[1], 8, 16, "bdf", seed=2)]
+    srv.step()
+    srv.step()
+    tickets.append(srv.submit(mix[2], 4, 12, "fdf", seed=3))
+    tr = srv.submit(R, 6, 20, "fdf", seed=3)  # joins while others are mid-solve
+    srv.step()
+    tickets += [srv.submit(M, 4, 8 + 2 * i, "fdf", seed=5 + i) for i, M in enumerate(mix[3:])]
+    got = _drain(srv, tickets + [tr])
+    inmix = got[tr]
+    for a, b in zip(alone, inmix):
+        assert np.array_equal(a, b)
+
+
+def test_graph_and_direct_steps_agree(te):
+    mix = _mix()[:4]
+    res = []
+    for graph in (True, False):
+        srv = te.Server(max_slots=3, max_krylov_steps=32, budget=512 << 20, use_graph=graph)
+        ts = [srv.submit(M, 4, 10, "fdf", seed=i) for i, M in enumerate(mix)]
+        res.append(_drain(srv, list(ts)))
+        srv.close()
+    for t0, t1 in zip(sorted(res[0]), sorted(res[1])):
+        for a, b in zip(res[0][t0], res[1][t1]):
+            assert np.array_equal(a, b)
+
+
+def test_memory_admission_and_oversize_request(te):
+    budget = 24 << 20
+    srv = te.Server(max_slots=16, max_krylov_steps=32, budget=budget)
+    mats = [synth.uniform_sym(40000, 4, 30 + i) for i in range(6)]  # ~9 MB of pool each
+    big = synth.uniform_sym(400000, 8, 40)                          # larger than the pool
+    tickets = [srv.submit(M, 4, 12, "fdf", seed=i) for i, M in enumerate(mats)]
+    tb = srv.submit(big, 4, 12, "fdf", seed=9)
+    queued_while_running = False
+    done = {}
+    for _ in range(2000):
+        live, pend = srv.step()
+        st = srv.stats()
+        assert st["pool_used"] <= budget and st["pool_peak"] <= budget
+        if live >= 1 and pend >= 1:
+            queued_while_running = True
+        for t in list(tickets):
+            r = srv.poll(t, vectors=False)
+            if r is not None:
+                done[t] = r
+                tickets.remove(t)
+        if not tickets:
+            break
+    assert not tickets and queued_while_running
+    with pytest.raises(te.TEError) as e:
+        for _ in range(100):
+            if srv.poll(tb) is not None:
+                break
+            srv.step()
+    assert e.value.status == 2
+    # every request equals its own single-solve result
+    for i, M in enumerate(mats):
+        ev_p, _, _ = te.topk_eigs(te.CSR.from_host(M, "fdf"), 4, 12, "fdf", seed=i, vectors=False)
+        ev = done[i + 1][0]
+        scale = np.max(np.abs(ev_p.numpy()))
+        match_pairs(ev, ev_p.numpy(), 1e-6 * scale)
+
+
+def test_bf16_request_matches_oracle(te):
+    A = synth.uniform_sym(8000, 8, 5)
+    Aq = synth.CSR(A.n, A.row_ptr, A.col, oracle.round_bf16(A.val)[1])
+    v1 = synth.start_vector(A.n, 11)
+    ref = oracle.topk_eigs(Aq, 8, 16, v1, seed=11)
+    srv = te.Server(max_slots=2, max_krylov_steps=16, budget=128 << 20)
+    t = srv.submit(A, 8, 16, "bdf", seed=11)
+    ev, U, _ = _drain(srv, [t])[t]
+    scale = np.max(np.abs(ref.eigvals))
+    perm = match_pairs(ev, ref.eigvals, 1e-6 * scale)
+    assert np.max(np.abs(ev - ref.eigvals[perm])) <= 1e-6 * scale
