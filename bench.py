@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the DDD and K=8 timings")
     p.add_argument("--oracle-steps", type=int, default=6)
+    p.add_argument("--no-serving", action="store_true",
+                   help="skip the serving leg (Poisson arrivals of small solves)")
+    p.add_argument("--serving-requests", type=int, default=200)
     p.add_argument("--no-ooc", action="store_true",
                    help="skip the host-streamed solve (R-MAT 2^25, edge factor 16, 4 GB budget)")
     p.add_argument("--no-sweep", action="store_true",
@@ -330,6 +333,53 @@ def out_of_core(te, world, steps=2, warmup=1):
             "generate_s": gen_s, "plan_build_s": build_s}
 
 
+def serving(te, nreq, rates=(100, 300, 1000, 3000, 5000), seed=4):
+    """Continuous-batching serving: the same `nreq` requests (synth's serving
+    mix: n log-uniform in [2^10, 2^18], degree 4-64, uniform or R-MAT, K in
+    {4, 8, 16}, m = 2K, binary32 or bfloat16 values) arrive as a Poisson
+    process at each rate; a client loop submits them on arrival, runs engine
+    steps and polls results (eigenvalues and Ritz vectors to host memory).
+    Latency = completion minus scheduled arrival."""
+    import numpy as np
+    import synth
+    t0 = time.perf_counter()
+    reqs = synth.serving_requests(nreq, seed)
+    gen_s = time.perf_counter() - t0
+    nnz = [int(A.nnz) for A, _, _, _ in reqs]
+    out = {"workload": f"serving_mix_seed{seed}", "requests_per_rate": nreq,
+           "mean_nnz": float(np.mean(nnz)), "generate_s": gen_s, "rates": {}}
+    rng = np.random.default_rng(seed + 1)
+    for rate in rates:
+        arrive = np.cumsum(rng.exponential(1.0 / rate, nreq))
+        srv = te.Server(max_slots=64, max_krylov_steps=32, budget=24 << 30)
+        lat, tickets, max_live, steps = [], {}, 0, 0
+        i = 0
+        start = time.perf_counter()
+        while len(lat) < nreq:
+            now = time.perf_counter() - start
+            while i < nreq and arrive[i] <= now:
+                A, K, m, prec = reqs[i]
+                tickets[srv.submit(A, K, m, prec, seed=i)] = arrive[i]
+                i += 1
+            if not tickets:
+                time.sleep(max(0.0, min(arrive[i] - now, 0.01)))
+                continue
+            live, _ = srv.step()
+            steps += 1
+            max_live = max(max_live, live)
+            for t in list(tickets):
+                if srv.poll(t) is not None:
+                    lat.append(time.perf_counter() - start - tickets.pop(t))
+        wall = time.perf_counter() - start
+        lat_ms = np.array(lat) * 1e3
+        out["rates"][str(rate)] = {
+            "solves_per_s": nreq / (wall - arrive[0]), "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "engine_steps": steps,
+            "max_resident": max_live, "wall_s": wall, "host_s": srv.timing()}
+        srv.close()
+    return out
+
+
 def time_plan(plan, steps, warmup, world, want_vectors=True):
     import torch
     ev = torch.empty(plan.K, dtype=torch.float64, device="cuda")
@@ -465,6 +515,8 @@ def main():
 
     if not args.no_sweep and world == 1:
         extras["precision_sweep"] = precision_sweep(te, world)
+    if not args.no_serving and world == 1:
+        extras["serving"] = serving(te, args.serving_requests)
     if not args.no_ooc and world == 1:
         extras["out_of_core"] = out_of_core(te, world)
 

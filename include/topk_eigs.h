@@ -304,18 +304,23 @@ typedef struct {
  * owns). */
 te_status te_server_create(const te_server_options* opt, te_server** out);
 
-/* Queue one solve: A in host memory (copied by the call; it may be freed on
- * return), K eigenpairs largest in modulo from m = krylov_steps Lanczos steps,
- * start vector from `seed`.  *ticket identifies the request.  Malformed input
- * is rejected here (TE_ERR_INVALID_ARG); a request larger than the whole pool
- * fails with TE_ERR_OUT_OF_MEMORY when it reaches the head of the queue. */
+/* Queue one solve: A in host memory, K eigenpairs largest in modulo from
+ * m = krylov_steps Lanczos steps, start vector from `seed`.  *ticket
+ * identifies the request.  The server reads A's arrays when it admits the
+ * request: they must stay valid and unchanged until te_server_poll reports
+ * the request done.  Malformed row pointers are rejected here
+ * (TE_ERR_INVALID_ARG); column indices are checked on the device at
+ * admission (a request with one outside [0, n) finishes with
+ * TE_ERR_INVALID_ARG before its first SpMV); a request larger than the whole
+ * pool fails with TE_ERR_OUT_OF_MEMORY when it reaches the head of the queue. */
 te_status te_server_submit(te_server* srv, const te_csr* A, int32_t K, int32_t krylov_steps,
                            te_precision p, uint64_t seed, int64_t* ticket);
 
-/* One engine step: wait for the previous step, retire finished solves, admit
- * pending ones, and launch one Lanczos step of every resident solve.  *live
- * and *pending (may be NULL) receive the counts after admission.  Returns
- * without waiting for the launched step. */
+/* One engine step: wait for the previous step, retire finished solves, launch
+ * one Lanczos step of every resident solve, then admit pending requests
+ * (their layouts are built behind the step; they join the batch at the next
+ * step).  *live (resident + just admitted) and *pending (may be NULL) receive
+ * the counts.  Returns without waiting for the launched work. */
 te_status te_server_step(te_server* srv, int32_t* live, int32_t* pending);
 
 /* *done = 1 when the request has finished: eigvals (K), residual estimates
@@ -328,6 +333,11 @@ te_status te_server_poll(te_server* srv, int64_t ticket, int32_t* done, double* 
 /* Resident and queued solves, pool bytes in use now and at most so far. */
 te_status te_server_stats(const te_server* srv, int32_t* live, int32_t* pending,
                           size_t* pool_used, size_t* pool_peak);
+
+/* Cumulative host seconds: waiting for engine steps, admitting requests
+ * (layout analysis and uploads), launching steps, and inside submit. */
+te_status te_server_timing(const te_server* srv, double* wait_s, double* admit_s,
+                           double* launch_s, double* submit_s);
 
 void te_server_destroy(te_server* srv);
 

@@ -108,6 +108,8 @@ _SIGS = {
     "te_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "te_server_destroy": (None, [ctypes.c_void_p]),
+    "te_server_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
     "te_gram": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p]),
     "te_spmv_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -362,7 +364,8 @@ class Server:
         t = ctypes.c_int64()
         _check(self._lib.te_server_submit(self._h, ctypes.byref(A), K, krylov_steps,
                                           _prec(precision), seed, ctypes.byref(t)))
-        self._meta[t.value] = (int(host_csr.n), K)
+        # the server reads the arrays at admission: keep them alive until done
+        self._meta[t.value] = (int(host_csr.n), K, rp, ci, va)
         return t.value
 
     def step(self):
@@ -375,10 +378,10 @@ class Server:
         """None while running; else (eigvals [K], eigvecs [n, K] or None,
         residual estimates [K]) as numpy arrays (raises on a failed request)."""
         import numpy as np
-        n, K = self._meta[ticket]
-        ev = np.zeros(K)
-        res = np.zeros(K)
-        U = np.zeros((K, n)) if vectors else None
+        n, K = self._meta[ticket][:2]
+        ev = np.empty(K)
+        res = np.empty(K)
+        U = np.empty((K, n)) if vectors else None
         done = ctypes.c_int32()
         rc = self._lib.te_server_poll(self._h, ticket, ctypes.byref(done),
                                       ctypes.c_void_p(ev.ctypes.data),
@@ -398,6 +401,12 @@ class Server:
                                          ctypes.byref(used), ctypes.byref(peak)))
         return {"live": live.value, "pending": pend.value, "pool_used": used.value,
                 "pool_peak": peak.value}
+
+    def timing(self):
+        """Cumulative host seconds: wait, admit, launch, submit."""
+        v = [ctypes.c_double() for _ in range(4)]
+        _check(self._lib.te_server_timing(self._h, *[ctypes.byref(x) for x in v]))
+        return {k: x.value for k, x in zip(("wait_s", "admit_s", "launch_s", "submit_s"), v)}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -27,6 +28,11 @@ using namespace te;
 namespace {
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
 
 te_status srv_fail(te_status s, const std::string& m) {
   set_last_error(m);
@@ -95,14 +101,18 @@ class Pool {
   std::map<size_t, size_t> free_;
 };
 
-enum ReqState { REQ_PENDING = 0, REQ_RUNNING = 1, REQ_FINISHED = 2 };
+// pending -> admitted (layout built, columns being checked on the device) ->
+// running (resident in the batch) -> finished
+enum ReqState { REQ_PENDING = 0, REQ_RUNNING = 1, REQ_FINISHED = 2, REQ_ADMITTED = 3 };
 
 struct Request {
   int64_t ticket = 0;
   int64_t n = 0, nnz = 0, n_pad = 0;
-  std::vector<int64_t> rp;
-  std::vector<int32_t> ci;
-  std::vector<char> vals;  // binary64 or binary32, as given
+  // the caller's CSR (borrowed: it stays valid until the request is done)
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const void* vals = nullptr;  // binary64 or binary32, as given
+  size_t val_bytes = 0;
   int in_type = TE_F32, vk = TE_F32;
   int K = 0, m = 0, ncta = 1;
   uint64_t seed = 0;
@@ -116,6 +126,8 @@ struct SlotResult {  // pinned, written by the finishing copies
   double theta[MAX_M];
   double resid[MAX_M];
   int hdr[4];  // restart_flag, restarts, status, sweeps (as in LzState)
+  int bad_cols;  // admission: a column index outside [0, n)
+  int pad_;
 };
 
 int64_t pad_rows(int64_t n) { return (n + TILE_R - 1) / TILE_R * TILE_R; }
@@ -148,6 +160,7 @@ struct te_server {
   std::vector<Request*> slots;
   std::vector<std::pair<size_t, size_t>> deferred;  // pool blocks to free after the next sync
   std::vector<int> finishing;                       // slots whose solve ends this step
+  double t_wait = 0, t_admit = 0, t_launch = 0, t_submit = 0;  // host seconds, cumulative
 };
 
 namespace {
@@ -167,7 +180,7 @@ cudaError_t enqueue_step(te_server* S, cudaStream_t s) {
 // device work memory of a request: the SELL copy, the solver vectors and
 // state; `tmp`: what only the admission needs; `res`: the Ritz vectors
 struct AdmitLayout {
-  size_t slices, vout, cols, vals, lrows, vpart, V, ytil, w, partials, st, total;
+  size_t slices, vout, cols, vals, lrows, vpart, V, ytil, w, partials, st, flag, total;
   size_t t_rp, t_ci, t_val, t_src, t_len, t_q, t_total;
 };
 
@@ -191,6 +204,7 @@ AdmitLayout admit_layout(const Request& R, const SellHost& H) {
   L.w = take((size_t)R.n_pad * 8);
   L.partials = take((size_t)R.ncta * PSTRIDE * 8);
   L.st = take(sizeof(LzState));
+  L.flag = take(16);
   L.total = off;
   off = 0;
   L.t_rp = take((size_t)(R.n + 1) * 8);
@@ -208,7 +222,7 @@ AdmitLayout admit_layout(const Request& R, const SellHost& H) {
 int admit(te_server* S, Request* R, int k, te_status* err) {
   SellHost H;
   std::string perr;
-  make_sell(R->rp.data(), R->n, R->nnz, H, perr);  // validated at submit
+  make_sell(R->rp, R->n, R->nnz, H, perr);  // row pointers validated at submit
   const AdmitLayout L = admit_layout(*R, H);
   size_t work = 0, res = 0, tmp = 0;
   if (!S->pool.alloc(L.total, &work)) return 0;
@@ -233,9 +247,16 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
   auto h2d = [&](void* dst, const void* src, size_t b) {
     if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s);
   };
-  h2d(T + L.t_rp, R->rp.data(), (size_t)(R->n + 1) * 8);
-  h2d(T + L.t_ci, R->ci.data(), (size_t)R->nnz * 4);
-  h2d(T + L.t_val, R->vals.data(), R->vals.size());
+  h2d(T + L.t_rp, R->rp, (size_t)(R->n + 1) * 8);
+  h2d(T + L.t_ci, R->ci, (size_t)R->nnz * 4);
+  h2d(T + L.t_val, R->vals, R->val_bytes);
+  // column indices are checked here, before the solve's first SpMV (the
+  // request joins the batch only after the next step has read the flag)
+  int* flag = reinterpret_cast<int*>(W + L.flag);
+  if (e == cudaSuccess)
+    e = launch_validate_cols(reinterpret_cast<const int32_t*>(T + L.t_ci), R->nnz, R->n, flag, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&S->res_h[k].bad_cols, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
   h2d(T + L.t_src, H.vsrc.data(), H.vsrc.size() * 8);
   h2d(T + L.t_len, H.vlen.data(), H.vlen.size() * 4);
   h2d(W + L.slices, H.slices.data(), H.slices.size() * sizeof(SellSlice));
@@ -310,12 +331,8 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
     return -1;
   }
   R->slot = k;
-  R->state = REQ_RUNNING;
+  R->state = REQ_ADMITTED;
   R->step = 0;
-  // the host copies are no longer needed
-  std::vector<int64_t>().swap(R->rp);
-  std::vector<int32_t>().swap(R->ci);
-  std::vector<char>().swap(R->vals);
   return 1;
 }
 
@@ -467,16 +484,20 @@ void te_server_destroy(te_server* S) {
 te_status te_server_submit(te_server* S, const te_csr* A, int32_t K, int32_t m, te_precision p,
                            uint64_t seed, int64_t* ticket) {
   if (!S || !ticket) return srv_fail(TE_ERR_INVALID_ARG, "NULL argument");
+  const double t0 = now_s();
+  struct Acc {
+    double t0;
+    double& acc;
+    ~Acc() { acc += now_s() - t0; }
+  } acc{t0, S->t_submit};
   te_status r = check_request(A, K, m, p, S->max_m);
   if (r != TE_OK) return r;
-  // validate the CSR on the host now, so that admission cannot fail on it
+  // row pointers are checked now (the layout is built from them); column
+  // indices on the device at admission
   const int64_t* rp = A->row_ptr;
   if (rp[0] != 0 || rp[A->n] != A->nnz) return srv_fail(TE_ERR_INVALID_ARG, "malformed row_ptr");
   for (int64_t i = 0; i < A->n; ++i)
     if (rp[i + 1] < rp[i]) return srv_fail(TE_ERR_INVALID_ARG, "row_ptr must be non-decreasing");
-  for (int64_t k = 0; k < A->nnz; ++k)
-    if (A->col_idx[k] < 0 || (int64_t)A->col_idx[k] >= A->n)
-      return srv_fail(TE_ERR_INVALID_ARG, "a column index is outside [0, n)");
   Request* R = new Request();
   R->ticket = S->next_ticket++;
   R->n = A->n;
@@ -488,11 +509,10 @@ te_status te_server_submit(te_server* S, const te_csr* A, int32_t K, int32_t m, 
   R->vk = p.values;
   R->in_type = A->values_f64 ? TE_F64 : TE_F32;
   R->ncta = ctas_for(R->n_pad);
-  R->rp.assign(rp, rp + A->n + 1);
-  R->ci.assign(A->col_idx, A->col_idx + A->nnz);
-  const size_t vb = (size_t)A->nnz * (R->in_type == TE_F64 ? 8 : 4);
-  R->vals.resize(vb);
-  if (vb) memcpy(R->vals.data(), A->values, vb);
+  R->rp = rp;
+  R->ci = A->col_idx;
+  R->vals = A->values;
+  R->val_bytes = (size_t)A->nnz * (R->in_type == TE_F64 ? 8 : 4);
   S->reqs[R->ticket] = R;
   S->pending.push_back(R);
   *ticket = R->ticket;
@@ -501,7 +521,9 @@ te_status te_server_submit(te_server* S, const te_csr* A, int32_t K, int32_t m, 
 
 te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) {
   if (!S) return srv_fail(TE_ERR_INVALID_ARG, "server is NULL");
-  // 1. the previous step has finished: retire the solves that ended in it
+  double t0 = now_s();
+  // 1. the previous step has finished: retire the solves that ended in it,
+  //    and let the requests admitted in it join the batch (or fail them)
   if (S->inflight) {
     SRV_CK(cudaEventSynchronize(S->ev), "engine step");
     S->inflight = false;
@@ -519,8 +541,61 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
     S->finishing.clear();
     for (auto& d : S->deferred) S->pool.release(d.first, d.second);
     S->deferred.clear();
+    for (int k = 0; k < S->max_slots; ++k) {
+      Request* R = S->slots[k];
+      if (!R || R->state != REQ_ADMITTED) continue;
+      if (S->res_h[k].bad_cols) {
+        R->status = TE_ERR_INVALID_ARG;
+        R->state = REQ_FINISHED;
+        S->pool.release(R->work_off, R->work_bytes);
+        S->pool.release(R->res_off, R->res_bytes);
+        R->res_bytes = 0;
+        S->slots[k] = nullptr;
+        R->slot = -1;
+      } else {
+        R->state = REQ_RUNNING;
+      }
+    }
   }
-  // 2. admit in submission order while a slot and pool memory are free
+  double t1 = now_s();
+  S->t_wait += t1 - t0;
+  // 2. one Lanczos step of every resident solve
+  BatchTable* T = S->table_h;
+  int ns = 0;
+  T->slice_off[0] = 0;
+  T->lrow_off[0] = 0;
+  T->item_off[0] = 0;
+  for (int k = 0; k < S->max_slots; ++k) {
+    Request* R = S->slots[k];
+    if (!R || R->state != REQ_RUNNING) continue;
+    R->desc.step = R->step;
+    T->slot[ns] = R->desc;
+    T->slice_off[ns + 1] = T->slice_off[ns] + R->desc.nslices;
+    T->lrow_off[ns + 1] = T->lrow_off[ns] + R->desc.nlrows;
+    T->item_off[ns + 1] = T->item_off[ns] + R->desc.ncta;
+    ++ns;
+  }
+  T->nslots = ns;
+  if (ns > 0) {
+    SRV_CK(cudaMemcpyAsync(S->table_d, T, sizeof(BatchTable), cudaMemcpyHostToDevice, S->s),
+           "upload the step table");
+    if (S->gexec) SRV_CK(cudaGraphLaunch(S->gexec, S->s), "launch the engine step");
+    else SRV_CK(enqueue_step(S, S->s), "engine step");
+    // solves that completed their m steps: Jacobi and Ritz vectors
+    for (int k = 0; k < S->max_slots; ++k) {
+      Request* R = S->slots[k];
+      if (!R || R->state != REQ_RUNNING) continue;
+      R->step += 1;
+      if (R->step == R->m) {
+        SRV_CK(enqueue_finish(S, R), "finish a solve");
+        S->finishing.push_back(k);
+      }
+    }
+  }
+  double t2 = now_s();
+  S->t_launch += t2 - t1;
+  // 3. admit in submission order while a slot and pool memory are free; the
+  //    host work overlaps the step just launched, the uploads follow it
   int live = 0;
   for (Request* R : S->slots) live += R != nullptr;
   while (!S->pending.empty() && live < S->max_slots) {
@@ -544,49 +619,23 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
     S->slots[k] = R;
     ++live;
   }
+  S->t_admit += now_s() - t2;
   if (live_out) *live_out = live;
   if (pending_out) *pending_out = (int32_t)S->pending.size();
-  if (live == 0) {
-    if (!S->deferred.empty()) {
-      SRV_CK(cudaEventRecord(S->ev, S->s), "record");
-      S->inflight = true;
-    }
-    return TE_OK;
+  if (live > 0 || !S->deferred.empty()) {
+    SRV_CK(cudaEventRecord(S->ev, S->s), "record");
+    S->inflight = true;
   }
-  // 3. the table of resident solves for this step
-  BatchTable* T = S->table_h;
-  int ns = 0;
-  T->slice_off[0] = 0;
-  T->lrow_off[0] = 0;
-  T->item_off[0] = 0;
-  for (int k = 0; k < S->max_slots; ++k) {
-    Request* R = S->slots[k];
-    if (!R) continue;
-    R->desc.step = R->step;
-    T->slot[ns] = R->desc;
-    T->slice_off[ns + 1] = T->slice_off[ns] + R->desc.nslices;
-    T->lrow_off[ns + 1] = T->lrow_off[ns] + R->desc.nlrows;
-    T->item_off[ns + 1] = T->item_off[ns] + R->desc.ncta;
-    ++ns;
-  }
-  T->nslots = ns;
-  SRV_CK(cudaMemcpyAsync(S->table_d, T, sizeof(BatchTable), cudaMemcpyHostToDevice, S->s),
-         "upload the step table");
-  // 4. one Lanczos step of every resident solve
-  if (S->gexec) SRV_CK(cudaGraphLaunch(S->gexec, S->s), "launch the engine step");
-  else SRV_CK(enqueue_step(S, S->s), "engine step");
-  // 5. solves that completed their m steps: Jacobi and Ritz vectors
-  for (int k = 0; k < S->max_slots; ++k) {
-    Request* R = S->slots[k];
-    if (!R) continue;
-    R->step += 1;
-    if (R->step == R->m) {
-      SRV_CK(enqueue_finish(S, R), "finish a solve");
-      S->finishing.push_back(k);
-    }
-  }
-  SRV_CK(cudaEventRecord(S->ev, S->s), "record");
-  S->inflight = true;
+  return TE_OK;
+}
+
+te_status te_server_timing(const te_server* S, double* wait_s, double* admit_s, double* launch_s,
+                           double* submit_s) {
+  if (!S) return srv_fail(TE_ERR_INVALID_ARG, "server is NULL");
+  if (wait_s) *wait_s = S->t_wait;
+  if (admit_s) *admit_s = S->t_admit;
+  if (launch_s) *launch_s = S->t_launch;
+  if (submit_s) *submit_s = S->t_submit;
   return TE_OK;
 }
 

@@ -143,6 +143,38 @@ def rmat_sym(scale: int, edge_factor: int, seed: int, a: float = 0.57, b: float 
     return _take(_load().synth_rmat_sym(scale, edge_factor, a, b, c, seed, int(normalized)))
 
 
+def normalize_sym(A: CSR) -> CSR:
+    """D^-1/2 W D^-1/2 with the weighted degrees d_i = sum_j |w_ij| (an input
+    transformation: rows of weight 0 stay empty)."""
+    d = np.add.reduceat(np.abs(A.val), A.row_ptr[:-1]) if A.nnz else np.zeros(A.n)
+    d = np.where(np.diff(A.row_ptr) > 0, d, 0.0)
+    inv = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    return CSR(A.n, A.row_ptr.copy(), A.col.copy(), A.val * inv[rows] * inv[A.col])
+
+
+def serving_requests(count: int, seed: int):
+    """Independent solve requests shaped like a serving mix: n log-uniform in
+    [2^10, 2^18], mean degree uniform in [4, 64], half uniform-random (values
+    uniform(0,1), symmetrically normalised) and half R-MAT (normalised
+    adjacency), K in {4, 8, 16} with m = 2K, binary32 or bfloat16 values.
+    Returns a list of (matrix, K, m, precision)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(2.0 ** rng.uniform(10, 18))
+        deg = int(rng.integers(4, 65))
+        K = int(rng.choice([4, 8, 16]))
+        prec = "fdf" if rng.random() < 0.5 else "bdf"
+        mseed = int(seed) * 1_000_003 + i
+        if rng.random() < 0.5:
+            A = normalize_sym(uniform_sym(n, max(1, deg // 2), mseed))
+        else:
+            A = rmat_sym(max(10, int(round(np.log2(n)))), max(1, deg // 2), mseed)
+        out.append((A, K, 2 * K, prec))
+    return out
+
+
 def from_triplets(n: int, rows, cols, vals) -> CSR:
     """CSR from (row, col, value) entries; duplicates summed, columns sorted."""
     r = np.ascontiguousarray(rows, dtype=np.int32)

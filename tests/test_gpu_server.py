@@ -145,3 +145,21 @@ def test_bf16_request_matches_oracle(te):
     scale = np.max(np.abs(ref.eigvals))
     perm = match_pairs(ev, ref.eigvals, 1e-6 * scale)
     assert np.max(np.abs(ev - ref.eigvals[perm])) <= 1e-6 * scale
+
+
+def test_bad_column_is_rejected_before_the_first_spmv(te):
+    A = synth.uniform_sym(3000, 5, 9)
+    bad = synth.CSR(A.n, A.row_ptr, A.col.copy(), A.val)
+    bad.col[17] = A.n  # outside [0, n): checked on the device at admission
+    srv = te.Server(max_slots=4, max_krylov_steps=16, budget=64 << 20)
+    tb = srv.submit(bad, 4, 8, "fdf", seed=1)
+    tg = srv.submit(A, 4, 8, "fdf", seed=1)
+    with pytest.raises(te.TEError) as e:
+        for _ in range(50):
+            if srv.poll(tb) is not None:
+                break
+            srv.step()
+    assert e.value.status == 1
+    ev = _drain(srv, [tg])[tg][0]
+    ev_p, _, _ = te.topk_eigs(te.CSR.from_host(A, "fdf"), 4, 8, "fdf", seed=1, vectors=False)
+    match_pairs(ev, ev_p.numpy(), 1e-6 * np.max(np.abs(ev_p.numpy())))
