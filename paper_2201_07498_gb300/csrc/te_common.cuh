@@ -176,6 +176,22 @@ TE_DEV uint64_t policy_evict_first() {
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
+TE_DEV uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// gathers of the SpMV's x: read-only, kept in L2 ahead of the streamed layout
+TE_DEV float ld_keep_f32(const float* a, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+TE_DEV double ld_keep_f64(const double* a, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+  return v;
+}
 TE_DEV int ld_stream_i32(const int32_t* a, uint64_t pol) {
   int v;
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;"
@@ -202,12 +218,17 @@ TE_DEV uint32_t ld_stream_u8(const uint8_t* a, uint64_t pol) {
 }
 // reduced-precision matrix values -> binary32 (exact)
 TE_DEV float bf16_to_f32(uint32_t code) { return __uint_as_float(code << 16); }
-// FP8 E4M3: sign, 4 exponent bits (bias 7), 3 fraction bits; exponent 0 is
-// subnormal (m * 2^-9).  The all-ones NaN code is never produced.
+// FP8 E4M3 (sign, 4 exponent bits with bias 7, 3 fraction bits; exponent 0
+// subnormal) -> binary32 by the hardware conversion to half precision, which
+// is exact for every finite E4M3 value, then half -> binary32 (exact).  The
+// code is placed in both bytes of the converted pair, so either half holds it.
 TE_DEV float e4m3_to_f32(uint32_t code) {
-  const uint32_t e = (code >> 3) & 15u, m = code & 7u;
-  const float v = e ? __uint_as_float(((e + 120u) << 23) | (m << 20)) : (float)m * 0x1p-9f;
-  return (code & 0x80u) ? -v : v;
+  const unsigned short pair = (unsigned short)((code & 0xffu) * 0x0101u);
+  uint32_t h2;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(pair));
+  float f;
+  asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"((unsigned short)(h2 & 0xffffu)));
+  return f;
 }
 TE_DEV double ld_stream_f64(const double* a, uint64_t pol) {
   double v;

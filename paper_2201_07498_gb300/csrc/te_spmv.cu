@@ -27,32 +27,19 @@
 
 namespace te {
 
-bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err) {
-  out = SellHost();
-  if (rp[0] != 0) {
-    err = "row_ptr[0] must be 0";
-    return false;
-  }
-  for (int64_t r = 0; r < n; ++r) {
-    if (rp[r + 1] < rp[r]) {
-      err = "row_ptr must be non-decreasing (row " + std::to_string(r) + ")";
-      return false;
-    }
-  }
-  if (rp[n] != nnz) {
-    err = "row_ptr[n] != nnz";
-    return false;
-  }
+// Windows of rows [w0, w1) into `out`, with entry offsets and cut-row piece
+// slots numbered from 0 (the caller shifts them).
+static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, SellHost& out) {
   struct Piece {
     int64_t src;
     int32_t len, out, row;
   };
   std::vector<Piece> win, sorted;
   std::vector<int64_t> pos(SELL_VMAX + 2);
-  for (int64_t w0 = 0; w0 < n; w0 += SELL_WINDOW) {
-    const int64_t w1 = std::min<int64_t>(w0 + SELL_WINDOW, n);
+  for (int64_t w = w0; w < w1; ++w) {
+    const int64_t r0 = w * SELL_WINDOW, r1 = std::min<int64_t>(r0 + SELL_WINDOW, n);
     win.clear();
-    for (int64_t r = w0; r < w1; ++r) {
+    for (int64_t r = r0; r < r1; ++r) {
       const int64_t L = rp[r + 1] - rp[r];
       if (L == 0) continue;  // empty rows: never written by the kernel
       if (L <= SELL_VMAX) {
@@ -107,19 +94,121 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
       out.entries += (int64_t)SELL_C * sl.len;
     }
   }
-  // cut rows with the most pieces first (their finalising lanes run longest)
-  std::stable_sort(out.lrows.begin(), out.lrows.end(),
-                   [](const LongRow& a, const LongRow& b) { return a.count > b.count; });
+}
+
+// Threads take contiguous ranges of windows; the parts are joined with their
+// entry and piece offsets, so the result equals a sequential build.
+bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err) {
+  out = SellHost();
+  if (rp[0] != 0) {
+    err = "row_ptr[0] must be 0";
+    return false;
+  }
+  if (rp[n] != nnz) {
+    err = "row_ptr[n] != nnz";
+    return false;
+  }
+  const int64_t W = (n + SELL_WINDOW - 1) / SELL_WINDOW;
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > 32) nt = 32;
+  if ((int64_t)nt > W / 16) nt = (unsigned)std::max<int64_t>(1, W / 16);
+  std::vector<int64_t> bad(nt, -1);
+  std::vector<SellHost> part(nt);
+  auto work = [&](unsigned t) {
+    const int64_t w0 = W * t / nt, w1 = W * (t + 1) / nt;
+    const int64_t r0 = w0 * SELL_WINDOW, r1 = std::min<int64_t>(w1 * SELL_WINDOW, n);
+    for (int64_t r = r0; r < r1; ++r)
+      if (rp[r + 1] < rp[r]) {
+        bad[t] = r;
+        return;
+      }
+    sell_windows(rp, n, w0, w1, part[t]);
+  };
+  if (nt == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+  }
+  for (unsigned t = 0; t < nt; ++t)
+    if (bad[t] >= 0) {
+      err = "row_ptr must be non-decreasing (row " + std::to_string(bad[t]) + ")";
+      return false;
+    }
+  // join the parts
+  size_t ns = 0, nl = 0, nr = 0;
+  for (const SellHost& p : part) {
+    ns += p.slices.size();
+    nl += p.vout.size();
+    nr += p.lrows.size();
+  }
+  out.slices.resize(ns);
+  out.vout.resize(nl);
+  out.vsrc.resize(nl);
+  out.vlen.resize(nl);
+  out.vrow.resize(nl);
+  std::vector<LongRow> lrows(nr);
+  std::vector<size_t> so(nt + 1, 0), lo(nt + 1, 0), ro(nt + 1, 0);
+  std::vector<int64_t> eo(nt + 1, 0), po(nt + 1, 0);
+  for (unsigned t = 0; t < nt; ++t) {
+    so[t + 1] = so[t] + part[t].slices.size();
+    lo[t + 1] = lo[t] + part[t].vout.size();
+    ro[t + 1] = ro[t] + part[t].lrows.size();
+    eo[t + 1] = eo[t] + part[t].entries;
+    po[t + 1] = po[t] + part[t].pieces;
+  }
+  auto join = [&](unsigned t) {
+    const SellHost& p = part[t];
+    for (size_t i = 0; i < p.slices.size(); ++i) {
+      SellSlice sl = p.slices[i];
+      sl.base += eo[t];
+      out.slices[so[t] + i] = sl;
+    }
+    for (size_t i = 0; i < p.vout.size(); ++i) {
+      int32_t v = p.vout[i];
+      if (v < 0 && v != SELL_SKIP) v = -1 - (int32_t)(po[t] + (-1 - (int64_t)v));
+      out.vout[lo[t] + i] = v;
+      out.vsrc[lo[t] + i] = p.vsrc[i];
+      out.vlen[lo[t] + i] = p.vlen[i];
+      out.vrow[lo[t] + i] = p.vrow[i];
+    }
+    for (size_t i = 0; i < p.lrows.size(); ++i) {
+      LongRow lr = p.lrows[i];
+      lr.first += (int32_t)po[t];
+      lrows[ro[t] + i] = lr;
+    }
+  };
+  if (nt == 1) {
+    join(0);
+  } else {
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(join, t);
+    for (auto& x : th) x.join();
+  }
+  out.entries = eo[nt];
+  out.pieces = po[nt];
+  // cut rows with the most pieces first (their finalising lanes run longest):
+  // a stable counting sort by piece count
+  int32_t maxc = 0;
+  for (const LongRow& lr : lrows) maxc = std::max(maxc, lr.count);
+  std::vector<int64_t> cpos((size_t)maxc + 2, 0);
+  for (const LongRow& lr : lrows) ++cpos[lr.count];
+  int64_t acc = 0;
+  for (int32_t c = maxc; c >= 0; --c) {
+    const int64_t k = cpos[c];
+    cpos[c] = acc;
+    acc += k;
+  }
+  out.lrows.resize(nr);
+  for (const LongRow& lr : lrows) out.lrows[cpos[lr.count]++] = lr;
   out.nbig = 0;
   while (out.nbig < (int64_t)out.lrows.size() && out.lrows[out.nbig].count > SELL_BIG_PIECES)
     ++out.nbig;
   return true;
 }
 
-// ---------------------------------------------------------------------------
-// layout conversion: one thread per lane, entries k = 0..len-1 (padding:
-// column 0, value 0)
-// ---------------------------------------------------------------------------
 // Host build of the SELL arrays (for a matrix that stays in host memory and
 // is streamed to the device in row blocks): the same arrangement the device
 // build produces; binary64 -> binary32 rounds to nearest even.  Threads split
@@ -331,6 +420,7 @@ __device__ __forceinline__ void spmv_slice(const SpmvArgs& a, const int slice, c
   const SellSlice sl = a.slices[slice];
   const int32_t out = a.vout[(int64_t)slice * SELL_C + lane];
   const uint64_t pol = policy_evict_first();
+  const uint64_t keep = policy_evict_last();
   const int32_t* cp = a.cols + (sl.base - a.ebase) + lane;
   const store_t* vp = static_cast<const store_t*>(a.vals) + (sl.base - a.ebase) + lane;
   const x_t* x = static_cast<const x_t*>(a.x);
@@ -359,7 +449,10 @@ __device__ __forceinline__ void spmv_slice(const SpmvArgs& a, const int slice, c
     }
     x_t xv[SPMV_UNROLL];
 #pragma unroll
-    for (int u = 0; u < SPMV_UNROLL; ++u) xv[u] = __ldg(x + c[u]);  // padding reads x[0]
+    for (int u = 0; u < SPMV_UNROLL; ++u) {  // padding reads x[0]
+      if constexpr (sizeof(x_t) == 4) xv[u] = ld_keep_f32(x + c[u], keep);
+      else xv[u] = ld_keep_f64(x + c[u], keep);
+    }
 #pragma unroll
     for (int u = 0; u < SPMV_UNROLL; u += 2) {
       add(acc0, v[u], xv[u]);

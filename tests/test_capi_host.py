@@ -205,7 +205,8 @@ def _check_layout(rp, L):
 
 
 def test_layout_covers_every_entry_once(te):
-    mats = [synth.uniform_sym(5000, 7, 3), synth.rmat_sym(14, 8, 5)]
+    # (scale 17: 64 windows of rows, built by several threads and joined)
+    mats = [synth.uniform_sym(5000, 7, 3), synth.rmat_sym(14, 8, 5), synth.rmat_sym(17, 4, 6)]
     # crafted: empty rows, a star (one very long row), rows around the cut length
     n = 20000
     lens = np.zeros(n, dtype=np.int64)
