@@ -123,6 +123,10 @@ typedef struct {
                        current one.  Binary64 or binary32 values only (DDD, FDD, FDF);
                        no refinement.  A TE_DEVICE matrix over the budget is an error
                        (TE_ERR_OUT_OF_MEMORY). */
+  int32_t autotune; /* 1: at plan creation, build the SpMV layout with a few settings of
+                       its window (rows sorted together) and piece length, time each
+                       on this matrix and keep the fastest (te_plan_layout reports it);
+                       resident plans only.  0 (default): window 2048, pieces of 64. */
 } te_options;
 
 /* Fill `opt` with the defaults: seed 0, v1 NULL, largest magnitude, graphs on,
@@ -206,6 +210,10 @@ te_status te_plan_profile(te_plan* plan, double* ms, int32_t* launches, double* 
 
 /* Number of kernels one solve launches (graph nodes when captured). */
 int32_t te_plan_kernel_count(const te_plan* plan);
+
+/* The SpMV layout of the plan: rows sorted together (window) and the longest
+ * piece a row is cut into (vmax). */
+te_status te_plan_layout(const te_plan* plan, int32_t* window, int32_t* vmax);
 
 /* Row blocks each SpMV streams from host memory (0: the matrix is resident). */
 int64_t te_plan_stream_blocks(const te_plan* plan);
@@ -343,19 +351,20 @@ void te_server_destroy(te_server* srv);
 
 /* Host-side layout behind the SpMV (no GPU needed; row_ptr in host memory):
  * the SELL-C-sigma arrangement a plan builds (Kreutzer et al., SIAM J. Sci.
- * Comput. 2014).  Rows are cut into pieces of at most 64 entries; within each
- * window of 2048 consecutive rows the pieces are sorted by length (longest
- * first) and grouped into slices of 32 lanes, each slice padded to its
- * longest piece.  Writes the slice count, the padded entry count and the
+ * Comput. 2014).  Rows are cut into pieces of at most vmax entries (0: 64);
+ * within each window of `window` consecutive rows (0: 2048) the pieces are
+ * sorted by length (longest first) and grouped into slices of 32 lanes, each
+ * slice padded to its longest piece.  Writes the slice count, the padded entry count and the
  * number of rows cut into several pieces.  Optional per-slice output
  * slice_len[nslices]; optional per-lane outputs (32 * nslices entries):
  * lane_out = the row the lane sums (>= 0), -1 - p for piece p of a cut row,
  * or INT32_MIN for an empty lane; lane_src = first CSR entry of its piece;
  * lane_len = entries of its piece.  Returns TE_ERR_INVALID_ARG for a
  * malformed row_ptr. */
-te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int64_t* nslices,
-                         int64_t* entries, int64_t* nlong_rows, int32_t* slice_len,
-                         int32_t* lane_out, int64_t* lane_src, int32_t* lane_len);
+te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t window,
+                         int32_t vmax, int64_t* nslices, int64_t* entries, int64_t* nlong_rows,
+                         int32_t* slice_len, int32_t* lane_out, int64_t* lane_src,
+                         int32_t* lane_len);
 
 #ifdef __cplusplus
 }

@@ -55,7 +55,7 @@ class te_options(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("v1", ctypes.c_void_p), ("which", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("device_budget_bytes", ctypes.c_size_t),
                 ("reorth", ctypes.c_int32), ("refine", ctypes.c_int32),
-                ("matrix_budget_bytes", ctypes.c_size_t)]
+                ("matrix_budget_bytes", ctypes.c_size_t), ("autotune", ctypes.c_int32)]
 
 
 class te_server_options(ctypes.Structure):
@@ -83,6 +83,7 @@ _SIGS = {
     "te_plan_status": (ctypes.c_int, [ctypes.c_void_p]),
     "te_plan_kernel_count": (ctypes.c_int32, [ctypes.c_void_p]),
     "te_plan_stream_blocks": (ctypes.c_int64, [ctypes.c_void_p]),
+    "te_plan_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "te_plan_destroy": (None, [ctypes.c_void_p]),
     "te_spmv": (ctypes.c_int, [ctypes.c_void_p, te_precision, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_void_p]),
@@ -113,6 +114,7 @@ _SIGS = {
     "te_gram": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p]),
     "te_spmv_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
@@ -218,7 +220,7 @@ class CSR:
 
 
 def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full",
-             refine=False, matrix_budget=0) -> te_options:
+             refine=False, matrix_budget=0, autotune=False) -> te_options:
     o = te_options()
     load_library().te_default_options(ctypes.byref(o))
     o.seed = seed
@@ -229,6 +231,7 @@ def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full
     o.reorth = REORTH[reorth] if isinstance(reorth, str) else int(reorth)
     o.refine = 1 if refine else 0
     o.matrix_budget_bytes = matrix_budget
+    o.autotune = 1 if autotune else 0
     return o
 
 
@@ -264,11 +267,13 @@ class Plan:
 
     def __init__(self, csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0,
                  v1=None, which="LM", use_graph: bool = True, budget: int = 0,
-                 reorth="full", refine: bool = False, matrix_budget: int = 0, stream=None):
+                 reorth="full", refine: bool = False, matrix_budget: int = 0,
+                 autotune: bool = False, stream=None):
         self._lib = load_library()
         self.csr, self.K, self.m, self.n = csr, K, krylov_steps, csr.n
         A = csr.to_ctypes()
-        opt = _options(seed, v1, which, use_graph, budget, reorth, refine, matrix_budget)
+        opt = _options(seed, v1, which, use_graph, budget, reorth, refine, matrix_budget,
+                       autotune)
         h = ctypes.c_void_p()
         rc = self._lib.te_plan_create(ctypes.byref(A), K, krylov_steps, _prec(precision),
                                       ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h))
@@ -278,6 +283,13 @@ class Plan:
     @property
     def kernel_count(self) -> int:
         return int(self._lib.te_plan_kernel_count(self._h))
+
+    @property
+    def layout(self):
+        """(window, vmax) of the plan's SpMV layout."""
+        w, v = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.te_plan_layout(self._h, ctypes.byref(w), ctypes.byref(v)))
+        return w.value, v.value
 
     @property
     def stream_blocks(self) -> int:
@@ -467,7 +479,7 @@ def spmv_noalloc(csr: CSR, x, y=None, precision="ddd", stream=None):
     return y
 
 
-def spmv_layout(row_ptr, nnz: int):
+def spmv_layout(row_ptr, nnz: int, window: int = 0, vmax: int = 0):
     """The SELL-C-sigma layout a plan builds for the SpMV (host analysis):
     returns a dict with slice lengths [S], and per lane (32 per slice) the
     output (row, -1 - piece, or INT32_MIN), the first CSR entry and the length
@@ -477,17 +489,19 @@ def spmv_layout(row_ptr, nnz: int):
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     n = len(rp) - 1
     ns, ne, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    rc = lib.te_spmv_layout(ctypes.c_void_p(rp.ctypes.data), n, nnz, ctypes.byref(ns),
-                            ctypes.byref(ne), ctypes.byref(nl), None, None, None, None)
+    rc = lib.te_spmv_layout(ctypes.c_void_p(rp.ctypes.data), n, nnz, window, vmax,
+                            ctypes.byref(ns), ctypes.byref(ne), ctypes.byref(nl), None, None,
+                            None, None)
     _check(rc)
     S = ns.value
     slen = np.zeros(S, dtype=np.int32)
     lout = np.zeros(S * 32, dtype=np.int32)
     lsrc = np.zeros(S * 32, dtype=np.int64)
     llen = np.zeros(S * 32, dtype=np.int32)
-    rc = lib.te_spmv_layout(ctypes.c_void_p(rp.ctypes.data), n, nnz, None, None, None,
-                            ctypes.c_void_p(slen.ctypes.data), ctypes.c_void_p(lout.ctypes.data),
-                            ctypes.c_void_p(lsrc.ctypes.data), ctypes.c_void_p(llen.ctypes.data))
+    rc = lib.te_spmv_layout(ctypes.c_void_p(rp.ctypes.data), n, nnz, window, vmax, None, None,
+                            None, ctypes.c_void_p(slen.ctypes.data),
+                            ctypes.c_void_p(lout.ctypes.data), ctypes.c_void_p(lsrc.ctypes.data),
+                            ctypes.c_void_p(llen.ctypes.data))
     _check(rc)
     return {"slice_len": slen, "lane_out": lout, "lane_src": lsrc, "lane_len": llen,
             "entries": int(ne.value), "long_rows": int(nl.value)}

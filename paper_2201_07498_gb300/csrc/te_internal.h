@@ -80,7 +80,9 @@ struct SellHost {
 };
 constexpr int SELL_BIG_PIECES = 16;  // cut rows with more pieces get a whole warp
 // returns false (and a message) if row_ptr is malformed
-bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err);
+// window: rows sorted together (sigma); vmax: longest piece (rows above are cut)
+bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err,
+               int window = SELL_WINDOW, int vmax = SELL_VMAX);
 
 // Device copy of a SELL layout.
 struct DevSell {

@@ -167,6 +167,7 @@ struct te_plan {
   int in_type = TE_F64;  // type of the caller's values (TE_F64 or the precision's)
   int vk = TE_F64;       // storage type of the plan's copy of the values
   bool refine = false, noreorth = false;
+  int sell_window = SELL_WINDOW, sell_vmax = SELL_VMAX;  // the SpMV layout's parameters
   te_options opt{};
   const int64_t* rp = nullptr;
   const int32_t* ci = nullptr;
@@ -294,6 +295,77 @@ cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const
   if (q) cudaFree(q);
   if (rscale) cudaFree(rscale);
   return e;
+}
+
+// SpMV layout candidates (rows sorted together, longest piece) tried by the
+// autotuner; the first is the default
+constexpr int TUNE_N = 5;
+constexpr int TUNE_WINDOW[TUNE_N] = {SELL_WINDOW, SELL_WINDOW, SELL_WINDOW, 256, 16384};
+constexpr int TUNE_VMAX[TUNE_N] = {SELL_VMAX, 32, 128, SELL_VMAX, SELL_VMAX};
+
+// Build each candidate layout of the device CSR (rp, ci, val) in temporary
+// memory, time its SpMV (CUDA events on s, after two warm-up calls), and
+// return the index of the fastest.
+cudaError_t autotune_layout(int prec, int vk, int in_type, const int64_t* rph, const int64_t* rp,
+                            const int32_t* ci, const void* val, int64_t n, int64_t nnz,
+                            cudaStream_t s, int* best) {
+  *best = 0;
+  float best_ms = 0.f;
+  const size_t xelt = prec == PREC_DDD ? 8 : 4;
+  for (int c = 0; c < TUNE_N; ++c) {
+    SellHost H;
+    std::string err;
+    if (!make_sell(rph, n, nnz, H, err, TUNE_WINDOW[c], TUNE_VMAX[c])) return cudaErrorInvalidValue;
+    const size_t b_sl = al256(std::max<size_t>(H.slices.size(), 1) * sizeof(SellSlice));
+    const size_t b_vo = al256(std::max<size_t>(H.vout.size(), 1) * 4);
+    const size_t b_co = al256(std::max<size_t>((size_t)H.entries, 1) * 4);
+    const size_t b_va = al256(std::max<size_t>((size_t)H.entries, 1) * elt_of(vk));
+    const size_t b_lr = al256(std::max<size_t>(H.lrows.size(), 1) * sizeof(LongRow));
+    const size_t b_vp = al256(std::max<size_t>((size_t)H.pieces, 1) * 8);
+    const size_t b_ls = vk == TE_FP8_E4M3 ? b_vo : 0;
+    const size_t b_x = al256((size_t)n * xelt), b_y = al256((size_t)n * 8);
+    char* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, b_sl + b_vo + b_co + b_va + b_lr + b_vp + b_ls + b_x + b_y);
+    if (e != cudaSuccess) return e;
+    DevSell D;
+    size_t off = 0;
+    D.slices = reinterpret_cast<SellSlice*>(buf);
+    D.vout = reinterpret_cast<int32_t*>(buf + (off += b_sl));
+    D.cols = reinterpret_cast<int32_t*>(buf + (off += b_vo));
+    D.vals = buf + (off += b_co);
+    D.lrows = reinterpret_cast<LongRow*>(buf + (off += b_va));
+    D.vpart = buf + (off += b_lr);
+    float* ls = b_ls ? reinterpret_cast<float*>(buf + (off += b_vp)) : nullptr;
+    if (!b_ls) off += b_vp;
+    void* x = buf + (off += b_ls);
+    void* y = buf + off + b_x;
+    D.vk = vk;
+    D.lscale = ls;
+    D.nslices = (int)H.slices.size();
+    D.nlrows = (int)H.lrows.size();
+    D.nlbig = (int)H.nbig;
+    e = cudaMemsetAsync(x, 0, b_x + b_y, s);
+    if (e == cudaSuccess) e = upload_sell(in_type, H, rp, ci, val, n, nnz, D, nullptr, ls, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int it = 0; it < 2 && e == cudaSuccess; ++it) e = launch_spmv(prec, D, x, y, false, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int it = 0; it < 5 && e == cudaSuccess; ++it) e = launch_spmv(prec, D, x, y, false, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (e != cudaSuccess) return e;
+    if (c == 0 || ms < best_ms) {
+      best_ms = ms;
+      *best = c;
+    }
+  }
+  return cudaSuccess;
 }
 
 PassArgs base_args(te_plan* P) {
@@ -748,6 +820,49 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     if (cur.nslices > 0) P->blocks.push_back(cur);
   }
 
+  if (opt.autotune && !P->streaming) {
+    // the device CSR the candidates are built from (a host matrix is copied
+    // for the trials); its columns are checked before any SpMV reads them
+    const size_t in_elt = in_type == TE_F64 ? 8 : 4;
+    const int64_t* drp = A->row_ptr;
+    const int32_t* dci = A->col_idx;
+    const void* dval = A->values;
+    char* tmp = nullptr;
+    if (A->where == TE_HOST) {
+      const size_t brp = al256(sizeof(int64_t) * (A->n + 1)), bci = al256(4 * (size_t)A->nnz);
+      TE_CK(cudaMalloc(&tmp, brp + bci + in_elt * (size_t)A->nnz + 256), "allocate tuning CSR");
+      TE_CK(cudaMemcpyAsync(tmp, A->row_ptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyHostToDevice,
+                            s),
+            "copy row_ptr");
+      TE_CK(cudaMemcpyAsync(tmp + brp, A->col_idx, 4 * (size_t)A->nnz, cudaMemcpyHostToDevice, s),
+            "copy col_idx");
+      TE_CK(cudaMemcpyAsync(tmp + brp + bci, A->values, in_elt * (size_t)A->nnz,
+                            cudaMemcpyHostToDevice, s),
+            "copy values");
+      drp = reinterpret_cast<const int64_t*>(tmp);
+      dci = reinterpret_cast<const int32_t*>(tmp + brp);
+      dval = tmp + brp + bci;
+    }
+    int* flag = nullptr;
+    cudaError_t e = cudaMalloc(&flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_validate_cols(dci, A->nnz, A->n, flag, s);
+    int hflag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (flag) cudaFree(flag);
+    int best = 0;
+    if (e == cudaSuccess && !hflag)
+      e = autotune_layout(P->prec, P->vk, in_type, rph, drp, dci, dval, A->n, A->nnz, s, &best);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune the SpMV layout");
+    if (hflag) return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
+    P->sell_window = TUNE_WINDOW[best];
+    P->sell_vmax = TUNE_VMAX[best];
+    if (best != 0 && !make_sell(rph, A->n, A->nnz, sell, perr, P->sell_window, P->sell_vmax))
+      return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+  }
+
   SellSizes zs;
   zs.slices = sell.slices.size();
   zs.entries = P->streaming ? (size_t)(2 * P->cap_entries) : (size_t)sell.entries;
@@ -892,6 +1007,13 @@ te_status te_plan_status(te_plan* P) {
 }
 
 int32_t te_plan_kernel_count(const te_plan* P) { return P ? P->nkernels : 0; }
+
+te_status te_plan_layout(const te_plan* P, int32_t* window, int32_t* vmax) {
+  if (!P) return fail(TE_ERR_INVALID_ARG, "plan is NULL");
+  if (window) *window = P->sell_window;
+  if (vmax) *vmax = P->sell_vmax;
+  return TE_OK;
+}
 
 int64_t te_plan_stream_blocks(const te_plan* P) {
   return (P && P->streaming) ? (int64_t)P->blocks.size() : 0;
@@ -1199,13 +1321,18 @@ te_status te_gram(int64_t n, int32_t K, const double* U, double* G, void* stream
   return TE_OK;
 }
 
-te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int64_t* nslices,
-                         int64_t* entries, int64_t* nlong_rows, int32_t* slice_len,
-                         int32_t* lane_out, int64_t* lane_src, int32_t* lane_len) {
+te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t window,
+                         int32_t vmax, int64_t* nslices, int64_t* entries, int64_t* nlong_rows,
+                         int32_t* slice_len, int32_t* lane_out, int64_t* lane_src,
+                         int32_t* lane_len) {
   if (!row_ptr || n < 1 || nnz < 0) return fail(TE_ERR_INVALID_ARG, "bad arguments");
+  if (window == 0) window = SELL_WINDOW;
+  if (vmax == 0) vmax = SELL_VMAX;
+  if (window < 1 || vmax < 1 || vmax > 1024)
+    return fail(TE_ERR_INVALID_ARG, "window >= 1 and 1 <= vmax <= 1024");
   SellHost sell;
   std::string perr;
-  if (!make_sell(row_ptr, n, nnz, sell, perr))
+  if (!make_sell(row_ptr, n, nnz, sell, perr, window, vmax))
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
   if (nslices) *nslices = (int64_t)sell.slices.size();
   if (entries) *entries = sell.entries;

@@ -29,31 +29,32 @@ namespace te {
 
 // Windows of rows [w0, w1) into `out`, with entry offsets and cut-row piece
 // slots numbered from 0 (the caller shifts them).
-static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, SellHost& out) {
+static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, int window,
+                         int vmax, SellHost& out) {
   struct Piece {
     int64_t src;
     int32_t len, out, row;
   };
   std::vector<Piece> win, sorted;
-  std::vector<int64_t> pos(SELL_VMAX + 2);
+  std::vector<int64_t> pos((size_t)vmax + 2);
   for (int64_t w = w0; w < w1; ++w) {
-    const int64_t r0 = w * SELL_WINDOW, r1 = std::min<int64_t>(r0 + SELL_WINDOW, n);
+    const int64_t r0 = w * window, r1 = std::min<int64_t>(r0 + window, n);
     win.clear();
     for (int64_t r = r0; r < r1; ++r) {
       const int64_t L = rp[r + 1] - rp[r];
       if (L == 0) continue;  // empty rows: never written by the kernel
-      if (L <= SELL_VMAX) {
+      if (L <= vmax) {
         win.push_back({rp[r], (int32_t)L, (int32_t)r, (int32_t)r});
         continue;
       }
       LongRow lr;
       lr.row = (int32_t)r;
       lr.first = (int32_t)out.pieces;
-      lr.count = (int32_t)((L + SELL_VMAX - 1) / SELL_VMAX);
+      lr.count = (int32_t)((L + vmax - 1) / vmax);
       lr.pad_ = 0;
       for (int32_t c = 0; c < lr.count; ++c) {
-        const int64_t s0 = rp[r] + (int64_t)c * SELL_VMAX;
-        const int64_t l = std::min<int64_t>(SELL_VMAX, rp[r + 1] - s0);
+        const int64_t s0 = rp[r] + (int64_t)c * vmax;
+        const int64_t l = std::min<int64_t>(vmax, rp[r + 1] - s0);
         win.push_back({s0, (int32_t)l, -1 - (int32_t)(out.pieces + c), (int32_t)r});
       }
       out.pieces += lr.count;
@@ -64,7 +65,7 @@ static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, S
     std::fill(pos.begin(), pos.end(), 0);
     for (const Piece& p : win) ++pos[p.len];
     int64_t acc = 0;
-    for (int L = SELL_VMAX; L >= 1; --L) {
+    for (int L = vmax; L >= 1; --L) {
       const int64_t c = pos[L];
       pos[L] = acc;
       acc += c;
@@ -98,7 +99,8 @@ static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, S
 
 // Threads take contiguous ranges of windows; the parts are joined with their
 // entry and piece offsets, so the result equals a sequential build.
-bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err) {
+bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err,
+               int window, int vmax) {
   out = SellHost();
   if (rp[0] != 0) {
     err = "row_ptr[0] must be 0";
@@ -108,7 +110,7 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
     err = "row_ptr[n] != nnz";
     return false;
   }
-  const int64_t W = (n + SELL_WINDOW - 1) / SELL_WINDOW;
+  const int64_t W = (n + window - 1) / window;
   unsigned nt = std::thread::hardware_concurrency();
   if (nt < 1) nt = 1;
   if (nt > 32) nt = 32;
@@ -117,13 +119,13 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
   std::vector<SellHost> part(nt);
   auto work = [&](unsigned t) {
     const int64_t w0 = W * t / nt, w1 = W * (t + 1) / nt;
-    const int64_t r0 = w0 * SELL_WINDOW, r1 = std::min<int64_t>(w1 * SELL_WINDOW, n);
+    const int64_t r0 = w0 * window, r1 = std::min<int64_t>(w1 * window, n);
     for (int64_t r = r0; r < r1; ++r)
       if (rp[r + 1] < rp[r]) {
         bad[t] = r;
         return;
       }
-    sell_windows(rp, n, w0, w1, part[t]);
+    sell_windows(rp, n, w0, w1, window, vmax, part[t]);
   };
   if (nt == 1) {
     work(0);

@@ -154,7 +154,7 @@ def test_workspace_bytes(te):
 VMAX, C, WINDOW = 64, 32, 2048
 
 
-def _check_layout(rp, L):
+def _check_layout(rp, L, VMAX=VMAX, WINDOW=WINDOW):
     """Every entry of every non-empty row is summed by exactly one lane piece;
     short rows are one lane, cut rows are contiguous pieces of <= VMAX; slices
     hold pieces of one window, longest first, padded to their longest piece."""
@@ -220,6 +220,14 @@ def test_layout_covers_every_entry_once(te):
     L = te.spmv_layout(rp, int(rp[-1]))
     _check_layout(rp, L)
     assert L["long_rows"] == 6
+
+
+@pytest.mark.parametrize("window,vmax", [(2048, 32), (2048, 128), (256, 64), (16384, 64), (7, 5)])
+def test_layout_parameters_cover_every_entry_once(te, window, vmax):
+    """The autotuner's candidate layouts (and an odd one) keep every property."""
+    for A in (synth.rmat_sym(13, 8, 2), synth.uniform_sym(3000, 6, 3)):
+        L = te.spmv_layout(A.row_ptr, A.nnz, window, vmax)
+        _check_layout(A.row_ptr, L, VMAX=vmax, WINDOW=window)
 
 
 def test_layout_rejects_malformed_row_ptr(te):

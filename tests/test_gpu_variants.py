@@ -303,3 +303,22 @@ def test_refine_recovers_diagonal_eigenvalues_from_reduced_values(te, prec):
     err_raw = np.abs(ev0.numpy() - exact[match_pairs(ev0.numpy(), exact, 0.5)])
     assert np.max(err_ref) <= 1e-11 * 5, err_ref
     assert np.max(err_raw) >= (1e-5 if prec == "bdf" else 1e-8), err_raw
+
+
+@pytest.mark.parametrize("prec,tol", [("ddd", 1e-10), ("fdf", 1e-6)])
+def test_autotuned_plan_matches_oracle(te, prec, tol):
+    """The autotuner picks one of its candidate layouts; the solve on it
+    matches the oracle like the default layout does."""
+    from test_gpu_parity import threshold_rows
+    for A in (synth.uniform_sym(20000, 8, 7), threshold_rows(symmetric=True)):
+        Ar = A if prec == "ddd" else f32_matrix(A)
+        v1 = synth.start_vector(A.n, 2)
+        ref = oracle.topk_eigs(Ar, 6, 16, v1, seed=2)
+        plan = te.Plan(te.CSR.from_host(A, prec), 6, 16, prec, seed=2, autotune=True,
+                       v1=torch.from_numpy(v1).cuda())
+        assert plan.layout in {(2048, 64), (2048, 32), (2048, 128), (256, 64), (16384, 64)}
+        ev, _, _ = plan.solve()
+        ev = ev.numpy()
+        scale = np.max(np.abs(ref.eigvals))
+        perm = match_pairs(ev, ref.eigvals, tol * scale)
+        assert np.max(np.abs(ev - ref.eigvals[perm])) <= tol * scale
