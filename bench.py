@@ -480,6 +480,15 @@ def main():
                         "the refined residual bounds each value's distance to an eigenvalue",
             },
         })
+        # the layout autotuner on this matrix
+        t0 = time.perf_counter()
+        plan_t = te.Plan(csr_f, K, m, "fdf", seed=args.seed, autotune=True)
+        tune_s = time.perf_counter() - t0
+        ms_t, _, _ = time_plan(plan_t, max(2, args.steps // 2), args.warmup, world)
+        extras["autotune"] = {"layout_window_vmax": list(plan_t.layout), "solve_ms": ms_t,
+                              "spmv_ms": plan_t.profile()["spmv"][0], "plan_create_s": tune_s,
+                              "default_layout_spmv_ms": sp_ms}
+        del plan_t
         Ks, ms_ = max(1, K // 3), max(2, m // 3)
         plan_fs = te.Plan(csr_f, Ks, ms_, "fdf", seed=args.seed)
         ms_fs, ev_fs, _ = time_plan(plan_fs, args.steps, args.warmup, world)
