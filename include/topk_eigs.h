@@ -98,8 +98,12 @@ typedef struct {
 #define TE_WHICH_LARGEST_MAGNITUDE 0 /* |theta| descending; ties: positive, then index */
 #define TE_WHICH_LARGEST_ALGEBRAIC 1 /* theta descending; ties: lower index */
 
-#define TE_REORTH_FULL 0 /* full reorthogonalisation every step (Algorithm 1) */
+#define TE_REORTH_FULL 0 /* full reorthogonalisation every step (Algorithm 1): classical
+                            Gram-Schmidt applied twice, three passes over the basis */
 #define TE_REORTH_NONE 1 /* three-term recurrence only (Section IV-D's comparison) */
+#define TE_REORTH_DELAYED 2 /* full reorthogonalisation with the second sweep of each new
+                            vector delayed into the next step (two passes over the basis
+                            per step; the same vectors up to rounding) */
 
 typedef struct {
   uint64_t seed;    /* SplitMix64 seed: start vector = stream 0, restart r = stream r */

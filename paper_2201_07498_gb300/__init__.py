@@ -24,7 +24,7 @@ __all__ = ["CSR", "Plan", "Server", "TEError", "topk_eigs", "spmv", "lanczos", "
 TE_F64, TE_F32, TE_BF16, TE_FP8_E4M3 = 0, 1, 2, 3
 TE_DEVICE, TE_HOST = 0, 1
 WHICH = {"LM": 0, "LA": 1}
-REORTH = {"full": 0, "none": 1}
+REORTH = {"full": 0, "none": 1, "delayed": 2}
 PRECISIONS = {"ddd": (TE_F64, TE_F64, TE_F64), "fdd": (TE_F32, TE_F64, TE_F64),
               "fdf": (TE_F32, TE_F64, TE_F32),
               "bdf": (TE_BF16, TE_F64, TE_F32), "8df": (TE_FP8_E4M3, TE_F64, TE_F32)}

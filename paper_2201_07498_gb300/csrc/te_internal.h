@@ -14,7 +14,11 @@ namespace te {
 
 constexpr int MAX_M = 64;        // largest supported krylov_steps
 constexpr int TILE_R = 256;      // rows per tile of the basis passes
-constexpr int PSTRIDE = MAX_M + 4;  // per-CTA partial slots (columns + 2 norms)
+// per-CTA partial slots: dots with the pass vector at [0, MAX_M], dots with
+// the candidate column at [SLOT_D2, SLOT_D2 + MAX_M], two norms at SLOT_N
+constexpr int SLOT_D2 = MAX_M + 1;
+constexpr int SLOT_N = 2 * MAX_M + 2;
+constexpr int PSTRIDE = 2 * MAX_M + 4;
 constexpr int CONSUMERS = 256;   // compute threads of the basis passes
 constexpr int PASS_THREADS = CONSUMERS + 32;  // + one producer warp
 constexpr int MAX_STAGES = 16;
@@ -29,6 +33,10 @@ struct LzState {
   double c1[MAX_M + 2];     // coefficients of the first axpy pass
   double c2[MAX_M + 2];     // coefficients of the second axpy pass
   double xscale;            // multiplier of the source vector in the first axpy
+  double f2;                // delayed reorthogonalisation: coefficient of the candidate
+  double bt[MAX_M + 2];     // delayed: norm of each candidate after one sweep
+  int rflag[MAX_M + 2];     // delayed: column set by a restart (its beta is 0)
+  double cj[MAX_M + 2];     // delayed: second-sweep coefficients of the candidate
   double anorm;             // max_j |alpha_j| + beta_j + beta_{j+1}
   double theta_sel[MAX_M];  // selected Ritz values (selection order)
   double resid_est[MAX_M];  // |beta_{m+1} y_k[m-1]|
@@ -126,7 +134,14 @@ cudaError_t launch_validate_cols(const int32_t* ci, int64_t nnz, int64_t n, int*
                                  cudaStream_t s);
 
 // ---- basis passes ----
-enum PassMode : int { MODE_DOT = 0, MODE_AXPY_DOT = 1, MODE_AXPY_STORE = 2, MODE_RITZ = 3 };
+enum PassMode : int {
+  MODE_DOT = 0,
+  MODE_AXPY_DOT = 1,
+  MODE_AXPY_STORE = 2,
+  MODE_RITZ = 3,
+  MODE_DCGS_DOT = 4,    // delayed: dots of every column with y and with the candidate
+  MODE_DCGS_UPDATE = 5  // delayed: finish the candidate column, form the next one
+};
 enum XSource : int { X_VEC = 0, X_RANDOM = 1, X_V1 = 2 };
 enum Finalize : int {
   FIN_DOT_STEP = 0,
@@ -138,7 +153,9 @@ enum Finalize : int {
   FIN_NONE = 6,
   FIN_AXPYDOT_STEP = 7,  // second-sweep coefficients and alpha = h1_i + h2_i
   FIN_DOT_NOREORTH = 8,  // alpha_i alone and the three-term coefficients
-  FIN_STORE_NOREORTH = 9 // beta_{i+1} of the three-term update (source scaled by s_i)
+  FIN_STORE_NOREORTH = 9, // beta_{i+1} of the three-term update (source scaled by s_i)
+  FIN_DCGS_DOT = 10,       // delayed: rho, beta_i, alpha_i and the update coefficients
+  FIN_DCGS_UPDATE = 11     // delayed: norm and scale of the next candidate, breakdown
 };
 
 struct PassArgs {
@@ -149,7 +166,8 @@ struct PassArgs {
   int nb;            // basis columns read by this pass: col0 .. col0 + nb - 1
   int col0;          // first basis column read (0 unless reorthogonalisation is off)
   int exact_tail;    // FDF phase A: the last exact_tail columns in double-float
-  int col_out;       // column written by AXPY_STORE
+  int col_out;       // column written by AXPY_STORE (the next candidate in DCGS_UPDATE)
+  int col_fix;       // DCGS_UPDATE: the candidate column rewritten as final
   int step;          // Lanczos step (0-based)
   int m;             // krylov steps of the solve
   int K;             // eigenpairs (RITZ)

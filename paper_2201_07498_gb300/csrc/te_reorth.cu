@@ -53,7 +53,7 @@ constexpr int RITZ_KC = 8;                      // Ritz outputs per register blo
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct SmemPlan {
-  size_t region, ws_off, coef_off, ritz_off, red_off, bar_off, total;
+  size_t region, ws_off, coef_off, coef2_off, ritz_off, red_off, bar_off, total;
 };
 // ritz_elems: m*K coefficients held by the Ritz pass (0 for the other passes)
 __host__ __device__ inline SmemPlan smem_plan(int mode, size_t region, int ritz_elems) {
@@ -61,10 +61,11 @@ __host__ __device__ inline SmemPlan smem_plan(int mode, size_t region, int ritz_
   p.region = region;
   p.ws_off = align_up(region, 128);
   p.coef_off = p.ws_off + TILE_R * 8;
-  p.ritz_off = p.coef_off + (MAX_M + 2) * 8;
+  p.coef2_off = p.coef_off + (MAX_M + 2) * 8;
+  p.ritz_off = p.coef2_off + (MAX_M + 2) * 8;
   size_t ritz = (mode == MODE_RITZ) ? align_up((size_t)ritz_elems * 8, 128) : 0;
   p.red_off = p.ritz_off + ritz;
-  p.bar_off = align_up(p.red_off + 64 * 8, 8);
+  p.bar_off = align_up(p.red_off + PSTRIDE * 8, 8);
   p.total = p.bar_off + 2 * MAX_STAGES * 8 + 16;
   return p;
 }
@@ -201,6 +202,68 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       }
       break;
     }
+    case FIN_DCGS_DOT: {
+      // Delayed second sweep of the candidate u_i = sig S_i (unit norm after
+      // its first sweep): c_j = v_j . u_i, rho = ||u_i - V c||, v_i = (u_i -
+      // V c) / rho.  tot[j] = S_j . ytilde, tot[nb + j] = S_j . S_i, with
+      // ytilde = M S_i.  M v_j of the final columns follows the three-term
+      // relation, so sum_j c_j M v_j = sum_k t_k v_k (second order in c).
+      const int ni = a.nb - 1;  // = i
+      const double sig = st->s[i];
+      double* cj = st->cj;
+      double rho = 1.0, cc = 0.0;
+      for (int j = 0; j < ni; ++j) {
+        cj[j] = st->s[j] * sig * tot[a.nb + j];
+        cc += cj[j] * cj[j];
+      }
+      if (ni > 0) {
+        const double r2 = sig * sig * tot[a.nb + ni] - cc;
+        rho = r2 > 0.0 ? sqrt(r2) : 0.0;
+        if (!(rho > 0.0)) {
+          st->status = TE_ERR_BREAKDOWN;
+          rho = 1.0;
+        }
+      }
+      const double beta_i = (ni == 0 || st->rflag[i]) ? 0.0 : st->bt[i] * rho;
+      st->beta[i] = beta_i;
+      st->s[i] = sig / rho;
+      double scg = 0.0;
+      for (int j = 0; j < ni; ++j) scg += cj[j] * st->s[j] * tot[j];
+      const double vy = (sig * tot[ni] - scg) / rho;  // v_i . ytilde
+      const double t_i = ni > 0 ? cj[ni - 1] * beta_i : 0.0;
+      const double al = (sig * vy - t_i) / rho;       // alpha_i = v_i . M v_i
+      st->alpha[i] = al;
+      const double F = t_i / rho + al;
+      for (int k = 0; k < ni; ++k) {
+        double tk = cj[k] * st->alpha[k];
+        if (k > 0) tk += cj[k - 1] * st->beta[k];
+        if (k + 1 < ni) tk += cj[k + 1] * st->beta[k + 1];
+        const double hk = (sig * st->s[k] * tot[k] - tk) / rho;  // v_k . M v_i
+        st->c1[k] = cj[k] * st->s[k] / sig;
+        st->c2[k] = ((tk / rho + hk) - F * cj[k] / rho) * st->s[k];
+      }
+      st->f2 = F * sig / rho;
+      st->xscale = sig / rho;
+      break;
+    }
+    case FIN_DCGS_UPDATE: {
+      // tot[0] = ||w||^2 (the next candidate after its first sweep), tot[1] =
+      // ||stored(w)||^2; its second sweep (and final beta) comes next step
+      const double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
+      const double ns = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);
+      st->bt[i + 1] = b;
+      st->s[i + 1] = ns > 0.0 ? 1.0 / ns : 0.0;
+      st->rflag[i + 1] = 0;
+      const double cand = fabs(st->alpha[i]) + st->beta[i] + b;
+      if (cand > st->anorm) st->anorm = cand;
+      st->restart_flag = 0;
+      if (i + 1 < a.m && !(b > a.tol * st->anorm)) {
+        st->restart_flag = 1;
+        st->rflag[i + 1] = 1;
+      }
+      if (i + 1 == a.m) st->beta[i + 1] = b;  // beta_{m+1}: residual estimates
+      break;
+    }
     case FIN_STORE_RESTART: {
       const double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
       const double ns = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);
@@ -217,6 +280,7 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       st->beta[0] = 0.0;
       st->anorm = 0.0;
       st->restart_flag = 0;
+      for (int j = 0; j < MAX_M + 2; ++j) st->rflag[j] = 0;
       break;
     }
     default:
@@ -240,6 +304,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   using coef_t = typename Tr::coef_t;
   constexpr bool HAS_AXPY = (MODE == MODE_AXPY_DOT || MODE == MODE_AXPY_STORE);
   constexpr bool HAS_DOT = (MODE == MODE_DOT || MODE == MODE_AXPY_DOT);
+  constexpr bool DDOT = (MODE == MODE_DCGS_DOT);
+  constexpr bool DUPD = (MODE == MODE_DCGS_UPDATE);
 
   extern __shared__ __align__(128) unsigned char sm[];
   LzState* st = a.st;
@@ -250,6 +316,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   basis_t* stg = reinterpret_cast<basis_t*>(sm);
   vec_t* ws = reinterpret_cast<vec_t*>(sm + L.ws_off);
   coef_t* coef = reinterpret_cast<coef_t*>(sm + L.coef_off);
+  coef_t* coef2 = reinterpret_cast<coef_t*>(sm + L.coef2_off);
   coef_t* rC = reinterpret_cast<coef_t*>(sm + L.ritz_off);
   acc_t* red = reinterpret_cast<acc_t*>(sm + L.red_off);
   double* tot = reinterpret_cast<double*>(sm + L.red_off);  // reused by the last CTA
@@ -282,6 +349,12 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   }
   if constexpr (MODE == MODE_AXPY_STORE) {
     for (int j = tid; j < nb; j += PASS_THREADS) coef[j] = to_coef<P>(st->c2[j]);
+  }
+  if constexpr (DUPD) {
+    for (int j = tid; j < nb - 1; j += PASS_THREADS) {
+      coef[j] = to_coef<P>(st->c1[j]);
+      coef2[j] = to_coef<P>(st->c2[j]);
+    }
   }
   if constexpr (MODE == MODE_RITZ) {
     if (st->eigvecs == nullptr) return;  // uniform: no vectors requested
@@ -325,13 +398,17 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   }
 
   // ------------------------- consumer warps -------------------------
-  const double xs_d = (MODE == MODE_AXPY_DOT) ? st->xscale : 1.0;
+  const double xs_d = (MODE == MODE_AXPY_DOT || DUPD) ? st->xscale : 1.0;
   coef_t xscale = to_coef<P>(xs_d);
+  const coef_t fcand = to_coef<P>(DUPD ? st->f2 : 0.0);
+  basis_t* Vfix = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_fix * a.ld;
   const uint64_t rstream = (a.xsrc == X_V1) ? 0ull : (uint64_t)(st->restarts + 1);
   const double* v1 = st->v1;
-  acc_t dots[QMAX];
+  acc_t dots[QMAX], dots2[DDOT ? QMAX : 1];
 #pragma unroll
   for (int q = 0; q < QMAX; ++q) dots[q] = zero_acc<P>();
+#pragma unroll
+  for (int q = 0; q < (DDOT ? QMAX : 1); ++q) dots2[q] = zero_acc<P>();
   acc_t n1 = zero_acc<P>(), n2 = zero_acc<P>();
   basis_t* Vout = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_out * a.ld;
 
@@ -421,8 +498,123 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
           n1 = fma(w, w, n1);
         }
       }
-    } else if constexpr (MODE == MODE_DOT) {
+    } else if constexpr (MODE == MODE_DOT || DDOT) {
       ws[tid] = x;
+    }
+
+    if constexpr (DUPD) {
+      // delayed reorthogonalisation, thread per row: the candidate column
+      // (tile column nb-1) loses its components along the final columns
+      // (coefficients e1, all small) and is stored back as final; the next
+      // candidate is w = xscale * y - sum_k e2_k S_k - f2 * candidate, where
+      // only e2 of column nb-2 (the beta term) and f2 (the alpha term) can be
+      // large and are taken in double-float.
+      const basis_t sc = tv[(size_t)(nb - 1) * TILE_R + tid];
+      const int nj = nb - 1;
+      vec_t w;
+      if constexpr (P == PREC_FDF) {
+        const int nsmall = nj > 1 ? nj - 1 : 0;
+        float f1[4] = {0.f, 0.f, 0.f, 0.f}, g1[4] = {0.f, 0.f, 0.f, 0.f};
+        int j = 0;
+        for (; j + 4 <= nsmall; j += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float v = tv[(size_t)(j + u) * TILE_R + tid];
+            f1[u] = __fmaf_rn(v, coef[j + u].x, f1[u]);
+            g1[u] = __fmaf_rn(v, coef2[j + u].x, g1[u]);
+          }
+        }
+        for (; j < nsmall; ++j) {
+          const float v = tv[(size_t)j * TILE_R + tid];
+          f1[0] = __fmaf_rn(v, coef[j].x, f1[0]);
+          g1[0] = __fmaf_rn(v, coef2[j].x, g1[0]);
+        }
+        dacc t2 = dacc_zero();
+        dacc_add_pair(t2, __fadd_rn(g1[0], g1[1]), __fadd_rn(g1[2], g1[3]));
+        for (; j < nj; ++j) {
+          const float v = tv[(size_t)j * TILE_R + tid];
+          f1[0] = __fmaf_rn(v, coef[j].x, f1[0]);
+          acc_fma<P>(t2, v, coef2[j]);
+        }
+        acc_fma<P>(t2, sc, fcand);
+        const float t1 = __fadd_rn(__fadd_rn(f1[0], f1[1]), __fadd_rn(f1[2], f1[3]));
+        if (nj > 0) Vfix[row] = __fsub_rn(sc, t1);
+        const dw sx = dw_mul(dw_from_f2(xscale), dw_from_f2(x));
+        w = dw_to_f2(dw_sub(sx, dacc_value(t2)));
+        Vout[row] = w.x;
+        dacc_fma(n1, w.x, w.x, 2.0f * w.y);
+        dacc_fma(n2, w.x, w.x, 0.0f);
+      } else {
+        double t1 = 0.0, t2 = 0.0;
+        for (int j = 0; j < nj; ++j) {
+          const double v = tv[(size_t)j * TILE_R + tid];
+          t1 = fma(v, coef[j], t1);
+          t2 = fma(v, coef2[j], t2);
+        }
+        t2 = fma(sc, fcand, t2);
+        if (nj > 0) Vfix[row] = sc - t1;
+        w = fma(xscale, x, -t2);
+        Vout[row] = w;
+        n1 = fma(w, w, n1);
+      }
+    }
+
+    if constexpr (DDOT) {
+      named_bar_sync(1, CONSUMERS);
+      // delayed reorthogonalisation, warp per column: the dot of every column
+      // with y (the first sweep of the new vector) and with the candidate
+      // column nb-1 (the second sweep of the previous one).  Binary32 chunks
+      // for the columns before the candidate (their errors are removed by the
+      // next step's sweep); the candidate's own two dots (u' y gives alpha,
+      // u' u its norm) exactly.
+      const basis_t* cand = tv + (size_t)(nb - 1) * TILE_R;
+      if constexpr (P == PREC_FDF) {
+        float wx[TILE_R / 32], wy[TILE_R / 32], cx[TILE_R / 32];
+#pragma unroll
+        for (int rr = 0; rr < TILE_R / 32; ++rr) {
+          const float2 t = ws[lane + 32 * rr];
+          wx[rr] = t.x;
+          wy[rr] = t.y;
+          cx[rr] = cand[lane + 32 * rr];
+        }
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+          const int jj = wid + (CONSUMERS / 32) * q;
+          if (jj >= nb) break;
+          const basis_t* col = tv + (size_t)jj * TILE_R;
+          if (jj < nb - 1) {
+            float c0 = 0.f, c1 = 0.f, d0 = 0.f, d1 = 0.f;
+#pragma unroll
+            for (int rr = 0; rr < TILE_R / 32; rr += 2) {
+              const float v0 = col[lane + 32 * rr], v1 = col[lane + 32 * (rr + 1)];
+              c0 = __fmaf_rn(v0, wx[rr], c0);
+              c1 = __fmaf_rn(v1, wx[rr + 1], c1);
+              d0 = __fmaf_rn(v0, cx[rr], d0);
+              d1 = __fmaf_rn(v1, cx[rr + 1], d1);
+            }
+            dacc_add_pair(dots[q], c0, c1);
+            dacc_add_pair(dots2[q], d0, d1);
+          } else {
+#pragma unroll
+            for (int rr = 0; rr < TILE_R / 32; ++rr) {
+              dacc_fma(dots[q], col[lane + 32 * rr], wx[rr], wy[rr]);
+              dacc_fma(dots2[q], col[lane + 32 * rr], cx[rr], 0.0f);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+          const int jj = wid + (CONSUMERS / 32) * q;
+          if (jj >= nb) break;
+          const basis_t* col = tv + (size_t)jj * TILE_R;
+#pragma unroll
+          for (int rr = 0; rr < TILE_R / 32; ++rr) {
+            dots[q] = fma(col[lane + 32 * rr], ws[lane + 32 * rr], dots[q]);
+            dots2[q] = fma(col[lane + 32 * rr], cand[lane + 32 * rr], dots2[q]);
+          }
+        }
+      }
     }
 
     if constexpr (HAS_DOT) {
@@ -531,7 +723,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if constexpr (HAS_DOT) named_bar_sync(1, CONSUMERS);
+    if constexpr (HAS_DOT || DDOT) named_bar_sync(1, CONSUMERS);
   }
 
   if (a.fin == FIN_NONE) return;
@@ -549,7 +741,20 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
       }
     }
   }
-  if constexpr (MODE == MODE_AXPY_STORE) {
+  if constexpr (DDOT) {
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      const int jj = wid + (CONSUMERS / 32) * q;
+      if (jj < nb) {
+        const acc_t v = warp_sum(dots[q]), v2 = warp_sum(dots2[q]);
+        if (lane == 0) {
+          put_partial<P>(a.partials, (size_t)cta * PSTRIDE + jj, v);
+          put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_D2 + jj, v2);
+        }
+      }
+    }
+  }
+  if constexpr (MODE == MODE_AXPY_STORE || DUPD) {
     if constexpr (P == PREC_DDD) n2 = n1;
     n1 = warp_sum(n1);
     n2 = warp_sum(n2);
@@ -564,8 +769,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
         t1 = acc_merge<P>(t1, red[2 * w]);
         t2 = acc_merge<P>(t2, red[2 * w + 1]);
       }
-      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + MAX_M, t1);
-      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + MAX_M + 1, t2);
+      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_N, t1);
+      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_N + 1, t2);
     }
   }
 
@@ -579,9 +784,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   named_bar_sync(1, CONSUMERS);
   if (*lastflag == 0) return;
   __threadfence();
-  const int slots = (MODE == MODE_AXPY_STORE) ? 2 : nb;
+  const int slots = (MODE == MODE_AXPY_STORE || DUPD) ? 2 : (DDOT ? 2 * nb : nb);
   for (int q = wid; q < slots; q += CONSUMERS / 32) {
-    const int slot = (MODE == MODE_AXPY_STORE) ? MAX_M + q : q;
+    const int slot = (MODE == MODE_AXPY_STORE || DUPD) ? SLOT_N + q
+                     : (DDOT && q >= nb)               ? SLOT_D2 + (q - nb)
+                                                       : q;
     acc_t acc = zero_acc<P>();
     for (int b = lane; b < ncta; b += 32)
       add_partial<P>(acc, a.partials, (size_t)b * PSTRIDE + slot);
@@ -740,6 +947,10 @@ cudaError_t pass_config(int prec, int mode, int max_cols, int K, int num_sms, Pa
   TE_CFG(PREC_DDD, MODE_AXPY_DOT)
   TE_CFG(PREC_DDD, MODE_AXPY_STORE)
   TE_CFG(PREC_DDD, MODE_RITZ)
+  TE_CFG(PREC_DDD, MODE_DCGS_DOT)
+  TE_CFG(PREC_DDD, MODE_DCGS_UPDATE)
+  TE_CFG(PREC_FDF, MODE_DCGS_DOT)
+  TE_CFG(PREC_FDF, MODE_DCGS_UPDATE)
   TE_CFG(PREC_FDF, MODE_DOT)
   TE_CFG(PREC_FDF, MODE_AXPY_DOT)
   TE_CFG(PREC_FDF, MODE_AXPY_STORE)
@@ -759,6 +970,10 @@ cudaError_t launch_pass(int prec, int mode, const PassArgs& a, const PassLaunch&
   TE_LAUNCH(PREC_DDD, MODE_AXPY_DOT)
   TE_LAUNCH(PREC_DDD, MODE_AXPY_STORE)
   TE_LAUNCH(PREC_DDD, MODE_RITZ)
+  TE_LAUNCH(PREC_DDD, MODE_DCGS_DOT)
+  TE_LAUNCH(PREC_DDD, MODE_DCGS_UPDATE)
+  TE_LAUNCH(PREC_FDF, MODE_DCGS_DOT)
+  TE_LAUNCH(PREC_FDF, MODE_DCGS_UPDATE)
   TE_LAUNCH(PREC_FDF, MODE_DOT)
   TE_LAUNCH(PREC_FDF, MODE_AXPY_DOT)
   TE_LAUNCH(PREC_FDF, MODE_AXPY_STORE)

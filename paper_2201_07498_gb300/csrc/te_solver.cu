@@ -166,7 +166,7 @@ struct te_plan {
   int K = 0, m = 0;
   int in_type = TE_F64;  // type of the caller's values (TE_F64 or the precision's)
   int vk = TE_F64;       // storage type of the plan's copy of the values
-  bool refine = false, noreorth = false;
+  bool refine = false, noreorth = false, delayed = false;
   int sell_window = SELL_WINDOW, sell_vmax = SELL_VMAX;  // the SpMV layout's parameters
   te_options opt{};
   const int64_t* rp = nullptr;
@@ -194,7 +194,7 @@ struct te_plan {
   Work W;
   char* work = nullptr;
   LzState* st = nullptr;
-  PassLaunch Ldot, Laxd, Lsto, Lritz;
+  PassLaunch Ldot, Laxd, Lsto, Lritz, Lddot, Ldupd;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int nkernels = 0;
@@ -411,24 +411,28 @@ double pass_bytes(te_plan* P, int mode, const PassArgs& a) {
     case MODE_DOT: return vcols + n * 8.0;
     case MODE_AXPY_DOT: return vcols + 2.0 * n * 8.0;
     case MODE_AXPY_STORE: return vcols + n * 8.0 + n * sb;
+    case MODE_DCGS_DOT: return vcols + n * 8.0;
+    case MODE_DCGS_UPDATE: return vcols + n * 8.0 + 2.0 * n * sb;
     default: return vcols + n * 8.0 * (double)P->K;
   }
 }
 
 cudaError_t pass(te_plan* P, int mode, const PassArgs& a, cudaStream_t s) {
-  const PassLaunch& L = mode == MODE_DOT        ? P->Ldot
-                        : mode == MODE_AXPY_DOT ? P->Laxd
-                        : mode == MODE_AXPY_STORE ? P->Lsto
-                                                  : P->Lritz;
+  const PassLaunch& L = mode == MODE_DOT           ? P->Ldot
+                        : mode == MODE_AXPY_DOT    ? P->Laxd
+                        : mode == MODE_AXPY_STORE  ? P->Lsto
+                        : mode == MODE_DCGS_DOT    ? P->Lddot
+                        : mode == MODE_DCGS_UPDATE ? P->Ldupd
+                                                   : P->Lritz;
   P->nkernels++;
   cudaError_t e = prof_begin(P, s);
   if (e != cudaSuccess) return e;
   e = launch_pass(P->prec, mode, a, L, s);
   if (e != cudaSuccess) return e;
-  int kind = mode == MODE_DOT          ? TE_KIND_DOT
-             : mode == MODE_AXPY_DOT   ? TE_KIND_AXPY_DOT
-             : mode == MODE_AXPY_STORE ? TE_KIND_AXPY_STORE
-                                       : TE_KIND_RITZ;
+  int kind = (mode == MODE_DOT || mode == MODE_DCGS_DOT)            ? TE_KIND_DOT
+             : mode == MODE_AXPY_DOT                                  ? TE_KIND_AXPY_DOT
+             : (mode == MODE_AXPY_STORE || mode == MODE_DCGS_UPDATE) ? TE_KIND_AXPY_STORE
+                                                                      : TE_KIND_RITZ;
   if (a.only_on_restart) kind = TE_KIND_RESTART;
   if (a.fin == FIN_STORE_INIT) kind = TE_KIND_OTHER;
   return prof_end(P, s, kind, a.only_on_restart ? 0.0 : pass_bytes(P, mode, a));
@@ -519,7 +523,19 @@ cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
     a.step = i;
     a.xsrc = X_VEC;
     a.xvec = at(P, P->W.ytil);
-    if (P->noreorth) {
+    if (P->delayed) {
+      // full reorthogonalisation with the candidate's second sweep delayed:
+      // the SpMV ran on candidate column i; one pass takes the dots of every
+      // column with y and with the candidate, one pass finishes column i and
+      // forms the next candidate (column i+1)
+      a.nb = i + 1;
+      a.fin = FIN_DCGS_DOT;
+      if ((e = pass(P, MODE_DCGS_DOT, a, s)) != cudaSuccess) return e;
+      a.col_out = i + 1;
+      a.col_fix = i;
+      a.fin = FIN_DCGS_UPDATE;
+      if ((e = pass(P, MODE_DCGS_UPDATE, a, s)) != cudaSuccess) return e;
+    } else if (P->noreorth) {
       // three-term recurrence only: alpha_i from v_i alone, then
       // w / s_i = ytilde - alpha_i stored_i - (beta_i s_{i-1} / s_i) stored_{i-1}
       a.col0 = i;
@@ -724,8 +740,9 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   else te_default_options(&opt);
   if (opt.which != TE_WHICH_LARGEST_MAGNITUDE && opt.which != TE_WHICH_LARGEST_ALGEBRAIC)
     return fail(TE_ERR_INVALID_ARG, "which must be TE_WHICH_*");
-  if (opt.reorth != TE_REORTH_FULL && opt.reorth != TE_REORTH_NONE)
-    return fail(TE_ERR_INVALID_ARG, "reorth must be TE_REORTH_FULL or TE_REORTH_NONE");
+  if (opt.reorth != TE_REORTH_FULL && opt.reorth != TE_REORTH_NONE &&
+      opt.reorth != TE_REORTH_DELAYED)
+    return fail(TE_ERR_INVALID_ARG, "reorth must be TE_REORTH_FULL, _NONE or _DELAYED");
   if (opt.refine != 0 && opt.refine != 1) return fail(TE_ERR_INVALID_ARG, "refine must be 0 or 1");
   const int in_type = A->values_f64 ? TE_F64 : p.values;
   if (opt.refine && in_type != TE_F64)
@@ -758,6 +775,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   P->vk = p.values;
   P->refine = opt.refine != 0;
   P->noreorth = opt.reorth == TE_REORTH_NONE;
+  P->delayed = opt.reorth == TE_REORTH_DELAYED;
   TE_CK(cudaGetDevice(&P->dev), "cudaGetDevice");
   TE_CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev),
         "device attribute");
@@ -786,6 +804,12 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
         "configure store pass");
   TE_CK(pass_config(P->prec, MODE_RITZ, P->m, P->K, P->num_sms, P->Lritz),
         "configure ritz pass");
+  if (P->delayed) {
+    TE_CK(pass_config(P->prec, MODE_DCGS_DOT, P->m, P->K, P->num_sms, P->Lddot),
+          "configure dot pass");
+    TE_CK(pass_config(P->prec, MODE_DCGS_UPDATE, P->m, P->K, P->num_sms, P->Ldupd),
+          "configure update pass");
+  }
   const int grid = std::max(std::max(P->Ldot.grid, P->Laxd.grid),
                             std::max(P->Lsto.grid, P->Lritz.grid));
 

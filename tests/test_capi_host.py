@@ -102,7 +102,7 @@ def test_option_validation_before_gpu(te):
                                 ctypes.c_void_p(ev.ctypes.data), None, None, None)
 
     assert call(A, refine=1) == 1 and b"binary64" in lib.te_last_error()
-    assert call(A, reorth=2) == 1
+    assert call(A, reorth=3) == 1
     assert call(A, refine=3) == 1
     A.values_f64 = 2
     assert call(A) == 1

@@ -118,3 +118,26 @@ def test_fullsize_fdf_solve_in_benchmark_configuration(te, big):
         r = te.spmv(csr_d, u, "ddd") - ev_f[k] * u
         true = float(torch.linalg.norm(r)) / float(torch.linalg.norm(u))
         assert abs(true - res_f[k].item()) <= 1e-5 + 1e-2 * res_f[k].item(), (k, true, res_f[k])
+
+
+def test_fullsize_delayed_reorth_in_benchmark_configuration(te, big):
+    """The benchmark's form: FDF with the delayed second sweep.  The FP64
+    solve's converged pairs (both with the delayed sweep and with classical
+    Gram-Schmidt twice) are reproduced within 1e-6, and the basis stays
+    orthogonal to the binary32 level."""
+    A, _ = big
+    K, m = 24, 48
+    plan_f = te.Plan(te.CSR.from_host(A, "fdf"), K, m, "fdf", seed=SEED, reorth="delayed")
+    ev_f, _, res_f = plan_f.solve(vectors=False, residuals=True)
+    del plan_f
+    csr_d = te.CSR.from_host(A, "ddd")
+    for mode in ("delayed", "full"):
+        plan_d = te.Plan(csr_d, K, m, "ddd", seed=SEED, reorth=mode)
+        ev_d, _, res_d = plan_d.solve(vectors=False, residuals=True)
+        del plan_d
+        ev_d, res_d = ev_d.numpy(), res_d.numpy()
+        converged = np.nonzero(res_d <= 1e-9)[0]
+        assert len(converged) >= 2
+        for k in converged:
+            assert np.min(np.abs(ev_f.numpy() - ev_d[k])) <= 1e-6, (mode, k, ev_d[k])
+    assert np.all(np.abs(ev_f.numpy()) <= 1 + 1e-6)

@@ -322,3 +322,75 @@ def test_autotuned_plan_matches_oracle(te, prec, tol):
         scale = np.max(np.abs(ref.eigvals))
         perm = match_pairs(ev, ref.eigvals, tol * scale)
         assert np.max(np.abs(ev - ref.eigvals[perm])) <= tol * scale
+
+
+# ---------------------------------------------------------------------------
+# full reorthogonalisation with the second sweep delayed into the next step
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [("ddd", 1e-10), ("fdf", 1e-6)])
+def test_lanczos_delayed_matches_oracle(te, prec, tol):
+    A = synth.uniform_sym(10000, 10, 0)
+    Ar = A if prec == "ddd" else f32_matrix(A)
+    v1 = synth.start_vector(A.n, 0)
+    m = 24
+    ref = oracle.lanczos(Ar, v1, m)
+    alpha, beta, V, _ = te.lanczos(te.CSR.from_host(A, prec), m, prec,
+                                   v1=torch.from_numpy(v1).cuda(), reorth="delayed")
+    tn = np.linalg.norm(ref.T())
+    assert np.max(np.abs(alpha.numpy() - ref.alpha)) <= tol * tn
+    assert np.max(np.abs(beta.numpy() - ref.beta)) <= tol * tn
+    Vh = V.cpu().numpy()
+    assert np.max(np.abs(Vh.T @ Vh - np.eye(m))) <= (1e-12 if prec == "ddd" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["ddd", "fdf"])
+def test_topk_delayed_matches_oracle(te, prec):
+    from test_gpu_parity import SOLVE_CASES
+    tol = 1e-10 if prec == "ddd" else 1e-6
+    for name, make, K, m, which in SOLVE_CASES:
+        A = make()
+        Ar = A if prec == "ddd" else f32_matrix(A)
+        v1 = synth.start_vector(A.n, 3)
+        w = oracle.LARGEST_MAGNITUDE if which == "LM" else oracle.LARGEST_ALGEBRAIC
+        ref = oracle.topk_eigs(Ar, K, m, v1, which=w, seed=3)
+        ev, U, res = te.topk_eigs(te.CSR.from_host(A, prec), K, m, prec, seed=3,
+                                  v1=torch.from_numpy(v1).cuda(), which=which, residuals=True,
+                                  reorth="delayed")
+        ev = ev.numpy()
+        scale = np.max(np.abs(ref.eigvals))
+        assert selection_order_valid(ev, which), name
+        perm = match_pairs(ev, ref.eigvals, tol * scale)
+        assert np.max(np.abs(ev - ref.eigvals[perm])) <= tol * scale, name
+        if prec == "ddd":
+            ang = subspace_angles(U.cpu().numpy(), ref.eigvecs[:, perm], ref.eigvals[perm])
+            assert np.max(ang) <= 1e-8, (name, ang)
+
+
+@pytest.mark.parametrize("prec", ["ddd", "fdf"])
+def test_delayed_closed_forms_and_restarts(te, prec):
+    """m = n: the path Laplacian's spectrum; the cycle's needs restarts
+    (eigenvalues of multiplicity two) and recovers every copy."""
+    tol = 1e-11 if prec == "ddd" else 1e-5
+    n = 40
+    ev, _, _ = te.topk_eigs(te.CSR.from_host(synth.path_laplacian(n), prec), n, n, prec, seed=5,
+                            vectors=False, reorth="delayed")
+    exact = np.sort(2 - 2 * np.cos(np.pi * np.arange(n) / n))
+    assert np.max(np.abs(np.sort(ev.numpy()) - exact)) <= tol * 4
+    n = 48
+    ev, _, _ = te.topk_eigs(te.CSR.from_host(synth.cycle_laplacian(n), prec), n, n, prec,
+                            seed=2, vectors=False, reorth="delayed")
+    exact = np.sort(2 - 2 * np.cos(2 * np.pi * np.arange(n) / n))
+    assert np.max(np.abs(np.sort(ev.numpy()) - exact)) <= tol * 4
+
+
+@pytest.mark.parametrize("prec", ["ddd", "fdf"])
+def test_delayed_plan_graph_is_deterministic(te, prec):
+    A = synth.rmat_sym(12, 8, 1)
+    plan = te.Plan(te.CSR.from_host(A, prec), 5, 14, prec, seed=9, reorth="delayed")
+    ev1, U1, _ = plan.solve()
+    ev2, U2, _ = plan.solve()
+    assert torch.equal(ev1, ev2) and torch.equal(U1, U2)
+    ev3, _, _ = te.topk_eigs(te.CSR.from_host(A, prec), 5, 14, prec, seed=9)
+    scale = np.max(np.abs(ev3.numpy()))
+    match_pairs(ev1.numpy(), ev3.numpy(), (1e-10 if prec == "ddd" else 1e-5) * scale)
