@@ -487,6 +487,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
       if constexpr (MODE == MODE_AXPY_DOT) {
         static_cast<vec_t*>(a.wout)[row] = w;
         ws[tid] = w;
+        if constexpr (P == PREC_FDF) {
+          // the second-sweep dot of column i (it enters alpha_i) is exact; a
+          // thread per row keeps the warps of phase B balanced
+          dacc_fma(n1, tv[(size_t)(nb - 1) * TILE_R + tid], w.x, w.y);
+        }
       } else {
         // store the next basis vector (unnormalised) and its two norms
         if constexpr (P == PREC_FDF) {
@@ -500,6 +505,18 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
       }
     } else if constexpr (MODE == MODE_DOT || DDOT) {
       ws[tid] = x;
+    }
+    if constexpr (DDOT) {
+      // the candidate's own two dots (u' y gives alpha, u' u its norm) are
+      // exact; a thread per row keeps the warps of phase B balanced
+      const basis_t sc = tv[(size_t)(nb - 1) * TILE_R + tid];
+      if constexpr (P == PREC_FDF) {
+        dacc_fma(n1, sc, x.x, x.y);
+        dacc_fma(n2, sc, sc, 0.0f);
+      } else {
+        n1 = fma(sc, x, n1);
+        n2 = fma(sc, sc, n2);
+      }
     }
 
     if constexpr (DUPD) {
@@ -569,44 +586,34 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
       // u' u its norm) exactly.
       const basis_t* cand = tv + (size_t)(nb - 1) * TILE_R;
       if constexpr (P == PREC_FDF) {
-        float wx[TILE_R / 32], wy[TILE_R / 32], cx[TILE_R / 32];
+        float wx[TILE_R / 32], cx[TILE_R / 32];
 #pragma unroll
         for (int rr = 0; rr < TILE_R / 32; ++rr) {
-          const float2 t = ws[lane + 32 * rr];
-          wx[rr] = t.x;
-          wy[rr] = t.y;
+          wx[rr] = ws[lane + 32 * rr].x;
           cx[rr] = cand[lane + 32 * rr];
         }
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
           const int jj = wid + (CONSUMERS / 32) * q;
-          if (jj >= nb) break;
+          if (jj >= nb - 1) break;
           const basis_t* col = tv + (size_t)jj * TILE_R;
-          if (jj < nb - 1) {
-            float c0 = 0.f, c1 = 0.f, d0 = 0.f, d1 = 0.f;
+          float c0 = 0.f, c1 = 0.f, d0 = 0.f, d1 = 0.f;
 #pragma unroll
-            for (int rr = 0; rr < TILE_R / 32; rr += 2) {
-              const float v0 = col[lane + 32 * rr], v1 = col[lane + 32 * (rr + 1)];
-              c0 = __fmaf_rn(v0, wx[rr], c0);
-              c1 = __fmaf_rn(v1, wx[rr + 1], c1);
-              d0 = __fmaf_rn(v0, cx[rr], d0);
-              d1 = __fmaf_rn(v1, cx[rr + 1], d1);
-            }
-            dacc_add_pair(dots[q], c0, c1);
-            dacc_add_pair(dots2[q], d0, d1);
-          } else {
-#pragma unroll
-            for (int rr = 0; rr < TILE_R / 32; ++rr) {
-              dacc_fma(dots[q], col[lane + 32 * rr], wx[rr], wy[rr]);
-              dacc_fma(dots2[q], col[lane + 32 * rr], cx[rr], 0.0f);
-            }
+          for (int rr = 0; rr < TILE_R / 32; rr += 2) {
+            const float v0 = col[lane + 32 * rr], v1 = col[lane + 32 * (rr + 1)];
+            c0 = __fmaf_rn(v0, wx[rr], c0);
+            c1 = __fmaf_rn(v1, wx[rr + 1], c1);
+            d0 = __fmaf_rn(v0, cx[rr], d0);
+            d1 = __fmaf_rn(v1, cx[rr + 1], d1);
           }
+          dacc_add_pair(dots[q], c0, c1);
+          dacc_add_pair(dots2[q], d0, d1);
         }
       } else {
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
           const int jj = wid + (CONSUMERS / 32) * q;
-          if (jj >= nb) break;
+          if (jj >= nb - 1) break;
           const basis_t* col = tv + (size_t)jj * TILE_R;
 #pragma unroll
           for (int rr = 0; rr < TILE_R / 32; ++rr) {
@@ -637,10 +644,12 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
           wx[rr] = t.x;
           wy[rr] = t.y;
         }
+        // (AXPY_DOT's last column is summed thread per row above)
+        const int jend = MODE == MODE_AXPY_DOT ? nb - 1 : nb;
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
           const int jj = wid + (CONSUMERS / 32) * q;
-          if (jj >= nb) break;
+          if (jj >= jend) break;
           const basis_t* col = tv + (size_t)jj * TILE_R;
           if ((MODE == MODE_DOT && a.fin != FIN_DOT_NOREORTH) ||
               (MODE == MODE_AXPY_DOT && jj < nb - 1)) {
@@ -730,10 +739,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
 
   // ---- per-CTA partial sums ----
   if constexpr (HAS_DOT) {
+    const int jend = (MODE == MODE_AXPY_DOT && P == PREC_FDF) ? nb - 1 : nb;
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) {
       const int jj = wid + (CONSUMERS / 32) * q;
-      if (jj < nb) {
+      if (jj < jend) {
         acc_t v = dots[q];
         if constexpr (P == PREC_FDF) v = warp_sum(v);
         else v = warp_sum(v);
@@ -745,7 +755,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
 #pragma unroll
     for (int q = 0; q < QMAX; ++q) {
       const int jj = wid + (CONSUMERS / 32) * q;
-      if (jj < nb) {
+      if (jj < nb - 1) {
         const acc_t v = warp_sum(dots[q]), v2 = warp_sum(dots2[q]);
         if (lane == 0) {
           put_partial<P>(a.partials, (size_t)cta * PSTRIDE + jj, v);
@@ -754,8 +764,18 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
       }
     }
   }
-  if constexpr (MODE == MODE_AXPY_STORE || DUPD) {
-    if constexpr (P == PREC_DDD) n2 = n1;
+  if constexpr (MODE == MODE_AXPY_DOT && P == PREC_FDF) {
+    n1 = warp_sum(n1);
+    if (lane == 0) red[wid] = n1;
+    named_bar_sync(1, CONSUMERS);
+    if (tid == 0) {
+      acc_t t1 = red[0];
+      for (int w = 1; w < CONSUMERS / 32; ++w) t1 = acc_merge<P>(t1, red[w]);
+      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + nb - 1, t1);
+    }
+  }
+  if constexpr (MODE == MODE_AXPY_STORE || DUPD || DDOT) {
+    if constexpr (P == PREC_DDD && !DDOT) n2 = n1;
     n1 = warp_sum(n1);
     n2 = warp_sum(n2);
     if (lane == 0) {
@@ -769,8 +789,13 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
         t1 = acc_merge<P>(t1, red[2 * w]);
         t2 = acc_merge<P>(t2, red[2 * w + 1]);
       }
-      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_N, t1);
-      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_N + 1, t2);
+      if constexpr (DDOT) {  // the candidate's dots, in its columns' slots
+        put_partial<P>(a.partials, (size_t)cta * PSTRIDE + nb - 1, t1);
+        put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_D2 + nb - 1, t2);
+      } else {
+        put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_N, t1);
+        put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_N + 1, t2);
+      }
     }
   }
 
