@@ -412,20 +412,30 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   acc_t n1 = zero_acc<P>(), n2 = zero_acc<P>();
   basis_t* Vout = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_out * a.ld;
 
+  // the source value of a row: the pass vector, the start vector, or a
+  // seeded random draw (restarts)
+  auto load_x = [&](int64_t row) {
+    vec_t v = vec_zero<P>();
+    if constexpr (MODE != MODE_RITZ) {
+      if (a.xsrc == X_VEC) {
+        v = static_cast<const vec_t*>(a.xvec)[row];
+      } else if (a.xsrc == X_V1 && v1 != nullptr) {
+        if (row < a.n) v = vec_from_double<P>(v1[row]);
+      } else {
+        if (row < a.n) v = vec_from_double<P>(sm64_uniform_pm1(a.seed, rstream, (uint64_t)row));
+      }
+    }
+    return v;
+  };
+  // fetched one tile ahead, so that its load latency hides behind a tile's work
+  vec_t x_next = vec_zero<P>();
+  if (cta < tiles) x_next = load_x((int64_t)cta * TILE_R + tid);
+
   int it = 0;
   for (int64_t t = cta; t < tiles; t += ncta, ++it) {
     const int64_t row = t * TILE_R + tid;
-    // the source value is fetched before waiting on the tile to overlap latency
-    vec_t x = vec_zero<P>();
-    if constexpr (MODE != MODE_RITZ) {
-      if (a.xsrc == X_VEC) {
-        x = static_cast<const vec_t*>(a.xvec)[row];
-      } else if (a.xsrc == X_V1 && v1 != nullptr) {
-        if (row < a.n) x = vec_from_double<P>(v1[row]);
-      } else {
-        if (row < a.n) x = vec_from_double<P>(sm64_uniform_pm1(a.seed, rstream, (uint64_t)row));
-      }
-    }
+    const vec_t x = x_next;
+    if (t + ncta < tiles) x_next = load_x((t + ncta) * TILE_R + tid);
     int s = 0;
     if (nb > 0) {
       s = it % S;
