@@ -163,6 +163,34 @@ def make_inputs(args):
     return A, v1, gen_s
 
 
+# DRAM bytes per SpMV step (slice kernel + cut-row finaliser) measured by ncu
+# on this workload (profiles/spmv_dram_fdf_rmat24_ef8.md), valid for the
+# kernel sources whose SHA-256 is recorded with it
+SPMV_TRAFFIC = {
+    "workload": "rmat24_ef8_normadj_seed1",
+    "bytes_per_step": 3.242e9,
+    "sources": {
+        "paper_2201_07498_gb300/csrc/te_spmv.cu":
+            "dcdcc6ae3f2ef236f5978688d5b0e79adfa936cc168df01fdc4e0059ca057449",
+        "paper_2201_07498_gb300/csrc/te_common.cuh":
+            "5304355202f6101830cdde8e0bda909c110216310622e6ab0cd5c3a37f802bf1",
+    },
+}
+
+
+def spmv_traffic(workload):
+    """The measured traffic when the SpMV sources are unchanged since the
+    capture and the workload matches, else None."""
+    import hashlib
+    if not workload.startswith(SPMV_TRAFFIC["workload"]):
+        return None
+    for path, digest in SPMV_TRAFFIC["sources"].items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return SPMV_TRAFFIC["bytes_per_step"]
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -449,6 +477,9 @@ def main():
     achieved = d_bytes / (d_ms * 1e-3) / 1e9
     sp_ms, sp_n, sp_bytes = prof["spmv"]
     spmv_gbs = sp_bytes / (sp_ms * 1e-3) / 1e9
+    # the gather ceiling: random reads of a table the size of x (binary32)
+    gather_rate = te.probe_gather(int(A.n))
+    spmv_gather_rate = A.nnz * sp_n / (sp_ms * 1e-3)
 
     extras = {}
     if not args.no_extras:
@@ -550,7 +581,18 @@ def main():
             "config": workload_config(args, A),
             "solves_per_s": 1e3 * world / ms_f_max,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": (spmv_traffic(workload_config(args, A)["workload"])
+                                     if dom == "spmv" else None),
+                         "traffic_unit": "bytes per SpMV step (ncu, DRAM read + write)",
+                         "algorithmic_bytes_per_step": d_bytes / max(d_n, 1),
+                         "gather_ceiling": {
+                             "note": "the SpMV reads one scattered 4-byte x value per "
+                                     "non-zero; te_probe_gather measures the GPU's rate of "
+                                     "random reads from a table the size of x",
+                             "probe_gathers_per_s": gather_rate,
+                             "spmv_gathers_per_s": spmv_gather_rate,
+                             "frac": spmv_gather_rate / gather_rate},
                          "peak_kind": peak_kind,
                          "launches_per_solve": d_n, "ms_per_solve": d_ms,
                          "algorithmic_bytes_per_solve": d_bytes},

@@ -279,6 +279,13 @@ te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void* x, double
  * finite with magnitude below 2^127.  Synchronises `stream`. */
 te_status te_quantize(const te_csr* A, int32_t to, void* out, float* row_scale, void* stream);
 
+/* Measure the rate (reads per second) at which the GPU serves random 4-byte
+ * reads from a device table of table_elems floats (the bound of an SpMV whose
+ * column indices are random: one scattered read of x per non-zero).  Best of
+ * two timed launches after one warm-up, CUDA events on `stream`.  Not part of
+ * the paper's method: a measurement for the SpMV's roofline. */
+te_status te_probe_gather(int64_t table_elems, void* stream, double* gathers_per_s);
+
 /* Gram matrix G = U^T U of K vectors (U: n x K, column-major, device), summed
  * in binary64 in a fixed order; G (K x K, row-major) is written to host memory.
  * For the orthogonality metric of Section IV-D (the mean angle between pairs

@@ -111,6 +111,7 @@ _SIGS = {
     "te_server_destroy": (None, [ctypes.c_void_p]),
     "te_server_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "te_probe_gather": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "te_gram": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p]),
     "te_spmv_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -524,6 +525,15 @@ def quantize(csr: CSR, to: str, stream=None):
                          _stream_ptr(stream))
     _check(rc)
     return out[:csr.nnz], scale
+
+
+def probe_gather(table_elems: int, stream=None) -> float:
+    """Random 4-byte reads per second from a device table (the SpMV's gather
+    ceiling)."""
+    lib = load_library()
+    r = ctypes.c_double()
+    _check(lib.te_probe_gather(table_elems, _stream_ptr(stream), ctypes.byref(r)))
+    return r.value
 
 
 def gram(U, stream=None):

@@ -394,3 +394,11 @@ def test_delayed_plan_graph_is_deterministic(te, prec):
     ev3, _, _ = te.topk_eigs(te.CSR.from_host(A, prec), 5, 14, prec, seed=9)
     scale = np.max(np.abs(ev3.numpy()))
     match_pairs(ev1.numpy(), ev3.numpy(), (1e-10 if prec == "ddd" else 1e-5) * scale)
+
+
+def test_gather_probe_reports_a_rate(te):
+    """The gather-ceiling probe runs and a table that fits on chip serves
+    random reads at least as fast as one that does not."""
+    small = te.probe_gather(1 << 12)
+    big = te.probe_gather(1 << 26)
+    assert big > 1e9 and small >= 0.9 * big
