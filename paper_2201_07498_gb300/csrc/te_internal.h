@@ -21,7 +21,7 @@ constexpr int SLOT_N = 2 * MAX_M + 2;
 constexpr int PSTRIDE = 2 * MAX_M + 4;
 constexpr int CONSUMERS = 256;   // compute threads of the basis passes
 constexpr int PASS_THREADS = CONSUMERS + 32;  // + one producer warp
-constexpr int MAX_STAGES = 16;
+constexpr int MAX_STAGES = 32;
 
 enum Prec : int { PREC_DDD = 0, PREC_FDF = 1 };
 
@@ -159,9 +159,12 @@ enum Finalize : int {
 };
 
 struct PassArgs {
-  const void* V;     // stored basis (column-major, leading dimension ld)
+  const void* V;     // stored basis: element (r, c) at (r / TILE_R) * tstride + c * cstride + r % TILE_R
   void* Vmut;        // same buffer, for the column written by AXPY_STORE
   int64_t ld;        // padded rows
+  int64_t tstride;   // elements from a tile to the next tile of the same column
+  int64_t cstride;   // elements from a column to the next (TILE_R: tile-major)
+  void* xcopy;       // optional: the column a pass stores, also written contiguously
   int64_t n;         // true rows
   int nb;            // basis columns read by this pass: col0 .. col0 + nb - 1
   int col0;          // first basis column read (0 unless reorthogonalisation is off)
@@ -276,7 +279,8 @@ double breakdown_tolerance(int prec);
 // ---- small utilities ----
 // record the thread-local message returned by te_last_error()
 void set_last_error(const std::string& msg);
-cudaError_t launch_basis_to_f64(int prec, const void* V, int64_t ld, int64_t n, int cols,
-                                const double* s_dev, double* out, cudaStream_t st);
+cudaError_t launch_basis_to_f64(int prec, const void* V, int64_t tstride, int64_t cstride,
+                                int64_t n, int cols, const double* s_dev, double* out,
+                                cudaStream_t st);
 
 }  // namespace te

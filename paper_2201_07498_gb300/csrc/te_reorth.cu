@@ -4,13 +4,17 @@
 // and the next basis vector, and the Ritz-vector contraction V*Y
 // (Section III).
 //
-// One persistent kernel template serves every pass.  The basis V is stored
-// column-major with a padded leading dimension (a multiple of TILE_R rows, the
-// padding kept at zero); column j holds an unnormalised vector whose scale
-// s_j (so that v_j = s_j * stored_j) lives in the device state.  A CTA owns
-// every gridDim.x-th tile of TILE_R rows.  One producer warp moves the
-// tile's basis columns into shared memory with bulk (TMA) copies into a
-// multi-stage mbarrier pipeline; eight consumer warps then
+// One persistent kernel template serves every pass.  The basis V holds rows
+// padded to a multiple of TILE_R (the padding kept at zero) in tiles of TILE_R
+// rows; a solve plan stores it tile-major (the columns of one tile side by
+// side, so that one bulk copy moves a tile's columns), the serving engine
+// column-major.  Column j holds an unnormalised vector whose scale s_j (so
+// that v_j = s_j * stored_j) lives in the device state.  A stage of the
+// pipeline holds a group of G consecutive tiles (G > 1 when the tiles are
+// small, so that each stage still moves tens of KB) and the pass vector's
+// rows; a CTA owns every gridDim.x-th group.  One producer warp moves the
+// stage into shared memory with bulk (TMA) copies into a multi-stage mbarrier
+// pipeline; eight consumer warps then, tile by tile,
 //   phase A (axpy):  w_r = xscale * x_r - sum_j c_j V[r, j]    (thread per row)
 //   phase B (dots):  g_j += sum_r V[r, j] w_r                  (warp per column)
 // so the second Gram-Schmidt sweep's dot products read the same shared-memory
@@ -35,6 +39,7 @@ struct PassTr<PREC_DDD> {
   using vec_t = double;
   using acc_t = double;
   using coef_t = double;
+  using part_t = double;
 };
 template <>
 struct PassTr<PREC_FDF> {
@@ -42,6 +47,7 @@ struct PassTr<PREC_FDF> {
   using vec_t = float2;
   using acc_t = dacc;
   using coef_t = float2;
+  using part_t = float2;  // a double-float partial sum as stored
 };
 
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
@@ -49,12 +55,20 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;
 __host__ __device__ constexpr int pass_ctas_per_sm(int prec) { return prec == PREC_FDF ? 2 : 1; }
 constexpr int QMAX = MAX_M / (CONSUMERS / 32);  // dot columns per warp
 constexpr int RITZ_KC = 8;                      // Ritz outputs per register block
+constexpr int RED_LOADS = 10;                   // partial loads per lane in flight
+// tile groups of a tile-major basis: stages of up to GROUP_BYTES, at most
+// GROUP_MAX tiles, and at least GROUP_MIN_PER_CTA groups for every CTA
+constexpr uint32_t GROUP_BYTES = 24u << 10;
+constexpr int GROUP_MAX = 16;
+constexpr int GROUP_MIN_PER_CTA = 8;
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct SmemPlan {
-  size_t region, ws_off, coef_off, coef2_off, ritz_off, red_off, bar_off, total;
+  size_t region, ws_off, coef_off, coef2_off, ritz_off, red_off, fin_off, bar_off, total;
 };
+// finalize scratch (doubles): copies of s, alpha, beta, the c_j, warp sums
+constexpr int FIN_SCRATCH = 4 * (MAX_M + 2) + 2 * (CONSUMERS / 32) + 8;
 // ritz_elems: m*K coefficients held by the Ritz pass (0 for the other passes)
 __host__ __device__ inline SmemPlan smem_plan(int mode, size_t region, int ritz_elems) {
   SmemPlan p{};
@@ -65,7 +79,8 @@ __host__ __device__ inline SmemPlan smem_plan(int mode, size_t region, int ritz_
   p.ritz_off = p.coef2_off + (MAX_M + 2) * 8;
   size_t ritz = (mode == MODE_RITZ) ? align_up((size_t)ritz_elems * 8, 128) : 0;
   p.red_off = p.ritz_off + ritz;
-  p.bar_off = align_up(p.red_off + PSTRIDE * 8, 8);
+  p.fin_off = align_up(p.red_off + PSTRIDE * 8, 8);
+  p.bar_off = p.fin_off + FIN_SCRATCH * 8;
   p.total = p.bar_off + 2 * MAX_STAGES * 8 + 16;
   return p;
 }
@@ -115,19 +130,24 @@ TE_DEV typename PassTr<P>::vec_t vec_zero() {
   else return 0.0;
 }
 // partial slot (8 bytes) <-> accumulator
+// per-CTA partial sums, slot-major: the CTAs' values of one slot are adjacent,
+// so that the last CTA reads each slot with coalesced loads
+TE_DEV size_t pidx(int slot, int cta, int ncta) { return (size_t)slot * ncta + cta; }
+
 template <int P>
 TE_DEV void put_partial(void* part, size_t idx, typename PassTr<P>::acc_t a) {
   if constexpr (P == PREC_FDF) static_cast<float2*>(part)[idx] = dw_to_f2(dacc_value(a));
   else static_cast<double*>(part)[idx] = a;
 }
 template <int P>
-TE_DEV void add_partial(typename PassTr<P>::acc_t& acc, const void* part, size_t idx) {
-  if constexpr (P == PREC_FDF) {
-    float2 v = __ldcg(static_cast<const float2*>(part) + idx);
-    dacc_add_pair(acc, v.x, v.y);
-  } else {
-    acc += __ldcg(static_cast<const double*>(part) + idx);
-  }
+TE_DEV typename PassTr<P>::part_t load_partial(const void* part, size_t idx) {
+  using T = typename PassTr<P>::part_t;
+  return __ldcg(static_cast<const T*>(part) + idx);
+}
+template <int P>
+TE_DEV void add_partial(typename PassTr<P>::acc_t& acc, typename PassTr<P>::part_t v) {
+  if constexpr (P == PREC_FDF) dacc_add_pair(acc, v.x, v.y);
+  else acc += v;
 }
 template <int P>
 TE_DEV double acc_to_double(typename PassTr<P>::acc_t a) {
@@ -138,40 +158,47 @@ TE_DEV double acc_to_double(typename PassTr<P>::acc_t a) {
 // ---------------------------------------------------------------------------
 // last-CTA epilogue: turns the reduced sums into the next coefficients
 // ---------------------------------------------------------------------------
-TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
+// Run by every consumer thread of the last CTA (tid = 0 .. CONSUMERS-1): the
+// loops over basis columns are spread over the threads, the scalar updates
+// are made by thread 0.  `scr` is FIN_SCRATCH doubles of shared memory.
+TE_DEV void finalize_pass(const PassArgs& a, const double* tot, double* scr, const int tid) {
   LzState* st = a.st;
   const int i = a.step;
   switch (a.fin) {
     case FIN_DOT_STEP: {
       // tot[j] = stored_j . ytilde with y = s_i ytilde = M v_i
       const double si = st->s[i];
-      for (int j = 0; j < a.nb; ++j) {
-        double h = st->s[j] * si * tot[j];  // v_j . M v_i (first sweep)
-        st->c1[j] = h * st->s[j];
+      for (int j = tid; j < a.nb; j += CONSUMERS) {
+        const double sj = st->s[j];
+        const double h = sj * si * tot[j];  // v_j . M v_i (first sweep)
+        st->c1[j] = h * sj;
       }
       // Algorithm 1's alpha_i = v_i . M v_i; the second sweep adds its
       // correction (FIN_AXPYDOT_STEP), so alpha keeps full accuracy even when
       // the first sweep's dots are taken in binary32 chunks
-      st->alpha[i] = st->s[i] * si * tot[i];
-      st->xscale = si;
+      if (tid == 0) {
+        st->alpha[i] = si * si * tot[i];
+        st->xscale = si;
+      }
       break;
     }
     case FIN_AXPYDOT_STEP: {
-      for (int j = 0; j < a.nb; ++j) st->c2[j] = st->s[j] * st->s[j] * tot[j];
-      st->alpha[i] += st->s[i] * tot[i];  // + v_i . w after the first sweep
+      for (int j = tid; j < a.nb; j += CONSUMERS) st->c2[j] = st->s[j] * st->s[j] * tot[j];
+      if (tid == 0) st->alpha[i] += st->s[i] * tot[i];  // + v_i . w after the first sweep
       break;
     }
     case FIN_DOT_RESTART: {
-      for (int j = 0; j < a.nb; ++j) st->c1[j] = st->s[j] * st->s[j] * tot[j];
-      st->xscale = 1.0;
+      for (int j = tid; j < a.nb; j += CONSUMERS) st->c1[j] = st->s[j] * st->s[j] * tot[j];
+      if (tid == 0) st->xscale = 1.0;
       break;
     }
     case FIN_AXPYDOT: {
-      for (int j = 0; j < a.nb; ++j) st->c2[j] = st->s[j] * st->s[j] * tot[j];
+      for (int j = tid; j < a.nb; j += CONSUMERS) st->c2[j] = st->s[j] * st->s[j] * tot[j];
       break;
     }
     case FIN_STORE_STEP:
     case FIN_STORE_NOREORTH: {
+      if (tid != 0) break;
       // tot[0] = ||w||^2, tot[1] = ||stored(w)||^2 (beta_{i+1} of Algorithm 1);
       // without reorthogonalisation the pass formed w / s_i
       double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
@@ -189,6 +216,7 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       break;
     }
     case FIN_DOT_NOREORTH: {
+      if (tid != 0) break;
       // tot[0] = stored_i . ytilde: alpha_i = v_i . M v_i.  The store pass then
       // forms w / s_i = ytilde - alpha_i stored_i - (beta_i s_{i-1} / s_i) stored_{i-1}
       const double si = st->s[i];
@@ -209,44 +237,74 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       // ytilde = M S_i.  M v_j of the final columns follows the three-term
       // relation, so sum_j c_j M v_j = sum_k t_k v_k (second order in c).
       const int ni = a.nb - 1;  // = i
+      constexpr int NW = CONSUMERS / 32;
+      double* sv = scr;                 // s_j
+      double* av = sv + (MAX_M + 2);    // alpha_j
+      double* bv = av + (MAX_M + 2);    // beta_j
+      double* cj = bv + (MAX_M + 2);    // c_j
+      double* wred = cj + (MAX_M + 2);  // warp sums
+      double* sc = wred + 2 * NW;       // scalars from thread 0
       const double sig = st->s[i];
-      double* cj = st->cj;
-      double rho = 1.0, cc = 0.0;
-      for (int j = 0; j < ni; ++j) {
-        cj[j] = st->s[j] * sig * tot[a.nb + j];
-        cc += cj[j] * cj[j];
+      double pc = 0.0, ps = 0.0;
+      for (int j = tid; j < ni; j += CONSUMERS) {
+        const double sj = st->s[j];
+        sv[j] = sj;
+        av[j] = st->alpha[j];
+        bv[j] = st->beta[j];
+        const double c = sj * sig * tot[a.nb + j];
+        cj[j] = c;
+        pc = fma(c, c, pc);                // ||c||^2
+        ps = fma(c * sj, tot[j], ps);      // sum_j c_j v_j . ytilde / sig
       }
-      if (ni > 0) {
-        const double r2 = sig * sig * tot[a.nb + ni] - cc;
-        rho = r2 > 0.0 ? sqrt(r2) : 0.0;
-        if (!(rho > 0.0)) {
-          st->status = TE_ERR_BREAKDOWN;
-          rho = 1.0;
+      pc = warp_sum(pc);
+      ps = warp_sum(ps);
+      if ((tid & 31) == 0) {
+        wred[tid >> 5] = pc;
+        wred[NW + (tid >> 5)] = ps;
+      }
+      named_bar_sync(1, CONSUMERS);
+      if (tid == 0) {
+        double cc = 0.0, scg = 0.0;
+        for (int w = 0; w < NW; ++w) {
+          cc += wred[w];
+          scg += wred[NW + w];
         }
+        double rho = 1.0;
+        if (ni > 0) {
+          const double r2 = sig * sig * tot[a.nb + ni] - cc;
+          rho = r2 > 0.0 ? sqrt(r2) : 0.0;
+          if (!(rho > 0.0)) {
+            st->status = TE_ERR_BREAKDOWN;
+            rho = 1.0;
+          }
+        }
+        const double beta_i = (ni == 0 || st->rflag[i]) ? 0.0 : st->bt[i] * rho;
+        st->beta[i] = beta_i;
+        st->s[i] = sig / rho;
+        const double vy = (sig * tot[ni] - scg) / rho;  // v_i . ytilde
+        const double t_i = ni > 0 ? cj[ni - 1] * beta_i : 0.0;
+        const double al = (sig * vy - t_i) / rho;       // alpha_i = v_i . M v_i
+        st->alpha[i] = al;
+        const double F = t_i / rho + al;
+        st->f2 = F * sig / rho;
+        st->xscale = sig / rho;
+        sc[0] = rho;
+        sc[1] = F;
       }
-      const double beta_i = (ni == 0 || st->rflag[i]) ? 0.0 : st->bt[i] * rho;
-      st->beta[i] = beta_i;
-      st->s[i] = sig / rho;
-      double scg = 0.0;
-      for (int j = 0; j < ni; ++j) scg += cj[j] * st->s[j] * tot[j];
-      const double vy = (sig * tot[ni] - scg) / rho;  // v_i . ytilde
-      const double t_i = ni > 0 ? cj[ni - 1] * beta_i : 0.0;
-      const double al = (sig * vy - t_i) / rho;       // alpha_i = v_i . M v_i
-      st->alpha[i] = al;
-      const double F = t_i / rho + al;
-      for (int k = 0; k < ni; ++k) {
-        double tk = cj[k] * st->alpha[k];
-        if (k > 0) tk += cj[k - 1] * st->beta[k];
-        if (k + 1 < ni) tk += cj[k + 1] * st->beta[k + 1];
-        const double hk = (sig * st->s[k] * tot[k] - tk) / rho;  // v_k . M v_i
-        st->c1[k] = cj[k] * st->s[k] / sig;
-        st->c2[k] = ((tk / rho + hk) - F * cj[k] / rho) * st->s[k];
+      named_bar_sync(1, CONSUMERS);
+      const double rho = sc[0], F = sc[1];
+      for (int k = tid; k < ni; k += CONSUMERS) {
+        double tk = cj[k] * av[k];
+        if (k > 0) tk += cj[k - 1] * bv[k];
+        if (k + 1 < ni) tk += cj[k + 1] * bv[k + 1];
+        const double hk = (sig * sv[k] * tot[k] - tk) / rho;  // v_k . M v_i
+        st->c1[k] = cj[k] * sv[k] / sig;
+        st->c2[k] = ((tk / rho + hk) - F * cj[k] / rho) * sv[k];
       }
-      st->f2 = F * sig / rho;
-      st->xscale = sig / rho;
       break;
     }
     case FIN_DCGS_UPDATE: {
+      if (tid != 0) break;
       // tot[0] = ||w||^2 (the next candidate after its first sweep), tot[1] =
       // ||stored(w)||^2; its second sweep (and final beta) comes next step
       const double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
@@ -265,6 +323,7 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       break;
     }
     case FIN_STORE_RESTART: {
+      if (tid != 0) break;
       const double b = sqrt(tot[0] > 0.0 ? tot[0] : 0.0);
       const double ns = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);
       if (ns > 0.0 && b > 0.0) st->s[i + 1] = 1.0 / ns;
@@ -274,13 +333,14 @@ TE_DEV void finalize_pass(const PassArgs& a, const double* tot) {
       break;
     }
     case FIN_STORE_INIT: {
+      for (int j = tid; j < MAX_M + 2; j += CONSUMERS) st->rflag[j] = 0;
+      if (tid != 0) break;
       const double ns = sqrt(tot[1] > 0.0 ? tot[1] : 0.0);
       if (ns > 0.0) st->s[0] = 1.0 / ns;
       else st->status = TE_ERR_INVALID_ARG;
       st->beta[0] = 0.0;
       st->anorm = 0.0;
       st->restart_flag = 0;
-      for (int j = 0; j < MAX_M + 2; ++j) st->rflag[j] = 0;
       break;
     }
     default:
@@ -313,7 +373,6 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
     if (*((volatile int*)&st->restart_flag) == 0) return;
   }
   const SmemPlan L = smem_plan(MODE, region, MODE == MODE_RITZ ? a.nb * a.K : 0);
-  basis_t* stg = reinterpret_cast<basis_t*>(sm);
   vec_t* ws = reinterpret_cast<vec_t*>(sm + L.ws_off);
   coef_t* coef = reinterpret_cast<coef_t*>(sm + L.coef_off);
   coef_t* coef2 = reinterpret_cast<coef_t*>(sm + L.coef2_off);
@@ -328,12 +387,32 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int64_t tiles = a.ld / TILE_R;
   const int nb = a.nb;
-  const size_t stage_elems = (size_t)nb * TILE_R;
-  const uint32_t stage_bytes = (uint32_t)(stage_elems * sizeof(basis_t));
+  // A pass vector held in memory travels with the basis tiles: the producer
+  // copies its rows behind the group's columns, so that its latency is hidden
+  // by the same pipeline (it is twice a column's bytes in FDF).
+  const bool xst = MODE != MODE_RITZ && a.xsrc == X_VEC && nb > 0;
+  const uint32_t col_bytes = (uint32_t)((size_t)nb * TILE_R * sizeof(basis_t));
+  const uint32_t xbytes = xst ? (uint32_t)(TILE_R * sizeof(vec_t)) : 0u;
+  // tiles per group: enough for GROUP_BYTES per stage (tile-major basis
+  // only), yet at least GROUP_MIN_PER_CTA groups per CTA
+  int G = 1;
+  if (nb > 0 && a.cstride == TILE_R) {
+    const int64_t gb = (int64_t)(GROUP_BYTES / (col_bytes + xbytes));
+    const int64_t gl = tiles / ((int64_t)ncta * GROUP_MIN_PER_CTA);
+    int64_t g = gb < gl ? gb : gl;
+    if (g > GROUP_MAX) g = GROUP_MAX;
+    if (g > 1) G = (int)g;
+  }
+  const int64_t groups = (tiles + G - 1) / G;
+  const uint32_t stage_bytes = (uint32_t)G * (col_bytes + xbytes);
   int S = 0;
   if (nb > 0) {
     S = (int)(region / stage_bytes);
     if (S > MAX_STAGES) S = MAX_STAGES;
+    if (S < 1) {  // more columns than the launch was configured for
+      if (threadIdx.x == 0) atomicExch(&a.st->status, (int)TE_ERR_INVALID_ARG);
+      return;
+    }
   }
 
   if (tid == 0) *abortflag = 0;
@@ -362,27 +441,40 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   }
   __syncthreads();
 
-  const basis_t* Vg = static_cast<const basis_t*>(a.V) + (size_t)a.col0 * a.ld;
+  const basis_t* Vg = static_cast<const basis_t*>(a.V) + (size_t)a.col0 * a.cstride;
 
   // ------------------------- producer warp -------------------------
   if (wid == CONSUMERS / 32) {
     if (nb > 0 && lane == 0) {
       const uint64_t pol = policy_evict_first();
+      const bool tmaj = a.cstride == TILE_R;
       int it = 0;
       bool ok = true;
-      for (int64_t t = cta; t < tiles; t += ncta, ++it) {
+      for (int64_t T = cta; T < groups; T += ncta, ++it) {
         const int s = it % S, k = it / S;
         if (k > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)((k - 1) & 1), WAIT_LIMIT)) {
           atomicExch(&st->status, (int)TE_ERR_TIMEOUT);
           ok = false;
           break;
         }
-        mbar_arrive_expect_tx(&full[s], stage_bytes);
-        basis_t* dst = stg + (size_t)s * stage_elems;
-        const basis_t* src = Vg + t * TILE_R;
-        for (int j = 0; j < nb; ++j)
-          bulk_g2s(dst + (size_t)j * TILE_R, src + (size_t)j * a.ld,
-                   (uint32_t)(TILE_R * sizeof(basis_t)), &full[s], pol);
+        const int64_t t0 = T * G;
+        const int gc = (int)(tiles - t0 < G ? tiles - t0 : G);
+        mbar_arrive_expect_tx(&full[s], (uint32_t)gc * (col_bytes + xbytes));
+        unsigned char* dst = sm + (size_t)s * stage_bytes;
+        for (int g = 0; g < gc; ++g) {
+          const basis_t* src = Vg + (t0 + g) * a.tstride;
+          basis_t* d = reinterpret_cast<basis_t*>(dst + (size_t)g * col_bytes);
+          if (tmaj) {
+            bulk_g2s(d, src, col_bytes, &full[s], pol);
+          } else {
+            for (int j = 0; j < nb; ++j)
+              bulk_g2s(d + (size_t)j * TILE_R, src + (size_t)j * a.cstride,
+                       (uint32_t)(TILE_R * sizeof(basis_t)), &full[s], pol);
+          }
+        }
+        if (xst)
+          bulk_g2s(dst + (size_t)G * col_bytes, static_cast<const vec_t*>(a.xvec) + t0 * TILE_R,
+                   (uint32_t)gc * xbytes, &full[s], pol);
       }
       // drain: every issued copy must land before this warp retires
       const int issued = it;
@@ -401,7 +493,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   const double xs_d = (MODE == MODE_AXPY_DOT || DUPD) ? st->xscale : 1.0;
   coef_t xscale = to_coef<P>(xs_d);
   const coef_t fcand = to_coef<P>(DUPD ? st->f2 : 0.0);
-  basis_t* Vfix = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_fix * a.ld;
+  basis_t* Vfix = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_fix * a.cstride;
+  basis_t* xcopy = static_cast<basis_t*>(a.xcopy);
   const uint64_t rstream = (a.xsrc == X_V1) ? 0ull : (uint64_t)(st->restarts + 1);
   const double* v1 = st->v1;
   acc_t dots[QMAX], dots2[DDOT ? QMAX : 1];
@@ -410,7 +503,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
 #pragma unroll
   for (int q = 0; q < (DDOT ? QMAX : 1); ++q) dots2[q] = zero_acc<P>();
   acc_t n1 = zero_acc<P>(), n2 = zero_acc<P>();
-  basis_t* Vout = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_out * a.ld;
+  basis_t* Vout = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_out * a.cstride;
 
   // the source value of a row: the pass vector, the start vector, or a
   // seeded random draw (restarts)
@@ -427,15 +520,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
     }
     return v;
   };
-  // fetched one tile ahead, so that its load latency hides behind a tile's work
-  vec_t x_next = vec_zero<P>();
-  if (cta < tiles) x_next = load_x((int64_t)cta * TILE_R + tid);
-
   int it = 0;
-  for (int64_t t = cta; t < tiles; t += ncta, ++it) {
-    const int64_t row = t * TILE_R + tid;
-    const vec_t x = x_next;
-    if (t + ncta < tiles) x_next = load_x((t + ncta) * TILE_R + tid);
+  for (int64_t T = cta; T < groups; T += ncta, ++it) {
     int s = 0;
     if (nb > 0) {
       s = it % S;
@@ -447,302 +533,316 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
       named_bar_sync(1, CONSUMERS);
       if (*abortflag) break;
     }
-    const basis_t* tv = stg + (size_t)s * stage_elems;
+    const unsigned char* sbase = sm + (size_t)s * stage_bytes;
+    const int64_t t0 = T * G;
+    const int gc = (int)(tiles - t0 < G ? tiles - t0 : G);
+    for (int g = 0; g < gc; ++g) {
+      const int64_t t = t0 + g;
+      const int64_t row = t * TILE_R + tid;
+      const int64_t vrow = t * a.tstride + tid;  // this row's element of a basis column
+      const basis_t* tv = reinterpret_cast<const basis_t*>(sbase + (size_t)g * col_bytes);
+      const vec_t* xs = reinterpret_cast<const vec_t*>(sbase + (size_t)G * col_bytes);
+      const vec_t x = xst ? xs[g * TILE_R + tid] : load_x(row);
 
-    if constexpr (HAS_AXPY) {
-      // phase A: t_r = sum_j c_j V[r, j] with four independent chains
-      acc_t tacc;
-      if constexpr (P == PREC_FDF) {
-        // Only two coefficients can be large: those of v_i and v_{i-1} in the
-        // first sweep (alpha_i and beta_i of the three-term recurrence).  The
-        // others sit at the basis' loss-of-orthogonality level, as do all
-        // second-sweep coefficients, so binary32 products and sums of those
-        // columns add an error far below the binary32 rounding of the stored
-        // result.  The host marks the trailing columns whose coefficients can
-        // be large (exact_tail: 2 in the first sweep, all of them without
-        // reorthogonalisation and in restarts); those are taken exactly in
-        // double-float.
-        const int nsmall = nb > a.exact_tail ? nb - a.exact_tail : 0;
-        float f[4] = {0.f, 0.f, 0.f, 0.f};
-        int j = 0;
-        for (; j + 4 <= nsmall; j += 4) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            f[u] = __fmaf_rn(tv[(size_t)(j + u) * TILE_R + tid], coef[j + u].x, f[u]);
-        }
-        for (; j < nsmall; ++j) f[0] = __fmaf_rn(tv[(size_t)j * TILE_R + tid], coef[j].x, f[0]);
-        tacc = dacc_zero();
-        dacc_add_pair(tacc, __fadd_rn(f[0], f[1]), __fadd_rn(f[2], f[3]));
-        for (; j < nb; ++j) acc_fma<P>(tacc, tv[(size_t)j * TILE_R + tid], coef[j]);
-      } else {
-        acc_t ta[4] = {zero_acc<P>(), zero_acc<P>(), zero_acc<P>(), zero_acc<P>()};
-        int j = 0;
-        for (; j + 4 <= nb; j += 4) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            acc_fma<P>(ta[u], tv[(size_t)(j + u) * TILE_R + tid], coef[j + u]);
-        }
-        for (; j < nb; ++j) acc_fma<P>(ta[0], tv[(size_t)j * TILE_R + tid], coef[j]);
-        tacc = acc_merge<P>(acc_merge<P>(ta[0], ta[1]), acc_merge<P>(ta[2], ta[3]));
-      }
-      vec_t w;
-      if constexpr (P == PREC_FDF) {
-        dw xv = dw_from_f2(x);
-        dw sx = (MODE == MODE_AXPY_DOT) ? dw_mul(dw_from_f2(xscale), xv) : xv;
-        dw wd = dw_sub(sx, dacc_value(tacc));
-        w = dw_to_f2(wd);
-      } else {
-        w = (MODE == MODE_AXPY_DOT) ? fma(xscale, x, -tacc) : x - tacc;
-      }
-      if constexpr (MODE == MODE_AXPY_DOT) {
-        static_cast<vec_t*>(a.wout)[row] = w;
-        ws[tid] = w;
+      if constexpr (HAS_AXPY) {
+        // phase A: t_r = sum_j c_j V[r, j] with four independent chains
+        acc_t tacc;
         if constexpr (P == PREC_FDF) {
-          // the second-sweep dot of column i (it enters alpha_i) is exact; a
-          // thread per row keeps the warps of phase B balanced
-          dacc_fma(n1, tv[(size_t)(nb - 1) * TILE_R + tid], w.x, w.y);
+          // Only two coefficients can be large: those of v_i and v_{i-1} in the
+          // first sweep (alpha_i and beta_i of the three-term recurrence).  The
+          // others sit at the basis' loss-of-orthogonality level, as do all
+          // second-sweep coefficients, so binary32 products and sums of those
+          // columns add an error far below the binary32 rounding of the stored
+          // result.  The host marks the trailing columns whose coefficients can
+          // be large (exact_tail: 2 in the first sweep, all of them without
+          // reorthogonalisation and in restarts); those are taken exactly in
+          // double-float.
+          const int nsmall = nb > a.exact_tail ? nb - a.exact_tail : 0;
+          float f[4] = {0.f, 0.f, 0.f, 0.f};
+          int j = 0;
+          for (; j + 4 <= nsmall; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              f[u] = __fmaf_rn(tv[(size_t)(j + u) * TILE_R + tid], coef[j + u].x, f[u]);
+          }
+          for (; j < nsmall; ++j) f[0] = __fmaf_rn(tv[(size_t)j * TILE_R + tid], coef[j].x, f[0]);
+          tacc = dacc_zero();
+          dacc_add_pair(tacc, __fadd_rn(f[0], f[1]), __fadd_rn(f[2], f[3]));
+          for (; j < nb; ++j) acc_fma<P>(tacc, tv[(size_t)j * TILE_R + tid], coef[j]);
+        } else {
+          acc_t ta[4] = {zero_acc<P>(), zero_acc<P>(), zero_acc<P>(), zero_acc<P>()};
+          int j = 0;
+          for (; j + 4 <= nb; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              acc_fma<P>(ta[u], tv[(size_t)(j + u) * TILE_R + tid], coef[j + u]);
+          }
+          for (; j < nb; ++j) acc_fma<P>(ta[0], tv[(size_t)j * TILE_R + tid], coef[j]);
+          tacc = acc_merge<P>(acc_merge<P>(ta[0], ta[1]), acc_merge<P>(ta[2], ta[3]));
         }
-      } else {
-        // store the next basis vector (unnormalised) and its two norms
+        vec_t w;
         if constexpr (P == PREC_FDF) {
-          Vout[row] = w.x;
+          dw xv = dw_from_f2(x);
+          dw sx = (MODE == MODE_AXPY_DOT) ? dw_mul(dw_from_f2(xscale), xv) : xv;
+          dw wd = dw_sub(sx, dacc_value(tacc));
+          w = dw_to_f2(wd);
+        } else {
+          w = (MODE == MODE_AXPY_DOT) ? fma(xscale, x, -tacc) : x - tacc;
+        }
+        if constexpr (MODE == MODE_AXPY_DOT) {
+          static_cast<vec_t*>(a.wout)[row] = w;
+          ws[tid] = w;
+          if constexpr (P == PREC_FDF) {
+            // the second-sweep dot of column i (it enters alpha_i) is exact; a
+            // thread per row keeps the warps of phase B balanced
+            dacc_fma(n1, tv[(size_t)(nb - 1) * TILE_R + tid], w.x, w.y);
+          }
+        } else {
+          // store the next basis vector (unnormalised) and its two norms
+          if constexpr (P == PREC_FDF) {
+            Vout[vrow] = w.x;
+            if (xcopy) xcopy[row] = w.x;
+            dacc_fma(n1, w.x, w.x, 2.0f * w.y);
+            dacc_fma(n2, w.x, w.x, 0.0f);
+          } else {
+            Vout[vrow] = w;
+            if (xcopy) xcopy[row] = w;
+            n1 = fma(w, w, n1);
+          }
+        }
+      } else if constexpr (MODE == MODE_DOT || DDOT) {
+        ws[tid] = x;
+      }
+      if constexpr (DDOT) {
+        // the candidate's own two dots (u' y gives alpha, u' u its norm) are
+        // exact; a thread per row keeps the warps of phase B balanced
+        const basis_t sc = tv[(size_t)(nb - 1) * TILE_R + tid];
+        if constexpr (P == PREC_FDF) {
+          dacc_fma(n1, sc, x.x, x.y);
+          dacc_fma(n2, sc, sc, 0.0f);
+        } else {
+          n1 = fma(sc, x, n1);
+          n2 = fma(sc, sc, n2);
+        }
+      }
+
+      if constexpr (DUPD) {
+        // delayed reorthogonalisation, thread per row: the candidate column
+        // (tile column nb-1) loses its components along the final columns
+        // (coefficients e1, all small) and is stored back as final; the next
+        // candidate is w = xscale * y - sum_k e2_k S_k - f2 * candidate, where
+        // only e2 of column nb-2 (the beta term) and f2 (the alpha term) can be
+        // large and are taken in double-float.
+        const basis_t sc = tv[(size_t)(nb - 1) * TILE_R + tid];
+        const int nj = nb - 1;
+        vec_t w;
+        if constexpr (P == PREC_FDF) {
+          const int nsmall = nj > 1 ? nj - 1 : 0;
+          float f1[4] = {0.f, 0.f, 0.f, 0.f}, g1[4] = {0.f, 0.f, 0.f, 0.f};
+          int j = 0;
+          for (; j + 4 <= nsmall; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float v = tv[(size_t)(j + u) * TILE_R + tid];
+              f1[u] = __fmaf_rn(v, coef[j + u].x, f1[u]);
+              g1[u] = __fmaf_rn(v, coef2[j + u].x, g1[u]);
+            }
+          }
+          for (; j < nsmall; ++j) {
+            const float v = tv[(size_t)j * TILE_R + tid];
+            f1[0] = __fmaf_rn(v, coef[j].x, f1[0]);
+            g1[0] = __fmaf_rn(v, coef2[j].x, g1[0]);
+          }
+          dacc t2 = dacc_zero();
+          dacc_add_pair(t2, __fadd_rn(g1[0], g1[1]), __fadd_rn(g1[2], g1[3]));
+          for (; j < nj; ++j) {
+            const float v = tv[(size_t)j * TILE_R + tid];
+            f1[0] = __fmaf_rn(v, coef[j].x, f1[0]);
+            acc_fma<P>(t2, v, coef2[j]);
+          }
+          acc_fma<P>(t2, sc, fcand);
+          const float t1 = __fadd_rn(__fadd_rn(f1[0], f1[1]), __fadd_rn(f1[2], f1[3]));
+          if (nj > 0) Vfix[vrow] = __fsub_rn(sc, t1);
+          const dw sx = dw_mul(dw_from_f2(xscale), dw_from_f2(x));
+          w = dw_to_f2(dw_sub(sx, dacc_value(t2)));
+          Vout[vrow] = w.x;
+          if (xcopy) xcopy[row] = w.x;
           dacc_fma(n1, w.x, w.x, 2.0f * w.y);
           dacc_fma(n2, w.x, w.x, 0.0f);
         } else {
-          Vout[row] = w;
+          double t1 = 0.0, t2 = 0.0;
+          for (int j = 0; j < nj; ++j) {
+            const double v = tv[(size_t)j * TILE_R + tid];
+            t1 = fma(v, coef[j], t1);
+            t2 = fma(v, coef2[j], t2);
+          }
+          t2 = fma(sc, fcand, t2);
+          if (nj > 0) Vfix[vrow] = sc - t1;
+          w = fma(xscale, x, -t2);
+          Vout[vrow] = w;
+          if (xcopy) xcopy[row] = w;
           n1 = fma(w, w, n1);
         }
       }
-    } else if constexpr (MODE == MODE_DOT || DDOT) {
-      ws[tid] = x;
-    }
-    if constexpr (DDOT) {
-      // the candidate's own two dots (u' y gives alpha, u' u its norm) are
-      // exact; a thread per row keeps the warps of phase B balanced
-      const basis_t sc = tv[(size_t)(nb - 1) * TILE_R + tid];
-      if constexpr (P == PREC_FDF) {
-        dacc_fma(n1, sc, x.x, x.y);
-        dacc_fma(n2, sc, sc, 0.0f);
-      } else {
-        n1 = fma(sc, x, n1);
-        n2 = fma(sc, sc, n2);
-      }
-    }
 
-    if constexpr (DUPD) {
-      // delayed reorthogonalisation, thread per row: the candidate column
-      // (tile column nb-1) loses its components along the final columns
-      // (coefficients e1, all small) and is stored back as final; the next
-      // candidate is w = xscale * y - sum_k e2_k S_k - f2 * candidate, where
-      // only e2 of column nb-2 (the beta term) and f2 (the alpha term) can be
-      // large and are taken in double-float.
-      const basis_t sc = tv[(size_t)(nb - 1) * TILE_R + tid];
-      const int nj = nb - 1;
-      vec_t w;
-      if constexpr (P == PREC_FDF) {
-        const int nsmall = nj > 1 ? nj - 1 : 0;
-        float f1[4] = {0.f, 0.f, 0.f, 0.f}, g1[4] = {0.f, 0.f, 0.f, 0.f};
-        int j = 0;
-        for (; j + 4 <= nsmall; j += 4) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float v = tv[(size_t)(j + u) * TILE_R + tid];
-            f1[u] = __fmaf_rn(v, coef[j + u].x, f1[u]);
-            g1[u] = __fmaf_rn(v, coef2[j + u].x, g1[u]);
-          }
-        }
-        for (; j < nsmall; ++j) {
-          const float v = tv[(size_t)j * TILE_R + tid];
-          f1[0] = __fmaf_rn(v, coef[j].x, f1[0]);
-          g1[0] = __fmaf_rn(v, coef2[j].x, g1[0]);
-        }
-        dacc t2 = dacc_zero();
-        dacc_add_pair(t2, __fadd_rn(g1[0], g1[1]), __fadd_rn(g1[2], g1[3]));
-        for (; j < nj; ++j) {
-          const float v = tv[(size_t)j * TILE_R + tid];
-          f1[0] = __fmaf_rn(v, coef[j].x, f1[0]);
-          acc_fma<P>(t2, v, coef2[j]);
-        }
-        acc_fma<P>(t2, sc, fcand);
-        const float t1 = __fadd_rn(__fadd_rn(f1[0], f1[1]), __fadd_rn(f1[2], f1[3]));
-        if (nj > 0) Vfix[row] = __fsub_rn(sc, t1);
-        const dw sx = dw_mul(dw_from_f2(xscale), dw_from_f2(x));
-        w = dw_to_f2(dw_sub(sx, dacc_value(t2)));
-        Vout[row] = w.x;
-        dacc_fma(n1, w.x, w.x, 2.0f * w.y);
-        dacc_fma(n2, w.x, w.x, 0.0f);
-      } else {
-        double t1 = 0.0, t2 = 0.0;
-        for (int j = 0; j < nj; ++j) {
-          const double v = tv[(size_t)j * TILE_R + tid];
-          t1 = fma(v, coef[j], t1);
-          t2 = fma(v, coef2[j], t2);
-        }
-        t2 = fma(sc, fcand, t2);
-        if (nj > 0) Vfix[row] = sc - t1;
-        w = fma(xscale, x, -t2);
-        Vout[row] = w;
-        n1 = fma(w, w, n1);
-      }
-    }
-
-    if constexpr (DDOT) {
-      named_bar_sync(1, CONSUMERS);
-      // delayed reorthogonalisation, warp per column: the dot of every column
-      // with y (the first sweep of the new vector) and with the candidate
-      // column nb-1 (the second sweep of the previous one).  Binary32 chunks
-      // for the columns before the candidate (their errors are removed by the
-      // next step's sweep); the candidate's own two dots (u' y gives alpha,
-      // u' u its norm) exactly.
-      const basis_t* cand = tv + (size_t)(nb - 1) * TILE_R;
-      if constexpr (P == PREC_FDF) {
-        float wx[TILE_R / 32], cx[TILE_R / 32];
-#pragma unroll
-        for (int rr = 0; rr < TILE_R / 32; ++rr) {
-          wx[rr] = ws[lane + 32 * rr].x;
-          cx[rr] = cand[lane + 32 * rr];
-        }
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-          const int jj = wid + (CONSUMERS / 32) * q;
-          if (jj >= nb - 1) break;
-          const basis_t* col = tv + (size_t)jj * TILE_R;
-          float c0 = 0.f, c1 = 0.f, d0 = 0.f, d1 = 0.f;
-#pragma unroll
-          for (int rr = 0; rr < TILE_R / 32; rr += 2) {
-            const float v0 = col[lane + 32 * rr], v1 = col[lane + 32 * (rr + 1)];
-            c0 = __fmaf_rn(v0, wx[rr], c0);
-            c1 = __fmaf_rn(v1, wx[rr + 1], c1);
-            d0 = __fmaf_rn(v0, cx[rr], d0);
-            d1 = __fmaf_rn(v1, cx[rr + 1], d1);
-          }
-          dacc_add_pair(dots[q], c0, c1);
-          dacc_add_pair(dots2[q], d0, d1);
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-          const int jj = wid + (CONSUMERS / 32) * q;
-          if (jj >= nb - 1) break;
-          const basis_t* col = tv + (size_t)jj * TILE_R;
+      if constexpr (DDOT) {
+        named_bar_sync(1, CONSUMERS);
+        // delayed reorthogonalisation, warp per column: the dot of every column
+        // with y (the first sweep of the new vector) and with the candidate
+        // column nb-1 (the second sweep of the previous one).  Binary32 chunks
+        // for the columns before the candidate (their errors are removed by the
+        // next step's sweep); the candidate's own two dots (u' y gives alpha,
+        // u' u its norm) exactly.
+        const basis_t* cand = tv + (size_t)(nb - 1) * TILE_R;
+        if constexpr (P == PREC_FDF) {
+          float wx[TILE_R / 32], cx[TILE_R / 32];
 #pragma unroll
           for (int rr = 0; rr < TILE_R / 32; ++rr) {
-            dots[q] = fma(col[lane + 32 * rr], ws[lane + 32 * rr], dots[q]);
-            dots2[q] = fma(col[lane + 32 * rr], cand[lane + 32 * rr], dots2[q]);
+            wx[rr] = ws[lane + 32 * rr].x;
+            cx[rr] = cand[lane + 32 * rr];
+          }
+#pragma unroll
+          for (int q = 0; q < QMAX; ++q) {
+            const int jj = wid + (CONSUMERS / 32) * q;
+            if (jj >= nb - 1) break;
+            const basis_t* col = tv + (size_t)jj * TILE_R;
+            float c0 = 0.f, c1 = 0.f, d0 = 0.f, d1 = 0.f;
+#pragma unroll
+            for (int rr = 0; rr < TILE_R / 32; rr += 2) {
+              const float v0 = col[lane + 32 * rr], v1 = col[lane + 32 * (rr + 1)];
+              c0 = __fmaf_rn(v0, wx[rr], c0);
+              c1 = __fmaf_rn(v1, wx[rr + 1], c1);
+              d0 = __fmaf_rn(v0, cx[rr], d0);
+              d1 = __fmaf_rn(v1, cx[rr + 1], d1);
+            }
+            dacc_add_pair(dots[q], c0, c1);
+            dacc_add_pair(dots2[q], d0, d1);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < QMAX; ++q) {
+            const int jj = wid + (CONSUMERS / 32) * q;
+            if (jj >= nb - 1) break;
+            const basis_t* col = tv + (size_t)jj * TILE_R;
+#pragma unroll
+            for (int rr = 0; rr < TILE_R / 32; ++rr) {
+              dots[q] = fma(col[lane + 32 * rr], ws[lane + 32 * rr], dots[q]);
+              dots2[q] = fma(col[lane + 32 * rr], cand[lane + 32 * rr], dots2[q]);
+            }
           }
         }
       }
-    }
 
-    if constexpr (HAS_DOT) {
-      named_bar_sync(1, CONSUMERS);
-      // phase B: warp `wid` owns columns wid, wid+8, ...; lanes stride rows.
-      // The column loop stops at this warp's last column (uniform branch).
-      // FDF sums the dots in binary32 over the tile's 8 rows per lane and
-      // adds each chunk exactly.  For the first sweep the error is removed by
-      // the second; for the second sweep it leaves a component of about
-      // u32 |w| along V, the level of w's own binary32 rounding.  The one
-      // second-sweep dot that enters alpha_i (column i, the last) keeps
-      // exact products and double-float sums, and so does alpha_i's dot
-      // without reorthogonalisation (no second sweep corrects it).  Each
-      // lane's 8 vector values are read from shared memory once per tile.
-      if constexpr (P == PREC_FDF) {
-        float wx[TILE_R / 32], wy[TILE_R / 32];
+      if constexpr (HAS_DOT) {
+        named_bar_sync(1, CONSUMERS);
+        // phase B: warp `wid` owns columns wid, wid+8, ...; lanes stride rows.
+        // The column loop stops at this warp's last column (uniform branch).
+        // FDF sums the dots in binary32 over the tile's 8 rows per lane and
+        // adds each chunk exactly.  For the first sweep the error is removed by
+        // the second; for the second sweep it leaves a component of about
+        // u32 |w| along V, the level of w's own binary32 rounding.  The one
+        // second-sweep dot that enters alpha_i (column i, the last) keeps
+        // exact products and double-float sums, and so does alpha_i's dot
+        // without reorthogonalisation (no second sweep corrects it).  Each
+        // lane's 8 vector values are read from shared memory once per tile.
+        if constexpr (P == PREC_FDF) {
+          float wx[TILE_R / 32], wy[TILE_R / 32];
 #pragma unroll
-        for (int rr = 0; rr < TILE_R / 32; ++rr) {
-          const float2 t = ws[lane + 32 * rr];
-          wx[rr] = t.x;
-          wy[rr] = t.y;
-        }
-        // (AXPY_DOT's last column is summed thread per row above)
-        const int jend = MODE == MODE_AXPY_DOT ? nb - 1 : nb;
+          for (int rr = 0; rr < TILE_R / 32; ++rr) {
+            const float2 t = ws[lane + 32 * rr];
+            wx[rr] = t.x;
+            wy[rr] = t.y;
+          }
+          // (AXPY_DOT's last column is summed thread per row above)
+          const int jend = MODE == MODE_AXPY_DOT ? nb - 1 : nb;
 #pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-          const int jj = wid + (CONSUMERS / 32) * q;
-          if (jj >= jend) break;
-          const basis_t* col = tv + (size_t)jj * TILE_R;
-          if ((MODE == MODE_DOT && a.fin != FIN_DOT_NOREORTH) ||
-              (MODE == MODE_AXPY_DOT && jj < nb - 1)) {
-            float c0 = 0.f, c1 = 0.f;
+          for (int q = 0; q < QMAX; ++q) {
+            const int jj = wid + (CONSUMERS / 32) * q;
+            if (jj >= jend) break;
+            const basis_t* col = tv + (size_t)jj * TILE_R;
+            if ((MODE == MODE_DOT && a.fin != FIN_DOT_NOREORTH) ||
+                (MODE == MODE_AXPY_DOT && jj < nb - 1)) {
+              float c0 = 0.f, c1 = 0.f;
 #pragma unroll
-            for (int rr = 0; rr < TILE_R / 32; rr += 2) {
-              c0 = __fmaf_rn(col[lane + 32 * rr], wx[rr], c0);
-              c1 = __fmaf_rn(col[lane + 32 * (rr + 1)], wx[rr + 1], c1);
+              for (int rr = 0; rr < TILE_R / 32; rr += 2) {
+                c0 = __fmaf_rn(col[lane + 32 * rr], wx[rr], c0);
+                c1 = __fmaf_rn(col[lane + 32 * (rr + 1)], wx[rr + 1], c1);
+              }
+              dacc_add_pair(dots[q], c0, c1);
+            } else {
+              acc_t e0 = zero_acc<P>(), e1 = zero_acc<P>();
+#pragma unroll
+              for (int rr = 0; rr < TILE_R / 32; rr += 2) {
+                dacc_fma(e0, col[lane + 32 * rr], wx[rr], wy[rr]);
+                dacc_fma(e1, col[lane + 32 * (rr + 1)], wx[rr + 1], wy[rr + 1]);
+              }
+              dots[q] = acc_merge<P>(dots[q], acc_merge<P>(e0, e1));
             }
-            dacc_add_pair(dots[q], c0, c1);
-          } else {
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < QMAX; ++q) {
+            const int jj = wid + (CONSUMERS / 32) * q;
+            if (jj >= nb) break;
+            const basis_t* col = tv + (size_t)jj * TILE_R;
             acc_t e0 = zero_acc<P>(), e1 = zero_acc<P>();
 #pragma unroll
             for (int rr = 0; rr < TILE_R / 32; rr += 2) {
-              dacc_fma(e0, col[lane + 32 * rr], wx[rr], wy[rr]);
-              dacc_fma(e1, col[lane + 32 * (rr + 1)], wx[rr + 1], wy[rr + 1]);
+              e0 = fma(col[lane + 32 * rr], ws[lane + 32 * rr], e0);
+              e1 = fma(col[lane + 32 * (rr + 1)], ws[lane + 32 * (rr + 1)], e1);
             }
             dots[q] = acc_merge<P>(dots[q], acc_merge<P>(e0, e1));
           }
         }
-      } else {
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-          const int jj = wid + (CONSUMERS / 32) * q;
-          if (jj >= nb) break;
-          const basis_t* col = tv + (size_t)jj * TILE_R;
-          acc_t e0 = zero_acc<P>(), e1 = zero_acc<P>();
-#pragma unroll
-          for (int rr = 0; rr < TILE_R / 32; rr += 2) {
-            e0 = fma(col[lane + 32 * rr], ws[lane + 32 * rr], e0);
-            e1 = fma(col[lane + 32 * (rr + 1)], ws[lane + 32 * (rr + 1)], e1);
-          }
-          dots[q] = acc_merge<P>(dots[q], acc_merge<P>(e0, e1));
-        }
       }
-    }
 
-    if constexpr (MODE == MODE_RITZ) {
-      const int K = a.K;
-      double* U = st->eigvecs;
-      for (int k0 = 0; k0 < K; k0 += RITZ_KC) {
-        acc_t ra[RITZ_KC];
+      if constexpr (MODE == MODE_RITZ) {
+        const int K = a.K;
+        double* U = st->eigvecs;
+        for (int k0 = 0; k0 < K; k0 += RITZ_KC) {
+          acc_t ra[RITZ_KC];
 #pragma unroll
-        for (int kk = 0; kk < RITZ_KC; ++kk) ra[kk] = zero_acc<P>();
-        if constexpr (P == PREC_FDF) {
-          // binary32 partial sums over 8 basis columns, each added exactly to
-          // a double-float accumulator: the error stays within a small
-          // multiple of the binary32 rounding the stored basis already has
-          for (int j0 = 0; j0 < nb; j0 += 8) {
-            float f[RITZ_KC];
+          for (int kk = 0; kk < RITZ_KC; ++kk) ra[kk] = zero_acc<P>();
+          if constexpr (P == PREC_FDF) {
+            // binary32 partial sums over 8 basis columns, each added exactly to
+            // a double-float accumulator: the error stays within a small
+            // multiple of the binary32 rounding the stored basis already has
+            for (int j0 = 0; j0 < nb; j0 += 8) {
+              float f[RITZ_KC];
 #pragma unroll
-            for (int kk = 0; kk < RITZ_KC; ++kk) f[kk] = 0.f;
-            const int j1 = j0 + 8 < nb ? j0 + 8 : nb;
-            for (int j = j0; j < j1; ++j) {
-              const float v = tv[(size_t)j * TILE_R + tid];
+              for (int kk = 0; kk < RITZ_KC; ++kk) f[kk] = 0.f;
+              const int j1 = j0 + 8 < nb ? j0 + 8 : nb;
+              for (int j = j0; j < j1; ++j) {
+                const float v = tv[(size_t)j * TILE_R + tid];
+#pragma unroll
+                for (int kk = 0; kk < RITZ_KC; ++kk)
+                  if (k0 + kk < K) f[kk] = __fmaf_rn(v, rC[j * K + k0 + kk].x, f[kk]);
+              }
+#pragma unroll
+              for (int kk = 0; kk < RITZ_KC; ++kk) dacc_add_pair(ra[kk], f[kk], 0.f);
+            }
+          } else {
+            for (int j = 0; j < nb; ++j) {
+              const basis_t v = tv[(size_t)j * TILE_R + tid];
 #pragma unroll
               for (int kk = 0; kk < RITZ_KC; ++kk)
-                if (k0 + kk < K) f[kk] = __fmaf_rn(v, rC[j * K + k0 + kk].x, f[kk]);
+                if (k0 + kk < K) acc_fma<P>(ra[kk], v, rC[j * K + k0 + kk]);
             }
-#pragma unroll
-            for (int kk = 0; kk < RITZ_KC; ++kk) dacc_add_pair(ra[kk], f[kk], 0.f);
           }
-        } else {
-          for (int j = 0; j < nb; ++j) {
-            const basis_t v = tv[(size_t)j * TILE_R + tid];
+          if (row < a.n) {
 #pragma unroll
             for (int kk = 0; kk < RITZ_KC; ++kk)
-              if (k0 + kk < K) acc_fma<P>(ra[kk], v, rC[j * K + k0 + kk]);
+              if (k0 + kk < K) U[(size_t)(k0 + kk) * a.n + row] = acc_to_double<P>(ra[kk]);
           }
         }
-        if (row < a.n) {
-#pragma unroll
-          for (int kk = 0; kk < RITZ_KC; ++kk)
-            if (k0 + kk < K) U[(size_t)(k0 + kk) * a.n + row] = acc_to_double<P>(ra[kk]);
-        }
       }
-    }
 
+      if constexpr (HAS_DOT || DDOT) named_bar_sync(1, CONSUMERS);
+    }  // tiles of the group
     if (nb > 0) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
     }
-    if constexpr (HAS_DOT || DDOT) named_bar_sync(1, CONSUMERS);
   }
 
   if (a.fin == FIN_NONE) return;
@@ -757,7 +857,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
         acc_t v = dots[q];
         if constexpr (P == PREC_FDF) v = warp_sum(v);
         else v = warp_sum(v);
-        if (lane == 0) put_partial<P>(a.partials, (size_t)cta * PSTRIDE + jj, v);
+        if (lane == 0) put_partial<P>(a.partials, pidx(jj, cta, ncta), v);
       }
     }
   }
@@ -768,8 +868,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
       if (jj < nb - 1) {
         const acc_t v = warp_sum(dots[q]), v2 = warp_sum(dots2[q]);
         if (lane == 0) {
-          put_partial<P>(a.partials, (size_t)cta * PSTRIDE + jj, v);
-          put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_D2 + jj, v2);
+          put_partial<P>(a.partials, pidx(jj, cta, ncta), v);
+          put_partial<P>(a.partials, pidx(SLOT_D2 + jj, cta, ncta), v2);
         }
       }
     }
@@ -781,7 +881,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
     if (tid == 0) {
       acc_t t1 = red[0];
       for (int w = 1; w < CONSUMERS / 32; ++w) t1 = acc_merge<P>(t1, red[w]);
-      put_partial<P>(a.partials, (size_t)cta * PSTRIDE + nb - 1, t1);
+      put_partial<P>(a.partials, pidx(nb - 1, cta, ncta), t1);
     }
   }
   if constexpr (MODE == MODE_AXPY_STORE || DUPD || DDOT) {
@@ -800,11 +900,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
         t2 = acc_merge<P>(t2, red[2 * w + 1]);
       }
       if constexpr (DDOT) {  // the candidate's dots, in its columns' slots
-        put_partial<P>(a.partials, (size_t)cta * PSTRIDE + nb - 1, t1);
-        put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_D2 + nb - 1, t2);
+        put_partial<P>(a.partials, pidx(nb - 1, cta, ncta), t1);
+        put_partial<P>(a.partials, pidx(SLOT_D2 + nb - 1, cta, ncta), t2);
       } else {
-        put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_N, t1);
-        put_partial<P>(a.partials, (size_t)cta * PSTRIDE + SLOT_N + 1, t2);
+        put_partial<P>(a.partials, pidx(SLOT_N, cta, ncta), t1);
+        put_partial<P>(a.partials, pidx(SLOT_N + 1, cta, ncta), t2);
       }
     }
   }
@@ -825,17 +925,25 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
                      : (DDOT && q >= nb)               ? SLOT_D2 + (q - nb)
                                                        : q;
     acc_t acc = zero_acc<P>();
-    for (int b = lane; b < ncta; b += 32)
-      add_partial<P>(acc, a.partials, (size_t)b * PSTRIDE + slot);
+    // each lane adds the CTAs lane, lane + 32, ... in order; a chunk's loads
+    // are all issued before its sums
+    for (int b0 = 0; b0 < ncta; b0 += 32 * RED_LOADS) {
+      typename Tr::part_t v[RED_LOADS];
+#pragma unroll
+      for (int u = 0; u < RED_LOADS; ++u) {
+        const int b = b0 + lane + 32 * u;
+        if (b < ncta) v[u] = load_partial<P>(a.partials, pidx(slot, b, ncta));
+      }
+#pragma unroll
+      for (int u = 0; u < RED_LOADS; ++u)
+        if (b0 + lane + 32 * u < ncta) add_partial<P>(acc, v[u]);
+    }
     acc = warp_sum(acc);
     if (lane == 0) tot[q] = acc_to_double<P>(acc);
   }
   named_bar_sync(1, CONSUMERS);
-  if (tid == 0) {
-    finalize_pass(a, tot);
-    __threadfence();
-    st->ticket = 0;
-  }
+  finalize_pass(a, tot, reinterpret_cast<double*>(sm + L.fin_off), tid);
+  if (tid == 0) st->ticket = 0;
 }
 
 template <int P, int MODE>
@@ -866,6 +974,8 @@ __global__ void __launch_bounds__(PASS_THREADS, pass_ctas_per_sm(PREC_FDF))
   a.V = B.V;
   a.Vmut = B.V;
   a.ld = B.n_pad;
+  a.tstride = TILE_R;  // column-major
+  a.cstride = B.n_pad;
   a.n = B.n;
   a.m = B.m;
   a.K = B.K;
@@ -959,11 +1069,14 @@ static cudaError_t config_t(int max_cols, int K, int num_sms, PassLaunch& out) {
   const size_t half = (size_t)persm / pass_ctas_per_sm(P) - 1024;
   const size_t cap = half < (size_t)optin ? half : (size_t)optin;
   size_t avail = cap > fixed ? cap - fixed : 0;
-  const size_t per_stage = (size_t)(max_cols > 0 ? max_cols : 1) * TILE_R * sizeof(basis_t);
-  int stages = (int)(avail / per_stage);
-  if (stages > 4) stages = 4;
+  // a stage: max_cols basis columns of a tile, plus the pass vector's rows
+  const size_t per_stage = (size_t)(max_cols > 0 ? max_cols : 1) * TILE_R * sizeof(basis_t) +
+                           (MODE == MODE_RITZ ? 0 : (size_t)TILE_R * 8);
+  // every byte that fits: the kernel fits region / (its stage) stages, so
+  // that passes over few columns keep many tiles in flight
+  const size_t region = avail / 128 * 128;
+  const int stages = (int)(region / per_stage);
   if (stages < 1) return cudaErrorInvalidConfiguration;
-  const size_t region = align_up((size_t)stages * per_stage, 128);
   const size_t total = smem_plan(MODE, region, ritz_elems).total;
   e = cudaFuncSetAttribute(pass_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)total);
@@ -1017,30 +1130,31 @@ cudaError_t launch_pass(int prec, int mode, const PassArgs& a, const PassLaunch&
   return cudaErrorInvalidValue;
 }
 
-// out[j*n + r] = s_j * V[j*ld + r]
+// out[j*n + r] = s_j * V(r, j), V(r, j) at (r / TILE_R) * tstride + j * cstride + r % TILE_R
 template <typename B>
-__global__ void basis_to_f64_kernel(const B* V, int64_t ld, int64_t n, int cols,
-                                    const double* s, double* out) {
+__global__ void basis_to_f64_kernel(const B* V, int64_t tstride, int64_t cstride, int64_t n,
+                                    int cols, const double* s, double* out) {
   const int64_t total = n * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / n, r = e - j * n;
-    out[e] = s[j] * (double)V[j * ld + r];
+    out[e] = s[j] * (double)V[(r / TILE_R) * tstride + j * cstride + r % TILE_R];
   }
 }
 
-cudaError_t launch_basis_to_f64(int prec, const void* V, int64_t ld, int64_t n, int cols,
-                                const double* s_dev, double* out, cudaStream_t st) {
+cudaError_t launch_basis_to_f64(int prec, const void* V, int64_t tstride, int64_t cstride,
+                                int64_t n, int cols, const double* s_dev, double* out,
+                                cudaStream_t st) {
   const int64_t total = n * cols;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks < 1) blocks = 1;
   if (prec == PREC_DDD)
-    basis_to_f64_kernel<double><<<(int)blocks, 256, 0, st>>>(static_cast<const double*>(V), ld,
-                                                              n, cols, s_dev, out);
+    basis_to_f64_kernel<double><<<(int)blocks, 256, 0, st>>>(
+        static_cast<const double*>(V), tstride, cstride, n, cols, s_dev, out);
   else
-    basis_to_f64_kernel<float><<<(int)blocks, 256, 0, st>>>(static_cast<const float*>(V), ld, n,
-                                                             cols, s_dev, out);
+    basis_to_f64_kernel<float><<<(int)blocks, 256, 0, st>>>(
+        static_cast<const float*>(V), tstride, cstride, n, cols, s_dev, out);
   return cudaGetLastError();
 }
 

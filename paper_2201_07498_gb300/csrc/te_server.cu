@@ -311,6 +311,8 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
     a.V = B.V;
     a.Vmut = B.V;
     a.ld = B.n_pad;
+    a.tstride = TILE_R;  // column-major
+    a.cstride = B.n_pad;
     a.n = B.n;
     a.m = B.m;
     a.K = B.K;
@@ -359,6 +361,8 @@ cudaError_t enqueue_finish(te_server* S, Request* R) {
     a.V = B.V;
     a.Vmut = B.V;
     a.ld = B.n_pad;
+    a.tstride = TILE_R;  // column-major
+    a.cstride = B.n_pad;
     a.n = B.n;
     a.m = B.m;
     a.K = B.K;

@@ -74,7 +74,7 @@ bool is_device_ptr(const void* p) {
 
 struct Work {
   // byte offsets inside one allocation
-  size_t V = 0, ytil = 0, w = 0, partials = 0, st = 0, Uint = 0, slices = 0, vout = 0,
+  size_t V = 0, ytil = 0, xcur = 0, w = 0, partials = 0, st = 0, Uint = 0, slices = 0, vout = 0,
          scols = 0, svals = 0, svals64 = 0, lscale = 0, lrows = 0, vpart = 0, flag = 0,
          total = 0;
 };
@@ -99,6 +99,7 @@ Work layout(int prec, int vk, int64_t n_pad, int m, int grid, const SellSizes& z
   };
   w.V = take((size_t)n_pad * (size_t)(m + 1) * basis_elt(prec));
   w.ytil = take((size_t)n_pad * 8);
+  w.xcur = take((size_t)n_pad * basis_elt(prec));
   w.w = take((size_t)n_pad * 8);
   w.partials = take((size_t)grid * PSTRIDE * 8);
   w.st = take(sizeof(LzState));
@@ -368,12 +369,20 @@ cudaError_t autotune_layout(int prec, int vk, int in_type, const int64_t* rph, c
   return cudaSuccess;
 }
 
+// The plan stores the basis tile-major: tile t of column c at
+// (t * (m + 1) + c) * TILE_R, so that a pass moves the columns of a tile with
+// one bulk copy.  The SpMV reads the newest column from a contiguous copy.
+int64_t basis_tstride(const te_plan* P) { return (int64_t)(P->m + 1) * TILE_R; }
+
 PassArgs base_args(te_plan* P) {
   PassArgs a;
   memset(&a, 0, sizeof(a));
   a.V = at(P, P->W.V);
   a.Vmut = at(P, P->W.V);
   a.ld = P->n_pad;
+  a.tstride = basis_tstride(P);
+  a.cstride = TILE_R;
+  a.xcopy = at(P, P->W.xcur);
   a.n = P->n;
   a.m = P->m;
   a.K = P->K;
@@ -496,7 +505,6 @@ cudaError_t enqueue_spmv(te_plan* P, const void* x, void* y, bool out_f64, cudaS
 // Enqueue the Lanczos phase (Algorithm 1): init + m steps.
 cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
   cudaError_t e;
-  const size_t belt = basis_elt(P->prec);
   // v_1 = normalised start vector (stored unnormalised, scale s_0)
   {
     PassArgs a = base_args(P);
@@ -508,7 +516,7 @@ cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
     if ((e = pass(P, MODE_AXPY_STORE, a, s)) != cudaSuccess) return e;
   }
   for (int i = 0; i < P->m; ++i) {
-    const void* xi = static_cast<const char*>(at(P, P->W.V)) + (size_t)i * P->n_pad * belt;
+    const void* xi = at(P, P->W.xcur);  // column i, written by the pass that formed it
     if ((e = prof_begin(P, s)) != cudaSuccess) return e;
     e = enqueue_spmv(P, xi, at(P, P->W.ytil), false, s);
     if (e != cudaSuccess) return e;
@@ -1253,8 +1261,8 @@ te_status te_lanczos(const te_csr* A, int32_t krylov_steps, te_precision p, cons
   if (r == TE_OK && e == cudaSuccess)
     e = cudaMemcpyAsync(hst, &P->st->restart_flag, sizeof(hst), cudaMemcpyDeviceToHost, s);
   if (r == TE_OK && e == cudaSuccess && basis)
-    e = launch_basis_to_f64(P->prec, at(P, P->W.V), P->n_pad, P->n, krylov_steps, P->st->s,
-                            basis, s);
+    e = launch_basis_to_f64(P->prec, at(P, P->W.V), basis_tstride(P), TILE_R, P->n,
+                            krylov_steps, P->st->s, basis, s);
   if (r == TE_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (r == TE_OK && e != cudaSuccess) r = cuda_fail(e, "te_lanczos");
   if (r == TE_OK) {

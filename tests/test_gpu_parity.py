@@ -201,6 +201,27 @@ def test_lanczos_fdf_close_to_oracle(te):
     assert np.max(np.abs(Vh.T @ Vh - np.eye(16))) <= 1e-6
 
 
+@pytest.mark.parametrize("reorth", ["full", "delayed"])
+def test_lanczos_tile_groups_match_oracle(te, reorth):
+    """A basis of 7423 tiles of 256 rows (the last one ragged): the passes move
+    groups of several tiles per pipeline stage while few columns exist, the
+    last group holding fewer tiles than the others."""
+    n = 7423 * 256 - 100
+    A = synth.uniform_sym(n, 4, 5)
+    m = 12
+    v1 = synth.start_vector(n, 9)
+    ref = oracle.lanczos(A, v1, m, seed=9)
+    alpha, beta, V, restarts = te.lanczos(te.CSR.from_host(A, "ddd"), m, "ddd", seed=9,
+                                          v1=torch.from_numpy(v1).cuda(), reorth=reorth)
+    tn = np.linalg.norm(ref.T())
+    assert restarts == ref.restarts == 0
+    assert np.max(np.abs(alpha.numpy() - ref.alpha)) <= 1e-10 * tn
+    assert np.max(np.abs(beta.numpy() - ref.beta)) <= 1e-10 * tn
+    rows = np.r_[0:300, n // 2 - 200:n // 2 + 200, n - 700:n]  # first, middle, ragged end
+    Vs = V[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.max(np.abs(Vs - ref.V[rows])) <= 1e-8
+
+
 # ---------------------------------------------------------------------------
 # Jacobi phase
 # ---------------------------------------------------------------------------
