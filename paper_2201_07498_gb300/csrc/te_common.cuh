@@ -57,6 +57,30 @@ TE_DEV dw dw_from_double(double x) {
 }
 TE_DEV double dw_to_double(dw v) { return (double)v.hi + (double)v.lo; }
 
+// The same value, hi + lo rounded to nearest binary64, built with integer
+// operations (GB300 issues binary64 arithmetic and conversions at a small
+// fraction of its binary32 rate).  Needs |lo| <= ulp(hi) / 2, as a two_sum
+// leaves it.  hi's binary64 pattern is its sign, its exponent rebiased and
+// its significand moved up 29 bits; lo is then added as a whole number of
+// binary64 units in the last place of hi, 2^(e - 52), rounded to nearest
+// even.  When hi is a power of two and lo lowers its magnitude, the result
+// lies in the binade below, whose units are half as large.  Zeros,
+// subnormals, infinities, NaNs and |hi| < 2^-74 take the binary64 path.
+TE_DEV double dw_to_double_bits(dw v) {
+  const uint32_t hb = __float_as_uint(v.hi);
+  const uint32_t e8 = (hb >> 23) & 0xffu;
+  if (e8 < 53u || e8 == 0xffu) return dw_to_double(v);
+  const uint32_t mant = hb & 0x7fffffu;
+  const bool opposite = ((__float_as_uint(v.lo) ^ hb) >> 31) != 0u;
+  const uint32_t down = (mant == 0u && opposite) ? 1u : 0u;
+  // 2^(52 - e + down) as a binary32, e = e8 - 127: exponent field 306 - e8 + down
+  const float scale = __uint_as_float((306u - e8 + down) << 23);
+  const int L = __float2int_rn(__fmul_rn(v.lo, scale));  // |L| <= 2^29
+  const int64_t delta = (hb >> 31) ? -(int64_t)L : (int64_t)L;  // in magnitude units
+  const uint64_t mag = (((uint64_t)(e8 + 896u) << 52) | ((uint64_t)mant << 29)) + (uint64_t)delta;
+  return __longlong_as_double((long long)(((uint64_t)(hb >> 31) << 63) | mag));
+}
+
 // AccurateDWPlusDW (Joldes et al. 2017, Alg. 6): relative error <= 3u^2
 TE_DEV dw dw_add(dw x, dw y) {
   float sh, sl, th, tl;

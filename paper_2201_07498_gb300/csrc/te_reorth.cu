@@ -56,9 +56,10 @@ __host__ __device__ constexpr int pass_ctas_per_sm(int prec) { return prec == PR
 constexpr int QMAX = MAX_M / (CONSUMERS / 32);  // dot columns per warp
 constexpr int RITZ_KC = 8;                      // Ritz outputs per register block
 constexpr int RED_LOADS = 10;                   // partial loads per lane in flight
-// tile groups of a tile-major basis: stages of up to GROUP_BYTES, at most
-// GROUP_MAX tiles, and at least GROUP_MIN_PER_CTA groups for every CTA
-constexpr uint32_t GROUP_BYTES = 24u << 10;
+// tile groups of a tile-major basis: stages of up to GROUP_BYTES (and at
+// most half the stage region, so that two stages fit), at most GROUP_MAX
+// tiles, and at least GROUP_MIN_PER_CTA groups for every CTA
+constexpr uint32_t GROUP_BYTES = 48u << 10;
 constexpr int GROUP_MAX = 16;
 constexpr int GROUP_MIN_PER_CTA = 8;
 
@@ -372,7 +373,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   if (a.only_on_restart) {
     if (*((volatile int*)&st->restart_flag) == 0) return;
   }
-  const SmemPlan L = smem_plan(MODE, region, MODE == MODE_RITZ ? a.nb * a.K : 0);
+  const SmemPlan L = smem_plan(
+      MODE, region, MODE == MODE_RITZ ? a.nb * ((a.K + RITZ_KC - 1) / RITZ_KC * RITZ_KC) : 0);
   vec_t* ws = reinterpret_cast<vec_t*>(sm + L.ws_off);
   coef_t* coef = reinterpret_cast<coef_t*>(sm + L.coef_off);
   coef_t* coef2 = reinterpret_cast<coef_t*>(sm + L.coef2_off);
@@ -397,7 +399,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   // only), yet at least GROUP_MIN_PER_CTA groups per CTA
   int G = 1;
   if (nb > 0 && a.cstride == TILE_R) {
-    const int64_t gb = (int64_t)(GROUP_BYTES / (col_bytes + xbytes));
+    const size_t cap = region / 2 < GROUP_BYTES ? region / 2 : GROUP_BYTES;
+    const int64_t gb = (int64_t)(cap / (col_bytes + xbytes));
     const int64_t gl = tiles / ((int64_t)ncta * GROUP_MIN_PER_CTA);
     int64_t g = gb < gl ? gb : gl;
     if (g > GROUP_MAX) g = GROUP_MAX;
@@ -435,9 +438,17 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
       coef2[j] = to_coef<P>(st->c2[j]);
     }
   }
+  // Ritz coefficients C (nb x K) with the row stride padded to Kp (a multiple
+  // of RITZ_KC, zeros beyond K); FDF keeps their binary32 roundings only
+  const int Kp = (a.K + RITZ_KC - 1) / RITZ_KC * RITZ_KC;
   if constexpr (MODE == MODE_RITZ) {
     if (st->eigvecs == nullptr) return;  // uniform: no vectors requested
-    for (int e = tid; e < nb * a.K; e += PASS_THREADS) rC[e] = to_coef<P>(st->C[e]);
+    for (int e = tid; e < nb * Kp; e += PASS_THREADS) {
+      const int j = e / Kp, k = e - j * Kp;
+      const double c = k < a.K ? st->C[j * a.K + k] : 0.0;
+      if constexpr (P == PREC_FDF) reinterpret_cast<float*>(rC)[e] = __double2float_rn(c);
+      else rC[e] = c;
+    }
   }
   __syncthreads();
 
@@ -806,17 +817,27 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
           if constexpr (P == PREC_FDF) {
             // binary32 partial sums over 8 basis columns, each added exactly to
             // a double-float accumulator: the error stays within a small
-            // multiple of the binary32 rounding the stored basis already has
+            // multiple of the binary32 rounding the stored basis already has.
+            // The 8 coefficients of a column come in two 16-byte broadcasts.
+            const float* rh = reinterpret_cast<const float*>(rC) + k0;
             for (int j0 = 0; j0 < nb; j0 += 8) {
               float f[RITZ_KC];
 #pragma unroll
               for (int kk = 0; kk < RITZ_KC; ++kk) f[kk] = 0.f;
               const int j1 = j0 + 8 < nb ? j0 + 8 : nb;
+#pragma unroll 4
               for (int j = j0; j < j1; ++j) {
                 const float v = tv[(size_t)j * TILE_R + tid];
-#pragma unroll
-                for (int kk = 0; kk < RITZ_KC; ++kk)
-                  if (k0 + kk < K) f[kk] = __fmaf_rn(v, rC[j * K + k0 + kk].x, f[kk]);
+                const float4 c0 = *reinterpret_cast<const float4*>(rh + j * Kp);
+                const float4 c1 = *reinterpret_cast<const float4*>(rh + j * Kp + 4);
+                f[0] = __fmaf_rn(v, c0.x, f[0]);
+                f[1] = __fmaf_rn(v, c0.y, f[1]);
+                f[2] = __fmaf_rn(v, c0.z, f[2]);
+                f[3] = __fmaf_rn(v, c0.w, f[3]);
+                f[4] = __fmaf_rn(v, c1.x, f[4]);
+                f[5] = __fmaf_rn(v, c1.y, f[5]);
+                f[6] = __fmaf_rn(v, c1.z, f[6]);
+                f[7] = __fmaf_rn(v, c1.w, f[7]);
               }
 #pragma unroll
               for (int kk = 0; kk < RITZ_KC; ++kk) dacc_add_pair(ra[kk], f[kk], 0.f);
@@ -825,14 +846,18 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
             for (int j = 0; j < nb; ++j) {
               const basis_t v = tv[(size_t)j * TILE_R + tid];
 #pragma unroll
-              for (int kk = 0; kk < RITZ_KC; ++kk)
-                if (k0 + kk < K) acc_fma<P>(ra[kk], v, rC[j * K + k0 + kk]);
+              for (int kk = 0; kk < RITZ_KC; ++kk) acc_fma<P>(ra[kk], v, rC[j * Kp + k0 + kk]);
             }
           }
           if (row < a.n) {
 #pragma unroll
             for (int kk = 0; kk < RITZ_KC; ++kk)
-              if (k0 + kk < K) U[(size_t)(k0 + kk) * a.n + row] = acc_to_double<P>(ra[kk]);
+              if (k0 + kk < K) {
+                if constexpr (P == PREC_FDF)
+                  U[(size_t)(k0 + kk) * a.n + row] = dw_to_double_bits(dacc_value(ra[kk]));
+                else
+                  U[(size_t)(k0 + kk) * a.n + row] = ra[kk];
+              }
           }
         }
       }
@@ -1059,7 +1084,7 @@ static cudaError_t config_t(int max_cols, int K, int num_sms, PassLaunch& out) {
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  const int ritz_elems = MODE == MODE_RITZ ? max_cols * K : 0;
+  const int ritz_elems = MODE == MODE_RITZ ? max_cols * ((K + RITZ_KC - 1) / RITZ_KC * RITZ_KC) : 0;
   // pass_ctas_per_sm CTAs per SM share the SM's shared memory (minus the
   // per-CTA reservation of 1 KB)
   const size_t fixed = smem_plan(MODE, 0, ritz_elems).total + 128;
