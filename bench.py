@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--K", type=int, default=24)
     p.add_argument("--m", type=int, default=48)
+    p.add_argument("--order", choices=["keep", "degree"], default="degree",
+                   help="degree: the plans relabel the rows by length (longest first) so that "
+                        "the SpMV's reads of the most connected columns share cache lines")
     p.add_argument("--reorth", choices=["full", "delayed"], default="delayed",
                    help="full: classical Gram-Schmidt twice per step (three passes); delayed: "
                         "the second sweep folded into the next step (two passes)")
@@ -253,6 +256,8 @@ def workload_config(args, A):
         "reorthogonalisation": ("classical Gram-Schmidt twice per step" if args.reorth == "full"
                                 else "classical Gram-Schmidt twice, second sweep delayed "
                                      "into the next step"),
+        "row_order": ("rows relabelled by length, longest first (the caller sees its own "
+                      "order)" if args.order == "degree" else "the generator's order"),
         "l2": "no flush: inputs larger than L2 (CSR and basis are several GB each)",
         "parallelism": "replicas",
     }
@@ -459,7 +464,7 @@ def main():
     K, m = args.K, args.m
 
     csr_f = te.CSR.from_host(A, "fdf")
-    plan_f = te.Plan(csr_f, K, m, "fdf", seed=args.seed, reorth=args.reorth)
+    plan_f = te.Plan(csr_f, K, m, "fdf", seed=args.seed, reorth=args.reorth, order=args.order)
     kernels_per_solve = plan_f.kernel_count + 1  # + the per-solve set-up kernel
 
     peak, peak_kind = measured_peaks()
@@ -485,7 +490,8 @@ def main():
     if not args.no_extras:
         # the plain FP64 path (DDD) on the same workload
         csr_d = te.CSR.from_host(A, "ddd")
-        plan_d = te.Plan(csr_d, K, m, "ddd", seed=args.seed, reorth=args.reorth)
+        plan_d = te.Plan(csr_d, K, m, "ddd", seed=args.seed, reorth=args.reorth,
+                         order=args.order)
         ms_d, _, _ = time_plan(plan_d, max(2, args.steps // 2), args.warmup, world)
         ev_d, _, res_d = plan_d.solve(vectors=False, residuals=True)
         ev_d, res_d = ev_d.numpy(), res_d.numpy()
@@ -494,7 +500,8 @@ def main():
         del plan_d
         # the chosen form with the binary64 Rayleigh-quotient refinement
         csr_r = te.CSR.from_host(A, "fdf", values_f64=True)
-        plan_r = te.Plan(csr_r, K, m, "fdf", seed=args.seed, refine=True, reorth=args.reorth)
+        plan_r = te.Plan(csr_r, K, m, "fdf", seed=args.seed, refine=True, reorth=args.reorth,
+                         order=args.order)
         ms_r, _, _ = time_plan(plan_r, max(2, args.steps // 2), args.warmup, world)
         ev_r, _, res_r = plan_r.solve(vectors=False, residuals=True)
         ev_r, res_r = ev_r.numpy(), res_r.numpy()
@@ -520,7 +527,8 @@ def main():
         })
         # the layout autotuner on this matrix
         t0 = time.perf_counter()
-        plan_t = te.Plan(csr_f, K, m, "fdf", seed=args.seed, autotune=True, reorth=args.reorth)
+        plan_t = te.Plan(csr_f, K, m, "fdf", seed=args.seed, autotune=True, reorth=args.reorth,
+                         order=args.order)
         tune_s = time.perf_counter() - t0
         ms_t, _, _ = time_plan(plan_t, max(2, args.steps // 2), args.warmup, world)
         extras["autotune"] = {"layout_window_vmax": list(plan_t.layout), "solve_ms": ms_t,
@@ -528,9 +536,11 @@ def main():
                               "default_layout_spmv_ms": sp_ms}
         del plan_t
         Ks, ms_ = max(1, K // 3), max(2, m // 3)
-        plan_fs = te.Plan(csr_f, Ks, ms_, "fdf", seed=args.seed, reorth=args.reorth)
+        plan_fs = te.Plan(csr_f, Ks, ms_, "fdf", seed=args.seed, reorth=args.reorth,
+                          order=args.order)
         ms_fs, ev_fs, _ = time_plan(plan_fs, args.steps, args.warmup, world)
-        plan_ds = te.Plan(csr_d, Ks, ms_, "ddd", seed=args.seed, reorth=args.reorth)
+        plan_ds = te.Plan(csr_d, Ks, ms_, "ddd", seed=args.seed, reorth=args.reorth,
+                          order=args.order)
         ms_ds, ev_ds, _ = time_plan(plan_ds, max(2, args.steps // 2), args.warmup, world)
         extras[f"solve_ms_K{Ks}_m{ms_}"] = {
             "fdf": ms_fs, "ddd": ms_ds,
@@ -553,7 +563,8 @@ def main():
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(s)
-        te.topk_eigs(host, K, m, "fdf", seed=args.seed, reorth=args.reorth, out=(ev_out, U_out))
+        te.topk_eigs(host, K, m, "fdf", seed=args.seed, reorth=args.reorth, order=args.order,
+                     out=(ev_out, U_out))
         a1.record(s)
         torch.cuda.synchronize()
         if it > 0:

@@ -111,7 +111,7 @@ typedef struct {
   int32_t which;    /* TE_WHICH_* */
   int32_t use_graph; /* plans: capture the whole solve as one CUDA graph (default 1) */
   size_t device_budget_bytes; /* 0 = no limit on the work memory */
-  int32_t reorth;   /* TE_REORTH_FULL (default) or TE_REORTH_NONE */
+  int32_t reorth;   /* TE_REORTH_FULL (default), TE_REORTH_NONE or TE_REORTH_DELAYED */
   int32_t refine;   /* 1: after the Ritz vectors, replace each selected Ritz value by
                        the binary64 Rayleigh quotient u'Mu/u'u of its vector against
                        the binary64 matrix, and its residual by the true residual
@@ -131,7 +131,21 @@ typedef struct {
                        its window (rows sorted together) and piece length, time each
                        on this matrix and keep the fastest (te_plan_layout reports it);
                        resident plans only.  0 (default): window 2048, pieces of 64. */
+  int32_t order;    /* TE_ORDER_KEEP (default) or TE_ORDER_DEGREE: the plan relabels the
+                       rows (and the same columns) by length, longest first, so that the
+                       SpMV's reads of the vector for the most connected columns share
+                       cache lines (power-law graphs).  The matrix is M' = P M P^T for
+                       that permutation P; the caller sees no difference: the start
+                       vector and restart draws are indexed by the caller's rows and
+                       the Ritz vectors come back in the caller's row order.
+                       Eigenvalues agree with TE_ORDER_KEEP up to rounding (the sums
+                       over rows run in another order).  Costs a counting sort of the
+                       rows at plan creation, the permutation (8 bytes per row) and
+                       the plan's own copy of the Ritz vectors (n x K binary64). */
 } te_options;
+
+#define TE_ORDER_KEEP 0   /* rows in the caller's order */
+#define TE_ORDER_DEGREE 1 /* rows by length, longest first (ties: caller's order) */
 
 /* Fill `opt` with the defaults: seed 0, v1 NULL, largest magnitude, graphs on,
  * no budget, full reorthogonalisation, no refinement. */

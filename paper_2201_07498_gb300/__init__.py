@@ -25,6 +25,7 @@ TE_F64, TE_F32, TE_BF16, TE_FP8_E4M3 = 0, 1, 2, 3
 TE_DEVICE, TE_HOST = 0, 1
 WHICH = {"LM": 0, "LA": 1}
 REORTH = {"full": 0, "none": 1, "delayed": 2}
+ORDERS = {"keep": 0, "degree": 1}
 PRECISIONS = {"ddd": (TE_F64, TE_F64, TE_F64), "fdd": (TE_F32, TE_F64, TE_F64),
               "fdf": (TE_F32, TE_F64, TE_F32),
               "bdf": (TE_BF16, TE_F64, TE_F32), "8df": (TE_FP8_E4M3, TE_F64, TE_F32)}
@@ -55,7 +56,8 @@ class te_options(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("v1", ctypes.c_void_p), ("which", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("device_budget_bytes", ctypes.c_size_t),
                 ("reorth", ctypes.c_int32), ("refine", ctypes.c_int32),
-                ("matrix_budget_bytes", ctypes.c_size_t), ("autotune", ctypes.c_int32)]
+                ("matrix_budget_bytes", ctypes.c_size_t), ("autotune", ctypes.c_int32),
+                ("order", ctypes.c_int32)]
 
 
 class te_server_options(ctypes.Structure):
@@ -221,7 +223,7 @@ class CSR:
 
 
 def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full",
-             refine=False, matrix_budget=0, autotune=False) -> te_options:
+             refine=False, matrix_budget=0, autotune=False, order="keep") -> te_options:
     o = te_options()
     load_library().te_default_options(ctypes.byref(o))
     o.seed = seed
@@ -233,12 +235,13 @@ def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full
     o.refine = 1 if refine else 0
     o.matrix_budget_bytes = matrix_budget
     o.autotune = 1 if autotune else 0
+    o.order = ORDERS[order] if isinstance(order, str) else int(order)
     return o
 
 
 def topk_eigs(csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0, v1=None,
               which="LM", vectors: bool = True, residuals: bool = False, reorth="full",
-              refine: bool = False, matrix_budget: int = 0, stream=None, out=None):
+              refine: bool = False, matrix_budget: int = 0, order="keep", stream=None, out=None):
     """One Top-K solve; returns (eigvals [K] float64 cpu, eigvecs [n, K] float64 or None,
     residuals [K] or None: estimates, or true binary64 residuals with refine).
     Vectors live where the matrix lives unless `out = (eigvals [K], eigvecs
@@ -246,7 +249,8 @@ def topk_eigs(csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int
     import torch
     lib = load_library()
     A = csr.to_ctypes()
-    opt = _options(seed, v1, which, reorth=reorth, refine=refine, matrix_budget=matrix_budget)
+    opt = _options(seed, v1, which, reorth=reorth, refine=refine, matrix_budget=matrix_budget,
+                   order=order)
     if out is not None:
         ev, U = out
     else:
@@ -269,12 +273,12 @@ class Plan:
     def __init__(self, csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0,
                  v1=None, which="LM", use_graph: bool = True, budget: int = 0,
                  reorth="full", refine: bool = False, matrix_budget: int = 0,
-                 autotune: bool = False, stream=None):
+                 autotune: bool = False, order="keep", stream=None):
         self._lib = load_library()
         self.csr, self.K, self.m, self.n = csr, K, krylov_steps, csr.n
         A = csr.to_ctypes()
         opt = _options(seed, v1, which, use_graph, budget, reorth, refine, matrix_budget,
-                       autotune)
+                       autotune, order)
         h = ctypes.c_void_p()
         rc = self._lib.te_plan_create(ctypes.byref(A), K, krylov_steps, _prec(precision),
                                       ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h))
@@ -446,12 +450,12 @@ def spmv(csr: CSR, x, precision="ddd", stream=None):
 
 
 def lanczos(csr: CSR, krylov_steps: int, precision="ddd", *, seed: int = 0, v1=None,
-            basis: bool = True, reorth="full", stream=None):
+            basis: bool = True, reorth="full", order="keep", stream=None):
     """The Lanczos phase: returns (alpha [m], beta [m+1], V [n, m] or None, restarts)."""
     import torch
     lib = load_library()
     A = csr.to_ctypes()
-    opt = _options(seed, v1, "LM", False, reorth=reorth)
+    opt = _options(seed, v1, "LM", False, reorth=reorth, order=order)
     alpha = torch.empty(krylov_steps, dtype=torch.float64)
     beta = torch.empty(krylov_steps + 1, dtype=torch.float64)
     V = (torch.empty((krylov_steps, csr.n), dtype=torch.float64, device="cuda")

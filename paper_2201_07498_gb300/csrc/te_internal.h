@@ -89,8 +89,13 @@ struct SellHost {
 constexpr int SELL_BIG_PIECES = 16;  // cut rows with more pieces get a whole warp
 // returns false (and a message) if row_ptr is malformed
 // window: rows sorted together (sigma); vmax: longest piece (rows above are cut)
+// perm (optional): row r of the layout is CSR row perm[r] and writes output r
 bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err,
-               int window = SELL_WINDOW, int vmax = SELL_VMAX);
+               int window = SELL_WINDOW, int vmax = SELL_VMAX, const int32_t* perm = nullptr);
+// row_ptr starts at 0, ends at nnz and never decreases
+bool rows_valid(const int64_t* rp, int64_t n, int64_t nnz, std::string& err);
+// rows by length, longest first (stable): perm[r] = row placed at r, iperm = inverse
+void degree_order(const int64_t* rp, int64_t n, int32_t* perm, int32_t* iperm);
 
 // Device copy of a SELL layout.
 struct DevSell {
@@ -115,11 +120,12 @@ struct DevSell {
 cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, const void* val,
                               const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
                               int nslices, int32_t* cols, void* vals, const int32_t* vrow,
-                              const float* row_scale, float* lane_scale, cudaStream_t s);
+                              const float* row_scale, float* lane_scale, const int32_t* colmap,
+                              cudaStream_t s);  // colmap (optional): column c -> colmap[c]
 // the same arrays built on the host (in_type F64 or F32 -> vk F64 or F32);
 // false if a column index lies outside [0, n)
 bool build_sell_host(const SellHost& H, const int32_t* ci, const void* val, int in_type, int vk,
-                     int64_t n, int32_t* cols, void* vals);
+                     int64_t n, const int32_t* colmap, int32_t* cols, void* vals);
 // binary64 CSR values -> `to` (TE_F32, TE_BF16 codes, TE_FP8_E4M3 codes with
 // per-row scales); round to nearest, ties to even (te_quant.cu)
 cudaError_t launch_quantize(int to, const int64_t* rp, const double* val, int64_t n, int64_t nnz,
@@ -165,6 +171,7 @@ struct PassArgs {
   int64_t tstride;   // elements from a tile to the next tile of the same column
   int64_t cstride;   // elements from a column to the next (TILE_R: tile-major)
   void* xcopy;       // optional: the column a pass stores, also written contiguously
+  const int32_t* perm;  // optional: row r of the vectors is the caller's row perm[r]
   int64_t n;         // true rows
   int nb;            // basis columns read by this pass: col0 .. col0 + nb - 1
   int col0;          // first basis column read (0 unless reorthogonalisation is off)
@@ -226,6 +233,11 @@ int refine_grid(int num_sms);
 // copy `count` doubles from src to st->eigvecs_user (no-op when it is NULL)
 cudaError_t launch_copy_out(LzState* st, const double* src, size_t count, int grid,
                             cudaStream_t s);
+// st->eigvecs_user[k*n + v] = src[k*n + iperm[v]] for k < K, v < n: Ritz
+// vectors of the relabelled rows back in the caller's row order (no-op when
+// eigvecs_user is NULL)
+cudaError_t launch_copy_out_perm(LzState* st, const double* src, int64_t n, int K,
+                                 const int32_t* iperm, int grid, cudaStream_t s);
 // G[a*K + b] = u_a . u_b (device), per-block partials in `partials`
 // (grid * K*(K+1)/2 doubles)
 cudaError_t launch_gram(const double* U, int64_t n, int K, double* partials, int grid,
@@ -280,7 +292,7 @@ double breakdown_tolerance(int prec);
 // record the thread-local message returned by te_last_error()
 void set_last_error(const std::string& msg);
 cudaError_t launch_basis_to_f64(int prec, const void* V, int64_t tstride, int64_t cstride,
-                                int64_t n, int cols, const double* s_dev, double* out,
-                                cudaStream_t st);
+                                int64_t n, int cols, const double* s_dev, const int32_t* iperm,
+                                double* out, cudaStream_t st);
 
 }  // namespace te

@@ -109,6 +109,27 @@ cudaError_t launch_copy_out(LzState* st, const double* src, size_t count, int gr
   return cudaGetLastError();
 }
 
+// Thread per caller row, column by column: the writes are coalesced, the
+// reads gather from one column (n doubles) at a time, which the L2 keeps.
+__global__ void copy_out_perm_kernel(const LzState* st, const double* src, int64_t n, int K,
+                                     const int32_t* iperm) {
+  double* dst = st->eigvecs_user;
+  if (dst == nullptr) return;
+  for (int k = 0; k < K; ++k) {
+    const double* sk = src + (size_t)k * n;
+    double* dk = dst + (size_t)k * n;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+      dk[v] = sk[iperm[v]];
+  }
+}
+
+cudaError_t launch_copy_out_perm(LzState* st, const double* src, int64_t n, int K,
+                                 const int32_t* iperm, int grid, cudaStream_t s) {
+  copy_out_perm_kernel<<<grid, 256, 0, s>>>(st, src, n, K, iperm);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Gram matrix: G[a][b] = sum_r U[r, a] U[r, b] for a <= b (pair index p in
 // row-major upper-triangle order).  Each block stages GR rows of U in shared

@@ -517,16 +517,17 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   basis_t* Vout = static_cast<basis_t*>(a.Vmut) + (size_t)a.col_out * a.cstride;
 
   // the source value of a row: the pass vector, the start vector, or a
-  // seeded random draw (restarts)
+  // seeded random draw (restarts); the last two are indexed by the caller's
+  // row (perm maps the solver's rows to the caller's)
   auto load_x = [&](int64_t row) {
     vec_t v = vec_zero<P>();
     if constexpr (MODE != MODE_RITZ) {
       if (a.xsrc == X_VEC) {
         v = static_cast<const vec_t*>(a.xvec)[row];
-      } else if (a.xsrc == X_V1 && v1 != nullptr) {
-        if (row < a.n) v = vec_from_double<P>(v1[row]);
-      } else {
-        if (row < a.n) v = vec_from_double<P>(sm64_uniform_pm1(a.seed, rstream, (uint64_t)row));
+      } else if (row < a.n) {
+        const int64_t orow = a.perm ? (int64_t)a.perm[row] : row;
+        if (a.xsrc == X_V1 && v1 != nullptr) v = vec_from_double<P>(v1[orow]);
+        else v = vec_from_double<P>(sm64_uniform_pm1(a.seed, rstream, (uint64_t)orow));
       }
     }
     return v;
@@ -1155,31 +1156,34 @@ cudaError_t launch_pass(int prec, int mode, const PassArgs& a, const PassLaunch&
   return cudaErrorInvalidValue;
 }
 
-// out[j*n + r] = s_j * V(r, j), V(r, j) at (r / TILE_R) * tstride + j * cstride + r % TILE_R
+// out[j*n + v] = s_j * V(r, j) with r = iperm[v] (iperm NULL: r = v), V(r, j)
+// at (r / TILE_R) * tstride + j * cstride + r % TILE_R
 template <typename B>
 __global__ void basis_to_f64_kernel(const B* V, int64_t tstride, int64_t cstride, int64_t n,
-                                    int cols, const double* s, double* out) {
+                                    int cols, const double* s, const int32_t* iperm,
+                                    double* out) {
   const int64_t total = n * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / n, r = e - j * n;
+    const int64_t j = e / n, v = e - j * n;
+    const int64_t r = iperm ? (int64_t)iperm[v] : v;
     out[e] = s[j] * (double)V[(r / TILE_R) * tstride + j * cstride + r % TILE_R];
   }
 }
 
 cudaError_t launch_basis_to_f64(int prec, const void* V, int64_t tstride, int64_t cstride,
-                                int64_t n, int cols, const double* s_dev, double* out,
-                                cudaStream_t st) {
+                                int64_t n, int cols, const double* s_dev, const int32_t* iperm,
+                                double* out, cudaStream_t st) {
   const int64_t total = n * cols;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks < 1) blocks = 1;
   if (prec == PREC_DDD)
     basis_to_f64_kernel<double><<<(int)blocks, 256, 0, st>>>(
-        static_cast<const double*>(V), tstride, cstride, n, cols, s_dev, out);
+        static_cast<const double*>(V), tstride, cstride, n, cols, s_dev, iperm, out);
   else
     basis_to_f64_kernel<float><<<(int)blocks, 256, 0, st>>>(
-        static_cast<const float*>(V), tstride, cstride, n, cols, s_dev, out);
+        static_cast<const float*>(V), tstride, cstride, n, cols, s_dev, iperm, out);
   return cudaGetLastError();
 }
 

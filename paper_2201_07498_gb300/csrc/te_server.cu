@@ -277,7 +277,7 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
                           reinterpret_cast<const int64_t*>(T + L.t_src),
                           reinterpret_cast<const int32_t*>(T + L.t_len), (int)H.slices.size(),
                           reinterpret_cast<int32_t*>(W + L.cols), W + L.vals, nullptr, nullptr,
-                          nullptr, s);
+                          nullptr, nullptr, s);
   LzState* st = reinterpret_cast<LzState*>(W + L.st);
   double* U = reinterpret_cast<double*>(S->pool.base + res);
   if (e == cudaSuccess) e = launch_solve_begin(st, nullptr, U, nullptr, nullptr, s);

@@ -74,7 +74,7 @@ bool is_device_ptr(const void* p) {
 
 struct Work {
   // byte offsets inside one allocation
-  size_t V = 0, ytil = 0, xcur = 0, w = 0, partials = 0, st = 0, Uint = 0, slices = 0, vout = 0,
+  size_t V = 0, ytil = 0, xcur = 0, perm = 0, iperm = 0, w = 0, partials = 0, st = 0, Uint = 0, slices = 0, vout = 0,
          scols = 0, svals = 0, svals64 = 0, lscale = 0, lrows = 0, vpart = 0, flag = 0,
          total = 0;
 };
@@ -87,9 +87,10 @@ struct SellSizes {
 };
 
 // refine: room for the plan's own Ritz vectors (n x K) and, for a
-// mixed-precision form, a binary64 copy of the SELL values
+// mixed-precision form, a binary64 copy of the SELL values; reorder: the row
+// permutation both ways and the plan's own Ritz vectors (relabelled rows)
 Work layout(int prec, int vk, int64_t n_pad, int m, int grid, const SellSizes& z,
-            bool refine = false, int64_t n = 0, int K = 0) {
+            bool refine = false, int64_t n = 0, int K = 0, bool reorder = false) {
   Work w;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -103,7 +104,9 @@ Work layout(int prec, int vk, int64_t n_pad, int m, int grid, const SellSizes& z
   w.w = take((size_t)n_pad * 8);
   w.partials = take((size_t)grid * PSTRIDE * 8);
   w.st = take(sizeof(LzState));
-  w.Uint = refine ? take((size_t)n * (size_t)K * 8) : 0;
+  w.Uint = (refine || reorder) ? take((size_t)n * (size_t)K * 8) : 0;
+  w.perm = reorder ? take((size_t)n * 4) : 0;
+  w.iperm = reorder ? take((size_t)n * 4) : 0;
   w.slices = take(std::max<size_t>(z.slices, 1) * sizeof(SellSlice));
   w.vout = take(std::max<size_t>(z.slices, 1) * SELL_C * sizeof(int32_t));
   w.scols = take(std::max<size_t>(z.entries, 1) * sizeof(int32_t));
@@ -191,7 +194,10 @@ struct te_plan {
   cudaStream_t cs = nullptr;   // copy stream
   cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  double* ubase = nullptr;  // with refinement: the plan's Ritz vectors (n x K)
+  double* ubase = nullptr;  // with refinement or reordering: the plan's Ritz vectors (n x K)
+  bool reorder = false;     // rows relabelled by degree (te_options.order)
+  int32_t* dperm = nullptr;   // solver row r = caller row dperm[r] (device)
+  int32_t* diperm = nullptr;  // its inverse
   Work W;
   char* work = nullptr;
   LzState* st = nullptr;
@@ -244,7 +250,7 @@ cudaError_t upload_meta(const SellHost& H, const DevSell& D, cudaStream_t s) {
 
 cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const int32_t* ci,
                         const void* val, int64_t n, int64_t nnz, const DevSell& D, void* vals64,
-                        float* lane_scale, cudaStream_t s) {
+                        float* lane_scale, const int32_t* colmap, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (!H.slices.empty()) {
     e = cudaMemcpyAsync(const_cast<SellSlice*>(D.slices), H.slices.data(),
@@ -285,10 +291,10 @@ cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const
   if (e == cudaSuccess)
     e = launch_sell_build(quant ? D.vk : in_type, D.vk, ci, quant ? q : val, D.slices, dsrc,
                           dlen, D.nslices, D.cols, D.vals, drow, rscale,
-                          fp8 ? lane_scale : nullptr, s);
+                          fp8 ? lane_scale : nullptr, colmap, s);
   if (e == cudaSuccess && vals64)
     e = launch_sell_build(TE_F64, TE_F64, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols,
-                          vals64, nullptr, nullptr, nullptr, s);
+                          vals64, nullptr, nullptr, nullptr, colmap, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(dsrc);
   cudaFree(dlen);
@@ -309,14 +315,16 @@ constexpr int TUNE_VMAX[TUNE_N] = {SELL_VMAX, 32, 128, SELL_VMAX, SELL_VMAX};
 // return the index of the fastest.
 cudaError_t autotune_layout(int prec, int vk, int in_type, const int64_t* rph, const int64_t* rp,
                             const int32_t* ci, const void* val, int64_t n, int64_t nnz,
-                            cudaStream_t s, int* best) {
+                            const int32_t* hperm, const int32_t* dcolmap, cudaStream_t s,
+                            int* best) {
   *best = 0;
   float best_ms = 0.f;
   const size_t xelt = prec == PREC_DDD ? 8 : 4;
   for (int c = 0; c < TUNE_N; ++c) {
     SellHost H;
     std::string err;
-    if (!make_sell(rph, n, nnz, H, err, TUNE_WINDOW[c], TUNE_VMAX[c])) return cudaErrorInvalidValue;
+    if (!make_sell(rph, n, nnz, H, err, TUNE_WINDOW[c], TUNE_VMAX[c], hperm))
+      return cudaErrorInvalidValue;
     const size_t b_sl = al256(std::max<size_t>(H.slices.size(), 1) * sizeof(SellSlice));
     const size_t b_vo = al256(std::max<size_t>(H.vout.size(), 1) * 4);
     const size_t b_co = al256(std::max<size_t>((size_t)H.entries, 1) * 4);
@@ -346,7 +354,8 @@ cudaError_t autotune_layout(int prec, int vk, int in_type, const int64_t* rph, c
     D.nlrows = (int)H.lrows.size();
     D.nlbig = (int)H.nbig;
     e = cudaMemsetAsync(x, 0, b_x + b_y, s);
-    if (e == cudaSuccess) e = upload_sell(in_type, H, rp, ci, val, n, nnz, D, nullptr, ls, s);
+    if (e == cudaSuccess)
+      e = upload_sell(in_type, H, rp, ci, val, n, nnz, D, nullptr, ls, dcolmap, s);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -383,6 +392,7 @@ PassArgs base_args(te_plan* P) {
   a.tstride = basis_tstride(P);
   a.cstride = TILE_R;
   a.xcopy = at(P, P->W.xcur);
+  a.perm = P->dperm;
   a.n = P->n;
   a.m = P->m;
   a.K = P->K;
@@ -617,11 +627,20 @@ cudaError_t enqueue_solve(te_plan* P, cudaStream_t s) {
   a.nb = P->m;
   a.fin = FIN_NONE;
   if ((e = pass(P, MODE_RITZ, a, s)) != cudaSuccess) return e;
-  if (!P->refine) return cudaSuccess;
+  const int rgrid = refine_grid(P->num_sms);
+  if (!P->refine) {
+    if (!P->reorder) return cudaSuccess;
+    // the Ritz vectors of the relabelled rows, back in the caller's order
+    P->nkernels++;
+    if ((e = prof_begin(P, s)) != cudaSuccess) return e;
+    if ((e = launch_copy_out_perm(P->st, P->ubase, P->n, P->K, P->diperm, rgrid * 4, s)) !=
+        cudaSuccess)
+      return e;
+    return prof_end(P, s, TE_KIND_RITZ, (16.0 + 4.0 / P->K) * (double)P->n * P->K);
+  }
   // binary64 Rayleigh-quotient refinement: y = M u_k, then the reduction
   double* y = static_cast<double*>(at(P, P->W.ytil));
   double* part = static_cast<double*>(at(P, P->W.partials));
-  const int rgrid = refine_grid(P->num_sms);
   for (int k = 0; k < P->K; ++k) {
     P->nkernels += 2 + (P->sell64.nlrows > 0 ? 1 : 0);
     if ((e = prof_begin(P, s)) != cudaSuccess) return e;
@@ -636,16 +655,18 @@ cudaError_t enqueue_solve(te_plan* P, cudaStream_t s) {
   // the refined vectors stay the Ritz vectors: hand them to the caller's buffer
   P->nkernels++;
   if ((e = prof_begin(P, s)) != cudaSuccess) return e;
-  if ((e = launch_copy_out(P->st, P->ubase, (size_t)P->n * P->K, rgrid * 4, s)) != cudaSuccess)
-    return e;
+  e = P->reorder ? launch_copy_out_perm(P->st, P->ubase, P->n, P->K, P->diperm, rgrid * 4, s)
+                 : launch_copy_out(P->st, P->ubase, (size_t)P->n * P->K, rgrid * 4, s);
+  if (e != cudaSuccess) return e;
   return prof_end(P, s, TE_KIND_REFINE, 16.0 * (double)P->n * P->K);
 }
 
 __global__ void solve_begin_kernel(LzState* st, const double* v1, double* eigvecs,
                                    double* eigvals, double* plan_vecs) {
   st->v1 = v1;
-  // with refinement the Ritz vectors go to the plan's buffer (the refinement
-  // SpMVs read them at a fixed address) and are copied out at the end
+  // with refinement (or relabelled rows) the Ritz vectors go to the plan's
+  // buffer (the refinement SpMVs read them at a fixed address) and are
+  // copied out at the end
   st->eigvecs = plan_vecs ? plan_vecs : eigvecs;
   st->eigvecs_user = plan_vecs ? eigvecs : nullptr;
   st->eigvals_out = eigvals;
@@ -669,8 +690,11 @@ namespace {
 
 te_status plan_begin(te_plan* P, const double* v1, double* eigvecs_dev, double* eigvals_dev,
                      cudaStream_t s) {
+  // refinement and relabelled rows keep the Ritz vectors in the plan's own
+  // buffer (copied out to the caller's at the end)
+  const bool own = P->refine || (P->reorder && eigvecs_dev != nullptr);
   solve_begin_kernel<<<1, 1, 0, s>>>(P->st, v1 ? v1 : P->opt.v1, eigvecs_dev, eigvals_dev,
-                                     P->refine ? P->ubase : nullptr);
+                                     own ? P->ubase : nullptr);
   TE_CK(cudaGetLastError(), "solve_begin launch");
   return TE_OK;
 }
@@ -752,6 +776,8 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
       opt.reorth != TE_REORTH_DELAYED)
     return fail(TE_ERR_INVALID_ARG, "reorth must be TE_REORTH_FULL, _NONE or _DELAYED");
   if (opt.refine != 0 && opt.refine != 1) return fail(TE_ERR_INVALID_ARG, "refine must be 0 or 1");
+  if (opt.order != TE_ORDER_KEEP && opt.order != TE_ORDER_DEGREE)
+    return fail(TE_ERR_INVALID_ARG, "order must be TE_ORDER_KEEP or TE_ORDER_DEGREE");
   const int in_type = A->values_f64 ? TE_F64 : p.values;
   if (opt.refine && in_type != TE_F64)
     return fail(TE_ERR_INVALID_ARG,
@@ -784,6 +810,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   P->refine = opt.refine != 0;
   P->noreorth = opt.reorth == TE_REORTH_NONE;
   P->delayed = opt.reorth == TE_REORTH_DELAYED;
+  P->reorder = opt.order == TE_ORDER_DEGREE;
   TE_CK(cudaGetDevice(&P->dev), "cudaGetDevice");
   TE_CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev),
         "device attribute");
@@ -801,7 +828,16 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   }
   SellHost sell;
   std::string perr;
-  if (!make_sell(rph, A->n, A->nnz, sell, perr))
+  // relabelled rows: the solver's row r is the caller's row hperm[r]
+  std::vector<int32_t> hperm, hiperm;
+  if (P->reorder) {
+    if (!rows_valid(rph, A->n, A->nnz, perr)) return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+    hperm.resize((size_t)A->n);
+    hiperm.resize((size_t)A->n);
+    degree_order(rph, A->n, hperm.data(), hiperm.data());
+  }
+  const int32_t* hp = P->reorder ? hperm.data() : nullptr;
+  if (!make_sell(rph, A->n, A->nnz, sell, perr, SELL_WINDOW, SELL_VMAX, hp))
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
 
   // launch shapes of the basis passes
@@ -876,7 +912,11 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
       dval = tmp + brp + bci;
     }
     int* flag = nullptr;
+    int32_t* tmap = nullptr;  // the column relabelling, for the trial layouts
     cudaError_t e = cudaMalloc(&flag, sizeof(int));
+    if (e == cudaSuccess && P->reorder) e = cudaMalloc(&tmap, sizeof(int32_t) * A->n);
+    if (e == cudaSuccess && P->reorder)
+      e = cudaMemcpyAsync(tmap, hiperm.data(), sizeof(int32_t) * A->n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
     if (e == cudaSuccess) e = launch_validate_cols(dci, A->nnz, A->n, flag, s);
     int hflag = 0;
@@ -885,13 +925,15 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     if (flag) cudaFree(flag);
     int best = 0;
     if (e == cudaSuccess && !hflag)
-      e = autotune_layout(P->prec, P->vk, in_type, rph, drp, dci, dval, A->n, A->nnz, s, &best);
+      e = autotune_layout(P->prec, P->vk, in_type, rph, drp, dci, dval, A->n, A->nnz, hp, tmap, s,
+                          &best);
     if (tmp) cudaFree(tmp);
+    if (tmap) cudaFree(tmap);
     if (e != cudaSuccess) return cuda_fail(e, "autotune the SpMV layout");
     if (hflag) return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
     P->sell_window = TUNE_WINDOW[best];
     P->sell_vmax = TUNE_VMAX[best];
-    if (best != 0 && !make_sell(rph, A->n, A->nnz, sell, perr, P->sell_window, P->sell_vmax))
+    if (best != 0 && !make_sell(rph, A->n, A->nnz, sell, perr, P->sell_window, P->sell_vmax, hp))
       return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
   }
 
@@ -900,7 +942,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   zs.entries = P->streaming ? (size_t)(2 * P->cap_entries) : (size_t)sell.entries;
   zs.lrows = sell.lrows.size();
   zs.pieces = (size_t)sell.pieces;
-  P->W = layout(P->prec, P->vk, P->n_pad, P->m, grid, zs, P->refine, P->n, P->K);
+  P->W = layout(P->prec, P->vk, P->n_pad, P->m, grid, zs, P->refine, P->n, P->K, P->reorder);
   const size_t in_elt = in_type == TE_F64 ? 8 : 4;
   size_t csr_bytes = 0;
   if (A->where == TE_HOST && !P->streaming)
@@ -921,7 +963,8 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     TE_CK(cudaHostAlloc(&P->hvals, std::max<size_t>((size_t)sell.entries, 1) * velt,
                         cudaHostAllocDefault),
           "allocate pinned layout");
-    if (!build_sell_host(sell, A->col_idx, A->values, in_type, P->vk, A->n, P->hcols, P->hvals))
+    if (!build_sell_host(sell, A->col_idx, A->values, in_type, P->vk, A->n,
+                         P->reorder ? hiperm.data() : nullptr, P->hcols, P->hvals))
       return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
     TE_CK(cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking), "create copy stream");
     for (cudaEvent_t* e : {&P->ev_ready[0], &P->ev_ready[1], &P->ev_free[0], &P->ev_free[1],
@@ -965,6 +1008,17 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     TE_CK(cudaStreamSynchronize(s), "plan setup");
     if (hflag) return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
   }
+  if (P->reorder) {
+    P->dperm = static_cast<int32_t*>(at(P, P->W.perm));
+    P->diperm = static_cast<int32_t*>(at(P, P->W.iperm));
+    TE_CK(cudaMemcpyAsync(P->dperm, hperm.data(), sizeof(int32_t) * A->n, cudaMemcpyHostToDevice,
+                          s),
+          "upload the row order");
+    TE_CK(cudaMemcpyAsync(P->diperm, hiperm.data(), sizeof(int32_t) * A->n,
+                          cudaMemcpyHostToDevice, s),
+          "upload the row order");
+    TE_CK(cudaStreamSynchronize(s), "upload the row order");
+  }
   // the SELL copy of the matrix that the solve streams
   P->sell.slices = static_cast<SellSlice*>(at(P, P->W.slices));
   P->sell.vout = static_cast<int32_t*>(at(P, P->W.vout));
@@ -982,15 +1036,16 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     TE_CK(upload_meta(sell, P->sell, s), "upload the SELL layout");
   else
     TE_CK(upload_sell(in_type, sell, P->rp, P->ci, P->val, P->n, P->nnz, P->sell, vals64,
-                      P->W.lscale ? static_cast<float*>(at(P, P->W.lscale)) : nullptr, s),
+                      P->W.lscale ? static_cast<float*>(at(P, P->W.lscale)) : nullptr,
+                      P->diperm, s),
           "build the SELL layout");
   if (P->refine) {
     P->sell64 = P->sell;
     P->sell64.vk = TE_F64;
     P->sell64.lscale = nullptr;
     if (vals64) P->sell64.vals = vals64;
-    P->ubase = static_cast<double*>(at(P, P->W.Uint));
   }
+  if (P->refine || P->reorder) P->ubase = static_cast<double*>(at(P, P->W.Uint));
   if (P->owned_csr) {  // the solve reads only the SELL copy
     cudaFree(P->owned_csr);
     P->owned_csr = nullptr;
@@ -1225,7 +1280,7 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
   const int in_type = A->values_f64 ? TE_F64 : p.values;
   if (e == cudaSuccess)
     e = upload_sell(in_type, sell, A->row_ptr, A->col_idx, A->values, A->n, A->nnz, D, nullptr,
-                    lscale, s);
+                    lscale, nullptr, s);
   // the kernel writes rows with entries only
   if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, sizeof(double) * A->n, s);
   if (e == cudaSuccess) e = launch_spmv(prec, D, x, y, true, s);
@@ -1262,7 +1317,7 @@ te_status te_lanczos(const te_csr* A, int32_t krylov_steps, te_precision p, cons
     e = cudaMemcpyAsync(hst, &P->st->restart_flag, sizeof(hst), cudaMemcpyDeviceToHost, s);
   if (r == TE_OK && e == cudaSuccess && basis)
     e = launch_basis_to_f64(P->prec, at(P, P->W.V), basis_tstride(P), TILE_R, P->n,
-                            krylov_steps, P->st->s, basis, s);
+                            krylov_steps, P->st->s, P->diperm, basis, s);
   if (r == TE_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (r == TE_OK && e != cudaSuccess) r = cuda_fail(e, "te_lanczos");
   if (r == TE_OK) {

@@ -28,9 +28,10 @@
 namespace te {
 
 // Windows of rows [w0, w1) into `out`, with entry offsets and cut-row piece
-// slots numbered from 0 (the caller shifts them).
+// slots numbered from 0 (the caller shifts them).  Row r of the layout is CSR
+// row perm[r] (perm NULL: row r); it writes output r.
 static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, int window,
-                         int vmax, SellHost& out) {
+                         int vmax, const int32_t* perm, SellHost& out) {
   struct Piece {
     int64_t src;
     int32_t len, out, row;
@@ -41,10 +42,11 @@ static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, i
     const int64_t r0 = w * window, r1 = std::min<int64_t>(r0 + window, n);
     win.clear();
     for (int64_t r = r0; r < r1; ++r) {
-      const int64_t L = rp[r + 1] - rp[r];
+      const int64_t o = perm ? (int64_t)perm[r] : r;  // the CSR row
+      const int64_t L = rp[o + 1] - rp[o];
       if (L == 0) continue;  // empty rows: never written by the kernel
       if (L <= vmax) {
-        win.push_back({rp[r], (int32_t)L, (int32_t)r, (int32_t)r});
+        win.push_back({rp[o], (int32_t)L, (int32_t)r, (int32_t)o});
         continue;
       }
       LongRow lr;
@@ -53,9 +55,9 @@ static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, i
       lr.count = (int32_t)((L + vmax - 1) / vmax);
       lr.pad_ = 0;
       for (int32_t c = 0; c < lr.count; ++c) {
-        const int64_t s0 = rp[r] + (int64_t)c * vmax;
-        const int64_t l = std::min<int64_t>(vmax, rp[r + 1] - s0);
-        win.push_back({s0, (int32_t)l, -1 - (int32_t)(out.pieces + c), (int32_t)r});
+        const int64_t s0 = rp[o] + (int64_t)c * vmax;
+        const int64_t l = std::min<int64_t>(vmax, rp[o + 1] - s0);
+        win.push_back({s0, (int32_t)l, -1 - (int32_t)(out.pieces + c), (int32_t)o});
       }
       out.pieces += lr.count;
       out.lrows.push_back(lr);
@@ -98,9 +100,10 @@ static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, i
 }
 
 // Threads take contiguous ranges of windows; the parts are joined with their
-// entry and piece offsets, so the result equals a sequential build.
+// entry and piece offsets, so the result equals a sequential build.  The row
+// pointers are checked (all rows) before any window is built.
 bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err,
-               int window, int vmax) {
+               int window, int vmax, const int32_t* perm) {
   out = SellHost();
   if (rp[0] != 0) {
     err = "row_ptr[0] must be 0";
@@ -117,7 +120,7 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
   if ((int64_t)nt > W / 16) nt = (unsigned)std::max<int64_t>(1, W / 16);
   std::vector<int64_t> bad(nt, -1);
   std::vector<SellHost> part(nt);
-  auto work = [&](unsigned t) {
+  auto check = [&](unsigned t) {
     const int64_t w0 = W * t / nt, w1 = W * (t + 1) / nt;
     const int64_t r0 = w0 * window, r1 = std::min<int64_t>(w1 * window, n);
     for (int64_t r = r0; r < r1; ++r)
@@ -125,20 +128,27 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
         bad[t] = r;
         return;
       }
-    sell_windows(rp, n, w0, w1, window, vmax, part[t]);
   };
-  if (nt == 1) {
-    work(0);
-  } else {
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t) th.emplace_back(work, t);
-    for (auto& x : th) x.join();
-  }
+  auto work = [&](unsigned t) {
+    const int64_t w0 = W * t / nt, w1 = W * (t + 1) / nt;
+    sell_windows(rp, n, w0, w1, window, vmax, perm, part[t]);
+  };
+  auto run = [&](auto&& f) {
+    if (nt == 1) {
+      f(0u);
+    } else {
+      std::vector<std::thread> th;
+      for (unsigned t = 0; t < nt; ++t) th.emplace_back(f, t);
+      for (auto& x : th) x.join();
+    }
+  };
+  run(check);
   for (unsigned t = 0; t < nt; ++t)
     if (bad[t] >= 0) {
       err = "row_ptr must be non-decreasing (row " + std::to_string(bad[t]) + ")";
       return false;
     }
+  run(work);
   // join the parts
   size_t ns = 0, nl = 0, nr = 0;
   for (const SellHost& p : part) {
@@ -211,6 +221,46 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
   return true;
 }
 
+bool rows_valid(const int64_t* rp, int64_t n, int64_t nnz, std::string& err) {
+  if (rp[0] != 0) {
+    err = "row_ptr[0] must be 0";
+    return false;
+  }
+  if (rp[n] != nnz) {
+    err = "row_ptr[n] != nnz";
+    return false;
+  }
+  for (int64_t r = 0; r < n; ++r)
+    if (rp[r + 1] < rp[r]) {
+      err = "row_ptr must be non-decreasing (row " + std::to_string(r) + ")";
+      return false;
+    }
+  return true;
+}
+
+// Rows by length, longest first, ties in row order (a stable counting sort
+// over the row lengths): perm[r] = the row placed at r, iperm its inverse.
+// Sparse graphs whose degrees follow a power law then keep their
+// high-degree vertices together, so that the SpMV's reads of x for those
+// columns share cache lines.  The row pointers must be valid.
+void degree_order(const int64_t* rp, int64_t n, int32_t* perm, int32_t* iperm) {
+  int64_t maxl = 0;
+  for (int64_t r = 0; r < n; ++r) maxl = std::max<int64_t>(maxl, rp[r + 1] - rp[r]);
+  std::vector<int64_t> pos((size_t)maxl + 2, 0);
+  for (int64_t r = 0; r < n; ++r) ++pos[(size_t)(rp[r + 1] - rp[r])];
+  int64_t acc = 0;
+  for (int64_t L = maxl; L >= 0; --L) {
+    const int64_t c = pos[(size_t)L];
+    pos[(size_t)L] = acc;
+    acc += c;
+  }
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t at = pos[(size_t)(rp[r + 1] - rp[r])]++;
+    perm[at] = (int32_t)r;
+    iperm[r] = (int32_t)at;
+  }
+}
+
 // Host build of the SELL arrays (for a matrix that stays in host memory and
 // is streamed to the device in row blocks): the same arrangement the device
 // build produces; binary64 -> binary32 rounds to nearest even.  Threads split
@@ -218,7 +268,7 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
 // column index lies outside [0, n).
 template <typename Vin, typename Vout>
 static bool build_sell_host_t(const SellHost& H, const int32_t* ci, const Vin* val, int64_t n,
-                              int32_t* cols, Vout* vals) {
+                              const int32_t* colmap, int32_t* cols, Vout* vals) {
   const int64_t S = (int64_t)H.slices.size();
   unsigned nt = std::thread::hardware_concurrency();
   if (nt < 1) nt = 1;
@@ -237,8 +287,9 @@ static bool build_sell_host_t(const SellHost& H, const int32_t* ci, const Vin* v
             const int64_t dst = q.base + (int64_t)k * SELL_C + lane;
             if (k < len) {
               const int32_t c = ci[src + k];
-              if (c < 0 || (int64_t)c >= n) bad[t] = 1;
-              cols[dst] = c;
+              const bool ok = c >= 0 && (int64_t)c < n;
+              if (!ok) bad[t] = 1;
+              cols[dst] = (colmap && ok) ? colmap[c] : c;
               vals[dst] = (Vout)val[src + k];
             } else {
               cols[dst] = 0;
@@ -256,15 +307,15 @@ static bool build_sell_host_t(const SellHost& H, const int32_t* ci, const Vin* v
 }
 
 bool build_sell_host(const SellHost& H, const int32_t* ci, const void* val, int in_type, int vk,
-                     int64_t n, int32_t* cols, void* vals) {
+                     int64_t n, const int32_t* colmap, int32_t* cols, void* vals) {
   if (in_type == TE_F64 && vk == TE_F64)
-    return build_sell_host_t(H, ci, static_cast<const double*>(val), n, cols,
+    return build_sell_host_t(H, ci, static_cast<const double*>(val), n, colmap, cols,
                              static_cast<double*>(vals));
   if (in_type == TE_F64 && vk == TE_F32)
-    return build_sell_host_t(H, ci, static_cast<const double*>(val), n, cols,
+    return build_sell_host_t(H, ci, static_cast<const double*>(val), n, colmap, cols,
                              static_cast<float*>(vals));
   if (in_type == TE_F32 && vk == TE_F32)
-    return build_sell_host_t(H, ci, static_cast<const float*>(val), n, cols,
+    return build_sell_host_t(H, ci, static_cast<const float*>(val), n, colmap, cols,
                              static_cast<float*>(vals));
   return false;
 }
@@ -280,7 +331,8 @@ template <typename Vin, typename Vout>
 __global__ void sell_build_kernel(const int32_t* ci, const Vin* val, const SellSlice* slices,
                                   const int64_t* vsrc, const int32_t* vlen, int nslices,
                                   int32_t* cols, Vout* vals, const int32_t* vrow,
-                                  const float* row_scale, float* lane_scale) {
+                                  const float* row_scale, float* lane_scale,
+                                  const int32_t* colmap) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)nslices * SELL_C) return;
   const int64_t s = t / SELL_C;
@@ -295,7 +347,8 @@ __global__ void sell_build_kernel(const int32_t* ci, const Vin* val, const SellS
   for (int k = 0; k < sl.len; ++k) {
     const int64_t dst = sl.base + (int64_t)k * SELL_C + lane;
     if (k < len) {
-      cols[dst] = ci[src + k];
+      const int32_t c = ci[src + k];  // checked to lie in [0, n) before the build
+      cols[dst] = colmap ? colmap[c] : c;
       vals[dst] = convert_value<Vin, Vout>(val[src + k]);
     } else {
       cols[dst] = 0;
@@ -307,7 +360,8 @@ __global__ void sell_build_kernel(const int32_t* ci, const Vin* val, const SellS
 cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, const void* val,
                               const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
                               int nslices, int32_t* cols, void* vals, const int32_t* vrow,
-                              const float* row_scale, float* lane_scale, cudaStream_t s) {
+                              const float* row_scale, float* lane_scale, const int32_t* colmap,
+                              cudaStream_t s) {
   if (nslices <= 0) return cudaSuccess;
   const int64_t lanes = (int64_t)nslices * SELL_C;
   const unsigned blocks = (unsigned)((lanes + 255) / 256);
@@ -316,7 +370,7 @@ cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, cons
     sell_build_kernel<TI, TO><<<blocks, 256, 0, s>>>(ci, static_cast<const TI*>(val), slices, \
                                                      vsrc, vlen, nslices, cols,                \
                                                      static_cast<TO*>(vals), vrow, row_scale,  \
-                                                     lane_scale);                              \
+                                                     lane_scale, colmap);                      \
     return cudaGetLastError();                                                                 \
   }
   TE_BUILD(TE_F64, TE_F64, double, double)
