@@ -391,6 +391,13 @@ te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t
                          int32_t* slice_len, int32_t* lane_out, int64_t* lane_src,
                          int32_t* lane_len);
 
+/* The row order of TE_ORDER_DEGREE (host only, no GPU needed): rows by
+ * length, longest first, rows of equal length in increasing index order.
+ * perm[r] (n, host) = the caller's row placed at r; iperm (n, host, may be
+ * NULL) = its inverse.  Returns TE_ERR_INVALID_ARG for a malformed row_ptr. */
+te_status te_degree_order(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t* perm,
+                          int32_t* iperm);
+
 #ifdef __cplusplus
 }
 #endif

@@ -121,6 +121,8 @@ _SIGS = {
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
+    "te_degree_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -510,6 +512,20 @@ def spmv_layout(row_ptr, nnz: int, window: int = 0, vmax: int = 0):
     _check(rc)
     return {"slice_len": slen, "lane_out": lout, "lane_src": lsrc, "lane_len": llen,
             "entries": int(ne.value), "long_rows": int(nl.value)}
+
+
+def degree_order(row_ptr, nnz: int):
+    """The row order of order="degree" (host): (perm, iperm), perm[r] = the
+    caller's row placed at r."""
+    import numpy as np
+    lib = load_library()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    n = len(rp) - 1
+    perm = np.empty(n, dtype=np.int32)
+    iperm = np.empty(n, dtype=np.int32)
+    _check(lib.te_degree_order(ctypes.c_void_p(rp.ctypes.data), n, nnz,
+                               ctypes.c_void_p(perm.ctypes.data), ctypes.c_void_p(iperm.ctypes.data)))
+    return perm, iperm
 
 
 def quantize(csr: CSR, to: str, stream=None):

@@ -89,13 +89,22 @@ struct SellHost {
 constexpr int SELL_BIG_PIECES = 16;  // cut rows with more pieces get a whole warp
 // returns false (and a message) if row_ptr is malformed
 // window: rows sorted together (sigma); vmax: longest piece (rows above are cut)
-// perm (optional): row r of the layout is CSR row perm[r] and writes output r
+// A row order: row r of the layout is CSR row perm[r], whose entries start at
+// src[r] and number len[r]
+struct RowOrder {
+  const int32_t* perm;
+  const int64_t* src;
+  const int32_t* len;
+};
+// ord (optional): row r of the layout is CSR row ord->perm[r] and writes output r
 bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err,
-               int window = SELL_WINDOW, int vmax = SELL_VMAX, const int32_t* perm = nullptr);
+               int window = SELL_WINDOW, int vmax = SELL_VMAX, const RowOrder* ord = nullptr);
 // row_ptr starts at 0, ends at nnz and never decreases
 bool rows_valid(const int64_t* rp, int64_t n, int64_t nnz, std::string& err);
-// rows by length, longest first (stable): perm[r] = row placed at r, iperm = inverse
-void degree_order(const int64_t* rp, int64_t n, int32_t* perm, int32_t* iperm);
+// rows by length, longest first (stable): perm[r] = row placed at r, iperm = inverse,
+// src/len = that row's first entry and length
+void degree_order(const int64_t* rp, int64_t n, int32_t* perm, int32_t* iperm, int64_t* src,
+                  int32_t* len);
 
 // Device copy of a SELL layout.
 struct DevSell {
@@ -172,6 +181,8 @@ struct PassArgs {
   int64_t cstride;   // elements from a column to the next (TILE_R: tile-major)
   void* xcopy;       // optional: the column a pass stores, also written contiguously
   const int32_t* perm;  // optional: row r of the vectors is the caller's row perm[r]
+  double* urows;     // RITZ, optional: write the vectors by rows (K rounded up to even
+                     // per row) here instead of by columns to st->eigvecs
   int64_t n;         // true rows
   int nb;            // basis columns read by this pass: col0 .. col0 + nb - 1
   int col0;          // first basis column read (0 unless reorthogonalisation is off)
@@ -237,6 +248,10 @@ cudaError_t launch_copy_out(LzState* st, const double* src, size_t count, int gr
 // vectors of the relabelled rows back in the caller's row order (no-op when
 // eigvecs_user is NULL)
 cudaError_t launch_copy_out_perm(LzState* st, const double* src, int64_t n, int K,
+                                 const int32_t* iperm, int grid, cudaStream_t s);
+// the same from vectors stored by rows: st->eigvecs_user[k*n + v] =
+// src[iperm[v] * Kr + k], Kr = K rounded up to even
+cudaError_t launch_copy_out_rows(LzState* st, const double* src, int64_t n, int K,
                                  const int32_t* iperm, int grid, cudaStream_t s);
 // G[a*K + b] = u_a . u_b (device), per-block partials in `partials`
 // (grid * K*(K+1)/2 doubles)

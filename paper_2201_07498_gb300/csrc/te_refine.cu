@@ -130,6 +130,30 @@ cudaError_t launch_copy_out_perm(LzState* st, const double* src, int64_t n, int 
   return cudaGetLastError();
 }
 
+// Thread per caller row: its K values are one contiguous row of src (read
+// with 16-byte loads), written to the K columns (coalesced across threads).
+__global__ void copy_out_rows_kernel(const LzState* st, const double* src, int64_t n, int K,
+                                     const int32_t* iperm) {
+  double* dst = st->eigvecs_user;
+  if (dst == nullptr) return;
+  const int Kr = (K + 1) & ~1;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const double2* row = reinterpret_cast<const double2*>(src + (size_t)iperm[v] * Kr);
+    for (int k = 0; k < K; k += 2) {
+      const double2 t = row[k >> 1];
+      dst[(size_t)k * n + v] = t.x;
+      if (k + 1 < K) dst[(size_t)(k + 1) * n + v] = t.y;
+    }
+  }
+}
+
+cudaError_t launch_copy_out_rows(LzState* st, const double* src, int64_t n, int K,
+                                 const int32_t* iperm, int grid, cudaStream_t s) {
+  copy_out_rows_kernel<<<grid, 256, 0, s>>>(st, src, n, K, iperm);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Gram matrix: G[a][b] = sum_r U[r, a] U[r, b] for a <= b (pair index p in
 // row-major upper-triangle order).  Each block stages GR rows of U in shared

@@ -851,14 +851,22 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
             }
           }
           if (row < a.n) {
+            double o[RITZ_KC];
 #pragma unroll
-            for (int kk = 0; kk < RITZ_KC; ++kk)
-              if (k0 + kk < K) {
-                if constexpr (P == PREC_FDF)
-                  U[(size_t)(k0 + kk) * a.n + row] = dw_to_double_bits(dacc_value(ra[kk]));
-                else
-                  U[(size_t)(k0 + kk) * a.n + row] = ra[kk];
-              }
+            for (int kk = 0; kk < RITZ_KC; ++kk) {
+              if constexpr (P == PREC_FDF) o[kk] = dw_to_double_bits(dacc_value(ra[kk]));
+              else o[kk] = ra[kk];
+            }
+            if (a.urows) {  // by rows: pairs of outputs as 16-byte stores
+              double2* ur = reinterpret_cast<double2*>(a.urows + (size_t)row * ((K + 1) & ~1) + k0);
+#pragma unroll
+              for (int kk = 0; kk < RITZ_KC; kk += 2)
+                if (k0 + kk < K) ur[kk >> 1] = make_double2(o[kk], o[kk + 1]);
+            } else {
+#pragma unroll
+              for (int kk = 0; kk < RITZ_KC; ++kk)
+                if (k0 + kk < K) U[(size_t)(k0 + kk) * a.n + row] = o[kk];
+            }
           }
         }
       }

@@ -104,7 +104,9 @@ Work layout(int prec, int vk, int64_t n_pad, int m, int grid, const SellSizes& z
   w.w = take((size_t)n_pad * 8);
   w.partials = take((size_t)grid * PSTRIDE * 8);
   w.st = take(sizeof(LzState));
-  w.Uint = (refine || reorder) ? take((size_t)n * (size_t)K * 8) : 0;
+  // by rows (K rounded up to even) for relabelled rows without refinement
+  const size_t kcols = (reorder && !refine) ? (size_t)((K + 1) & ~1) : (size_t)K;
+  w.Uint = (refine || reorder) ? take((size_t)n * kcols * 8) : 0;
   w.perm = reorder ? take((size_t)n * 4) : 0;
   w.iperm = reorder ? take((size_t)n * 4) : 0;
   w.slices = take(std::max<size_t>(z.slices, 1) * sizeof(SellSlice));
@@ -315,7 +317,7 @@ constexpr int TUNE_VMAX[TUNE_N] = {SELL_VMAX, 32, 128, SELL_VMAX, SELL_VMAX};
 // return the index of the fastest.
 cudaError_t autotune_layout(int prec, int vk, int in_type, const int64_t* rph, const int64_t* rp,
                             const int32_t* ci, const void* val, int64_t n, int64_t nnz,
-                            const int32_t* hperm, const int32_t* dcolmap, cudaStream_t s,
+                            const RowOrder* hord, const int32_t* dcolmap, cudaStream_t s,
                             int* best) {
   *best = 0;
   float best_ms = 0.f;
@@ -323,7 +325,7 @@ cudaError_t autotune_layout(int prec, int vk, int in_type, const int64_t* rph, c
   for (int c = 0; c < TUNE_N; ++c) {
     SellHost H;
     std::string err;
-    if (!make_sell(rph, n, nnz, H, err, TUNE_WINDOW[c], TUNE_VMAX[c], hperm))
+    if (!make_sell(rph, n, nnz, H, err, TUNE_WINDOW[c], TUNE_VMAX[c], hord))
       return cudaErrorInvalidValue;
     const size_t b_sl = al256(std::max<size_t>(H.slices.size(), 1) * sizeof(SellSlice));
     const size_t b_vo = al256(std::max<size_t>(H.vout.size(), 1) * 4);
@@ -626,6 +628,7 @@ cudaError_t enqueue_solve(te_plan* P, cudaStream_t s) {
   PassArgs a = base_args(P);
   a.nb = P->m;
   a.fin = FIN_NONE;
+  if (P->reorder && !P->refine) a.urows = P->ubase;  // stored by rows, gathered below
   if ((e = pass(P, MODE_RITZ, a, s)) != cudaSuccess) return e;
   const int rgrid = refine_grid(P->num_sms);
   if (!P->refine) {
@@ -633,7 +636,7 @@ cudaError_t enqueue_solve(te_plan* P, cudaStream_t s) {
     // the Ritz vectors of the relabelled rows, back in the caller's order
     P->nkernels++;
     if ((e = prof_begin(P, s)) != cudaSuccess) return e;
-    if ((e = launch_copy_out_perm(P->st, P->ubase, P->n, P->K, P->diperm, rgrid * 4, s)) !=
+    if ((e = launch_copy_out_rows(P->st, P->ubase, P->n, P->K, P->diperm, rgrid * 4, s)) !=
         cudaSuccess)
       return e;
     return prof_end(P, s, TE_KIND_RITZ, (16.0 + 4.0 / P->K) * (double)P->n * P->K);
@@ -815,6 +818,27 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   TE_CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->dev),
         "device attribute");
 
+  // a host matrix that stays resident: its copy to the device starts now and
+  // overlaps the host analysis below
+  if (A->where == TE_HOST && opt.matrix_budget_bytes == 0) {
+    const size_t e_in = in_type == TE_F64 ? 8 : 4;
+    const size_t brp = al256(sizeof(int64_t) * (A->n + 1)), bci = al256(sizeof(int32_t) * A->nnz);
+    TE_CK(cudaMalloc(&P->owned_csr, brp + bci + al256(e_in * A->nnz)), "allocate device CSR");
+    char* b = static_cast<char*>(P->owned_csr);
+    TE_CK(cudaMemcpyAsync(b, A->row_ptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyHostToDevice, s),
+          "copy row_ptr");
+    if (A->nnz > 0) {
+      TE_CK(cudaMemcpyAsync(b + brp, A->col_idx, sizeof(int32_t) * A->nnz, cudaMemcpyHostToDevice,
+                            s),
+            "copy col_idx");
+      TE_CK(cudaMemcpyAsync(b + brp + bci, A->values, e_in * A->nnz, cudaMemcpyHostToDevice, s),
+            "copy values");
+    }
+    P->rp = reinterpret_cast<const int64_t*>(b);
+    P->ci = reinterpret_cast<const int32_t*>(b + brp);
+    P->val = b + brp + bci;
+  }
+
   // row pointers on the host for the partition
   std::vector<int64_t> rp_host;
   const int64_t* rph = A->row_ptr;
@@ -829,14 +853,20 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   SellHost sell;
   std::string perr;
   // relabelled rows: the solver's row r is the caller's row hperm[r]
-  std::vector<int32_t> hperm, hiperm;
+  std::vector<int32_t> hperm, hiperm, hlen;
+  std::vector<int64_t> hsrc;
+  RowOrder ord{nullptr, nullptr, nullptr};
   if (P->reorder) {
-    if (!rows_valid(rph, A->n, A->nnz, perr)) return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+    if (!rows_valid(rph, A->n, A->nnz, perr))
+      return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
     hperm.resize((size_t)A->n);
     hiperm.resize((size_t)A->n);
-    degree_order(rph, A->n, hperm.data(), hiperm.data());
+    hsrc.resize((size_t)A->n);
+    hlen.resize((size_t)A->n);
+    degree_order(rph, A->n, hperm.data(), hiperm.data(), hsrc.data(), hlen.data());
+    ord = RowOrder{hperm.data(), hsrc.data(), hlen.data()};
   }
-  const int32_t* hp = P->reorder ? hperm.data() : nullptr;
+  const RowOrder* hp = P->reorder ? &ord : nullptr;
   if (!make_sell(rph, A->n, A->nnz, sell, perr, SELL_WINDOW, SELL_VMAX, hp))
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
 
@@ -896,7 +926,11 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     const int32_t* dci = A->col_idx;
     const void* dval = A->values;
     char* tmp = nullptr;
-    if (A->where == TE_HOST) {
+    if (P->owned_csr) {
+      drp = P->rp;
+      dci = P->ci;
+      dval = P->val;
+    } else if (A->where == TE_HOST) {
       const size_t brp = al256(sizeof(int64_t) * (A->n + 1)), bci = al256(4 * (size_t)A->nnz);
       TE_CK(cudaMalloc(&tmp, brp + bci + in_elt * (size_t)A->nnz + 256), "allocate tuning CSR");
       TE_CK(cudaMemcpyAsync(tmp, A->row_ptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyHostToDevice,
@@ -970,6 +1004,8 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     for (cudaEvent_t* e : {&P->ev_ready[0], &P->ev_ready[1], &P->ev_free[0], &P->ev_free[1],
                            &P->ev_fork, &P->ev_join})
       TE_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "create event");
+  } else if (P->owned_csr) {
+    // copied at the start
   } else if (A->where == TE_HOST) {
     TE_CK(cudaMalloc(&P->owned_csr, csr_bytes), "allocate device CSR");
     char* b = static_cast<char*>(P->owned_csr);
@@ -1431,6 +1467,23 @@ te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t
     if (lane_src) lane_src[l] = sell.vsrc[l];
     if (lane_len) lane_len[l] = sell.vlen[l];
   }
+  return TE_OK;
+}
+
+te_status te_degree_order(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t* perm,
+                          int32_t* iperm) {
+  if (!row_ptr || !perm || n < 1 || n >= (int64_t)1 << 31 || nnz < 0)
+    return fail(TE_ERR_INVALID_ARG, "bad arguments");
+  std::string perr;
+  if (!rows_valid(row_ptr, n, nnz, perr)) return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+  std::vector<int32_t> inv, len;
+  std::vector<int64_t> src((size_t)n);
+  len.resize((size_t)n);
+  if (!iperm) {
+    inv.resize((size_t)n);
+    iperm = inv.data();
+  }
+  degree_order(row_ptr, n, perm, iperm, src.data(), len.data());
   return TE_OK;
 }
 

@@ -20,6 +20,7 @@
 // uses binary64 FMA.  Pieces of a cut row leave partial sums that a second
 // kernel adds in piece order (deterministic).
 #include <algorithm>
+#include <atomic>
 #include <thread>
 
 #include "te_common.cuh"
@@ -29,9 +30,9 @@ namespace te {
 
 // Windows of rows [w0, w1) into `out`, with entry offsets and cut-row piece
 // slots numbered from 0 (the caller shifts them).  Row r of the layout is CSR
-// row perm[r] (perm NULL: row r); it writes output r.
+// row ord->perm[r] (ord NULL: row r); it writes output r.
 static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, int window,
-                         int vmax, const int32_t* perm, SellHost& out) {
+                         int vmax, const RowOrder* ord, SellHost& out) {
   struct Piece {
     int64_t src;
     int32_t len, out, row;
@@ -42,11 +43,12 @@ static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, i
     const int64_t r0 = w * window, r1 = std::min<int64_t>(r0 + window, n);
     win.clear();
     for (int64_t r = r0; r < r1; ++r) {
-      const int64_t o = perm ? (int64_t)perm[r] : r;  // the CSR row
-      const int64_t L = rp[o + 1] - rp[o];
+      const int64_t o = ord ? (int64_t)ord->perm[r] : r;  // the CSR row
+      const int64_t first = ord ? ord->src[r] : rp[r];
+      const int64_t L = ord ? (int64_t)ord->len[r] : rp[r + 1] - rp[r];
       if (L == 0) continue;  // empty rows: never written by the kernel
       if (L <= vmax) {
-        win.push_back({rp[o], (int32_t)L, (int32_t)r, (int32_t)o});
+        win.push_back({first, (int32_t)L, (int32_t)r, (int32_t)o});
         continue;
       }
       LongRow lr;
@@ -55,8 +57,8 @@ static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, i
       lr.count = (int32_t)((L + vmax - 1) / vmax);
       lr.pad_ = 0;
       for (int32_t c = 0; c < lr.count; ++c) {
-        const int64_t s0 = rp[o] + (int64_t)c * vmax;
-        const int64_t l = std::min<int64_t>(vmax, rp[o + 1] - s0);
+        const int64_t s0 = first + (int64_t)c * vmax;
+        const int64_t l = std::min<int64_t>(vmax, first + L - s0);
         win.push_back({s0, (int32_t)l, -1 - (int32_t)(out.pieces + c), (int32_t)o});
       }
       out.pieces += lr.count;
@@ -99,11 +101,14 @@ static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, i
   }
 }
 
-// Threads take contiguous ranges of windows; the parts are joined with their
-// entry and piece offsets, so the result equals a sequential build.  The row
-// pointers are checked (all rows) before any window is built.
+// Threads take chunks of consecutive windows from a shared counter (the work
+// of a window grows with its rows' lengths, so a row order that puts the
+// longest rows first would leave one static range with most of it); the
+// chunks' parts are joined in chunk order with their entry and piece
+// offsets, so the result equals a sequential build.  The row pointers are
+// checked (all rows) before any window is built.
 bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err,
-               int window, int vmax, const int32_t* perm) {
+               int window, int vmax, const RowOrder* ord) {
   out = SellHost();
   if (rp[0] != 0) {
     err = "row_ptr[0] must be 0";
@@ -118,20 +123,38 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
   if (nt < 1) nt = 1;
   if (nt > 32) nt = 32;
   if ((int64_t)nt > W / 16) nt = (unsigned)std::max<int64_t>(1, W / 16);
+  const int64_t nc = nt == 1 ? 1 : std::min<int64_t>(W, (int64_t)nt * 16);  // chunks
   std::vector<int64_t> bad(nt, -1);
-  std::vector<SellHost> part(nt);
+  std::vector<SellHost> part((size_t)nc);
+  std::vector<int64_t> cw((size_t)nc + 1, 0);  // chunk c: windows [cw[c], cw[c+1])
+  std::atomic<int64_t> next{0};
   auto check = [&](unsigned t) {
-    const int64_t w0 = W * t / nt, w1 = W * (t + 1) / nt;
-    const int64_t r0 = w0 * window, r1 = std::min<int64_t>(w1 * window, n);
+    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
     for (int64_t r = r0; r < r1; ++r)
       if (rp[r + 1] < rp[r]) {
         bad[t] = r;
         return;
       }
   };
-  auto work = [&](unsigned t) {
+  auto work = [&](unsigned) {
+    for (int64_t c = next++; c < nc; c = next++)
+      sell_windows(rp, n, cw[(size_t)c], cw[(size_t)c + 1], window, vmax, ord, part[(size_t)c]);
+  };
+  // the work of a window ~ its pieces ~ rows + entries / vmax; chunks of
+  // equal work (a chunk holds at least one window)
+  std::vector<int64_t> wwork((size_t)W, 0);
+  auto weigh = [&](unsigned t) {
     const int64_t w0 = W * t / nt, w1 = W * (t + 1) / nt;
-    sell_windows(rp, n, w0, w1, window, vmax, perm, part[t]);
+    for (int64_t w = w0; w < w1; ++w) {
+      const int64_t r0 = w * window, r1 = std::min<int64_t>(r0 + window, n);
+      int64_t e = 0;
+      if (ord) {
+        for (int64_t r = r0; r < r1; ++r) e += ord->len[r];
+      } else {
+        e = rp[r1] - rp[r0];
+      }
+      wwork[(size_t)w] = (r1 - r0) + e / vmax;
+    }
   };
   auto run = [&](auto&& f) {
     if (nt == 1) {
@@ -148,6 +171,20 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
       err = "row_ptr must be non-decreasing (row " + std::to_string(bad[t]) + ")";
       return false;
     }
+  if (nc > 1) {
+    run(weigh);
+    int64_t total = 0;
+    for (int64_t w = 0; w < W; ++w) total += wwork[(size_t)w];
+    int64_t c = 1, acc = 0;
+    for (int64_t w = 0; w < W && c < nc; ++w) {
+      acc += wwork[(size_t)w];
+      // close chunk c-1 after window w once it holds its share of the work,
+      // leaving at least one window for each later chunk
+      while (c < nc && acc * nc >= total * c && W - (w + 1) >= nc - c) cw[(size_t)c++] = w + 1;
+    }
+    for (; c < nc; ++c) cw[(size_t)c] = W - (nc - c);
+  }
+  cw[(size_t)nc] = W;
   run(work);
   // join the parts
   size_t ns = 0, nl = 0, nr = 0;
@@ -162,45 +199,42 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
   out.vlen.resize(nl);
   out.vrow.resize(nl);
   std::vector<LongRow> lrows(nr);
-  std::vector<size_t> so(nt + 1, 0), lo(nt + 1, 0), ro(nt + 1, 0);
-  std::vector<int64_t> eo(nt + 1, 0), po(nt + 1, 0);
-  for (unsigned t = 0; t < nt; ++t) {
+  std::vector<size_t> so(nc + 1, 0), lo(nc + 1, 0), ro(nc + 1, 0);
+  std::vector<int64_t> eo(nc + 1, 0), po(nc + 1, 0);
+  for (int64_t t = 0; t < nc; ++t) {
     so[t + 1] = so[t] + part[t].slices.size();
     lo[t + 1] = lo[t] + part[t].vout.size();
     ro[t + 1] = ro[t] + part[t].lrows.size();
     eo[t + 1] = eo[t] + part[t].entries;
     po[t + 1] = po[t] + part[t].pieces;
   }
-  auto join = [&](unsigned t) {
-    const SellHost& p = part[t];
-    for (size_t i = 0; i < p.slices.size(); ++i) {
-      SellSlice sl = p.slices[i];
-      sl.base += eo[t];
-      out.slices[so[t] + i] = sl;
-    }
-    for (size_t i = 0; i < p.vout.size(); ++i) {
-      int32_t v = p.vout[i];
-      if (v < 0 && v != SELL_SKIP) v = -1 - (int32_t)(po[t] + (-1 - (int64_t)v));
-      out.vout[lo[t] + i] = v;
-      out.vsrc[lo[t] + i] = p.vsrc[i];
-      out.vlen[lo[t] + i] = p.vlen[i];
-      out.vrow[lo[t] + i] = p.vrow[i];
-    }
-    for (size_t i = 0; i < p.lrows.size(); ++i) {
-      LongRow lr = p.lrows[i];
-      lr.first += (int32_t)po[t];
-      lrows[ro[t] + i] = lr;
+  next = 0;
+  auto join = [&](unsigned) {
+    for (int64_t t = next++; t < nc; t = next++) {
+      const SellHost& p = part[(size_t)t];
+      for (size_t i = 0; i < p.slices.size(); ++i) {
+        SellSlice sl = p.slices[i];
+        sl.base += eo[t];
+        out.slices[so[t] + i] = sl;
+      }
+      for (size_t i = 0; i < p.vout.size(); ++i) {
+        int32_t v = p.vout[i];
+        if (v < 0 && v != SELL_SKIP) v = -1 - (int32_t)(po[t] + (-1 - (int64_t)v));
+        out.vout[lo[t] + i] = v;
+        out.vsrc[lo[t] + i] = p.vsrc[i];
+        out.vlen[lo[t] + i] = p.vlen[i];
+        out.vrow[lo[t] + i] = p.vrow[i];
+      }
+      for (size_t i = 0; i < p.lrows.size(); ++i) {
+        LongRow lr = p.lrows[i];
+        lr.first += (int32_t)po[t];
+        lrows[ro[t] + i] = lr;
+      }
     }
   };
-  if (nt == 1) {
-    join(0);
-  } else {
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t) th.emplace_back(join, t);
-    for (auto& x : th) x.join();
-  }
-  out.entries = eo[nt];
-  out.pieces = po[nt];
+  run(join);
+  out.entries = eo[nc];
+  out.pieces = po[nc];
   // cut rows with the most pieces first (their finalising lanes run longest):
   // a stable counting sort by piece count
   int32_t maxc = 0;
@@ -221,6 +255,26 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
   return true;
 }
 
+// Host threads for a pass over n rows (at least ~64K rows each).
+static unsigned row_threads(int64_t n) {
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > 32) nt = 32;
+  const int64_t cap = n / 65536;
+  if ((int64_t)nt > cap) nt = (unsigned)std::max<int64_t>(1, cap);
+  return nt;
+}
+template <typename F>
+static void run_threads(unsigned nt, F&& f) {
+  if (nt == 1) {
+    f(0u);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) th.emplace_back(f, t);
+  for (auto& x : th) x.join();
+}
+
 bool rows_valid(const int64_t* rp, int64_t n, int64_t nnz, std::string& err) {
   if (rp[0] != 0) {
     err = "row_ptr[0] must be 0";
@@ -230,35 +284,72 @@ bool rows_valid(const int64_t* rp, int64_t n, int64_t nnz, std::string& err) {
     err = "row_ptr[n] != nnz";
     return false;
   }
-  for (int64_t r = 0; r < n; ++r)
-    if (rp[r + 1] < rp[r]) {
-      err = "row_ptr must be non-decreasing (row " + std::to_string(r) + ")";
+  const unsigned nt = row_threads(n);
+  std::vector<int64_t> bad(nt, -1);
+  run_threads(nt, [&](unsigned t) {
+    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
+    for (int64_t r = r0; r < r1; ++r)
+      if (rp[r + 1] < rp[r]) {
+        bad[t] = r;
+        return;
+      }
+  });
+  for (int64_t b : bad)
+    if (b >= 0) {
+      err = "row_ptr must be non-decreasing (row " + std::to_string(b) + ")";
       return false;
     }
   return true;
 }
 
 // Rows by length, longest first, ties in row order (a stable counting sort
-// over the row lengths): perm[r] = the row placed at r, iperm its inverse.
+// over the row lengths): perm[r] = the row placed at r, iperm its inverse;
+// src[r] and len[r] = the first CSR entry and the length of that row, so that
+// the layout reads them in order.  Threads take contiguous row ranges, each
+// with its own histogram; the offsets of (length, range) follow lengths
+// descending, then ranges in order, so the result equals the sequential sort.
 // Sparse graphs whose degrees follow a power law then keep their
 // high-degree vertices together, so that the SpMV's reads of x for those
 // columns share cache lines.  The row pointers must be valid.
-void degree_order(const int64_t* rp, int64_t n, int32_t* perm, int32_t* iperm) {
-  int64_t maxl = 0;
-  for (int64_t r = 0; r < n; ++r) maxl = std::max<int64_t>(maxl, rp[r + 1] - rp[r]);
-  std::vector<int64_t> pos((size_t)maxl + 2, 0);
-  for (int64_t r = 0; r < n; ++r) ++pos[(size_t)(rp[r + 1] - rp[r])];
+void degree_order(const int64_t* rp, int64_t n, int32_t* perm, int32_t* iperm, int64_t* src,
+                  int32_t* len) {
+  unsigned nt = row_threads(n);
+  std::vector<int64_t> maxl(nt, 0);
+  run_threads(nt, [&](unsigned t) {
+    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
+    int64_t m = 0;
+    for (int64_t r = r0; r < r1; ++r) m = std::max<int64_t>(m, rp[r + 1] - rp[r]);
+    maxl[t] = m;
+  });
+  const int64_t L = *std::max_element(maxl.begin(), maxl.end()) + 1;
+  // the histograms hold nt * L counts: fewer threads when rows are very long
+  while (nt > 1 && (int64_t)nt * L > std::max<int64_t>(n, (int64_t)1 << 22)) --nt;
+  std::vector<int64_t> cnt((size_t)nt * L, 0);  // [thread][length]
+  run_threads(nt, [&](unsigned t) {
+    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
+    int64_t* c = cnt.data() + (size_t)t * L;
+    for (int64_t r = r0; r < r1; ++r) ++c[rp[r + 1] - rp[r]];
+  });
   int64_t acc = 0;
-  for (int64_t L = maxl; L >= 0; --L) {
-    const int64_t c = pos[(size_t)L];
-    pos[(size_t)L] = acc;
-    acc += c;
-  }
-  for (int64_t r = 0; r < n; ++r) {
-    const int64_t at = pos[(size_t)(rp[r + 1] - rp[r])]++;
-    perm[at] = (int32_t)r;
-    iperm[r] = (int32_t)at;
-  }
+  for (int64_t l = L - 1; l >= 0; --l)
+    for (unsigned t = 0; t < nt; ++t) {
+      int64_t& c = cnt[(size_t)t * L + l];
+      const int64_t k = c;
+      c = acc;
+      acc += k;
+    }
+  run_threads(nt, [&](unsigned t) {
+    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
+    int64_t* c = cnt.data() + (size_t)t * L;
+    for (int64_t r = r0; r < r1; ++r) {
+      const int64_t l = rp[r + 1] - rp[r];
+      const int64_t at = c[l]++;
+      perm[at] = (int32_t)r;
+      iperm[r] = (int32_t)at;
+      src[at] = rp[r];
+      len[at] = (int32_t)l;
+    }
+  });
 }
 
 // Host build of the SELL arrays (for a matrix that stays in host memory and

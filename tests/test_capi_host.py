@@ -104,6 +104,7 @@ def test_option_validation_before_gpu(te):
     assert call(A, refine=1) == 1 and b"binary64" in lib.te_last_error()
     assert call(A, reorth=3) == 1
     assert call(A, refine=3) == 1
+    assert call(A, order=2) == 1 and b"order" in lib.te_last_error()
     A.values_f64 = 2
     assert call(A) == 1
     A.values_f64 = 1
@@ -238,6 +239,27 @@ def test_layout_rejects_malformed_row_ptr(te):
         te.spmv_layout(np.array([1, 3, 4]), 4)
     with pytest.raises(te.TEError):
         te.spmv_layout(np.array([0, 3, 4]), 5)
+
+
+def test_degree_order_is_the_stable_sort_by_length(te):
+    """Against numpy's stable argsort on minus the row lengths; the large
+    R-MAT case spreads the histograms over several host threads, the star
+    case has one row as long as the matrix."""
+    n = 20000
+    lens = np.zeros(n, dtype=np.int64)
+    lens[::7] = 3
+    lens[5] = n - 1
+    lens[11::13] = 64
+    star = np.concatenate([[0], np.cumsum(lens)])
+    for rp in (synth.rmat_sym(20, 4, 1).row_ptr, synth.uniform_sym(3000, 6, 3).row_ptr, star,
+               np.array([0, 0, 0]), np.array([0, 5])):
+        perm, iperm = te.degree_order(rp, int(rp[-1]))
+        ref = np.argsort(-np.diff(rp), kind="stable")
+        assert np.array_equal(perm, ref)
+        assert np.array_equal(iperm[perm], np.arange(len(rp) - 1))
+    with pytest.raises(te.TEError) as e:
+        te.degree_order(np.array([0, 3, 2, 5]), 5)
+    assert e.value.status == 1
 
 
 def test_product_path_has_no_cpu_fallback():
