@@ -122,40 +122,41 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
   unsigned nt = std::thread::hardware_concurrency();
   if (nt < 1) nt = 1;
   if (nt > 32) nt = 32;
-  if ((int64_t)nt > W / 16) nt = (unsigned)std::max<int64_t>(1, W / 16);
+  // small layouts (a serving request) are built by the calling thread alone
+  if ((int64_t)nt > W / 64) nt = (unsigned)std::max<int64_t>(1, W / 64);
   const int64_t nc = nt == 1 ? 1 : std::min<int64_t>(W, (int64_t)nt * 16);  // chunks
   std::vector<int64_t> bad(nt, -1);
   std::vector<SellHost> part((size_t)nc);
   std::vector<int64_t> cw((size_t)nc + 1, 0);  // chunk c: windows [cw[c], cw[c+1])
   std::atomic<int64_t> next{0};
+  // the row pointers (all rows) and, for several chunks, the work of each
+  // window in one pass
+  std::vector<int64_t> wwork(nc > 1 ? (size_t)W : 0, 0);
   auto check = [&](unsigned t) {
-    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
-    for (int64_t r = r0; r < r1; ++r)
-      if (rp[r + 1] < rp[r]) {
-        bad[t] = r;
-        return;
+    const int64_t w0 = W * t / nt, w1 = W * (t + 1) / nt;
+    for (int64_t w = w0; w < w1; ++w) {
+      const int64_t r0 = w * window, r1 = std::min<int64_t>(r0 + window, n);
+      for (int64_t r = r0; r < r1; ++r)
+        if (rp[r + 1] < rp[r]) {
+          bad[t] = r;
+          return;
+        }
+      if (nc > 1) {  // the work of a window ~ its pieces ~ rows + entries / vmax
+        int64_t e = 0;
+        if (ord) {
+          for (int64_t r = r0; r < r1; ++r) e += ord->len[r];
+        } else {
+          e = rp[r1] - rp[r0];
+        }
+        wwork[(size_t)w] = (r1 - r0) + e / vmax;
       }
+    }
   };
   auto work = [&](unsigned) {
     for (int64_t c = next++; c < nc; c = next++)
       sell_windows(rp, n, cw[(size_t)c], cw[(size_t)c + 1], window, vmax, ord, part[(size_t)c]);
   };
-  // the work of a window ~ its pieces ~ rows + entries / vmax; chunks of
-  // equal work (a chunk holds at least one window)
-  std::vector<int64_t> wwork((size_t)W, 0);
-  auto weigh = [&](unsigned t) {
-    const int64_t w0 = W * t / nt, w1 = W * (t + 1) / nt;
-    for (int64_t w = w0; w < w1; ++w) {
-      const int64_t r0 = w * window, r1 = std::min<int64_t>(r0 + window, n);
-      int64_t e = 0;
-      if (ord) {
-        for (int64_t r = r0; r < r1; ++r) e += ord->len[r];
-      } else {
-        e = rp[r1] - rp[r0];
-      }
-      wwork[(size_t)w] = (r1 - r0) + e / vmax;
-    }
-  };
+
   auto run = [&](auto&& f) {
     if (nt == 1) {
       f(0u);
@@ -171,8 +172,7 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
       err = "row_ptr must be non-decreasing (row " + std::to_string(bad[t]) + ")";
       return false;
     }
-  if (nc > 1) {
-    run(weigh);
+  if (nc > 1) {  // chunks of equal work (a chunk holds at least one window)
     int64_t total = 0;
     for (int64_t w = 0; w < W; ++w) total += wwork[(size_t)w];
     int64_t c = 1, acc = 0;
