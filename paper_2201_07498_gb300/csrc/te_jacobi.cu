@@ -8,7 +8,8 @@
 // before the Ritz contraction.  One CTA holds T and the eigenvector matrix Y in
 // shared memory and applies cyclic Jacobi with the parallel (round-robin,
 // "circle method") ordering of Brent & Luk: every round rotates m/2 disjoint
-// index pairs at once, T <- J^T T J, Y <- Y J.  Rotation angle (textbook
+// index pairs at once, T <- J^T T J (on 2x2 blocks of the upper triangle,
+// mirrored), Y <- Y J.  Rotation angle (textbook
 // form, e.g. Golub & Van Loan Sec. 8.5): zeta = (t_qq - t_pp) / (2 t_pq),
 // t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = t c;
 // a pair is rotated when |t_pq| > 1e-16 ||T||_F and the sweeps stop after
@@ -108,38 +109,61 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
         }
       }
       __syncthreads();
-      // rows p, q  <-  J^T T
-      for (int e = tid; e < half * mm; e += JAC_THREADS) {
-        const int k = e / mm, col = e % mm;
-        if (!rot[k]) continue;
-        const int p = rp_[k], q = rq_[k];
-        const double c = rc[k], s = rs[k];
-        const double g = T[p * JLD + col], h = T[q * JLD + col];
-        T[p * JLD + col] = c * g - s * h;
-        T[q * JLD + col] = s * g + c * h;
-      }
-      __syncthreads();
-      // columns p, q  <-  T J, and Y <- Y J
-      for (int e = tid; e < half * mm; e += JAC_THREADS) {
-        const int k = e / mm, row = e % mm;
-        if (!rot[k]) continue;
-        const int p = rp_[k], q = rq_[k];
-        const double c = rc[k], s = rs[k];
-        const double g = T[row * JLD + p], h = T[row * JLD + q];
-        T[row * JLD + p] = c * g - s * h;
-        T[row * JLD + q] = s * g + c * h;
-        const double gy = Y[row * JLD + p], hy = Y[row * JLD + q];
-        Y[row * JLD + p] = c * gy - s * hy;
-        Y[row * JLD + q] = s * gy + c * hy;
-      }
-      __syncthreads();
-      // the 2x2 block of each pair: exact post-rotation values
-      if (tid < half && rot[tid]) {
-        const int p = rp_[tid], q = rq_[tid];
-        T[p * JLD + p] = d_pp[tid] - rt[tid] * d_pq[tid];
-        T[q * JLD + q] = d_qq[tid] + rt[tid] * d_pq[tid];
-        T[p * JLD + q] = 0.0;
-        T[q * JLD + p] = 0.0;
+      // T <- J^T T J on 2x2 blocks: block (a, b) of pairs a <= b is
+      // J_a^T T[{p_a,q_a},{p_b,q_b}] J_b, written with its mirror image (T
+      // stays exactly symmetric); a rotated pair's own block takes the exact
+      // post-rotation values.  Y <- Y J in the same phase.
+      const int nblk = half * (half + 1) / 2;
+      for (int e = tid; e < nblk + half * mm; e += JAC_THREADS) {
+        if (e < nblk) {
+          int a = 0, rem = e;  // e -> (a, b), a <= b, row-major upper triangle
+          while (rem >= half - a) {
+            rem -= half - a;
+            ++a;
+          }
+          const int b = a + rem;
+          const int pa = rp_[a], qa = rq_[a], pb = rp_[b], qb = rq_[b];
+          if (a == b) {
+            if (rot[a]) {
+              T[pa * JLD + pa] = d_pp[a] - rt[a] * d_pq[a];
+              T[qa * JLD + qa] = d_qq[a] + rt[a] * d_pq[a];
+              T[pa * JLD + qa] = 0.0;
+              T[qa * JLD + pa] = 0.0;
+            }
+            continue;
+          }
+          if (!rot[a] && !rot[b]) continue;
+          double x00 = T[pa * JLD + pb], x01 = T[pa * JLD + qb];
+          double x10 = T[qa * JLD + pb], x11 = T[qa * JLD + qb];
+          if (rot[a]) {  // rows: J_a^T
+            const double c = rc[a], sn = rs[a];
+            const double y00 = c * x00 - sn * x10, y01 = c * x01 - sn * x11;
+            const double y10 = sn * x00 + c * x10, y11 = sn * x01 + c * x11;
+            x00 = y00; x01 = y01; x10 = y10; x11 = y11;
+          }
+          if (rot[b]) {  // columns: J_b
+            const double c = rc[b], sn = rs[b];
+            const double y00 = c * x00 - sn * x01, y01 = sn * x00 + c * x01;
+            const double y10 = c * x10 - sn * x11, y11 = sn * x10 + c * x11;
+            x00 = y00; x01 = y01; x10 = y10; x11 = y11;
+          }
+          T[pa * JLD + pb] = x00;
+          T[pa * JLD + qb] = x01;
+          T[qa * JLD + pb] = x10;
+          T[qa * JLD + qb] = x11;
+          T[pb * JLD + pa] = x00;
+          T[qb * JLD + pa] = x01;
+          T[pb * JLD + qa] = x10;
+          T[qb * JLD + qa] = x11;
+        } else {
+          const int f = e - nblk, k = f / mm, row = f % mm;
+          if (!rot[k]) continue;
+          const int p = rp_[k], q = rq_[k];
+          const double c = rc[k], sn = rs[k];
+          const double gy = Y[row * JLD + p], hy = Y[row * JLD + q];
+          Y[row * JLD + p] = c * gy - sn * hy;
+          Y[row * JLD + q] = sn * gy + c * hy;
+        }
       }
       __syncthreads();
     }
