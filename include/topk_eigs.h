@@ -23,8 +23,9 @@
  *     device.  "Host" outputs may be pageable or pinned.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
  *     return results to the host synchronise that stream once, at the end.
- *   - Matrices are square (n x n), symmetric (Lanczos requires it; symmetry
- *     is not checked), stored as CSR with int64 row pointers (n+1 entries,
+ *   - Matrices are square (n x n), symmetric (Lanczos requires it; the solver
+ *     does not check it, te_check_symmetric does), stored as CSR with int64
+ *     row pointers (n+1 entries,
  *     row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz) and int32 column
  *     indices in [0, n).  Column order within a row is free.
  *   - Dense results are column-major: eigenvector k occupies
@@ -390,6 +391,14 @@ te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t
                          int32_t vmax, int64_t* nslices, int64_t* entries, int64_t* nlong_rows,
                          int32_t* slice_len, int32_t* lane_out, int64_t* lane_src,
                          int32_t* lane_len);
+
+/* Debug check of the symmetry Lanczos assumes (host only, no GPU needed; the
+ * solver itself does not check it): A must be TE_HOST with binary64 values
+ * (values_f64 = 1).  Duplicate entries of a row are summed and a missing
+ * mirror entry counts as zero.  *max_abs_diff (may be NULL) receives
+ * max |a_ij - a_ji|; returns TE_OK when that is <= tol, TE_ERR_INVALID_ARG
+ * (with the value in te_last_error) otherwise or for a malformed CSR. */
+te_status te_check_symmetric(const te_csr* A, double tol, double* max_abs_diff);
 
 /* The row order of TE_ORDER_DEGREE (host only, no GPU needed): rows by
  * length, longest first, rows of equal length in increasing index order.

@@ -123,6 +123,7 @@ _SIGS = {
                                       ctypes.c_void_p]),
     "te_degree_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "te_check_symmetric": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -512,6 +513,16 @@ def spmv_layout(row_ptr, nnz: int, window: int = 0, vmax: int = 0):
     _check(rc)
     return {"slice_len": slen, "lane_out": lout, "lane_src": lsrc, "lane_len": llen,
             "entries": int(ne.value), "long_rows": int(nl.value)}
+
+
+def check_symmetric(host_csr, tol: float = 0.0):
+    """max |a_ij - a_ji| of a host matrix (an object with n, row_ptr, col, val);
+    raises TEError when it exceeds tol."""
+    csr = CSR.from_host(host_csr, "ddd", device="cpu", values_f64=True)
+    diff = ctypes.c_double()
+    _check(load_library().te_check_symmetric(ctypes.byref(csr.to_ctypes()), tol,
+                                             ctypes.byref(diff)))
+    return diff.value
 
 
 def degree_order(row_ptr, nnz: int):

@@ -1470,6 +1470,72 @@ te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t
   return TE_OK;
 }
 
+te_status te_check_symmetric(const te_csr* A, double tol, double* max_abs_diff) {
+  if (!A || !A->row_ptr || A->n < 1 || A->nnz < 0 || (A->nnz > 0 && (!A->col_idx || !A->values)))
+    return fail(TE_ERR_INVALID_ARG, "bad arguments");
+  if (A->where != TE_HOST) return fail(TE_ERR_INVALID_ARG, "the check reads a TE_HOST matrix");
+  if (!A->values_f64) return fail(TE_ERR_INVALID_ARG, "the check reads binary64 values (values_f64 = 1)");
+  if (!(tol >= 0.0)) return fail(TE_ERR_INVALID_ARG, "tol must be >= 0");
+  const int64_t n = A->n, nnz = A->nnz;
+  const int64_t* rp = A->row_ptr;
+  const int32_t* ci = A->col_idx;
+  const double* va = static_cast<const double*>(A->values);
+  std::string perr;
+  if (!rows_valid(rp, n, nnz, perr)) return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+  for (int64_t k = 0; k < nnz; ++k)
+    if (ci[k] < 0 || (int64_t)ci[k] >= n)
+      return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
+  // the transpose by a counting sort over the columns
+  std::vector<int64_t> tp((size_t)n + 1, 0);
+  for (int64_t k = 0; k < nnz; ++k) ++tp[(size_t)ci[k] + 1];
+  for (int64_t r = 0; r < n; ++r) tp[(size_t)r + 1] += tp[(size_t)r];
+  std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+  std::vector<int32_t> tc((size_t)nnz);
+  std::vector<double> tv((size_t)nnz);
+  for (int64_t r = 0; r < n; ++r)
+    for (int64_t k = rp[r]; k < rp[r + 1]; ++k) {
+      const int64_t at = fill[(size_t)ci[k]]++;
+      tc[(size_t)at] = (int32_t)r;
+      tv[(size_t)at] = va[k];
+    }
+  // row r of M against row r of M^T, both sorted by column, duplicates summed
+  double worst = 0.0;
+  std::vector<std::pair<int32_t, double>> a, b;
+  auto merged = [](std::vector<std::pair<int32_t, double>>& v) {
+    std::sort(v.begin(), v.end(),
+              [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+                return x.first < y.first;
+              });
+    size_t o = 0;
+    for (size_t i = 0; i < v.size(); ++i) {
+      if (o > 0 && v[o - 1].first == v[i].first) v[o - 1].second += v[i].second;
+      else v[o++] = v[i];
+    }
+    v.resize(o);
+  };
+  for (int64_t r = 0; r < n; ++r) {
+    a.clear();
+    b.clear();
+    for (int64_t k = rp[r]; k < rp[r + 1]; ++k) a.emplace_back(ci[k], va[k]);
+    for (int64_t k = tp[(size_t)r]; k < tp[(size_t)r + 1]; ++k) b.emplace_back(tc[(size_t)k], tv[(size_t)k]);
+    merged(a);
+    merged(b);
+    size_t i = 0, j = 0;
+    while (i < a.size() || j < b.size()) {  // a missing mirror entry counts as zero
+      double d;
+      if (j == b.size() || (i < a.size() && a[i].first < b[j].first)) d = a[i++].second;
+      else if (i == a.size() || b[j].first < a[i].first) d = b[j++].second;
+      else d = a[i++].second - b[j++].second;
+      worst = std::max(worst, std::fabs(d));
+    }
+  }
+  if (max_abs_diff) *max_abs_diff = worst;
+  if (worst > tol)
+    return fail(TE_ERR_INVALID_ARG, "the matrix is not symmetric: max |a_ij - a_ji| = " +
+                                        std::to_string(worst));
+  return TE_OK;
+}
+
 te_status te_degree_order(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t* perm,
                           int32_t* iperm) {
   if (!row_ptr || !perm || n < 1 || n >= (int64_t)1 << 31 || nnz < 0)

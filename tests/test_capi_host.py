@@ -263,6 +263,26 @@ def test_degree_order_is_the_stable_sort_by_length(te):
     assert e.value.status == 1
 
 
+def test_symmetry_check(te):
+    for A in (synth.uniform_sym(2000, 5, 1), synth.rmat_sym(12, 8, 2), synth.path_laplacian(30)):
+        assert te.check_symmetric(A) == 0.0
+    A = synth.uniform_sym(500, 4, 3)
+    B = synth.CSR(A.n, A.row_ptr, A.col.copy(), A.val.copy())
+    k = int(B.row_ptr[7])  # entry (7, c): its mirror (c, 7) keeps the old value
+    B.val[k] += 0.25
+    with pytest.raises(te.TEError) as e:
+        te.check_symmetric(B)
+    assert e.value.status == 1 and "0.25" in str(e.value)
+    assert te.check_symmetric(B, tol=0.3) == pytest.approx(0.25)
+    # a missing mirror entry counts as zero; duplicates within a row are summed
+    C = synth.from_triplets(3, [0, 1, 1], [1, 0, 2], [2.0, 2.0, 5.0])
+    with pytest.raises(te.TEError):
+        te.check_symmetric(C)
+    D = synth.CSR(2, np.array([0, 2, 3]), np.array([1, 1, 0], dtype=np.int32),
+                  np.array([1.0, 2.0, 3.0]))
+    assert te.check_symmetric(D) == 0.0
+
+
 def test_product_path_has_no_cpu_fallback():
     """The product package must not import the oracle or the generators."""
     pkg = os.path.join(ROOT, "paper_2201_07498_gb300")
