@@ -325,6 +325,24 @@ def test_topk_fdf_close_to_oracle(te, name, make, K, m, which):
     assert np.max(ang) <= 1e-3, ang
 
 
+@pytest.mark.parametrize("reorth", ["full", "delayed", "none"])
+def test_captured_restarts_equal_uncaptured(te, reorth):
+    """The cycle Laplacian breaks down several times in 40 steps: the restart
+    passes (captured in the plan's graph, or launched one by one) do the work
+    after each breakdown and return at once otherwise.  Same kernels, same
+    order: bit-identical results."""
+    A = synth.cycle_laplacian(64)
+    assert oracle.lanczos(A, synth.start_vector(A.n, 7), 40, seed=7).restarts > 0
+    csr = te.CSR.from_host(A, "ddd")
+    p_g = te.Plan(csr, 8, 40, "ddd", seed=7, reorth=reorth)
+    p_d = te.Plan(csr, 8, 40, "ddd", seed=7, reorth=reorth, use_graph=False)
+    ev_g, U_g, r_g = p_g.solve(residuals=True)
+    ev_d, U_d, r_d = p_d.solve(residuals=True)
+    assert torch.equal(ev_g, ev_d) and torch.equal(U_g, U_d) and torch.equal(r_g, r_d)
+    ev_g2, _, _ = p_g.solve()
+    assert torch.equal(ev_g, ev_g2)
+
+
 @pytest.mark.parametrize("prec", ["ddd", "fdf"])
 def test_plan_graph_replay_is_deterministic(te, prec):
     A = synth.rmat_sym(12, 8, 1)
