@@ -30,7 +30,10 @@
  *     indices in [0, n).  Column order within a row is free.
  *   - Dense results are column-major: eigenvector k occupies
  *     eigvecs[k*n .. k*n+n-1].
- *   - On any error the outputs are left untouched.
+ *   - On an error found before the device work starts (arguments, CSR,
+ *     allocation) the outputs are left untouched; after a device-side failure
+ *     (TE_ERR_TIMEOUT, TE_ERR_NOT_CONVERGED) eigenvector buffers the kernels
+ *     write directly (device or pinned host) may hold partial results.
  */
 #ifndef TOPK_EIGS_H
 #define TOPK_EIGS_H
@@ -168,7 +171,10 @@ size_t te_workspace_bytes(const te_csr* A, int32_t K, int32_t krylov_steps, te_p
  *   krylov_steps m, the Lanczos steps (size of T), K <= m <= min(n, 64)
  *   eigvals      K doubles, host or device: the selected Ritz values
  *   eigvecs      n*K doubles (column-major), host or device, or NULL to skip
- *                the Ritz-vector contraction
+ *                the Ritz-vector contraction.  Device memory and pinned host
+ *                memory the device can address (cudaHostAlloc, or registered)
+ *                are written by the kernels directly; pageable host memory
+ *                is filled from a device copy at the end
  *   residuals    K doubles, host or device, or NULL: the Ritz residual
  *                estimates |beta_{m+1} * y_k[m]| (= ||M u_k - theta_k u_k|| in
  *                exact arithmetic), or with opt->refine the true residuals

@@ -72,6 +72,19 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Pinned host memory the device can address (cudaHostAlloc'd or registered):
+// the device-side pointer, else NULL.  Kernels then write results straight
+// into it (over NVLink-C2C on Grace-Blackwell) with no device staging copy.
+void* mapped_host_ptr(void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 struct Work {
   // byte offsets inside one allocation
   size_t V = 0, ytil = 0, xcur = 0, perm = 0, iperm = 0, w = 0, partials = 0, st = 0, Uint = 0, slices = 0, vout = 0,
@@ -1189,8 +1202,11 @@ te_status te_plan_solve(te_plan* P, const double* v1, double* eigvals, double* e
   double* U = eigvecs;
   double* Utmp = nullptr;
   if (eigvecs && !is_device_ptr(eigvecs)) {
-    TE_CK(cudaMalloc(&Utmp, sizeof(double) * (size_t)P->n * P->K), "allocate eigvecs staging");
-    U = Utmp;
+    U = static_cast<double*>(mapped_host_ptr(eigvecs));
+    if (!U) {  // pageable host memory: stage on the device, copy at the end
+      TE_CK(cudaMalloc(&Utmp, sizeof(double) * (size_t)P->n * P->K), "allocate eigvecs staging");
+      U = Utmp;
+    }
   }
   te_status r = te_plan_launch(P, v1, nullptr, U, stream);
   if (r != TE_OK) {

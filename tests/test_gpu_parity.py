@@ -325,6 +325,26 @@ def test_topk_fdf_close_to_oracle(te, name, make, K, m, which):
     assert np.max(ang) <= 1e-3, ang
 
 
+@pytest.mark.parametrize("order", ["keep", "degree"])
+def test_host_outputs_pinned_and_pageable(te, order):
+    """Ritz vectors into device memory, into pinned host memory (written by the
+    kernels directly) and into pageable host memory (staged): the same bits."""
+    A = synth.rmat_sym(13, 8, 3)
+    K, m = 6, 20
+    csr = te.CSR.from_host(A, "fdf")
+    ev_d, U_d, _ = te.topk_eigs(csr, K, m, "fdf", seed=2, order=order)
+    outs = []
+    for pin in (True, False):
+        ev = torch.empty(K, dtype=torch.float64)
+        U = torch.empty((K, A.n), dtype=torch.float64)
+        if pin:
+            ev, U = ev.pin_memory(), U.pin_memory()
+        te.topk_eigs(csr, K, m, "fdf", seed=2, order=order, out=(ev, U))
+        outs.append((ev, U))
+    for ev, U in outs:
+        assert torch.equal(ev, ev_d) and torch.equal(U, U_d.t().cpu())
+
+
 @pytest.mark.parametrize("reorth", ["full", "delayed", "none"])
 def test_captured_restarts_equal_uncaptured(te, reorth):
     """The cycle Laplacian breaks down several times in 40 steps: the restart
