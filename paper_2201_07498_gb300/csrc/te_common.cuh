@@ -216,6 +216,38 @@ TE_DEV double ld_keep_f64(const double* a, uint64_t pol) {
   asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
   return v;
 }
+// a gather issued only where `on` is set (predicated: a warp's gathers stay in
+// flight together), allocating in L1 or not; 0 elsewhere
+template <bool ALLOC>
+TE_DEV float ld_keep_f32_if(const float* a, bool on, uint64_t pol) {
+  float v = 0.f;
+  if constexpr (ALLOC)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %2, 0;\n"
+        " @p ld.global.nc.L2::cache_hint.f32 %0, [%1], %3;\n}"
+        : "+f"(v) : "l"(a), "r"((unsigned)on), "l"(pol));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %2, 0;\n"
+        " @p ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %3;\n}"
+        : "+f"(v) : "l"(a), "r"((unsigned)on), "l"(pol));
+  return v;
+}
+template <bool ALLOC>
+TE_DEV double ld_keep_f64_if(const double* a, bool on, uint64_t pol) {
+  double v = 0.0;
+  if constexpr (ALLOC)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %2, 0;\n"
+        " @p ld.global.nc.L2::cache_hint.f64 %0, [%1], %3;\n}"
+        : "+d"(v) : "l"(a), "r"((unsigned)on), "l"(pol));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %2, 0;\n"
+        " @p ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %3;\n}"
+        : "+d"(v) : "l"(a), "r"((unsigned)on), "l"(pol));
+  return v;
+}
 TE_DEV int ld_stream_i32(const int32_t* a, uint64_t pol) {
   int v;
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;"

@@ -120,6 +120,7 @@ struct DevSell {
   const LongRow* lrows = nullptr;
   int nslices = 0, nlrows = 0;
   int nlbig = 0;  // lrows[0, nlbig) have more than SELL_BIG_PIECES pieces
+  int64_t hot = 0;  // rows by degree: gathers of x[c >= min(hot, what L1 holds)] skip L1
 };
 
 // fill cols/vals of the SELL layout from the CSR (one thread per lane)

@@ -1080,6 +1080,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   P->sell.nlbig = (int)sell.nbig;
   void* vals64 = P->W.svals64 ? at(P, P->W.svals64) : nullptr;
   P->sell.vk = P->vk;
+  P->sell.hot = P->reorder ? P->n : 0;  // the first columns are the most connected
   P->sell.lscale = P->W.lscale ? static_cast<const float*>(at(P, P->W.lscale)) : nullptr;
   if (P->streaming)
     TE_CK(upload_meta(sell, P->sell, s), "upload the SELL layout");

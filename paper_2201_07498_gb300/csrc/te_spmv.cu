@@ -519,9 +519,13 @@ struct SpmvArgs {
   void* y;
   void* vpart;
   int nslices;
+  int hot;  // gathers of x[c], c >= hot, skip L1 allocation (0: all allocate)
 };
 
 constexpr int SPMV_WPB = 8;     // warps (slices) per CTA
+// with rows relabelled by degree, the first HOT_BYTES of x (the most
+// connected columns) are the ones L1 keeps
+constexpr int64_t HOT_BYTES = 128 << 10;
 constexpr int SPMV_UNROLL = 8;  // entries per lane in flight
 
 // stored matrix value type per te_dtype, and its streaming load + exact
@@ -597,8 +601,16 @@ __device__ __forceinline__ void spmv_slice(const SpmvArgs& a, const int slice, c
     x_t xv[SPMV_UNROLL];
 #pragma unroll
     for (int u = 0; u < SPMV_UNROLL; ++u) {  // padding reads x[0]
-      if constexpr (sizeof(x_t) == 4) xv[u] = ld_keep_f32(x + c[u], keep);
-      else xv[u] = ld_keep_f64(x + c[u], keep);
+      if (a.hot > 0) {  // uniform: cold columns leave L1 to the hot ones
+        const bool h = c[u] < a.hot;
+        if constexpr (sizeof(x_t) == 4)
+          xv[u] = ld_keep_f32_if<true>(x + c[u], h, keep) + ld_keep_f32_if<false>(x + c[u], !h, keep);
+        else
+          xv[u] = ld_keep_f64_if<true>(x + c[u], h, keep) + ld_keep_f64_if<false>(x + c[u], !h, keep);
+      } else {
+        if constexpr (sizeof(x_t) == 4) xv[u] = ld_keep_f32(x + c[u], keep);
+        else xv[u] = ld_keep_f64(x + c[u], keep);
+      }
     }
 #pragma unroll
     for (int u = 0; u < SPMV_UNROLL; u += 2) {
@@ -713,6 +725,7 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) batch_spmv_kernel(const BatchTa
     a.y = B.ytil;
     a.vpart = B.vpart;
     a.nslices = B.nslices;
+    a.hot = 0;
     const int slice = (int)(g - T->slice_off[sidx]);
     if (B.vk == TE_BF16) spmv_slice<PREC_FDF, TE_BF16, false>(a, slice, lane);
     else spmv_slice<PREC_FDF, TE_F32, false>(a, slice, lane);
@@ -767,6 +780,7 @@ cudaError_t launch_spmv(int prec, const DevSell& S, const void* x, void* y, bool
   a.y = y;
   a.vpart = S.vpart;
   a.nslices = S.nslices;
+  a.hot = (int)std::min<int64_t>(S.hot, (int64_t)(HOT_BYTES / (prec == PREC_DDD ? 8 : 4)));
   if (prec == PREC_DDD) {
     if (S.vk == TE_F64) return launch_spmv_t<PREC_DDD, TE_F64, true>(a, S, s);
     if (S.vk == TE_F32) return launch_spmv_t<PREC_DDD, TE_F32, true>(a, S, s);
