@@ -181,6 +181,8 @@ struct PassArgs {
   int64_t tstride;   // elements from a tile to the next tile of the same column
   int64_t cstride;   // elements from a column to the next (TILE_R: tile-major)
   void* xcopy;       // optional: the column a pass stores, also written contiguously
+  const void* cand;  // delayed form: the candidate (column nb-1 of the pass) is read from
+                     // this contiguous copy, and a new candidate is written only there
   const int32_t* perm;  // optional: row r of the vectors is the caller's row perm[r]
   double* urows;     // RITZ, optional: write the vectors by rows (K rounded up to even
                      // per row) here instead of by columns to st->eigvecs

@@ -475,7 +475,13 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
         for (int g = 0; g < gc; ++g) {
           const basis_t* src = Vg + (t0 + g) * a.tstride;
           basis_t* d = reinterpret_cast<basis_t*>(dst + (size_t)g * col_bytes);
-          if (tmaj) {
+          if (tmaj && a.cand) {  // the final columns, then the candidate's tile
+            const uint32_t vb = col_bytes - (uint32_t)(TILE_R * sizeof(basis_t));
+            if (vb > 0) bulk_g2s(d, src, vb, &full[s], pol);
+            bulk_g2s(d + (size_t)(nb - 1) * TILE_R,
+                     static_cast<const basis_t*>(a.cand) + (t0 + g) * TILE_R,
+                     (uint32_t)(TILE_R * sizeof(basis_t)), &full[s], pol);
+          } else if (tmaj) {
             bulk_g2s(d, src, col_bytes, &full[s], pol);
           } else {
             for (int j = 0; j < nb; ++j)
@@ -677,7 +683,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
           if (nj > 0) Vfix[vrow] = __fsub_rn(sc, t1);
           const dw sx = dw_mul(dw_from_f2(xscale), dw_from_f2(x));
           w = dw_to_f2(dw_sub(sx, dacc_value(t2)));
-          Vout[vrow] = w.x;
+          if (!a.cand) Vout[vrow] = w.x;  // (the delayed form keeps it in the copy only)
           if (xcopy) xcopy[row] = w.x;
           dacc_fma(n1, w.x, w.x, 2.0f * w.y);
           dacc_fma(n2, w.x, w.x, 0.0f);
@@ -691,7 +697,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
           t2 = fma(sc, fcand, t2);
           if (nj > 0) Vfix[vrow] = sc - t1;
           w = fma(xscale, x, -t2);
-          Vout[vrow] = w;
+          if (!a.cand) Vout[vrow] = w;
           if (xcopy) xcopy[row] = w;
           n1 = fma(w, w, n1);
         }

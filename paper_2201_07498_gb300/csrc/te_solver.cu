@@ -563,6 +563,7 @@ cudaError_t enqueue_lanczos(te_plan* P, cudaStream_t s) {
       // forms the next candidate (column i+1)
       a.nb = i + 1;
       a.fin = FIN_DCGS_DOT;
+      a.cand = at(P, P->W.xcur);  // the candidate lives in the contiguous copy
       if ((e = pass(P, MODE_DCGS_DOT, a, s)) != cudaSuccess) return e;
       a.col_out = i + 1;
       a.col_fix = i;
