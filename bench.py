@@ -175,9 +175,9 @@ SPMV_TRAFFIC = {
     "bytes_per_step": 2.271e9,
     "sources": {
         "paper_2201_07498_gb300/csrc/te_spmv.cu":
-            "7dd81cead00070a328c174435d6e0cd199374a198e5db62b4f1d551a4d250e62",
+            "089059b045376a1eecd8e887b6e45a65e3606449d822cb39d97616f43bbf9e76",
         "paper_2201_07498_gb300/csrc/te_common.cuh":
-            "582e786f547e13fe07f8ba3eb3f36e42d2e38dde4cb199bd2afe2d22adc91a86",
+            "4a92b110c7810ee9286055e9629f3bb8af147b489cdb6326cff63482fe82bba1",
     },
 }
 
