@@ -122,8 +122,7 @@ bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::st
   unsigned nt = std::thread::hardware_concurrency();
   if (nt < 1) nt = 1;
   if (nt > 32) nt = 32;
-  // small layouts (a serving request) are built by the calling thread alone
-  if ((int64_t)nt > W / 64) nt = (unsigned)std::max<int64_t>(1, W / 64);
+  if ((int64_t)nt > W / 16) nt = (unsigned)std::max<int64_t>(1, W / 16);
   const int64_t nc = nt == 1 ? 1 : std::min<int64_t>(W, (int64_t)nt * 16);  // chunks
   std::vector<int64_t> bad(nt, -1);
   std::vector<SellHost> part((size_t)nc);
