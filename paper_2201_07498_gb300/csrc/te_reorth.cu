@@ -825,7 +825,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
             // binary32 partial sums over 8 basis columns, each added exactly to
             // a double-float accumulator: the error stays within a small
             // multiple of the binary32 rounding the stored basis already has.
-            // The 8 coefficients of a column come in two 16-byte broadcasts.
+            // The coefficients of a column come in 16-byte broadcasts.
             const float* rh = reinterpret_cast<const float*>(rC) + k0;
             for (int j0 = 0; j0 < nb; j0 += 8) {
               float f[RITZ_KC];
@@ -835,16 +835,14 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
 #pragma unroll 4
               for (int j = j0; j < j1; ++j) {
                 const float v = tv[(size_t)j * TILE_R + tid];
-                const float4 c0 = *reinterpret_cast<const float4*>(rh + j * Kp);
-                const float4 c1 = *reinterpret_cast<const float4*>(rh + j * Kp + 4);
-                f[0] = __fmaf_rn(v, c0.x, f[0]);
-                f[1] = __fmaf_rn(v, c0.y, f[1]);
-                f[2] = __fmaf_rn(v, c0.z, f[2]);
-                f[3] = __fmaf_rn(v, c0.w, f[3]);
-                f[4] = __fmaf_rn(v, c1.x, f[4]);
-                f[5] = __fmaf_rn(v, c1.y, f[5]);
-                f[6] = __fmaf_rn(v, c1.z, f[6]);
-                f[7] = __fmaf_rn(v, c1.w, f[7]);
+#pragma unroll
+                for (int k4 = 0; k4 < RITZ_KC; k4 += 4) {
+                  const float4 c = *reinterpret_cast<const float4*>(rh + j * Kp + k4);
+                  f[k4] = __fmaf_rn(v, c.x, f[k4]);
+                  f[k4 + 1] = __fmaf_rn(v, c.y, f[k4 + 1]);
+                  f[k4 + 2] = __fmaf_rn(v, c.z, f[k4 + 2]);
+                  f[k4 + 3] = __fmaf_rn(v, c.w, f[k4 + 3]);
+                }
               }
 #pragma unroll
               for (int kk = 0; kk < RITZ_KC; ++kk) dacc_add_pair(ra[kk], f[kk], 0.f);
