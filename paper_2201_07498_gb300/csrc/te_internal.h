@@ -5,7 +5,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "topk_eigs.h"
@@ -54,6 +57,30 @@ struct LzState {
   double* eigvecs_user;  // with refinement: the caller's buffer (eigvecs is the plan's)
 };
 
+// Host arrays whose resize() leaves new elements default-initialised (no
+// zero fill): the layout and ordering arrays are written in full by worker
+// threads, which then also take the first-touch page faults in parallel.
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <typename U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <typename U>
+  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <typename U, typename... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+template <typename T>
+using hvec = std::vector<T, NoInitAlloc<T>>;
+
 struct LongRow {
   int32_t row, first, count, pad_;  // a row cut into `count` pieces, partials at [first, ...)
 };
@@ -76,12 +103,12 @@ struct SellSlice {
 };
 
 struct SellHost {
-  std::vector<SellSlice> slices;
-  std::vector<int32_t> vout;  // per lane: row (>= 0), -1 - partial slot, or SELL_SKIP
-  std::vector<int64_t> vsrc;  // per lane: first CSR entry of its piece
-  std::vector<int32_t> vlen;  // per lane: entries of its piece
-  std::vector<int32_t> vrow;  // per lane: the row its piece belongs to (-1: empty lane)
-  std::vector<LongRow> lrows;
+  hvec<SellSlice> slices;
+  hvec<int32_t> vout;  // per lane: row (>= 0), -1 - partial slot, or SELL_SKIP
+  hvec<int64_t> vsrc;  // per lane: first CSR entry of its piece
+  hvec<int32_t> vlen;  // per lane: entries of its piece
+  hvec<int32_t> vrow;  // per lane: the row its piece belongs to (-1: empty lane)
+  hvec<LongRow> lrows;
   int64_t entries = 0;        // padded entries
   int64_t pieces = 0;         // partial sums of cut rows
   int64_t nbig = 0;           // leading cut rows (most pieces first) summed by a whole warp

@@ -131,19 +131,28 @@ cudaError_t launch_copy_out_perm(LzState* st, const double* src, int64_t n, int 
 }
 
 // Thread per caller row: its K values are one contiguous row of src (read
-// with 16-byte loads), written to the K columns (coalesced across threads).
-__global__ void copy_out_rows_kernel(const LzState* st, const double* src, int64_t n, int K,
-                                     const int32_t* iperm) {
-  double* dst = st->eigvecs_user;
+// with 16-byte loads, up to eight in flight per thread), written to the K
+// columns (coalesced across threads).
+__global__ void copy_out_rows_kernel(const LzState* st, const double* __restrict__ src, int64_t n,
+                                     int K, const int32_t* __restrict__ iperm) {
+  double* __restrict__ dst = st->eigvecs_user;
   if (dst == nullptr) return;
   const int Kr = (K + 1) & ~1;
+  constexpr int CH = 8;  // 16-byte loads of one row in flight per thread
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const double2* row = reinterpret_cast<const double2*>(src + (size_t)iperm[v] * Kr);
-    for (int k = 0; k < K; k += 2) {
-      const double2 t = row[k >> 1];
-      dst[(size_t)k * n + v] = t.x;
-      if (k + 1 < K) dst[(size_t)(k + 1) * n + v] = t.y;
+    for (int k0 = 0; k0 < K; k0 += 2 * CH) {
+      double2 t[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (k0 + 2 * q < K) t[q] = row[(k0 >> 1) + q];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int k = k0 + 2 * q;
+        if (k < K) dst[(size_t)k * n + v] = t[q].x;
+        if (k + 1 < K) dst[(size_t)(k + 1) * n + v] = t[q].y;
+      }
     }
   }
 }

@@ -55,6 +55,7 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;
 __host__ __device__ constexpr int pass_ctas_per_sm(int prec) { return prec == PREC_FDF ? 2 : 1; }
 constexpr int QMAX = MAX_M / (CONSUMERS / 32);  // dot columns per warp
 constexpr int RITZ_KC = 8;                      // Ritz outputs per register block
+constexpr int RITZ_JG = 16;                     // FDF Ritz: basis columns per binary32 partial sum
 constexpr int RED_LOADS = 10;                   // partial loads per lane in flight
 // tile groups of a tile-major basis: stages of up to GROUP_BYTES (and at
 // most half the stage region, so that two stages fit), at most GROUP_MAX
@@ -822,16 +823,16 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
 #pragma unroll
           for (int kk = 0; kk < RITZ_KC; ++kk) ra[kk] = zero_acc<P>();
           if constexpr (P == PREC_FDF) {
-            // binary32 partial sums over 8 basis columns, each added exactly to
-            // a double-float accumulator: the error stays within a small
-            // multiple of the binary32 rounding the stored basis already has.
-            // The coefficients of a column come in 16-byte broadcasts.
+            // binary32 partial sums over RITZ_JG basis columns, each added
+            // exactly to a double-float accumulator: the error stays within a
+            // small multiple of the binary32 rounding the stored basis already
+            // has.  The coefficients of a column come in 16-byte broadcasts.
             const float* rh = reinterpret_cast<const float*>(rC) + k0;
-            for (int j0 = 0; j0 < nb; j0 += 8) {
+            for (int j0 = 0; j0 < nb; j0 += RITZ_JG) {
               float f[RITZ_KC];
 #pragma unroll
               for (int kk = 0; kk < RITZ_KC; ++kk) f[kk] = 0.f;
-              const int j1 = j0 + 8 < nb ? j0 + 8 : nb;
+              const int j1 = j0 + RITZ_JG < nb ? j0 + RITZ_JG : nb;
 #pragma unroll 4
               for (int j = j0; j < j1; ++j) {
                 const float v = tv[(size_t)j * TILE_R + tid];

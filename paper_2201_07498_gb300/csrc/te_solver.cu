@@ -854,7 +854,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   }
 
   // row pointers on the host for the partition
-  std::vector<int64_t> rp_host;
+  hvec<int64_t> rp_host;
   const int64_t* rph = A->row_ptr;
   if (A->where == TE_DEVICE) {
     rp_host.resize((size_t)A->n + 1);
@@ -867,8 +867,8 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   SellHost sell;
   std::string perr;
   // relabelled rows: the solver's row r is the caller's row hperm[r]
-  std::vector<int32_t> hperm, hiperm, hlen;
-  std::vector<int64_t> hsrc;
+  hvec<int32_t> hperm, hiperm, hlen;
+  hvec<int64_t> hsrc;
   RowOrder ord{nullptr, nullptr, nullptr};
   if (P->reorder) {
     if (!rows_valid(rph, A->n, A->nnz, perr))
@@ -1560,8 +1560,8 @@ te_status te_degree_order(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_
     return fail(TE_ERR_INVALID_ARG, "bad arguments");
   std::string perr;
   if (!rows_valid(row_ptr, n, nnz, perr)) return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
-  std::vector<int32_t> inv, len;
-  std::vector<int64_t> src((size_t)n);
+  hvec<int32_t> inv, len;
+  hvec<int64_t> src((size_t)n);
   len.resize((size_t)n);
   if (!iperm) {
     inv.resize((size_t)n);

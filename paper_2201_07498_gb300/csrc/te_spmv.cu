@@ -10,7 +10,9 @@
 // length of its longest piece; sorting keeps that padding small even on
 // power-law graphs, and keeping the sort inside windows keeps the row writes
 // local.  The plan keeps this copy in HBM and the solve never re-reads the
-// caller's CSR.
+// caller's CSR.  The arrangement (slices, lanes, cut rows) is computed on the
+// host (te_layout.cu); the kernel below fills it with column indices and
+// values on the device.
 //
 // Kernel: a warp streams its slice with coalesced 128-byte loads (marked L2
 // evict-first so that the gathered vector stays resident in L2), gathers
@@ -19,396 +21,10 @@
 // as a float pair and sums in double-float (Dot2 of Ogita, Rump & Oishi); DDD
 // uses binary64 FMA.  Pieces of a cut row leave partial sums that a second
 // kernel adds in piece order (deterministic).
-#include <algorithm>
-#include <atomic>
-#include <thread>
-
 #include "te_common.cuh"
 #include "te_internal.h"
 
 namespace te {
-
-// Windows of rows [w0, w1) into `out`, with entry offsets and cut-row piece
-// slots numbered from 0 (the caller shifts them).  Row r of the layout is CSR
-// row ord->perm[r] (ord NULL: row r); it writes output r.
-static void sell_windows(const int64_t* rp, int64_t n, int64_t w0, int64_t w1, int window,
-                         int vmax, const RowOrder* ord, SellHost& out) {
-  struct Piece {
-    int64_t src;
-    int32_t len, out, row;
-  };
-  std::vector<Piece> win, sorted;
-  std::vector<int64_t> pos((size_t)vmax + 2);
-  for (int64_t w = w0; w < w1; ++w) {
-    const int64_t r0 = w * window, r1 = std::min<int64_t>(r0 + window, n);
-    win.clear();
-    for (int64_t r = r0; r < r1; ++r) {
-      const int64_t o = ord ? (int64_t)ord->perm[r] : r;  // the CSR row
-      const int64_t first = ord ? ord->src[r] : rp[r];
-      const int64_t L = ord ? (int64_t)ord->len[r] : rp[r + 1] - rp[r];
-      if (L == 0) continue;  // empty rows: never written by the kernel
-      if (L <= vmax) {
-        win.push_back({first, (int32_t)L, (int32_t)r, (int32_t)o});
-        continue;
-      }
-      LongRow lr;
-      lr.row = (int32_t)r;
-      lr.first = (int32_t)out.pieces;
-      lr.count = (int32_t)((L + vmax - 1) / vmax);
-      lr.pad_ = 0;
-      for (int32_t c = 0; c < lr.count; ++c) {
-        const int64_t s0 = first + (int64_t)c * vmax;
-        const int64_t l = std::min<int64_t>(vmax, first + L - s0);
-        win.push_back({s0, (int32_t)l, -1 - (int32_t)(out.pieces + c), (int32_t)o});
-      }
-      out.pieces += lr.count;
-      out.lrows.push_back(lr);
-    }
-    if (win.empty()) continue;
-    // stable counting sort by length, longest first
-    std::fill(pos.begin(), pos.end(), 0);
-    for (const Piece& p : win) ++pos[p.len];
-    int64_t acc = 0;
-    for (int L = vmax; L >= 1; --L) {
-      const int64_t c = pos[L];
-      pos[L] = acc;
-      acc += c;
-    }
-    sorted.assign(win.size(), Piece{0, 0, 0, 0});
-    for (const Piece& p : win) sorted[pos[p.len]++] = p;
-    // slices of SELL_C lanes
-    for (size_t i = 0; i < sorted.size(); i += SELL_C) {
-      SellSlice sl;
-      sl.base = out.entries;
-      sl.len = sorted[i].len;
-      sl.pad_ = 0;
-      out.slices.push_back(sl);
-      for (int l = 0; l < SELL_C; ++l) {
-        if (i + l < sorted.size()) {
-          out.vout.push_back(sorted[i + l].out);
-          out.vsrc.push_back(sorted[i + l].src);
-          out.vlen.push_back(sorted[i + l].len);
-          out.vrow.push_back(sorted[i + l].row);
-        } else {
-          out.vout.push_back(SELL_SKIP);
-          out.vsrc.push_back(0);
-          out.vlen.push_back(0);
-          out.vrow.push_back(-1);
-        }
-      }
-      out.entries += (int64_t)SELL_C * sl.len;
-    }
-  }
-}
-
-// Threads take chunks of consecutive windows from a shared counter (the work
-// of a window grows with its rows' lengths, so a row order that puts the
-// longest rows first would leave one static range with most of it); the
-// chunks' parts are joined in chunk order with their entry and piece
-// offsets, so the result equals a sequential build.  The row pointers are
-// checked (all rows) before any window is built.
-bool make_sell(const int64_t* rp, int64_t n, int64_t nnz, SellHost& out, std::string& err,
-               int window, int vmax, const RowOrder* ord) {
-  out = SellHost();
-  if (rp[0] != 0) {
-    err = "row_ptr[0] must be 0";
-    return false;
-  }
-  if (rp[n] != nnz) {
-    err = "row_ptr[n] != nnz";
-    return false;
-  }
-  const int64_t W = (n + window - 1) / window;
-  unsigned nt = std::thread::hardware_concurrency();
-  if (nt < 1) nt = 1;
-  if (nt > 32) nt = 32;
-  if ((int64_t)nt > W / 16) nt = (unsigned)std::max<int64_t>(1, W / 16);
-  const int64_t nc = nt == 1 ? 1 : std::min<int64_t>(W, (int64_t)nt * 16);  // chunks
-  std::vector<int64_t> bad(nt, -1);
-  std::vector<SellHost> part((size_t)nc);
-  std::vector<int64_t> cw((size_t)nc + 1, 0);  // chunk c: windows [cw[c], cw[c+1])
-  std::atomic<int64_t> next{0};
-  // the row pointers (all rows) and, for several chunks, the work of each
-  // window in one pass
-  std::vector<int64_t> wwork(nc > 1 ? (size_t)W : 0, 0);
-  auto check = [&](unsigned t) {
-    const int64_t w0 = W * t / nt, w1 = W * (t + 1) / nt;
-    for (int64_t w = w0; w < w1; ++w) {
-      const int64_t r0 = w * window, r1 = std::min<int64_t>(r0 + window, n);
-      for (int64_t r = r0; r < r1; ++r)
-        if (rp[r + 1] < rp[r]) {
-          bad[t] = r;
-          return;
-        }
-      if (nc > 1) {  // the work of a window ~ its pieces ~ rows + entries / vmax
-        int64_t e = 0;
-        if (ord) {
-          for (int64_t r = r0; r < r1; ++r) e += ord->len[r];
-        } else {
-          e = rp[r1] - rp[r0];
-        }
-        wwork[(size_t)w] = (r1 - r0) + e / vmax;
-      }
-    }
-  };
-  auto work = [&](unsigned) {
-    for (int64_t c = next++; c < nc; c = next++)
-      sell_windows(rp, n, cw[(size_t)c], cw[(size_t)c + 1], window, vmax, ord, part[(size_t)c]);
-  };
-
-  auto run = [&](auto&& f) {
-    if (nt == 1) {
-      f(0u);
-    } else {
-      std::vector<std::thread> th;
-      for (unsigned t = 0; t < nt; ++t) th.emplace_back(f, t);
-      for (auto& x : th) x.join();
-    }
-  };
-  run(check);
-  for (unsigned t = 0; t < nt; ++t)
-    if (bad[t] >= 0) {
-      err = "row_ptr must be non-decreasing (row " + std::to_string(bad[t]) + ")";
-      return false;
-    }
-  if (nc > 1) {  // chunks of equal work (a chunk holds at least one window)
-    int64_t total = 0;
-    for (int64_t w = 0; w < W; ++w) total += wwork[(size_t)w];
-    int64_t c = 1, acc = 0;
-    for (int64_t w = 0; w < W && c < nc; ++w) {
-      acc += wwork[(size_t)w];
-      // close chunk c-1 after window w once it holds its share of the work,
-      // leaving at least one window for each later chunk
-      while (c < nc && acc * nc >= total * c && W - (w + 1) >= nc - c) cw[(size_t)c++] = w + 1;
-    }
-    for (; c < nc; ++c) cw[(size_t)c] = W - (nc - c);
-  }
-  cw[(size_t)nc] = W;
-  run(work);
-  // join the parts
-  size_t ns = 0, nl = 0, nr = 0;
-  for (const SellHost& p : part) {
-    ns += p.slices.size();
-    nl += p.vout.size();
-    nr += p.lrows.size();
-  }
-  out.slices.resize(ns);
-  out.vout.resize(nl);
-  out.vsrc.resize(nl);
-  out.vlen.resize(nl);
-  out.vrow.resize(nl);
-  std::vector<LongRow> lrows(nr);
-  std::vector<size_t> so(nc + 1, 0), lo(nc + 1, 0), ro(nc + 1, 0);
-  std::vector<int64_t> eo(nc + 1, 0), po(nc + 1, 0);
-  for (int64_t t = 0; t < nc; ++t) {
-    so[t + 1] = so[t] + part[t].slices.size();
-    lo[t + 1] = lo[t] + part[t].vout.size();
-    ro[t + 1] = ro[t] + part[t].lrows.size();
-    eo[t + 1] = eo[t] + part[t].entries;
-    po[t + 1] = po[t] + part[t].pieces;
-  }
-  next = 0;
-  auto join = [&](unsigned) {
-    for (int64_t t = next++; t < nc; t = next++) {
-      const SellHost& p = part[(size_t)t];
-      for (size_t i = 0; i < p.slices.size(); ++i) {
-        SellSlice sl = p.slices[i];
-        sl.base += eo[t];
-        out.slices[so[t] + i] = sl;
-      }
-      for (size_t i = 0; i < p.vout.size(); ++i) {
-        int32_t v = p.vout[i];
-        if (v < 0 && v != SELL_SKIP) v = -1 - (int32_t)(po[t] + (-1 - (int64_t)v));
-        out.vout[lo[t] + i] = v;
-        out.vsrc[lo[t] + i] = p.vsrc[i];
-        out.vlen[lo[t] + i] = p.vlen[i];
-        out.vrow[lo[t] + i] = p.vrow[i];
-      }
-      for (size_t i = 0; i < p.lrows.size(); ++i) {
-        LongRow lr = p.lrows[i];
-        lr.first += (int32_t)po[t];
-        lrows[ro[t] + i] = lr;
-      }
-    }
-  };
-  run(join);
-  out.entries = eo[nc];
-  out.pieces = po[nc];
-  // cut rows with the most pieces first (their finalising lanes run longest):
-  // a stable counting sort by piece count
-  int32_t maxc = 0;
-  for (const LongRow& lr : lrows) maxc = std::max(maxc, lr.count);
-  std::vector<int64_t> cpos((size_t)maxc + 2, 0);
-  for (const LongRow& lr : lrows) ++cpos[lr.count];
-  int64_t acc = 0;
-  for (int32_t c = maxc; c >= 0; --c) {
-    const int64_t k = cpos[c];
-    cpos[c] = acc;
-    acc += k;
-  }
-  out.lrows.resize(nr);
-  for (const LongRow& lr : lrows) out.lrows[cpos[lr.count]++] = lr;
-  out.nbig = 0;
-  while (out.nbig < (int64_t)out.lrows.size() && out.lrows[out.nbig].count > SELL_BIG_PIECES)
-    ++out.nbig;
-  return true;
-}
-
-// Host threads for a pass over n rows (at least ~64K rows each).
-static unsigned row_threads(int64_t n) {
-  unsigned nt = std::thread::hardware_concurrency();
-  if (nt < 1) nt = 1;
-  if (nt > 32) nt = 32;
-  const int64_t cap = n / 65536;
-  if ((int64_t)nt > cap) nt = (unsigned)std::max<int64_t>(1, cap);
-  return nt;
-}
-template <typename F>
-static void run_threads(unsigned nt, F&& f) {
-  if (nt == 1) {
-    f(0u);
-    return;
-  }
-  std::vector<std::thread> th;
-  for (unsigned t = 0; t < nt; ++t) th.emplace_back(f, t);
-  for (auto& x : th) x.join();
-}
-
-bool rows_valid(const int64_t* rp, int64_t n, int64_t nnz, std::string& err) {
-  if (rp[0] != 0) {
-    err = "row_ptr[0] must be 0";
-    return false;
-  }
-  if (rp[n] != nnz) {
-    err = "row_ptr[n] != nnz";
-    return false;
-  }
-  const unsigned nt = row_threads(n);
-  std::vector<int64_t> bad(nt, -1);
-  run_threads(nt, [&](unsigned t) {
-    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
-    for (int64_t r = r0; r < r1; ++r)
-      if (rp[r + 1] < rp[r]) {
-        bad[t] = r;
-        return;
-      }
-  });
-  for (int64_t b : bad)
-    if (b >= 0) {
-      err = "row_ptr must be non-decreasing (row " + std::to_string(b) + ")";
-      return false;
-    }
-  return true;
-}
-
-// Rows by length, longest first, ties in row order (a stable counting sort
-// over the row lengths): perm[r] = the row placed at r, iperm its inverse;
-// src[r] and len[r] = the first CSR entry and the length of that row, so that
-// the layout reads them in order.  Threads take contiguous row ranges, each
-// with its own histogram; the offsets of (length, range) follow lengths
-// descending, then ranges in order, so the result equals the sequential sort.
-// Sparse graphs whose degrees follow a power law then keep their
-// high-degree vertices together, so that the SpMV's reads of x for those
-// columns share cache lines.  The row pointers must be valid.
-void degree_order(const int64_t* rp, int64_t n, int32_t* perm, int32_t* iperm, int64_t* src,
-                  int32_t* len) {
-  unsigned nt = row_threads(n);
-  std::vector<int64_t> maxl(nt, 0);
-  run_threads(nt, [&](unsigned t) {
-    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
-    int64_t m = 0;
-    for (int64_t r = r0; r < r1; ++r) m = std::max<int64_t>(m, rp[r + 1] - rp[r]);
-    maxl[t] = m;
-  });
-  const int64_t L = *std::max_element(maxl.begin(), maxl.end()) + 1;
-  // the histograms hold nt * L counts: fewer threads when rows are very long
-  while (nt > 1 && (int64_t)nt * L > std::max<int64_t>(n, (int64_t)1 << 22)) --nt;
-  std::vector<int64_t> cnt((size_t)nt * L, 0);  // [thread][length]
-  run_threads(nt, [&](unsigned t) {
-    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
-    int64_t* c = cnt.data() + (size_t)t * L;
-    for (int64_t r = r0; r < r1; ++r) ++c[rp[r + 1] - rp[r]];
-  });
-  int64_t acc = 0;
-  for (int64_t l = L - 1; l >= 0; --l)
-    for (unsigned t = 0; t < nt; ++t) {
-      int64_t& c = cnt[(size_t)t * L + l];
-      const int64_t k = c;
-      c = acc;
-      acc += k;
-    }
-  run_threads(nt, [&](unsigned t) {
-    const int64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
-    int64_t* c = cnt.data() + (size_t)t * L;
-    for (int64_t r = r0; r < r1; ++r) {
-      const int64_t l = rp[r + 1] - rp[r];
-      const int64_t at = c[l]++;
-      perm[at] = (int32_t)r;
-      iperm[r] = (int32_t)at;
-      src[at] = rp[r];
-      len[at] = (int32_t)l;
-    }
-  });
-}
-
-// Host build of the SELL arrays (for a matrix that stays in host memory and
-// is streamed to the device in row blocks): the same arrangement the device
-// build produces; binary64 -> binary32 rounds to nearest even.  Threads split
-// the slices; the output does not depend on their number.  Returns false if a
-// column index lies outside [0, n).
-template <typename Vin, typename Vout>
-static bool build_sell_host_t(const SellHost& H, const int32_t* ci, const Vin* val, int64_t n,
-                              const int32_t* colmap, int32_t* cols, Vout* vals) {
-  const int64_t S = (int64_t)H.slices.size();
-  unsigned nt = std::thread::hardware_concurrency();
-  if (nt < 1) nt = 1;
-  if (nt > 64) nt = 64;
-  std::vector<int> bad(nt, 0);
-  std::vector<std::thread> th;
-  for (unsigned t = 0; t < nt; ++t) {
-    th.emplace_back([&, t] {
-      for (int64_t sl = (int64_t)t; sl < S; sl += nt) {
-        const SellSlice& q = H.slices[(size_t)sl];
-        for (int lane = 0; lane < SELL_C; ++lane) {
-          const size_t l = (size_t)sl * SELL_C + lane;
-          const int64_t src = H.vsrc[l];
-          const int len = H.vlen[l];
-          for (int k = 0; k < q.len; ++k) {
-            const int64_t dst = q.base + (int64_t)k * SELL_C + lane;
-            if (k < len) {
-              const int32_t c = ci[src + k];
-              const bool ok = c >= 0 && (int64_t)c < n;
-              if (!ok) bad[t] = 1;
-              cols[dst] = (colmap && ok) ? colmap[c] : c;
-              vals[dst] = (Vout)val[src + k];
-            } else {
-              cols[dst] = 0;
-              vals[dst] = (Vout)0;
-            }
-          }
-        }
-      }
-    });
-  }
-  for (auto& x : th) x.join();
-  for (int b : bad)
-    if (b) return false;
-  return true;
-}
-
-bool build_sell_host(const SellHost& H, const int32_t* ci, const void* val, int in_type, int vk,
-                     int64_t n, const int32_t* colmap, int32_t* cols, void* vals) {
-  if (in_type == TE_F64 && vk == TE_F64)
-    return build_sell_host_t(H, ci, static_cast<const double*>(val), n, colmap, cols,
-                             static_cast<double*>(vals));
-  if (in_type == TE_F64 && vk == TE_F32)
-    return build_sell_host_t(H, ci, static_cast<const double*>(val), n, colmap, cols,
-                             static_cast<float*>(vals));
-  if (in_type == TE_F32 && vk == TE_F32)
-    return build_sell_host_t(H, ci, static_cast<const float*>(val), n, colmap, cols,
-                             static_cast<float*>(vals));
-  return false;
-}
 
 // Vin -> Vout: binary64 -> binary32 rounds to nearest even (__double2float_rn)
 template <typename Vin, typename Vout>
