@@ -49,11 +49,20 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
   __shared__ int any_rot;
   __shared__ int sel[MAX_M];
   __shared__ double thr_s;
+  // the (a, b) pair indices of block e, a <= b, row-major upper triangle
+  constexpr int MAX_BLK = MAX_M / 2 * (MAX_M / 2 + 1) / 2;
+  __shared__ unsigned char blk_a[MAX_BLK], blk_b[MAX_BLK];
 
   const int tid = threadIdx.x;
   const int m = a.m;
   const int mm = m + (m & 1);  // even size; a dummy index never rotates
   const int half = mm / 2;
+  const int nblk = half * (half + 1) / 2;
+  // The rotation of pair k is computed by thread (k % 4) * 32 + k / 4: the
+  // pairs spread over four warps, one per scheduler, so that their binary64
+  // divisions and square roots issue from all four schedulers of the SM.
+  const int rk = (tid & 31) * 4 + (tid >> 5);  // the pair thread tid computes
+  const bool rthread = tid < 128 && rk < half;
 
   for (int e = tid; e < mm * mm; e += JAC_THREADS) {
     const int r = e / mm, c = e % mm;
@@ -70,6 +79,11 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
     for (int r = 0; r < m; ++r) f += a.alpha[r] * a.alpha[r];
     for (int r = 1; r < m; ++r) f += 2.0 * a.beta[r] * a.beta[r];
     thr_s = 1e-16 * sqrt(f);
+    for (int x = 0, e = 0; x < half; ++x)
+      for (int y = x; y < half; ++y, ++e) {
+        blk_a[e] = (unsigned char)x;
+        blk_b[e] = (unsigned char)y;
+      }
   }
   __syncthreads();
   const double thr = thr_s;
@@ -79,15 +93,16 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
     if (tid == 0) any_rot = 0;
     __syncthreads();
     for (int round = 0; round < mm - 1; ++round) {
-      if (tid < half) {
-        int p = rr_player(tid, round, mm), q = rr_player(mm - 1 - tid, round, mm);
+      if (rthread) {
+        const int k = rk;
+        int p = rr_player(k, round, mm), q = rr_player(mm - 1 - k, round, mm);
         if (p > q) {
           int tmp = p;
           p = q;
           q = tmp;
         }
-        rp_[tid] = p;
-        rq_[tid] = q;
+        rp_[k] = p;
+        rq_[k] = q;
         const double tpq = T[p * JLD + q];
         if (fabs(tpq) > thr) {
           const double tpp = T[p * JLD + p], tqq = T[q * JLD + q];
@@ -96,16 +111,16 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
           if (fabs(zeta) > 1e150) t = 0.5 / zeta;
           else t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t);
-          rc[tid] = c;
-          rs[tid] = t * c;
-          rt[tid] = t;
-          d_pp[tid] = tpp;
-          d_qq[tid] = tqq;
-          d_pq[tid] = tpq;
-          rot[tid] = 1;
+          rc[k] = c;
+          rs[k] = t * c;
+          rt[k] = t;
+          d_pp[k] = tpp;
+          d_qq[k] = tqq;
+          d_pq[k] = tpq;
+          rot[k] = 1;
           any_rot = 1;
         } else {
-          rot[tid] = 0;
+          rot[k] = 0;
         }
       }
       __syncthreads();
@@ -113,15 +128,9 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
       // J_a^T T[{p_a,q_a},{p_b,q_b}] J_b, written with its mirror image (T
       // stays exactly symmetric); a rotated pair's own block takes the exact
       // post-rotation values.  Y <- Y J in the same phase.
-      const int nblk = half * (half + 1) / 2;
       for (int e = tid; e < nblk + half * mm; e += JAC_THREADS) {
         if (e < nblk) {
-          int a = 0, rem = e;  // e -> (a, b), a <= b, row-major upper triangle
-          while (rem >= half - a) {
-            rem -= half - a;
-            ++a;
-          }
-          const int b = a + rem;
+          const int a = blk_a[e], b = blk_b[e];
           const int pa = rp_[a], qa = rq_[a], pb = rp_[b], qb = rq_[b];
           if (a == b) {
             if (rot[a]) {

@@ -257,34 +257,74 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) spmv_kernel(SpmvArgs a) {
   spmv_slice<P, VK, F64OUT>(a, slice, threadIdx.x & 31);
 }
 
-// Cut rows: the first nbig rows (most pieces first) get a whole warp each,
-// the others FIN_G lanes each (most cut rows have a handful of pieces).
-// Each lane sums a strided subset of the row's piece partials, then a fixed
-// shuffle tree adds the lanes (deterministic).
+// Cut rows: the first nbig rows (most pieces first) get a whole warp each:
+// each lane sums a strided subset of the row's piece partials, then a fixed
+// shuffle tree adds the lanes.  Every other row (at most SELL_BIG_PIECES
+// pieces, most have a handful) gets one thread, which loads all its
+// partials at once and sums them in the same fixed order as FIN_G lanes
+// would: chain s takes pieces s, s + FIN_G, ..., then the chains are added
+// as the xor tree over FIN_G lanes adds them, ((0, 2), (1, 3)).  The order
+// is fixed, so the result is deterministic.
 constexpr int FIN_G = 4;
+constexpr int FIN_PF = 8;  // partial loads in flight per lane of a whole-warp row
+static_assert(FIN_G == 4, "the per-thread merge order below is the xor tree of four lanes");
+template <int P>
+using part_t = typename std::conditional<P == PREC_FDF, float2, double>::type;
+template <int P>
+TE_DEV void acc_add_partial(typename SpmvTr<P>::acc_t& acc, const part_t<P>& v) {
+  if constexpr (P == PREC_FDF) dacc_add_pair(acc, v.x, v.y);
+  else acc += v;
+}
+template <int P>
+TE_DEV typename SpmvTr<P>::acc_t acc_join(const typename SpmvTr<P>::acc_t& a,
+                                         const typename SpmvTr<P>::acc_t& b) {
+  if constexpr (P == PREC_FDF) return dacc_merge(a, b);
+  else return a + b;
+}
+
 template <int P, bool F64OUT>
 __global__ void spmv_long_finalize(const LongRow* lrows, int nl, int nbig, int big_blocks,
                                    const void* vpart, void* y) {
-  const bool big = (int)blockIdx.x < big_blocks;  // uniform per block
-  const int G = big ? 32 : FIN_G;
-  const int64_t t = (int64_t)(big ? blockIdx.x : blockIdx.x - big_blocks) * blockDim.x + threadIdx.x;
-  const int64_t g = (big ? 0 : nbig) + t / G;
-  const int sub = threadIdx.x & (G - 1);
-  const bool live = big ? (g < nbig) : (g < nl);  // every lane reaches the shuffles below
-  LongRow lr{0, 0, 0, 0};
-  if (live) lr = lrows[g];
-  typename SpmvTr<P>::acc_t acc;
-  acc_zero<P>(acc);
-  for (int c = sub; c < lr.count; c += G) {
-    if constexpr (P == PREC_FDF) {
-      float2 v = static_cast<const float2*>(vpart)[lr.first + c];
-      dacc_add_pair(acc, v.x, v.y);
-    } else {
-      acc += static_cast<const double*>(vpart)[lr.first + c];
+  using acc_t = typename SpmvTr<P>::acc_t;
+  const part_t<P>* vp = static_cast<const part_t<P>*>(vpart);
+  if ((int)blockIdx.x < big_blocks) {  // uniform per block
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int sub = threadIdx.x & 31;
+    const bool live = g < nbig;  // every lane reaches the shuffles below
+    LongRow lr{0, 0, 0, 0};
+    if (live) lr = lrows[g];
+    acc_t acc;
+    acc_zero<P>(acc);
+    // the lane's pieces in order, FIN_PF loads in flight (the most connected
+    // rows have thousands of pieces, so the lanes' chains set the kernel's end)
+    for (int c0 = sub; c0 < lr.count; c0 += 32 * FIN_PF) {
+      part_t<P> v[FIN_PF];
+#pragma unroll
+      for (int u = 0; u < FIN_PF; ++u)
+        if (c0 + 32 * u < lr.count) v[u] = vp[(int64_t)lr.first + c0 + 32 * u];
+#pragma unroll
+      for (int u = 0; u < FIN_PF; ++u)
+        if (c0 + 32 * u < lr.count) acc_add_partial<P>(acc, v[u]);
     }
+    acc = group_sum(acc, 32);
+    if (live && sub == 0) store_row<P, F64OUT>(y, lr.row, acc);
+    return;
   }
-  acc = group_sum(acc, G);
-  if (live && sub == 0) store_row<P, F64OUT>(y, lr.row, acc);
+  const int64_t g = nbig + (int64_t)(blockIdx.x - big_blocks) * blockDim.x + threadIdx.x;
+  if (g >= nl) return;
+  const LongRow lr = lrows[g];
+  part_t<P> v[SELL_BIG_PIECES];
+#pragma unroll
+  for (int c = 0; c < SELL_BIG_PIECES; ++c)
+    if (c < lr.count) v[c] = vp[(int64_t)lr.first + c];
+  acc_t ch[FIN_G];
+#pragma unroll
+  for (int q = 0; q < FIN_G; ++q) acc_zero<P>(ch[q]);
+#pragma unroll
+  for (int c = 0; c < SELL_BIG_PIECES; ++c)
+    if (c < lr.count) acc_add_partial<P>(ch[c % FIN_G], v[c]);
+  const acc_t acc = acc_join<P>(acc_join<P>(ch[0], ch[2]), acc_join<P>(ch[1], ch[3]));
+  store_row<P, F64OUT>(y, lr.row, acc);
 }
 
 template <int P, int VK, bool F64OUT>
@@ -294,8 +334,7 @@ static cudaError_t launch_spmv_t(const SpmvArgs& a, const DevSell& S, cudaStream
   if (S.nlrows > 0) {
     const int threads = 256;
     const int big_blocks = (int)(((int64_t)S.nlbig * 32 + threads - 1) / threads);
-    const int small_blocks =
-        (int)(((int64_t)(S.nlrows - S.nlbig) * FIN_G + threads - 1) / threads);
+    const int small_blocks = (int)(((int64_t)(S.nlrows - S.nlbig) + threads - 1) / threads);
     spmv_long_finalize<P, F64OUT><<<big_blocks + small_blocks, threads, 0, s>>>(
         S.lrows, S.nlrows, S.nlbig, big_blocks, S.vpart, a.y);
   }

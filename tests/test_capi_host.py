@@ -206,8 +206,8 @@ def _check_layout(rp, L, VMAX=VMAX, WINDOW=WINDOW):
 
 
 def test_layout_covers_every_entry_once(te):
-    # (scale 18: 128 windows of rows, built by several threads in chunks of
-    # equal work and joined)
+    # (scale 18: 128 windows of rows, counted and then written at their
+    # offsets by several threads)
     mats = [synth.uniform_sym(5000, 7, 3), synth.rmat_sym(14, 8, 5), synth.rmat_sym(18, 2, 6)]
     # crafted: empty rows, a star (one very long row), rows around the cut length
     n = 20000
