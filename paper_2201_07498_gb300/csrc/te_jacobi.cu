@@ -14,6 +14,16 @@
 // t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = t c;
 // a pair is rotated when |t_pq| > 1e-16 ||T||_F and the sweeps stop after
 // one without rotations.  Arithmetic is binary64.
+//
+// GB300 runs binary64 at two operations per SM and clock, so for m >= 24 the
+// rounds are spread over a cluster of JAC_CLUSTER CTAs: every CTA keeps a full
+// copy of T, computes all rotations of a round (the same values everywhere),
+// updates the blocks e = rank (mod JAC_CLUSTER) and the rows of Y with the
+// same residue, and pushes its updated blocks into the other CTAs' copies
+// through distributed shared memory; two cluster barriers per round order
+// the reads of the angles before the pushes, and the pushes before the next
+// round.  Each element is computed by the same formula from the same inputs
+// as in the one-CTA form, so both give the same bits.
 #include "te_common.cuh"
 #include "te_internal.h"
 
@@ -22,6 +32,28 @@ namespace te {
 constexpr int JAC_THREADS = 256;
 constexpr int JAC_MAX_SWEEPS = 100;
 constexpr int JLD = MAX_M + 1;  // padded row length in shared memory
+constexpr int JAC_CLUSTER = 8;  // CTAs of the cluster form (a portable cluster size)
+constexpr int JAC_CLUSTER_MIN_M = 24;  // smaller T: one CTA (barriers would dominate)
+
+TE_DEV uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// the shared::cluster address of the same location in CTA `rank` of the cluster
+TE_DEV uint32_t cluster_map(uint32_t saddr, uint32_t rank) {
+  uint32_t d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(saddr), "r"(rank));
+  return d;
+}
+TE_DEV void st_cluster_f64(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+// every thread of every CTA of the cluster; orders shared-memory writes
+// (local and remote) before the barrier against reads after it
+TE_DEV void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
 
 // position j of the round-robin schedule in round r (player 0 stays put)
 TE_DEV int rr_player(int j, int r, int mm) { return j == 0 ? 0 : 1 + (j - 1 + r) % (mm - 1); }
@@ -39,7 +71,8 @@ TE_DEV bool sel_before(double a, int ia, double b, int ib, int which) {
 
 constexpr size_t JAC_SMEM = 2 * (size_t)MAX_M * JLD * sizeof(double);
 
-__global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
+template <int CL>
+__global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(JacobiArgs a) {
   extern __shared__ __align__(16) double jsm[];
   double* T = jsm;
   double* Y = jsm + MAX_M * JLD;
@@ -63,6 +96,12 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
   // divisions and square roots issue from all four schedulers of the SM.
   const int rk = (tid & 31) * 4 + (tid >> 5);  // the pair thread tid computes
   const bool rthread = tid < 128 && rk < half;
+  // this CTA's share: blocks e = rank + i CL (i < nb_mine), rows of Y
+  // r = rank + i CL (i < ny_rows); CL = 1: everything
+  const int rank = CL > 1 ? (int)cluster_ctarank() : 0;
+  const int nb_mine = (nblk - rank + CL - 1) / CL;
+  const int ny_rows = (mm - rank + CL - 1) / CL;
+  const uint32_t T_s = smem_addr(T);
 
   for (int e = tid; e < mm * mm; e += JAC_THREADS) {
     const int r = e / mm, c = e % mm;
@@ -123,13 +162,16 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
           rot[k] = 0;
         }
       }
-      __syncthreads();
+      // the angles are read from every copy of T before any copy changes
+      if constexpr (CL > 1) cluster_barrier();
+      else __syncthreads();
       // T <- J^T T J on 2x2 blocks: block (a, b) of pairs a <= b is
       // J_a^T T[{p_a,q_a},{p_b,q_b}] J_b, written with its mirror image (T
       // stays exactly symmetric); a rotated pair's own block takes the exact
       // post-rotation values.  Y <- Y J in the same phase.
-      for (int e = tid; e < nblk + half * mm; e += JAC_THREADS) {
-        if (e < nblk) {
+      for (int i = tid; i < nb_mine + half * ny_rows; i += JAC_THREADS) {
+        if (i < nb_mine) {
+          const int e = rank + i * CL;
           const int a = blk_a[e], b = blk_b[e];
           const int pa = rp_[a], qa = rq_[a], pb = rp_[b], qb = rq_[b];
           if (a == b) {
@@ -165,7 +207,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
           T[pb * JLD + qa] = x10;
           T[qb * JLD + qa] = x11;
         } else {
-          const int f = e - nblk, k = f / mm, row = f % mm;
+          const int f = i - nb_mine, k = f / ny_rows, row = rank + (f % ny_rows) * CL;
           if (!rot[k]) continue;
           const int p = rp_[k], q = rq_[k];
           const double c = rc[k], sn = rs[k];
@@ -175,9 +217,37 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
         }
       }
       __syncthreads();
+      if constexpr (CL > 1) {
+        // push this CTA's changed blocks (all eight positions, the mirror
+        // included) into the other copies of T
+        for (int i = tid; i < nb_mine * 8 * (CL - 1); i += JAC_THREADS) {
+          const int j = i / (8 * (CL - 1)), rem = i - j * (8 * (CL - 1));
+          const int el = rem / (CL - 1), rr = rem - el * (CL - 1);
+          const int e = rank + j * CL;
+          const int a = blk_a[e], b = blk_b[e];
+          if (!rot[a] && !rot[b]) continue;
+          const int pa = rp_[a], qa = rq_[a], pb = rp_[b], qb = rq_[b];
+          const int ra = (el & 2) ? qa : pa, cb = (el & 1) ? qb : pb;
+          const int off = (el < 4) ? ra * JLD + cb : cb * JLD + ra;
+          const int dst = rr < rank ? rr : rr + 1;
+          st_cluster_f64(cluster_map(T_s + (uint32_t)off * 8u, (uint32_t)dst), T[off]);
+        }
+        cluster_barrier();
+      }
     }
     if (!any_rot) break;
     __syncthreads();
+  }
+  if constexpr (CL > 1) {
+    // the rows of Y into CTA 0, which selects and writes the outputs
+    const uint32_t Y0 = cluster_map(smem_addr(Y), 0u);
+    if (rank != 0)
+      for (int i = tid; i < ny_rows * mm; i += JAC_THREADS) {
+        const int row = rank + (i / mm) * CL, c = i % mm;
+        st_cluster_f64(Y0 + (uint32_t)(row * JLD + c) * 8u, Y[row * JLD + c]);
+      }
+    cluster_barrier();
+    if (rank != 0) return;
   }
 
   // selection: rank of each Ritz value under the selection order
@@ -239,13 +309,31 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
 }
 
 cudaError_t jacobi_prepare() {
-  return cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)JAC_SMEM);
+  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)JAC_SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(jacobi_kernel<JAC_CLUSTER>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JAC_SMEM);
 }
 
 cudaError_t launch_jacobi(const JacobiArgs& a, cudaStream_t s) {
-  jacobi_kernel<<<1, JAC_THREADS, JAC_SMEM, s>>>(a);
-  return cudaGetLastError();
+  if (a.m < JAC_CLUSTER_MIN_M) {
+    jacobi_kernel<1><<<1, JAC_THREADS, JAC_SMEM, s>>>(a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(JAC_CLUSTER, 1, 1);
+  cfg.blockDim = dim3(JAC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = JAC_SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = JAC_CLUSTER;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi_kernel<JAC_CLUSTER>, a);
 }
 
 }  // namespace te
