@@ -168,16 +168,18 @@ def make_inputs(args):
 
 # DRAM bytes per SpMV step (slice kernel + cut-row finaliser) measured by ncu
 # on this workload (profiles/spmv_dram_fdf_rmat24_ef8.md), valid for the
-# kernel sources whose SHA-256 is recorded with it
+# kernel and layout sources whose SHA-256 is recorded with it
 SPMV_TRAFFIC = {
     "workload": "rmat24_ef8_normadj_seed1",
     "order": "degree",
     "bytes_per_step": 2.271e9,
     "sources": {
         "paper_2201_07498_gb300/csrc/te_spmv.cu":
-            "089059b045376a1eecd8e887b6e45a65e3606449d822cb39d97616f43bbf9e76",
+            "18ccde1ac8879239c8124a80fc982e33007d76671678b21277296b6136c76b83",
         "paper_2201_07498_gb300/csrc/te_common.cuh":
             "4a92b110c7810ee9286055e9629f3bb8af147b489cdb6326cff63482fe82bba1",
+        "paper_2201_07498_gb300/csrc/te_layout.cu":
+            "2e04e36f6ff8dddb6c1ec280a506a01b4a00e23d1e40214dc16daa4f7279106c",
     },
 }
 
