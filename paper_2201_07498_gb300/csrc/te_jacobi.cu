@@ -11,7 +11,8 @@
 // index pairs at once, T <- J^T T J (on 2x2 blocks of the upper triangle,
 // mirrored), Y <- Y J.  Rotation angle (textbook
 // form, e.g. Golub & Van Loan Sec. 8.5): zeta = (t_qq - t_pp) / (2 t_pq),
-// t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = t c;
+// t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = t c
+// (evaluated as |2 t_pq| sgn(zeta) / (|d| + hypot(d, 2 t_pq)), d = t_qq - t_pp);
 // a pair is rotated when |t_pq| > 1e-16 ||T||_F and the sweeps stop after
 // one without rotations.  Arithmetic is binary64.
 //
@@ -145,11 +146,14 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(JacobiArgs a) {
         const double tpq = T[p * JLD + q];
         if (fabs(tpq) > thr) {
           const double tpp = T[p * JLD + p], tqq = T[q * JLD + q];
-          const double zeta = (tqq - tpp) / (2.0 * tpq);
-          double t;
-          if (fabs(zeta) > 1e150) t = 0.5 / zeta;
-          else t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
+          // t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = d / (2 t_pq),
+          // d = t_qq - t_pp, multiplied through by |2 t_pq|: one hypot, one
+          // division and one reciprocal square root in the dependent chain
+          // (sgn(0) = +1 as before)
+          const double d = tqq - tpp, two = 2.0 * tpq;
+          const double sz = (d == 0.0 || (d > 0.0) == (tpq > 0.0)) ? 1.0 : -1.0;
+          const double t = sz * fabs(two) / (fabs(d) + hypot(d, two));
+          const double c = rsqrt(1.0 + t * t);
           rc[k] = c;
           rs[k] = t * c;
           rt[k] = t;
