@@ -20,11 +20,12 @@
 // rounds are spread over a cluster of JAC_CLUSTER CTAs: every CTA keeps a full
 // copy of T, computes all rotations of a round (the same values everywhere),
 // updates the blocks e = rank (mod JAC_CLUSTER) and the rows of Y with the
-// same residue, and pushes its updated blocks into the other CTAs' copies
-// through distributed shared memory; two cluster barriers per round order
-// the reads of the angles before the pushes, and the pushes before the next
-// round.  Each element is computed by the same formula from the same inputs
-// as in the one-CTA form, so both give the same bits.
+// same residue, writes every diagonal block (they depend on the angles
+// only), and pushes its updated off-diagonal blocks into the other CTAs'
+// copies through distributed shared memory; one cluster barrier per round
+// orders the pushes before the next round's angles.  Each element is
+// computed by the same formula from the same inputs as in the one-CTA form,
+// so both give the same bits.
 #include "te_common.cuh"
 #include "te_internal.h"
 
@@ -166,28 +167,27 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(JacobiArgs a) {
           rot[k] = 0;
         }
       }
-      // the angles are read from every copy of T before any copy changes
-      if constexpr (CL > 1) cluster_barrier();
-      else __syncthreads();
+      __syncthreads();
       // T <- J^T T J on 2x2 blocks: block (a, b) of pairs a <= b is
       // J_a^T T[{p_a,q_a},{p_b,q_b}] J_b, written with its mirror image (T
       // stays exactly symmetric); a rotated pair's own block takes the exact
-      // post-rotation values.  Y <- Y J in the same phase.
-      for (int i = tid; i < nb_mine + half * ny_rows; i += JAC_THREADS) {
-        if (i < nb_mine) {
-          const int e = rank + i * CL;
-          const int a = blk_a[e], b = blk_b[e];
-          const int pa = rp_[a], qa = rq_[a], pb = rp_[b], qb = rq_[b];
-          if (a == b) {
-            if (rot[a]) {
-              T[pa * JLD + pa] = d_pp[a] - rt[a] * d_pq[a];
-              T[qa * JLD + qa] = d_qq[a] + rt[a] * d_pq[a];
-              T[pa * JLD + qa] = 0.0;
-              T[qa * JLD + pa] = 0.0;
-            }
-            continue;
+      // post-rotation values.  Those diagonal blocks depend only on the angles
+      // and every CTA writes all of them into its own copy; the off-diagonal
+      // blocks are this CTA's share.  Y <- Y J in the same phase.
+      for (int i = tid; i < half + nb_mine + half * ny_rows; i += JAC_THREADS) {
+        if (i < half) {
+          if (rot[i]) {
+            const int pa = rp_[i], qa = rq_[i];
+            T[pa * JLD + pa] = d_pp[i] - rt[i] * d_pq[i];
+            T[qa * JLD + qa] = d_qq[i] + rt[i] * d_pq[i];
+            T[pa * JLD + qa] = 0.0;
+            T[qa * JLD + pa] = 0.0;
           }
-          if (!rot[a] && !rot[b]) continue;
+        } else if (i < half + nb_mine) {
+          const int e = rank + (i - half) * CL;
+          const int a = blk_a[e], b = blk_b[e];
+          if (a == b || (!rot[a] && !rot[b])) continue;
+          const int pa = rp_[a], qa = rq_[a], pb = rp_[b], qb = rq_[b];
           double x00 = T[pa * JLD + pb], x01 = T[pa * JLD + qb];
           double x10 = T[qa * JLD + pb], x11 = T[qa * JLD + qb];
           if (rot[a]) {  // rows: J_a^T
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(JacobiArgs a) {
           T[pb * JLD + qa] = x10;
           T[qb * JLD + qa] = x11;
         } else {
-          const int f = i - nb_mine, k = f / ny_rows, row = rank + (f % ny_rows) * CL;
+          const int f = i - half - nb_mine, k = f / ny_rows, row = rank + (f % ny_rows) * CL;
           if (!rot[k]) continue;
           const int p = rp_[k], q = rq_[k];
           const double c = rc[k], sn = rs[k];
@@ -222,14 +222,17 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(JacobiArgs a) {
       }
       __syncthreads();
       if constexpr (CL > 1) {
-        // push this CTA's changed blocks (all eight positions, the mirror
-        // included) into the other copies of T
+        // push this CTA's changed off-diagonal blocks (all eight positions,
+        // the mirror included) into the other copies of T.  They hold no
+        // element that any CTA reads for this round's angles (those lie in
+        // the diagonal blocks), so a slower CTA may still be computing its
+        // angles: one cluster barrier per round suffices.
         for (int i = tid; i < nb_mine * 8 * (CL - 1); i += JAC_THREADS) {
           const int j = i / (8 * (CL - 1)), rem = i - j * (8 * (CL - 1));
           const int el = rem / (CL - 1), rr = rem - el * (CL - 1);
           const int e = rank + j * CL;
           const int a = blk_a[e], b = blk_b[e];
-          if (!rot[a] && !rot[b]) continue;
+          if (a == b || (!rot[a] && !rot[b])) continue;
           const int pa = rp_[a], qa = rq_[a], pb = rp_[b], qb = rq_[b];
           const int ra = (el & 2) ? qa : pa, cb = (el & 1) ? qb : pb;
           const int off = (el < 4) ? ra * JLD + cb : cb * JLD + ra;
