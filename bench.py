@@ -63,6 +63,8 @@ def parse():
                    help="skip the host-streamed solve (R-MAT 2^25, edge factor 16, 4 GB budget)")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the precision sweep (R-MAT 2^22, edge factor 16, K=16, m=32)")
+    p.add_argument("--no-banded", action="store_true",
+                   help="skip the SpMV on a banded matrix of the same size (cache-friendly gathers)")
     return p.parse_args()
 
 
@@ -329,6 +331,27 @@ def precision_sweep(te, world, steps=5, warmup=3):
     return out
 
 
+def spmv_banded(te, peak, peak_kind):
+    """The FDF SpMV kernel on a banded matrix of the benchmark's size (n =
+    2^24; each row draws 8 columns among the 1024 right of the diagonal, then
+    A + A^T: about 16 non-zeros per row; binary32 values), rows in their own
+    order.  Its x reads stay within a few KB of the slice's rows and hit
+    cache, so this measures how close the kernel streams to the HBM peak when
+    random gathers do not bound it.  Algorithmic bytes and time per SpMV from
+    the plan's per-kernel CUDA events (best of three un-graphed solves)."""
+    import synth
+    A = synth.banded_sym(1 << 24, 8, 1024, 5)
+    plan = te.Plan(te.CSR.from_host(A, "fdf"), 8, 16, "fdf", seed=5)
+    plan.solve(vectors=False)
+    ms, launches, by = min(plan.profile()["spmv"] for _ in range(3))
+    del plan
+    gbs = by / (ms * 1e-3) / 1e9
+    return {"workload": "banded_n16777216_8perrow_hw1024_seed5_K8_m16", "n": int(A.n),
+            "nnz": int(A.nnz), "spmv_ms_per_launch": ms / launches,
+            "algorithmic_bytes_per_launch": by / launches, "gbs": gbs, "peak": peak,
+            "frac": gbs / peak, "peak_kind": peak_kind}
+
+
 def h2d_probe(nbytes=1 << 30, reps=5):
     """Pinned host -> device copy bandwidth (GB/s, best of reps, CUDA events)."""
     import torch
@@ -576,6 +599,8 @@ def main():
 
     if not args.no_sweep and world == 1:
         extras["precision_sweep"] = precision_sweep(te, world)
+    if not args.no_banded and world == 1:
+        extras["spmv_banded"] = spmv_banded(te, peak, peak_kind)
     if not args.no_serving and world == 1:
         extras["serving"] = serving(te, args.serving_requests)
     if not args.no_ooc and world == 1:

@@ -55,6 +55,8 @@ def _load():
         lib.synth_uniform_pm1.restype = None
         lib.synth_uniform_sym.argtypes = [i64, i32, u64]
         lib.synth_uniform_sym.restype = vp
+        lib.synth_banded_sym.argtypes = [i64, i32, i32, u64]
+        lib.synth_banded_sym.restype = vp
         lib.synth_rmat_sym.argtypes = [i32, i32, dbl, dbl, dbl, u64, ctypes.c_int]
         lib.synth_rmat_sym.restype = vp
         lib.synth_from_triplets.argtypes = [i64, i64, vp, vp, vp]
@@ -135,6 +137,13 @@ def start_vector(n: int, seed: int) -> np.ndarray:
 def uniform_sym(n: int, per_row: int, seed: int) -> CSR:
     """``per_row`` uniform-random columns per row, values uniform(0,1), then A + A^T."""
     return _take(_load().synth_uniform_sym(n, per_row, seed))
+
+
+def banded_sym(n: int, per_row: int, half_width: int, seed: int) -> CSR:
+    """``per_row`` columns per row drawn from the ``half_width`` columns right of
+    the diagonal, values uniform(0,1), then A + A^T: a banded, mesh-like matrix
+    whose SpMV reads x with locality (see ``synth.c``)."""
+    return _take(_load().synth_banded_sym(n, per_row, half_width, seed))
 
 
 def rmat_sym(scale: int, edge_factor: int, seed: int, a: float = 0.57, b: float = 0.19,

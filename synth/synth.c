@@ -232,6 +232,42 @@ synth_csr* synth_uniform_sym(int64_t n, int32_t per_row, uint64_t seed) {
 }
 
 /*
+ * Banded symmetric matrix: row i of A draws `per_row` entries with column
+ * i + d, d uniform in [1, half_width] (stream 103), and value uniform(0,1)
+ * (stream 104); draws past the last column are dropped, duplicates summed,
+ * then S = A + A^T.  Every column of row i lies within half_width of i: a
+ * mesh-like structure whose SpMV reads x with locality.
+ */
+synth_csr* synth_banded_sym(int64_t n, int32_t per_row, int32_t half_width, uint64_t seed) {
+  if (n <= 0 || per_row < 0 || half_width < 1 || n > INT32_MAX) return NULL;
+  int64_t e = n * per_row;
+  int32_t* r = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * e > 0 ? 2 * e : 1));
+  int32_t* c = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * e > 0 ? 2 * e : 1));
+  double* v = (double*)malloc(sizeof(double) * (size_t)(2 * e > 0 ? 2 * e : 1));
+  int64_t* keep = (int64_t*)malloc(sizeof(int64_t) * (size_t)(e > 0 ? e : 1));
+  if (!r || !c || !v || !keep) { free(r); free(c); free(v); free(keep); return NULL; }
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < e; ++k) {
+    int64_t i = k / per_row;
+    int64_t j = i + 1 + (int64_t)uint_below(synth_rng_u64(seed, 103, (uint64_t)k),
+                                            (uint64_t)half_width);
+    keep[k] = j < n ? j : -1;
+  }
+  int64_t m = 0;
+  for (int64_t k = 0; k < e; ++k) {
+    if (keep[k] < 0) continue;
+    int32_t i = (int32_t)(k / per_row), j = (int32_t)keep[k];
+    double x = u01(synth_rng_u64(seed, 104, (uint64_t)k));
+    r[m] = i; c[m] = j; v[m] = x; ++m;
+    r[m] = j; c[m] = i; v[m] = x; ++m;
+  }
+  free(keep);
+  synth_csr* A = build_csr(n, m, r, c, v);
+  free(r); free(c); free(v);
+  return A;
+}
+
+/*
  * R-MAT / Kronecker graph (Chakrabarti, Zhan & Faloutsos 2004) with
  * n = 2^scale vertices and edge_factor * n edge draws.  Each draw descends
  * `scale` levels, picking quadrant (0,0),(0,1),(1,0),(1,1) with probabilities

@@ -292,3 +292,23 @@ def test_product_path_has_no_cpu_fallback():
         assert "import oracle" not in src and "from oracle" not in src, f
         assert "oracle.h" not in src, f
         assert "import synth" not in src, f
+
+
+def test_banded_generator_and_its_layout(te):
+    """synth.banded_sym: symmetric, every column within the band, no diagonal,
+    at most per_row draws above the diagonal per row, reproducible from its
+    seed; its SpMV layout keeps every layout property."""
+    n, per_row, hw = 3000, 6, 40
+    A = synth.banded_sym(n, per_row, hw, 4)
+    D = A.to_dense()
+    assert np.array_equal(D, D.T)
+    rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+    off = A.col.astype(np.int64) - rows
+    assert np.all(off != 0) and np.max(np.abs(off)) <= hw
+    assert np.all(np.count_nonzero(np.triu(D, 1), axis=1) <= per_row)
+    assert np.all((A.val > 0) & (A.val < 2 * per_row))
+    B = synth.banded_sym(n, per_row, hw, 4)
+    assert np.array_equal(A.row_ptr, B.row_ptr) and np.array_equal(A.col, B.col)
+    assert np.array_equal(A.val, B.val)
+    assert not np.array_equal(A.col, synth.banded_sym(n, per_row, hw, 5).col)
+    _check_layout(A.row_ptr, te.spmv_layout(A.row_ptr, A.nnz))
