@@ -33,33 +33,62 @@ TE_DEV Vout convert_value(Vin v) {
   else return (Vout)v;
 }
 
+// Device fill of the SELL arrays, a warp per slice.  The 32 pieces of a
+// slice are contiguous runs of the CSR, while the slice stores them
+// column-major (entry k of lane l at base + 32 k + l).  The warp moves them
+// 32 columns of k at a time through a shared-memory tile: it reads each
+// piece's next 32 entries with one coalesced load per array, then writes the
+// tile's columns with coalesced stores, so the CSR reads and the slice writes
+// both move whole cache lines.  Values are converted on the way (binary64 ->
+// binary32 rounds to nearest even); columns go through colmap when the rows
+// are relabelled; padding entries are (column 0, value 0).
+template <typename Vout>
+constexpr int build_warps() { return sizeof(Vout) == 8 ? 2 : 4; }  // tiles within 48 KB
+
 template <typename Vin, typename Vout>
-__global__ void sell_build_kernel(const int32_t* ci, const Vin* val, const SellSlice* slices,
-                                  const int64_t* vsrc, const int32_t* vlen, int nslices,
-                                  int32_t* cols, Vout* vals, const int32_t* vrow,
-                                  const float* row_scale, float* lane_scale,
-                                  const int32_t* colmap) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nslices * SELL_C) return;
-  const int64_t s = t / SELL_C;
-  const int lane = (int)(t % SELL_C);
+__global__ void __launch_bounds__(32 * build_warps<Vout>())
+    sell_build_kernel(const int32_t* ci, const Vin* val, const SellSlice* slices,
+                      const int64_t* vsrc, const int32_t* vlen, int nslices, int32_t* cols,
+                      Vout* vals, const int32_t* vrow, const float* row_scale, float* lane_scale,
+                      const int32_t* colmap) {
+  constexpr int WARPS = build_warps<Vout>();
+  __shared__ int32_t tc[WARPS][SELL_C][SELL_C + 1];
+  __shared__ Vout tv[WARPS][SELL_C][SELL_C + 1];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * WARPS + w;
+  if (s >= nslices) return;  // uniform per warp
   const SellSlice sl = slices[s];
-  const int64_t src = vsrc[t];
-  const int len = vlen[t];
+  const int64_t t = s * SELL_C + lane;
+  const int64_t my_src = vsrc[t];
+  const int my_len = vlen[t];
   if (lane_scale) {
     const int32_t r = vrow[t];
     lane_scale[t] = r >= 0 ? row_scale[r] : 0.f;
   }
-  for (int k = 0; k < sl.len; ++k) {
-    const int64_t dst = sl.base + (int64_t)k * SELL_C + lane;
-    if (k < len) {
-      const int32_t c = ci[src + k];  // checked to lie in [0, n) before the build
-      cols[dst] = colmap ? colmap[c] : c;
-      vals[dst] = convert_value<Vin, Vout>(val[src + k]);
-    } else {
-      cols[dst] = 0;
-      vals[dst] = (Vout)0;
+  for (int k0 = 0; k0 < sl.len; k0 += SELL_C) {
+    const int k = k0 + lane;
+#pragma unroll 8
+    for (int l = 0; l < SELL_C; ++l) {  // piece l, entries k0 .. k0 + 31
+      const int64_t src = __shfl_sync(0xffffffffu, my_src, l);
+      const int len = __shfl_sync(0xffffffffu, my_len, l);
+      int32_t c = 0;
+      Vout v = (Vout)0;
+      if (k < len) {
+        const int32_t c0 = ci[src + k];  // checked to lie in [0, n) before the build
+        c = colmap ? colmap[c0] : c0;
+        v = convert_value<Vin, Vout>(val[src + k]);
+      }
+      tc[w][l][lane] = c;
+      tv[w][l][lane] = v;
     }
+    __syncwarp();
+    const int kn = sl.len - k0 < SELL_C ? sl.len - k0 : SELL_C;
+    for (int j = 0; j < kn; ++j) {  // column k0 + j: lane l's entry
+      const int64_t dst = sl.base + (int64_t)(k0 + j) * SELL_C + lane;
+      cols[dst] = tc[w][lane][j];
+      vals[dst] = tv[w][lane][j];
+    }
+    __syncwarp();
   }
 }
 
@@ -69,15 +98,15 @@ cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, cons
                               const float* row_scale, float* lane_scale, const int32_t* colmap,
                               cudaStream_t s) {
   if (nslices <= 0) return cudaSuccess;
-  const int64_t lanes = (int64_t)nslices * SELL_C;
-  const unsigned blocks = (unsigned)((lanes + 255) / 256);
-#define TE_BUILD(IN, OUT, TI, TO)                                                               \
-  if (in_type == IN && out_type == OUT) {                                                      \
-    sell_build_kernel<TI, TO><<<blocks, 256, 0, s>>>(ci, static_cast<const TI*>(val), slices, \
-                                                     vsrc, vlen, nslices, cols,                \
-                                                     static_cast<TO*>(vals), vrow, row_scale,  \
-                                                     lane_scale, colmap);                      \
-    return cudaGetLastError();                                                                 \
+#define TE_BUILD(IN, OUT, TI, TO)                                                              \
+  if (in_type == IN && out_type == OUT) {                                                     \
+    constexpr int W = build_warps<TO>();                                                      \
+    const unsigned blocks = (unsigned)(((int64_t)nslices + W - 1) / W);                       \
+    sell_build_kernel<TI, TO><<<blocks, 32 * W, 0, s>>>(ci, static_cast<const TI*>(val),      \
+                                                        slices, vsrc, vlen, nslices, cols,    \
+                                                        static_cast<TO*>(vals), vrow,         \
+                                                        row_scale, lane_scale, colmap);       \
+    return cudaGetLastError();                                                                \
   }
   TE_BUILD(TE_F64, TE_F64, double, double)
   TE_BUILD(TE_F64, TE_F32, double, float)
