@@ -177,7 +177,7 @@ SPMV_TRAFFIC = {
     "bytes_per_step": 2.271e9,
     "sources": {
         "paper_2201_07498_gb300/csrc/te_spmv.cu":
-            "18ccde1ac8879239c8124a80fc982e33007d76671678b21277296b6136c76b83",
+            "1580eee85d0a35494e21ec94b9d48149cb3ac7130d84464146c3fe7deaed5cbb",
         "paper_2201_07498_gb300/csrc/te_common.cuh":
             "4a92b110c7810ee9286055e9629f3bb8af147b489cdb6326cff63482fe82bba1",
         "paper_2201_07498_gb300/csrc/te_layout.cu":
