@@ -150,7 +150,7 @@ struct DevSell {
   int64_t hot = 0;  // rows by degree: gathers of x[c >= min(hot, what L1 holds)] skip L1
 };
 
-// fill cols/vals of the SELL layout from the CSR (one thread per lane)
+// fill cols/vals of the SELL layout from the CSR (a warp per slice)
 // in_type / out_type (te_dtype): F64 -> F64, F64 -> F32 (round to nearest
 // even), F32 -> F32, BF16 -> BF16, FP8_E4M3 -> FP8_E4M3 (codes copied).  For
 // FP8 also lane_scale[lane] = row_scale[vrow[lane]] (0 for empty lanes).
