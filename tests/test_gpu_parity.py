@@ -128,6 +128,7 @@ SPMV_CASES = {
     "star_ragged": lambda: star_plus_random(9000, 3),
     "rmat14": lambda: synth.rmat_sym(14, 8, 2),
     "thresholds": lambda: threshold_rows(),
+    "banded": lambda: synth.banded_sym(20000, 8, 300, 7),
 }
 
 
