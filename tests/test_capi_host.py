@@ -312,3 +312,61 @@ def test_banded_generator_and_its_layout(te):
     assert np.array_equal(A.val, B.val)
     assert not np.array_equal(A.col, synth.banded_sym(n, per_row, hw, 5).col)
     _check_layout(A.row_ptr, te.spmv_layout(A.row_ptr, A.nnz))
+
+
+def _reference_layout(rp, window, vmax):
+    """The SELL-C-sigma arrangement written out plainly: per window of rows,
+    the pieces in row order (rows longer than vmax cut into pieces of vmax,
+    numbered in row order across windows), stably sorted longest first, 32
+    per slice, each slice as long as its first piece, empty lanes INT32_MIN."""
+    n = len(rp) - 1
+    skip = np.iinfo(np.int32).min
+    slen, out, src, ln = [], [], [], []
+    pieces = 0
+    for r0 in range(0, n, window):
+        win = []
+        for r in range(r0, min(r0 + window, n)):
+            L = int(rp[r + 1] - rp[r])
+            if L == 0:
+                continue
+            if L <= vmax:
+                win.append((int(rp[r]), L, r))
+                continue
+            count = (L + vmax - 1) // vmax
+            for c in range(count):
+                s0 = int(rp[r]) + c * vmax
+                win.append((s0, min(vmax, int(rp[r]) + L - s0), -1 - (pieces + c)))
+            pieces += count
+        win.sort(key=lambda p: -p[1])  # stable
+        for i in range(0, len(win), 32):
+            part = win[i:i + 32]
+            slen.append(part[0][1])
+            for lane in range(32):
+                if lane < len(part):
+                    src.append(part[lane][0]); ln.append(part[lane][1]); out.append(part[lane][2])
+                else:
+                    src.append(0); ln.append(0); out.append(skip)
+    return (np.array(slen, dtype=np.int32), np.array(out, dtype=np.int32),
+            np.array(src, dtype=np.int64), np.array(ln, dtype=np.int32))
+
+
+@pytest.mark.parametrize("window,vmax", [(2048, 64), (2048, 128), (256, 32), (7, 5)])
+def test_layout_equals_the_plain_arrangement(te, window, vmax):
+    """The threaded two-pass layout build (counts per window, then every window
+    written at its offsets) equals the plain sequential arrangement exactly:
+    slice lengths, lane outputs and piece slots, piece starts and lengths."""
+    n = 6000
+    lens = np.zeros(n, dtype=np.int64)
+    lens[::5] = 3
+    lens[7] = n // 2
+    for i, L in enumerate([63, 64, 65, 127, 128, 129, 700]):
+        lens[100 + 37 * i] = L
+    star = np.concatenate([[0], np.cumsum(lens)])
+    for rp in (synth.rmat_sym(13, 8, 4).row_ptr, synth.banded_sym(5000, 6, 50, 2).row_ptr, star):
+        L = te.spmv_layout(rp, int(rp[-1]), window, vmax)
+        slen, out, src, ln = _reference_layout(rp, window, vmax)
+        assert np.array_equal(L["slice_len"], slen)
+        assert np.array_equal(L["lane_out"], out)
+        assert np.array_equal(L["lane_src"], src)
+        assert np.array_equal(L["lane_len"], ln)
+        assert L["entries"] == 32 * int(slen.astype(np.int64).sum())
