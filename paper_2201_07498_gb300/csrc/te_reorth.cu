@@ -57,6 +57,33 @@ constexpr int QMAX = MAX_M / (CONSUMERS / 32);  // dot columns per warp
 constexpr int RITZ_KC = 8;                      // Ritz outputs per register block
 constexpr int RITZ_JG = 16;                     // FDF Ritz: basis columns per binary32 partial sum
 constexpr int RED_LOADS = 10;                   // partial loads per lane in flight
+
+// Packed binary32 pairs (Blackwell's .f32x2 instructions): the low half holds
+// the first value.  Each half is computed and rounded as the scalar
+// instruction with the same rounding mode would.
+TE_DEV uint64_t f32x2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+TE_DEV void f32x2_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+TE_DEV uint64_t f32x2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+TE_DEV uint64_t f32x2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+TE_DEV uint64_t f32x2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 // tile groups of a tile-major basis: stages of up to GROUP_BYTES (and at
 // most half the stage region, so that two stages fit), at most GROUP_MAX
 // tiles, and at least GROUP_MIN_PER_CTA groups for every CTA
@@ -827,26 +854,45 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
             // exactly to a double-float accumulator: the error stays within a
             // small multiple of the binary32 rounding the stored basis already
             // has.  The coefficients of a column come in 16-byte broadcasts.
+            // Outputs go in pairs through the packed binary32 instructions
+            // (fma/add/sub .rn.f32x2): each half rounds as the scalar
+            // instruction would, so the results are those of the scalar
+            // form, with half the FMA and double-float addition instructions.
             const float* rh = reinterpret_cast<const float*>(rC) + k0;
-            for (int j0 = 0; j0 < nb; j0 += RITZ_JG) {
-              float f[RITZ_KC];
+            uint64_t as2[RITZ_KC / 2], ac2[RITZ_KC / 2];  // double-float (s, c) pairs
 #pragma unroll
-              for (int kk = 0; kk < RITZ_KC; ++kk) f[kk] = 0.f;
+            for (int q = 0; q < RITZ_KC / 2; ++q) as2[q] = ac2[q] = 0ull;
+            for (int j0 = 0; j0 < nb; j0 += RITZ_JG) {
+              uint64_t f2[RITZ_KC / 2];
+#pragma unroll
+              for (int q = 0; q < RITZ_KC / 2; ++q) f2[q] = 0ull;
               const int j1 = j0 + RITZ_JG < nb ? j0 + RITZ_JG : nb;
 #pragma unroll 4
               for (int j = j0; j < j1; ++j) {
                 const float v = tv[(size_t)j * TILE_R + tid];
+                const uint64_t vv = f32x2_pack(v, v);
 #pragma unroll
                 for (int k4 = 0; k4 < RITZ_KC; k4 += 4) {
-                  const float4 c = *reinterpret_cast<const float4*>(rh + j * Kp + k4);
-                  f[k4] = __fmaf_rn(v, c.x, f[k4]);
-                  f[k4 + 1] = __fmaf_rn(v, c.y, f[k4 + 1]);
-                  f[k4 + 2] = __fmaf_rn(v, c.z, f[k4 + 2]);
-                  f[k4 + 3] = __fmaf_rn(v, c.w, f[k4 + 3]);
+                  const ulonglong2 c = *reinterpret_cast<const ulonglong2*>(rh + j * Kp + k4);
+                  f2[k4 / 2] = f32x2_fma(vv, c.x, f2[k4 / 2]);
+                  f2[k4 / 2 + 1] = f32x2_fma(vv, c.y, f2[k4 / 2 + 1]);
                 }
               }
+              // (s, c) += (f, 0) exactly, as dacc_add_pair does per output
 #pragma unroll
-              for (int kk = 0; kk < RITZ_KC; ++kk) dacc_add_pair(ra[kk], f[kk], 0.f);
+              for (int q = 0; q < RITZ_KC / 2; ++q) {
+                const uint64_t sn = f32x2_add(as2[q], f2[q]);
+                const uint64_t bb = f32x2_sub(sn, as2[q]);
+                const uint64_t es = f32x2_add(f32x2_sub(as2[q], f32x2_sub(sn, bb)),
+                                              f32x2_sub(f2[q], bb));
+                as2[q] = sn;
+                ac2[q] = f32x2_add(ac2[q], f32x2_add(es, 0ull));
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < RITZ_KC / 2; ++q) {
+              f32x2_unpack(as2[q], ra[2 * q].s, ra[2 * q + 1].s);
+              f32x2_unpack(ac2[q], ra[2 * q].c, ra[2 * q + 1].c);
             }
           } else {
             for (int j = 0; j < nb; ++j) {
