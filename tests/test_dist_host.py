@@ -1,0 +1,69 @@
+"""The replica path of the benchmark on N > 1 ranks, on CPU: two gloo ranks.
+
+Each rank solves on its own GPU with no data-path collective; the ranks only
+meet at barriers and take the maximum of their timings.  These tests run that
+plumbing (process group, barrier, max over ranks) with world size 2 over gloo,
+and the reference arm launched the way the benchmark's driver launches it
+(torch.distributed.run, two processes): rank 0 alone prints its JSON line.
+"""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port),
+                       "RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    sys.path.insert(0, ROOT)
+    import bench
+    import torch.distributed as dist
+    w, r, _ = bench.dist_setup(None)
+    bench.barrier(w)
+    m = bench.max_over_ranks(10.0 + 3.5 * r, w)
+    bench.barrier(w)
+    q.put((r, w, dist.get_backend(), m))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_barrier_and_max():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs)
+    got = sorted(q.get(timeout=5) for _ in range(world))
+    assert [g[0] for g in got] == [0, 1]
+    assert all(g[1] == 2 and g[2] == "gloo" and g[3] == 13.5 for g in got)
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py",
+           "--impl", "reference", "--gpus", "2", "--scale", "10", "--oracle-steps", "2",
+           "--steps", "1", "--warmup", "0"]
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle"
