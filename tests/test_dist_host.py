@@ -25,8 +25,10 @@ def _free_port():
 
 
 def _worker(rank, world, port, q):
+    # CPU ranks even on a host with a GPU: the plumbing then takes gloo
     os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port),
-                       "RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+                       "RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank),
+                       "CUDA_VISIBLE_DEVICES": ""})
     sys.path.insert(0, ROOT)
     import bench
     import torch.distributed as dist
@@ -59,7 +61,7 @@ def test_reference_arm_under_torchrun_prints_once():
            "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py",
            "--impl", "reference", "--gpus", "2", "--scale", "10", "--oracle-steps", "2",
            "--steps", "1", "--warmup", "0"]
-    env = dict(os.environ, OMP_NUM_THREADS="2")
+    env = dict(os.environ, OMP_NUM_THREADS="2", CUDA_VISIBLE_DEVICES="")
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
