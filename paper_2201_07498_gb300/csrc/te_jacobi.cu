@@ -127,6 +127,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(JacobiArgs a) {
       }
   }
   __syncthreads();
+  // every copy of T is initialised before any CTA pushes into another
+  if constexpr (CL > 1) cluster_barrier();
   const double thr = thr_s;
 
   int sweep = 0;
