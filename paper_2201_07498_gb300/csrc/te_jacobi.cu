@@ -23,7 +23,8 @@
 // same residue, writes every diagonal block (they depend on the angles
 // only), and pushes its updated off-diagonal blocks into the other CTAs'
 // copies through distributed shared memory; one cluster barrier per round
-// orders the pushes before the next round's angles.  Each element is
+// orders the pushes before the next round's angles (and one after the
+// copies are initialised, before the first push).  Each element is
 // computed by the same formula from the same inputs as in the one-CTA form,
 // so both give the same bits.
 #include "te_common.cuh"
