@@ -55,7 +55,12 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3, help="0 skips the end-to-end leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the DDD and K=8 timings")
-    p.add_argument("--oracle-steps", type=int, default=6)
+    p.add_argument("--oracle-steps", type=int, default=2,
+                   help="Lanczos steps of the oracle timed with all host cores and with one")
+    p.add_argument("--no-small", action="store_true",
+                   help="skip the latency leg (uniform n = 10^4, K = 8, m = 16, FP64)")
+    p.add_argument("--no-fixed-error", action="store_true",
+                   help="skip the fixed-error leg (planted communities, n = 2^24, K = 24, m = 48)")
     p.add_argument("--no-serving", action="store_true",
                    help="skip the serving leg (Poisson arrivals of small solves)")
     p.add_argument("--serving-requests", type=int, default=200)
@@ -217,39 +222,69 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle on a bounded sample of the workload
+# CPU oracle, timed on the host cores
 # ---------------------------------------------------------------------------
-def oracle_sample(A, v1, K, m, steps, seed):
-    """Time the oracle's Lanczos for the first `steps` steps on the full matrix
-    plus one SpMV, and extrapolate to the m-step solve with
-    t_step(i) = t_spmv + (i+1) t_col, t_ritz = K m t_col / 2."""
+def oracle_solve_timed(A, v1, K, m, seed, vectors=True):
+    """One complete oracle solve (m Lanczos steps with MGS, Jacobi, selection
+    and, with `vectors`, the K Ritz vectors), timed once: (ms, result)."""
     import oracle
     t0 = time.perf_counter()
-    oracle.spmv(A, v1)
-    t_spmv = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.lanczos(A, v1, steps, seed=seed)
-    t_s = time.perf_counter() - t0
-    cols = steps * (steps + 1) / 2
-    t_col = max(t_s - steps * t_spmv, 0.0) / cols
-    est = m * t_spmv + t_col * m * (m + 1) / 2 + K * m * t_col / 2
-    sample = (f"oracle Lanczos, first {steps} of {m} steps on the full matrix ({t_s:.1f} s) "
-              f"+ one SpMV ({t_spmv:.2f} s), extrapolated to the {m}-step solve + Ritz "
-              f"with t_step(i) = t_SpMV + (i+1) t_MGS-column")
-    return est * 1e3, sample, oracle.num_threads(), t_s + t_spmv
+    r = oracle.topk_eigs(A, K, m, v1, seed=seed, want_vectors=vectors)
+    return (time.perf_counter() - t0) * 1e3, r
+
+
+def oracle_thread_scaling(A, v1, steps, seed):
+    """The oracle's first `steps` Lanczos steps on the full matrix, timed with
+    every host core and with one thread (the same sample both times)."""
+    import oracle
+    full = oracle.num_threads()
+    out = {"sample": f"the oracle's first {steps} Lanczos steps (SpMV + MGS) on the full matrix",
+           "threads": full}
+    try:
+        for th, key in ((full, "ms_all_threads"), (1, "ms_1_thread")):
+            oracle.set_num_threads(th)
+            t0 = time.perf_counter()
+            oracle.lanczos(A, v1, steps, seed=seed)
+            out[key] = (time.perf_counter() - t0) * 1e3
+    finally:
+        oracle.set_num_threads(full)
+    out["speedup"] = out["ms_1_thread"] / out["ms_all_threads"]
+    return out
+
+
+def oracle_config(args, A):
+    c = workload_config(args, A)
+    c["precision"] = "FP64 oracle: binary64 values, vectors and arithmetic"
+    c["reorthogonalisation"] = "modified Gram-Schmidt, one pass per step (Algorithm 1)"
+    c["row_order"] = "the generator's order"
+    return c
 
 
 def run_reference(args, world, rank):
+    """The oracle, as it stands, on the benchmark's workload: every timed step
+    is one complete solve (no sampling or extrapolation); each warm-up step is
+    one oracle SpMV over the whole matrix (it pages the matrix in)."""
     if rank != 0:
         return
+    import oracle
     A, v1, _ = make_inputs(args)
-    ms, sample, cores, spent = oracle_sample(A, v1, args.K, args.m, args.oracle_steps, args.seed)
+    for _ in range(args.warmup):
+        oracle.spmv(A, v1)
+    times = []
+    for _ in range(args.steps):
+        ms, _ = oracle_solve_timed(A, v1, args.K, args.m, args.seed)
+        times.append(ms)
+    ms = sum(times) / len(times)
+    cores = oracle.num_threads()
+    sample = (f"{args.steps} complete oracle solves ({args.m} Lanczos steps with MGS, Jacobi, "
+              f"{args.K} Ritz vectors) on the full matrix, each timed; median "
+              f"{statistics.median(times):.0f} ms")
     out = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(args, A),
+        "config": oracle_config(args, A),
         "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -296,6 +331,79 @@ def nearest_rel_err(ev_test, ev_ref):
     return float(max(np.min(np.abs(ev_ref - t)) / abs(t) for t in ev_test))
 
 
+def small_latency(te, world, solves=200, warmup=20, oracle_runs=20):
+    """The small FP64 case: uniform-random symmetric n = 10^4 (10 draws per
+    row, values uniform(0,1), A + A^T), seed 0, K = 8, m = 16, plain FP64
+    (DDD), one CUDA graph per solve with the matrix resident.  Latency-bound:
+    reports microseconds and kernels per solve, with the oracle timed beside
+    it (median of `oracle_runs` complete solves on the host cores)."""
+    import numpy as np
+    import oracle
+    import synth
+    A = synth.uniform_sym(10_000, 10, 0)
+    K, m, seed = 8, 16, 0
+    plan = te.Plan(te.CSR.from_host(A, "ddd"), K, m, "ddd", seed=seed)
+    ms, ev, _ = time_plan(plan, solves, warmup, world, want_vectors=True)
+    ev_g, _, _ = plan.solve(vectors=False)
+    kernels = plan.kernel_count + 1
+    del plan
+    v1 = synth.start_vector(A.n, seed)
+    t_o = []
+    for _ in range(oracle_runs):
+        t, r = oracle_solve_timed(A, v1, K, m, seed)
+        t_o.append(t)
+    rel = float(np.max(np.abs(np.sort(ev_g.numpy()) - np.sort(r.eigvals))
+                       / np.abs(np.sort(r.eigvals))))
+    return {"workload": "uniform_n10000_10perrow_seed0_K8_m16_ddd", "n": int(A.n),
+            "nnz": int(A.nnz), "us_per_solve": ms * 1e3, "solves_per_s": 1e3 / ms,
+            "kernels_per_solve": kernels, "graph": True,
+            "oracle_ms_median": statistics.median(t_o), "oracle_runs": oracle_runs,
+            "oracle_cores": oracle.num_threads(),
+            "max_rel_err_vs_oracle": rel}
+
+
+def fixed_error_planted(te, world, steps, warmup):
+    """Solve time at a fixed error.  Workload: the uniform background of the
+    small case at n = 2^24 (8 draws per row, values uniform(0,1), A + A^T) plus
+    24 planted unit cliques of sizes round(16 * 1.25^k), seed 6: 24 eigenvalues
+    (about 15 to 2,700) stand out of the background's spectrum, so an m = 48
+    Lanczos run converges all K = 24 of them (the community structure that
+    spectral clustering, Section I, looks for).  The oracle solves it once on
+    the host (binary64 values); each GPU form is timed as one CUDA graph per
+    solve, and its K values are compared with the oracle's, sorted."""
+    import numpy as np
+    import synth
+    t0 = time.perf_counter()
+    A = synth.planted_sym(1 << 24, 8, 24, 16, 1.25, 6)
+    gen_s = time.perf_counter() - t0
+    K, m, seed = 24, 48, 6
+    v1 = synth.start_vector(A.n, seed)
+    ms_o, r_o = oracle_solve_timed(A, v1, K, m, seed, vectors=False)
+    ev_o = np.sort(r_o.eigvals)
+    conv = int(np.sum(r_o.residuals <= 1e-9 * np.abs(r_o.eigvals)))
+    out = {"workload": "planted24_n16777216_8perrow_smin16_ratio1.25_seed6_K24_m48",
+           "n": int(A.n), "nnz": int(A.nnz), "generate_s": gen_s, "oracle_ms": ms_o,
+           "oracle_converged_pairs": conv,
+           "oracle_max_rel_residual": float(np.max(r_o.residuals / np.abs(r_o.eigvals))),
+           "forms": {}}
+    csr64 = te.CSR.from_host(A, "ddd")
+    for name, prec, refine in (("ddd", "ddd", False), ("fdf", "fdf", False),
+                               ("fdf_refined", "fdf", True), ("bdf", "bdf", False)):
+        plan = te.Plan(csr64, K, m, prec, seed=seed, refine=refine, reorth="delayed",
+                       order="degree")
+        ms, _, _ = time_plan(plan, max(3, steps // 2), warmup, world)
+        ev, _, res = plan.solve(vectors=False, residuals=True)
+        del plan
+        ev = np.sort(ev.numpy())
+        out["forms"][name] = {
+            "solve_ms": ms,
+            "max_rel_err_vs_oracle": float(np.max(np.abs(ev - ev_o) / np.abs(ev_o)))}
+    d = out["forms"]["ddd"]["solve_ms"]
+    for name, row in out["forms"].items():
+        row["speedup_vs_ddd"] = d / row["solve_ms"]
+    return out
+
+
 def precision_sweep(te, world, steps=5, warmup=3):
     """Every supported form on R-MAT scale 22, edge factor 16, seed 2
     (normalised adjacency), K = 16, m = 32: solve time, and the error of the
@@ -305,7 +413,7 @@ def precision_sweep(te, world, steps=5, warmup=3):
     import synth
     A = synth.rmat_sym(22, 16, 2)
     K, m, seed = 16, 32, 2
-    csr = te.CSR.from_host(A, "ddd", values_f64=True)  # binary64 values serve every form
+    csr = te.CSR.from_host(A, "ddd")  # binary64 values serve every form
     out = {"workload": "rmat22_ef16_normadj_seed2_K16_m32", "n": int(A.n), "nnz": int(A.nnz),
            "forms": {}}
     plan = te.Plan(csr, K, m, "ddd", seed=seed)
@@ -532,7 +640,7 @@ def main():
         spd_ms, _, spd_bytes = prof_d["spmv"]
         del plan_d
         # the chosen form with the binary64 Rayleigh-quotient refinement
-        csr_r = te.CSR.from_host(A, "fdf", values_f64=True)
+        csr_r = te.CSR.from_host(A, "fdf")
         plan_r = te.Plan(csr_r, K, m, "fdf", seed=args.seed, refine=True, reorth=args.reorth,
                          order=args.order)
         ms_r, _, _ = time_plan(plan_r, max(2, args.steps // 2), args.warmup, world)
@@ -584,8 +692,10 @@ def main():
         extras["spmv_gbs"] = spmv_gbs
 
     # end to end through the public API: host (pinned) CSR in, host results out
+    # the caller's binary64 CSR in pinned host memory: the library copies it
+    # and rounds the values to binary32 inside the timed call
     host = te.CSR.from_host(A, "fdf", device="cpu", pin=True)
-    h2d = host.row_ptr.numel() * 8 + host.col.numel() * 4 + host.val.numel() * 4
+    h2d = sum(t.numel() * t.element_size() for t in (host.row_ptr, host.col, host.val))
     d2h = K * 8 + A.n * K * 8
     e2e_ms = []
     ev_out = torch.empty(K, dtype=torch.float64).pin_memory()
@@ -604,6 +714,10 @@ def main():
             e2e_ms.append(a0.elapsed_time(a1))
     e2e = max_over_ranks(statistics.median(e2e_ms), world) if e2e_ms else None
 
+    if not args.no_small and world == 1:
+        extras["small_latency"] = small_latency(te, world)
+    if not args.no_fixed_error and world == 1:
+        extras["fixed_error_planted"] = fixed_error_planted(te, world, args.steps, args.warmup)
     if not args.no_sweep and world == 1:
         extras["precision_sweep"] = precision_sweep(te, world)
     if not args.no_banded and world == 1:
@@ -615,8 +729,12 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms_o, sample, cores, _ = oracle_sample(A, v1, K, m, args.oracle_steps, args.seed)
-        cpu = {"value": ms_o, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample}
+        import oracle
+        ms_o, _ = oracle_solve_timed(A, v1, K, m, args.seed)
+        cpu = {"value": ms_o, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"one complete oracle solve on the full workload ({m} Lanczos steps "
+                         f"with MGS, Jacobi, {K} Ritz vectors), timed once, not extrapolated",
+               "thread_scaling": oracle_thread_scaling(A, v1, args.oracle_steps, args.seed)}
 
     if rank == 0:
         out = {

@@ -146,6 +146,13 @@ typedef struct {
                        over rows run in another order).  Costs a counting sort of the
                        rows at plan creation, the permutation (8 bytes per row) and
                        the plan's own copy of the Ritz vectors (n x K binary64). */
+  int32_t stall_first_pass; /* test hook for the device-side failure path, 0 (default) in
+                       normal use.  1: the first pass over the basis of the plan's first
+                       solve issues none of its copies, so its consumer warps' bounded
+                       waits expire (after a shortened limit); the pass raises
+                       TE_ERR_TIMEOUT in the status word and every kernel still returns,
+                       with no copy in flight.  That solve returns TE_ERR_TIMEOUT (its
+                       outputs are meaningless); the plan's later solves run normally. */
 } te_options;
 
 #define TE_ORDER_KEEP 0   /* rows in the caller's order */
@@ -277,11 +284,17 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
  * the library, shared by all calls on a device, which limits nnz to
  * 131072 * 2048 (DDD) or 131072 * 4096 (FDF); larger matrices get
  * TE_ERR_INVALID_ARG.  The first call on each device looks up the array's
- * device address (do that first call before any stream capture).  Calls that
- * overlap on the GPU (other streams, other host threads) race on the array
- * and must be serialised by the caller.  A must be TE_DEVICE with
- * values_f64 = 0 (there is no room to round the values); x has n
- * elements of type p.vectors; y receives n doubles.  Synchronises `stream`. */
+ * device address (do that first call before any stream capture); the
+ * address is kept for the life of the process, so a program that resets a
+ * device (cudaDeviceReset) must not call this entry point on it afterwards.
+ * Calls that overlap on the GPU (other streams, other host threads) race on
+ * the array and must be serialised by the caller.  A must be TE_DEVICE with
+ * values_f64 = 0 (there is no room to round the values); x has n elements of
+ * type p.vectors; y receives n doubles.  A column index outside [0, n) or a
+ * malformed row_ptr (row_ptr[0] != 0, decreasing, row_ptr[n] != nnz) is
+ * found on the device and returns TE_ERR_INVALID_ARG (y is then
+ * meaningless).  The work grows with n as well as nnz (every row is
+ * visited).  Synchronises `stream`. */
 te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void* x, double* y,
                           void* stream);
 

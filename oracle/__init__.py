@@ -76,6 +76,8 @@ def _load():
         lib.oracle_set_fault.argtypes = [ctypes.c_int]
         lib.oracle_set_fault.restype = None
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_num_threads.restype = None
         lib.oracle_spmv.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.oracle_spmv.restype = None
         lib.oracle_spmv_row.argtypes = [vp, vp, vp, vp, i64]
@@ -139,6 +141,12 @@ class fault:
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(threads: int) -> None:
+    """Thread count of the oracle's OpenMP regions from now on (for timing;
+    the results do not depend on it)."""
+    _load().oracle_set_num_threads(int(threads))
 
 
 def spmv(csr, x) -> np.ndarray:

@@ -502,3 +502,13 @@ int oracle_num_threads(void) {
   return 1;
 #endif
 }
+
+/* thread count of the OpenMP regions that follow (timing only: results do
+   not depend on it) */
+void oracle_set_num_threads(int threads) {
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#else
+  (void)threads;
+#endif
+}

@@ -40,6 +40,7 @@ extern "C" {
 void oracle_set_fault(int kind);
 int oracle_get_fault(void);
 int oracle_num_threads(void);
+void oracle_set_num_threads(int threads); /* timing only; results do not depend on it */
 
 /* Algorithm 1, SpMV step: y = M x (each row summed left to right) */
 void oracle_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,

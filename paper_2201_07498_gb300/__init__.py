@@ -57,7 +57,7 @@ class te_options(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("device_budget_bytes", ctypes.c_size_t),
                 ("reorth", ctypes.c_int32), ("refine", ctypes.c_int32),
                 ("matrix_budget_bytes", ctypes.c_size_t), ("autotune", ctypes.c_int32),
-                ("order", ctypes.c_int32)]
+                ("order", ctypes.c_int32), ("stall_first_pass", ctypes.c_int32)]
 
 
 class te_server_options(ctypes.Structure):
@@ -178,14 +178,14 @@ def _stream_ptr(stream):
 class CSR:
     """CSR matrix held in torch tensors (device or host).
 
-    row_ptr: int64 (n+1); col: int32 (nnz); val: float64 (DDD, or any form
-    when values_f64: the library rounds them itself) or float32 (FDF).
+    row_ptr: int64 (n+1); col: int32 (nnz); val: float64 (binary64 values,
+    which serve every form: the library rounds them to the form's value type
+    itself) or float32 (the binary32 values of FDD / FDF).
     """
     n: int
     row_ptr: "object"
     col: "object"
     val: "object"
-    values_f64: bool = False
 
     @property
     def nnz(self) -> int:
@@ -194,6 +194,11 @@ class CSR:
     @property
     def on_device(self) -> bool:
         return bool(self.row_ptr.is_cuda)
+
+    @property
+    def values_f64(self) -> bool:
+        import torch
+        return self.val.dtype == torch.float64
 
     def to_ctypes(self) -> te_csr:
         for t in (self.row_ptr, self.col, self.val):
@@ -204,29 +209,35 @@ class CSR:
                       1 if self.values_f64 else 0)
 
     @staticmethod
-    def from_host(host_csr, precision: str = "ddd", device: str = "cuda", pin: bool = False,
-                  values_f64: bool = False):
-        """Make a CSR from numpy arrays (an object with n, row_ptr, col, val).
-        values_f64 keeps binary64 values for any precision (the library rounds
-        them; needed for refinement)."""
+    def from_host(host_csr, precision: str = "ddd", device: str = "cuda", pin: bool = False):
+        """Wrap a host CSR (an object with n, row_ptr, col, val as numpy
+        arrays) without touching its values.  float64 values are passed as
+        binary64 (te_csr.values_f64 = 1: the library rounds them to the form's
+        value type and keeps them for refinement); float32 values are the
+        binary32 values of FDD / FDF and are refused for other forms."""
         import numpy as np
         import torch
         pv = _prec(precision).values
-        if pv in (TE_BF16, TE_FP8_E4M3):
-            values_f64 = True  # the library quantises binary64 values itself
-        vdt = np.float32 if (pv == TE_F32 and not values_f64) else np.float64
+        val = np.asarray(host_csr.val)
+        if val.dtype == np.float32:
+            if pv != TE_F32:
+                raise ValueError("float32 values serve only the binary32-valued forms "
+                                 "(FDD, FDF); pass float64 values")
+        elif val.dtype != np.float64:
+            raise ValueError(f"values must be float64 or float32, not {val.dtype}")
         rp = torch.from_numpy(np.ascontiguousarray(host_csr.row_ptr, dtype=np.int64))
         ci = torch.from_numpy(np.ascontiguousarray(host_csr.col, dtype=np.int32))
-        va = torch.from_numpy(np.ascontiguousarray(host_csr.val, dtype=vdt))
+        va = torch.from_numpy(np.ascontiguousarray(val))
         if device == "cpu":
             if pin:
                 rp, ci, va = rp.pin_memory(), ci.pin_memory(), va.pin_memory()
-            return CSR(int(host_csr.n), rp, ci, va, values_f64)
-        return CSR(int(host_csr.n), rp.to(device), ci.to(device), va.to(device), values_f64)
+            return CSR(int(host_csr.n), rp, ci, va)
+        return CSR(int(host_csr.n), rp.to(device), ci.to(device), va.to(device))
 
 
 def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full",
-             refine=False, matrix_budget=0, autotune=False, order="keep") -> te_options:
+             refine=False, matrix_budget=0, autotune=False, order="keep",
+             stall_first_pass=False) -> te_options:
     o = te_options()
     load_library().te_default_options(ctypes.byref(o))
     o.seed = seed
@@ -239,6 +250,7 @@ def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full
     o.matrix_budget_bytes = matrix_budget
     o.autotune = 1 if autotune else 0
     o.order = ORDERS[order] if isinstance(order, str) else int(order)
+    o.stall_first_pass = 1 if stall_first_pass else 0
     return o
 
 
@@ -276,12 +288,15 @@ class Plan:
     def __init__(self, csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0,
                  v1=None, which="LM", use_graph: bool = True, budget: int = 0,
                  reorth="full", refine: bool = False, matrix_budget: int = 0,
-                 autotune: bool = False, order="keep", stream=None):
+                 autotune: bool = False, order="keep", stall_first_pass: bool = False,
+                 stream=None):
+        """stall_first_pass: test hook of the device-side failure path (the
+        first solve's first basis pass times out; see te_options)."""
         self._lib = load_library()
         self.csr, self.K, self.m, self.n = csr, K, krylov_steps, csr.n
         A = csr.to_ctypes()
         opt = _options(seed, v1, which, use_graph, budget, reorth, refine, matrix_budget,
-                       autotune, order)
+                       autotune, order, stall_first_pass)
         h = ctypes.c_void_p()
         rc = self._lib.te_plan_create(ctypes.byref(A), K, krylov_steps, _prec(precision),
                                       ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h))
@@ -518,10 +533,10 @@ def spmv_layout(row_ptr, nnz: int, window: int = 0, vmax: int = 0):
 def check_symmetric(host_csr, tol: float = 0.0):
     """max |a_ij - a_ji| of a host matrix (an object with n, row_ptr, col, val);
     raises TEError when it exceeds tol."""
-    csr = CSR.from_host(host_csr, "ddd", device="cpu", values_f64=True)
+    csr = CSR.from_host(host_csr, "ddd", device="cpu")
+    A = csr.to_ctypes()
     diff = ctypes.c_double()
-    _check(load_library().te_check_symmetric(ctypes.byref(csr.to_ctypes()), tol,
-                                             ctypes.byref(diff)))
+    _check(load_library().te_check_symmetric(ctypes.byref(A), tol, ctypes.byref(diff)))
     return diff.value
 
 

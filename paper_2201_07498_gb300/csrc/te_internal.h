@@ -49,7 +49,8 @@ struct LzState {
   int status;               // te_status of the solve so far
   int sweeps;               // Jacobi sweeps
   unsigned int ticket;      // last-CTA counter
-  int pad_;
+  int stall_armed;          // test hook (te_options.stall_first_pass): the next pass that
+                            // reads the basis waits for copies that are never issued
   // per-solve inputs (written by the host before each solve)
   const double* v1;
   double* eigvecs;
@@ -225,6 +226,7 @@ struct PassArgs {
   int xsrc;          // XSource
   int fin;           // Finalize
   int only_on_restart;  // exit at once unless st->restart_flag is set
+  int stall;         // test hook: honour st->stall_armed (a plan with stall_first_pass)
   const void* xvec;  // source vector (precision's vector type), X_VEC
   void* wout;        // AXPY_DOT: output vector
   uint64_t seed;

@@ -16,6 +16,8 @@
 // scratch array, and a second kernel adds those partials in chunk order
 // (deterministic) and writes the empty rows.  The scratch holds one 32-byte
 // record per chunk, so a matrix may have at most NOALLOC_MAX_CHUNKS chunks.
+// A chunk's CTA walks every row its entries touch, empty ones included, and
+// the second kernel visits every row: the cost grows with n as well as nnz.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -153,15 +155,25 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_chunk_kernel(
   }
 }
 
+// Adds the chunks' partial sums, writes the empty rows, and checks the row
+// pointers (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz): a malformed
+// row_ptr sets bit 2 of the status word.  The chunk kernel keeps every access
+// in bounds whatever row_ptr holds; its results are discarded then.
 template <int P>
-__global__ void noalloc_fixup_kernel(const int64_t* rp, double* y, int64_t n, int64_t nchunks,
-                                     const unsigned char* scratch) {
+__global__ void noalloc_fixup_kernel(const int64_t* rp, double* y, int64_t n, int64_t nnz,
+                                     int64_t nchunks, unsigned char* scratch) {
   constexpr int CH = NaTr<P>::CHUNK;
+  int* status = reinterpret_cast<int*>(scratch);
   const Carry* carry = reinterpret_cast<const Carry*>(scratch + 256);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nchunks || i < n;
-       i += stride) {
-    if (i < n && __ldg(rp + i) == __ldg(rp + i + 1)) y[i] = 0.0;
+  const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (first == 0 && (__ldg(rp) != 0 || __ldg(rp + n) != nnz)) atomicOr(status, 2);
+  for (int64_t i = first; i < nchunks || i < n; i += stride) {
+    if (i < n) {
+      const int64_t b = __ldg(rp + i), e = __ldg(rp + i + 1);
+      if (b == e) y[i] = 0.0;
+      if (b > e) atomicOr(status, 2);
+    }
     if (i < nchunks) {
       const Carry rec = carry[i];
       const int64_t k0 = i * CH;
@@ -232,7 +244,8 @@ extern "C" te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void
   if (e != cudaSuccess) return fail(TE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
     return fail(TE_ERR_UNSUPPORTED, "te_spmv_noalloc: device index too large");
-  // once per device, with that device current: the scratch array's device address
+  // once per device, with that device current: the scratch array's device
+  // address (kept for the life of the process; a device reset invalidates it)
   unsigned char* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_na_mu);
@@ -262,16 +275,17 @@ extern "C" te_status te_spmv_noalloc(const te_csr* A, te_precision p, const void
     if (blocks > 16384) blocks = 16384;
     if (prec == PREC_DDD)
       noalloc_fixup_kernel<PREC_DDD><<<(unsigned)blocks, 256, 0, s>>>(A->row_ptr, y, A->n,
-                                                                       nchunks, scratch);
+                                                                       A->nnz, nchunks, scratch);
     else
       noalloc_fixup_kernel<PREC_FDF><<<(unsigned)blocks, 256, 0, s>>>(A->row_ptr, y, A->n,
-                                                                       nchunks, scratch);
+                                                                       A->nnz, nchunks, scratch);
     e = cudaGetLastError();
   }
   int status = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, scratch, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(TE_ERR_CUDA, std::string("te_spmv_noalloc: ") + cudaGetErrorString(e));
+  if (status & 2) return fail(TE_ERR_INVALID_ARG, "te_spmv_noalloc: malformed row_ptr");
   if (status) return fail(TE_ERR_INVALID_ARG, "te_spmv_noalloc: a column index is outside [0, n)");
   return TE_OK;
 }

@@ -51,6 +51,8 @@ struct PassTr<PREC_FDF> {
 };
 
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
+// the shortened limit of a pass stalled by the test hook (stall_first_pass)
+constexpr uint32_t STALL_WAIT_LIMIT = 1u << 12;
 // FDF tiles are half the size of DDD tiles: two CTAs per SM still double-buffer
 __host__ __device__ constexpr int pass_ctas_per_sm(int prec) { return prec == PREC_FDF ? 2 : 1; }
 constexpr int QMAX = MAX_M / (CONSUMERS / 32);  // dot columns per warp
@@ -446,6 +448,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
     }
   }
 
+  // test hook: a stalled pass issues no copies, so every wait of its consumers
+  // expires; the last CTA disarms the hook once every CTA has read it
+  const bool stall = a.stall && nb > 0 && a.fin != FIN_NONE &&
+                     *((volatile int*)&st->stall_armed) != 0;
+  const uint32_t wait_limit = stall ? STALL_WAIT_LIMIT : WAIT_LIMIT;
   if (tid == 0) *abortflag = 0;
   if (tid == 0 && nb > 0) {
     for (int s = 0; s < S; ++s) {
@@ -484,7 +491,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
 
   // ------------------------- producer warp -------------------------
   if (wid == CONSUMERS / 32) {
-    if (nb > 0 && lane == 0) {
+    if (nb > 0 && lane == 0 && !stall) {
       const uint64_t pol = policy_evict_first();
       const bool tmaj = a.cstride == TILE_R;
       int it = 0;
@@ -571,7 +578,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
     int s = 0;
     if (nb > 0) {
       s = it % S;
-      if (!mbar_wait_bounded(&full[s], (uint32_t)((it / S) & 1), WAIT_LIMIT)) {
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((it / S) & 1), wait_limit)) {
         atomicExch(&st->status, (int)TE_ERR_TIMEOUT);
         *abortflag = 1;
       }
@@ -1028,7 +1035,10 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, size_t region, cons
   }
   named_bar_sync(1, CONSUMERS);
   finalize_pass(a, tot, reinterpret_cast<double*>(sm + L.fin_off), tid);
-  if (tid == 0) st->ticket = 0;
+  if (tid == 0) {
+    st->ticket = 0;
+    if (stall) st->stall_armed = 0;
+  }
 }
 
 template <int P, int MODE>

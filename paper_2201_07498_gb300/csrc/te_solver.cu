@@ -416,6 +416,7 @@ PassArgs base_args(te_plan* P) {
   a.st = P->st;
   a.partials = at(P, P->W.partials);
   a.fin = FIN_NONE;
+  a.stall = P->opt.stall_first_pass != 0;
   return a;
 }
 
@@ -795,6 +796,8 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   if (opt.refine != 0 && opt.refine != 1) return fail(TE_ERR_INVALID_ARG, "refine must be 0 or 1");
   if (opt.order != TE_ORDER_KEEP && opt.order != TE_ORDER_DEGREE)
     return fail(TE_ERR_INVALID_ARG, "order must be TE_ORDER_KEEP or TE_ORDER_DEGREE");
+  if (opt.stall_first_pass != 0 && opt.stall_first_pass != 1)
+    return fail(TE_ERR_INVALID_ARG, "stall_first_pass must be 0 or 1");
   const int in_type = A->values_f64 ? TE_F64 : p.values;
   if (opt.refine && in_type != TE_F64)
     return fail(TE_ERR_INVALID_ARG,
@@ -1048,6 +1051,13 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   // zero the solver vectors and state (the padded rows of V, y and w and the
   // empty rows of y must stay zero); the SELL arrays are written below
   TE_CK(cudaMemsetAsync(P->work, 0, P->W.slices, s), "clear work memory");
+  if (opt.stall_first_pass) {
+    // test hook: arm the stall of the first basis pass (solve_begin keeps it)
+    static const int one = 1;
+    TE_CK(cudaMemcpyAsync(&P->st->stall_armed, &one, sizeof(int), cudaMemcpyHostToDevice, s),
+          "arm the stall hook");
+    TE_CK(cudaStreamSynchronize(s), "arm the stall hook");
+  }
   if (!P->streaming) {
     // column indices must lie in [0, n)
     int* dflag = static_cast<int*>(at(P, P->W.flag));

@@ -59,6 +59,8 @@ def _load():
         lib.synth_banded_sym.restype = vp
         lib.synth_rmat_sym.argtypes = [i32, i32, dbl, dbl, dbl, u64, ctypes.c_int]
         lib.synth_rmat_sym.restype = vp
+        lib.synth_planted_sym.argtypes = [i64, i32, i32, i32, dbl, u64]
+        lib.synth_planted_sym.restype = vp
         lib.synth_from_triplets.argtypes = [i64, i64, vp, vp, vp]
         lib.synth_from_triplets.restype = vp
         lib.synth_csr_n.argtypes = [vp]
@@ -100,6 +102,11 @@ class CSR:
     def values_f32(self) -> np.ndarray:
         """Values rounded to binary32 (round to nearest even)."""
         return self.val.astype(np.float32)
+
+    def with_f32_values(self) -> "CSR":
+        """The same matrix holding binary32 values (rounded to nearest even):
+        the input of a caller whose data is binary32 already."""
+        return CSR(self.n, self.row_ptr, self.col, self.values_f32())
 
 
 def _take(handle, out=None) -> CSR:
@@ -160,6 +167,14 @@ def normalize_sym(A: CSR) -> CSR:
     inv = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)
     rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
     return CSR(A.n, A.row_ptr.copy(), A.col.copy(), A.val * inv[rows] * inv[A.col])
+
+
+def planted_sym(n: int, per_row: int, ncomm: int, smin: int, ratio: float, seed: int) -> CSR:
+    """The uniform background of ``uniform_sym`` plus ``ncomm`` disjoint unit
+    cliques of sizes round(smin * ratio^k), k = 0 .. ncomm-1, on seeded random
+    vertices: ``ncomm`` eigenvalues near the clique sizes minus one stand out
+    of the background's spectrum in a geometric progression (see ``synth.c``)."""
+    return _take(_load().synth_planted_sym(n, per_row, ncomm, smin, ratio, seed))
 
 
 def serving_requests(count: int, seed: int):

@@ -16,7 +16,8 @@
  * do not depend on the thread count or on the machine.
  *
  * Stream numbers used here: 0 start vectors; 101/102 uniform-matrix columns /
- * values; 110 R-MAT quadrant draws; 111 R-MAT vertex permutation.
+ * values; 110 R-MAT quadrant draws; 111 R-MAT vertex permutation; 112 the
+ * vertex permutation of the planted communities.
  */
 #include <math.h>
 #include <stdint.h>
@@ -354,6 +355,70 @@ synth_csr* synth_rmat_sym(int32_t scale, int32_t edge_factor, double a, double b
       }
     }
   }
+  return A;
+}
+
+/*
+ * Planted communities: the uniform-random background of synth_uniform_sym
+ * (`per_row` draws per row, streams 101/102, then A + A^T) plus `ncomm`
+ * disjoint cliques of unit weight.  Community k (k = 0 .. ncomm-1) has
+ * s_k = round(smin * ratio^(ncomm-1-k)) vertices, taken in order from a
+ * seeded Fisher-Yates permutation of the vertex ids (stream 112); every pair
+ * (i, j), i != j, of a community gets the entry 1 (added to a background
+ * entry at the same position).  A clique of s vertices contributes an
+ * eigenvalue near s - 1, so with ratio > 1 the matrix has ncomm outlying
+ * eigenvalues in a geometric progression above the background's spectrum:
+ * the community structure spectral clustering looks for.
+ */
+synth_csr* synth_planted_sym(int64_t n, int32_t per_row, int32_t ncomm, int32_t smin,
+                             double ratio, uint64_t seed) {
+  if (n <= 0 || per_row < 0 || ncomm < 0 || smin < 2 || !(ratio >= 1.0) || n > INT32_MAX)
+    return NULL;
+  int64_t* size = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ncomm > 0 ? ncomm : 1));
+  if (!size) return NULL;
+  int64_t members = 0, pairs = 0;
+  for (int32_t k = 0; k < ncomm; ++k) {
+    size[k] = (int64_t)floor((double)smin * pow(ratio, (double)(ncomm - 1 - k)) + 0.5);
+    members += size[k];
+    pairs += size[k] * (size[k] - 1);
+  }
+  if (members > n) { free(size); return NULL; }
+  const int64_t e = n * per_row, m = 2 * e + pairs;
+  int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t* r = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  int32_t* c = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  double* v = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  if (!perm || !r || !c || !v) {
+    free(size); free(perm); free(r); free(c); free(v);
+    return NULL;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < e; ++k) {
+    int32_t i = (int32_t)(k / per_row);
+    int32_t j = (int32_t)uint_below(synth_rng_u64(seed, 101, (uint64_t)k), (uint64_t)n);
+    double x = u01(synth_rng_u64(seed, 102, (uint64_t)k));
+    r[2 * k] = i; c[2 * k] = j; v[2 * k] = x;
+    r[2 * k + 1] = j; c[2 * k + 1] = i; v[2 * k + 1] = x;
+  }
+  for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+  for (int64_t i = n - 1; i >= 1; --i) {
+    int64_t j = (int64_t)uint_below(synth_rng_u64(seed, 112, (uint64_t)i), (uint64_t)(i + 1));
+    int32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+  }
+  int64_t first = 0, at = 2 * e;
+  for (int32_t k = 0; k < ncomm; ++k) {
+    const int64_t s = size[k];
+    for (int64_t a = 0; a < s; ++a)
+      for (int64_t b = 0; b < s; ++b) {
+        if (a == b) continue;
+        r[at] = perm[first + a]; c[at] = perm[first + b]; v[at] = 1.0; ++at;
+      }
+    first += s;
+  }
+  free(size);
+  free(perm);
+  synth_csr* A = build_csr(n, m, r, c, v);
+  free(r); free(c); free(v);
   return A;
 }
 

@@ -105,6 +105,7 @@ def test_option_validation_before_gpu(te):
     assert call(A, reorth=3) == 1
     assert call(A, refine=3) == 1
     assert call(A, order=2) == 1 and b"order" in lib.te_last_error()
+    assert call(A, stall_first_pass=2) == 1 and b"stall_first_pass" in lib.te_last_error()
     A.values_f64 = 2
     assert call(A) == 1
     A.values_f64 = 1
@@ -370,3 +371,46 @@ def test_layout_equals_the_plain_arrangement(te, window, vmax):
         assert np.array_equal(L["lane_src"], src)
         assert np.array_equal(L["lane_len"], ln)
         assert L["entries"] == 32 * int(slen.astype(np.int64).sum())
+
+
+def test_planted_generator_spectrum():
+    """synth.planted_sym without a background is a block diagonal of unit
+    cliques (zero diagonal) of sizes round(smin * ratio^k): its spectrum is
+    s_k - 1 once per clique, -1 with multiplicity sum (s_k - 1), and 0 for
+    the vertices outside every clique (dense eigensolver, brute force).  With
+    the background it stays symmetric and holds the background's entries."""
+    n, ncomm, smin, ratio = 400, 5, 4, 1.5
+    A = synth.planted_sym(n, 0, ncomm, smin, ratio, 3)
+    D = A.to_dense()
+    assert np.array_equal(D, D.T) and np.all(np.diag(D) == 0)
+    sizes = [int(np.floor(smin * ratio ** (ncomm - 1 - k) + 0.5)) for k in range(ncomm)]
+    assert A.nnz == sum(s * (s - 1) for s in sizes)
+    ev = np.sort(np.linalg.eigvalsh(D))
+    expect = np.sort(np.concatenate([[s - 1.0 for s in sizes],
+                                     -np.ones(sum(s - 1 for s in sizes)),
+                                     np.zeros(n - sum(sizes))]))
+    assert np.max(np.abs(ev - expect)) <= 1e-12 * max(sizes)
+    B = synth.planted_sym(n, 3, ncomm, smin, ratio, 3)
+    DB = B.to_dense()
+    assert np.array_equal(DB, DB.T)
+    bg = synth.uniform_sym(n, 3, 3).to_dense()
+    assert np.allclose(DB - bg, D, rtol=0, atol=1e-15)
+    assert not np.array_equal(A.col, synth.planted_sym(n, 0, ncomm, smin, ratio, 4).col)
+
+
+def test_binding_passes_values_through(te):
+    """CSR.from_host only marshals: binary64 values for a binary32 form are
+    flagged values_f64 (the library rounds them for a narrower form),
+    binary32 values pass as they are, and a binary64 form refuses binary32
+    values."""
+    A = synth.uniform_sym(50, 3, 1)
+    c = te.CSR.from_host(A, "fdf", device="cpu")
+    assert c.values_f64 and c.to_ctypes().values_f64 == 1
+    assert np.array_equal(c.val.numpy(), A.val)
+    c32 = te.CSR.from_host(A.with_f32_values(), "fdf", device="cpu")
+    assert not c32.values_f64 and c32.to_ctypes().values_f64 == 0
+    assert np.array_equal(c32.val.numpy(), A.val.astype(np.float32))
+    with pytest.raises(ValueError):
+        te.CSR.from_host(A.with_f32_values(), "ddd", device="cpu")
+    with pytest.raises(ValueError):
+        te.CSR.from_host(A.with_f32_values(), "bdf", device="cpu")

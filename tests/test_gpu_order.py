@@ -103,7 +103,7 @@ def test_degree_order_refinement(te):
     the caller's order and match the refined solve in the caller's order."""
     A = synth.rmat_sym(13, 8, 6)
     K, m = 6, 24
-    csr = te.CSR.from_host(A, "fdf", values_f64=True)
+    csr = te.CSR.from_host(A, "fdf")
     ev_k, U_k, r_k = te.topk_eigs(csr, K, m, "fdf", seed=2, refine=True, residuals=True)
     ev_d, U_d, r_d = te.topk_eigs(csr, K, m, "fdf", seed=2, refine=True, residuals=True,
                                   order="degree")

@@ -54,7 +54,7 @@ def test_streaming_limits(te):
     with pytest.raises(te.TEError) as e:  # a device matrix over the budget cannot stream
         te.Plan(dev, 4, 8, "fdf", matrix_budget=64 * 1024)
     assert e.value.status == 2
-    host64 = te.CSR.from_host(A, "fdf", device="cpu", pin=True, values_f64=True)
+    host64 = te.CSR.from_host(A, "fdf", device="cpu", pin=True)
     with pytest.raises(te.TEError) as e:
         te.Plan(host64, 4, 8, "fdf", refine=True, matrix_budget=64 * 1024)
     assert e.value.status == 7

@@ -48,15 +48,16 @@ def test_values_f64_rounding_is_round_to_nearest_even(te):
     same SpMV, bit for bit, as values rounded by numpy beforehand."""
     A = synth.rmat_sym(13, 8, 4)
     x = torch.from_numpy(synth.uniform_pm1(A.n, 5, 2).astype(np.float32)).cuda()
-    y_lib = te.spmv(te.CSR.from_host(A, "fdf", values_f64=True), x, "fdf")
-    y_pre = te.spmv(te.CSR.from_host(A, "fdf"), x, "fdf")
+    y_lib = te.spmv(te.CSR.from_host(A, "fdf"), x, "fdf")
+    y_pre = te.spmv(te.CSR.from_host(A.with_f32_values(), "fdf"), x, "fdf")
     assert torch.equal(y_lib, y_pre)
 
 
 def test_values_f64_solve_equals_prerounded(te):
     A = synth.uniform_sym(5000, 8, 6)
-    ev1, U1, _ = te.topk_eigs(te.CSR.from_host(A, "fdf", values_f64=True), 4, 10, "fdf", seed=1)
-    ev2, U2, _ = te.topk_eigs(te.CSR.from_host(A, "fdf"), 4, 10, "fdf", seed=1)
+    ev1, U1, _ = te.topk_eigs(te.CSR.from_host(A, "fdf"), 4, 10, "fdf", seed=1)
+    ev2, U2, _ = te.topk_eigs(te.CSR.from_host(A.with_f32_values(), "fdf"), 4, 10, "fdf",
+                              seed=1)
     assert torch.equal(ev1, ev2) and torch.equal(U1, U2)
 
 
@@ -89,7 +90,7 @@ def test_refine_fdf_matches_oracle_rayleigh_quotients(te, plan):
     K, m = 8, 16
     v1 = synth.start_vector(A.n, 0)
     ref32 = oracle.topk_eigs(f32_matrix(A), K, m, v1, seed=0)
-    csr = te.CSR.from_host(A, "fdf", values_f64=True)
+    csr = te.CSR.from_host(A, "fdf")
     if plan:
         p = te.Plan(csr, K, m, "fdf", seed=0, refine=True)
         ev, U, res = p.solve(residuals=True)
@@ -119,9 +120,9 @@ def test_refine_recovers_fp64_eigenvalues_of_converged_pairs(te):
     d = d + 1e-3 * np.sin(np.arange(n))  # values that do not round exactly to binary32
     A = synth.diagonal(d)
     K, m = 3, 40
-    ev, _, res = te.topk_eigs(te.CSR.from_host(A, "fdf", values_f64=True), K, m, "fdf", seed=4,
+    ev, _, res = te.topk_eigs(te.CSR.from_host(A, "fdf"), K, m, "fdf", seed=4,
                               refine=True, residuals=True)
-    ev0, _, _ = te.topk_eigs(te.CSR.from_host(A, "fdf"), K, m, "fdf", seed=4)
+    ev0, _, _ = te.topk_eigs(te.CSR.from_host(A.with_f32_values(), "fdf"), K, m, "fdf", seed=4)
     exact = d[:3]
     perm = match_pairs(ev.numpy(), exact, 1e-5)
     err_ref = np.abs(ev.numpy() - exact[perm])
@@ -227,7 +228,7 @@ def _quant_test_matrix():
 
 def test_quantize_is_bit_exact(te):
     A = _quant_test_matrix()
-    csr = te.CSR.from_host(A, "ddd", values_f64=True)
+    csr = te.CSR.from_host(A, "ddd")
     codes, _ = te.quantize(csr, "bf16")
     want, _ = oracle.round_bf16(A.val)
     assert np.array_equal(codes.cpu().numpy().view(np.uint16), want)
@@ -402,3 +403,64 @@ def test_gather_probe_reports_a_rate(te):
     small = te.probe_gather(1 << 12)
     big = te.probe_gather(1 << 26)
     assert big > 1e9 and small >= 0.9 * big
+
+
+# ---------------------------------------------------------------------------
+# device-side failure path: a bounded wait that runs out
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,reorth", [("ddd", "full"), ("fdf", "delayed")])
+def test_expired_wait_returns_timeout_then_plan_recovers(te, prec, reorth):
+    """The test hook stall_first_pass makes the first basis pass of the plan's
+    first solve wait for copies that are never issued: its consumers' bounded
+    waits expire, the pass sets TE_ERR_TIMEOUT and every kernel returns (no
+    copy is in flight, nothing waits without a limit).  The solve reports the
+    status; the context and the plan stay usable, and the next solve of the
+    same plan (graph replay) matches the oracle."""
+    import time
+    A = synth.uniform_sym(10000, 10, 0)
+    K, m = 8, 16
+    v1 = synth.start_vector(A.n, 0)
+    A_ref = A if prec == "ddd" else f32_matrix(A)
+    ref = oracle.topk_eigs(A_ref, K, m, v1, seed=0)
+    plan = te.Plan(te.CSR.from_host(A, prec), K, m, prec, seed=0, reorth=reorth,
+                   stall_first_pass=True)
+    t0 = time.perf_counter()
+    with pytest.raises(te.TEError) as e:
+        plan.solve()
+    assert e.value.status == 6, e.value  # TE_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    ev, U, _ = plan.solve()
+    ev = ev.numpy()
+    scale = np.max(np.abs(ref.eigvals))
+    tol = 1e-10 if prec == "ddd" else 1e-6
+    perm = match_pairs(ev, ref.eigvals, tol * scale)
+    assert np.max(np.abs(ev - ref.eigvals[perm]) / np.abs(ref.eigvals[perm])) <= tol
+    # a plan without the hook is unaffected
+    ev2, _, _ = te.Plan(te.CSR.from_host(A, prec), K, m, prec, seed=0, reorth=reorth).solve()
+    assert torch.equal(torch.from_numpy(ev), ev2)
+
+
+# ---------------------------------------------------------------------------
+# Jacobi on a cluster of CTAs: repeated launches give the same bits
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m", [48, 64])
+def test_cluster_jacobi_is_repeatable(te, m):
+    """For m >= 24 the Jacobi phase runs on a cluster of eight CTAs that each
+    keep a copy of T and push their blocks into the others' copies.  A copy
+    overwritten out of order (a missing barrier) would make launches disagree
+    with each other under varying schedules; fifty launches must give the same
+    bits, matching the oracle."""
+    rng = np.random.default_rng(100 + m)
+    alpha = rng.standard_normal(m)
+    beta = np.concatenate([[0.0], np.abs(rng.standard_normal(m))])
+    a_d, b_d = torch.from_numpy(alpha).cuda(), torch.from_numpy(beta).cuda()
+    th0, Y0, _ = te.tridiag_eigs(a_d, b_d, "LM")
+    for _ in range(49):
+        th, Y, _ = te.tridiag_eigs(a_d, b_d, "LM")
+        assert torch.equal(th, th0) and torch.equal(Y, Y0)
+    T = np.diag(alpha) + np.diag(beta[1:m], 1) + np.diag(beta[1:m], -1)
+    th_ref, _, _, _ = oracle.jacobi(T)
+    idx = oracle.select_topk(th_ref, m, oracle.LARGEST_MAGNITUDE)
+    assert np.max(np.abs(th0.cpu().numpy() - th_ref[idx])) <= 1e-13 * np.linalg.norm(T)
