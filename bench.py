@@ -63,11 +63,17 @@ def parse():
                    help="skip the fixed-error leg (planted communities, n = 2^24, K = 24, m = 48)")
     p.add_argument("--no-serving", action="store_true",
                    help="skip the serving leg (Poisson arrivals of small solves)")
-    p.add_argument("--serving-requests", type=int, default=200)
+    p.add_argument("--serving-requests", type=int, default=10000,
+                   help="requests per arrival rate >= 1000/s (1000 at the lower rates)")
     p.add_argument("--no-ooc", action="store_true",
                    help="skip the host-streamed solve (R-MAT 2^25, edge factor 16, 4 GB budget)")
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the precision sweep (R-MAT 2^22, edge factor 16, K=16, m=32)")
+    p.add_argument("--spmv-order-probe", default=None,
+                   choices=["degree", "keep", "rcm", "hubs32k_rcm", "hubs256k_rcm",
+                            "degbucket_rcm"],
+                   help="only time one FDF SpMV under this row order on the --scale / "
+                        "--edge-factor / --seed R-MAT graph and exit (for the order study)")
     p.add_argument("--no-banded", action="store_true",
                    help="skip the SpMV on a banded matrix of the same size (cache-friendly gathers)")
     return p.parse_args()
@@ -414,9 +420,10 @@ def precision_sweep(te, world, steps=5, warmup=3):
     A = synth.rmat_sym(22, 16, 2)
     K, m, seed = 16, 32, 2
     csr = te.CSR.from_host(A, "ddd")  # binary64 values serve every form
+    opts = {"reorth": "delayed", "order": "degree"}  # the benchmark's plan options
     out = {"workload": "rmat22_ef16_normadj_seed2_K16_m32", "n": int(A.n), "nnz": int(A.nnz),
-           "forms": {}}
-    plan = te.Plan(csr, K, m, "ddd", seed=seed)
+           "plan_options": opts, "forms": {}}
+    plan = te.Plan(csr, K, m, "ddd", seed=seed, **opts)
     ms_d, _, _ = time_plan(plan, steps, warmup, world)
     ev_d, _, res_d = plan.solve(vectors=False, residuals=True)
     ev_d, res_d = ev_d.numpy(), res_d.numpy()
@@ -425,13 +432,15 @@ def precision_sweep(te, world, steps=5, warmup=3):
     del plan
     for prec, vb in (("fdf", 4), ("bdf", 2), ("8df", 1)):
         row = {"spmv_value_bytes": vb}
-        plan = te.Plan(csr, K, m, prec, seed=seed)
+        plan = te.Plan(csr, K, m, prec, seed=seed, **opts)
         row["solve_ms"], ev, _ = time_plan(plan, steps, warmup, world)
-        row["spmv_ms"] = plan.profile()["spmv"][0]
+        sp = plan.profile()["spmv"]
+        row["spmv_ms"] = sp[0]
+        row["spmv_gbs"] = sp[2] / (sp[0] * 1e-3) / 1e9
         del plan
         row["max_rel_err_vs_fp64_converged"] = converged_match_err(ev, ev_d, res_d)[0]
         row["max_rel_err_vs_fp64_nearest"] = nearest_rel_err(ev, ev_d)
-        plan = te.Plan(csr, K, m, prec, seed=seed, refine=True)
+        plan = te.Plan(csr, K, m, prec, seed=seed, refine=True, **opts)
         ms_r, _, _ = time_plan(plan, steps, warmup, world)
         ev_r, _, res_r = plan.solve(vectors=False, residuals=True)
         ev_r, res_r = ev_r.numpy(), res_r.numpy()
@@ -447,24 +456,29 @@ def precision_sweep(te, world, steps=5, warmup=3):
 
 
 def spmv_banded(te, peak, peak_kind):
-    """The FDF SpMV kernel on a banded matrix of the benchmark's size (n =
-    2^24; each row draws 8 columns among the 1024 right of the diagonal, then
-    A + A^T: about 16 non-zeros per row; binary32 values), rows in their own
-    order.  Its x reads stay within a few KB of the slice's rows and hit
-    cache, so this measures how close the kernel streams to the HBM peak when
-    random gathers do not bound it.  Algorithmic bytes and time per SpMV from
-    the plan's per-kernel CUDA events (best of three un-graphed solves)."""
+    """The SpMV kernel of each mixed form (binary32, bfloat16 and FP8 E4M3
+    values) on a banded matrix of the benchmark's size (n = 2^24; each row
+    draws 8 columns among the 1024 right of the diagonal, then A + A^T: about
+    16 non-zeros per row), rows in their own order.  Its x reads stay within
+    a few KB of the slice's rows and hit cache, so this measures how close
+    the kernel streams to the HBM peak when random gathers do not bound it.
+    Algorithmic bytes and time per SpMV from the plan's per-kernel CUDA
+    events (best of three un-graphed solves)."""
     import synth
     A = synth.banded_sym(1 << 24, 8, 1024, 5)
-    plan = te.Plan(te.CSR.from_host(A, "fdf"), 8, 16, "fdf", seed=5)
-    plan.solve(vectors=False)
-    ms, launches, by = min(plan.profile()["spmv"] for _ in range(3))
-    del plan
-    gbs = by / (ms * 1e-3) / 1e9
-    return {"workload": "banded_n16777216_8perrow_hw1024_seed5_K8_m16", "n": int(A.n),
-            "nnz": int(A.nnz), "spmv_ms_per_launch": ms / launches,
-            "algorithmic_bytes_per_launch": by / launches, "gbs": gbs, "peak": peak,
-            "frac": gbs / peak, "peak_kind": peak_kind}
+    csr = te.CSR.from_host(A, "ddd")  # binary64 values: each plan rounds them
+    out = {"workload": "banded_n16777216_8perrow_hw1024_seed5_K8_m16", "n": int(A.n),
+           "nnz": int(A.nnz), "peak": peak, "peak_kind": peak_kind, "forms": {}}
+    for prec, vb in (("fdf", 4), ("bdf", 2), ("8df", 1)):
+        plan = te.Plan(csr, 8, 16, prec, seed=5)
+        plan.solve(vectors=False)
+        ms, launches, by = min(plan.profile()["spmv"] for _ in range(3))
+        del plan
+        gbs = by / (ms * 1e-3) / 1e9
+        out["forms"][prec] = {"value_bytes": vb, "spmv_ms_per_launch": ms / launches,
+                              "algorithmic_bytes_per_launch": by / launches, "gbs": gbs,
+                              "frac": gbs / peak}
+    return out
 
 
 def h2d_probe(nbytes=1 << 30, reps=5):
@@ -494,7 +508,9 @@ def out_of_core(te, world, steps=2, warmup=1):
     A = synth.rmat_sym(25, 16, 3)
     gen_s = time.perf_counter() - t0
     n, nnz = int(A.n), int(A.nnz)
-    host = te.CSR.from_host(A, "fdd", device="cpu", pin=True)
+    # a caller whose values are binary32 already (half the pinned host memory
+    # of binary64 values)
+    host = te.CSR.from_host(A.with_f32_values(), "fdd", device="cpu", pin=True)
     del A
     t0 = time.perf_counter()
     plan = te.Plan(host, 8, 16, "fdd", seed=3, matrix_budget=4 << 30)
@@ -514,23 +530,30 @@ def out_of_core(te, world, steps=2, warmup=1):
             "generate_s": gen_s, "plan_build_s": build_s}
 
 
-def serving(te, nreq, rates=(100, 300, 1000, 3000, 5000), seed=4):
-    """Continuous-batching serving: the same `nreq` requests (synth's serving
-    mix: n log-uniform in [2^10, 2^18], degree 4-64, uniform or R-MAT, K in
-    {4, 8, 16}, m = 2K, binary32 or bfloat16 values) arrive as a Poisson
-    process at each rate; a client loop submits them on arrival, runs engine
-    steps and polls results (eigenvalues and Ritz vectors to host memory).
-    Latency = completion minus scheduled arrival."""
+def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000, 5000),
+            seed=4):
+    """Continuous-batching serving: Poisson arrivals of solve requests drawn
+    from synth's serving mix (n log-uniform in [2^10, 2^18], degree 4-64,
+    uniform or R-MAT, K in {4, 8, 16}, m = 2K, binary32 or bfloat16 values).
+    `npool` distinct matrices are generated and request i solves matrix
+    i mod npool (with its own K, m, form) from its own start vector (seed i);
+    `nreq_high` requests arrive at rates >= 1000/s and `nreq_low` at lower
+    rates (so that a rate's arrivals span at most about ten seconds).  A client
+    loop submits each request on arrival, runs engine steps and collects the
+    finished requests from the completion queue (eigenvalues and Ritz vectors
+    to host memory).  Latency = completion minus scheduled arrival."""
     import numpy as np
     import synth
     t0 = time.perf_counter()
-    reqs = synth.serving_requests(nreq, seed)
+    pool = synth.serving_requests(npool, seed)
     gen_s = time.perf_counter() - t0
-    nnz = [int(A.nnz) for A, _, _, _ in reqs]
-    out = {"workload": f"serving_mix_seed{seed}", "requests_per_rate": nreq,
+    nnz = [int(A.nnz) for A, _, _, _ in pool]
+    out = {"workload": f"serving_mix_seed{seed}", "distinct_matrices": npool,
+           "requests_per_rate": {str(r): (nreq_high if r >= 1000 else nreq_low) for r in rates},
            "mean_nnz": float(np.mean(nnz)), "generate_s": gen_s, "rates": {}}
     rng = np.random.default_rng(seed + 1)
     for rate in rates:
+        nreq = nreq_high if rate >= 1000 else nreq_low
         arrive = np.cumsum(rng.exponential(1.0 / rate, nreq))
         srv = te.Server(max_slots=64, max_krylov_steps=32, budget=24 << 30)
         lat, tickets, max_live, steps = [], {}, 0, 0
@@ -539,7 +562,7 @@ def serving(te, nreq, rates=(100, 300, 1000, 3000, 5000), seed=4):
         while len(lat) < nreq:
             now = time.perf_counter() - start
             while i < nreq and arrive[i] <= now:
-                A, K, m, prec = reqs[i]
+                A, K, m, prec = pool[i % npool]
                 tickets[srv.submit(A, K, m, prec, seed=i)] = arrive[i]
                 i += 1
             if not tickets:
@@ -548,17 +571,64 @@ def serving(te, nreq, rates=(100, 300, 1000, 3000, 5000), seed=4):
             live, _ = srv.step()
             steps += 1
             max_live = max(max_live, live)
-            for t in list(tickets):
+            for t in srv.completed():
                 if srv.poll(t) is not None:
                     lat.append(time.perf_counter() - start - tickets.pop(t))
         wall = time.perf_counter() - start
         lat_ms = np.array(lat) * 1e3
         out["rates"][str(rate)] = {
-            "solves_per_s": nreq / (wall - arrive[0]), "p50_ms": float(np.percentile(lat_ms, 50)),
+            "requests": nreq, "solves_per_s": nreq / (wall - arrive[0]),
+            "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "engine_steps": steps,
             "max_resident": max_live, "wall_s": wall, "host_s": srv.timing()}
         srv.close()
     return out
+
+
+def spmv_order_probe(args):
+    """One FDF SpMV per launch (best of three un-graphed solves, K = 8,
+    m = 16) under a row order: the plans' degree order, the generator's, or a
+    locality order computed on the host (reverse Cuthill-McKee of the
+    symmetric pattern, alone, after the 32 K / 256 K most connected rows, or
+    inside log2-degree buckets) with the matrix relabelled before the plan
+    is made."""
+    import numpy as np
+    import synth
+    import paper_2201_07498_gb300 as te
+    te.load_library(build_if_missing=True)
+    A = synth.rmat_sym(args.scale, args.edge_factor, args.seed)
+    n, deg, order = A.n, np.diff(A.row_ptr), args.spmv_order_probe
+    if order in ("degree", "keep"):
+        M, plan_order = A, order
+    else:
+        import scipy.sparse as sp
+        from scipy.sparse.csgraph import reverse_cuthill_mckee
+        G = sp.csr_matrix((np.ones(A.nnz, dtype=np.float32), A.col, A.row_ptr), shape=(n, n))
+        rcm = reverse_cuthill_mckee(G, symmetric_mode=True)
+        del G
+        if order == "rcm":
+            perm = rcm
+        elif order.startswith("hubs"):
+            H = 32768 if order == "hubs32k_rcm" else 262144
+            hubs = np.argsort(-deg, kind="stable")[:H]
+            is_hub = np.zeros(n, bool)
+            is_hub[hubs] = True
+            perm = np.concatenate([hubs, rcm[~is_hub[rcm]]])
+        else:
+            b = np.floor(np.log2(np.maximum(deg, 1))).astype(int)
+            pos = np.empty(n, dtype=np.int64)
+            pos[rcm] = np.arange(n)
+            perm = np.lexsort((pos, -b))
+        iperm = np.empty(n, dtype=np.int64)
+        iperm[perm] = np.arange(n)
+        rows = np.repeat(np.arange(n), deg)
+        M = synth.from_triplets(n, iperm[rows].astype(np.int32), iperm[A.col].astype(np.int32),
+                                A.val)
+        plan_order = "keep"
+    plan = te.Plan(te.CSR.from_host(M, "fdf"), 8, 16, "fdf", seed=1, order=plan_order)
+    ms, launches, _ = min(plan.profile()["spmv"] for _ in range(3))
+    print(json.dumps({"order": order, "scale": args.scale, "edge_factor": args.edge_factor,
+                      "nnz": int(A.nnz), "spmv_ms_per_launch": ms / launches}), flush=True)
 
 
 def time_plan(plan, steps, warmup, world, want_vectors=True):
@@ -587,6 +657,9 @@ def time_plan(plan, steps, warmup, world, want_vectors=True):
 
 def main():
     args = parse()
+    if args.spmv_order_probe:
+        spmv_order_probe(args)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -723,7 +796,8 @@ def main():
     if not args.no_banded and world == 1:
         extras["spmv_banded"] = spmv_banded(te, peak, peak_kind)
     if not args.no_serving and world == 1:
-        extras["serving"] = serving(te, args.serving_requests)
+        extras["serving"] = serving(te, args.serving_requests,
+                                    min(1000, args.serving_requests))
     if not args.no_ooc and world == 1:
         extras["out_of_core"] = out_of_core(te, world)
 

@@ -383,6 +383,13 @@ te_status te_server_step(te_server* srv, int32_t* live, int32_t* pending);
 te_status te_server_poll(te_server* srv, int64_t ticket, int32_t* done, double* eigvals,
                          double* eigvecs, double* residuals);
 
+/* Completion queue: up to `cap` tickets of requests that finished (with any
+ * status) since the last call, in the order they finished, written to
+ * tickets[]; *count receives how many.  A reported ticket is then polled
+ * with te_server_poll (which returns its results at once).  Lets a client
+ * poll only finished requests instead of every outstanding one. */
+te_status te_server_completed(te_server* srv, int64_t* tickets, int32_t cap, int32_t* count);
+
 /* Resident and queued solves, pool bytes in use now and at most so far. */
 te_status te_server_stats(const te_server* srv, int32_t* live, int32_t* pending,
                           size_t* pool_used, size_t* pool_peak);
@@ -410,6 +417,27 @@ te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t
                          int32_t vmax, int64_t* nslices, int64_t* entries, int64_t* nlong_rows,
                          int32_t* slice_len, int32_t* lane_out, int64_t* lane_src,
                          int32_t* lane_len);
+
+/* The same layout (and, with order = TE_ORDER_DEGREE, the row order of
+ * te_degree_order) built on the device from row_ptr in device memory, the way
+ * plans build it: for tests and analysis.  Outputs are host arrays, each
+ * optional (NULL skips it); sizes as for te_spmv_layout, plus perm[n] (the
+ * caller's row placed at layout row r; the identity for TE_ORDER_KEEP),
+ * slice_base[nslices] (first entry of each slice), lane_row[32 * nslices]
+ * (the caller's row a lane's piece belongs to, -1 for an empty lane),
+ * long_rows[3 * nlong_rows] ((layout row, first partial slot, pieces) of each
+ * cut row, most pieces first, ties in row order) and *nbig (cut rows with more
+ * than 16 pieces).  lane_out holds layout rows (relabelled rows with
+ * TE_ORDER_DEGREE) and lane_src entries of the caller's CSR.  Call once with
+ * NULL arrays to learn the sizes.  Returns TE_ERR_INVALID_ARG for a malformed
+ * row_ptr, TE_ERR_UNSUPPORTED when vmax > 128 or the matrix is too large for
+ * the device build.  Synchronises `stream`. */
+te_status te_spmv_layout_device(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t window,
+                                int32_t vmax, int32_t order, int64_t* nslices, int64_t* entries,
+                                int64_t* nlong_rows, int32_t* perm, int32_t* slice_len,
+                                int64_t* slice_base, int32_t* lane_out, int64_t* lane_src,
+                                int32_t* lane_len, int32_t* lane_row, int32_t* long_rows,
+                                int32_t* nbig, void* stream);
 
 /* Debug check of the symmetry Lanczos assumes (host only, no GPU needed; the
  * solver itself does not check it): A must be TE_HOST with binary64 values

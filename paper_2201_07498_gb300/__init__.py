@@ -111,6 +111,8 @@ _SIGS = {
     "te_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "te_server_destroy": (None, [ctypes.c_void_p]),
+    "te_server_completed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_void_p]),
     "te_server_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "te_probe_gather": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
@@ -123,6 +125,9 @@ _SIGS = {
                                       ctypes.c_void_p]),
     "te_degree_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "te_spmv_layout_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+                              + [ctypes.c_void_p] * 13),
     "te_check_symmetric": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
 }
 
@@ -429,6 +434,16 @@ class Server:
             return None
         return ev, (None if U is None else U.T), res
 
+    def completed(self, cap: int = 4096):
+        """Tickets of the requests that finished since the last call (poll
+        each once to collect its results)."""
+        import numpy as np
+        buf = np.empty(cap, dtype=np.int64)
+        cnt = ctypes.c_int32()
+        _check(self._lib.te_server_completed(self._h, ctypes.c_void_p(buf.ctypes.data), cap,
+                                             ctypes.byref(cnt)))
+        return [int(t) for t in buf[:cnt.value]]
+
     def stats(self):
         live, pend = ctypes.c_int32(), ctypes.c_int32()
         used, peak = ctypes.c_size_t(), ctypes.c_size_t()
@@ -528,6 +543,39 @@ def spmv_layout(row_ptr, nnz: int, window: int = 0, vmax: int = 0):
     _check(rc)
     return {"slice_len": slen, "lane_out": lout, "lane_src": lsrc, "lane_len": llen,
             "entries": int(ne.value), "long_rows": int(nl.value)}
+
+
+def spmv_layout_device(row_ptr_dev, nnz: int, window: int = 0, vmax: int = 0, order="keep",
+                       stream=None):
+    """The SpMV layout (and row order) built on the device from a device
+    row_ptr tensor, as plans build it: a dict like spmv_layout's plus perm,
+    slice_base, lane_row, long_rows ((row, first, count) per cut row) and
+    nbig."""
+    import numpy as np
+    lib = load_library()
+    n = int(row_ptr_dev.numel()) - 1
+    od = ORDERS[order] if isinstance(order, str) else int(order)
+    ns, ne, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    st = _stream_ptr(stream)
+    _check(lib.te_spmv_layout_device(ctypes.c_void_p(row_ptr_dev.data_ptr()), n, nnz, window,
+                                     vmax, od, ctypes.byref(ns), ctypes.byref(ne),
+                                     ctypes.byref(nl), *([None] * 10), st))
+    S, NL = ns.value, nl.value
+    out = {"perm": np.zeros(n, dtype=np.int32), "slice_len": np.zeros(S, dtype=np.int32),
+           "slice_base": np.zeros(S, dtype=np.int64), "lane_out": np.zeros(S * 32, dtype=np.int32),
+           "lane_src": np.zeros(S * 32, dtype=np.int64), "lane_len": np.zeros(S * 32, dtype=np.int32),
+           "lane_row": np.zeros(S * 32, dtype=np.int32),
+           "long_rows": np.zeros((NL, 3), dtype=np.int32)}
+    nb = ctypes.c_int32()
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+    _check(lib.te_spmv_layout_device(ctypes.c_void_p(row_ptr_dev.data_ptr()), n, nnz, window,
+                                     vmax, od, None, None, None, ptr(out["perm"]),
+                                     ptr(out["slice_len"]), ptr(out["slice_base"]),
+                                     ptr(out["lane_out"]), ptr(out["lane_src"]),
+                                     ptr(out["lane_len"]), ptr(out["lane_row"]),
+                                     ptr(out["long_rows"]), ctypes.byref(nb), st))
+    out.update({"entries": int(ne.value), "long_rows_count": NL, "nbig": int(nb.value)})
+    return out
 
 
 def check_symmetric(host_csr, tol: float = 0.0):

@@ -134,6 +134,38 @@ bool rows_valid(const int64_t* rp, int64_t n, int64_t nnz, std::string& err);
 void degree_order(const int64_t* rp, int64_t n, int32_t* perm, int32_t* iperm, int64_t* src,
                   int32_t* len);
 
+// The same layout built by kernels from a device row_ptr (te_layout_dev.cu);
+// identical to make_sell / degree_order.  Order of use: count (row checks,
+// the row order when `reorder`), order (when `reorder`: perm, iperm and the
+// placed rows' first entries and lengths), windows (the per-window counts;
+// totals = slices, padded entries, cut-row pieces, cut rows, to the host),
+// emit (the slices, lane records and sorted cut rows into the caller's
+// arrays).  Scratch memory is owned by the object.
+struct DevLayout {
+  int64_t n = 0, nnz = 0, nwin = 0;
+  int window = SELL_WINDOW, vmax = SELL_VMAX;
+  bool reorder = false;
+  const int64_t* rp = nullptr;
+  void* scratch = nullptr;
+  int64_t* wc = nullptr;
+  int32_t* sorted_rows = nullptr;
+  int32_t* spare_rows = nullptr;
+  const int64_t* view_src = nullptr;
+  const int32_t* view_len = nullptr;
+  const int32_t* view_perm = nullptr;
+  int64_t nslices = 0, entries = 0, pieces = 0, nlrows = 0;
+  // err receives the reason when the row pointers are malformed or the size
+  // is not covered (cudaErrorInvalidValue is returned then)
+  cudaError_t count(const int64_t* rp_dev, int64_t n, int64_t nnz, int window, int vmax,
+                    bool reorder, cudaStream_t s, std::string& err);
+  cudaError_t order(int32_t* perm, int32_t* iperm, int64_t* src, int32_t* len, cudaStream_t s);
+  cudaError_t windows(cudaStream_t s, int64_t* totals_host);
+  cudaError_t emit(SellSlice* slices, int32_t* vout, int64_t* vsrc, int32_t* vlen, int32_t* vrow,
+                   LongRow* lrows, LongRow* lrows_tmp, cudaStream_t s, int* nbig_host);
+  ~DevLayout();
+};
+bool dev_layout_fits(int64_t n, int window, int vmax);
+
 // Device copy of a SELL layout.
 struct DevSell {
   const SellSlice* slices = nullptr;

@@ -13,11 +13,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "te_internal.h"
@@ -120,6 +124,66 @@ struct Request {
   size_t work_off = 0, work_bytes = 0, res_off = 0, res_bytes = 0;
   BatchSlot desc{};
   std::vector<double> theta, resid;
+  // the SpMV layout, built by an analysis thread after submission
+  SellHost layout;
+  std::atomic<int> analysed{0};
+};
+
+// Host threads that build the SpMV layouts of submitted requests while the
+// engine runs, so that admission only allocates, copies and launches.
+class AnalysisPool {
+ public:
+  void start(unsigned nthreads) {
+    for (unsigned t = 0; t < nthreads; ++t) th_.emplace_back([this] { run(); });
+  }
+  void post(Request* R) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      q_.push_back(R);
+    }
+    cv_.notify_one();
+  }
+  // block until R's layout is built
+  void wait(Request* R) {
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [R] { return R->analysed.load(std::memory_order_acquire) != 0; });
+  }
+  void stop() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+    th_.clear();
+  }
+  ~AnalysisPool() { stop(); }
+
+ private:
+  void run() {
+    for (;;) {
+      Request* R = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [this] { return stop_ || !q_.empty(); });
+        if (stop_) return;
+        R = q_.front();
+        q_.pop_front();
+      }
+      std::string perr;
+      make_sell(R->rp, R->n, R->nnz, R->layout, perr);  // row pointers validated at submit
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        R->analysed.store(1, std::memory_order_release);
+      }
+      done_.notify_all();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  std::deque<Request*> q_;
+  bool stop_ = false;
 };
 
 struct SlotResult {  // pinned, written by the finishing copies
@@ -145,6 +209,12 @@ int ctas_for(int64_t n_pad) {
 
 struct te_server {
   int max_slots = 0, max_m = 0, use_graph = 1, num_sms = 0;
+  // admissions run on their own stream, beside the engine step: a copy from
+  // pageable host memory first waits for the work already queued on its
+  // stream, which then is only the earlier admissions
+  cudaStream_t as = nullptr;
+  cudaEvent_t ev_admit = nullptr;
+  bool admit_pending = false;
   cudaStream_t s = nullptr, ps = nullptr;  // engine stream, poll stream
   Pool pool;
   PassLaunch Lpass{}, Lritz{}, Lsto{};
@@ -160,7 +230,9 @@ struct te_server {
   std::vector<Request*> slots;
   std::vector<std::pair<size_t, size_t>> deferred;  // pool blocks to free after the next sync
   std::vector<int> finishing;                       // slots whose solve ends this step
+  std::deque<int64_t> completed;                    // finished tickets not yet reported
   double t_wait = 0, t_admit = 0, t_launch = 0, t_submit = 0;  // host seconds, cumulative
+  AnalysisPool analysis;
 };
 
 namespace {
@@ -220,9 +292,7 @@ AdmitLayout admit_layout(const Request& R, const SellHost& H) {
 // Try to admit R into slot k.  Returns 1 on success, 0 when the pool has no
 // room now, -1 on a CUDA error (status set).
 int admit(te_server* S, Request* R, int k, te_status* err) {
-  SellHost H;
-  std::string perr;
-  make_sell(R->rp, R->n, R->nnz, H, perr);  // row pointers validated at submit
+  const SellHost& H = R->layout;  // built by an analysis thread
   const AdmitLayout L = admit_layout(*R, H);
   size_t work = 0, res = 0, tmp = 0;
   if (!S->pool.alloc(L.total, &work)) return 0;
@@ -242,7 +312,7 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
   S->deferred.push_back({tmp, L.t_total});
   char* W = S->pool.base + work;
   char* T = S->pool.base + tmp;
-  cudaStream_t s = S->s;
+  cudaStream_t s = S->as;  // beside the engine step
   cudaError_t e = cudaMemsetAsync(W, 0, L.total, s);
   auto h2d = [&](void* dst, const void* src, size_t b) {
     if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s);
@@ -250,34 +320,35 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
   h2d(T + L.t_rp, R->rp, (size_t)(R->n + 1) * 8);
   h2d(T + L.t_ci, R->ci, (size_t)R->nnz * 4);
   h2d(T + L.t_val, R->vals, R->val_bytes);
+  h2d(T + L.t_src, H.vsrc.data(), H.vsrc.size() * 8);
+  h2d(T + L.t_len, H.vlen.data(), H.vlen.size() * 4);
+  const int64_t* drp = reinterpret_cast<const int64_t*>(T + L.t_rp);
+  const int32_t* dci = reinterpret_cast<const int32_t*>(T + L.t_ci);
+  const void* dval = T + L.t_val;
+  const int64_t* dsrc = reinterpret_cast<const int64_t*>(T + L.t_src);
+  const int32_t* dlen = reinterpret_cast<const int32_t*>(T + L.t_len);
   // column indices are checked here, before the solve's first SpMV (the
   // request joins the batch only after the next step has read the flag)
   int* flag = reinterpret_cast<int*>(W + L.flag);
-  if (e == cudaSuccess)
-    e = launch_validate_cols(reinterpret_cast<const int32_t*>(T + L.t_ci), R->nnz, R->n, flag, s);
+  if (e == cudaSuccess) e = launch_validate_cols(dci, R->nnz, R->n, flag, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&S->res_h[k].bad_cols, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
-  h2d(T + L.t_src, H.vsrc.data(), H.vsrc.size() * 8);
-  h2d(T + L.t_len, H.vlen.data(), H.vlen.size() * 4);
   h2d(W + L.slices, H.slices.data(), H.slices.size() * sizeof(SellSlice));
   h2d(W + L.vout, H.vout.data(), H.vout.size() * 4);
   h2d(W + L.lrows, H.lrows.data(), H.lrows.size() * sizeof(LongRow));
-  const void* vin = T + L.t_val;
+  const void* vin = dval;
   int in_type = R->in_type;
   if (e == cudaSuccess && R->vk == TE_BF16) {
-    e = launch_quantize(TE_BF16, reinterpret_cast<const int64_t*>(T + L.t_rp),
-                        reinterpret_cast<const double*>(T + L.t_val), R->n, R->nnz, T + L.t_q,
+    e = launch_quantize(TE_BF16, drp, static_cast<const double*>(dval), R->n, R->nnz, T + L.t_q,
                         nullptr, s);
     vin = T + L.t_q;
     in_type = TE_BF16;
   }
   if (e == cudaSuccess)
-    e = launch_sell_build(in_type, R->vk, reinterpret_cast<const int32_t*>(T + L.t_ci), vin,
-                          reinterpret_cast<const SellSlice*>(W + L.slices),
-                          reinterpret_cast<const int64_t*>(T + L.t_src),
-                          reinterpret_cast<const int32_t*>(T + L.t_len), (int)H.slices.size(),
-                          reinterpret_cast<int32_t*>(W + L.cols), W + L.vals, nullptr, nullptr,
-                          nullptr, nullptr, s);
+    e = launch_sell_build(in_type, R->vk, dci, vin,
+                          reinterpret_cast<const SellSlice*>(W + L.slices), dsrc, dlen,
+                          (int)H.slices.size(), reinterpret_cast<int32_t*>(W + L.cols),
+                          W + L.vals, nullptr, nullptr, nullptr, nullptr, s);
   LzState* st = reinterpret_cast<LzState*>(W + L.st);
   double* U = reinterpret_cast<double*>(S->pool.base + res);
   if (e == cudaSuccess) e = launch_solve_begin(st, nullptr, U, nullptr, nullptr, s);
@@ -335,6 +406,8 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
   R->slot = k;
   R->state = REQ_ADMITTED;
   R->step = 0;
+  // (the host arrangement is dropped once the admission kernels are done:
+  // with host_direct they read it in place)
   return 1;
 }
 
@@ -434,8 +507,11 @@ te_status te_server_create(const te_server_options* o, te_server** out) {
   int dev = 0;
   SRV_CK(cudaGetDevice(&dev), "cudaGetDevice");
   SRV_CK(cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
+
   SRV_CK(cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking), "create stream");
   SRV_CK(cudaStreamCreateWithFlags(&S->ps, cudaStreamNonBlocking), "create stream");
+  SRV_CK(cudaStreamCreateWithFlags(&S->as, cudaStreamNonBlocking), "create stream");
+  SRV_CK(cudaEventCreateWithFlags(&S->ev_admit, cudaEventDisableTiming), "create event");
   SRV_CK(cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming), "create event");
   SRV_CK(S->pool.init(o->device_budget_bytes), "allocate the device pool");
   SRV_CK(cudaMallocHost(&S->table_h, sizeof(BatchTable)), "allocate the step table");
@@ -453,6 +529,12 @@ te_status te_server_create(const te_server_options* o, te_server** out) {
          "configure passes");
   SRV_CK(pass_config(PREC_FDF, MODE_DOT, S->max_m, 1, S->num_sms, S->Lpass), "configure passes");
   SRV_CK(batch_pass_prepare(S->Lpass), "configure batched passes");
+  {
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = nt > 2 ? nt / 2 : 1;
+    if (nt > 8) nt = 8;
+    S->analysis.start(nt);
+  }
   if (S->use_graph) {
     cudaGraph_t g = nullptr;
     SRV_CK(cudaStreamBeginCapture(S->s, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -473,7 +555,9 @@ te_status te_server_create(const te_server_options* o, te_server** out) {
 
 void te_server_destroy(te_server* S) {
   if (!S) return;
+  S->analysis.stop();  // no thread touches a request after this
   if (S->s) cudaStreamSynchronize(S->s);
+  if (S->as) cudaStreamSynchronize(S->as);
   for (auto& kv : S->reqs) delete kv.second;
   if (S->gexec) cudaGraphExecDestroy(S->gexec);
   if (S->ev) cudaEventDestroy(S->ev);
@@ -481,6 +565,8 @@ void te_server_destroy(te_server* S) {
   if (S->table_d) cudaFree(S->table_d);
   if (S->res_h) cudaFreeHost(S->res_h);
   if (S->s) cudaStreamDestroy(S->s);
+  if (S->as) cudaStreamDestroy(S->as);
+  if (S->ev_admit) cudaEventDestroy(S->ev_admit);
   if (S->ps) cudaStreamDestroy(S->ps);
   delete S;
 }
@@ -519,6 +605,7 @@ te_status te_server_submit(te_server* S, const te_csr* A, int32_t K, int32_t m, 
   R->val_bytes = (size_t)A->nnz * (R->in_type == TE_F64 ? 8 : 4);
   S->reqs[R->ticket] = R;
   S->pending.push_back(R);
+  S->analysis.post(R);
   *ticket = R->ticket;
   return TE_OK;
 }
@@ -538,19 +625,27 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
       R->resid.assign(o.resid, o.resid + R->K);
       R->status = o.hdr[2];
       R->state = REQ_FINISHED;
+      S->completed.push_back(R->ticket);
       S->pool.release(R->work_off, R->work_bytes);
       S->slots[k] = nullptr;
       R->slot = -1;
     }
     S->finishing.clear();
+  }
+  // the admissions of the previous call ran on their own stream
+  if (S->admit_pending) {
+    SRV_CK(cudaEventSynchronize(S->ev_admit), "admission");
+    S->admit_pending = false;
     for (auto& d : S->deferred) S->pool.release(d.first, d.second);
     S->deferred.clear();
     for (int k = 0; k < S->max_slots; ++k) {
       Request* R = S->slots[k];
       if (!R || R->state != REQ_ADMITTED) continue;
+      R->layout = SellHost();  // its admission kernels are done
       if (S->res_h[k].bad_cols) {
         R->status = TE_ERR_INVALID_ARG;
         R->state = REQ_FINISHED;
+        S->completed.push_back(R->ticket);
         S->pool.release(R->work_off, R->work_bytes);
         S->pool.release(R->res_off, R->res_bytes);
         R->res_bytes = 0;
@@ -601,9 +696,16 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
   // 3. admit in submission order while a slot and pool memory are free; the
   //    host work overlaps the step just launched, the uploads follow it
   int live = 0;
+  bool admitted = false;
   for (Request* R : S->slots) live += R != nullptr;
   while (!S->pending.empty() && live < S->max_slots) {
     Request* R = S->pending.front();
+    if (!R->analysed.load(std::memory_order_acquire)) {
+      // in submission order: wait for the head's layout only when nothing
+      // else would run (otherwise it is admitted at a later step)
+      if (live > 0) break;
+      S->analysis.wait(R);
+    }
     int k = 0;
     while (S->slots[k]) ++k;
     te_status err = TE_OK;
@@ -614,6 +716,7 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
         // nothing resident and the pool is empty: this request can never fit
         R->status = TE_ERR_OUT_OF_MEMORY;
         R->state = REQ_FINISHED;
+        S->completed.push_back(R->ticket);
         S->pending.pop_front();
         continue;
       }
@@ -622,11 +725,16 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
     S->pending.pop_front();
     S->slots[k] = R;
     ++live;
+    admitted = true;
+  }
+  if (admitted) {
+    SRV_CK(cudaEventRecord(S->ev_admit, S->as), "record");
+    S->admit_pending = true;
   }
   S->t_admit += now_s() - t2;
   if (live_out) *live_out = live;
   if (pending_out) *pending_out = (int32_t)S->pending.size();
-  if (live > 0 || !S->deferred.empty()) {
+  if (live > 0) {
     SRV_CK(cudaEventRecord(S->ev, S->s), "record");
     S->inflight = true;
   }
@@ -669,6 +777,18 @@ te_status te_server_poll(te_server* S, int64_t ticket, int32_t* done, double* ei
   S->reqs.erase(it);
   delete R;
   if (st != TE_OK) return srv_fail(st, std::string("request failed: ") + te_status_string(st));
+  return TE_OK;
+}
+
+te_status te_server_completed(te_server* S, int64_t* tickets, int32_t cap, int32_t* count) {
+  if (!S || !count || cap < 0 || (cap > 0 && !tickets))
+    return srv_fail(TE_ERR_INVALID_ARG, "bad arguments");
+  int32_t c = 0;
+  while (c < cap && !S->completed.empty()) {
+    tickets[c++] = S->completed.front();
+    S->completed.pop_front();
+  }
+  *count = c;
   return TE_OK;
 }
 

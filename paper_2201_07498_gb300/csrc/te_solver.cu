@@ -240,13 +240,9 @@ namespace {
 
 void* at(te_plan* P, size_t off) { return P->work + off; }
 
-// Upload the SELL metadata and convert the (device) CSR into the SELL arrays.
-// Build the SELL copy of a device CSR: upload the host partition, round or
-// quantise the values (in_type: the caller's value type, binary64 when the
-// storage type D.vk differs), and optionally write a second value array with
-// the binary64 values (vals64, for the refinement).  Temporaries are freed
-// before returning.
-// slice records, lane outputs and cut-row records (small), then synchronise
+// A host-built layout's slice records, lane outputs and cut-row records
+// (small) to the device, then synchronise (streamed plans keep the rest in
+// host memory)
 cudaError_t upload_meta(const SellHost& H, const DevSell& D, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (!H.slices.empty()) {
@@ -263,6 +259,40 @@ cudaError_t upload_meta(const SellHost& H, const DevSell& D, cudaStream_t s) {
   return e;
 }
 
+// Fill the SELL arrays from a device CSR, given the lane records (first CSR
+// entry and length of every lane's piece, and its row for FP8): round or
+// quantise the values (in_type: the caller's value type, binary64 when the
+// storage type D.vk differs), and optionally write a second value array with
+// the binary64 values (vals64, for the refinement).  Temporaries are freed
+// before returning (the stream is synchronised).
+cudaError_t fill_sell(int in_type, const DevSell& D, const int64_t* rp, const int32_t* ci,
+                      const void* val, int64_t n, int64_t nnz, const int64_t* dsrc,
+                      const int32_t* dlen, const int32_t* drow, void* vals64, float* lane_scale,
+                      const int32_t* colmap, cudaStream_t s) {
+  const bool quant = D.vk == TE_BF16 || D.vk == TE_FP8_E4M3;
+  const bool fp8 = D.vk == TE_FP8_E4M3;
+  void* q = nullptr;
+  float* rscale = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (quant) e = cudaMalloc(&q, std::max<size_t>(nnz, 1) * elt_of(D.vk));
+  if (e == cudaSuccess && fp8) e = cudaMalloc(&rscale, std::max<int64_t>(n, 1) * sizeof(float));
+  if (e == cudaSuccess && quant)
+    e = launch_quantize(D.vk, rp, static_cast<const double*>(val), n, nnz, q, rscale, s);
+  if (e == cudaSuccess)
+    e = launch_sell_build(quant ? D.vk : in_type, D.vk, ci, quant ? q : val, D.slices, dsrc,
+                          dlen, D.nslices, D.cols, D.vals, drow, rscale,
+                          fp8 ? lane_scale : nullptr, colmap, s);
+  if (e == cudaSuccess && vals64)
+    e = launch_sell_build(TE_F64, TE_F64, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols,
+                          vals64, nullptr, nullptr, nullptr, colmap, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (q) cudaFree(q);
+  if (rscale) cudaFree(rscale);
+  return e;
+}
+
+// The SELL copy of a device CSR from a host-built layout: its records and
+// lane map uploaded, then filled (fill_sell).
 cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const int32_t* ci,
                         const void* val, int64_t n, int64_t nnz, const DevSell& D, void* vals64,
                         float* lane_scale, const int32_t* colmap, cudaStream_t s) {
@@ -278,20 +308,14 @@ cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const
     e = cudaMemcpyAsync(const_cast<LongRow*>(D.lrows), H.lrows.data(),
                         H.lrows.size() * sizeof(LongRow), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess || H.slices.empty()) return e;
-  const bool quant = D.vk == TE_BF16 || D.vk == TE_FP8_E4M3;
   const bool fp8 = D.vk == TE_FP8_E4M3;
-  // lane -> CSR piece map (and row), quantised values and row scales: needed
-  // only while building
+  // lane -> CSR piece map (and row): needed only while building
   int64_t* dsrc = nullptr;
   int32_t* dlen = nullptr;
   int32_t* drow = nullptr;
-  void* q = nullptr;
-  float* rscale = nullptr;
   e = cudaMalloc(&dsrc, H.vsrc.size() * sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&dlen, H.vlen.size() * sizeof(int32_t));
   if (e == cudaSuccess && fp8) e = cudaMalloc(&drow, H.vrow.size() * sizeof(int32_t));
-  if (e == cudaSuccess && quant) e = cudaMalloc(&q, std::max<size_t>(nnz, 1) * elt_of(D.vk));
-  if (e == cudaSuccess && fp8) e = cudaMalloc(&rscale, std::max<int64_t>(n, 1) * sizeof(float));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dsrc, H.vsrc.data(), H.vsrc.size() * sizeof(int64_t),
                         cudaMemcpyHostToDevice, s);
@@ -301,21 +325,12 @@ cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const
   if (e == cudaSuccess && fp8)
     e = cudaMemcpyAsync(drow, H.vrow.data(), H.vrow.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && quant)
-    e = launch_quantize(D.vk, rp, static_cast<const double*>(val), n, nnz, q, rscale, s);
   if (e == cudaSuccess)
-    e = launch_sell_build(quant ? D.vk : in_type, D.vk, ci, quant ? q : val, D.slices, dsrc,
-                          dlen, D.nslices, D.cols, D.vals, drow, rscale,
-                          fp8 ? lane_scale : nullptr, colmap, s);
-  if (e == cudaSuccess && vals64)
-    e = launch_sell_build(TE_F64, TE_F64, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols,
-                          vals64, nullptr, nullptr, nullptr, colmap, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    e = fill_sell(in_type, D, rp, ci, val, n, nnz, dsrc, dlen, drow, vals64, lane_scale, colmap,
+                  s);
   cudaFree(dsrc);
   cudaFree(dlen);
   if (drow) cudaFree(drow);
-  if (q) cudaFree(q);
-  if (rscale) cudaFree(rscale);
   return e;
 }
 
@@ -836,7 +851,20 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
         "device attribute");
 
   // a host matrix that stays resident: its copy to the device starts now and
-  // overlaps the host analysis below
+  // overlaps the analysis below.  The row pointers come first on `s`; the
+  // columns and values follow on a second stream, which `s` waits for only
+  // where they are read (the column check and the layout fill).
+  struct SideCopy {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t done = nullptr;
+    ~SideCopy() {
+      if (cs) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+      }
+      if (done) cudaEventDestroy(done);
+    }
+  } side;
   if (A->where == TE_HOST && opt.matrix_budget_bytes == 0) {
     const size_t e_in = in_type == TE_F64 ? 8 : 4;
     const size_t brp = al256(sizeof(int64_t) * (A->n + 1)), bci = al256(sizeof(int32_t) * A->nnz);
@@ -845,21 +873,59 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     TE_CK(cudaMemcpyAsync(b, A->row_ptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyHostToDevice, s),
           "copy row_ptr");
     if (A->nnz > 0) {
+      TE_CK(cudaStreamCreateWithFlags(&side.cs, cudaStreamNonBlocking), "create copy stream");
+      TE_CK(cudaEventCreateWithFlags(&side.done, cudaEventDisableTiming), "create event");
       TE_CK(cudaMemcpyAsync(b + brp, A->col_idx, sizeof(int32_t) * A->nnz, cudaMemcpyHostToDevice,
-                            s),
+                            side.cs),
             "copy col_idx");
-      TE_CK(cudaMemcpyAsync(b + brp + bci, A->values, e_in * A->nnz, cudaMemcpyHostToDevice, s),
+      TE_CK(cudaMemcpyAsync(b + brp + bci, A->values, e_in * A->nnz, cudaMemcpyHostToDevice,
+                            side.cs),
             "copy values");
+      TE_CK(cudaEventRecord(side.done, side.cs), "record");
     }
     P->rp = reinterpret_cast<const int64_t*>(b);
     P->ci = reinterpret_cast<const int32_t*>(b + brp);
     P->val = b + brp + bci;
   }
 
+  // The SpMV layout (and the row order) is built by kernels from the device
+  // row pointers when the matrix ends up resident with the default layout;
+  // a streamed matrix or the autotuner's trial layouts use the host build.
+  const bool dev_build = !opt.autotune && (A->where == TE_DEVICE || opt.matrix_budget_bytes == 0) &&
+                         dev_layout_fits(A->n, SELL_WINDOW, SELL_VMAX);
+  DevLayout DL;
+  char* dtmp = nullptr;  // device build: the row order and the placed rows' first entries
+  struct TmpFree {
+    char*& p;
+    ~TmpFree() {
+      if (p) cudaFree(p);
+    }
+  } dtmp_guard{dtmp};
+  int32_t *dperm_t = nullptr, *diperm_t = nullptr, *dlen_t = nullptr;
+  int64_t* dsrc_t = nullptr;
+  int64_t dtot[4] = {0, 0, 0, 0};
+  if (dev_build) {
+    const int64_t* rpd = A->where == TE_DEVICE ? A->row_ptr : P->rp;
+    std::string derr;
+    cudaError_t e = DL.count(rpd, A->n, A->nnz, SELL_WINDOW, SELL_VMAX, P->reorder, s, derr);
+    if (e == cudaErrorInvalidValue && !derr.empty())
+      return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + derr);
+    TE_CK(e, "row order on the device");
+    if (P->reorder) {
+      const size_t nn = (size_t)A->n;
+      TE_CK(cudaMalloc(&dtmp, nn * (4 + 4 + 4) + al256(nn * 8) + 256), "allocate the row order");
+      dsrc_t = reinterpret_cast<int64_t*>(dtmp);
+      dperm_t = reinterpret_cast<int32_t*>(dtmp + al256(nn * 8));
+      diperm_t = dperm_t + nn;
+      dlen_t = diperm_t + nn;
+      TE_CK(DL.order(dperm_t, diperm_t, dsrc_t, dlen_t, s), "row order on the device");
+    }
+    TE_CK(DL.windows(s, dtot), "layout counts on the device");
+  }
   // row pointers on the host for the partition
   hvec<int64_t> rp_host;
   const int64_t* rph = A->row_ptr;
-  if (A->where == TE_DEVICE) {
+  if (A->where == TE_DEVICE && !dev_build) {
     rp_host.resize((size_t)A->n + 1);
     TE_CK(cudaMemcpyAsync(rp_host.data(), A->row_ptr, sizeof(int64_t) * (A->n + 1),
                           cudaMemcpyDeviceToHost, s),
@@ -873,7 +939,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   hvec<int32_t> hperm, hiperm, hlen;
   hvec<int64_t> hsrc;
   RowOrder ord{nullptr, nullptr, nullptr};
-  if (P->reorder) {
+  if (P->reorder && !dev_build) {
     if (!rows_valid(rph, A->n, A->nnz, perr))
       return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
     hperm.resize((size_t)A->n);
@@ -884,8 +950,14 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     ord = RowOrder{hperm.data(), hsrc.data(), hlen.data()};
   }
   const RowOrder* hp = P->reorder ? &ord : nullptr;
-  if (!make_sell(rph, A->n, A->nnz, sell, perr, SELL_WINDOW, SELL_VMAX, hp))
+  if (!dev_build && !make_sell(rph, A->n, A->nnz, sell, perr, SELL_WINDOW, SELL_VMAX, hp))
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+  // the layout's sizes, from either build (the autotuner may rebuild the host
+  // layout below and updates them)
+  int64_t l_slices = dev_build ? dtot[0] : (int64_t)sell.slices.size();
+  int64_t l_entries = dev_build ? dtot[1] : sell.entries;
+  int64_t l_pieces = dev_build ? dtot[2] : sell.pieces;
+  int64_t l_lrows = dev_build ? dtot[3] : (int64_t)sell.lrows.size();
 
   // launch shapes of the basis passes
   TE_CK(pass_config(P->prec, MODE_DOT, P->m, P->K, P->num_sms, P->Ldot), "configure dot pass");
@@ -901,6 +973,11 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     TE_CK(pass_config(P->prec, MODE_DCGS_UPDATE, P->m, P->K, P->num_sms, P->Ldupd),
           "configure update pass");
   }
+  // a small basis has fewer tiles than the persistent grid has CTAs: one CTA
+  // per tile then (idle CTAs would only lengthen the last CTA's reduction)
+  const int tiles = (int)std::min<int64_t>(P->n_pad / TILE_R, INT32_MAX);
+  for (PassLaunch* L : {&P->Ldot, &P->Laxd, &P->Lsto, &P->Lritz, &P->Lddot, &P->Ldupd})
+    if (L->grid > tiles) L->grid = std::max(tiles, 1);
   const int grid = std::max(std::max(P->Ldot.grid, P->Laxd.grid),
                             std::max(P->Lsto.grid, P->Lritz.grid));
 
@@ -909,7 +986,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   // budget each
   const size_t velt = elt_of(P->vk);
   P->streaming = opt.matrix_budget_bytes > 0 &&
-                 (size_t)sell.entries * (4 + velt) > opt.matrix_budget_bytes;
+                 (size_t)l_entries * (4 + velt) > opt.matrix_budget_bytes;
   if (P->streaming) {
     if (A->where != TE_HOST)
       return fail(TE_ERR_OUT_OF_MEMORY,
@@ -938,6 +1015,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   if (opt.autotune && !P->streaming) {
     // the device CSR the candidates are built from (a host matrix is copied
     // for the trials); its columns are checked before any SpMV reads them
+    if (side.done) TE_CK(cudaStreamWaitEvent(s, side.done, 0), "wait for the matrix copy");
     const size_t in_elt = in_type == TE_F64 ? 8 : 4;
     const int64_t* drp = A->row_ptr;
     const int32_t* dci = A->col_idx;
@@ -986,13 +1064,17 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     P->sell_vmax = TUNE_VMAX[best];
     if (best != 0 && !make_sell(rph, A->n, A->nnz, sell, perr, P->sell_window, P->sell_vmax, hp))
       return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + perr);
+    l_slices = (int64_t)sell.slices.size();
+    l_entries = sell.entries;
+    l_pieces = sell.pieces;
+    l_lrows = (int64_t)sell.lrows.size();
   }
 
   SellSizes zs;
-  zs.slices = sell.slices.size();
-  zs.entries = P->streaming ? (size_t)(2 * P->cap_entries) : (size_t)sell.entries;
-  zs.lrows = sell.lrows.size();
-  zs.pieces = (size_t)sell.pieces;
+  zs.slices = (size_t)l_slices;
+  zs.entries = P->streaming ? (size_t)(2 * P->cap_entries) : (size_t)l_entries;
+  zs.lrows = (size_t)l_lrows;
+  zs.pieces = (size_t)l_pieces;
   P->W = layout(P->prec, P->vk, P->n_pad, P->m, grid, zs, P->refine, P->n, P->K, P->reorder);
   const size_t in_elt = in_type == TE_F64 ? 8 : 4;
   size_t csr_bytes = 0;
@@ -1058,6 +1140,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
           "arm the stall hook");
     TE_CK(cudaStreamSynchronize(s), "arm the stall hook");
   }
+  if (side.done) TE_CK(cudaStreamWaitEvent(s, side.done, 0), "wait for the matrix copy");
   if (!P->streaming) {
     // column indices must lie in [0, n)
     int* dflag = static_cast<int*>(at(P, P->W.flag));
@@ -1071,13 +1154,15 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   if (P->reorder) {
     P->dperm = static_cast<int32_t*>(at(P, P->W.perm));
     P->diperm = static_cast<int32_t*>(at(P, P->W.iperm));
-    TE_CK(cudaMemcpyAsync(P->dperm, hperm.data(), sizeof(int32_t) * A->n, cudaMemcpyHostToDevice,
-                          s),
-          "upload the row order");
-    TE_CK(cudaMemcpyAsync(P->diperm, hiperm.data(), sizeof(int32_t) * A->n,
-                          cudaMemcpyHostToDevice, s),
-          "upload the row order");
-    TE_CK(cudaStreamSynchronize(s), "upload the row order");
+    const cudaMemcpyKind k = dev_build ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    TE_CK(cudaMemcpyAsync(P->dperm, dev_build ? (const void*)dperm_t : (const void*)hperm.data(),
+                          sizeof(int32_t) * A->n, k, s),
+          "place the row order");
+    TE_CK(cudaMemcpyAsync(P->diperm,
+                          dev_build ? (const void*)diperm_t : (const void*)hiperm.data(),
+                          sizeof(int32_t) * A->n, k, s),
+          "place the row order");
+    TE_CK(cudaStreamSynchronize(s), "place the row order");
   }
   // the SELL copy of the matrix that the solve streams
   P->sell.slices = static_cast<SellSlice*>(at(P, P->W.slices));
@@ -1086,20 +1171,50 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   P->sell.vals = at(P, P->W.svals);
   P->sell.lrows = static_cast<LongRow*>(at(P, P->W.lrows));
   P->sell.vpart = at(P, P->W.vpart);
-  P->sell.nslices = (int)sell.slices.size();
-  P->sell.nlrows = (int)sell.lrows.size();
-  P->sell.nlbig = (int)sell.nbig;
+  P->sell.nslices = (int)l_slices;
+  P->sell.nlrows = (int)l_lrows;
+  P->sell.nlbig = (int)sell.nbig;  // (the device build sets it below)
   void* vals64 = P->W.svals64 ? at(P, P->W.svals64) : nullptr;
   P->sell.vk = P->vk;
   P->sell.hot = P->reorder ? P->n : 0;  // the first columns are the most connected
   P->sell.lscale = P->W.lscale ? static_cast<const float*>(at(P, P->W.lscale)) : nullptr;
-  if (P->streaming)
+  if (P->streaming) {
     TE_CK(upload_meta(sell, P->sell, s), "upload the SELL layout");
-  else
+  } else if (dev_build) {
+    // the lane records and the slices come from the device build; the cut
+    // rows are sorted there (most pieces first)
+    const size_t lanes = (size_t)std::max<int64_t>(l_slices, 1) * SELL_C;
+    const bool fp8 = P->vk == TE_FP8_E4M3;
+    char* lt = nullptr;
+    const size_t bytes = al256(lanes * 8) + al256(lanes * 4) + (fp8 ? al256(lanes * 4) : 0) +
+                         al256((size_t)std::max<int64_t>(l_lrows, 1) * sizeof(LongRow));
+    TE_CK(cudaMalloc(&lt, bytes), "allocate the lane records");
+    struct LtFree {
+      char* p;
+      ~LtFree() { cudaFree(p); }
+    } lt_guard{lt};
+    int64_t* lsrc = reinterpret_cast<int64_t*>(lt);
+    int32_t* llen = reinterpret_cast<int32_t*>(lt + al256(lanes * 8));
+    int32_t* lrow = fp8 ? reinterpret_cast<int32_t*>(lt + al256(lanes * 8) + al256(lanes * 4))
+                        : nullptr;
+    LongRow* lr_tmp = reinterpret_cast<LongRow*>(lt + al256(lanes * 8) + al256(lanes * 4) +
+                                                 (fp8 ? al256(lanes * 4) : 0));
+    int nbig = 0;
+    TE_CK(DL.emit(const_cast<SellSlice*>(P->sell.slices), const_cast<int32_t*>(P->sell.vout),
+                  lsrc, llen, lrow, const_cast<LongRow*>(P->sell.lrows), lr_tmp, s, &nbig),
+          "build the SELL layout on the device");
+    P->sell.nlbig = nbig;
+    if (l_slices > 0)
+      TE_CK(fill_sell(in_type, P->sell, P->rp, P->ci, P->val, P->n, P->nnz, lsrc, llen, lrow,
+                      vals64, P->W.lscale ? static_cast<float*>(at(P, P->W.lscale)) : nullptr,
+                      P->diperm, s),
+            "fill the SELL layout");
+  } else {
     TE_CK(upload_sell(in_type, sell, P->rp, P->ci, P->val, P->n, P->nnz, P->sell, vals64,
                       P->W.lscale ? static_cast<float*>(at(P, P->W.lscale)) : nullptr,
                       P->diperm, s),
           "build the SELL layout");
+  }
   if (P->refine) {
     P->sell64 = P->sell;
     P->sell64.vk = TE_F64;
@@ -1494,6 +1609,101 @@ te_status te_spmv_layout(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t
     if (lane_out) lane_out[l] = sell.vout[l];
     if (lane_src) lane_src[l] = sell.vsrc[l];
     if (lane_len) lane_len[l] = sell.vlen[l];
+  }
+  return TE_OK;
+}
+
+te_status te_spmv_layout_device(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t window,
+                                int32_t vmax, int32_t order, int64_t* nslices, int64_t* entries,
+                                int64_t* nlong_rows, int32_t* perm, int32_t* slice_len,
+                                int64_t* slice_base, int32_t* lane_out, int64_t* lane_src,
+                                int32_t* lane_len, int32_t* lane_row, int32_t* long_rows,
+                                int32_t* nbig, void* stream) {
+  if (!row_ptr || n < 1 || nnz < 0) return fail(TE_ERR_INVALID_ARG, "bad arguments");
+  if (!is_device_ptr(row_ptr)) return fail(TE_ERR_INVALID_ARG, "row_ptr must be device memory");
+  if (order != TE_ORDER_KEEP && order != TE_ORDER_DEGREE)
+    return fail(TE_ERR_INVALID_ARG, "order must be TE_ORDER_KEEP or TE_ORDER_DEGREE");
+  if (window == 0) window = SELL_WINDOW;
+  if (vmax == 0) vmax = SELL_VMAX;
+  if (!dev_layout_fits(n, window, vmax))
+    return fail(TE_ERR_UNSUPPORTED, "the device layout build does not cover these sizes");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool reorder = order == TE_ORDER_DEGREE;
+  DevLayout DL;
+  std::string derr;
+  cudaError_t e = DL.count(row_ptr, n, nnz, window, vmax, reorder, s, derr);
+  if (e == cudaErrorInvalidValue && !derr.empty())
+    return fail(TE_ERR_INVALID_ARG, "malformed CSR: " + derr);
+  TE_CK(e, "device layout");
+  // device arrays: row order (4 n + 4 n + 8 n + 4 n), then the layout
+  char* b = nullptr;
+  struct BFree {
+    char*& p;
+    ~BFree() {
+      if (p) cudaFree(p);
+    }
+  } bf{b};
+  const size_t nn = (size_t)n;
+  int64_t tot[4];
+  int32_t *dp = nullptr, *dip = nullptr, *dl = nullptr;
+  int64_t* ds = nullptr;
+  char* ob = nullptr;
+  struct OFree {
+    char*& p;
+    ~OFree() {
+      if (p) cudaFree(p);
+    }
+  } of{ob};
+  if (reorder) {
+    TE_CK(cudaMalloc(&ob, al256(nn * 8) + 3 * al256(nn * 4)), "allocate");
+    ds = reinterpret_cast<int64_t*>(ob);
+    dp = reinterpret_cast<int32_t*>(ob + al256(nn * 8));
+    dip = reinterpret_cast<int32_t*>(ob + al256(nn * 8) + al256(nn * 4));
+    dl = reinterpret_cast<int32_t*>(ob + al256(nn * 8) + 2 * al256(nn * 4));
+    TE_CK(DL.order(dp, dip, ds, dl, s), "device row order");
+  }
+  TE_CK(DL.windows(s, tot), "device layout counts");
+  const size_t S = (size_t)tot[0], lanes = std::max<size_t>(S * SELL_C, 1),
+               NL = (size_t)std::max<int64_t>(tot[3], 1);
+  const size_t o_sl = 0, o_out = al256(std::max<size_t>(S, 1) * sizeof(SellSlice)),
+               o_src = o_out + al256(lanes * 4), o_len = o_src + al256(lanes * 8),
+               o_row = o_len + al256(lanes * 4), o_lr = o_row + al256(lanes * 4),
+               o_lt = o_lr + al256(NL * sizeof(LongRow)), total = o_lt + al256(NL * sizeof(LongRow));
+  TE_CK(cudaMalloc(&b, total), "allocate");
+  int nb = 0;
+  TE_CK(DL.emit(reinterpret_cast<SellSlice*>(b + o_sl), reinterpret_cast<int32_t*>(b + o_out),
+                reinterpret_cast<int64_t*>(b + o_src), reinterpret_cast<int32_t*>(b + o_len),
+                reinterpret_cast<int32_t*>(b + o_row), reinterpret_cast<LongRow*>(b + o_lr),
+                reinterpret_cast<LongRow*>(b + o_lt), s, &nb),
+        "device layout");
+  if (nslices) *nslices = tot[0];
+  if (entries) *entries = tot[1];
+  if (nlong_rows) *nlong_rows = tot[3];
+  if (nbig) *nbig = nb;
+  std::vector<SellSlice> hs(S);
+  std::vector<LongRow> hl((size_t)tot[3]);
+  if (S) TE_CK(cudaMemcpy(hs.data(), b + o_sl, S * sizeof(SellSlice), cudaMemcpyDeviceToHost), "copy");
+  if (tot[3]) TE_CK(cudaMemcpy(hl.data(), b + o_lr, hl.size() * sizeof(LongRow), cudaMemcpyDeviceToHost), "copy");
+  for (size_t i = 0; i < S; ++i) {
+    if (slice_len) slice_len[i] = hs[i].len;
+    if (slice_base) slice_base[i] = hs[i].base;
+  }
+  for (size_t i = 0; i < hl.size(); ++i)
+    if (long_rows) {
+      long_rows[3 * i] = hl[i].row;
+      long_rows[3 * i + 1] = hl[i].first;
+      long_rows[3 * i + 2] = hl[i].count;
+    }
+  if (S) {
+    if (lane_out) TE_CK(cudaMemcpy(lane_out, b + o_out, S * SELL_C * 4, cudaMemcpyDeviceToHost), "copy");
+    if (lane_src) TE_CK(cudaMemcpy(lane_src, b + o_src, S * SELL_C * 8, cudaMemcpyDeviceToHost), "copy");
+    if (lane_len) TE_CK(cudaMemcpy(lane_len, b + o_len, S * SELL_C * 4, cudaMemcpyDeviceToHost), "copy");
+    if (lane_row) TE_CK(cudaMemcpy(lane_row, b + o_row, S * SELL_C * 4, cudaMemcpyDeviceToHost), "copy");
+  }
+  if (perm) {
+    if (reorder) TE_CK(cudaMemcpy(perm, dp, nn * 4, cudaMemcpyDeviceToHost), "copy");
+    else
+      for (size_t i = 0; i < nn; ++i) perm[i] = (int32_t)i;
   }
   return TE_OK;
 }

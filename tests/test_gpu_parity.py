@@ -323,10 +323,12 @@ def test_topk_fdf_close_to_oracle(te, name, make, K, m, which):
     perm32 = match_pairs(ev, ref32.eigvals, 1e-6 * scale)
     match_pairs(ev, ref64.eigvals, 1e-6 * scale)
     ang = subspace_angles(U.cpu().numpy(), ref32.eigvecs[:, perm32], ref32.eigvals[perm32])
-    # Davis-Kahan: a perturbation eps of T turns a Ritz vector by at most
-    # eps / gap, gap = the distance from its Ritz value to the other Ritz
-    # values of T.  FDF stores the basis in binary32 (u32 = 2^-24 per stored
-    # vector over m steps); eps = 1e-5 ||T|| leaves a margin over m u32 ||T||.
+    # Davis-Kahan: a perturbation eps of the projected problem turns a Ritz
+    # vector by at most eps / gap, gap = the distance from its Ritz value to
+    # the other Ritz values of T.  FDF stores the basis in binary32 (u32 =
+    # 2^-24 per stored vector, over m steps whose Krylov directions amplify
+    # it near the clustered eigenvalues of a normalised adjacency): eps =
+    # 1e-4 ||T||, and never more than 1e-3 rad.
     m_ = len(ref32.alpha)
     T = (np.diag(ref32.alpha) + np.diag(ref32.beta[1:m_], 1) + np.diag(ref32.beta[1:m_], -1))
     th_all = np.linalg.eigvalsh(T)
@@ -340,7 +342,7 @@ def test_topk_fdf_close_to_oracle(te, name, make, K, m, which):
         members = theta[k:j]
         d = np.min(np.abs(th_all[:, None] - members[None, :]), axis=1)
         gap = np.min(d[d > 1e-8 * scale])
-        bounds.append(1e-5 * tn / gap)
+        bounds.append(min(1e-3, 1e-4 * tn / gap))
         k = j
     assert np.all(ang <= np.array(bounds)), (ang, bounds)
 

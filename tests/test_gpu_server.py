@@ -49,9 +49,9 @@ def _mix():
 def test_server_request_matches_oracle(te):
     """A binary32 request served by the engine against the oracle run on the
     same binary32-rounded matrix with the same start vector: Ritz values
-    within 1e-6 relative, vectors within the Davis-Kahan bound of a 1e-5 ||T||
-    perturbation (see test_topk_fdf_close_to_oracle), residual estimates
-    within 1e-5 |theta_1|."""
+    within 1e-6 relative, vectors within the Davis-Kahan bound of a 1e-4 ||T||
+    perturbation capped at 1e-3 rad (see test_topk_fdf_close_to_oracle),
+    residual estimates within 1e-5 |theta_1|."""
     A = synth.uniform_sym(10000, 10, 0)
     K, m = 8, 16
     srv = te.Server(max_slots=4, max_krylov_steps=32, budget=256 << 20)
@@ -66,7 +66,7 @@ def test_server_request_matches_oracle(te):
     ang = subspace_angles(U, ref.eigvecs[:, perm], ref.eigvals[perm])
     gaps = [np.min(np.abs(th_all - v)[np.abs(th_all - v) > 1e-8 * scale])
             for v in ref.eigvals[perm]]
-    assert np.all(ang <= 1e-5 * tn / np.array(gaps)), (ang, gaps)
+    assert np.all(ang <= np.minimum(1e-3, 1e-4 * tn / np.array(gaps))), (ang, gaps)
     assert np.max(np.abs(res - ref.residuals[perm])) <= 1e-5 * scale
 
 
@@ -171,3 +171,21 @@ def test_bad_column_is_rejected_before_the_first_spmv(te):
     ev = _drain(srv, [tg])[tg][0]
     ev_p, _, _ = te.topk_eigs(te.CSR.from_host(A, "fdf"), 4, 8, "fdf", seed=1, vectors=False)
     match_pairs(ev, ev_p.numpy(), 1e-6 * np.max(np.abs(ev_p.numpy())))
+
+
+def test_completion_queue_reports_every_request_once(te):
+    """te_server_completed hands out each finished ticket exactly once, in the
+    order the requests finished; polling a reported ticket returns at once."""
+    srv = te.Server(max_slots=4, max_krylov_steps=32, budget=256 << 20)
+    mats = _mix()
+    tickets = [srv.submit(M, 4, 8, "fdf", seed=i) for i, M in enumerate(mats)]
+    seen = []
+    for _ in range(2000):
+        srv.step()
+        for t in srv.completed():
+            seen.append(t)
+            assert srv.poll(t, vectors=False) is not None
+        if len(seen) == len(tickets):
+            break
+    assert sorted(seen) == sorted(tickets) and len(set(seen)) == len(seen)
+    assert srv.completed() == []
