@@ -351,6 +351,15 @@ typedef struct {
   int32_t max_krylov_steps;   /* largest m accepted, <= 64 */
   size_t device_budget_bytes; /* device pool for resident solves and finished results */
   int32_t use_graph;          /* replay each engine step as one captured CUDA graph */
+  int32_t autotune;           /* 1: tune the SpMV layout per request class (value type,
+                                 log2 n, log2 mean row length): the class's first
+                                 request times the autotuner's layout candidates on
+                                 its own matrix (host analysis thread, its own stream
+                                 and temporary device memory outside the pool) and
+                                 later requests of the class use the fastest.  The
+                                 choice is timing-based, so two servers may pick
+                                 different layouts for a class (results then differ
+                                 in the last bits).  0 (default): the default layout */
 } te_server_options;
 
 /* Create a server (allocates the pool; work is issued on a stream the server
@@ -389,6 +398,13 @@ te_status te_server_poll(te_server* srv, int64_t ticket, int32_t* done, double* 
  * with te_server_poll (which returns its results at once).  Lets a client
  * poll only finished requests instead of every outstanding one. */
 te_status te_server_completed(te_server* srv, int64_t* tickets, int32_t cap, int32_t* count);
+
+/* The autotuner's choices so far (te_server_options.autotune): for up to `cap`
+ * tuned request classes, the class key ((value type * 64 + floor(log2 n)) * 32
+ * + floor(log2(nnz / n))), the window and the longest piece of its layout
+ * (arrays may be NULL); *count receives the number of tuned classes. */
+te_status te_server_classes(te_server* srv, int32_t* class_key, int32_t* window, int32_t* vmax,
+                            int32_t cap, int32_t* count);
 
 /* Resident and queued solves, pool bytes in use now and at most so far. */
 te_status te_server_stats(const te_server* srv, int32_t* live, int32_t* pending,

@@ -62,7 +62,8 @@ class te_options(ctypes.Structure):
 
 class te_server_options(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int32), ("max_krylov_steps", ctypes.c_int32),
-                ("device_budget_bytes", ctypes.c_size_t), ("use_graph", ctypes.c_int32)]
+                ("device_budget_bytes", ctypes.c_size_t), ("use_graph", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
 
 
 # every symbol the header declares, with its ctypes signature
@@ -113,6 +114,8 @@ _SIGS = {
     "te_server_destroy": (None, [ctypes.c_void_p]),
     "te_server_completed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_void_p]),
+    "te_server_classes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "te_server_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "te_probe_gather": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
@@ -384,9 +387,10 @@ class Server:
     submit host matrices, call step() repeatedly, poll() finished requests."""
 
     def __init__(self, max_slots: int = 32, max_krylov_steps: int = 32,
-                 budget: int = 4 << 30, use_graph: bool = True):
+                 budget: int = 4 << 30, use_graph: bool = True, autotune: bool = False):
         self._lib = load_library()
-        o = te_server_options(max_slots, max_krylov_steps, budget, 1 if use_graph else 0)
+        o = te_server_options(max_slots, max_krylov_steps, budget, 1 if use_graph else 0,
+                              1 if autotune else 0)
         h = ctypes.c_void_p()
         _check(self._lib.te_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -443,6 +447,18 @@ class Server:
         _check(self._lib.te_server_completed(self._h, ctypes.c_void_p(buf.ctypes.data), cap,
                                              ctypes.byref(cnt)))
         return [int(t) for t in buf[:cnt.value]]
+
+    def classes(self):
+        """{class key: (window, vmax)} chosen by the per-class autotuner."""
+        import numpy as np
+        cnt = ctypes.c_int32()
+        _check(self._lib.te_server_classes(self._h, None, None, None, 0, ctypes.byref(cnt)))
+        n = cnt.value
+        k, w, v = (np.zeros(max(n, 1), dtype=np.int32) for _ in range(3))
+        _check(self._lib.te_server_classes(self._h, ctypes.c_void_p(k.ctypes.data),
+                                           ctypes.c_void_p(w.ctypes.data),
+                                           ctypes.c_void_p(v.ctypes.data), n, ctypes.byref(cnt)))
+        return {int(k[i]): (int(w[i]), int(v[i])) for i in range(min(n, cnt.value))}
 
     def stats(self):
         live, pend = ctypes.c_int32(), ctypes.c_int32()

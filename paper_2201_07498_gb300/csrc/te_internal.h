@@ -166,6 +166,20 @@ struct DevLayout {
 };
 bool dev_layout_fits(int64_t n, int window, int vmax);
 
+// SpMV layout candidates (rows sorted together, longest piece) tried by the
+// autotuner; the first is the default
+constexpr int TUNE_N = 5;
+inline constexpr int TUNE_WINDOW[TUNE_N] = {SELL_WINDOW, SELL_WINDOW, SELL_WINDOW, 256, 16384};
+inline constexpr int TUNE_VMAX[TUNE_N] = {SELL_VMAX, 32, 128, SELL_VMAX, SELL_VMAX};
+// Build each candidate layout of a device CSR (rp, ci, val; rph: host row
+// pointers; hord / dcolmap: relabelled rows, or nullptr) in temporary
+// memory, time its SpMV with CUDA events on s and set *best to the fastest
+// candidate's index (te_solver.cu).
+cudaError_t autotune_layout(int prec, int vk, int in_type, const int64_t* rph, const int64_t* rp,
+                            const int32_t* ci, const void* val, int64_t n, int64_t nnz,
+                            const RowOrder* hord, const int32_t* dcolmap, cudaStream_t s,
+                            int* best);
+
 // Device copy of a SELL layout.
 struct DevSell {
   const SellSlice* slices = nullptr;

@@ -18,8 +18,10 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -107,7 +109,15 @@ class Pool {
 
 // pending -> admitted (layout built, columns being checked on the device) ->
 // running (resident in the batch) -> finished
-enum ReqState { REQ_PENDING = 0, REQ_RUNNING = 1, REQ_FINISHED = 2, REQ_ADMITTED = 3 };
+// pending -> admitted -> running -> finishing (Jacobi, Ritz vectors on the
+// finishing stream) -> finished
+enum ReqState {
+  REQ_PENDING = 0,
+  REQ_RUNNING = 1,
+  REQ_FINISHED = 2,
+  REQ_ADMITTED = 3,
+  REQ_FINISHING = 4
+};
 
 struct Request {
   int64_t ticket = 0;
@@ -124,8 +134,14 @@ struct Request {
   size_t work_off = 0, work_bytes = 0, res_off = 0, res_bytes = 0;
   BatchSlot desc{};
   std::vector<double> theta, resid;
-  // the SpMV layout, built by an analysis thread after submission
+  // the SpMV layout, built by an analysis thread after submission (with the
+  // layout candidate `cand` of the autotuner's list)
   SellHost layout;
+  int cand = 0;
+  // the CSR and the layout copied to the device staging area by the analysis
+  // thread (stage_bytes = 0: not staged; admission copies from the host)
+  int64_t seq = 0;  // submission order
+  size_t stage_off = 0, stage_bytes = 0;
   std::atomic<int> analysed{0};
 };
 
@@ -133,7 +149,11 @@ struct Request {
 // engine runs, so that admission only allocates, copies and launches.
 class AnalysisPool {
  public:
-  void start(unsigned nthreads) {
+  // fn builds a request's layout (on an analysis thread, device `dev`
+  // current, with a stream of its own)
+  void start(unsigned nthreads, int dev, std::function<void(Request*, cudaStream_t)> fn) {
+    fn_ = std::move(fn);
+    dev_ = dev;
     for (unsigned t = 0; t < nthreads; ++t) th_.emplace_back([this] { run(); });
   }
   void post(Request* R) {
@@ -161,22 +181,28 @@ class AnalysisPool {
 
  private:
   void run() {
+    cudaSetDevice(dev_);
+    cudaStream_t ts = nullptr;
+    cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
     for (;;) {
       Request* R = nullptr;
       {
         std::unique_lock<std::mutex> lk(mu_);
         cv_.wait(lk, [this] { return stop_ || !q_.empty(); });
-        if (stop_) return;
+        if (stop_) break;
         R = q_.front();
         q_.pop_front();
       }
-      std::string perr;
-      make_sell(R->rp, R->n, R->nnz, R->layout, perr);  // row pointers validated at submit
+      fn_(R, ts);
       {
         std::lock_guard<std::mutex> lk(mu_);
         R->analysed.store(1, std::memory_order_release);
       }
       done_.notify_all();
+    }
+    if (ts) {
+      cudaStreamSynchronize(ts);
+      cudaStreamDestroy(ts);
     }
   }
   std::vector<std::thread> th_;
@@ -184,6 +210,8 @@ class AnalysisPool {
   std::condition_variable cv_, done_;
   std::deque<Request*> q_;
   bool stop_ = false;
+  int dev_ = 0;
+  std::function<void(Request*, cudaStream_t)> fn_;
 };
 
 struct SlotResult {  // pinned, written by the finishing copies
@@ -229,13 +257,188 @@ struct te_server {
   std::deque<Request*> pending;
   std::vector<Request*> slots;
   std::vector<std::pair<size_t, size_t>> deferred;  // pool blocks to free after the next sync
-  std::vector<int> finishing;                       // slots whose solve ends this step
+  // solves that completed their m steps: their Jacobi and Ritz kernels run on
+  // a stream of their own, beside the following engine steps, and they are
+  // retired when that batch's event has completed
+  cudaStream_t fs = nullptr;
+  cudaEvent_t ev_step = nullptr;
+  struct FinishBatch {
+    cudaEvent_t ev;
+    std::vector<int> slots;
+  };
+  std::deque<FinishBatch> batches;
+  std::vector<cudaEvent_t> ev_free;
   std::deque<int64_t> completed;                    // finished tickets not yet reported
+  // per request class (value type, log2 n, log2 mean row length): the
+  // autotuner's layout candidate, tuned on the class's first request
+  bool autotune = false;
+  int dev = 0;
+  // device staging area: analysis threads copy each request's CSR and layout
+  // there in submission order (first-fit, freed after its admission), so that
+  // admission issues no copy from pageable host memory
+  Pool stage;
+  std::mutex stage_mu;
+  std::condition_variable stage_cv;
+  int64_t next_seq = 0, stage_turn = 0;
+  bool stopping = false;
+  std::mutex tune_mu;
+  std::condition_variable tune_cv;
+  std::map<int, int> tuned;
+  std::set<int> tuning;
   double t_wait = 0, t_admit = 0, t_launch = 0, t_submit = 0;  // host seconds, cumulative
   AnalysisPool analysis;
 };
 
 namespace {
+
+int request_class(const Request* R) {
+  int ln = 0, ld = 0;
+  while (ln < 40 && ((int64_t)1 << (ln + 1)) <= R->n) ++ln;
+  const int64_t deg = R->n > 0 ? R->nnz / R->n : 0;
+  while (ld < 20 && ((int64_t)1 << (ld + 1)) <= deg) ++ld;
+  return (R->vk * 64 + ln) * 32 + ld;
+}
+
+// Time the autotuner's layout candidates on R's matrix (its own stream and
+// temporary device memory, beside the engine); -1 when the matrix cannot be
+// tuned (a column index outside [0, n), or a CUDA error).
+int tune_request(const Request* R) {
+  cudaStream_t ts = nullptr;
+  if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) return -1;
+  const size_t b_rp = al256((size_t)(R->n + 1) * 8), b_ci = al256((size_t)R->nnz * 4 + 4),
+               b_v = al256(R->val_bytes + 8);
+  char* b = nullptr;
+  int best = -1;
+  cudaError_t e = cudaMalloc(&b, b_rp + b_ci + b_v + 256);
+  if (e == cudaSuccess) {
+    int* flag = reinterpret_cast<int*>(b + b_rp + b_ci + b_v);
+    e = cudaMemcpyAsync(b, R->rp, (size_t)(R->n + 1) * 8, cudaMemcpyHostToDevice, ts);
+    if (e == cudaSuccess && R->nnz)
+      e = cudaMemcpyAsync(b + b_rp, R->ci, (size_t)R->nnz * 4, cudaMemcpyHostToDevice, ts);
+    if (e == cudaSuccess && R->nnz)
+      e = cudaMemcpyAsync(b + b_rp + b_ci, R->vals, R->val_bytes, cudaMemcpyHostToDevice, ts);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), ts);
+    if (e == cudaSuccess)
+      e = launch_validate_cols(reinterpret_cast<const int32_t*>(b + b_rp), R->nnz, R->n, flag, ts);
+    int hflag = 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ts);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+    int c = 0;
+    if (e == cudaSuccess && !hflag &&
+        autotune_layout(PREC_FDF, R->vk, R->in_type, R->rp, reinterpret_cast<const int64_t*>(b),
+                        reinterpret_cast<const int32_t*>(b + b_rp), b + b_rp + b_ci, R->n, R->nnz,
+                        nullptr, nullptr, ts, &c) == cudaSuccess)
+      best = c;
+    cudaStreamSynchronize(ts);
+    cudaFree(b);
+  }
+  cudaStreamDestroy(ts);
+  return best;
+}
+
+// Offsets of a request's arrays in its staging block: row pointers, columns,
+// values, lane sources and lengths, slices, lane outputs, cut rows.
+struct StageLayout {
+  size_t rp, ci, val, src, len, sl, out, lr, total;
+};
+StageLayout stage_layout(const Request& R) {
+  const SellHost& H = R.layout;
+  StageLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off = al256(off + std::max<size_t>(b, 1));
+    return o;
+  };
+  L.rp = take((size_t)(R.n + 1) * 8);
+  L.ci = take((size_t)R.nnz * 4);
+  L.val = take(R.val_bytes);
+  L.src = take(H.vsrc.size() * 8);
+  L.len = take(H.vlen.size() * 4);
+  L.sl = take(H.slices.size() * sizeof(SellSlice));
+  L.out = take(H.vout.size() * 4);
+  L.lr = take(H.lrows.size() * sizeof(LongRow));
+  L.total = off;
+  return L;
+}
+
+// Copy R's CSR and layout into the staging area: the block is taken in
+// submission order (waiting while the area is full: admissions free it in
+// that order), the copies then run on the thread's stream.  A request larger
+// than the whole area is not staged.
+void stage_request(te_server* S, Request* R, cudaStream_t ts) {
+  const StageLayout L = stage_layout(*R);
+  {
+    std::unique_lock<std::mutex> lk(S->stage_mu);
+    S->stage_cv.wait(lk, [&] { return S->stopping || S->stage_turn == R->seq; });
+    if (S->stopping) return;
+    if (L.total <= S->stage.size) {
+      size_t off = 0;
+      S->stage_cv.wait(lk, [&] { return S->stopping || S->stage.alloc(L.total, &off); });
+      if (!S->stopping) {
+        R->stage_off = off;
+        R->stage_bytes = L.total;
+      }
+    }
+    S->stage_turn += 1;
+  }
+  S->stage_cv.notify_all();
+  if (!R->stage_bytes) return;
+  char* G = S->stage.base + R->stage_off;
+  const SellHost& H = R->layout;
+  cudaError_t e = cudaSuccess;
+  auto h2d = [&](size_t o, const void* src, size_t b) {
+    if (e == cudaSuccess && b) e = cudaMemcpyAsync(G + o, src, b, cudaMemcpyHostToDevice, ts);
+  };
+  h2d(L.rp, R->rp, (size_t)(R->n + 1) * 8);
+  h2d(L.ci, R->ci, (size_t)R->nnz * 4);
+  h2d(L.val, R->vals, R->val_bytes);
+  h2d(L.src, H.vsrc.data(), H.vsrc.size() * 8);
+  h2d(L.len, H.vlen.data(), H.vlen.size() * 4);
+  h2d(L.sl, H.slices.data(), H.slices.size() * sizeof(SellSlice));
+  h2d(L.out, H.vout.data(), H.vout.size() * 4);
+  h2d(L.lr, H.lrows.data(), H.lrows.size() * sizeof(LongRow));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+  if (e != cudaSuccess) {  // fall back to copies at admission
+    std::lock_guard<std::mutex> lk(S->stage_mu);
+    S->stage.release(R->stage_off, R->stage_bytes);
+    R->stage_bytes = 0;
+  }
+}
+
+// An analysis thread's work: the request's layout, with its class's tuned
+// candidate when the server tunes (the class's first request is tuned here;
+// others of the class wait for it), then its staging
+void analyse_request(te_server* S, Request* R, cudaStream_t ts) {
+  int cand = 0;
+  if (S->autotune) {
+    const int key = request_class(R);
+    std::unique_lock<std::mutex> lk(S->tune_mu);
+    for (;;) {
+      auto it = S->tuned.find(key);
+      if (it != S->tuned.end()) {
+        cand = it->second;
+        break;
+      }
+      if (!S->tuning.count(key)) {
+        S->tuning.insert(key);
+        lk.unlock();
+        const int c = tune_request(R);
+        lk.lock();
+        S->tuning.erase(key);
+        if (c >= 0) S->tuned[key] = c;  // an untunable request leaves the class open
+        S->tune_cv.notify_all();
+        cand = c >= 0 ? c : 0;
+        break;
+      }
+      S->tune_cv.wait(lk);
+    }
+  }
+  std::string perr;
+  make_sell(R->rp, R->n, R->nnz, R->layout, perr, TUNE_WINDOW[cand], TUNE_VMAX[cand]);
+  R->cand = cand;
+  stage_request(S, R, ts);
+}
 
 // the batched step: SpMV (+ cut rows), three passes, three restart passes
 cudaError_t enqueue_step(te_server* S, cudaStream_t s) {
@@ -257,6 +460,7 @@ struct AdmitLayout {
 };
 
 AdmitLayout admit_layout(const Request& R, const SellHost& H) {
+  const bool staged = R.stage_bytes > 0;  // the staging area holds the CSR and lane map
   AdmitLayout L{};
   size_t off = 0;
   auto take = [&](size_t b) {
@@ -279,11 +483,11 @@ AdmitLayout admit_layout(const Request& R, const SellHost& H) {
   L.flag = take(16);
   L.total = off;
   off = 0;
-  L.t_rp = take((size_t)(R.n + 1) * 8);
-  L.t_ci = take((size_t)R.nnz * 4);
-  L.t_val = take((size_t)R.nnz * (R.in_type == TE_F64 ? 8 : 4));
-  L.t_src = take(H.vsrc.size() * 8);
-  L.t_len = take(H.vlen.size() * 4);
+  L.t_rp = take(staged ? 0 : (size_t)(R.n + 1) * 8);
+  L.t_ci = take(staged ? 0 : (size_t)R.nnz * 4);
+  L.t_val = take(staged ? 0 : (size_t)R.nnz * (R.in_type == TE_F64 ? 8 : 4));
+  L.t_src = take(staged ? 0 : H.vsrc.size() * 8);
+  L.t_len = take(staged ? 0 : H.vlen.size() * 4);
   L.t_q = take(R.vk == TE_BF16 ? (size_t)R.nnz * 2 : 0);
   L.t_total = off;
   return L;
@@ -314,28 +518,44 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
   char* T = S->pool.base + tmp;
   cudaStream_t s = S->as;  // beside the engine step
   cudaError_t e = cudaMemsetAsync(W, 0, L.total, s);
+  // the CSR and layout: in the staging area (copied by the analysis thread)
+  // or copied from the host now
+  const bool staged = R->stage_bytes > 0;
+  const StageLayout G = stage_layout(*R);
+  const char* GB = S->stage.base + R->stage_off;
   auto h2d = [&](void* dst, const void* src, size_t b) {
     if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, s);
   };
-  h2d(T + L.t_rp, R->rp, (size_t)(R->n + 1) * 8);
-  h2d(T + L.t_ci, R->ci, (size_t)R->nnz * 4);
-  h2d(T + L.t_val, R->vals, R->val_bytes);
-  h2d(T + L.t_src, H.vsrc.data(), H.vsrc.size() * 8);
-  h2d(T + L.t_len, H.vlen.data(), H.vlen.size() * 4);
-  const int64_t* drp = reinterpret_cast<const int64_t*>(T + L.t_rp);
-  const int32_t* dci = reinterpret_cast<const int32_t*>(T + L.t_ci);
-  const void* dval = T + L.t_val;
-  const int64_t* dsrc = reinterpret_cast<const int64_t*>(T + L.t_src);
-  const int32_t* dlen = reinterpret_cast<const int32_t*>(T + L.t_len);
+  if (!staged) {
+    h2d(T + L.t_rp, R->rp, (size_t)(R->n + 1) * 8);
+    h2d(T + L.t_ci, R->ci, (size_t)R->nnz * 4);
+    h2d(T + L.t_val, R->vals, R->val_bytes);
+    h2d(T + L.t_src, H.vsrc.data(), H.vsrc.size() * 8);
+    h2d(T + L.t_len, H.vlen.data(), H.vlen.size() * 4);
+  }
+  const int64_t* drp = reinterpret_cast<const int64_t*>(staged ? GB + G.rp : T + L.t_rp);
+  const int32_t* dci = reinterpret_cast<const int32_t*>(staged ? GB + G.ci : T + L.t_ci);
+  const void* dval = staged ? (const void*)(GB + G.val) : (const void*)(T + L.t_val);
+  const int64_t* dsrc = reinterpret_cast<const int64_t*>(staged ? GB + G.src : T + L.t_src);
+  const int32_t* dlen = reinterpret_cast<const int32_t*>(staged ? GB + G.len : T + L.t_len);
   // column indices are checked here, before the solve's first SpMV (the
   // request joins the batch only after the next step has read the flag)
   int* flag = reinterpret_cast<int*>(W + L.flag);
   if (e == cudaSuccess) e = launch_validate_cols(dci, R->nnz, R->n, flag, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&S->res_h[k].bad_cols, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
-  h2d(W + L.slices, H.slices.data(), H.slices.size() * sizeof(SellSlice));
-  h2d(W + L.vout, H.vout.data(), H.vout.size() * 4);
-  h2d(W + L.lrows, H.lrows.data(), H.lrows.size() * sizeof(LongRow));
+  if (staged) {
+    auto d2d = [&](void* dst, const void* src, size_t b) {
+      if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToDevice, s);
+    };
+    d2d(W + L.slices, GB + G.sl, H.slices.size() * sizeof(SellSlice));
+    d2d(W + L.vout, GB + G.out, H.vout.size() * 4);
+    d2d(W + L.lrows, GB + G.lr, H.lrows.size() * sizeof(LongRow));
+  } else {
+    h2d(W + L.slices, H.slices.data(), H.slices.size() * sizeof(SellSlice));
+    h2d(W + L.vout, H.vout.data(), H.vout.size() * 4);
+    h2d(W + L.lrows, H.lrows.data(), H.lrows.size() * sizeof(LongRow));
+  }
   const void* vin = dval;
   int in_type = R->in_type;
   if (e == cudaSuccess && R->vk == TE_BF16) {
@@ -413,7 +633,7 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
 
 // Jacobi, selection and Ritz vectors of a solve that completed its m steps,
 // then its eigenvalues, residual estimates and status to the pinned slot area
-cudaError_t enqueue_finish(te_server* S, Request* R) {
+cudaError_t enqueue_finish(te_server* S, Request* R, cudaStream_t fs) {
   const BatchSlot& B = R->desc;
   JacobiArgs j;
   memset(&j, 0, sizeof(j));
@@ -427,7 +647,7 @@ cudaError_t enqueue_finish(te_server* S, Request* R) {
   j.C_out = B.st->C;
   j.resid_out = B.st->resid_est;
   j.st = B.st;
-  cudaError_t e = launch_jacobi(j, S->s);
+  cudaError_t e = launch_jacobi(j, fs);
   if (e == cudaSuccess) {
     PassArgs a;
     memset(&a, 0, sizeof(a));
@@ -445,18 +665,18 @@ cudaError_t enqueue_finish(te_server* S, Request* R) {
     a.fin = FIN_NONE;
     PassLaunch Lr = S->Lritz;
     Lr.grid = R->ncta;
-    e = launch_pass(PREC_FDF, MODE_RITZ, a, Lr, S->s);
+    e = launch_pass(PREC_FDF, MODE_RITZ, a, Lr, fs);
   }
   SlotResult* out = S->res_h + R->slot;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out->theta, B.st->theta_sel, sizeof(double) * B.K, cudaMemcpyDeviceToHost,
-                        S->s);
+                        fs);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out->resid, B.st->resid_est, sizeof(double) * B.K,
-                        cudaMemcpyDeviceToHost, S->s);
+                        cudaMemcpyDeviceToHost, fs);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out->hdr, &B.st->restart_flag, sizeof(out->hdr), cudaMemcpyDeviceToHost,
-                        S->s);
+                        fs);
   return e;
 }
 
@@ -492,6 +712,8 @@ te_status te_server_create(const te_server_options* o, te_server** out) {
     return srv_fail(TE_ERR_INVALID_ARG, "max_krylov_steps must be in [1, 64]");
   if (o->device_budget_bytes < ((size_t)1 << 20))
     return srv_fail(TE_ERR_INVALID_ARG, "device_budget_bytes must be at least 1 MiB");
+  if (o->autotune != 0 && o->autotune != 1)
+    return srv_fail(TE_ERR_INVALID_ARG, "autotune must be 0 or 1");
   te_server* S = new te_server();
   struct Guard {
     te_server*& p;
@@ -502,15 +724,25 @@ te_status te_server_create(const te_server_options* o, te_server** out) {
   } guard{S};
   S->max_slots = o->max_slots;
   S->max_m = o->max_krylov_steps;
+  S->autotune = o->autotune != 0;
   S->use_graph = o->use_graph != 0;
   S->slots.assign(S->max_slots, nullptr);
   int dev = 0;
   SRV_CK(cudaGetDevice(&dev), "cudaGetDevice");
+  S->dev = dev;
   SRV_CK(cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, dev), "attribute");
+  {
+    size_t sb = o->device_budget_bytes / 8;
+    sb = std::max<size_t>(sb, (size_t)64 << 20);
+    sb = std::min<size_t>(sb, (size_t)2 << 30);
+    SRV_CK(S->stage.init(sb), "allocate the staging area");
+  }
 
   SRV_CK(cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking), "create stream");
   SRV_CK(cudaStreamCreateWithFlags(&S->ps, cudaStreamNonBlocking), "create stream");
   SRV_CK(cudaStreamCreateWithFlags(&S->as, cudaStreamNonBlocking), "create stream");
+  SRV_CK(cudaStreamCreateWithFlags(&S->fs, cudaStreamNonBlocking), "create stream");
+  SRV_CK(cudaEventCreateWithFlags(&S->ev_step, cudaEventDisableTiming), "create event");
   SRV_CK(cudaEventCreateWithFlags(&S->ev_admit, cudaEventDisableTiming), "create event");
   SRV_CK(cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming), "create event");
   SRV_CK(S->pool.init(o->device_budget_bytes), "allocate the device pool");
@@ -533,7 +765,7 @@ te_status te_server_create(const te_server_options* o, te_server** out) {
     unsigned nt = std::thread::hardware_concurrency();
     nt = nt > 2 ? nt / 2 : 1;
     if (nt > 8) nt = 8;
-    S->analysis.start(nt);
+    S->analysis.start(nt, dev, [S](Request* R, cudaStream_t ts) { analyse_request(S, R, ts); });
   }
   if (S->use_graph) {
     cudaGraph_t g = nullptr;
@@ -555,9 +787,15 @@ te_status te_server_create(const te_server_options* o, te_server** out) {
 
 void te_server_destroy(te_server* S) {
   if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->stage_mu);
+    S->stopping = true;
+  }
+  S->stage_cv.notify_all();
   S->analysis.stop();  // no thread touches a request after this
   if (S->s) cudaStreamSynchronize(S->s);
   if (S->as) cudaStreamSynchronize(S->as);
+  if (S->fs) cudaStreamSynchronize(S->fs);
   for (auto& kv : S->reqs) delete kv.second;
   if (S->gexec) cudaGraphExecDestroy(S->gexec);
   if (S->ev) cudaEventDestroy(S->ev);
@@ -566,6 +804,10 @@ void te_server_destroy(te_server* S) {
   if (S->res_h) cudaFreeHost(S->res_h);
   if (S->s) cudaStreamDestroy(S->s);
   if (S->as) cudaStreamDestroy(S->as);
+  if (S->fs) cudaStreamDestroy(S->fs);
+  if (S->ev_step) cudaEventDestroy(S->ev_step);
+  for (auto& b : S->batches) cudaEventDestroy(b.ev);
+  for (cudaEvent_t e : S->ev_free) cudaEventDestroy(e);
   if (S->ev_admit) cudaEventDestroy(S->ev_admit);
   if (S->ps) cudaStreamDestroy(S->ps);
   delete S;
@@ -603,6 +845,7 @@ te_status te_server_submit(te_server* S, const te_csr* A, int32_t K, int32_t m, 
   R->ci = A->col_idx;
   R->vals = A->values;
   R->val_bytes = (size_t)A->nnz * (R->in_type == TE_F64 ? 8 : 4);
+  R->seq = S->next_seq++;
   S->reqs[R->ticket] = R;
   S->pending.push_back(R);
   S->analysis.post(R);
@@ -618,19 +861,38 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
   if (S->inflight) {
     SRV_CK(cudaEventSynchronize(S->ev), "engine step");
     S->inflight = false;
-    for (int k : S->finishing) {
-      Request* R = S->slots[k];
-      const SlotResult& o = S->res_h[k];
-      R->theta.assign(o.theta, o.theta + R->K);
-      R->resid.assign(o.resid, o.resid + R->K);
-      R->status = o.hdr[2];
-      R->state = REQ_FINISHED;
-      S->completed.push_back(R->ticket);
-      S->pool.release(R->work_off, R->work_bytes);
-      S->slots[k] = nullptr;
-      R->slot = -1;
+  }
+  // finished Jacobi / Ritz batches, oldest first; block on the oldest only
+  // when no solve is stepping (so that a client waiting for results moves on)
+  {
+    bool stepping = false, free_slot = false;
+    for (Request* R : S->slots) {
+      stepping |= R && (R->state == REQ_RUNNING || R->state == REQ_ADMITTED);
+      free_slot |= R == nullptr;
     }
-    S->finishing.clear();
+    while (!S->batches.empty()) {
+      te_server::FinishBatch& b = S->batches.front();
+      cudaError_t q = cudaEventQuery(b.ev);
+      if (q == cudaErrorNotReady) {
+        if (stepping || (free_slot && !S->pending.empty())) break;
+        q = cudaEventSynchronize(b.ev);
+      }
+      SRV_CK(q, "finish solves");
+      for (int k : b.slots) {
+        Request* R = S->slots[k];
+        const SlotResult& o = S->res_h[k];
+        R->theta.assign(o.theta, o.theta + R->K);
+        R->resid.assign(o.resid, o.resid + R->K);
+        R->status = o.hdr[2];
+        R->state = REQ_FINISHED;
+        S->completed.push_back(R->ticket);
+        S->pool.release(R->work_off, R->work_bytes);
+        S->slots[k] = nullptr;
+        R->slot = -1;
+      }
+      S->ev_free.push_back(b.ev);
+      S->batches.pop_front();
+    }
   }
   // the admissions of the previous call ran on their own stream
   if (S->admit_pending) {
@@ -642,6 +904,14 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
       Request* R = S->slots[k];
       if (!R || R->state != REQ_ADMITTED) continue;
       R->layout = SellHost();  // its admission kernels are done
+      if (R->stage_bytes) {
+        {
+          std::lock_guard<std::mutex> lk(S->stage_mu);
+          S->stage.release(R->stage_off, R->stage_bytes);
+          R->stage_bytes = 0;
+        }
+        S->stage_cv.notify_all();
+      }
       if (S->res_h[k].bad_cols) {
         R->status = TE_ERR_INVALID_ARG;
         R->state = REQ_FINISHED;
@@ -680,15 +950,33 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
            "upload the step table");
     if (S->gexec) SRV_CK(cudaGraphLaunch(S->gexec, S->s), "launch the engine step");
     else SRV_CK(enqueue_step(S, S->s), "engine step");
-    // solves that completed their m steps: Jacobi and Ritz vectors
+    // solves that completed their m steps: Jacobi and Ritz vectors on the
+    // finishing stream, after this step
+    te_server::FinishBatch batch;
     for (int k = 0; k < S->max_slots; ++k) {
       Request* R = S->slots[k];
       if (!R || R->state != REQ_RUNNING) continue;
       R->step += 1;
       if (R->step == R->m) {
-        SRV_CK(enqueue_finish(S, R), "finish a solve");
-        S->finishing.push_back(k);
+        if (batch.slots.empty()) {
+          SRV_CK(cudaEventRecord(S->ev_step, S->s), "record");
+          SRV_CK(cudaStreamWaitEvent(S->fs, S->ev_step, 0), "wait");
+        }
+        SRV_CK(enqueue_finish(S, R, S->fs), "finish a solve");
+        R->state = REQ_FINISHING;
+        batch.slots.push_back(k);
       }
+    }
+    if (!batch.slots.empty()) {
+      if (S->ev_free.empty()) {
+        cudaEvent_t e = nullptr;
+        SRV_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
+        S->ev_free.push_back(e);
+      }
+      batch.ev = S->ev_free.back();
+      S->ev_free.pop_back();
+      SRV_CK(cudaEventRecord(batch.ev, S->fs), "record");
+      S->batches.push_back(std::move(batch));
     }
   }
   double t2 = now_s();
@@ -717,6 +1005,14 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
         R->status = TE_ERR_OUT_OF_MEMORY;
         R->state = REQ_FINISHED;
         S->completed.push_back(R->ticket);
+        if (R->stage_bytes) {
+          {
+            std::lock_guard<std::mutex> lk(S->stage_mu);
+            S->stage.release(R->stage_off, R->stage_bytes);
+            R->stage_bytes = 0;
+          }
+          S->stage_cv.notify_all();
+        }
         S->pending.pop_front();
         continue;
       }
@@ -787,6 +1083,23 @@ te_status te_server_completed(te_server* S, int64_t* tickets, int32_t cap, int32
   while (c < cap && !S->completed.empty()) {
     tickets[c++] = S->completed.front();
     S->completed.pop_front();
+  }
+  *count = c;
+  return TE_OK;
+}
+
+te_status te_server_classes(te_server* S, int32_t* class_key, int32_t* window, int32_t* vmax,
+                            int32_t cap, int32_t* count) {
+  if (!S || !count || cap < 0) return srv_fail(TE_ERR_INVALID_ARG, "bad arguments");
+  std::lock_guard<std::mutex> lk(S->tune_mu);
+  int32_t c = 0;
+  for (const auto& kv : S->tuned) {
+    if (c < cap) {
+      if (class_key) class_key[c] = kv.first;
+      if (window) window[c] = TUNE_WINDOW[kv.second];
+      if (vmax) vmax[c] = TUNE_VMAX[kv.second];
+    }
+    ++c;
   }
   *count = c;
   return TE_OK;

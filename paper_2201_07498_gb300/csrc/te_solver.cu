@@ -334,16 +334,12 @@ cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const
   return e;
 }
 
-// SpMV layout candidates (rows sorted together, longest piece) tried by the
-// autotuner; the first is the default
-constexpr int TUNE_N = 5;
-constexpr int TUNE_WINDOW[TUNE_N] = {SELL_WINDOW, SELL_WINDOW, SELL_WINDOW, 256, 16384};
-constexpr int TUNE_VMAX[TUNE_N] = {SELL_VMAX, 32, 128, SELL_VMAX, SELL_VMAX};
+}  // namespace
 
 // Build each candidate layout of the device CSR (rp, ci, val) in temporary
 // memory, time its SpMV (CUDA events on s, after two warm-up calls), and
 // return the index of the fastest.
-cudaError_t autotune_layout(int prec, int vk, int in_type, const int64_t* rph, const int64_t* rp,
+cudaError_t te::autotune_layout(int prec, int vk, int in_type, const int64_t* rph, const int64_t* rp,
                             const int32_t* ci, const void* val, int64_t n, int64_t nnz,
                             const RowOrder* hord, const int32_t* dcolmap, cudaStream_t s,
                             int* best) {
@@ -407,6 +403,8 @@ cudaError_t autotune_layout(int prec, int vk, int in_type, const int64_t* rph, c
   }
   return cudaSuccess;
 }
+
+namespace {
 
 // The plan stores the basis tile-major: tile t of column c at
 // (t * (m + 1) + c) * TILE_R, so that a pass moves the columns of a tile with

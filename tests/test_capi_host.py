@@ -123,6 +123,8 @@ def test_server_options_validated_before_gpu(te):
     for slots, m, budget in [(0, 16, 1 << 30), (65, 16, 1 << 30), (8, 65, 1 << 30), (8, 16, 1000)]:
         o = te.te_server_options(slots, m, budget, 1)
         assert lib.te_server_create(ctypes.byref(o), ctypes.byref(h)) == 1
+    o = te.te_server_options(8, 16, 1 << 30, 1, 2)  # autotune takes 0 or 1
+    assert lib.te_server_create(ctypes.byref(o), ctypes.byref(h)) == 1
     assert lib.te_server_create(None, ctypes.byref(h)) == 1
 
 

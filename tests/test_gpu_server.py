@@ -189,3 +189,27 @@ def test_completion_queue_reports_every_request_once(te):
             break
     assert sorted(seen) == sorted(tickets) and len(set(seen)) == len(seen)
     assert srv.completed() == []
+
+
+def test_autotuned_server_matches_oracle(te):
+    """With the per-class autotuner on, each class's first request times the
+    layout candidates; every request still matches the oracle on its rounded
+    matrix (binary32 values) within the FDF tolerance, whichever layout its
+    class got."""
+    srv = te.Server(max_slots=8, max_krylov_steps=32, budget=512 << 20, autotune=True)
+    mats = [synth.rmat_sym(12, 6, 31), synth.rmat_sym(12, 6, 32), synth.uniform_sym(3000, 5, 33),
+            synth.uniform_sym(3000, 5, 34), synth.rmat_sym(14, 8, 35)]
+    tickets = {srv.submit(M, 4, 12, "fdf", seed=40 + i): i for i, M in enumerate(mats)}
+    res = _drain(srv, list(tickets))
+    classes = srv.classes()
+    assert 1 <= len(classes) <= len(mats)
+    for w, v in classes.values():
+        assert (w, v) in [(2048, 64), (2048, 32), (2048, 128), (256, 64), (16384, 64)]
+    for t, i in tickets.items():
+        A = mats[i]
+        ev = res[t][0]
+        ref = oracle.topk_eigs(f32_matrix(A), 4, 12, synth.start_vector(A.n, 40 + i), seed=40 + i,
+                               want_vectors=False)
+        scale = np.max(np.abs(ref.eigvals))
+        perm = match_pairs(ev, ref.eigvals, 1e-6 * scale)
+        assert np.max(np.abs(ev - ref.eigvals[perm])) <= 1e-6 * scale
