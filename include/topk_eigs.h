@@ -252,6 +252,29 @@ int64_t te_plan_stream_blocks(const te_plan* plan);
 
 void te_plan_destroy(te_plan* plan);
 
+/* ---- device memory of plans (no counterpart in the paper: runtime support) ----
+ * Plans (and te_topk_eigs, te_lanczos, the autotuner and the serving engine's
+ * per-class tuning) take their device memory from a stream-ordered memory pool
+ * per device that the library owns.  Memory a plan frees stays reserved by the
+ * pool and serves the next plan without the driver mapping pages again; the
+ * pool returns it to the driver when an allocation finds the device full, when
+ * te_release_cached_memory is called, or, past the release threshold set by
+ * te_set_memory_cache, at the next synchronisation.  Other allocators in the
+ * process (PyTorch's, for example) do not see the reserved memory as free. */
+
+/* Release threshold of every device's pool, in bytes (default UINT64_MAX: keep
+ * all freed memory; 0: return it at every synchronisation). */
+te_status te_set_memory_cache(uint64_t keep_bytes);
+
+/* Return every unused block of every pool to the driver.  Memory held by live
+ * plans is not affected. */
+te_status te_release_cached_memory(void);
+
+/* The pool of `device`: bytes reserved from the driver and bytes held by live
+ * allocations (both 0 before the first plan on that device).
+ * TE_ERR_INVALID_ARG for a NULL output or a device index outside [0, 64). */
+te_status te_memory_cached(int32_t device, uint64_t* reserved_bytes, uint64_t* used_bytes);
+
 /* ---- single phases, for testing and for callers composing their own solver ---- */
 
 /* y = M x with the solver's SpMV (Algorithm 1, SpMV step).  x: n elements of

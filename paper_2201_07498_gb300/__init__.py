@@ -132,6 +132,9 @@ _SIGS = {
                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
                               + [ctypes.c_void_p] * 13),
     "te_check_symmetric": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "te_set_memory_cache": (ctypes.c_int, [ctypes.c_uint64]),
+    "te_release_cached_memory": (ctypes.c_int, []),
+    "te_memory_cached": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -260,6 +263,24 @@ def _options(seed=0, v1=None, which="LM", use_graph=True, budget=0, reorth="full
     o.order = ORDERS[order] if isinstance(order, str) else int(order)
     o.stall_first_pass = 1 if stall_first_pass else 0
     return o
+
+
+def set_memory_cache(keep_bytes: int):
+    """Release threshold of the library's device memory pools (bytes kept
+    reserved after plans free them; default: all)."""
+    _check(load_library().te_set_memory_cache(int(keep_bytes)))
+
+
+def release_cached_memory():
+    """Return the device memory the library keeps for reuse to the driver."""
+    _check(load_library().te_release_cached_memory())
+
+
+def memory_cached(device: int = 0):
+    """(reserved, used) bytes of the library's memory pool on `device`."""
+    r, u = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load_library().te_memory_cached(device, ctypes.byref(r), ctypes.byref(u)))
+    return r.value, u.value
 
 
 def topk_eigs(csr: CSR, K: int, krylov_steps: int, precision="fdf", *, seed: int = 0, v1=None,

@@ -15,6 +15,19 @@
 
 namespace te {
 
+// Device memory of plans, layouts and temporaries (te_mem.cu): a stream-ordered
+// pool per device that keeps freed blocks for the next plan.  Same contract as
+// cudaMalloc / cudaFree (usable by every stream on return; the free waits for
+// the device to be idle first).
+cudaError_t dev_alloc(void** p, size_t bytes);
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc(reinterpret_cast<void**>(p), bytes);
+}
+cudaError_t dev_free(void* p);
+// free once the work queued on s so far is done (every user of p is on s)
+cudaError_t dev_free_on(void* p, cudaStream_t s);
+
 constexpr int MAX_M = 64;        // largest supported krylov_steps
 constexpr int TILE_R = 256;      // rows per tile of the basis passes
 // per-CTA partial slots: dots with the pass vector at [0, MAX_M], dots with
@@ -197,15 +210,21 @@ struct DevSell {
   int64_t hot = 0;  // rows by degree: gathers of x[c >= min(hot, what L1 holds)] skip L1
 };
 
-// fill cols/vals of the SELL layout from the CSR (a warp per slice)
-// in_type / out_type (te_dtype): F64 -> F64, F64 -> F32 (round to nearest
-// even), F32 -> F32, BF16 -> BF16, FP8_E4M3 -> FP8_E4M3 (codes copied).  For
-// FP8 also lane_scale[lane] = row_scale[vrow[lane]] (0 for empty lanes).
-cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, const void* val,
-                              const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
-                              int nslices, int32_t* cols, void* vals, const int32_t* vrow,
-                              const float* row_scale, float* lane_scale, const int32_t* colmap,
-                              cudaStream_t s);  // colmap (optional): column c -> colmap[c]
+// fill the SELL layout from the CSR (a warp per slice): the column indices
+// (through colmap when given: column c -> colmap[c]) and the values, in two
+// kernels.  Values: in_type / out_type (te_dtype) F64 -> F64, F64 -> F32
+// (round to nearest even), F32 -> F32, BF16 -> BF16, FP8_E4M3 -> FP8_E4M3
+// (codes copied); for FP8 also lane_scale[lane] = row_scale[vrow[lane]] (0
+// for empty lanes).  bad (optional, device): the kernels do nothing when *bad
+// is non-zero (the column check, earlier on s, found an invalid index).
+cudaError_t launch_sell_fill_cols(const int32_t* ci, const SellSlice* slices, const int64_t* vsrc,
+                                  const int32_t* vlen, int nslices, int32_t* cols,
+                                  const int32_t* colmap, const int* bad, cudaStream_t s);
+cudaError_t launch_sell_fill_vals(int in_type, int out_type, const void* val,
+                                  const SellSlice* slices, const int64_t* vsrc,
+                                  const int32_t* vlen, int nslices, void* vals,
+                                  const int32_t* vrow, const float* row_scale, float* lane_scale,
+                                  const int* bad, cudaStream_t s);
 // the same arrays built on the host (in_type F64 or F32 -> vk F64 or F32);
 // false if a column index lies outside [0, n)
 bool build_sell_host(const SellHost& H, const int32_t* ci, const void* val, int in_type, int vk,

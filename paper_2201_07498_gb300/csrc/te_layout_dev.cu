@@ -429,17 +429,35 @@ __global__ void __launch_bounds__(32 * LD_WARPS) win_emit_kernel(
     if (lane == 0) pos[w][vmax] += tf;
     if (s && lane == __ffs(peers) - 1) pos[w][s] = bs + __popc(peers);
     __syncwarp();
-    if (ok && L > 0) {
-      const int64_t first = R.first(r);
-      const int32_t o = R.csr_row(r);
-      const int64_t pid = piece_run + exp_;
-      for (int64_t c = 0; c < nfull; ++c) {
-        const int64_t l = lane0 + pf + c;
-        vout[l] = cut ? (int32_t)(-1 - (pid + c)) : (int32_t)r;
-        vsrc[l] = first + c * vmax;
+    const int64_t first = ok && L > 0 ? R.first(r) : 0;
+    const int32_t o = ok && L > 0 ? R.csr_row(r) : -1;
+    const int64_t pid = piece_run + exp_;
+    // full-length pieces: a row with one writes it; the pieces of a row cut
+    // into several are written by the whole warp, row by row (consecutive
+    // lanes, coalesced)
+    if (nfull == 1) {
+      const int64_t l = lane0 + pf;
+      vout[l] = cut ? (int32_t)(-1 - pid) : (int32_t)r;
+      vsrc[l] = first;
+      vlen[l] = vmax;
+      if (vrow) vrow[l] = o;
+    }
+    for (unsigned many = __ballot_sync(0xffffffffu, nfull > 1); many; many &= many - 1) {
+      const int src_lane = __ffs(many) - 1;
+      const int64_t nf = __shfl_sync(0xffffffffu, nfull, src_lane);
+      const int64_t pf_l = __shfl_sync(0xffffffffu, pf, src_lane);
+      const int64_t first_l = __shfl_sync(0xffffffffu, first, src_lane);
+      const int64_t pid_l = __shfl_sync(0xffffffffu, pid, src_lane);
+      const int32_t o_l = __shfl_sync(0xffffffffu, o, src_lane);
+      for (int64_t c = lane; c < nf; c += 32) {  // (a row cut into several pieces)
+        const int64_t l = lane0 + pf_l + c;
+        vout[l] = (int32_t)(-1 - (pid_l + c));
+        vsrc[l] = first_l + c * vmax;
         vlen[l] = vmax;
-        if (vrow) vrow[l] = o;
+        if (vrow) vrow[l] = o_l;
       }
+    }
+    if (ok && L > 0) {
       if (s) {
         const int64_t l = lane0 + bs + __popc(peers & lanemask_lt());
         vout[l] = cut ? (int32_t)(-1 - (pid + nfull)) : (int32_t)r;
@@ -570,7 +588,7 @@ cudaError_t DevLayout::count(const int64_t* rp_dev, int64_t n_, int64_t nnz_, in
   const size_t a = (size_t)std::max<int64_t>(n, 1);
   const size_t bytes = 4 * a * 4 + (size_t)ntiles * DS_BINS * 8 + (SCAN_MAX_BLOCKS + 1) * 8 +
                        (size_t)4 * std::max<int64_t>(nwin, 1) * 8 + 256;
-  cudaError_t e = cudaMalloc(&b, bytes);
+  cudaError_t e = dev_alloc(&b, bytes);
   if (e != cudaSuccess) return e;
   scratch = b;
   uint32_t* k0 = reinterpret_cast<uint32_t*>(b);
@@ -694,7 +712,7 @@ cudaError_t DevLayout::emit(SellSlice* slices, int32_t* vout, int64_t* vsrc, int
 }
 
 DevLayout::~DevLayout() {
-  if (scratch) cudaFree(scratch);
+  if (scratch) dev_free(scratch);
 }
 
 }  // namespace te

@@ -309,7 +309,7 @@ int tune_request(const Request* R) {
                b_v = al256(R->val_bytes + 8);
   char* b = nullptr;
   int best = -1;
-  cudaError_t e = cudaMalloc(&b, b_rp + b_ci + b_v + 256);
+  cudaError_t e = dev_alloc(&b, b_rp + b_ci + b_v + 256);
   if (e == cudaSuccess) {
     int* flag = reinterpret_cast<int*>(b + b_rp + b_ci + b_v);
     e = cudaMemcpyAsync(b, R->rp, (size_t)(R->n + 1) * 8, cudaMemcpyHostToDevice, ts);
@@ -330,7 +330,7 @@ int tune_request(const Request* R) {
                         nullptr, nullptr, ts, &c) == cudaSuccess)
       best = c;
     cudaStreamSynchronize(ts);
-    cudaFree(b);
+    dev_free_on(b, ts);
   }
   cudaStreamDestroy(ts);
   return best;
@@ -565,10 +565,13 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
     in_type = TE_BF16;
   }
   if (e == cudaSuccess)
-    e = launch_sell_build(in_type, R->vk, dci, vin,
-                          reinterpret_cast<const SellSlice*>(W + L.slices), dsrc, dlen,
-                          (int)H.slices.size(), reinterpret_cast<int32_t*>(W + L.cols),
-                          W + L.vals, nullptr, nullptr, nullptr, nullptr, s);
+    e = launch_sell_fill_cols(dci, reinterpret_cast<const SellSlice*>(W + L.slices), dsrc, dlen,
+                              (int)H.slices.size(), reinterpret_cast<int32_t*>(W + L.cols),
+                              nullptr, nullptr, s);
+  if (e == cudaSuccess)
+    e = launch_sell_fill_vals(in_type, R->vk, vin, reinterpret_cast<const SellSlice*>(W + L.slices),
+                              dsrc, dlen, (int)H.slices.size(), W + L.vals, nullptr, nullptr,
+                              nullptr, nullptr, s);
   LzState* st = reinterpret_cast<LzState*>(W + L.st);
   double* U = reinterpret_cast<double*>(S->pool.base + res);
   if (e == cudaSuccess) e = launch_solve_begin(st, nullptr, U, nullptr, nullptr, s);

@@ -260,34 +260,41 @@ cudaError_t upload_meta(const SellHost& H, const DevSell& D, cudaStream_t s) {
 }
 
 // Fill the SELL arrays from a device CSR, given the lane records (first CSR
-// entry and length of every lane's piece, and its row for FP8): round or
-// quantise the values (in_type: the caller's value type, binary64 when the
-// storage type D.vk differs), and optionally write a second value array with
-// the binary64 values (vals64, for the refinement).  Temporaries are freed
-// before returning (the stream is synchronised).
+// entry and length of every lane's piece, and its row for FP8): the columns,
+// then the values, rounded or quantised (in_type: the caller's value type,
+// binary64 when the storage type D.vk differs), and optionally a second value
+// array with the binary64 values (vals64, for the refinement).  The columns
+// wait for ev_cols and the values for ev_vals (when given: the arrival of the
+// CSR's column and value arrays); bad: see launch_sell_fill_cols.
+// Temporaries are freed before returning (the stream is synchronised).
 cudaError_t fill_sell(int in_type, const DevSell& D, const int64_t* rp, const int32_t* ci,
                       const void* val, int64_t n, int64_t nnz, const int64_t* dsrc,
                       const int32_t* dlen, const int32_t* drow, void* vals64, float* lane_scale,
-                      const int32_t* colmap, cudaStream_t s) {
+                      const int32_t* colmap, cudaStream_t s, cudaEvent_t ev_cols = nullptr,
+                      cudaEvent_t ev_vals = nullptr, const int* bad = nullptr) {
   const bool quant = D.vk == TE_BF16 || D.vk == TE_FP8_E4M3;
   const bool fp8 = D.vk == TE_FP8_E4M3;
   void* q = nullptr;
   float* rscale = nullptr;
   cudaError_t e = cudaSuccess;
-  if (quant) e = cudaMalloc(&q, std::max<size_t>(nnz, 1) * elt_of(D.vk));
-  if (e == cudaSuccess && fp8) e = cudaMalloc(&rscale, std::max<int64_t>(n, 1) * sizeof(float));
+  if (quant) e = dev_alloc(&q, std::max<size_t>(nnz, 1) * elt_of(D.vk));
+  if (e == cudaSuccess && fp8) e = dev_alloc(&rscale, std::max<int64_t>(n, 1) * sizeof(float));
+  if (e == cudaSuccess && ev_cols) e = cudaStreamWaitEvent(s, ev_cols, 0);
+  if (e == cudaSuccess)
+    e = launch_sell_fill_cols(ci, D.slices, dsrc, dlen, D.nslices, D.cols, colmap, bad, s);
+  if (e == cudaSuccess && ev_vals) e = cudaStreamWaitEvent(s, ev_vals, 0);
   if (e == cudaSuccess && quant)
     e = launch_quantize(D.vk, rp, static_cast<const double*>(val), n, nnz, q, rscale, s);
   if (e == cudaSuccess)
-    e = launch_sell_build(quant ? D.vk : in_type, D.vk, ci, quant ? q : val, D.slices, dsrc,
-                          dlen, D.nslices, D.cols, D.vals, drow, rscale,
-                          fp8 ? lane_scale : nullptr, colmap, s);
+    e = launch_sell_fill_vals(quant ? D.vk : in_type, D.vk, quant ? q : val, D.slices, dsrc, dlen,
+                              D.nslices, D.vals, drow, rscale, fp8 ? lane_scale : nullptr, bad,
+                              s);
   if (e == cudaSuccess && vals64)
-    e = launch_sell_build(TE_F64, TE_F64, ci, val, D.slices, dsrc, dlen, D.nslices, D.cols,
-                          vals64, nullptr, nullptr, nullptr, colmap, s);
+    e = launch_sell_fill_vals(TE_F64, TE_F64, val, D.slices, dsrc, dlen, D.nslices, vals64,
+                              nullptr, nullptr, nullptr, bad, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (q) cudaFree(q);
-  if (rscale) cudaFree(rscale);
+  if (q) dev_free(q);
+  if (rscale) dev_free(rscale);
   return e;
 }
 
@@ -313,9 +320,9 @@ cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const
   int64_t* dsrc = nullptr;
   int32_t* dlen = nullptr;
   int32_t* drow = nullptr;
-  e = cudaMalloc(&dsrc, H.vsrc.size() * sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&dlen, H.vlen.size() * sizeof(int32_t));
-  if (e == cudaSuccess && fp8) e = cudaMalloc(&drow, H.vrow.size() * sizeof(int32_t));
+  e = dev_alloc(&dsrc, H.vsrc.size() * sizeof(int64_t));
+  if (e == cudaSuccess) e = dev_alloc(&dlen, H.vlen.size() * sizeof(int32_t));
+  if (e == cudaSuccess && fp8) e = dev_alloc(&drow, H.vrow.size() * sizeof(int32_t));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dsrc, H.vsrc.data(), H.vsrc.size() * sizeof(int64_t),
                         cudaMemcpyHostToDevice, s);
@@ -328,9 +335,9 @@ cudaError_t upload_sell(int in_type, const SellHost& H, const int64_t* rp, const
   if (e == cudaSuccess)
     e = fill_sell(in_type, D, rp, ci, val, n, nnz, dsrc, dlen, drow, vals64, lane_scale, colmap,
                   s);
-  cudaFree(dsrc);
-  cudaFree(dlen);
-  if (drow) cudaFree(drow);
+  dev_free(dsrc);
+  dev_free(dlen);
+  if (drow) dev_free(drow);
   return e;
 }
 
@@ -360,7 +367,7 @@ cudaError_t te::autotune_layout(int prec, int vk, int in_type, const int64_t* rp
     const size_t b_ls = vk == TE_FP8_E4M3 ? b_vo : 0;
     const size_t b_x = al256((size_t)n * xelt), b_y = al256((size_t)n * 8);
     char* buf = nullptr;
-    cudaError_t e = cudaMalloc(&buf, b_sl + b_vo + b_co + b_va + b_lr + b_vp + b_ls + b_x + b_y);
+    cudaError_t e = dev_alloc(&buf, b_sl + b_vo + b_co + b_va + b_lr + b_vp + b_ls + b_x + b_y);
     if (e != cudaSuccess) return e;
     DevSell D;
     size_t off = 0;
@@ -394,7 +401,7 @@ cudaError_t te::autotune_layout(int prec, int vk, int in_type, const int64_t* rp
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(buf);
+    dev_free(buf);
     if (e != cudaSuccess) return e;
     if (c == 0 || ms < best_ms) {
       best_ms = ms;
@@ -786,8 +793,8 @@ void te_plan_destroy(te_plan* P) {
   if (P->hvals) cudaFreeHost(P->hvals);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->cap) cudaStreamDestroy(P->cap);
-  if (P->work) cudaFree(P->work);
-  if (P->owned_csr) cudaFree(P->owned_csr);
+  if (P->work) dev_free(P->work);
+  if (P->owned_csr) dev_free(P->owned_csr);
   if (P->hres) cudaFreeHost(P->hres);
   delete P;
 }
@@ -854,28 +861,32 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   // where they are read (the column check and the layout fill).
   struct SideCopy {
     cudaStream_t cs = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t cols_done = nullptr;  // the column indices have arrived
+    cudaEvent_t done = nullptr;       // columns and values have arrived
     ~SideCopy() {
       if (cs) {
         cudaStreamSynchronize(cs);
         cudaStreamDestroy(cs);
       }
+      if (cols_done) cudaEventDestroy(cols_done);
       if (done) cudaEventDestroy(done);
     }
   } side;
   if (A->where == TE_HOST && opt.matrix_budget_bytes == 0) {
     const size_t e_in = in_type == TE_F64 ? 8 : 4;
     const size_t brp = al256(sizeof(int64_t) * (A->n + 1)), bci = al256(sizeof(int32_t) * A->nnz);
-    TE_CK(cudaMalloc(&P->owned_csr, brp + bci + al256(e_in * A->nnz)), "allocate device CSR");
+    TE_CK(dev_alloc(&P->owned_csr, brp + bci + al256(e_in * A->nnz)), "allocate device CSR");
     char* b = static_cast<char*>(P->owned_csr);
     TE_CK(cudaMemcpyAsync(b, A->row_ptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyHostToDevice, s),
           "copy row_ptr");
     if (A->nnz > 0) {
       TE_CK(cudaStreamCreateWithFlags(&side.cs, cudaStreamNonBlocking), "create copy stream");
       TE_CK(cudaEventCreateWithFlags(&side.done, cudaEventDisableTiming), "create event");
+      TE_CK(cudaEventCreateWithFlags(&side.cols_done, cudaEventDisableTiming), "create event");
       TE_CK(cudaMemcpyAsync(b + brp, A->col_idx, sizeof(int32_t) * A->nnz, cudaMemcpyHostToDevice,
                             side.cs),
             "copy col_idx");
+      TE_CK(cudaEventRecord(side.cols_done, side.cs), "record");
       TE_CK(cudaMemcpyAsync(b + brp + bci, A->values, e_in * A->nnz, cudaMemcpyHostToDevice,
                             side.cs),
             "copy values");
@@ -896,7 +907,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   struct TmpFree {
     char*& p;
     ~TmpFree() {
-      if (p) cudaFree(p);
+      if (p) dev_free(p);
     }
   } dtmp_guard{dtmp};
   int32_t *dperm_t = nullptr, *diperm_t = nullptr, *dlen_t = nullptr;
@@ -911,7 +922,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     TE_CK(e, "row order on the device");
     if (P->reorder) {
       const size_t nn = (size_t)A->n;
-      TE_CK(cudaMalloc(&dtmp, nn * (4 + 4 + 4) + al256(nn * 8) + 256), "allocate the row order");
+      TE_CK(dev_alloc(&dtmp, nn * (4 + 4 + 4) + al256(nn * 8) + 256), "allocate the row order");
       dsrc_t = reinterpret_cast<int64_t*>(dtmp);
       dperm_t = reinterpret_cast<int32_t*>(dtmp + al256(nn * 8));
       diperm_t = dperm_t + nn;
@@ -1025,7 +1036,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
       dval = P->val;
     } else if (A->where == TE_HOST) {
       const size_t brp = al256(sizeof(int64_t) * (A->n + 1)), bci = al256(4 * (size_t)A->nnz);
-      TE_CK(cudaMalloc(&tmp, brp + bci + in_elt * (size_t)A->nnz + 256), "allocate tuning CSR");
+      TE_CK(dev_alloc(&tmp, brp + bci + in_elt * (size_t)A->nnz + 256), "allocate tuning CSR");
       TE_CK(cudaMemcpyAsync(tmp, A->row_ptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyHostToDevice,
                             s),
             "copy row_ptr");
@@ -1040,8 +1051,8 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     }
     int* flag = nullptr;
     int32_t* tmap = nullptr;  // the column relabelling, for the trial layouts
-    cudaError_t e = cudaMalloc(&flag, sizeof(int));
-    if (e == cudaSuccess && P->reorder) e = cudaMalloc(&tmap, sizeof(int32_t) * A->n);
+    cudaError_t e = dev_alloc(&flag, sizeof(int));
+    if (e == cudaSuccess && P->reorder) e = dev_alloc(&tmap, sizeof(int32_t) * A->n);
     if (e == cudaSuccess && P->reorder)
       e = cudaMemcpyAsync(tmap, hiperm.data(), sizeof(int32_t) * A->n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
@@ -1049,13 +1060,13 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     int hflag = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (flag) cudaFree(flag);
+    if (flag) dev_free(flag);
     int best = 0;
     if (e == cudaSuccess && !hflag)
       e = autotune_layout(P->prec, P->vk, in_type, rph, drp, dci, dval, A->n, A->nnz, hp, tmap, s,
                           &best);
-    if (tmp) cudaFree(tmp);
-    if (tmap) cudaFree(tmap);
+    if (tmp) dev_free(tmp);
+    if (tmap) dev_free(tmap);
     if (e != cudaSuccess) return cuda_fail(e, "autotune the SpMV layout");
     if (hflag) return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
     P->sell_window = TUNE_WINDOW[best];
@@ -1082,7 +1093,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   if (opt.device_budget_bytes > 0 && P->W.total + csr_bytes > opt.device_budget_bytes)
     return fail(TE_ERR_OUT_OF_MEMORY, "work memory exceeds device_budget_bytes");
 
-  TE_CK(cudaMalloc(&P->work, P->W.total), "allocate work memory");
+  TE_CK(dev_alloc(&P->work, P->W.total), "allocate work memory");
   TE_CK(cudaMallocHost(&P->hres, sizeof(te_plan::HostRes)), "allocate pinned result buffer");
   P->st = static_cast<LzState*>(at(P, P->W.st));
 
@@ -1104,7 +1115,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   } else if (P->owned_csr) {
     // copied at the start
   } else if (A->where == TE_HOST) {
-    TE_CK(cudaMalloc(&P->owned_csr, csr_bytes), "allocate device CSR");
+    TE_CK(dev_alloc(&P->owned_csr, csr_bytes), "allocate device CSR");
     char* b = static_cast<char*>(P->owned_csr);
     int64_t* drp = reinterpret_cast<int64_t*>(b);
     int32_t* dci = reinterpret_cast<int32_t*>(b + al256(sizeof(int64_t) * (A->n + 1)));
@@ -1138,10 +1149,14 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
           "arm the stall hook");
     TE_CK(cudaStreamSynchronize(s), "arm the stall hook");
   }
-  if (side.done) TE_CK(cudaStreamWaitEvent(s, side.done, 0), "wait for the matrix copy");
-  if (!P->streaming) {
+  // A host matrix still arriving with a device-built layout: the layout's
+  // emission runs during the copy, the column check and the columns' fill
+  // wait only for the column indices, the values' fill for the values.
+  const bool arriving = dev_build && side.done != nullptr;
+  int* dflag = static_cast<int*>(at(P, P->W.flag));
+  if (!arriving && side.done) TE_CK(cudaStreamWaitEvent(s, side.done, 0), "wait for the matrix copy");
+  if (!P->streaming && !arriving) {
     // column indices must lie in [0, n)
-    int* dflag = static_cast<int*>(at(P, P->W.flag));
     TE_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s), "clear flag");
     TE_CK(launch_validate_cols(P->ci, P->nnz, P->n, dflag, s), "validate columns");
     int hflag = 0;
@@ -1160,7 +1175,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
                           dev_build ? (const void*)diperm_t : (const void*)hiperm.data(),
                           sizeof(int32_t) * A->n, k, s),
           "place the row order");
-    TE_CK(cudaStreamSynchronize(s), "place the row order");
+    if (!dev_build) TE_CK(cudaStreamSynchronize(s), "place the row order");
   }
   // the SELL copy of the matrix that the solve streams
   P->sell.slices = static_cast<SellSlice*>(at(P, P->W.slices));
@@ -1186,10 +1201,10 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
     char* lt = nullptr;
     const size_t bytes = al256(lanes * 8) + al256(lanes * 4) + (fp8 ? al256(lanes * 4) : 0) +
                          al256((size_t)std::max<int64_t>(l_lrows, 1) * sizeof(LongRow));
-    TE_CK(cudaMalloc(&lt, bytes), "allocate the lane records");
+    TE_CK(dev_alloc(&lt, bytes), "allocate the lane records");
     struct LtFree {
       char* p;
-      ~LtFree() { cudaFree(p); }
+      ~LtFree() { dev_free(p); }
     } lt_guard{lt};
     int64_t* lsrc = reinterpret_cast<int64_t*>(lt);
     int32_t* llen = reinterpret_cast<int32_t*>(lt + al256(lanes * 8));
@@ -1202,11 +1217,25 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
                   lsrc, llen, lrow, const_cast<LongRow*>(P->sell.lrows), lr_tmp, s, &nbig),
           "build the SELL layout on the device");
     P->sell.nlbig = nbig;
+    if (arriving) {  // column indices must lie in [0, n)
+      TE_CK(cudaMemsetAsync(dflag, 0, sizeof(int), s), "clear flag");
+      TE_CK(cudaStreamWaitEvent(s, side.cols_done, 0), "wait for the column indices");
+      TE_CK(launch_validate_cols(P->ci, P->nnz, P->n, dflag, s), "validate columns");
+    }
     if (l_slices > 0)
       TE_CK(fill_sell(in_type, P->sell, P->rp, P->ci, P->val, P->n, P->nnz, lsrc, llen, lrow,
                       vals64, P->W.lscale ? static_cast<float*>(at(P, P->W.lscale)) : nullptr,
-                      P->diperm, s),
+                      P->diperm, s, arriving ? side.cols_done : nullptr,
+                      arriving ? side.done : nullptr, arriving ? dflag : nullptr),
             "fill the SELL layout");
+    if (arriving) {
+      TE_CK(cudaStreamWaitEvent(s, side.done, 0), "wait for the matrix copy");
+      int hflag = 0;
+      TE_CK(cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
+      TE_CK(cudaStreamSynchronize(s), "plan setup");
+      if (hflag)
+        return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
+    }
   } else {
     TE_CK(upload_sell(in_type, sell, P->rp, P->ci, P->val, P->n, P->nnz, P->sell, vals64,
                       P->W.lscale ? static_cast<float*>(at(P, P->W.lscale)) : nullptr,
@@ -1221,7 +1250,7 @@ te_status te_plan_create(const te_csr* A, int32_t K, int32_t krylov_steps, te_pr
   }
   if (P->refine || P->reorder) P->ubase = static_cast<double*>(at(P, P->W.Uint));
   if (P->owned_csr) {  // the solve reads only the SELL copy
-    cudaFree(P->owned_csr);
+    dev_free(P->owned_csr);
     P->owned_csr = nullptr;
   }
 
@@ -1285,10 +1314,10 @@ te_status te_plan_profile(te_plan* P, double* ms, int32_t* launches, double* byt
   if (!P) return fail(TE_ERR_INVALID_ARG, "plan is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* U = nullptr;  // the Ritz contraction needs somewhere to write
-  TE_CK(cudaMalloc(&U, sizeof(double) * (size_t)P->n * P->K), "allocate profile eigvecs");
+  TE_CK(dev_alloc(&U, sizeof(double) * (size_t)P->n * P->K), "allocate profile eigvecs");
   te_status r = plan_begin(P, nullptr, U, nullptr, s);
   if (r != TE_OK) {
-    cudaFree(U);
+    dev_free(U);
     return r;
   }
   P->prof = te_plan::Prof();
@@ -1309,7 +1338,7 @@ te_status te_plan_profile(te_plan* P, double* ms, int32_t* launches, double* byt
   }
   for (cudaEvent_t ev : P->prof.ev) cudaEventDestroy(ev);
   P->prof = te_plan::Prof();
-  cudaFree(U);
+  dev_free(U);
   if (e != cudaSuccess) return cuda_fail(e, "te_plan_profile");
   for (int k = 0; k < TE_NUM_KINDS; ++k) {
     if (ms) ms[k] = acc_ms[k];
@@ -1329,13 +1358,13 @@ te_status te_plan_solve(te_plan* P, const double* v1, double* eigvals, double* e
   if (eigvecs && !is_device_ptr(eigvecs)) {
     U = static_cast<double*>(mapped_host_ptr(eigvecs));
     if (!U) {  // pageable host memory: stage on the device, copy at the end
-      TE_CK(cudaMalloc(&Utmp, sizeof(double) * (size_t)P->n * P->K), "allocate eigvecs staging");
+      TE_CK(dev_alloc(&Utmp, sizeof(double) * (size_t)P->n * P->K), "allocate eigvecs staging");
       U = Utmp;
     }
   }
   te_status r = te_plan_launch(P, v1, nullptr, U, stream);
   if (r != TE_OK) {
-    if (Utmp) cudaFree(Utmp);
+    if (Utmp) dev_free(Utmp);
     return r;
   }
   cudaError_t e = cudaMemcpyAsync(&P->hres->restart_flag, &P->st->restart_flag, 4 * sizeof(int),
@@ -1348,19 +1377,19 @@ te_status te_plan_solve(te_plan* P, const double* v1, double* eigvals, double* e
                         cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    if (Utmp) cudaFree(Utmp);
+    if (Utmp) dev_free(Utmp);
     return cuda_fail(e, "solve");
   }
   const int status = P->hres->status;
   if (status != 0 && status != TE_ERR_BREAKDOWN) {
-    if (Utmp) cudaFree(Utmp);
+    if (Utmp) dev_free(Utmp);
     return fail((te_status)status, std::string("device-side failure: ") +
                                        te_status_string((te_status)status));
   }
   // outputs
   if (Utmp) {
     e = cudaMemcpy(eigvecs, Utmp, sizeof(double) * (size_t)P->n * P->K, cudaMemcpyDeviceToHost);
-    cudaFree(Utmp);
+    dev_free(Utmp);
     if (e != cudaSuccess) return cuda_fail(e, "copy eigvecs");
   }
   const cudaMemcpyKind kv = is_device_ptr(eigvals) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
@@ -1420,7 +1449,7 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
   const size_t b_ls =
       p.values == TE_FP8_E4M3 ? al256(std::max<size_t>(sell.vout.size(), 1) * 4) : 0;
   char* buf = nullptr;
-  TE_CK(cudaMalloc(&buf, b_sl + b_vo + b_co + b_va + b_lr + b_vp + b_ls + 256),
+  TE_CK(dev_alloc(&buf, b_sl + b_vo + b_co + b_va + b_lr + b_vp + b_ls + 256),
         "allocate SpMV layout");
   DevSell D;
   size_t off = 0;
@@ -1451,7 +1480,7 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
     e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && hflag) {
-    cudaFree(buf);
+    dev_free(buf);
     return fail(TE_ERR_INVALID_ARG, "malformed CSR: a column index is outside [0, n)");
   }
   const int in_type = A->values_f64 ? TE_F64 : p.values;
@@ -1462,7 +1491,7 @@ te_status te_spmv(const te_csr* A, te_precision p, const void* x, double* y, voi
   if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, sizeof(double) * A->n, s);
   if (e == cudaSuccess) e = launch_spmv(prec, D, x, y, true, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(buf);
+  dev_free(buf);
   if (e != cudaSuccess) return cuda_fail(e, "te_spmv");
   return TE_OK;
 }
@@ -1523,7 +1552,7 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
   if (prepare_kernels() != cudaSuccess) return cuda_fail(g_prep_err, "kernel set-up");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* dbuf = nullptr;
-  TE_CK(cudaMalloc(&dbuf, 2 * sizeof(int)), "allocate status");
+  TE_CK(dev_alloc(&dbuf, 2 * sizeof(int)), "allocate status");
   JacobiArgs j;
   memset(&j, 0, sizeof(j));
   j.alpha = alpha;
@@ -1539,7 +1568,7 @@ te_status te_tridiag_eigs(int32_t m, const double* alpha, const double* beta, in
   int h[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, dbuf, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(dbuf);
+  dev_free(dbuf);
   if (e != cudaSuccess) return cuda_fail(e, "te_tridiag_eigs");
   if (sweeps) *sweeps = h[0];
   if (h[1] != 0) return fail((te_status)h[1], "Jacobi sweeps did not converge");
@@ -1575,12 +1604,12 @@ te_status te_gram(int64_t n, int32_t K, const double* U, double* G, void* stream
   const int grid = sms * 2;
   const size_t np = (size_t)K * (K + 1) / 2;
   double* buf = nullptr;
-  TE_CK(cudaMalloc(&buf, sizeof(double) * (np * grid + (size_t)K * K)), "allocate Gram work");
+  TE_CK(dev_alloc(&buf, sizeof(double) * (np * grid + (size_t)K * K)), "allocate Gram work");
   cudaError_t e = launch_gram(U, n, K, buf, grid, buf + np * grid, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(G, buf + np * grid, sizeof(double) * K * K, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(buf);
+  dev_free(buf);
   if (e != cudaSuccess) return cuda_fail(e, "te_gram");
   return TE_OK;
 }
@@ -1638,7 +1667,7 @@ te_status te_spmv_layout_device(const int64_t* row_ptr, int64_t n, int64_t nnz, 
   struct BFree {
     char*& p;
     ~BFree() {
-      if (p) cudaFree(p);
+      if (p) dev_free(p);
     }
   } bf{b};
   const size_t nn = (size_t)n;
@@ -1649,11 +1678,11 @@ te_status te_spmv_layout_device(const int64_t* row_ptr, int64_t n, int64_t nnz, 
   struct OFree {
     char*& p;
     ~OFree() {
-      if (p) cudaFree(p);
+      if (p) dev_free(p);
     }
   } of{ob};
   if (reorder) {
-    TE_CK(cudaMalloc(&ob, al256(nn * 8) + 3 * al256(nn * 4)), "allocate");
+    TE_CK(dev_alloc(&ob, al256(nn * 8) + 3 * al256(nn * 4)), "allocate");
     ds = reinterpret_cast<int64_t*>(ob);
     dp = reinterpret_cast<int32_t*>(ob + al256(nn * 8));
     dip = reinterpret_cast<int32_t*>(ob + al256(nn * 8) + al256(nn * 4));
@@ -1667,7 +1696,7 @@ te_status te_spmv_layout_device(const int64_t* row_ptr, int64_t n, int64_t nnz, 
                o_src = o_out + al256(lanes * 4), o_len = o_src + al256(lanes * 8),
                o_row = o_len + al256(lanes * 4), o_lr = o_row + al256(lanes * 4),
                o_lt = o_lr + al256(NL * sizeof(LongRow)), total = o_lt + al256(NL * sizeof(LongRow));
-  TE_CK(cudaMalloc(&b, total), "allocate");
+  TE_CK(dev_alloc(&b, total), "allocate");
   int nb = 0;
   TE_CK(DL.emit(reinterpret_cast<SellSlice*>(b + o_sl), reinterpret_cast<int32_t*>(b + o_out),
                 reinterpret_cast<int64_t*>(b + o_src), reinterpret_cast<int32_t*>(b + o_len),

@@ -11,8 +11,9 @@
 // power-law graphs, and keeping the sort inside windows keeps the row writes
 // local.  The plan keeps this copy in HBM and the solve never re-reads the
 // caller's CSR.  The arrangement (slices, lanes, cut rows) is computed on the
-// host (te_layout.cu); the kernel below fills it with column indices and
-// values on the device.
+// device (te_layout_dev.cu) for a plan's device-resident copy, otherwise on
+// the host (te_layout.cu: host-streamed matrices, autotuned plans, serving
+// requests); the kernels below fill it with column indices and values.
 //
 // Kernel: a warp streams its slice with coalesced 128-byte loads (marked L2
 // evict-first so that the gathered vector stays resident in L2), gathers
@@ -33,87 +34,102 @@ TE_DEV Vout convert_value(Vin v) {
   else return (Vout)v;
 }
 
-// Device fill of the SELL arrays, a warp per slice.  The 32 pieces of a
-// slice are contiguous runs of the CSR, while the slice stores them
-// column-major (entry k of lane l at base + 32 k + l).  The warp moves them
-// 32 columns of k at a time through a shared-memory tile: it reads each
-// piece's next 32 entries with one coalesced load per array, then writes the
-// tile's columns with coalesced stores, so the CSR reads and the slice writes
-// both move whole cache lines.  Values are converted on the way (binary64 ->
-// binary32 rounds to nearest even); columns go through colmap when the rows
-// are relabelled; padding entries are (column 0, value 0).
-template <typename Vout>
-constexpr int build_warps() { return sizeof(Vout) == 8 ? 2 : 4; }  // tiles within 48 KB
+// Device fill of the SELL arrays, a warp per slice, lane i walking its own
+// piece (a contiguous run of the CSR) entry after entry and storing entry k
+// of the slice's 32 lanes with one coalesced store (entry k of lane i at
+// base + 32 k + i; padding: column 0, value 0).  A lane's successive loads
+// fall in the sector its previous load brought into L1.  No shared memory
+// and 32 registers: 64 warps per SM keep loads in flight (a shared-memory
+// transpose tile with coalesced loads ran no faster at R-MAT 2^24 and
+// allowed a third of the warps).  Columns and values are filled by separate
+// kernels so that each can start as soon as its CSR array has arrived.
+// Columns go through colmap when the rows are relabelled; values are
+// converted on the way (binary64 -> binary32 rounds to nearest even).  A
+// non-zero *bad (the column check found an index outside [0, n), earlier on
+// the stream) makes both kernels return at once: colmap is never indexed
+// with such a column.
+constexpr int SELL_FILL_WARPS = 8;
 
-template <typename Vin, typename Vout>
-__global__ void __launch_bounds__(32 * build_warps<Vout>())
-    sell_build_kernel(const int32_t* ci, const Vin* val, const SellSlice* slices,
-                      const int64_t* vsrc, const int32_t* vlen, int nslices, int32_t* cols,
-                      Vout* vals, const int32_t* vrow, const float* row_scale, float* lane_scale,
-                      const int32_t* colmap) {
-  constexpr int WARPS = build_warps<Vout>();
-  __shared__ int32_t tc[WARPS][SELL_C][SELL_C + 1];
-  __shared__ Vout tv[WARPS][SELL_C][SELL_C + 1];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t s = (int64_t)blockIdx.x * WARPS + w;
+__global__ void __launch_bounds__(32 * SELL_FILL_WARPS, 8)
+    sell_fill_cols_kernel(const int32_t* ci, const SellSlice* slices, const int64_t* vsrc,
+                          const int32_t* vlen, int nslices, int32_t* cols,
+                          const int32_t* colmap, const int* bad) {
+  if (bad && *bad) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * SELL_FILL_WARPS + (threadIdx.x >> 5);
   if (s >= nslices) return;  // uniform per warp
   const SellSlice sl = slices[s];
   const int64_t t = s * SELL_C + lane;
-  const int64_t my_src = vsrc[t];
+  const int32_t* cp = ci + vsrc[t];
+  const int my_len = vlen[t];
+  int32_t* co = cols + sl.base + lane;
+#pragma unroll 4
+  for (int k = 0; k < sl.len; ++k) {
+    int32_t c = 0;
+    if (k < my_len) {
+      const int32_t c0 = cp[k];
+      c = colmap ? colmap[c0] : c0;
+    }
+    __stcs(co + (int64_t)k * SELL_C, c);
+  }
+}
+
+template <typename Vin, typename Vout>
+__global__ void __launch_bounds__(32 * SELL_FILL_WARPS, 8)
+    sell_fill_vals_kernel(const Vin* val, const SellSlice* slices, const int64_t* vsrc,
+                          const int32_t* vlen, int nslices, Vout* vals, const int32_t* vrow,
+                          const float* row_scale, float* lane_scale, const int* bad) {
+  if (bad && *bad) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t s = (int64_t)blockIdx.x * SELL_FILL_WARPS + (threadIdx.x >> 5);
+  if (s >= nslices) return;  // uniform per warp
+  const SellSlice sl = slices[s];
+  const int64_t t = s * SELL_C + lane;
+  const Vin* vp = val + vsrc[t];
   const int my_len = vlen[t];
   if (lane_scale) {
     const int32_t r = vrow[t];
     lane_scale[t] = r >= 0 ? row_scale[r] : 0.f;
   }
-  for (int k0 = 0; k0 < sl.len; k0 += SELL_C) {
-    const int k = k0 + lane;
-#pragma unroll 8
-    for (int l = 0; l < SELL_C; ++l) {  // piece l, entries k0 .. k0 + 31
-      const int64_t src = __shfl_sync(0xffffffffu, my_src, l);
-      const int len = __shfl_sync(0xffffffffu, my_len, l);
-      int32_t c = 0;
-      Vout v = (Vout)0;
-      if (k < len) {
-        const int32_t c0 = ci[src + k];  // checked to lie in [0, n) before the build
-        c = colmap ? colmap[c0] : c0;
-        v = convert_value<Vin, Vout>(val[src + k]);
-      }
-      tc[w][l][lane] = c;
-      tv[w][l][lane] = v;
-    }
-    __syncwarp();
-    const int kn = sl.len - k0 < SELL_C ? sl.len - k0 : SELL_C;
-    for (int j = 0; j < kn; ++j) {  // column k0 + j: lane l's entry
-      const int64_t dst = sl.base + (int64_t)(k0 + j) * SELL_C + lane;
-      cols[dst] = tc[w][lane][j];
-      vals[dst] = tv[w][lane][j];
-    }
-    __syncwarp();
+  Vout* vo = vals + sl.base + lane;
+#pragma unroll 4
+  for (int k = 0; k < sl.len; ++k) {
+    Vout v = (Vout)0;
+    if (k < my_len) v = convert_value<Vin, Vout>(vp[k]);
+    __stcs(vo + (int64_t)k * SELL_C, v);
   }
 }
 
-cudaError_t launch_sell_build(int in_type, int out_type, const int32_t* ci, const void* val,
-                              const SellSlice* slices, const int64_t* vsrc, const int32_t* vlen,
-                              int nslices, int32_t* cols, void* vals, const int32_t* vrow,
-                              const float* row_scale, float* lane_scale, const int32_t* colmap,
-                              cudaStream_t s) {
+cudaError_t launch_sell_fill_cols(const int32_t* ci, const SellSlice* slices, const int64_t* vsrc,
+                                  const int32_t* vlen, int nslices, int32_t* cols,
+                                  const int32_t* colmap, const int* bad, cudaStream_t s) {
   if (nslices <= 0) return cudaSuccess;
-#define TE_BUILD(IN, OUT, TI, TO)                                                              \
-  if (in_type == IN && out_type == OUT) {                                                     \
-    constexpr int W = build_warps<TO>();                                                      \
-    const unsigned blocks = (unsigned)(((int64_t)nslices + W - 1) / W);                       \
-    sell_build_kernel<TI, TO><<<blocks, 32 * W, 0, s>>>(ci, static_cast<const TI*>(val),      \
-                                                        slices, vsrc, vlen, nslices, cols,    \
-                                                        static_cast<TO*>(vals), vrow,         \
-                                                        row_scale, lane_scale, colmap);       \
-    return cudaGetLastError();                                                                \
+  const unsigned blocks = (unsigned)(((int64_t)nslices + SELL_FILL_WARPS - 1) / SELL_FILL_WARPS);
+  sell_fill_cols_kernel<<<blocks, 32 * SELL_FILL_WARPS, 0, s>>>(ci, slices, vsrc, vlen, nslices,
+                                                                cols, colmap, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sell_fill_vals(int in_type, int out_type, const void* val,
+                                  const SellSlice* slices, const int64_t* vsrc,
+                                  const int32_t* vlen, int nslices, void* vals,
+                                  const int32_t* vrow, const float* row_scale, float* lane_scale,
+                                  const int* bad, cudaStream_t s) {
+  if (nslices <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)(((int64_t)nslices + SELL_FILL_WARPS - 1) / SELL_FILL_WARPS);
+#define TE_FILL(IN, OUT, TI, TO)                                                              \
+  if (in_type == IN && out_type == OUT) {                                                    \
+    sell_fill_vals_kernel<TI, TO><<<blocks, 32 * SELL_FILL_WARPS, 0, s>>>(                   \
+        static_cast<const TI*>(val), slices, vsrc, vlen, nslices, static_cast<TO*>(vals),    \
+        vrow, row_scale, lane_scale, bad);                                                   \
+    return cudaGetLastError();                                                               \
   }
-  TE_BUILD(TE_F64, TE_F64, double, double)
-  TE_BUILD(TE_F64, TE_F32, double, float)
-  TE_BUILD(TE_F32, TE_F32, float, float)
-  TE_BUILD(TE_BF16, TE_BF16, uint16_t, uint16_t)
-  TE_BUILD(TE_FP8_E4M3, TE_FP8_E4M3, uint8_t, uint8_t)
-#undef TE_BUILD
+  TE_FILL(TE_F64, TE_F64, double, double)
+  TE_FILL(TE_F64, TE_F32, double, float)
+  TE_FILL(TE_F32, TE_F32, float, float)
+  TE_FILL(TE_BF16, TE_BF16, uint16_t, uint16_t)
+  TE_FILL(TE_FP8_E4M3, TE_FP8_E4M3, uint8_t, uint8_t)
+#undef TE_FILL
   return cudaErrorInvalidValue;
 }
 

@@ -141,6 +141,18 @@ def test_null_and_reserved_arguments(te):
                             ctypes.c_void_p(ev.ctypes.data), None, None, None) == 1
 
 
+def test_memory_pool_queries_before_gpu(te):
+    """The pool queries validate their arguments and report an empty pool
+    for a device the library has not allocated on (no CUDA call needed)."""
+    lib = te.load_library()
+    r, u = ctypes.c_uint64(7), ctypes.c_uint64(7)
+    assert lib.te_memory_cached(-1, ctypes.byref(r), ctypes.byref(u)) == 1
+    assert lib.te_memory_cached(64, ctypes.byref(r), ctypes.byref(u)) == 1
+    assert lib.te_memory_cached(0, None, ctypes.byref(u)) == 1
+    assert lib.te_memory_cached(63, ctypes.byref(r), ctypes.byref(u)) == 0
+    assert (r.value, u.value) == (0, 0)
+
+
 def test_workspace_bytes(te):
     lib = te.load_library()
     n = 1 << 24
