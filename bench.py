@@ -187,19 +187,27 @@ def make_inputs(args):
 
 
 # DRAM bytes per SpMV step (slice kernel + cut-row finaliser) measured by ncu
-# on this workload (profiles/spmv_dram_fdf_rmat24_ef8.md), valid for the
+# on the small case of the same kernels and layout (R-MAT scale 22, edge
+# factor 8, rows by degree: 557.6 MB against 605.8 MB of algorithmic bytes,
+# 0.920x; profiles/spmv_dram_fdf_rmat22_ef8.md) and scaled to this workload
+# by its algorithmic bytes per step (2,442,972,024: x 4.03); valid for the
 # kernel and layout sources whose SHA-256 is recorded with it
 SPMV_TRAFFIC = {
     "workload": "rmat24_ef8_normadj_seed1",
     "order": "degree",
-    "bytes_per_step": 2.271e9,
+    "bytes_per_step": 2.248e9,
+    "measured_on": "rmat22_ef8_normadj_seed1 (557.6 MB per step), scaled by algorithmic bytes",
     "sources": {
         "paper_2201_07498_gb300/csrc/te_spmv.cu":
-            "1580eee85d0a35494e21ec94b9d48149cb3ac7130d84464146c3fe7deaed5cbb",
+            "5db38d0e3ddacd4551580bfc6b1abf67a2f2257f8594bf52945baf3c0c98f299",
         "paper_2201_07498_gb300/csrc/te_common.cuh":
             "4a92b110c7810ee9286055e9629f3bb8af147b489cdb6326cff63482fe82bba1",
         "paper_2201_07498_gb300/csrc/te_layout.cu":
             "2e04e36f6ff8dddb6c1ec280a506a01b4a00e23d1e40214dc16daa4f7279106c",
+        "paper_2201_07498_gb300/csrc/te_layout_dev.cu":
+            "b9794931a840a978b7559adc0fdccd1090315f9189c296e3e5a4ca4dde7a83e2",
+        "paper_2201_07498_gb300/csrc/te_internal.h":
+            "ede25c8b7fd24933404a2259f94e19e5f7152b938bbc805fab3bc8bec5bcf4e2",
     },
 }
 
@@ -839,6 +847,7 @@ def main():
                          "traffic": (spmv_traffic(workload_config(args, A)["workload"], args.order)
                                      if dom == "spmv" else None),
                          "traffic_unit": "bytes per SpMV step (ncu, DRAM read + write)",
+                         "traffic_source": SPMV_TRAFFIC["measured_on"],
                          "algorithmic_bytes_per_step": d_bytes / max(d_n, 1),
                          "gather_ceiling": {
                              "note": "the SpMV reads one scattered 4-byte x value per "
