@@ -23,6 +23,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -266,6 +267,25 @@ def oracle_thread_scaling(A, v1, steps, seed):
     return out
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def oracle_config(args, A):
     c = workload_config(args, A)
     c["precision"] = "FP64 oracle: binary64 values, vectors and arithmetic"
@@ -300,7 +320,7 @@ def run_reference(args, world, rank):
         "data": "synthetic",
         "config": oracle_config(args, A),
         "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -830,6 +850,7 @@ def main():
         import oracle
         ms_o, _ = oracle_solve_timed(A, v1, K, m, args.seed)
         cpu = {"value": ms_o, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+               "cpu_model": cpu_model(),
                "sample": f"one complete oracle solve on the full workload ({m} Lanczos steps "
                          f"with MGS, Jacobi, {K} Ritz vectors), timed once, not extrapolated",
                "thread_scaling": oracle_thread_scaling(A, v1, args.oracle_steps, args.seed)}
