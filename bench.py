@@ -568,8 +568,9 @@ def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000
     `nreq_high` requests arrive at rates >= 1000/s and `nreq_low` at lower
     rates (so that a rate's arrivals span at most about ten seconds).  A client
     loop submits each request on arrival, runs engine steps and collects the
-    finished requests from the completion queue (eigenvalues and Ritz vectors
-    to host memory).  Latency = completion minus scheduled arrival.  One
+    finished requests from the completion queue (eigenvalues, and Ritz
+    vectors into a pinned host buffer the client reuses).  Latency =
+    completion minus scheduled arrival.  One
     server runs every rate, with the per-class layout autotuner on; a warm-up
     pass over the pool (untimed) tunes its classes first."""
     import numpy as np
@@ -585,6 +586,9 @@ def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000
     # one long-running server with the per-class layout autotuner; a warm-up
     # pass over the pool lets it tune every request class first
     srv = te.Server(max_slots=64, max_krylov_steps=32, budget=24 << 30, autotune=True)
+    # the client collects each request's Ritz vectors into one pinned buffer
+    import torch
+    ubuf = torch.empty(max(A.n * K for A, K, _, _ in pool), dtype=torch.float64).pin_memory()
     t0 = time.perf_counter()
     pend = set(srv.submit(A, K, m, prec, seed=i) for i, (A, K, m, prec) in enumerate(pool))
     while pend:
@@ -598,7 +602,7 @@ def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000
         nreq = nreq_high if rate >= 1000 else nreq_low
         arrive = np.cumsum(rng.exponential(1.0 / rate, nreq))
         lat, tickets, max_live, steps = [], {}, 0, 0
-        host0 = srv.timing()
+        host0, an0 = srv.timing(), srv.analysis()
         i = 0
         start = time.perf_counter()
         while len(lat) < nreq:
@@ -614,17 +618,21 @@ def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000
             steps += 1
             max_live = max(max_live, live)
             for t in srv.completed():
-                if srv.poll(t) is not None:
+                if srv.poll(t, out=ubuf) is not None:
                     lat.append(time.perf_counter() - start - tickets.pop(t))
         wall = time.perf_counter() - start
         lat_ms = np.array(lat) * 1e3
-        host1 = srv.timing()
+        host1, an1 = srv.timing(), srv.analysis()
+        an = {k: an1[k] - an0[k] for k in an1}
         out["rates"][str(rate)] = {
             "requests": nreq, "solves_per_s": nreq / (wall - arrive[0]),
             "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "engine_steps": steps,
             "max_resident": max_live, "wall_s": wall,
-            "host_s": {k: host1[k] - host0[k] for k in host1}}
+            "host_s": {k: host1[k] - host0[k] for k in host1},
+            "mean_batch": an["resident_steps"] / max(an["engine_steps"], 1),
+            "analysis_threads_s": {k: an[k] for k in ("layout_s", "gather_s", "copy_s",
+                                                      "stage_wait_s")}}
     srv.close()
     return out
 

@@ -18,7 +18,8 @@
  *     thread-local message for the last failing call on this thread.
  *   - The caller owns every buffer it passes; the library never frees them.
  *     Work memory is allocated inside the call (or the plan) and freed before
- *     return (or at te_plan_destroy).
+ *     return (or at te_plan_destroy), into the library's device memory pool,
+ *     which keeps it for the next call (te_set_memory_cache).
  *   - Device pointers are CUDA device (or managed) memory of the current
  *     device.  "Host" outputs may be pageable or pinned.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
@@ -437,6 +438,16 @@ te_status te_server_stats(const te_server* srv, int32_t* live, int32_t* pending,
  * (layout analysis and uploads), launching steps, and inside submit. */
 te_status te_server_timing(const te_server* srv, double* wait_s, double* admit_s,
                            double* launch_s, double* submit_s);
+
+/* The analysis threads' cumulative seconds (summed over threads): building
+ * request layouts, gathering a request's arrays into pinned memory, copying
+ * them to the device staging area, waiting for a staging block (turn or
+ * space); the requests they analysed; and the engine steps launched with the
+ * number of solves those steps advanced (their ratio is the mean batch).
+ * Any output may be NULL. */
+te_status te_server_analysis(const te_server* srv, double* layout_s, double* gather_s,
+                             double* copy_s, double* stage_wait_s, int64_t* analysed,
+                             int64_t* engine_steps, int64_t* resident_steps);
 
 void te_server_destroy(te_server* srv);
 

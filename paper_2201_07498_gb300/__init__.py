@@ -118,6 +118,7 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "te_server_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "te_server_analysis": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 7),
     "te_probe_gather": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "te_gram": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p]),
@@ -439,14 +440,24 @@ class Server:
         _check(self._lib.te_server_step(self._h, ctypes.byref(live), ctypes.byref(pend)))
         return live.value, pend.value
 
-    def poll(self, ticket: int, vectors: bool = True):
+    def poll(self, ticket: int, vectors: bool = True, out=None):
         """None while running; else (eigvals [K], eigvecs [n, K] or None,
-        residual estimates [K]) as numpy arrays (raises on a failed request)."""
+        residual estimates [K]) as numpy arrays (raises on a failed request).
+        out: optional float64 buffer of at least K * n elements (a pinned
+        torch tensor, for example) that receives the Ritz vectors instead of
+        a new array; the returned eigvecs then view it."""
         import numpy as np
         n, K = self._meta[ticket][:2]
         ev = np.empty(K)
         res = np.empty(K)
-        U = np.empty((K, n)) if vectors else None
+        U = None
+        if vectors and out is not None:
+            flat = out.numpy() if hasattr(out, "numpy") else np.asarray(out)
+            if flat.dtype != np.float64 or flat.size < K * n or not flat.flags.c_contiguous:
+                raise ValueError("out must be a contiguous float64 buffer of at least K * n")
+            U = flat.reshape(-1)[:K * n].reshape(K, n)
+        elif vectors:
+            U = np.empty((K, n))
         done = ctypes.c_int32()
         rc = self._lib.te_server_poll(self._h, ticket, ctypes.byref(done),
                                       ctypes.c_void_p(ev.ctypes.data),
@@ -494,6 +505,17 @@ class Server:
         v = [ctypes.c_double() for _ in range(4)]
         _check(self._lib.te_server_timing(self._h, *[ctypes.byref(x) for x in v]))
         return {k: x.value for k, x in zip(("wait_s", "admit_s", "launch_s", "submit_s"), v)}
+
+    def analysis(self):
+        """Analysis threads' cumulative seconds (layout, gather into pinned
+        memory, copy to the device, staging wait), requests analysed, engine
+        steps and the solves they advanced."""
+        d = [ctypes.c_double() for _ in range(4)]
+        i = [ctypes.c_int64() for _ in range(3)]
+        _check(self._lib.te_server_analysis(self._h, *[ctypes.byref(x) for x in d + i]))
+        return {"layout_s": d[0].value, "gather_s": d[1].value, "copy_s": d[2].value,
+                "stage_wait_s": d[3].value, "analysed": i[0].value,
+                "engine_steps": i[1].value, "resident_steps": i[2].value}
 
     def close(self):
         if getattr(self, "_h", None):

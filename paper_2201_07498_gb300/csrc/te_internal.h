@@ -386,10 +386,12 @@ struct BatchTable {
   int item_off[SRV_MAX_SLOTS + 1];
   BatchSlot slot[SRV_MAX_SLOTS];
 };
-constexpr int SRV_SPMV_BLOCKS = 1216;  // persistent grid of the batched SpMV (8 warps each)
-constexpr int SRV_FIN_BLOCKS = 608;    // persistent grid of the batched finaliser
+// persistent grids of the batched SpMV (8 warps a block) and finaliser: as
+// many blocks as fit on num_sms SMs at once (te_spmv.cu)
+cudaError_t batch_spmv_grids(int num_sms, int* spmv_blocks, int* fin_blocks);
 // y_s = M_s v_{s, step_s} for every slot (te_spmv.cu)
-cudaError_t launch_batch_spmv(const BatchTable* T, cudaStream_t s);
+cudaError_t launch_batch_spmv(const BatchTable* T, int spmv_blocks, int fin_blocks,
+                              cudaStream_t s);
 // passes of the Lanczos step of every slot; restart = the breakdown passes
 // (te_reorth.cu); L: the launch configuration for the engine's largest m
 cudaError_t launch_batch_pass(int mode, const BatchTable* T, int restart, const PassLaunch& L,

@@ -147,11 +147,39 @@ struct Request {
 
 // Host threads that build the SpMV layouts of submitted requests while the
 // engine runs, so that admission only allocates, copies and launches.
+// An analysis thread's pinned bounce buffer: a request's arrays are copied
+// into it by the CPU and go to the device in one DMA.  (Copies straight from
+// pageable memory issued by several threads at once ran at ≈ 5 GB/s per
+// thread, and worse the more threads issued them.)
+constexpr size_t BOUNCE_MAX = (size_t)256 << 20;  // larger requests copy from pageable memory
+struct Bounce {
+  char* p = nullptr;
+  size_t cap = 0;
+  bool reserve(size_t b) {
+    if (b <= cap) return true;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    const size_t want = std::max(b + b / 2, (size_t)64 << 20);
+    if (cudaHostAlloc(reinterpret_cast<void**>(&p), want, cudaHostAllocDefault) != cudaSuccess) {
+      (void)cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    cap = want;
+    return true;
+  }
+  ~Bounce() {
+    if (p) cudaFreeHost(p);
+  }
+};
+
 class AnalysisPool {
  public:
   // fn builds a request's layout (on an analysis thread, device `dev`
-  // current, with a stream of its own)
-  void start(unsigned nthreads, int dev, std::function<void(Request*, cudaStream_t)> fn) {
+  // current, with a stream and a bounce buffer of its own)
+  void start(unsigned nthreads, int dev,
+             std::function<void(Request*, cudaStream_t, Bounce*)> fn) {
     fn_ = std::move(fn);
     dev_ = dev;
     for (unsigned t = 0; t < nthreads; ++t) th_.emplace_back([this] { run(); });
@@ -184,6 +212,7 @@ class AnalysisPool {
     cudaSetDevice(dev_);
     cudaStream_t ts = nullptr;
     cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+    Bounce bounce;
     for (;;) {
       Request* R = nullptr;
       {
@@ -193,7 +222,7 @@ class AnalysisPool {
         R = q_.front();
         q_.pop_front();
       }
-      fn_(R, ts);
+      fn_(R, ts, &bounce);
       {
         std::lock_guard<std::mutex> lk(mu_);
         R->analysed.store(1, std::memory_order_release);
@@ -211,7 +240,7 @@ class AnalysisPool {
   std::deque<Request*> q_;
   bool stop_ = false;
   int dev_ = 0;
-  std::function<void(Request*, cudaStream_t)> fn_;
+  std::function<void(Request*, cudaStream_t, Bounce*)> fn_;
 };
 
 struct SlotResult {  // pinned, written by the finishing copies
@@ -237,6 +266,7 @@ int ctas_for(int64_t n_pad) {
 
 struct te_server {
   int max_slots = 0, max_m = 0, use_graph = 1, num_sms = 0;
+  int spmv_blocks = 0, fin_blocks = 0;  // persistent grids of the batched SpMV and finaliser
   // admissions run on their own stream, beside the engine step: a copy from
   // pageable host memory first waits for the work already queued on its
   // stream, which then is only the earlier admissions
@@ -258,9 +288,13 @@ struct te_server {
   std::vector<Request*> slots;
   std::vector<std::pair<size_t, size_t>> deferred;  // pool blocks to free after the next sync
   // solves that completed their m steps: their Jacobi and Ritz kernels run on
-  // a stream of their own, beside the following engine steps, and they are
-  // retired when that batch's event has completed
-  cudaStream_t fs = nullptr;
+  // finishing streams, beside the following engine steps (round robin over
+  // SRV_FIN_STREAMS streams, so that the Jacobi kernels of solves finishing
+  // close together run at the same time on different SMs), and they are
+  // retired when their batch's event has completed
+  static constexpr int SRV_FIN_STREAMS = 8;
+  cudaStream_t fs[SRV_FIN_STREAMS] = {};
+  int fs_next = 0;
   cudaEvent_t ev_step = nullptr;
   struct FinishBatch {
     cudaEvent_t ev;
@@ -286,6 +320,11 @@ struct te_server {
   std::map<int, int> tuned;
   std::set<int> tuning;
   double t_wait = 0, t_admit = 0, t_launch = 0, t_submit = 0;  // host seconds, cumulative
+  // analysis threads (nanoseconds, summed over threads): layout builds, the
+  // gathers into the bounce buffers, the DMAs into the staging area, waits
+  // for the staging turn or space; requests analysed
+  std::atomic<int64_t> a_layout_ns{0}, a_gather_ns{0}, a_stage_ns{0}, a_wait_ns{0}, a_count{0};
+  int64_t engine_steps = 0, resident_steps = 0;  // steps launched, solves they advanced
   AnalysisPool analysis;
 };
 
@@ -341,8 +380,7 @@ int tune_request(const Request* R) {
 struct StageLayout {
   size_t rp, ci, val, src, len, sl, out, lr, total;
 };
-StageLayout stage_layout(const Request& R) {
-  const SellHost& H = R.layout;
+StageLayout stage_offsets(const Request& R, size_t lanes, size_t slices, size_t lrows) {
   StageLayout L{};
   size_t off = 0;
   auto take = [&](size_t b) {
@@ -353,53 +391,106 @@ StageLayout stage_layout(const Request& R) {
   L.rp = take((size_t)(R.n + 1) * 8);
   L.ci = take((size_t)R.nnz * 4);
   L.val = take(R.val_bytes);
-  L.src = take(H.vsrc.size() * 8);
-  L.len = take(H.vlen.size() * 4);
-  L.sl = take(H.slices.size() * sizeof(SellSlice));
-  L.out = take(H.vout.size() * 4);
-  L.lr = take(H.lrows.size() * sizeof(LongRow));
+  L.src = take(lanes * 8);
+  L.len = take(lanes * 4);
+  L.sl = take(slices * sizeof(SellSlice));
+  L.out = take(lanes * 4);
+  L.lr = take(lrows * sizeof(LongRow));
   L.total = off;
   return L;
 }
+// the offsets of R's built layout
+StageLayout stage_layout(const Request& R) {
+  const SellHost& H = R.layout;
+  return stage_offsets(R, H.vout.size(), H.slices.size(), H.lrows.size());
+}
+// a block that holds R's arrays under any candidate layout: a row of length
+// L > 0 gives at most L / vmax + 1 pieces, a window's pieces fill their
+// slices but the last, cut rows number at most nnz / vmax
+StageLayout stage_bound(const Request& R) {
+  int vmin = TUNE_VMAX[0], wmin = TUNE_WINDOW[0];
+  for (int c = 1; c < TUNE_N; ++c) {
+    vmin = std::min(vmin, TUNE_VMAX[c]);
+    wmin = std::min(wmin, TUNE_WINDOW[c]);
+  }
+  const size_t pieces = (size_t)R.n + (size_t)R.nnz / (size_t)vmin;
+  const size_t nwin = (size_t)((R.n + wmin - 1) / wmin);
+  const size_t slices = pieces / SELL_C + nwin + 1;
+  return stage_offsets(R, slices * SELL_C, slices, (size_t)R.nnz / (size_t)vmin + 1);
+}
 
-// Copy R's CSR and layout into the staging area: the block is taken in
-// submission order (waiting while the area is full: admissions free it in
-// that order), the copies then run on the thread's stream.  A request larger
-// than the whole area is not staged.
-void stage_request(te_server* S, Request* R, cudaStream_t ts) {
-  const StageLayout L = stage_layout(*R);
+// Take R's block of the staging area, sized by stage_bound, in submission
+// order (waiting while the area is full: admissions free it in that order,
+// so the head of the queue always progresses).  Called when an analysis
+// thread picks R up, so a thread waits only for the blocks of earlier
+// requests, not for their layouts.  A request larger than the whole area is
+// not staged (its copies run at admission).
+void stage_reserve(te_server* S, Request* R) {
+  const size_t bytes = stage_bound(*R).total;
+  const double w0 = now_s();
   {
     std::unique_lock<std::mutex> lk(S->stage_mu);
     S->stage_cv.wait(lk, [&] { return S->stopping || S->stage_turn == R->seq; });
     if (S->stopping) return;
-    if (L.total <= S->stage.size) {
+    if (bytes <= S->stage.size) {
       size_t off = 0;
-      S->stage_cv.wait(lk, [&] { return S->stopping || S->stage.alloc(L.total, &off); });
+      S->stage_cv.wait(lk, [&] { return S->stopping || S->stage.alloc(bytes, &off); });
       if (!S->stopping) {
         R->stage_off = off;
-        R->stage_bytes = L.total;
+        R->stage_bytes = bytes;
       }
     }
     S->stage_turn += 1;
   }
   S->stage_cv.notify_all();
+  S->a_wait_ns += (int64_t)((now_s() - w0) * 1e9);
+}
+
+// Copy R's CSR and built layout into its staging block: gathered by the CPU
+// into the thread's pinned bounce buffer, then one DMA on the thread's stream
+// (array by array from pageable memory when the buffer cannot hold them).
+void stage_fill(te_server* S, Request* R, cudaStream_t ts, Bounce* B) {
   if (!R->stage_bytes) return;
-  char* G = S->stage.base + R->stage_off;
+  const StageLayout L = stage_layout(*R);
   const SellHost& H = R->layout;
+  char* G = S->stage.base + R->stage_off;
+  const double c0 = now_s();
+  const bool bounced = L.total <= BOUNCE_MAX && B->reserve(L.total);
+  if (bounced) {
+    auto put = [&](size_t o, const void* src, size_t b) {
+      if (b) std::memcpy(B->p + o, src, b);
+    };
+    put(L.rp, R->rp, (size_t)(R->n + 1) * 8);
+    put(L.ci, R->ci, (size_t)R->nnz * 4);
+    put(L.val, R->vals, R->val_bytes);
+    put(L.src, H.vsrc.data(), H.vsrc.size() * 8);
+    put(L.len, H.vlen.data(), H.vlen.size() * 4);
+    put(L.sl, H.slices.data(), H.slices.size() * sizeof(SellSlice));
+    put(L.out, H.vout.data(), H.vout.size() * 4);
+    put(L.lr, H.lrows.data(), H.lrows.size() * sizeof(LongRow));
+  }
+  const double c1 = now_s();
+  S->a_gather_ns += (int64_t)((c1 - c0) * 1e9);
   cudaError_t e = cudaSuccess;
-  auto h2d = [&](size_t o, const void* src, size_t b) {
-    if (e == cudaSuccess && b) e = cudaMemcpyAsync(G + o, src, b, cudaMemcpyHostToDevice, ts);
-  };
-  h2d(L.rp, R->rp, (size_t)(R->n + 1) * 8);
-  h2d(L.ci, R->ci, (size_t)R->nnz * 4);
-  h2d(L.val, R->vals, R->val_bytes);
-  h2d(L.src, H.vsrc.data(), H.vsrc.size() * 8);
-  h2d(L.len, H.vlen.data(), H.vlen.size() * 4);
-  h2d(L.sl, H.slices.data(), H.slices.size() * sizeof(SellSlice));
-  h2d(L.out, H.vout.data(), H.vout.size() * 4);
-  h2d(L.lr, H.lrows.data(), H.lrows.size() * sizeof(LongRow));
+  if (bounced) {
+    e = cudaMemcpyAsync(G, B->p, L.total, cudaMemcpyHostToDevice, ts);
+  } else {
+    auto h2d = [&](size_t o, const void* src, size_t b) {
+      if (e == cudaSuccess && b) e = cudaMemcpyAsync(G + o, src, b, cudaMemcpyHostToDevice, ts);
+    };
+    h2d(L.rp, R->rp, (size_t)(R->n + 1) * 8);
+    h2d(L.ci, R->ci, (size_t)R->nnz * 4);
+    h2d(L.val, R->vals, R->val_bytes);
+    h2d(L.src, H.vsrc.data(), H.vsrc.size() * 8);
+    h2d(L.len, H.vlen.data(), H.vlen.size() * 4);
+    h2d(L.sl, H.slices.data(), H.slices.size() * sizeof(SellSlice));
+    h2d(L.out, H.vout.data(), H.vout.size() * 4);
+    h2d(L.lr, H.lrows.data(), H.lrows.size() * sizeof(LongRow));
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+  S->a_stage_ns += (int64_t)((now_s() - c1) * 1e9);
   if (e != cudaSuccess) {  // fall back to copies at admission
+    (void)cudaGetLastError();
     std::lock_guard<std::mutex> lk(S->stage_mu);
     S->stage.release(R->stage_off, R->stage_bytes);
     R->stage_bytes = 0;
@@ -409,7 +500,8 @@ void stage_request(te_server* S, Request* R, cudaStream_t ts) {
 // An analysis thread's work: the request's layout, with its class's tuned
 // candidate when the server tunes (the class's first request is tuned here;
 // others of the class wait for it), then its staging
-void analyse_request(te_server* S, Request* R, cudaStream_t ts) {
+void analyse_request(te_server* S, Request* R, cudaStream_t ts, Bounce* B) {
+  stage_reserve(S, R);
   int cand = 0;
   if (S->autotune) {
     const int key = request_class(R);
@@ -435,14 +527,17 @@ void analyse_request(te_server* S, Request* R, cudaStream_t ts) {
     }
   }
   std::string perr;
+  const double t0 = now_s();
   make_sell(R->rp, R->n, R->nnz, R->layout, perr, TUNE_WINDOW[cand], TUNE_VMAX[cand]);
+  S->a_layout_ns += (int64_t)((now_s() - t0) * 1e9);
   R->cand = cand;
-  stage_request(S, R, ts);
+  stage_fill(S, R, ts, B);
+  S->a_count += 1;
 }
 
 // the batched step: SpMV (+ cut rows), three passes, three restart passes
 cudaError_t enqueue_step(te_server* S, cudaStream_t s) {
-  cudaError_t e = launch_batch_spmv(S->table_d, s);
+  cudaError_t e = launch_batch_spmv(S->table_d, S->spmv_blocks, S->fin_blocks, s);
   for (int restart = 0; restart < 2 && e == cudaSuccess; ++restart) {
     if (e == cudaSuccess) e = launch_batch_pass(MODE_DOT, S->table_d, restart, S->Lpass, s);
     if (e == cudaSuccess) e = launch_batch_pass(MODE_AXPY_DOT, S->table_d, restart, S->Lpass, s);
@@ -744,7 +839,9 @@ te_status te_server_create(const te_server_options* o, te_server** out) {
   SRV_CK(cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking), "create stream");
   SRV_CK(cudaStreamCreateWithFlags(&S->ps, cudaStreamNonBlocking), "create stream");
   SRV_CK(cudaStreamCreateWithFlags(&S->as, cudaStreamNonBlocking), "create stream");
-  SRV_CK(cudaStreamCreateWithFlags(&S->fs, cudaStreamNonBlocking), "create stream");
+  for (cudaStream_t& f : S->fs)
+    SRV_CK(cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking), "create stream");
+  SRV_CK(batch_spmv_grids(S->num_sms, &S->spmv_blocks, &S->fin_blocks), "size the SpMV grids");
   SRV_CK(cudaEventCreateWithFlags(&S->ev_step, cudaEventDisableTiming), "create event");
   SRV_CK(cudaEventCreateWithFlags(&S->ev_admit, cudaEventDisableTiming), "create event");
   SRV_CK(cudaEventCreateWithFlags(&S->ev, cudaEventDisableTiming), "create event");
@@ -768,7 +865,9 @@ te_status te_server_create(const te_server_options* o, te_server** out) {
     unsigned nt = std::thread::hardware_concurrency();
     nt = nt > 2 ? nt / 2 : 1;
     if (nt > 8) nt = 8;
-    S->analysis.start(nt, dev, [S](Request* R, cudaStream_t ts) { analyse_request(S, R, ts); });
+    S->analysis.start(nt, dev, [S](Request* R, cudaStream_t ts, Bounce* B) {
+      analyse_request(S, R, ts, B);
+    });
   }
   if (S->use_graph) {
     cudaGraph_t g = nullptr;
@@ -798,7 +897,8 @@ void te_server_destroy(te_server* S) {
   S->analysis.stop();  // no thread touches a request after this
   if (S->s) cudaStreamSynchronize(S->s);
   if (S->as) cudaStreamSynchronize(S->as);
-  if (S->fs) cudaStreamSynchronize(S->fs);
+  for (cudaStream_t f : S->fs)
+    if (f) cudaStreamSynchronize(f);
   for (auto& kv : S->reqs) delete kv.second;
   if (S->gexec) cudaGraphExecDestroy(S->gexec);
   if (S->ev) cudaEventDestroy(S->ev);
@@ -807,7 +907,8 @@ void te_server_destroy(te_server* S) {
   if (S->res_h) cudaFreeHost(S->res_h);
   if (S->s) cudaStreamDestroy(S->s);
   if (S->as) cudaStreamDestroy(S->as);
-  if (S->fs) cudaStreamDestroy(S->fs);
+  for (cudaStream_t f : S->fs)
+    if (f) cudaStreamDestroy(f);
   if (S->ev_step) cudaEventDestroy(S->ev_step);
   for (auto& b : S->batches) cudaEventDestroy(b.ev);
   for (cudaEvent_t e : S->ev_free) cudaEventDestroy(e);
@@ -873,14 +974,21 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
       stepping |= R && (R->state == REQ_RUNNING || R->state == REQ_ADMITTED);
       free_slot |= R == nullptr;
     }
-    while (!S->batches.empty()) {
-      te_server::FinishBatch& b = S->batches.front();
+    bool retired = false;
+    for (auto it = S->batches.begin(); it != S->batches.end();) {
+      te_server::FinishBatch& b = *it;
       cudaError_t q = cudaEventQuery(b.ev);
       if (q == cudaErrorNotReady) {
-        if (stepping || (free_slot && !S->pending.empty())) break;
+        // the batches run on several streams: a later one may be done first
+        if (stepping || retired || (free_slot && !S->pending.empty()) ||
+            it != S->batches.begin()) {
+          ++it;
+          continue;
+        }
         q = cudaEventSynchronize(b.ev);
       }
       SRV_CK(q, "finish solves");
+      retired = true;
       for (int k : b.slots) {
         Request* R = S->slots[k];
         const SlotResult& o = S->res_h[k];
@@ -894,7 +1002,7 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
         R->slot = -1;
       }
       S->ev_free.push_back(b.ev);
-      S->batches.pop_front();
+      it = S->batches.erase(it);
     }
   }
   // the admissions of the previous call ran on their own stream
@@ -949,37 +1057,45 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
   }
   T->nslots = ns;
   if (ns > 0) {
+    S->engine_steps += 1;
+    S->resident_steps += ns;
     SRV_CK(cudaMemcpyAsync(S->table_d, T, sizeof(BatchTable), cudaMemcpyHostToDevice, S->s),
            "upload the step table");
     if (S->gexec) SRV_CK(cudaGraphLaunch(S->gexec, S->s), "launch the engine step");
     else SRV_CK(enqueue_step(S, S->s), "engine step");
     // solves that completed their m steps: Jacobi and Ritz vectors on the
     // finishing stream, after this step
-    te_server::FinishBatch batch;
+    te_server::FinishBatch batch[te_server::SRV_FIN_STREAMS];
+    bool recorded = false;
     for (int k = 0; k < S->max_slots; ++k) {
       Request* R = S->slots[k];
       if (!R || R->state != REQ_RUNNING) continue;
       R->step += 1;
       if (R->step == R->m) {
-        if (batch.slots.empty()) {
+        if (!recorded) {
           SRV_CK(cudaEventRecord(S->ev_step, S->s), "record");
-          SRV_CK(cudaStreamWaitEvent(S->fs, S->ev_step, 0), "wait");
+          recorded = true;
         }
-        SRV_CK(enqueue_finish(S, R, S->fs), "finish a solve");
+        const int f = S->fs_next;
+        S->fs_next = (f + 1) % te_server::SRV_FIN_STREAMS;
+        if (batch[f].slots.empty())
+          SRV_CK(cudaStreamWaitEvent(S->fs[f], S->ev_step, 0), "wait");
+        SRV_CK(enqueue_finish(S, R, S->fs[f]), "finish a solve");
         R->state = REQ_FINISHING;
-        batch.slots.push_back(k);
+        batch[f].slots.push_back(k);
       }
     }
-    if (!batch.slots.empty()) {
+    for (int f = 0; f < te_server::SRV_FIN_STREAMS; ++f) {
+      if (batch[f].slots.empty()) continue;
       if (S->ev_free.empty()) {
         cudaEvent_t e = nullptr;
         SRV_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "create event");
         S->ev_free.push_back(e);
       }
-      batch.ev = S->ev_free.back();
+      batch[f].ev = S->ev_free.back();
       S->ev_free.pop_back();
-      SRV_CK(cudaEventRecord(batch.ev, S->fs), "record");
-      S->batches.push_back(std::move(batch));
+      SRV_CK(cudaEventRecord(batch[f].ev, S->fs[f]), "record");
+      S->batches.push_back(std::move(batch[f]));
     }
   }
   double t2 = now_s();
@@ -1047,6 +1163,20 @@ te_status te_server_timing(const te_server* S, double* wait_s, double* admit_s, 
   if (admit_s) *admit_s = S->t_admit;
   if (launch_s) *launch_s = S->t_launch;
   if (submit_s) *submit_s = S->t_submit;
+  return TE_OK;
+}
+
+te_status te_server_analysis(const te_server* S, double* layout_s, double* gather_s,
+                             double* copy_s, double* stage_wait_s, int64_t* analysed,
+                             int64_t* engine_steps, int64_t* resident_steps) {
+  if (!S) return srv_fail(TE_ERR_INVALID_ARG, "server is NULL");
+  if (layout_s) *layout_s = 1e-9 * (double)S->a_layout_ns.load();
+  if (gather_s) *gather_s = 1e-9 * (double)S->a_gather_ns.load();
+  if (copy_s) *copy_s = 1e-9 * (double)S->a_stage_ns.load();
+  if (stage_wait_s) *stage_wait_s = 1e-9 * (double)S->a_wait_ns.load();
+  if (analysed) *analysed = S->a_count.load();
+  if (engine_steps) *engine_steps = S->engine_steps;
+  if (resident_steps) *resident_steps = S->resident_steps;
   return TE_OK;
 }
 

@@ -405,14 +405,33 @@ TE_DEV int find_slot(const int64_t* off, int nslots, int64_t g) {
   return lo;
 }
 
-__global__ void __launch_bounds__(32 * SPMV_WPB) batch_spmv_kernel(const BatchTable* T) {
-  const int lane = threadIdx.x & 31;
+// the step's table (offsets and slot records) in shared memory: each warp
+// looks up the solve of every slice it takes, so the lookups stay on chip
+struct BatchCache {
+  int64_t off[SRV_MAX_SLOTS + 1];
+  BatchSlot slot[SRV_MAX_SLOTS];
+};
+static_assert(sizeof(BatchSlot) % 8 == 0, "slot records are copied as 8-byte words");
+TE_DEV int load_batch_cache(BatchCache& c, const BatchTable* T, const int64_t* off) {
   const int ns = T->nslots;
-  const int64_t total = T->slice_off[ns];
+  for (int i = threadIdx.x; i <= ns; i += blockDim.x) c.off[i] = off[i];
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(T->slot);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(c.slot);
+  const int words = ns * (int)(sizeof(BatchSlot) / 8);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return ns;
+}
+
+__global__ void __launch_bounds__(32 * SPMV_WPB) batch_spmv_kernel(const BatchTable* T) {
+  __shared__ BatchCache c;
+  const int lane = threadIdx.x & 31;
+  const int ns = load_batch_cache(c, T, T->slice_off);
+  const int64_t total = c.off[ns];
   for (int64_t g = (int64_t)blockIdx.x * SPMV_WPB + (threadIdx.x >> 5); g < total;
        g += (int64_t)gridDim.x * SPMV_WPB) {
-    const int sidx = find_slot(T->slice_off, ns, g);
-    const BatchSlot& B = T->slot[sidx];
+    const int sidx = find_slot(c.off, ns, g);
+    const BatchSlot& B = c.slot[sidx];
     SpmvArgs a;
     a.slices = B.slices;
     a.vout = B.vout;
@@ -425,7 +444,7 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) batch_spmv_kernel(const BatchTa
     a.vpart = B.vpart;
     a.nslices = B.nslices;
     a.hot = 0;
-    const int slice = (int)(g - T->slice_off[sidx]);
+    const int slice = (int)(g - c.off[sidx]);
     if (B.vk == TE_BF16) spmv_slice<PREC_FDF, TE_BF16, false>(a, slice, lane);
     else spmv_slice<PREC_FDF, TE_F32, false>(a, slice, lane);
   }
@@ -434,8 +453,9 @@ __global__ void __launch_bounds__(32 * SPMV_WPB) batch_spmv_kernel(const BatchTa
 // cut rows of every live solve, FIN_G lanes per row; the loop runs whole
 // warps so that every lane reaches the shuffles
 __global__ void batch_finalize_kernel(const BatchTable* T) {
-  const int ns = T->nslots;
-  const int64_t total = T->lrow_off[ns];
+  __shared__ BatchCache c;
+  const int ns = load_batch_cache(c, T, T->lrow_off);
+  const int64_t total = c.off[ns];
   const int lane = threadIdx.x & 31, sub = lane & (FIN_G - 1);
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / FIN_G);
@@ -445,8 +465,9 @@ __global__ void batch_finalize_kernel(const BatchTable* T) {
     LongRow lr{0, 0, 0, 0};
     const BatchSlot* B = nullptr;
     if (live) {
-      B = &T->slot[find_slot(T->lrow_off, ns, g)];
-      lr = B->lrows[g - T->lrow_off[B - T->slot]];
+      const int sidx = find_slot(c.off, ns, g);
+      B = &c.slot[sidx];
+      lr = B->lrows[g - c.off[sidx]];
     }
     dacc acc = dacc_zero();
     for (int c = sub; c < lr.count; c += FIN_G) {
@@ -458,11 +479,26 @@ __global__ void batch_finalize_kernel(const BatchTable* T) {
   }
 }
 
-cudaError_t launch_batch_spmv(const BatchTable* T, cudaStream_t s) {
-  batch_spmv_kernel<<<SRV_SPMV_BLOCKS, 32 * SPMV_WPB, 0, s>>>(T);
+// persistent grids that fit on the GPU at once (a grid larger than that
+// leaves a second wave of blocks to start after the first ones finish)
+cudaError_t batch_spmv_grids(int num_sms, int* spmv_blocks, int* fin_blocks) {
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_spmv_kernel,
+                                                                32 * SPMV_WPB, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_finalize_kernel, 256, 0);
+  if (e != cudaSuccess) return e;
+  *spmv_blocks = std::max(a, 1) * num_sms;
+  *fin_blocks = std::max(b, 1) * num_sms;
+  return cudaSuccess;
+}
+
+cudaError_t launch_batch_spmv(const BatchTable* T, int spmv_blocks, int fin_blocks,
+                              cudaStream_t s) {
+  batch_spmv_kernel<<<spmv_blocks, 32 * SPMV_WPB, 0, s>>>(T);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  batch_finalize_kernel<<<SRV_FIN_BLOCKS, 256, 0, s>>>(T);
+  batch_finalize_kernel<<<fin_blocks, 256, 0, s>>>(T);
   return cudaGetLastError();
 }
 

@@ -213,3 +213,32 @@ def test_autotuned_server_matches_oracle(te):
         scale = np.max(np.abs(ref.eigvals))
         perm = match_pairs(ev, ref.eigvals, 1e-6 * scale)
         assert np.max(np.abs(ev - ref.eigvals[perm])) <= 1e-6 * scale
+
+
+def test_poll_into_pinned_buffer_and_many_finishing_together(te):
+    """Eight requests finish at the same step (their finishing work runs on
+    several streams at once): every result collected into a reused pinned
+    buffer equals the same request served alone into a new array."""
+    mats = _mix()[:4] * 2
+    srv = te.Server(max_slots=16, max_krylov_steps=32, budget=1 << 30)
+    tickets = [srv.submit(A, 6, 12, "fdf", seed=20 + i) for i, A in enumerate(mats)]
+    buf = torch.empty(max(A.n for A in mats) * 6, dtype=torch.float64).pin_memory()
+    got, pend = {}, list(tickets)
+    for _ in range(10000):
+        srv.step()
+        for t in list(pend):
+            r = srv.poll(t, out=buf)
+            if r is not None:
+                got[t] = (r[0].copy(), r[1].copy(), r[2].copy())
+                pend.remove(t)
+        if not pend:
+            break
+    assert not pend
+    srv.close()
+    for i, (A, t) in enumerate(zip(mats, tickets)):
+        alone = te.Server(max_slots=1, max_krylov_steps=32, budget=256 << 20)
+        ta = alone.submit(A, 6, 12, "fdf", seed=20 + i)
+        ev, U, res = _drain(alone, [ta])[ta]
+        alone.close()
+        assert np.array_equal(ev, got[t][0]) and np.array_equal(U, got[t][1])
+        assert np.array_equal(res, got[t][2])
