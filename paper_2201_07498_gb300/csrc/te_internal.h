@@ -357,7 +357,7 @@ cudaError_t launch_gram(const double* U, int64_t n, int K, double* partials, int
 
 // ---- serving engine: one launch per phase for every live solve ----
 constexpr int SRV_MAX_SLOTS = 64;  // solves resident at once
-constexpr int SRV_MAX_CTAS = 16;   // pass CTAs per solve (fixed by its size alone)
+constexpr int SRV_MAX_CTAS = 32;   // pass CTAs per solve (fixed by its size alone)
 
 // one live solve (FDF arithmetic: binary32 basis, binary32 or bfloat16 values)
 struct BatchSlot {
