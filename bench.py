@@ -189,7 +189,7 @@ def make_inputs(args):
 
 # DRAM bytes per SpMV step (slice kernel + cut-row finaliser) measured by ncu
 # on the small case of the same kernels and layout (R-MAT scale 22, edge
-# factor 8, rows by degree: 557.6 MB against 605.8 MB of algorithmic bytes,
+# factor 8, rows by degree: 557.4 MB against 605.8 MB of algorithmic bytes,
 # 0.920x; profiles/spmv_dram_fdf_rmat22_ef8.md) and scaled to this workload
 # by its algorithmic bytes per step (2,442,972,024: x 4.03); valid for the
 # kernel and layout sources whose SHA-256 is recorded with it
@@ -197,10 +197,10 @@ SPMV_TRAFFIC = {
     "workload": "rmat24_ef8_normadj_seed1",
     "order": "degree",
     "bytes_per_step": 2.248e9,
-    "measured_on": "rmat22_ef8_normadj_seed1 (557.6 MB per step), scaled by algorithmic bytes",
+    "measured_on": "rmat22_ef8_normadj_seed1 (557.4 MB per step), scaled by algorithmic bytes",
     "sources": {
         "paper_2201_07498_gb300/csrc/te_spmv.cu":
-            "5db38d0e3ddacd4551580bfc6b1abf67a2f2257f8594bf52945baf3c0c98f299",
+            "0ddeb9b3a8d19cd98cc189d7eb2a82f624f922edd1a0ad9b13b9a3ea11ef81ea",
         "paper_2201_07498_gb300/csrc/te_common.cuh":
             "4a92b110c7810ee9286055e9629f3bb8af147b489cdb6326cff63482fe82bba1",
         "paper_2201_07498_gb300/csrc/te_layout.cu":
@@ -208,7 +208,7 @@ SPMV_TRAFFIC = {
         "paper_2201_07498_gb300/csrc/te_layout_dev.cu":
             "b9794931a840a978b7559adc0fdccd1090315f9189c296e3e5a4ca4dde7a83e2",
         "paper_2201_07498_gb300/csrc/te_internal.h":
-            "ede25c8b7fd24933404a2259f94e19e5f7152b938bbc805fab3bc8bec5bcf4e2",
+            "ee27e2ed3bc30a8907acafd806e9458318e59c3f91e7fbdc16be11a9f6e74a8c",
     },
 }
 
