@@ -77,6 +77,10 @@ def parse():
                         "--edge-factor / --seed R-MAT graph and exit (for the order study)")
     p.add_argument("--no-banded", action="store_true",
                    help="skip the SpMV on a banded matrix of the same size (cache-friendly gathers)")
+    p.add_argument("--serving-only", default=None, metavar="RATES",
+                   help="only run the serving leg at these comma-separated arrival rates "
+                        "(--serving-requests requests each) and print its JSON (for profiling "
+                        "the engine)")
     return p.parse_args()
 
 
@@ -603,23 +607,30 @@ def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000
         arrive = np.cumsum(rng.exponential(1.0 / rate, nreq))
         lat, tickets, max_live, steps = [], {}, 0, 0
         host0, an0 = srv.timing(), srv.analysis()
+        client = {"submit_s": 0.0, "step_s": 0.0, "collect_s": 0.0}  # the client loop's wall time
         i = 0
         start = time.perf_counter()
         while len(lat) < nreq:
-            now = time.perf_counter() - start
+            c0 = time.perf_counter()
+            now = c0 - start
             while i < nreq and arrive[i] <= now:
                 A, K, m, prec = pool[i % npool]
                 tickets[srv.submit(A, K, m, prec, seed=i)] = arrive[i]
                 i += 1
+            c1 = time.perf_counter()
+            client["submit_s"] += c1 - c0
             if not tickets:
                 time.sleep(max(0.0, min(arrive[i] - now, 0.01)))
                 continue
             live, _ = srv.step()
+            c2 = time.perf_counter()
+            client["step_s"] += c2 - c1
             steps += 1
             max_live = max(max_live, live)
             for t in srv.completed():
                 if srv.poll(t, out=ubuf) is not None:
                     lat.append(time.perf_counter() - start - tickets.pop(t))
+            client["collect_s"] += time.perf_counter() - c2
         wall = time.perf_counter() - start
         lat_ms = np.array(lat) * 1e3
         host1, an1 = srv.timing(), srv.analysis()
@@ -631,6 +642,7 @@ def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000
             "max_resident": max_live, "wall_s": wall,
             "host_s": {k: host1[k] - host0[k] for k in host1},
             "mean_batch": an["resident_steps"] / max(an["engine_steps"], 1),
+            "client_s": client,
             "analysis_threads_s": {k: an[k] for k in ("layout_s", "gather_s", "copy_s",
                                                       "stage_wait_s")}}
     srv.close()
@@ -711,6 +723,13 @@ def main():
     args = parse()
     if args.spmv_order_probe:
         spmv_order_probe(args)
+        return
+    if args.serving_only:
+        import paper_2201_07498_gb300 as te
+        te.load_library(build_if_missing=True)
+        rates = tuple(int(r) for r in args.serving_only.split(","))
+        print(json.dumps(serving(te, args.serving_requests, min(1000, args.serving_requests),
+                                 rates=rates)), flush=True)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
