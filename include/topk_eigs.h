@@ -434,10 +434,13 @@ te_status te_server_classes(te_server* srv, int32_t* class_key, int32_t* window,
 te_status te_server_stats(const te_server* srv, int32_t* live, int32_t* pending,
                           size_t* pool_used, size_t* pool_peak);
 
-/* Cumulative host seconds: waiting for engine steps, admitting requests
- * (layout analysis and uploads), launching steps, and inside submit. */
+/* Cumulative host seconds of the calling threads: waiting for engine steps,
+ * admitting requests (pool allocation, device copies and fills), launching
+ * steps, inside submit, and inside poll (copying the Ritz vectors out;
+ * releasing the request).  Any output may be NULL. */
 te_status te_server_timing(const te_server* srv, double* wait_s, double* admit_s,
-                           double* launch_s, double* submit_s);
+                           double* launch_s, double* submit_s, double* poll_copy_s,
+                           double* poll_free_s);
 
 /* The analysis threads' cumulative seconds (summed over threads): building
  * request layouts, gathering a request's arrays into pinned memory, copying

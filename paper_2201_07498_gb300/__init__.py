@@ -116,8 +116,7 @@ _SIGS = {
                                            ctypes.c_void_p]),
     "te_server_classes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
-    "te_server_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "te_server_timing": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
     "te_server_analysis": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 7),
     "te_probe_gather": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "te_gram": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
@@ -501,10 +500,12 @@ class Server:
                 "pool_peak": peak.value}
 
     def timing(self):
-        """Cumulative host seconds: wait, admit, launch, submit."""
-        v = [ctypes.c_double() for _ in range(4)]
+        """Cumulative host seconds: wait, admit, launch, submit, and the
+        polls' copies and releases."""
+        v = [ctypes.c_double() for _ in range(6)]
         _check(self._lib.te_server_timing(self._h, *[ctypes.byref(x) for x in v]))
-        return {k: x.value for k, x in zip(("wait_s", "admit_s", "launch_s", "submit_s"), v)}
+        return {k: x.value for k, x in zip(("wait_s", "admit_s", "launch_s", "submit_s",
+                                            "poll_copy_s", "poll_free_s"), v)}
 
     def analysis(self):
         """Analysis threads' cumulative seconds (layout, gather into pinned

@@ -320,6 +320,7 @@ struct te_server {
   std::map<int, int> tuned;
   std::set<int> tuning;
   double t_wait = 0, t_admit = 0, t_launch = 0, t_submit = 0;  // host seconds, cumulative
+  double t_poll_copy = 0, t_poll_free = 0;  // polls: the Ritz vectors' copy, the request's release
   // analysis threads (nanoseconds, summed over threads): layout builds, the
   // gathers into the bounce buffers, the DMAs into the staging area, waits
   // for the staging turn or space; requests analysed
@@ -1157,12 +1158,14 @@ te_status te_server_step(te_server* S, int32_t* live_out, int32_t* pending_out) 
 }
 
 te_status te_server_timing(const te_server* S, double* wait_s, double* admit_s, double* launch_s,
-                           double* submit_s) {
+                           double* submit_s, double* poll_copy_s, double* poll_free_s) {
   if (!S) return srv_fail(TE_ERR_INVALID_ARG, "server is NULL");
   if (wait_s) *wait_s = S->t_wait;
   if (admit_s) *admit_s = S->t_admit;
   if (launch_s) *launch_s = S->t_launch;
   if (submit_s) *submit_s = S->t_submit;
+  if (poll_copy_s) *poll_copy_s = S->t_poll_copy;
+  if (poll_free_s) *poll_free_s = S->t_poll_free;
   return TE_OK;
 }
 
@@ -1190,6 +1193,7 @@ te_status te_server_poll(te_server* S, int64_t ticket, int32_t* done, double* ei
   if (R->state != REQ_FINISHED) return TE_OK;
   *done = 1;
   te_status st = (te_status)R->status;
+  const double p0 = now_s();
   if (R->res_bytes) {
     if ((st == TE_OK || st == TE_ERR_BREAKDOWN) && eigvecs) {
       cudaError_t e = cudaMemcpyAsync(eigvecs, S->pool.base + R->res_off, R->res_bytes,
@@ -1203,8 +1207,11 @@ te_status te_server_poll(te_server* S, int64_t ticket, int32_t* done, double* ei
     if (eigvals) memcpy(eigvals, R->theta.data(), sizeof(double) * R->K);
     if (residuals) memcpy(residuals, R->resid.data(), sizeof(double) * R->K);
   }
+  const double p1 = now_s();
   S->reqs.erase(it);
   delete R;
+  S->t_poll_copy += p1 - p0;
+  S->t_poll_free += now_s() - p1;
   if (st != TE_OK) return srv_fail(st, std::string("request failed: ") + te_status_string(st));
   return TE_OK;
 }
