@@ -16,7 +16,7 @@
 // a pair is rotated when |t_pq| > 1e-16 ||T||_F and the sweeps stop after
 // one without rotations.  Arithmetic is binary64.
 //
-// GB300 runs binary64 at two operations per SM and clock, so for m >= 24 the
+// GB300 runs binary64 at two operations per SM and clock, so for m >= 40 the
 // rounds are spread over a cluster of JAC_CLUSTER CTAs: every CTA keeps a full
 // copy of T, computes all rotations of a round (the same values everywhere),
 // updates the blocks e = rank (mod JAC_CLUSTER) and the rows of Y with the
@@ -36,7 +36,7 @@ constexpr int JAC_THREADS = 256;
 constexpr int JAC_MAX_SWEEPS = 100;
 constexpr int JLD = MAX_M + 1;  // padded row length in shared memory
 constexpr int JAC_CLUSTER = 8;  // CTAs of the cluster form (a portable cluster size)
-constexpr int JAC_CLUSTER_MIN_M = 24;  // smaller T: one CTA (barriers would dominate)
+constexpr int JAC_CLUSTER_MIN_M = 40;  // smaller T: one CTA (barriers would dominate)
 
 TE_DEV uint32_t cluster_ctarank() {
   uint32_t r;

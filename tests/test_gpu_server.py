@@ -242,3 +242,25 @@ def test_poll_into_pinned_buffer_and_many_finishing_together(te):
         alone.close()
         assert np.array_equal(ev, got[t][0]) and np.array_equal(U, got[t][1])
         assert np.array_equal(res, got[t][2])
+
+
+def test_server_counters(te):
+    """The engine's counters add up: every request is analysed once, each
+    step advances between one and max_slots solves, a solve of m steps is
+    advanced m times, and the host timers only grow."""
+    mats = _mix()[:3]
+    srv = te.Server(max_slots=8, max_krylov_steps=32, budget=1 << 30)
+    t0 = srv.timing()
+    tickets = [srv.submit(A, 4, 10, "fdf", seed=40 + i) for i, A in enumerate(mats)]
+    _drain(srv, list(tickets), vectors=True)
+    an, t1 = srv.analysis(), srv.timing()
+    srv.close()
+    assert an["analysed"] == len(mats)
+    assert an["engine_steps"] >= 10
+    assert an["resident_steps"] == 10 * len(mats)
+    assert an["engine_steps"] <= an["resident_steps"] <= 8 * an["engine_steps"]
+    for k in ("layout_s", "gather_s", "copy_s", "stage_wait_s"):
+        assert an[k] >= 0.0
+    for k in t1:
+        assert t1[k] >= t0[k] >= 0.0
+    assert t1["poll_copy_s"] > 0.0

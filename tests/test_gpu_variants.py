@@ -447,7 +447,7 @@ def test_expired_wait_returns_timeout_then_plan_recovers(te, prec, reorth):
 
 @pytest.mark.parametrize("m", [48, 64])
 def test_cluster_jacobi_is_repeatable(te, m):
-    """For m >= 24 the Jacobi phase runs on a cluster of eight CTAs that each
+    """For m >= 40 the Jacobi phase runs on a cluster of eight CTAs that each
     keep a copy of T and push their blocks into the others' copies.  A copy
     overwritten out of order (a missing barrier) would make launches disagree
     with each other under varying schedules; fifty launches must give the same
