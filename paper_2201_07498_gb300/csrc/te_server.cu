@@ -730,6 +730,28 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
   return 1;
 }
 
+// A request's Ritz vectors to a caller's pinned buffer, stored by a few SMs
+// through the buffer's device mapping (over NVLink-C2C): faster than a
+// device-to-host copy-engine transfer, and few enough CTAs to leave the
+// engine's kernels their SMs.
+constexpr int POLL_COPY_CTAS = 16;
+__global__ void __launch_bounds__(256) poll_copy_kernel(const double2* __restrict__ src,
+                                                        double2* __restrict__ dst, int64_t n2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// the device address of pinned host memory, else NULL (pageable memory)
+void* pinned_device_ptr(void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Jacobi, selection and Ritz vectors of a solve that completed its m steps,
 // then its eigenvalues, residual estimates and status to the pinned slot area
 cudaError_t enqueue_finish(te_server* S, Request* R, cudaStream_t fs) {
@@ -1196,8 +1218,18 @@ te_status te_server_poll(te_server* S, int64_t ticket, int32_t* done, double* ei
   const double p0 = now_s();
   if (R->res_bytes) {
     if ((st == TE_OK || st == TE_ERR_BREAKDOWN) && eigvecs) {
-      cudaError_t e = cudaMemcpyAsync(eigvecs, S->pool.base + R->res_off, R->res_bytes,
-                                      cudaMemcpyDeviceToHost, S->ps);
+      cudaError_t e = cudaSuccess;
+      void* mapped = pinned_device_ptr(eigvecs);
+      const char* src = S->pool.base + R->res_off;
+      if (mapped && ((reinterpret_cast<uintptr_t>(mapped) | reinterpret_cast<uintptr_t>(src)) &
+                     15) == 0 && R->res_bytes % 16 == 0) {
+        poll_copy_kernel<<<POLL_COPY_CTAS, 256, 0, S->ps>>>(
+            reinterpret_cast<const double2*>(src), static_cast<double2*>(mapped),
+            (int64_t)(R->res_bytes / 16));
+        e = cudaGetLastError();
+      } else {
+        e = cudaMemcpyAsync(eigvecs, src, R->res_bytes, cudaMemcpyDeviceToHost, S->ps);
+      }
       if (e == cudaSuccess) e = cudaStreamSynchronize(S->ps);
       if (e != cudaSuccess) return srv_cuda(e, "copy the Ritz vectors");
     }
