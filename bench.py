@@ -566,7 +566,8 @@ def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000
             seed=4):
     """Continuous-batching serving: Poisson arrivals of solve requests drawn
     from synth's serving mix (n log-uniform in [2^10, 2^18], degree 4-64,
-    uniform or R-MAT, K in {4, 8, 16}, m = 2K, binary32 or bfloat16 values).
+    uniform or R-MAT, K in {4, 8, 16}, m = 2K, binary32 or bfloat16 values;
+    binary32 requests carry binary32 values, bfloat16 ones binary64 values).
     `npool` distinct matrices are generated and request i solves matrix
     i mod npool (with its own K, m, form) from its own start vector (seed i);
     `nreq_high` requests arrive at rates >= 1000/s and `nreq_low` at lower
@@ -580,7 +581,10 @@ def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000
     import numpy as np
     import synth
     t0 = time.perf_counter()
-    pool = synth.serving_requests(npool, seed)
+    # the binary32-storage requests arrive with binary32 values, the bfloat16
+    # ones with binary64 values (the library rounds them)
+    pool = [(A.with_f32_values() if prec == "fdf" else A, K, m, prec)
+            for A, K, m, prec in synth.serving_requests(npool, seed)]
     gen_s = time.perf_counter() - t0
     nnz = [int(A.nnz) for A, _, _, _ in pool]
     out = {"workload": f"serving_mix_seed{seed}", "distinct_matrices": npool,

@@ -418,14 +418,17 @@ class Server:
         self._meta = {}
 
     def submit(self, host_csr, K: int, krylov_steps: int, precision="fdf", seed: int = 0) -> int:
-        """host_csr: an object with n, row_ptr, col, val (numpy); the values are
-        passed as binary64 (the library rounds them to the form's type)."""
+        """host_csr: an object with n, row_ptr, col, val (numpy).  Binary32
+        values of a binary32-storage request ("fdf") are passed as they are;
+        otherwise the values go as binary64 and the library rounds them to
+        the form's type."""
         import numpy as np
         rp = np.ascontiguousarray(host_csr.row_ptr, dtype=np.int64)
         ci = np.ascontiguousarray(host_csr.col, dtype=np.int32)
-        va = np.ascontiguousarray(host_csr.val, dtype=np.float64)
+        f32 = np.asarray(host_csr.val).dtype == np.float32 and _prec(precision).values == 1
+        va = np.ascontiguousarray(host_csr.val, dtype=np.float32 if f32 else np.float64)
         A = te_csr(int(host_csr.n), len(ci), rp.ctypes.data, ci.ctypes.data, va.ctypes.data,
-                   None, TE_HOST, 1)
+                   None, TE_HOST, 0 if f32 else 1)
         t = ctypes.c_int64()
         _check(self._lib.te_server_submit(self._h, ctypes.byref(A), K, krylov_steps,
                                           _prec(precision), seed, ctypes.byref(t)))

@@ -264,3 +264,17 @@ def test_server_counters(te):
     for k in t1:
         assert t1[k] >= t0[k] >= 0.0
     assert t1["poll_copy_s"] > 0.0
+
+
+def test_binary32_values_equal_binary64_submission(te):
+    """A binary32-storage request submitted with binary32 values gives the
+    same bits as one submitted with binary64 values (the library's rounding
+    is round to nearest even, the same as the caller's)."""
+    A = synth.rmat_sym(12, 8, 21)
+    srv = te.Server(max_slots=4, max_krylov_steps=32, budget=256 << 20)
+    t64 = srv.submit(A, 6, 12, "fdf", seed=5)
+    t32 = srv.submit(A.with_f32_values(), 6, 12, "fdf", seed=5)
+    out = _drain(srv, [t64, t32])
+    srv.close()
+    for a, b in zip(out[t64], out[t32]):
+        assert np.array_equal(a, b)
