@@ -563,7 +563,7 @@ def out_of_core(te, world, steps=2, warmup=1):
 
 
 def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000, 5000),
-            seed=4):
+            seed=4, max_slots=64):
     """Continuous-batching serving: Poisson arrivals of solve requests drawn
     from synth's serving mix (n log-uniform in [2^10, 2^18], degree 4-64,
     uniform or R-MAT, K in {4, 8, 16}, m = 2K, binary32 or bfloat16 values;
@@ -593,7 +593,7 @@ def serving(te, nreq_high, nreq_low=1000, npool=256, rates=(100, 300, 1000, 3000
     rng = np.random.default_rng(seed + 1)
     # one long-running server with the per-class layout autotuner; a warm-up
     # pass over the pool lets it tune every request class first
-    srv = te.Server(max_slots=64, max_krylov_steps=32, budget=24 << 30, autotune=True)
+    srv = te.Server(max_slots=max_slots, max_krylov_steps=32, budget=24 << 30, autotune=True)
     # the client collects each request's Ritz vectors into one pinned buffer
     import torch
     ubuf = torch.empty(max(A.n * K for A, K, _, _ in pool), dtype=torch.float64).pin_memory()
