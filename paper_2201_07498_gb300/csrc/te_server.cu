@@ -138,6 +138,10 @@ struct Request {
   // layout candidate `cand` of the autotuner's list)
   SellHost layout;
   int cand = 0;
+  // its sizes (from the host build, or from the device build, which fills
+  // the staged arrays directly and leaves `layout` empty)
+  size_t ls_slices = 0, ls_lanes = 0, ls_lrows = 0;
+  int64_t ls_entries = 0, ls_pieces = 0;
   // the CSR and the layout copied to the device staging area by the analysis
   // thread (stage_bytes = 0: not staged; admission copies from the host)
   int64_t seq = 0;  // submission order
@@ -402,8 +406,7 @@ StageLayout stage_offsets(const Request& R, size_t lanes, size_t slices, size_t 
 }
 // the offsets of R's built layout
 StageLayout stage_layout(const Request& R) {
-  const SellHost& H = R.layout;
-  return stage_offsets(R, H.vout.size(), H.slices.size(), H.lrows.size());
+  return stage_offsets(R, R.ls_lanes, R.ls_slices, R.ls_lrows);
 }
 // a block that holds R's arrays under any candidate layout: a row of length
 // L > 0 gives at most L / vmax + 1 pieces, a window's pieces fill their
@@ -498,6 +501,75 @@ void stage_fill(te_server* S, Request* R, cudaStream_t ts, Bounce* B) {
   }
 }
 
+// The request's CSR staged, then its SpMV layout built by the device layout
+// kernels straight into its staging block (the same arrangement as
+// make_sell's, element for element): the analysis thread only issues the
+// copies and the kernels.  False (nothing recorded) when the request is not
+// staged, the sizes are beyond the device build, or a call fails; the
+// thread then builds the layout on the host.
+bool analyse_on_device(te_server* S, Request* R, cudaStream_t ts, Bounce* B, int window,
+                       int vmax) {
+  if (!R->stage_bytes || !dev_layout_fits(R->n, window, vmax)) return false;
+  const StageLayout L0 = stage_offsets(*R, 0, 0, 0);  // the CSR's offsets
+  const size_t csr_bytes = L0.val + R->val_bytes;
+  char* G = S->stage.base + R->stage_off;
+  const double c0 = now_s();
+  cudaError_t e = cudaSuccess;
+  if (csr_bytes <= BOUNCE_MAX && B->reserve(csr_bytes)) {
+    std::memcpy(B->p + L0.rp, R->rp, (size_t)(R->n + 1) * 8);
+    if (R->nnz) std::memcpy(B->p + L0.ci, R->ci, (size_t)R->nnz * 4);
+    if (R->val_bytes) std::memcpy(B->p + L0.val, R->vals, R->val_bytes);
+    S->a_gather_ns += (int64_t)((now_s() - c0) * 1e9);
+    e = cudaMemcpyAsync(G, B->p, csr_bytes, cudaMemcpyHostToDevice, ts);
+  } else {
+    e = cudaMemcpyAsync(G + L0.rp, R->rp, (size_t)(R->n + 1) * 8, cudaMemcpyHostToDevice, ts);
+    if (e == cudaSuccess && R->nnz)
+      e = cudaMemcpyAsync(G + L0.ci, R->ci, (size_t)R->nnz * 4, cudaMemcpyHostToDevice, ts);
+    if (e == cudaSuccess && R->val_bytes)
+      e = cudaMemcpyAsync(G + L0.val, R->vals, R->val_bytes, cudaMemcpyHostToDevice, ts);
+  }
+  const double c1 = now_s();
+  DevLayout DL;
+  std::string err;
+  int64_t tot[4] = {0, 0, 0, 0};
+  char* tmp = nullptr;
+  int nbig = 0;
+  bool ok = false;
+  if (e == cudaSuccess)
+    e = DL.count(reinterpret_cast<const int64_t*>(G + L0.rp), R->n, R->nnz, window, vmax, false,
+                 ts, err);
+  if (e == cudaSuccess) e = DL.windows(ts, tot);
+  StageLayout L{};
+  if (e == cudaSuccess) {
+    L = stage_offsets(*R, (size_t)tot[0] * SELL_C, (size_t)tot[0], (size_t)tot[3]);
+    ok = L.total <= R->stage_bytes;
+  }
+  if (ok) e = dev_alloc(&tmp, (size_t)std::max<int64_t>(tot[3], 1) * sizeof(LongRow));
+  if (ok && e == cudaSuccess)
+    e = DL.emit(reinterpret_cast<SellSlice*>(G + L.sl), reinterpret_cast<int32_t*>(G + L.out),
+                reinterpret_cast<int64_t*>(G + L.src), reinterpret_cast<int32_t*>(G + L.len),
+                nullptr, reinterpret_cast<LongRow*>(G + L.lr), reinterpret_cast<LongRow*>(tmp),
+                ts, &nbig);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ts);
+  // the scratch goes back to the pool in stream order (no device-wide wait)
+  if (tmp) dev_free_on(tmp, ts);
+  if (DL.scratch) {
+    dev_free_on(DL.scratch, ts);
+    DL.scratch = nullptr;
+  }
+  S->a_layout_ns += (int64_t)((now_s() - c1) * 1e9);
+  if (e != cudaSuccess || !ok) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  R->ls_slices = (size_t)tot[0];
+  R->ls_lanes = (size_t)tot[0] * SELL_C;
+  R->ls_lrows = (size_t)tot[3];
+  R->ls_entries = tot[1];
+  R->ls_pieces = tot[2];
+  return true;
+}
+
 // An analysis thread's work: the request's layout, with its class's tuned
 // candidate when the server tunes (the class's first request is tuned here;
 // others of the class wait for it), then its staging
@@ -527,9 +599,22 @@ void analyse_request(te_server* S, Request* R, cudaStream_t ts, Bounce* B) {
       S->tune_cv.wait(lk);
     }
   }
+  R->cand = cand;
+  if (analyse_on_device(S, R, ts, B, TUNE_WINDOW[cand], TUNE_VMAX[cand])) {
+    S->a_count += 1;
+    return;
+  }
   std::string perr;
   const double t0 = now_s();
   make_sell(R->rp, R->n, R->nnz, R->layout, perr, TUNE_WINDOW[cand], TUNE_VMAX[cand]);
+  {
+    const SellHost& H = R->layout;
+    R->ls_slices = H.slices.size();
+    R->ls_lanes = H.vout.size();
+    R->ls_lrows = H.lrows.size();
+    R->ls_entries = H.entries;
+    R->ls_pieces = H.pieces;
+  }
   S->a_layout_ns += (int64_t)((now_s() - t0) * 1e9);
   R->cand = cand;
   stage_fill(S, R, ts, B);
@@ -565,12 +650,12 @@ AdmitLayout admit_layout(const Request& R, const SellHost& H) {
     return o;
   };
   const size_t velt = R.vk == TE_BF16 ? 2 : 4;
-  L.slices = take(H.slices.size() * sizeof(SellSlice));
-  L.vout = take(H.vout.size() * sizeof(int32_t));
-  L.cols = take((size_t)H.entries * 4);
-  L.vals = take((size_t)H.entries * velt);
-  L.lrows = take(H.lrows.size() * sizeof(LongRow));
-  L.vpart = take((size_t)H.pieces * 8);
+  L.slices = take(R.ls_slices * sizeof(SellSlice));
+  L.vout = take(R.ls_lanes * sizeof(int32_t));
+  L.cols = take((size_t)R.ls_entries * 4);
+  L.vals = take((size_t)R.ls_entries * velt);
+  L.lrows = take(R.ls_lrows * sizeof(LongRow));
+  L.vpart = take((size_t)R.ls_pieces * 8);
   L.V = take((size_t)R.n_pad * (R.m + 1) * 4);
   L.ytil = take((size_t)R.n_pad * 8);
   L.w = take((size_t)R.n_pad * 8);
@@ -582,8 +667,8 @@ AdmitLayout admit_layout(const Request& R, const SellHost& H) {
   L.t_rp = take(staged ? 0 : (size_t)(R.n + 1) * 8);
   L.t_ci = take(staged ? 0 : (size_t)R.nnz * 4);
   L.t_val = take(staged ? 0 : (size_t)R.nnz * (R.in_type == TE_F64 ? 8 : 4));
-  L.t_src = take(staged ? 0 : H.vsrc.size() * 8);
-  L.t_len = take(staged ? 0 : H.vlen.size() * 4);
+  L.t_src = take(staged ? 0 : R.ls_lanes * 8);
+  L.t_len = take(staged ? 0 : R.ls_lanes * 4);
   L.t_q = take(R.vk == TE_BF16 ? (size_t)R.nnz * 2 : 0);
   L.t_total = off;
   return L;
@@ -644,9 +729,9 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
     auto d2d = [&](void* dst, const void* src, size_t b) {
       if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToDevice, s);
     };
-    d2d(W + L.slices, GB + G.sl, H.slices.size() * sizeof(SellSlice));
-    d2d(W + L.vout, GB + G.out, H.vout.size() * 4);
-    d2d(W + L.lrows, GB + G.lr, H.lrows.size() * sizeof(LongRow));
+    d2d(W + L.slices, GB + G.sl, R->ls_slices * sizeof(SellSlice));
+    d2d(W + L.vout, GB + G.out, R->ls_lanes * 4);
+    d2d(W + L.lrows, GB + G.lr, R->ls_lrows * sizeof(LongRow));
   } else {
     h2d(W + L.slices, H.slices.data(), H.slices.size() * sizeof(SellSlice));
     h2d(W + L.vout, H.vout.data(), H.vout.size() * 4);
@@ -662,11 +747,11 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
   }
   if (e == cudaSuccess)
     e = launch_sell_fill_cols(dci, reinterpret_cast<const SellSlice*>(W + L.slices), dsrc, dlen,
-                              (int)H.slices.size(), reinterpret_cast<int32_t*>(W + L.cols),
+                              (int)R->ls_slices, reinterpret_cast<int32_t*>(W + L.cols),
                               nullptr, nullptr, s);
   if (e == cudaSuccess)
     e = launch_sell_fill_vals(in_type, R->vk, vin, reinterpret_cast<const SellSlice*>(W + L.slices),
-                              dsrc, dlen, (int)H.slices.size(), W + L.vals, nullptr, nullptr,
+                              dsrc, dlen, (int)R->ls_slices, W + L.vals, nullptr, nullptr,
                               nullptr, nullptr, s);
   LzState* st = reinterpret_cast<LzState*>(W + L.st);
   double* U = reinterpret_cast<double*>(S->pool.base + res);
@@ -689,8 +774,8 @@ int admit(te_server* S, Request* R, int k, te_status* err) {
   B.seed = R->seed;
   B.tol = breakdown_tolerance(PREC_FDF);
   B.vk = R->vk;
-  B.nslices = (int)H.slices.size();
-  B.nlrows = (int)H.lrows.size();
+  B.nslices = (int)R->ls_slices;
+  B.nlrows = (int)R->ls_lrows;
   B.m = R->m;
   B.K = R->K;
   B.step = 0;
