@@ -14,7 +14,9 @@
 // t = sgn(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = t c
 // (evaluated as |2 t_pq| sgn(zeta) / (|d| + hypot(d, 2 t_pq)), d = t_qq - t_pp);
 // a pair is rotated when |t_pq| > 1e-16 ||T||_F and the sweeps stop after
-// one without rotations.  Arithmetic is binary64.
+// one without rotations (which is skipped when no off-diagonal element left
+// after a sweep exceeds that threshold: it could rotate nothing).
+// Arithmetic is binary64.
 //
 // GB300 runs binary64 at two operations per SM and clock, so for m >= 40 the
 // rounds are spread over a cluster of JAC_CLUSTER CTAs: every CTA keeps a full
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(JacobiArgs a) {
   __shared__ int any_rot;
   __shared__ int sel[MAX_M];
   __shared__ double thr_s;
+  __shared__ double off_part[JAC_THREADS];  // the off-diagonal check's partial maxima
   // the (a, b) pair indices of block e, a <= b, row-major upper triangle
   constexpr int MAX_BLK = MAX_M / 2 * (MAX_M / 2 + 1) / 2;
   __shared__ unsigned char blk_a[MAX_BLK], blk_b[MAX_BLK];
@@ -246,6 +249,27 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_kernel(JacobiArgs a) {
       }
     }
     if (!any_rot) break;
+    // When no |t_pq| off the diagonal exceeds thr, the next sweep's first
+    // round rotates nothing, so T stays as it is and no later round rotates
+    // either: that sweep is skipped (same bits, and the same sweep count).
+    // The CTAs of a cluster hold the same T and all take the same decision.
+    {
+      double mx = 0.0;
+      for (int e = tid; e < m * m; e += JAC_THREADS) {
+        const int r = e / m, c = e - r * m;
+        if (r != c) mx = fmax(mx, fabs(T[r * JLD + c]));
+      }
+      off_part[tid] = mx;
+      __syncthreads();
+      for (int w = JAC_THREADS / 2; w > 0; w >>= 1) {
+        if (tid < w) off_part[tid] = fmax(off_part[tid], off_part[tid + w]);
+        __syncthreads();
+      }
+      if (off_part[0] <= thr) {
+        ++sweep;
+        break;
+      }
+    }
     __syncthreads();
   }
   if constexpr (CL > 1) {
