@@ -66,7 +66,8 @@ def _expected(rp, window, vmax, order):
 
 
 @pytest.mark.parametrize("order", ["keep", "degree"])
-@pytest.mark.parametrize("window,vmax", [(2048, 64), (2048, 128), (256, 32), (7, 5)])
+@pytest.mark.parametrize("window,vmax", [(2048, 64), (2048, 128), (2048, 32), (256, 64), (16384, 64),
+                                         (256, 32), (7, 5)])
 def test_device_layout_equals_the_plain_arrangement(te, order, window, vmax):
     for name, rp in _row_ptrs().items():
         nnz = int(rp[-1])
